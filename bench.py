@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of one hybridised solve (configuration 3c) on synthetic cubed-sphere meshes.
+
+A step is one call of the library's solve: B_lambda, right-preconditioned BiCGStab under
+the non-nested two-level cycle to a 1e-6 relative trace residual, and the FP64 recomputation
+of the final residual. Inputs (mesh, background, right-hand side) are resident in HBM before
+the timed region; the working set (S alone: 11 x 8 B per trace row) is far larger than L2,
+so no flush is needed between steps.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-6 rel. trace residual, unknowns/s, HBM roofline fraction"
+UNIT = "trace unknowns/s"
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture (see profiles/), keyed
+# by the sha256 of the kernel sources it was taken on; a changed source makes it stale (null).
+TRAFFIC = {}
+
+
+def workload_spec(name: str):
+    from paper_2210_11797_gb300 import inputs as I
+    if name.startswith("c"):          # cubed sphere C<N>, 30 quadratically stretched levels
+        n = int(name[1:])
+        return I.cubed_sphere(n, 30, tol=1e-6)
+    if name == "planar16":
+        return I.planar_helmholtz()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("trace_ops.cu", "device_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2210_11797_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def sweep_bytes(mesh, elem=8):
+    """Algorithmic bytes of one full line-smoother sweep (Algorithm 1, fused residual):
+    every nonzero of S once, lambda_in, b and lambda_out once, the two Thomas factors of
+    each lambda^z row, 1/diag of each lambda^h row, and the index tables."""
+    L, NH, NZ, T = mesh.nlev, mesh.n_trace_h, mesh.n_trace_z, mesh.n_trace
+    nnz = 11 * NH + mesh.ncol * (11 * (L - 1) + 2 * 6)
+    return elem * (nnz + 3 * T + 2 * NZ + NH) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
+
+
+def spmv_bytes(mesh, elem=8):
+    L, NH, T = mesh.nlev, mesh.n_trace_h, mesh.n_trace
+    nnz = 11 * NH + mesh.ncol * (11 * (L - 1) + 2 * 6)
+    return elem * (nnz + 2 * T) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sms.append(float(p[1]))
+                maxes.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2210_11797_gb300.hmg import Solver
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = workload_spec(args.workload)
+    if rank:                                   # replicas: independent right-hand sides
+        from paper_2210_11797_gb300 import inputs as I
+        w.Rub, w.Rpi = I.draw_rhs(w.mesh.ncell, rank, "normal")
+    stream = torch.cuda.current_stream()
+    solver = Solver(w.hier, w.coeffs, tol=w.tol, precision=args.precision, profile=1)
+    Rub = torch.as_tensor(w.Rub.ravel()).cuda()
+    Rpi = torch.as_tensor(w.Rpi).cuda()
+    lam = torch.empty(solver.ntrace, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        solver.solve(Rub, Rpi, lam)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            _l, st = solver.solve(Rub, Rpi, lam)
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    T = solver.ntrace
+    value = world * T / (ms_step / 1e3)
+    # per-component device times over the timed region
+    comp = {}
+    for st in stats:
+        for k, v in st["components"].items():
+            c = comp.setdefault(k, {"ms": 0.0, "launches": 0})
+            c["ms"] += v["ms"]
+            c["launches"] += v["launches"]
+    launches = sum(v["launches"] for v in comp.values())
+    dom = max(("line_sweep", "trace_apply"), key=lambda k: comp[k]["ms"])
+    elem = 8 if args.precision == "fp64" else 4
+    nbytes = sweep_bytes(w.mesh, elem) if dom == "line_sweep" else spmv_bytes(w.mesh, 8)
+    per_launch_ms = comp[dom]["ms"] / max(comp[dom]["launches"], 1)
+    achieved = nbytes / (per_launch_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    key = f"{dom}:{args.workload}:{args.precision}:{kernel_source_hash()}"
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": TRAFFIC.get(key), "algorithmic_bytes": nbytes,
+                "avg_launch_ms": round(per_launch_ms, 5)}
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Rub_h = torch.empty(Rub.numel(), dtype=torch.float64).pin_memory()
+    Rpi_h = torch.empty(Rpi.numel(), dtype=torch.float64).pin_memory()
+    Rub_h.copy_(torch.as_tensor(w.Rub.ravel()))
+    Rpi_h.copy_(torch.as_tensor(w.Rpi))
+    solver.set_options(profile=0)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lam_h, st_h = solver.solve_host(Rub_h.numpy(), Rpi_h.numpy())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    its = [s["iterations"] for s in stats]
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "mesh": f"cubed sphere C{w.mesh.n_per_side}, {w.mesh.nlev} quadratic levels",
+                   "ncell": w.mesh.ncell, "ntrace": T, "mg_levels": w.hier.nmg, "tol": w.tol,
+                   "precision": args.precision, "precond": "non-nested two-level (3c)",
+                   "iterations": its[0] if len(set(its)) == 1 else its,
+                   "true_rel_residual": stats[-1]["true_rel_residual"],
+                   "l2": "working set > L2 (S alone %.0f MB); no flush" % (11 * T * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "time_to_tol_ms": round(ms_step, 4),
+        "components_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in comp.items()},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "e2e": {"value": round(world * T / (e2e_ms / 1e3), 1), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * 7 * w.mesh.ncell, "d2h_bytes_per_step": 8 * T,
+                "ms_per_step": round(e2e_ms, 4)},
+        "clocks": clk.summary(),
+    }
+    solver.close()
+    return out
+
+
+def oracle_sample(workload: str, steps: int, warmup: int, seconds: float | None, its=None):
+    """Time the FP64 CPU oracle on the same workload: setup untimed; each step is
+    B_lambda plus one BiCGStab iteration of its solve, and unknowns/s is scaled by the
+    iteration count the oracle needs to reach the tolerance."""
+    import numpy as np
+    from oracle.nonnested import HybridSolver
+    w = workload_spec(workload)
+    t0 = time.perf_counter()
+    s = HybridSolver(w.hier, w.coeffs)
+    setup_s = time.perf_counter() - t0
+    B = s.rhs(w.Rub, w.Rpi)
+    t_rhs = []
+    t_it = []
+    its_needed = its
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        B = s.rhs(w.Rub, w.Rpi)
+        t1 = time.perf_counter()
+        _lam, hist, _st = s.solve_trace(B, 0.0, maxit=1)    # one iteration, no early exit
+        t2 = time.perf_counter()
+        if i >= warmup:
+            t_rhs.append(t1 - t0)
+            t_it.append(t2 - t1)
+        if seconds is not None and sum(t_rhs) + sum(t_it) > seconds and i >= warmup:
+            break
+    # iterations to the tolerance: given (the GPU arm passes its own count; the algorithm and
+    # the counts are the same, as the parity tests check), else one full oracle solve
+    if its_needed is None:
+        _lam, hist, _st = s.solve_trace(B, w.tol)
+        its_needed = len(hist) - 1
+    step_s = statistics.median(t_rhs) + its_needed * statistics.median(t_it)
+    return {"workload": w.name, "T": w.mesh.n_trace, "setup_s": setup_s, "rhs_s": statistics.median(t_rhs),
+            "iter_s": statistics.median(t_it), "its": its_needed, "step_s": step_s,
+            "samples": len(t_it), "value": w.mesh.n_trace / step_s}
+
+
+def run_oracle_subprocess(workload, steps, warmup, seconds, its=None):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-child", "--workload", workload,
+           "--steps", str(steps), "--warmup", str(warmup)]
+    if seconds is not None:
+        cmd += ["--_seconds", str(seconds)]
+    if its is not None:
+        cmd += ["--_its", str(its)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c96")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--_seconds", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--_its", type=int, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args._oracle_child:
+        print(json.dumps(oracle_sample(args.workload, args.steps, args.warmup, args._seconds, args._its)))
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = run_oracle_subprocess(args.workload, args.steps, args.warmup, None)
+        out = {"impl": "reference", "metric": METRIC, "value": round(r["value"], 1), "unit": UNIT,
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(r["step_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": r["workload"], "ntrace": r["T"], "tol": 1e-6},
+               "cpu_baseline": {"value": round(r["value"], 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"B_lambda + 1 of {r['its']} BiCGStab iterations per step "
+                                          f"({r['samples']} steps; setup {r['setup_s']:.0f} s untimed)"},
+               "e2e": {"value": round(r["value"], 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its = out["config"]["iterations"]
+        r = run_oracle_subprocess(args.workload, 3, 1, 30.0, its if isinstance(its, int) else max(its))
+        out["cpu_baseline"] = {"value": round(r["value"], 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{r['workload']}: B_lambda + {r['samples']} sampled BiCGStab "
+                                         f"iterations, scaled to the {r['its']} iterations to 1e-6; "
+                                         f"setup {r['setup_s']:.0f} s untimed"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * hmg.h - C ABI of a GB300 (sm_103a) library for the hybridised non-nested multigrid
+ * solve of the lowest-order compatible finite element system of
+ *   Betteridge, Cotter, Gibson, Griffith, Melvin, Mueller, "Hybridised multigrid
+ *   preconditioners for a compatible finite element dynamical core" (arXiv 2210.11797).
+ *
+ * One context holds one extruded mesh (with its pressure-multigrid hierarchy), one set of
+ * background coefficients, the assembled trace operator S and the preconditioner data.
+ * A solve takes the cell residuals (R_u^b, R_Pi) and returns the trace multipliers lambda
+ * of S lambda = B_lambda (Eq. hybrid_equation), using BiCGStab preconditioned by the
+ * non-nested two-level cycle (Algorithm 2) with one pressure V-cycle (configuration 3c).
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns an int status (HMG_OK = 0). Nothing aborts; device code
+ *    never traps. hmg_last_error() gives a one-line description of the last failure.
+ *  - Pointers: "host" pointers are read (or written) during the call only and stay owned
+ *    by the caller. "device" pointers are caller-owned CUDA global memory on the
+ *    context's device (e.g. torch.Tensor.data_ptr()); work on them is ordered on the
+ *    context's stream and the call returns after that work has completed.
+ *  - The library allocates device memory in hmg_set_mesh, hmg_set_coefficients and
+ *    hmg_assemble_trace only; solve/apply/reconstruct allocate nothing.
+ *  - Numbering: cells K = column * nlev + level (level 0 at the ground); local faces
+ *    e0..e3 (vertical, along the column corners counter-clockwise seen from above: e0 =
+ *    corner0->corner1, e1 = corner1->corner2, e2 = corner2->corner3, e3 = corner3->corner0),
+ *    then bottom (4) and top (5). Trace dofs lambda = [lambda^h: edge * nlev + level |
+ *    lambda^z: nedge * nlev + column * (nlev + 1) + interface], interfaces 0..nlev.
+ *  - All arithmetic of the FP64 path is IEEE double; results agree with a plain CPU
+ *    implementation up to rounding order, not bit for bit.
+ */
+#ifndef HMG_H
+#define HMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define HMG_OK 0
+#define HMG_ERR_INVALID_ARG 1   /* bad size, pointer, table entry or option */
+#define HMG_ERR_CUDA 2          /* a CUDA runtime call failed (message in hmg_last_error) */
+#define HMG_ERR_NOT_READY 3     /* mesh, coefficients or assembly missing */
+#define HMG_ERR_NOT_CONVERGED 4 /* max_iter reached or divergence detected */
+#define HMG_ERR_BREAKDOWN 5     /* BiCGStab breakdown: (rhat, v) = 0 or (t, t) = 0 */
+#define HMG_ERR_NONFINITE 6     /* NaN or Inf in the iteration */
+#define HMG_ERR_TIMEOUT 7       /* a bounded device-side wait expired */
+#define HMG_ERR_OUT_OF_MEMORY 8 /* device allocation failed */
+
+typedef struct hmg_ctx hmg_ctx; /* opaque, owned by the library */
+
+/* ---- inputs ------------------------------------------------------------------------ */
+
+/* One level of the extruded mesh (finest first). All pointers are host pointers, copied
+ * by hmg_set_mesh. The geometry follows Sec. 2.2 (hexahedral cells of an extruded mesh,
+ * here with trilinear cells between the level heights). */
+typedef struct {
+  int32_t geometry;          /* 0: planar, corners are (x, y, 0); 1: sphere, corners are
+                                unit vectors and a vertex at height z is corner*(radius+z) */
+  int32_t ncol, nlev, nedge; /* columns, layers, vertical edges (faces between columns) */
+  double radius;             /* sphere radius (geometry 1) */
+  const double *corners;     /* [ncol][4][3] column corners, counter-clockwise from above */
+  const double *z_levels;    /* [nlev+1] level heights, strictly increasing */
+  const int32_t *col_edges;  /* [ncol][4] edge of local face e0..e3 */
+  const int32_t *edge_cols;  /* [nedge][2] the two columns; the first is the edge's owner */
+  const int8_t *edge_face;   /* [nedge][2] local face index (0..3) in each column */
+  const int32_t *parent;     /* [ncol] column of the next coarser level containing this one
+                                (2x2 agglomeration); NULL on the coarsest level */
+} hmg_mesh_level;
+
+/* Background reference state of one multigrid level (Sec. 2.1-2.2): theta* and the
+ * W_theta projection of Exner* at level heights, Exner* at cell centres. Host pointers. */
+typedef struct {
+  const double *theta_lev; /* [ncol][nlev+1] */
+  const double *exner_lev; /* [ncol][nlev+1] */
+  const double *exner;     /* [ncol][nlev]   */
+} hmg_background;
+
+/* Scalars of Eqs. gh-u .. gh-pi. preset 0: the physical operator with theta elimination
+ * (Eq. 2x2system); preset 1: the constant-coefficient Helmholtz operator with
+ * G_K = -1, B_K = 1, K_K = I and M3^Pi = sigma |K| (no buoyancy terms). */
+typedef struct {
+  double dt, tau_u, tau_rho, tau_theta, cp, kappa;
+  int32_t preset;
+  double sigma;
+} hmg_scalars;
+
+/* ---- options ----------------------------------------------------------------------- */
+#define HMG_PRECISION_FP64 0   /* everything in FP64 */
+#define HMG_PRECISION_MIXED 1  /* preconditioner in FP32, Krylov and S apply in FP64 */
+#define HMG_PRECOND_NONE 0
+#define HMG_PRECOND_LINESMOOTH 1 /* configuration 2: Algorithm 1 from zero, n_smooth sweeps */
+#define HMG_PRECOND_NONNESTED 2  /* configuration 3c: Algorithm 2 with one pressure V-cycle */
+
+typedef struct {
+  int32_t precision;    /* HMG_PRECISION_* */
+  int32_t precond;      /* HMG_PRECOND_* */
+  int32_t n_pre, n_post; /* trace smoother sweeps around the coarse correction (1, 2) */
+  int32_t n_smooth;     /* sweeps of the single-level preconditioner (1) */
+  double omega;         /* trace smoother relaxation (0.6) */
+  int32_t mg_npre, mg_npost, mg_ncoarse; /* pressure MG sweeps (1, 2, 3 on the coarsest) */
+  double mg_omega;      /* pressure block-Jacobi relaxation (0.9) */
+  double tol;           /* relative residual ||B - S lambda|| / ||B|| to stop (1e-6) */
+  int32_t max_iter;     /* BiCGStab iterations (200) */
+  double divergence;    /* stop with NOT_CONVERGED if ||r|| > divergence * ||B|| (1e3) */
+  int32_t profile;      /* 1: time every solver component with CUDA events (see
+                           hmg_solve_stats.comp_ms); 0: no events (default) */
+} hmg_options;
+
+#define HMG_MAX_HISTORY 512
+/* Solver components timed when hmg_options.profile = 1 (cf. Table time_in_components):
+ * 0 B_lambda (forward substitution), 1 S apply in the Krylov loop (hybridised operator),
+ * 2 presmoothing sweep from zero, 3 full line-smoother sweeps (Algorithm 1),
+ * 4 trace residual + restriction + Gamma (Algorithm 2 lines 3-5), 5 pressure V-cycle,
+ * 6 prolongation (Algorithm 2 line 7), 7 Krylov vector updates and inner products. */
+#define HMG_NCOMP 8
+typedef struct {
+  int32_t status;            /* HMG_OK or the reason the iteration stopped */
+  int32_t iterations;        /* completed BiCGStab iterations */
+  double rel_residual;       /* recurrence residual ||r_i|| / ||B|| at exit */
+  double true_rel_residual;  /* ||B - S lambda|| / ||B|| recomputed in FP64 at exit */
+  double solve_ms;           /* device time of the call (CUDA events on the stream) */
+  int32_t n_history;         /* entries of history[] used: ||r_i|| / ||B||, i = 0.. */
+  double history[HMG_MAX_HISTORY];
+  double comp_ms[HMG_NCOMP]; /* device time per component (profile = 1), else 0 */
+  int32_t comp_calls[HMG_NCOMP]; /* kernel launches per component (profile = 1) */
+} hmg_solve_stats;
+
+/* ---- lifecycle --------------------------------------------------------------------- */
+
+/* Fill *opt with the paper's settings (Sec. 3.2): omega 0.6, 1 pre / 2 post sweeps,
+ * pressure MG omega 0.9 with 1 pre / 2 post sweeps, tol 1e-6, FP64, configuration 3c. */
+int hmg_default_options(hmg_options *opt);
+
+/* Create a context on the current CUDA device. opt: host, copied (NULL = defaults).
+ * cuda_stream: a cudaStream_t owned by the caller (NULL = the legacy default stream). */
+int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream);
+
+/* Replace the options (e.g. the tolerance or precision) without reassembling, except that
+ * switching to HMG_PRECISION_MIXED needs hmg_assemble_trace to build the FP32 copies. */
+int hmg_set_options(hmg_ctx *ctx, const hmg_options *opt);
+
+/* Set the mesh hierarchy: levels[0] finest ... levels[nmg-1] coarsest; every level has
+ * the same nlev, level l+1 has ncol/4 columns and each coarse column exactly four children.
+ * Tables are validated (INVALID_ARG on an inconsistent table). Host inputs, copied. */
+int hmg_set_mesh(hmg_ctx *ctx, int32_t nmg, const hmg_mesh_level *levels);
+
+/* Set the background (one hmg_background per level, host, copied) and the scalars. */
+int hmg_set_coefficients(hmg_ctx *ctx, const hmg_scalars *scalars, const hmg_background *levels);
+
+/* Build everything a solve needs (Eqs. bilinear_forms, hybrid-S, elliptic_pressure_system,
+ * scaling_matrix): per cell the 7x7 A_K by 3x3x3 Gauss quadrature, its LU with partial
+ * pivoting and inverse, S_K = (A_K^-1)_uu K_K; the rows of S (11 coefficients each); the
+ * Thomas factors of S^zz and 1/diag(S^hh); H and the Thomas factors of H_z on every level;
+ * Gamma = (H 1) / (P^T S P 1). Allocates the solver workspace. */
+int hmg_assemble_trace(hmg_ctx *ctx);
+
+/* Sizes: cells and trace unknowns of the finest level (either pointer may be NULL). */
+int hmg_sizes(const hmg_ctx *ctx, int64_t *ncell, int64_t *ntrace);
+
+void hmg_destroy(hmg_ctx *ctx);
+const char *hmg_status_string(int status);
+const char *hmg_last_error(const hmg_ctx *ctx);
+
+/* ---- the solve (device pointers) --------------------------------------------------- */
+
+/* B_lambda = C^T A^-1 R_X (Eq. hybrid-rhs). Rub [ncell][6], Rpi [ncell] in; B [ntrace] out. */
+int hmg_trace_rhs(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *B);
+
+/* Solve S lambda = B_lambda(Rub, Rpi) to the context tolerance. lambda [ntrace] device,
+ * overwritten (the iteration starts from zero); stats host (may be NULL). Returns the
+ * stop reason (HMG_OK when converged). */
+int hmg_solve(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *lambda,
+              hmg_solve_stats *stats);
+
+/* The same solve with HOST buffers: the inputs are copied to the device, the result back. */
+int hmg_solve_host(hmg_ctx *ctx, const double *Rub_host, const double *Rpi_host,
+                   double *lambda_host, hmg_solve_stats *stats);
+
+/* X_K = A_K^-1 (R_X - K lambda) per cell (Eq. hybrid-recovery): broken velocity ub
+ * [ncell][6] (outward fluxes) and Exner increment pi [ncell]. Device pointers. */
+int hmg_reconstruct(hmg_ctx *ctx, const double *lambda, const double *Rub, const double *Rpi,
+                    double *ub, double *pi);
+
+/* ---- single steps (device pointers), for tests and benchmarks ----------------------- */
+
+/* y = S x (Eq. hybrid-S), FP64. x, y [ntrace]; x and y must not overlap. */
+int hmg_apply_trace(hmg_ctx *ctx, const double *x, double *y);
+
+/* z = M^-1 r: one application of the configured preconditioner (Algorithm 2 for
+ * HMG_PRECOND_NONNESTED) in the configured precision. r, z [ntrace], no overlap. */
+int hmg_precond_apply(hmg_ctx *ctx, const double *r, double *z);
+
+/* nsweeps of Algorithm 1 on S lambda = b, updating lambda [ntrace] in place (FP64). */
+int hmg_line_smooth(hmg_ctx *ctx, const double *b, double *lambda, int32_t nsweeps);
+
+/* y = H_l x on multigrid level l (Eq. elliptic_pressure_system), FP64, [ncell_l]. */
+int hmg_apply_pressure(hmg_ctx *ctx, int32_t level, const double *x, double *y);
+
+/* x = one pressure-multigrid V-cycle for H_0 x = b from zero (Sec. 2.3), FP64, [ncell]. */
+int hmg_pressure_vcycle(hmg_ctx *ctx, const double *b, double *x);
+
+/* Gamma [ncell] of Eq. scaling_matrix (device, FP64). */
+int hmg_get_gamma(hmg_ctx *ctx, double *gamma);
+
+/* Copy the assembled S (Eq. hybrid-S) as 11 coefficient slots per trace row, slot-major:
+ * slots [11][ntrace] device, FP64. A lambda^h row (edge e joining columns c1, c2 through
+ * their local faces i1, i2; level k): slot 0 the diagonal; 1-3 the faces i1+1, i1+2, i1+3
+ * (mod 4) of cell (c1, k); 4, 5 its bottom and top; 6-8 the faces i2+1..3 of (c2, k);
+ * 9, 10 its bottom and top. A lambda^z row (column c, interface k): slot 0 the diagonal;
+ * 1-4 faces e0..e3 of the cell above (c, k); 5 its top; 6-9 faces e0..e3 of the cell
+ * below (c, k-1); 10 its bottom. Slots of a missing cell (ground, lid) hold 0. */
+int hmg_get_trace_operator(hmg_ctx *ctx, double *slots);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMG_H */

@@ -206,13 +206,46 @@ def trace_dof_ids(mesh, cells=None) -> np.ndarray:
     return g
 
 
+def local_inverse(A: np.ndarray) -> np.ndarray:
+    """A_K^-1 [n,7,7] by block elimination of A_K = [[M, g], [b^T, m]] (the cell-local
+    inversion of Sec. 2.4): with y = M^-1 g, z = M^-T b and the pressure Schur complement
+    s = m - b.y,
+        A^-1 = [[M^-1 + y z^T / s, -y / s], [-z^T / s, 1 / s]].
+    M^-1 is taken from the symmetrically equilibrated velocity block diag(M)^-1/2 M
+    diag(M)^-1/2. A_K's rows span ~20 orders of magnitude (|M| ~ 1e-11..1e-2, m ~ 1e13
+    on the sphere), where partial pivoting on A_K itself loses up to 1e-12 relative
+    accuracy; this form stays within a few ulps of the exact inverse."""
+    M, g, b, m = A[:, :6, :6], A[:, :6, 6], A[:, 6, :6], A[:, 6, 6]
+    d = 1.0 / np.sqrt(np.abs(np.diagonal(M, axis1=1, axis2=2)))
+    Minv = d[:, :, None] * np.linalg.inv(M * d[:, :, None] * d[:, None, :]) * d[:, None, :]
+    y = np.einsum("nij,nj->ni", Minv, g)
+    z = np.einsum("nji,nj->ni", Minv, b)
+    s = m - np.einsum("ni,ni->n", b, y)
+    Ainv = np.empty_like(A)
+    Ainv[:, :6, :6] = Minv + y[:, :, None] * z[:, None, :] / s[:, None, None]
+    Ainv[:, :6, 6] = -y / s[:, None]
+    Ainv[:, 6, :6] = -z / s[:, None]
+    Ainv[:, 6, 6] = 1.0 / s
+    return Ainv
+
+
 def condense(A: np.ndarray, Kdiag: np.ndarray) -> np.ndarray:
     """Local Schur complement S_K = C_K^T A_K^-1 K_K with C_K = identity on the six faces
-    (Eq. hybrid-S): solve A_K Z = [K_K; 0] by LU with partial pivoting, keep Z[:6]."""
-    n = A.shape[0]
-    rhs = np.zeros((n, 7, 6))
-    rhs[:, np.arange(6), np.arange(6)] = Kdiag
-    return np.linalg.solve(A, rhs)[:, :6, :]
+    (Eq. hybrid-S): the velocity rows of A_K^-1 times diag(K_K)."""
+    return local_inverse(A)[:, :6, :6] * Kdiag[:, None, :]
+
+
+def trace_row_sums(mesh, A: np.ndarray) -> np.ndarray:
+    """S 1, the row sums of the trace operator, without cancellation.
+
+    Since G_K = -K_K 1 (the volume and facet terms of g carry the same theta, Sec. 2.4),
+    A_K [0; -1] = [K_K 1; -m_K], hence A_K^-1 [K_K 1; 0] = [0; -1] + m_K A_K^-1 e_p and
+    S_K 1 = (A_K^-1)_uu K_K 1 = m_K (A_K^-1)_{u,p}. Summing S_K's rows entry by entry would
+    cancel to ~1e-9 of the row scale on the sphere; this form does not."""
+    contrib = A[:, 6, 6][:, None] * local_inverse(A)[:, :6, 6]
+    out = np.zeros(mesh.n_trace)
+    np.add.at(out, trace_dof_ids(mesh), contrib)
+    return out
 
 
 def assemble_trace_operator(mesh, S_K: np.ndarray) -> sp.csr_matrix:
@@ -227,7 +260,7 @@ def assemble_trace_operator(mesh, S_K: np.ndarray) -> sp.csr_matrix:
 def trace_rhs(mesh, A: np.ndarray, Rub: np.ndarray, Rpi: np.ndarray) -> np.ndarray:
     """B_lambda = C^T A^-1 R_X (Eq. hybrid-rhs), R_X = (R_u^b, R_Pi) per cell."""
     R = np.concatenate([Rub, Rpi[:, None]], axis=1)
-    Y = np.linalg.solve(A, R[:, :, None])[:, :, 0]
+    Y = np.einsum("nij,nj->ni", local_inverse(A), R)
     B = np.zeros(mesh.n_trace)
     np.add.at(B, trace_dof_ids(mesh), Y[:, :6])
     return B
@@ -236,7 +269,7 @@ def trace_rhs(mesh, A: np.ndarray, Rub: np.ndarray, Rpi: np.ndarray) -> np.ndarr
 def reconstruct(mesh, A, Kdiag, lam, Rub, Rpi):
     """X_K = A_K^-1 (R_K - K_K lambda_K) (Eq. hybrid-recovery): broken u [C,6], Pi [C]."""
     R = np.concatenate([Rub - Kdiag * lam[trace_dof_ids(mesh)], Rpi[:, None]], axis=1)
-    X = np.linalg.solve(A, R[:, :, None])[:, :, 0]
+    X = np.einsum("nij,nj->ni", local_inverse(A), R)
     return X[:, :6], X[:, 6]
 
 

@@ -22,7 +22,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import fem
-from .pressure_mg import PressureMultigrid
+from .pressure_mg import PressureMultigrid, pressure_operator_times
 from .smoother import LineSmoother
 
 
@@ -112,8 +112,10 @@ class HybridSolver:
         self.mg = PressureMultigrid(hier, coeffs, o.mg_omega, o.mg_npre, o.mg_npost, o.mg_ncoarse,
                                     finest_system=system)
         self.P = prolongation(mesh)
+        # Gamma = (H 1) / (P^T S P 1); P 1 = 1, and H 1, S 1 are formed without cancellation
         one = np.ones(mesh.ncell)
-        self.gamma = (self.mg.H[0] @ one) / (self.P.T @ (self.S @ (self.P @ one)))
+        h1 = pressure_operator_times(self.mg.parts0, one)
+        self.gamma = h1 / (self.P.T @ fem.trace_row_sums(mesh, self.A))
 
     # -- coarse solve (Alg. 2 line 6) -------------------------------------------------
     def coarse_solve(self, bbar):

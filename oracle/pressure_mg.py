@@ -31,8 +31,9 @@ from .smoother import thomas
 OPPOSITE = (2, 3, 0, 1, 5, 4)   # e0-e2, e1-e3, bottom-top
 
 
-def pressure_operator(mesh, bg, co, system=None) -> sp.csr_matrix:
-    """H = -B Mlump^-1 G + M3^Pi on continuous RT0 with u.n = 0 on ground and lid.
+def pressure_operator_parts(mesh, bg, co, system=None):
+    """The factors of H = -B Mlump^-1 G + M3^Pi on continuous RT0 with u.n = 0 on ground and
+    lid: (B [C x T], 1/Mlump [T] (0 on ground and lid faces), G [T x C], M3^Pi [C]).
     `system` may pass the (A, Kdiag, coefficients) of fem.cell_system for this mesh."""
     A, _Kd, cc = fem.cell_system(mesh, bg, co) if system is None else system
     g = fem.trace_dof_ids(mesh)
@@ -51,8 +52,21 @@ def pressure_operator(mesh, bg, co, system=None) -> sp.csr_matrix:
     cells = np.repeat(np.arange(C), 6)
     Bg = sp.coo_matrix(((s * A[:, 6, :6]).ravel(), (cells, g.ravel())), shape=(C, T)).tocsr()
     Gg = sp.coo_matrix(((s * A[:, :6, 6]).ravel(), (g.ravel(), cells)), shape=(T, C)).tocsr()
-    H = sp.diags(cc["m"]) - Bg @ sp.diags(inv_lump) @ Gg
-    return H.tocsr()
+    return Bg, inv_lump, Gg, cc["m"]
+
+
+def pressure_operator(mesh, bg, co, system=None) -> sp.csr_matrix:
+    """H = -B Mlump^-1 G + M3^Pi (Eq. elliptic_pressure_system) as one sparse matrix."""
+    Bg, inv_lump, Gg, m = pressure_operator_parts(mesh, bg, co, system)
+    return (sp.diags(m) - Bg @ sp.diags(inv_lump) @ Gg).tocsr()
+
+
+def pressure_operator_times(parts, x):
+    """H x evaluated right to left through the factors, -B (Mlump^-1 (G x)) + M3^Pi x. For a
+    constant x, G x vanishes exactly (the two cells of a facet contribute -k theta and
+    +k theta), so H 1 = M3^Pi 1 without the cancellation of summing the rows of H."""
+    Bg, inv_lump, Gg, m = parts
+    return m * x - Bg @ (inv_lump * (Gg @ x))
 
 
 def column_tridiagonal(mesh, H):
@@ -74,7 +88,11 @@ class PressureMultigrid:
         self.omega, self.npre, self.npost, self.ncoarse = omega, npre, npost, ncoarse
         self.H, self.Hz = [], []
         for l, (mesh, bg) in enumerate(zip(hier.meshes, coeffs.levels)):
-            H = pressure_operator(mesh, bg, coeffs, finest_system if l == 0 else None)
+            parts = pressure_operator_parts(mesh, bg, coeffs, finest_system if l == 0 else None)
+            if l == 0:
+                self.parts0 = parts
+            Bg, inv_lump, Gg, m = parts
+            H = (sp.diags(m) - Bg @ sp.diags(inv_lump) @ Gg).tocsr()
             self.H.append(H)
             self.Hz.append(column_tridiagonal(mesh, H))
 

@@ -1,0 +1,451 @@
+// C ABI of the library (declared in include/hmg.h): validation of the caller's tables,
+// upload of the mesh hierarchy and coefficients, allocation of the solver workspace, and
+// the entry points of the solve.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hmg_internal.cuh"
+
+namespace hmg {
+
+int fail(Ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(Ctx *c, cudaError_t e, const char *what) {
+  return fail(c, HMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+static int upload(Ctx *c, T **dst, const T *src, size_t n) {
+  int st = dev_alloc(c, dst, n);
+  if (st) return st;
+  HMG_CUDA(c, cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return HMG_OK;
+}
+
+static int check_options(Ctx *c, const hmg_options &o) {
+  auto bad = [&](const char *m) { return fail(c, HMG_ERR_INVALID_ARG, std::string("options: ") + m); };
+  if (o.precision != HMG_PRECISION_FP64 && o.precision != HMG_PRECISION_MIXED) return bad("precision");
+  if (o.precond < HMG_PRECOND_NONE || o.precond > HMG_PRECOND_NONNESTED) return bad("precond");
+  if (o.n_pre < 0 || o.n_post < 0 || o.n_smooth < 1) return bad("trace smoother sweep counts");
+  if (o.mg_npre < 1 || o.mg_npost < 1 || o.mg_ncoarse < 1) return bad("multigrid sweep counts must be >= 1");
+  if (!std::isfinite(o.omega) || !std::isfinite(o.mg_omega)) return bad("relaxation factors");
+  if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.divergence > 0.0)) return bad("tol / max_iter / divergence");
+  return HMG_OK;
+}
+
+static int next_event(Ctx *c) {
+  if (c->ev_next >= (int)c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_next++;
+}
+
+Prof::Prof(Ctx *c, int comp, int launches) : c_(c), comp_(comp), launches_(launches) {
+  if (!c_->opt.profile) return;
+  e0_ = next_event(c_);
+  if (e0_ >= 0) cudaEventRecord(c_->ev_pool[e0_], c_->stream);
+}
+
+Prof::~Prof() {
+  if (e0_ < 0) return;
+  const int e1 = next_event(c_);
+  if (e1 < 0) return;
+  cudaEventRecord(c_->ev_pool[e1], c_->stream);
+  c_->marks.push_back({comp_, e0_, e1, launches_});
+}
+
+static void free_all(Ctx *c) {
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+  for (void *p : c->owned) cudaFree(p);
+  c->owned.clear();
+  if (c->scal_host) cudaFreeHost(c->scal_host);
+  c->scal_host = nullptr;
+}
+
+}  // namespace hmg
+
+using namespace hmg;
+
+struct hmg_ctx : public Ctx {};
+
+extern "C" {
+
+int hmg_default_options(hmg_options *o) {
+  if (!o) return HMG_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HMG_PRECISION_FP64;
+  o->precond = HMG_PRECOND_NONNESTED;
+  o->n_pre = 1;
+  o->n_post = 2;
+  o->n_smooth = 1;
+  o->omega = 0.6;
+  o->mg_npre = 1;
+  o->mg_npost = 2;
+  o->mg_ncoarse = 3;
+  o->mg_omega = 0.9;
+  o->tol = 1e-6;
+  o->max_iter = 200;
+  o->divergence = 1e3;
+  return HMG_OK;
+}
+
+int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
+  if (!out) return HMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  hmg_ctx *c = new (std::nothrow) hmg_ctx();
+  if (!c) return HMG_ERR_OUT_OF_MEMORY;
+  hmg_default_options(&c->opt);
+  if (opt) {
+    int st = check_options(c, *opt);
+    if (st) { delete c; return st; }
+    c->opt = *opt;
+  }
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(double) * Scal::N);
+  if (e != cudaSuccess) {
+    delete c;
+    return HMG_ERR_CUDA;
+  }
+  int st = dev_alloc(c, &c->scal, Scal::N);
+  if (!st) st = dev_alloc(c, &c->part, (size_t)Scal::N * kMaxRedBlocks);
+  if (!st) st = dev_alloc(c, &c->counter, Scal::N);
+  if (!st && cudaMemset(c->counter, 0, sizeof(unsigned int) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
+  if (!st && cudaMemset(c->scal, 0, sizeof(double) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
+  if (st) {
+    free_all(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return HMG_OK;
+}
+
+int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
+  if (!c || !opt) return HMG_ERR_INVALID_ARG;
+  int st = check_options(c, *opt);
+  if (st) return st;
+  c->opt = *opt;
+  if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32)
+    c->assembled = false;  // the FP32 copies are built by hmg_assemble_trace
+  return HMG_OK;
+}
+
+int hmg_set_mesh(hmg_ctx *c, int32_t nmg, const hmg_mesh_level *levels) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (c->have_mesh) return fail(c, HMG_ERR_INVALID_ARG, "mesh already set (create a new context)");
+  if (nmg < 1 || nmg > kMaxLevels || !levels) return fail(c, HMG_ERR_INVALID_ARG, "nmg out of range");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  const int L = levels[0].nlev;
+  std::vector<std::vector<int32_t>> children(nmg);
+  for (int l = 0; l < nmg; ++l) {
+    const hmg_mesh_level &m = levels[l];
+    char buf[160];
+    auto bad = [&](const char *what) {
+      std::snprintf(buf, sizeof buf, "mesh level %d: %s", l, what);
+      return fail(c, HMG_ERR_INVALID_ARG, buf);
+    };
+    if (m.ncol < 1 || m.nlev < 1 || m.nedge < 1) return bad("empty mesh");
+    if (m.nlev != L) return bad("every level needs the same nlev");
+    if (m.geometry != 0 && m.geometry != 1) return bad("geometry must be 0 or 1");
+    if (m.geometry == 1 && !(m.radius > 0.0)) return bad("radius must be > 0");
+    if (!m.corners || !m.z_levels || !m.col_edges || !m.edge_cols || !m.edge_face) return bad("null table");
+    if ((int64_t)m.nedge * 2 != (int64_t)m.ncol * 4) return bad("every column needs 4 edges shared by 2 columns");
+    if ((int64_t)m.nedge * m.nlev + (int64_t)m.ncol * (m.nlev + 1) > INT32_MAX / kSlots)
+      return bad("mesh too large for 32-bit slot offsets");
+    for (int k = 0; k < m.nlev; ++k)
+      if (!(m.z_levels[k + 1] > m.z_levels[k])) return bad("z_levels must increase strictly");
+    for (int64_t i = 0; i < (int64_t)m.ncol * 4; ++i)
+      if (m.col_edges[i] < 0 || m.col_edges[i] >= m.nedge) return bad("col_edges out of range");
+    for (int64_t e = 0; e < m.nedge; ++e) {
+      for (int s = 0; s < 2; ++s) {
+        const int cc = m.edge_cols[2 * e + s], f = m.edge_face[2 * e + s];
+        if (cc < 0 || cc >= m.ncol || f < 0 || f > 3) return bad("edge_cols / edge_face out of range");
+        if (m.col_edges[4 * (int64_t)cc + f] != e) return bad("col_edges and edge_cols disagree");
+      }
+      if (m.edge_cols[2 * e] == m.edge_cols[2 * e + 1]) return bad("an edge joins a column to itself");
+    }
+    if (l + 1 < nmg) {
+      if (!m.parent) return bad("parent map missing");
+      const int nc = levels[l + 1].ncol;
+      std::vector<int32_t> ch((size_t)nc * 4, -1), cnt(nc, 0);
+      for (int cc = 0; cc < m.ncol; ++cc) {
+        const int p = m.parent[cc];
+        if (p < 0 || p >= nc || cnt[p] >= 4) return bad("parent map is not a 2x2 agglomeration");
+        ch[4 * (size_t)p + cnt[p]++] = cc;
+      }
+      for (int p = 0; p < nc; ++p)
+        if (cnt[p] != 4) return bad("a coarse column does not have four children");
+      children[l + 1] = ch;
+    }
+  }
+  for (int l = 0; l < nmg; ++l) {
+    const hmg_mesh_level &m = levels[l];
+    Level &lv = c->lv[l];
+    lv.geometry = m.geometry;
+    lv.ncol = m.ncol;
+    lv.nlev = m.nlev;
+    lv.nedge = m.nedge;
+    lv.radius = m.radius;
+    lv.ncell = (int64_t)m.ncol * m.nlev;
+    lv.nth = (int64_t)m.nedge * m.nlev;
+    lv.ntz = (int64_t)m.ncol * (m.nlev + 1);
+    lv.ntrace = lv.nth + lv.ntz;
+    std::vector<int32_t> nbr((size_t)m.ncol * 4), nbf((size_t)m.ncol * 4);
+    for (int cc = 0; cc < m.ncol; ++cc)
+      for (int f = 0; f < 4; ++f) {
+        const int e = m.col_edges[4 * (size_t)cc + f];
+        const bool first = m.edge_cols[2 * (size_t)e] == cc && m.edge_face[2 * (size_t)e] == f;
+        nbr[4 * (size_t)cc + f] = m.edge_cols[2 * (size_t)e + (first ? 1 : 0)];
+        nbf[4 * (size_t)cc + f] = m.edge_face[2 * (size_t)e + (first ? 1 : 0)];
+      }
+    int st;
+    if ((st = upload(c, &lv.col_edges, m.col_edges, (size_t)m.ncol * 4))) return st;
+    if ((st = upload(c, &lv.col_nbr, nbr.data(), nbr.size()))) return st;
+    if ((st = upload(c, &lv.col_nbr_face, nbf.data(), nbf.size()))) return st;
+    if ((st = upload(c, &lv.corners, m.corners, (size_t)m.ncol * 12))) return st;
+    if ((st = upload(c, &lv.z, m.z_levels, (size_t)m.nlev + 1))) return st;
+    if (l + 1 < nmg && (st = upload(c, &lv.parent, m.parent, (size_t)m.ncol))) return st;
+    if (l > 0 && (st = upload(c, &lv.children, children[l].data(), children[l].size()))) return st;
+    if (l == 0) {
+      std::vector<int32_t> sten((size_t)m.nedge * 8), fc((size_t)m.nedge * 2);
+      for (int64_t e = 0; e < m.nedge; ++e) {
+        const int c1 = m.edge_cols[2 * e], c2 = m.edge_cols[2 * e + 1];
+        const int i1 = m.edge_face[2 * e], i2 = m.edge_face[2 * e + 1];
+        int32_t *s = &sten[8 * e];
+        s[0] = c1;
+        s[1] = c2;
+        for (int q = 1; q <= 3; ++q) {
+          s[1 + q] = m.col_edges[4 * (size_t)c1 + ((i1 + q) & 3)];
+          s[4 + q] = m.col_edges[4 * (size_t)c2 + ((i2 + q) & 3)];
+        }
+        fc[2 * e] = i1;
+        fc[2 * e + 1] = i2;
+      }
+      if ((st = upload(c, &lv.edge_stencil, sten.data(), sten.size()))) return st;
+      if ((st = upload(c, &lv.edge_fc, fc.data(), fc.size()))) return st;
+    }
+    double *tmp;
+    if ((st = dev_alloc(c, &tmp, (size_t)lv.ncell))) return st;
+    lv.vb = tmp;
+    if ((st = dev_alloc(c, &tmp, (size_t)lv.ncell))) return st;
+    lv.vx = tmp;
+    if ((st = dev_alloc(c, &tmp, (size_t)lv.ncell))) return st;
+    lv.vy = tmp;
+  }
+  c->nmg = nmg;
+  c->have_mesh = true;
+  return HMG_OK;
+}
+
+int hmg_set_coefficients(hmg_ctx *c, const hmg_scalars *sc, const hmg_background *levels) {
+  if (!c || !sc || !levels) return HMG_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, HMG_ERR_NOT_READY, "set the mesh first");
+  if (sc->preset != 0 && sc->preset != 1) return fail(c, HMG_ERR_INVALID_ARG, "preset must be 0 or 1");
+  if (sc->preset == 1 && !(sc->sigma >= 0.0)) return fail(c, HMG_ERR_INVALID_ARG, "sigma must be >= 0");
+  if (sc->preset == 0 && !(sc->dt > 0.0 && sc->cp > 0.0 && sc->kappa > 0.0 && sc->kappa < 1.0))
+    return fail(c, HMG_ERR_INVALID_ARG, "dt, cp > 0 and 0 < kappa < 1 required");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  for (int l = 0; l < c->nmg; ++l) {
+    Level &lv = c->lv[l];
+    const hmg_background &b = levels[l];
+    if (!b.theta_lev || !b.exner_lev || !b.exner) return fail(c, HMG_ERR_INVALID_ARG, "null background");
+    const size_t nl = (size_t)lv.ncol * (lv.nlev + 1);
+    for (size_t i = 0; i < nl; ++i)
+      if (!(b.theta_lev[i] > 0.0) || !(b.exner_lev[i] > 0.0))
+        return fail(c, HMG_ERR_INVALID_ARG, "theta* and Exner* must be positive");
+    for (int64_t i = 0; i < lv.ncell; ++i)
+      if (!(b.exner[i] > 0.0)) return fail(c, HMG_ERR_INVALID_ARG, "Exner* must be positive");
+    int st;
+    if (lv.theta_lev) {
+      HMG_CUDA(c, cudaMemcpy(lv.theta_lev, b.theta_lev, nl * 8, cudaMemcpyHostToDevice));
+      HMG_CUDA(c, cudaMemcpy(lv.exner_lev, b.exner_lev, nl * 8, cudaMemcpyHostToDevice));
+      HMG_CUDA(c, cudaMemcpy(lv.exner, b.exner, (size_t)lv.ncell * 8, cudaMemcpyHostToDevice));
+    } else {
+      if ((st = upload(c, &lv.theta_lev, b.theta_lev, nl))) return st;
+      if ((st = upload(c, &lv.exner_lev, b.exner_lev, nl))) return st;
+      if ((st = upload(c, &lv.exner, b.exner, (size_t)lv.ncell))) return st;
+    }
+  }
+  c->sc = *sc;
+  c->have_coeffs = true;
+  c->assembled = false;
+  c->have_fp32 = false;
+  return HMG_OK;
+}
+
+int hmg_assemble_trace(hmg_ctx *c) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  const bool need_fp32 = c->opt.precision == HMG_PRECISION_MIXED;
+  if (c->have_fp32 && need_fp32) c->have_fp32 = false;  // rebuild copies from fresh FP64 data
+  int st = assemble_all(c);
+  if (st) return st;
+  const Level &f = c->lv[0];
+  const size_t T = (size_t)f.ntrace;
+  if (!c->B) {
+    double **vecs[] = {&c->B, &c->r, &c->rhat, &c->p, &c->v, &c->s, &c->t, &c->phat, &c->shat};
+    for (double **v : vecs)
+      if ((st = dev_alloc(c, v, T))) return st;
+    double *tmp;
+    if ((st = dev_alloc(c, &tmp, T))) return st;
+    c->w1 = tmp;
+    if ((st = dev_alloc(c, &tmp, T))) return st;
+    c->w2 = tmp;
+    if ((st = dev_alloc(c, &tmp, T))) return st;
+    c->w3 = tmp;
+    if ((st = dev_alloc(c, &tmp, (size_t)f.ncell))) return st;
+    c->cb = tmp;
+    if ((st = dev_alloc(c, &c->host_in, (size_t)7 * f.ncell + T))) return st;
+  }
+  c->assembled = true;
+  return HMG_OK;
+}
+
+int hmg_sizes(const hmg_ctx *c, int64_t *ncell, int64_t *ntrace) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (!c->have_mesh) return HMG_ERR_NOT_READY;
+  if (ncell) *ncell = c->lv[0].ncell;
+  if (ntrace) *ntrace = c->lv[0].ntrace;
+  return HMG_OK;
+}
+
+void hmg_destroy(hmg_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+const char *hmg_status_string(int s) {
+  switch (s) {
+    case HMG_OK: return "ok";
+    case HMG_ERR_INVALID_ARG: return "invalid argument";
+    case HMG_ERR_CUDA: return "CUDA error";
+    case HMG_ERR_NOT_READY: return "not ready (mesh, coefficients or assembly missing)";
+    case HMG_ERR_NOT_CONVERGED: return "not converged";
+    case HMG_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HMG_ERR_NONFINITE: return "non-finite value";
+    case HMG_ERR_TIMEOUT: return "device wait timed out";
+    case HMG_ERR_OUT_OF_MEMORY: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+const char *hmg_last_error(const hmg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+static int ready(hmg_ctx *c) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (!c->assembled) return fail(c, HMG_ERR_NOT_READY, "call hmg_assemble_trace first");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  return HMG_OK;
+}
+
+static int finish(hmg_ctx *c, int st) {
+  if (st) return st;
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
+int hmg_trace_rhs(hmg_ctx *c, const double *Rub, const double *Rpi, double *B) {
+  int st = ready(c);
+  if (st) return st;
+  if (!Rub || !Rpi || !B) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  return finish(c, launch_trace_rhs(c, Rub, Rpi, B));
+}
+
+int hmg_solve(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *stats) {
+  int st = ready(c);
+  if (st) return st;
+  if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  return krylov_solve(c, Rub, Rpi, lambda, stats);
+}
+
+int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *stats) {
+  int st = ready(c);
+  if (st) return st;
+  if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  const Level &f = c->lv[0];
+  double *dRub = c->host_in, *dRpi = dRub + 6 * f.ncell, *dlam = dRpi + f.ncell;
+  HMG_CUDA(c, cudaMemcpyAsync(dRub, Rub, sizeof(double) * 6 * f.ncell, cudaMemcpyHostToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * f.ncell, cudaMemcpyHostToDevice, c->stream));
+  const int solve_st = krylov_solve(c, dRub, dRpi, dlam, stats);
+  if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
+      solve_st != HMG_ERR_NONFINITE)
+    return solve_st;
+  HMG_CUDA(c, cudaMemcpyAsync(lambda, dlam, sizeof(double) * f.ntrace, cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return solve_st;
+}
+
+int hmg_reconstruct(hmg_ctx *c, const double *lambda, const double *Rub, const double *Rpi, double *ub, double *pi) {
+  int st = ready(c);
+  if (st) return st;
+  if (!lambda || !Rub || !Rpi || !ub || !pi) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  return finish(c, launch_reconstruct(c, lambda, Rub, Rpi, ub, pi));
+}
+
+int hmg_apply_trace(hmg_ctx *c, const double *x, double *y) {
+  int st = ready(c);
+  if (st) return st;
+  if (!x || !y || x == y) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  return finish(c, launch_spmv(c, x, y, 0, nullptr, 0, 0));
+}
+
+int hmg_precond_apply(hmg_ctx *c, const double *r, double *z) {
+  int st = ready(c);
+  if (st) return st;
+  if (!r || !z || r == z) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  return finish(c, precond_apply(c, r, z));
+}
+
+int hmg_line_smooth(hmg_ctx *c, const double *b, double *lambda, int32_t nsweeps) {
+  int st = ready(c);
+  if (st) return st;
+  if (!b || !lambda || nsweeps < 0) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  return finish(c, line_smooth_fp64(c, b, lambda, nsweeps));
+}
+
+int hmg_apply_pressure(hmg_ctx *c, int32_t level, const double *x, double *y) {
+  int st = ready(c);
+  if (st) return st;
+  if (level < 0 || level >= c->nmg || !x || !y || x == y) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  return finish(c, apply_pressure_fp64(c, level, x, y));
+}
+
+int hmg_pressure_vcycle(hmg_ctx *c, const double *b, double *x) {
+  int st = ready(c);
+  if (st) return st;
+  if (!b || !x) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  return finish(c, pressure_vcycle_fp64(c, b, x));
+}
+
+int hmg_get_gamma(hmg_ctx *c, double *gamma) {
+  int st = ready(c);
+  if (st) return st;
+  if (!gamma) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  HMG_CUDA(c, cudaMemcpyAsync(gamma, c->gamma, sizeof(double) * c->lv[0].ncell, cudaMemcpyDeviceToDevice, c->stream));
+  return finish(c, HMG_OK);
+}
+
+int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
+  int st = ready(c);
+  if (st) return st;
+  if (!slots) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  HMG_CUDA(c, cudaMemcpyAsync(slots, c->S, sizeof(double) * kSlots * c->lv[0].ntrace,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  return finish(c, HMG_OK);
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Device helpers shared by the kernels: deterministic grid reductions and the indexing of
+// the trace rows of S.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hmg_internal.cuh"
+
+namespace hmg {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic reduction of NV per-thread values over the whole grid (gridDim.x <=
+// kMaxRedBlocks, blockDim.x a multiple of 32, <= 1024). Each block writes its partial sums to
+// part[slot][blockIdx.x]; the block that takes the last ticket sums the partials in block
+// order and writes scal[slot]. The summation order depends only on the launch shape, so
+// repeated runs give bit-identical results. No block waits on another.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(const double (&val)[NV], const int (&slot)[NV],
+                                            double *part, unsigned int *counter, double *scal) {
+  __shared__ double sh[NV][32];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double v = warp_sum(val[i]);
+    if (lane == 0) sh[i][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double v = lane < nwarp ? sh[i][lane] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) part[(int64_t)slot[i] * kMaxRedBlocks + blockIdx.x] = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int ticket = atomicAdd(&counter[slot[0]], 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      v += __ldcg(&part[(int64_t)slot[i] * kMaxRedBlocks + b]);
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[i][warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < nwarp; ++w) s += sh[i][w];
+      scal[slot[i]] = s;
+    }
+  }
+  if (threadIdx.x == 0) counter[slot[0]] = 0u;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
+
+// ---- trace rows of S ------------------------------------------------------------------
+// h-row (edge e, level k): slot 0 self; 1-3 the other vertical faces of c1 (local faces
+// i1+1, i1+2, i1+3 mod 4); 4, 5 bottom/top of cell (c1, k); 6-8 the other vertical faces
+// of c2; 9, 10 bottom/top of (c2, k). st = edge_stencil + 8 e = {c1, c2, ea1..3, eb1..3}.
+// z-row (column c, interface k): slot 0 self; 1-4 vertical faces e0..e3 of the cell above
+// (c, k); 5 its top (k+1); 6-9 vertical faces of the cell below (c, k-1); 10 its bottom.
+struct TraceDims {
+  int L;          // layers
+  int64_t NH;     // h-rows = nedge * L
+  int64_t NT;     // all rows
+};
+
+template <typename TS, typename TX, typename TA>
+__device__ __forceinline__ TA s_row_h(const TS *__restrict__ S, const TX *__restrict__ x,
+                                      const int32_t *__restrict__ stencil, const TraceDims d,
+                                      int64_t row) {
+  const int e = (int)(row / d.L);
+  const int k = (int)(row - (int64_t)e * d.L);
+  const int32_t *st = stencil + 8 * (int64_t)e;
+  const int c1 = __ldg(st + 0), c2 = __ldg(st + 1);
+  const int64_t z1 = d.NH + (int64_t)c1 * (d.L + 1) + k;
+  const int64_t z2 = d.NH + (int64_t)c2 * (d.L + 1) + k;
+  const int64_t T = d.NT;
+  TA y = (TA)ld(S + row) * (TA)ld(x + row);
+  y += (TA)ld(S + T + row) * (TA)ld(x + (int64_t)__ldg(st + 2) * d.L + k);
+  y += (TA)ld(S + 2 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 3) * d.L + k);
+  y += (TA)ld(S + 3 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 4) * d.L + k);
+  y += (TA)ld(S + 4 * T + row) * (TA)ld(x + z1);
+  y += (TA)ld(S + 5 * T + row) * (TA)ld(x + z1 + 1);
+  y += (TA)ld(S + 6 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 5) * d.L + k);
+  y += (TA)ld(S + 7 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 6) * d.L + k);
+  y += (TA)ld(S + 8 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 7) * d.L + k);
+  y += (TA)ld(S + 9 * T + row) * (TA)ld(x + z2);
+  y += (TA)ld(S + 10 * T + row) * (TA)ld(x + z2 + 1);
+  return y;
+}
+
+template <typename TS, typename TX, typename TA>
+__device__ __forceinline__ TA s_row_z(const TS *__restrict__ S, const TX *__restrict__ x,
+                                      const int32_t *__restrict__ col_edges, const TraceDims d,
+                                      int64_t row) {
+  const int64_t zr = row - d.NH;
+  const int c = (int)(zr / (d.L + 1));
+  const int k = (int)(zr - (int64_t)c * (d.L + 1));
+  const int64_t T = d.NT;
+  const int32_t *ce = col_edges + 4 * (int64_t)c;
+  TA y = (TA)ld(S + row) * (TA)ld(x + row);
+  if (k < d.L) {
+    y += (TA)ld(S + T + row) * (TA)ld(x + (int64_t)__ldg(ce + 0) * d.L + k);
+    y += (TA)ld(S + 2 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 1) * d.L + k);
+    y += (TA)ld(S + 3 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 2) * d.L + k);
+    y += (TA)ld(S + 4 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 3) * d.L + k);
+    y += (TA)ld(S + 5 * T + row) * (TA)ld(x + row + 1);
+  }
+  if (k > 0) {
+    y += (TA)ld(S + 6 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 0) * d.L + k - 1);
+    y += (TA)ld(S + 7 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 1) * d.L + k - 1);
+    y += (TA)ld(S + 8 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 2) * d.L + k - 1);
+    y += (TA)ld(S + 9 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 3) * d.L + k - 1);
+    y += (TA)ld(S + 10 * T + row) * (TA)ld(x + row - 1);
+  }
+  return y;
+}
+
+template <typename TS, typename TX, typename TA>
+__device__ __forceinline__ TA s_row(const TS *__restrict__ S, const TX *__restrict__ x,
+                                    const int32_t *__restrict__ stencil,
+                                    const int32_t *__restrict__ col_edges, const TraceDims d,
+                                    int64_t row) {
+  return row < d.NH ? s_row_h<TS, TX, TA>(S, x, stencil, d, row)
+                    : s_row_z<TS, TX, TA>(S, x, col_edges, d, row);
+}
+
+}  // namespace hmg

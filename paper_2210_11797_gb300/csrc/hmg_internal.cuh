@@ -1,0 +1,171 @@
+// Internal declarations of the hmg library: the context, device tables and kernel
+// launchers shared by the translation units. Not part of the public C ABI (include/hmg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hmg.h"
+
+namespace hmg {
+
+constexpr int kMaxLevels = 8;
+constexpr int kSlots = 11;      // coefficients per trace row of S
+constexpr int kHCoef = 7;       // coefficients per cell of H: diag, e0..e3, below, above
+constexpr int kCellData = 40;   // per-cell assembly record (see CellRec)
+constexpr int kRedBlocks = 1216;  // blocks of the grid-stride vector reductions (8 per SM)
+constexpr int kMaxRedBlocks = 1 << 18;  // partial-sum slots per reduction (one row per thread)
+constexpr int kRedThreads = 256;
+
+// Per-cell record written by the geometry kernel on every multigrid level.
+// Offsets into a [ncell][kCellData] array.
+struct CellRec {
+  static constexpr int M = 0;      // 21 entries: upper triangle of M_K, row-major (f <= g)
+  static constexpr int B = 21;     // 6: pressure-row couplings b_K(f)
+  static constexpr int KTH = 27;   // 6: k * theta_f (diagonal of K_K; G_K = -KTH)
+  static constexpr int MPI = 33;   // 1: M3^Pi
+  static constexpr int LUMP = 34;  // 6: this cell's share of the lumped mass of each face
+};
+
+// Reduction slots of the scalar block kept on the device.
+struct Scal {
+  static constexpr int RHO0 = 0, RHO1 = 1;  // (rhat, r), double-buffered by iteration parity
+  static constexpr int RV = 2;              // (rhat, v)
+  static constexpr int TS = 3, TT = 4;      // (t, s), (t, t)
+  static constexpr int RR = 5;              // (r, r)
+  static constexpr int BB = 6;              // (B, B)
+  static constexpr int ALPHA = 7, OMEGA = 8;
+  static constexpr int AUX = 9;             // scratch for tests / true residual
+  static constexpr int N = 16;
+};
+
+// Device-side description of one multigrid level.
+struct Level {
+  int geometry = 0;
+  int ncol = 0, nlev = 0, nedge = 0;
+  int64_t ncell = 0, nth = 0, ntz = 0, ntrace = 0;
+  double radius = 0.0;
+  // mesh tables (device)
+  int32_t *col_edges = nullptr;     // [ncol][4]
+  int32_t *col_nbr = nullptr;       // [ncol][4] column across local face i
+  int32_t *col_nbr_face = nullptr;  // [ncol][4] that column's local face index of the edge
+  int32_t *edge_stencil = nullptr;  // [nedge][8] c1, c2, 3 other edges of c1, 3 of c2
+  int32_t *edge_fc = nullptr;       // [nedge][2] local face of the edge in c1 and in c2
+  int32_t *parent = nullptr;        // [ncol] column on level+1 (not on the coarsest)
+  int32_t *children = nullptr;      // [ncol][4] columns on level-1 (not on the finest)
+  double *corners = nullptr;        // [ncol][4][3]
+  double *z = nullptr;              // [nlev+1]
+  double *theta_lev = nullptr, *exner_lev = nullptr, *exner = nullptr;
+  // assembled pressure operator (device)
+  double *H = nullptr;              // [7][ncell]
+  double *Hz_inv = nullptr;         // [ncell] Thomas reciprocal pivots of H_z
+  double *Hz_cp = nullptr;          // [ncell] Thomas modified super-diagonal of H_z
+  float *H32 = nullptr, *Hz_inv32 = nullptr, *Hz_cp32 = nullptr;
+  // multigrid work vectors, sized for doubles (used as float in the mixed path)
+  void *vb = nullptr, *vx = nullptr, *vy = nullptr;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  hmg_options opt{};
+  hmg_scalars sc{};
+  std::string err;
+  int nmg = 0;
+  Level lv[kMaxLevels];
+  bool have_mesh = false, have_coeffs = false, assembled = false, have_fp32 = false;
+  // finest-level trace system (device)
+  double *S = nullptr;        // [11][ntrace]
+  double *Sz_inv = nullptr;   // [ntz] Thomas reciprocal pivots of S^zz
+  double *Sz_cp = nullptr;    // [ntz] Thomas modified super-diagonals
+  double *Sh_inv = nullptr;   // [nth] 1 / diag(S^hh)
+  double *Ainv = nullptr;     // [49][ncell] A_K^-1, entry (i, j) at (7 i + j) * ncell + K
+  double *kth = nullptr;      // [6][ncell] diagonal of K_K (k theta on each local face)
+  double *gamma = nullptr;    // [ncell]
+  float *S32 = nullptr, *Sz_inv32 = nullptr, *Sz_cp32 = nullptr, *Sh_inv32 = nullptr,
+        *gamma32 = nullptr;
+  // Krylov workspace (FP64, [ntrace] each)
+  double *B = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr,
+         *s = nullptr, *t = nullptr, *phat = nullptr, *shat = nullptr;
+  // preconditioner workspace, sized for doubles ([ntrace] each)
+  void *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;
+  void *cb = nullptr;          // restricted, scaled residual [ncell]
+  // host-visible buffers for stats and the e2e path
+  double *scal = nullptr;      // device [Scal::N]
+  double *part = nullptr;      // device [Scal::N][kMaxRedBlocks]
+  unsigned int *counter = nullptr;  // device [Scal::N] tickets of the last-block reductions
+  double *scal_host = nullptr; // pinned [Scal::N]
+  double *host_in = nullptr;   // device staging for hmg_solve_host (Rub | Rpi | lambda)
+  std::vector<void *> owned;   // every device allocation, freed by hmg_destroy
+  // component timing (hmg_options.profile): event pool and (component, start, end) marks
+  std::vector<cudaEvent_t> ev_pool;
+  struct Mark { int comp, e0, e1, launches; };
+  std::vector<Mark> marks;
+  int ev_next = 0;
+};
+
+// Records CUDA events around one solver component when profiling is on (no-op otherwise).
+class Prof {
+ public:
+  Prof(Ctx *c, int comp, int launches = 1);
+  ~Prof();
+ private:
+  Ctx *c_;
+  int comp_, e0_ = -1, launches_;
+};
+enum Comp { kCompRhs = 0, kCompApply, kCompPresmooth, kCompSweep, kCompResidual, kCompVcycle,
+            kCompProlong, kCompKrylov };
+
+// ---- error helpers --------------------------------------------------------------------
+int fail(Ctx *c, int code, const std::string &msg);
+int cuda_fail(Ctx *c, cudaError_t e, const char *what);
+#define HMG_CUDA(ctx, call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::hmg::cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+template <typename T>
+int dev_alloc(Ctx *c, T **p, size_t n) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, HMG_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->owned.push_back(q);
+  *p = static_cast<T *>(q);
+  return HMG_OK;
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return static_cast<unsigned>(g > 0 ? g : 1);
+}
+
+// ---- assembly (assemble.cu) -----------------------------------------------------------
+int assemble_all(Ctx *c);
+
+// ---- trace-space kernels (trace_ops.cu) -----------------------------------------------
+// y = S x (FP64). mode 0: plain; 1: also (w, y) -> scal[slot0]; 2: also (y, w) -> slot0 and
+// (y, y) -> slot1; 3: y is not stored, (b - S x, b - S x) -> slot0 with w = b.
+int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0,
+                int slot1);
+int launch_trace_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B);
+int launch_reconstruct(Ctx *c, const double *lam, const double *Rub, const double *Rpi,
+                       double *ub, double *pi);
+// preconditioners: z = M^-1 r, r and z FP64 Krylov vectors
+int precond_apply(Ctx *c, const double *r, double *z);
+int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps);
+int pressure_vcycle_fp64(Ctx *c, const double *b, double *x);
+int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
+
+// ---- Krylov (krylov.cu) ------------------------------------------------------------------
+int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
+                 hmg_solve_stats *st);
+int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
+
+}  // namespace hmg

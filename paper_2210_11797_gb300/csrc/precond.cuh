@@ -1,0 +1,39 @@
+// Templated preconditioner pieces shared between trace_ops.cu and pressure_mg.cu.
+#pragma once
+
+#include "hmg_internal.cuh"
+
+namespace hmg {
+
+// One pressure-multigrid V-cycle for H_0 x = b from a zero initial guess (Sec. 2.3), in
+// precision T (double: FP64 operator; float: the FP32 copies). b [ncell] in T. On return
+// *x points at the level-0 work vector holding the result (valid until the next V-cycle).
+template <typename T>
+int vcycle(Ctx *c, const T *b, T **x);
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static const double *S(const Ctx *c) { return c->S; }
+  static const double *Sz_inv(const Ctx *c) { return c->Sz_inv; }
+  static const double *Sz_cp(const Ctx *c) { return c->Sz_cp; }
+  static const double *Sh_inv(const Ctx *c) { return c->Sh_inv; }
+  static const double *gamma(const Ctx *c) { return c->gamma; }
+  static const double *H(const Level &l) { return l.H; }
+  static const double *Hz_inv(const Level &l) { return l.Hz_inv; }
+  static const double *Hz_cp(const Level &l) { return l.Hz_cp; }
+};
+template <>
+struct Prec<float> {
+  static const float *S(const Ctx *c) { return c->S32; }
+  static const float *Sz_inv(const Ctx *c) { return c->Sz_inv32; }
+  static const float *Sz_cp(const Ctx *c) { return c->Sz_cp32; }
+  static const float *Sh_inv(const Ctx *c) { return c->Sh_inv32; }
+  static const float *gamma(const Ctx *c) { return c->gamma32; }
+  static const float *H(const Level &l) { return l.H32; }
+  static const float *Hz_inv(const Level &l) { return l.Hz_inv32; }
+  static const float *Hz_cp(const Level &l) { return l.Hz_cp32; }
+};
+
+}  // namespace hmg

@@ -1,0 +1,213 @@
+// Tensor-product pressure multigrid (Sec. 2.3 of arXiv 2210.11797): the 7-point pressure
+// operator H, the column block-Jacobi smoother x <- x + omega H_z^-1 (b - H x)
+// (Eq. pressure_block_jacobi, Thomas algorithm per column), residual + restriction (sum over
+// the four horizontal children) and prolongation (injection), in one V-cycle with
+// mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level.
+#include "device_common.cuh"
+#include "hmg_internal.cuh"
+#include "precond.cuh"
+
+namespace hmg {
+
+struct MGArgs {
+  int L, ncol, cpb;
+  int64_t ncell;
+  const int32_t *col_nbr;
+  const int32_t *parent;   // MODE 2: column of the next coarser level
+};
+
+// x'(K) of the smoother input: x, or x + injected coarse correction e (MODE 2).
+template <typename T, int MODE>
+__device__ __forceinline__ T xin(const T *__restrict__ x, const T *__restrict__ e,
+                                 const int32_t *__restrict__ parent, int col, int k, int L) {
+  T v = x[(int64_t)col * L + k];
+  if (MODE == 2) v += e[(int64_t)__ldg(parent + col) * L + k];
+  return v;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x,
+                                     const T *__restrict__ e, const MGArgs &a, int c, int k) {
+  const int64_t C = a.ncell, K = (int64_t)c * a.L + k;
+  T y = __ldg(H + K) * xin<T, MODE>(x, e, a.parent, c, k, a.L);
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+    y += __ldg(H + (1 + f) * C + K) * xin<T, MODE>(x, e, a.parent, __ldg(a.col_nbr + 4 * (int64_t)c + f), k, a.L);
+  if (k > 0) y += __ldg(H + 5 * C + K) * xin<T, MODE>(x, e, a.parent, c, k - 1, a.L);
+  if (k < a.L - 1) y += __ldg(H + 6 * C + K) * xin<T, MODE>(x, e, a.parent, c, k + 1, a.L);
+  return y;
+}
+
+// MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x);
+// 2: as 1 with x replaced by x + P e (injection of the coarse correction e).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+    mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hinv,
+                     const T *__restrict__ hcp, const T *__restrict__ b, const T *__restrict__ x,
+                     const T *__restrict__ e, T *__restrict__ x_out, T omega) {
+  extern __shared__ unsigned char smem_raw[];
+  T *sr = reinterpret_cast<T *>(smem_raw);
+  T *ssub = sr + a.cpb * a.L, *sinv = ssub + a.cpb * a.L, *scp = sinv + a.cpb * a.L;
+  const int c0 = blockIdx.x * a.cpb;
+  const int nc = min(a.cpb, a.ncol - c0);
+  const int n = nc * a.L;
+  const int64_t base = (int64_t)c0 * a.L;
+  const int64_t C = a.ncell;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int c = c0 + i / a.L, k = i % a.L;
+    const int64_t K = base + i;
+    T r = b[K];
+    if (MODE != 0) r -= h_apply<T, MODE>(H, x, e, a, c, k);
+    sr[i] = r;
+    ssub[i] = k > 0 ? __ldg(H + 5 * C + K) : (T)0;
+    sinv[i] = __ldg(hinv + K);
+    scp[i] = __ldg(hcp + K);
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nc) {
+    const int o = threadIdx.x * a.L;
+    T y = sr[o] * sinv[o];
+    sr[o] = y;
+    for (int k = 1; k < a.L; ++k) {
+      y = (sr[o + k] - ssub[o + k] * y) * sinv[o + k];
+      sr[o + k] = y;
+    }
+    T xk = sr[o + a.L - 1];
+    for (int k = a.L - 2; k >= 0; --k) {
+      xk = sr[o + k] - scp[o + k] * xk;
+      sr[o + k] = xk;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int c = c0 + i / a.L, k = i % a.L;
+    const T old = MODE == 0 ? (T)0 : xin<T, MODE>(x, e, a.parent, c, k, a.L);
+    x_out[base + i] = old + omega * sr[i];
+  }
+}
+
+// b_coarse(cc, k) = sum over the four children ch of (b - H x)(ch, k); x == nullptr means 0.
+template <typename T>
+__global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict__ H,
+                                            const T *__restrict__ b, const T *__restrict__ x,
+                                            const int32_t *__restrict__ children, int ncol_c,
+                                            T *__restrict__ bc) {
+  const int64_t Kc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (Kc >= (int64_t)ncol_c * a.L) return;
+  const int cc = (int)(Kc / a.L), k = (int)(Kc - (int64_t)cc * a.L);
+  T s = (T)0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ch = __ldg(children + 4 * (int64_t)cc + i);
+    T r = b[(int64_t)ch * a.L + k];
+    if (x != nullptr) r -= h_apply<T, 1>(H, x, nullptr, a, ch, k);
+    s += r;
+  }
+  bc[Kc] = s;
+}
+
+template <typename T>
+__global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ x,
+                                T *__restrict__ y) {
+  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (K >= a.ncell) return;
+  const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
+  y[K] = h_apply<T, 1>(H, x, nullptr, a, c, k);
+}
+
+static MGArgs mg_args(const Ctx *c, int l) {
+  const Level &lv = c->lv[l];
+  MGArgs a;
+  a.L = lv.nlev;
+  a.ncol = lv.ncol;
+  a.cpb = 256 / lv.nlev > 0 ? 256 / lv.nlev : 1;
+  a.ncell = lv.ncell;
+  a.col_nbr = lv.col_nbr;
+  a.parent = lv.parent;
+  return a;
+}
+
+template <typename T, int MODE>
+static int smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
+  const Level &lv = c->lv[l];
+  MGArgs a = mg_args(c, l);
+  const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
+  const size_t smem = (size_t)4 * a.cpb * lv.nlev * sizeof(T);
+  mg_smooth_kernel<T, MODE><<<g, 256, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_inv(lv),
+                                                         Prec<T>::Hz_cp(lv), b, x, e, out,
+                                                         (T)c->opt.mg_omega);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// n sweeps on level l from zero (n >= 1); the result ends in *cur (one of lv.vx / lv.vy).
+template <typename T>
+static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur) {
+  Level &lv = c->lv[l];
+  T *x = static_cast<T *>(lv.vx), *y = static_cast<T *>(lv.vy);
+  int st;
+  if ((st = smooth<T, 0>(c, l, b, nullptr, nullptr, x))) return st;
+  for (int i = 1; i < n; ++i) {
+    if ((st = smooth<T, 1>(c, l, b, x, nullptr, y))) return st;
+    T *t = x; x = y; y = t;
+  }
+  *cur = x;
+  return HMG_OK;
+}
+
+template <typename T>
+int vcycle(Ctx *c, const T *b0, T **x_out) {
+  const int nmg = c->nmg;
+  const T *b[kMaxLevels];
+  T *x[kMaxLevels];
+  int st;
+  b[0] = b0;
+  for (int l = 0; l < nmg - 1; ++l) {
+    if ((st = sweeps_from_zero<T>(c, l, b[l], c->opt.mg_npre, &x[l]))) return st;
+    const Level &coarse = c->lv[l + 1];
+    MGArgs a = mg_args(c, l);
+    T *bc = static_cast<T *>(coarse.vb);
+    mg_residual_restrict_kernel<T><<<grid_for(coarse.ncell, 256), 256, 0, c->stream>>>(
+        a, Prec<T>::H(c->lv[l]), b[l], x[l], coarse.children, coarse.ncol, bc);
+    HMG_CUDA(c, cudaGetLastError());
+    b[l + 1] = bc;
+  }
+  const int lc = nmg - 1;
+  if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc]))) return st;
+  // options are validated to mg_npre >= 1 and mg_npost >= 1
+  for (int l = nmg - 2; l >= 0; --l) {
+    Level &lv = c->lv[l];
+    T *other = x[l] == static_cast<T *>(lv.vx) ? static_cast<T *>(lv.vy) : static_cast<T *>(lv.vx);
+    if ((st = smooth<T, 2>(c, l, b[l], x[l], x[l + 1], other))) return st;
+    T *cur = other, *nxt = x[l];
+    for (int i = 1; i < c->opt.mg_npost; ++i) {
+      if ((st = smooth<T, 1>(c, l, b[l], cur, nullptr, nxt))) return st;
+      T *t = cur; cur = nxt; nxt = t;
+    }
+    x[l] = cur;
+  }
+  *x_out = x[0];
+  return HMG_OK;
+}
+
+template int vcycle<double>(Ctx *, const double *, double **);
+template int vcycle<float>(Ctx *, const float *, float **);
+
+int pressure_vcycle_fp64(Ctx *c, const double *b, double *x) {
+  double *res = nullptr;
+  int st = vcycle<double>(c, b, &res);
+  if (st) return st;
+  HMG_CUDA(c, cudaMemcpyAsync(x, res, sizeof(double) * c->lv[0].ncell, cudaMemcpyDeviceToDevice,
+                              c->stream));
+  return HMG_OK;
+}
+
+int apply_pressure_fp64(Ctx *c, int l, const double *x, double *y) {
+  const Level &lv = c->lv[l];
+  MGArgs a = mg_args(c, l);
+  mg_apply_kernel<double><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(a, lv.H, x, y);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+}  // namespace hmg

@@ -1,0 +1,390 @@
+// Trace-space kernels of the solve: S apply (with fused inner products), the right-hand
+// side B_lambda, recovery, the line smoother (Algorithm 1), residual / restriction with the
+// coarse scaling, prolongation, and the two preconditioners (configuration 2: line smoother;
+// configuration 3c: Algorithm 2).
+//
+// Paper (arXiv 2210.11797): Eqs. hybrid-S, hybrid-rhs, hybrid-recovery (Sec. 2.4);
+// Algorithm 1 and Eq. banded_system; Algorithm 2; Sec. 2.5 intergrid operators
+// (P lambda = {{Pi}}, Restrict = P^T) and Eq. scaling_matrix.
+#include "device_common.cuh"
+#include "hmg_internal.cuh"
+#include "precond.cuh"
+
+namespace hmg {
+
+static TraceDims dims_of(const Level &f) { return TraceDims{f.nlev, f.nth, f.ntrace}; }
+
+// ---- y = S x with optional fused inner products -----------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads)
+    spmv_kernel(const double *__restrict__ S, const double *__restrict__ x, double *__restrict__ y,
+                const double *__restrict__ w, const TraceDims d, const int32_t *__restrict__ stencil,
+                const int32_t *__restrict__ col_edges, double *part, unsigned int *counter,
+                double *scal, int slot0, int slot1) {
+  double a0 = 0.0, a1 = 0.0;
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row < d.NT) {
+    double v = s_row<double, double, double>(S, x, stencil, col_edges, d, row);
+    if (MODE == 3) {
+      v = __ldg(w + row) - v;
+      a0 += v * v;
+    } else {
+      y[row] = v;
+      if (MODE == 1) a0 += __ldg(w + row) * v;
+      if (MODE == 2) { a0 += v * __ldg(w + row); a1 += v * v; }
+    }
+  }
+  if (MODE == 1 || MODE == 3) {
+    const double val[1] = {a0};
+    const int sl[1] = {slot0};
+    grid_reduce<1>(val, sl, part, counter, scal);
+  } else if (MODE == 2) {
+    const double val[2] = {a0, a1};
+    const int sl[2] = {slot0, slot1};
+    grid_reduce<2>(val, sl, part, counter, scal);
+  }
+}
+
+int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0,
+                int slot1) {
+  const Level &f = c->lv[0];
+  const TraceDims d = dims_of(f);
+  const unsigned g = grid_for(f.ntrace, kRedThreads);   // one row per thread
+  if (g > (unsigned)kMaxRedBlocks) return fail(c, HMG_ERR_INVALID_ARG, "too many rows for one reduction");
+  Prof prof(c, kCompApply);
+  switch (mode) {
+    case 0: spmv_kernel<0><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
+    case 1: spmv_kernel<1><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
+    case 2: spmv_kernel<2><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
+    default: spmv_kernel<3><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
+  }
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// ---- B_lambda = C^T A^-1 R_X ------------------------------------------------------------
+// Row f of B_lambda sums (A_K^-1 R_K)_{i} over the (one or two) cells K having f as local face i.
+__device__ __forceinline__ double ainv_row_dot(const double *__restrict__ Ainv, int64_t C, int64_t K,
+                                               int i, const double *__restrict__ Rub,
+                                               const double *__restrict__ Rpi) {
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s += __ldg(Ainv + (7 * i + j) * C + K) * __ldg(Rub + 6 * K + j);
+  s += __ldg(Ainv + (7 * i + 6) * C + K) * __ldg(Rpi + K);
+  return s;
+}
+
+__global__ void trace_rhs_kernel(const double *__restrict__ Ainv, const double *__restrict__ Rub,
+                                 const double *__restrict__ Rpi, double *__restrict__ B,
+                                 const TraceDims d, int64_t C, const int32_t *__restrict__ stencil,
+                                 const int32_t *__restrict__ edge_fc) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= d.NT) return;
+  double v;
+  if (row < d.NH) {
+    const int e = (int)(row / d.L), k = (int)(row - (int64_t)e * d.L);
+    const int64_t K1 = (int64_t)stencil[8 * (int64_t)e] * d.L + k;
+    const int64_t K2 = (int64_t)stencil[8 * (int64_t)e + 1] * d.L + k;
+    v = ainv_row_dot(Ainv, C, K1, edge_fc[2 * (int64_t)e], Rub, Rpi) +
+        ainv_row_dot(Ainv, C, K2, edge_fc[2 * (int64_t)e + 1], Rub, Rpi);
+  } else {
+    const int64_t zr = row - d.NH;
+    const int c = (int)(zr / (d.L + 1)), k = (int)(zr - (int64_t)c * (d.L + 1));
+    double va = 0.0, vb = 0.0;
+    if (k < d.L) va = ainv_row_dot(Ainv, C, (int64_t)c * d.L + k, 4, Rub, Rpi);
+    if (k > 0) vb = ainv_row_dot(Ainv, C, (int64_t)c * d.L + k - 1, 5, Rub, Rpi);
+    v = va + vb;
+  }
+  B[row] = v;
+}
+
+int launch_trace_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B) {
+  const Level &f = c->lv[0];
+  Prof prof(c, kCompRhs);
+  trace_rhs_kernel<<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
+      c->Ainv, Rub, Rpi, B, dims_of(f), f.ncell, f.edge_stencil, f.edge_fc);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// ---- X_K = A_K^-1 (R_K - K_K lambda_K) ---------------------------------------------------
+__global__ void reconstruct_kernel(const double *__restrict__ Ainv, const double *__restrict__ kth,
+                                   const double *__restrict__ lam, const double *__restrict__ Rub,
+                                   const double *__restrict__ Rpi, double *__restrict__ ub,
+                                   double *__restrict__ pi, const TraceDims d, int64_t C,
+                                   const int32_t *__restrict__ col_edges) {
+  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (K >= C) return;
+  const int c = (int)(K / d.L), k = (int)(K - (int64_t)c * d.L);
+  int64_t g[6];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) g[f] = (int64_t)col_edges[4 * (int64_t)c + f] * d.L + k;
+  g[4] = d.NH + (int64_t)c * (d.L + 1) + k;
+  g[5] = g[4] + 1;
+  double rm[7];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) rm[f] = Rub[6 * K + f] - kth[f * C + K] * lam[g[f]];
+  rm[6] = Rpi[K];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s += Ainv[(7 * i + j) * C + K] * rm[j];
+    if (i < 6) ub[6 * K + i] = s; else pi[K] = s;
+  }
+}
+
+int launch_reconstruct(Ctx *c, const double *lam, const double *Rub, const double *Rpi,
+                       double *ub, double *pi) {
+  const Level &f = c->lv[0];
+  reconstruct_kernel<<<grid_for(f.ncell, 128), 128, 0, c->stream>>>(
+      c->Ainv, c->kth, lam, Rub, Rpi, ub, pi, dims_of(f), f.ncell, f.col_edges);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// ---- Algorithm 1: one sweep ---------------------------------------------------------------
+// lam_out = lam_in + omega D^-1 (b - S lam_in), D = [diag(S^hh), blockdiag(S^zz_c)]. With
+// ZERO, lam_in = 0 and the sweep needs no S apply. Blocks [0, nzb) take CPB columns of
+// lambda^z each (residual rows staged in shared memory, one thread per column runs the
+// Thomas solve with the precomputed factors); the remaining blocks take lambda^h rows.
+struct SweepArgs {
+  TraceDims d;
+  int ncol, cpb, nzb;
+  const int32_t *stencil, *col_edges;
+};
+
+template <typename T, typename Tb, typename Tout, bool ZERO>
+__global__ void __launch_bounds__(256)
+    sweep_kernel(const SweepArgs a, const T *__restrict__ S, const T *__restrict__ zinv,
+                 const T *__restrict__ zcp, const T *__restrict__ hinv, const Tb *__restrict__ b,
+                 const T *__restrict__ lam_in, Tout *__restrict__ lam_out, T omega) {
+  extern __shared__ unsigned char smem_raw[];
+  const TraceDims &d = a.d;
+  if ((int)blockIdx.x < a.nzb) {
+    T *sr = reinterpret_cast<T *>(smem_raw);
+    const int L1 = d.L + 1;
+    const int c0 = blockIdx.x * a.cpb;
+    const int nc = min(a.cpb, a.ncol - c0);
+    const int nrow = nc * L1;
+    T *ssub = sr + a.cpb * L1, *sinv = ssub + a.cpb * L1, *scp = sinv + a.cpb * L1;
+    const int64_t base = d.NH + (int64_t)c0 * L1;
+    for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+      const int64_t row = base + i;
+      T r = (T)__ldg(b + row);
+      if (!ZERO) r -= s_row_z<T, T, T>(S, lam_in, a.col_edges, d, row);
+      const int k = i % L1;
+      sr[i] = r;
+      ssub[i] = k > 0 ? __ldg(S + 10 * d.NT + row) : (T)0;
+      sinv[i] = __ldg(zinv + (row - d.NH));
+      scp[i] = __ldg(zcp + (row - d.NH));
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nc) {
+      const int o = threadIdx.x * L1;
+      T y = sr[o] * sinv[o];
+      sr[o] = y;
+      for (int k = 1; k < L1; ++k) {
+        y = (sr[o + k] - ssub[o + k] * y) * sinv[o + k];
+        sr[o + k] = y;
+      }
+      T xk = sr[o + L1 - 1];
+      for (int k = L1 - 2; k >= 0; --k) {
+        xk = sr[o + k] - scp[o + k] * xk;
+        sr[o + k] = xk;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+      const int64_t row = base + i;
+      const T old = ZERO ? (T)0 : lam_in[row];
+      lam_out[row] = (Tout)(old + omega * sr[i]);
+    }
+  } else {
+    const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
+    if (row >= d.NH) return;
+    T r = (T)__ldg(b + row);
+    if (!ZERO) r -= s_row_h<T, T, T>(S, lam_in, a.stencil, d, row);
+    const T old = ZERO ? (T)0 : lam_in[row];
+    lam_out[row] = (Tout)(old + omega * r * __ldg(hinv + row));
+  }
+}
+
+template <typename T, typename Tb, typename Tout, bool ZERO>
+static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out) {
+  const Level &f = c->lv[0];
+  SweepArgs a;
+  a.d = dims_of(f);
+  a.ncol = f.ncol;
+  a.cpb = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
+  a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
+  a.stencil = f.edge_stencil;
+  a.col_edges = f.col_edges;
+  const unsigned nhb = grid_for(f.nth, 256);
+  const size_t smem = (size_t)4 * a.cpb * (f.nlev + 1) * sizeof(T);
+  Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
+  sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, 256, smem, c->stream>>>(
+      a, Prec<T>::S(c), Prec<T>::Sz_inv(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_inv(c), b, lam_in,
+      lam_out, (T)c->opt.omega);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// ---- R = b - S lam (Algorithm 2 line 3) ------------------------------------------------------
+template <typename T, typename Tb>
+__global__ void __launch_bounds__(256)
+    residual_kernel(const T *__restrict__ S, const Tb *__restrict__ b, const T *__restrict__ lam,
+                    T *__restrict__ R, const TraceDims d, const int32_t *__restrict__ stencil,
+                    const int32_t *__restrict__ col_edges) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= d.NT) return;
+  R[row] = (T)__ldg(b + row) - s_row<T, T, T>(S, lam, stencil, col_edges, d, row);
+}
+
+// ---- bbar = Gamma P^T R (Algorithm 2 lines 4-5) -----------------------------------------
+// P^T weights: 1/2 on interior faces (both neighbours share the facet), 1 on ground and lid.
+template <typename T>
+__global__ void restrict_kernel(const T *__restrict__ R, const T *__restrict__ gamma,
+                                T *__restrict__ bbar, const TraceDims d, int64_t C,
+                                const int32_t *__restrict__ col_edges) {
+  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (K >= C) return;
+  const int c = (int)(K / d.L), k = (int)(K - (int64_t)c * d.L);
+  const int32_t *ce = col_edges + 4 * (int64_t)c;
+  T s = (T)0.5 * (R[(int64_t)__ldg(ce) * d.L + k] + R[(int64_t)__ldg(ce + 1) * d.L + k] +
+                  R[(int64_t)__ldg(ce + 2) * d.L + k] + R[(int64_t)__ldg(ce + 3) * d.L + k]);
+  const int64_t zb = d.NH + (int64_t)c * (d.L + 1) + k;
+  s += (k == 0 ? (T)1 : (T)0.5) * R[zb];
+  s += (k == d.L - 1 ? (T)1 : (T)0.5) * R[zb + 1];
+  bbar[K] = gamma[K] * s;
+}
+
+// ---- lam_out = lam_in + P dPi (Algorithm 2 line 7) ---------------------------------------
+template <typename T>
+__global__ void prolong_kernel(const T *__restrict__ lam_in, const T *__restrict__ dpi,
+                               T *__restrict__ lam_out, const TraceDims d,
+                               const int32_t *__restrict__ stencil) {
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= d.NT) return;
+  T p;
+  if (row < d.NH) {
+    const int e = (int)(row / d.L), k = (int)(row - (int64_t)e * d.L);
+    p = (T)0.5 * (dpi[(int64_t)stencil[8 * (int64_t)e] * d.L + k] +
+                  dpi[(int64_t)stencil[8 * (int64_t)e + 1] * d.L + k]);
+  } else {
+    const int64_t zr = row - d.NH;
+    const int c = (int)(zr / (d.L + 1)), k = (int)(zr - (int64_t)c * (d.L + 1));
+    const int64_t K = (int64_t)c * d.L + k;
+    if (k == 0) p = dpi[K];
+    else if (k == d.L) p = dpi[K - 1];
+    else p = (T)0.5 * (dpi[K - 1] + dpi[K]);
+  }
+  lam_out[row] = lam_in[row] + p;
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (Tout)in[i];
+}
+
+// ---- preconditioners -----------------------------------------------------------------------
+// Configuration 2: n_smooth sweeps of Algorithm 1 from zero.
+template <typename T>
+static int line_precond(Ctx *c, const double *r, double *z) {
+  const int n = c->opt.n_smooth;
+  T *a = static_cast<T *>(c->w1), *b2 = static_cast<T *>(c->w2);
+  int st;
+  if (n == 1) return launch_sweep<T, double, double, true>(c, r, nullptr, z);
+  if ((st = launch_sweep<T, double, T, true>(c, r, nullptr, a))) return st;
+  for (int i = 1; i < n - 1; ++i) {
+    if ((st = launch_sweep<T, double, T, false>(c, r, a, b2))) return st;
+    T *t = a; a = b2; b2 = t;
+  }
+  return launch_sweep<T, double, double, false>(c, r, a, z);
+}
+
+// Configuration 3c: Algorithm 2 with one pressure V-cycle as the coarse solve.
+template <typename T>
+static int two_level(Ctx *c, const double *r, double *z) {
+  const Level &f = c->lv[0];
+  const TraceDims d = dims_of(f);
+  T *w1 = static_cast<T *>(c->w1), *w2 = static_cast<T *>(c->w2), *w3 = static_cast<T *>(c->w3);
+  int st;
+  // line 1-2: lambda = 0, presmooth
+  if (c->opt.n_pre >= 1) {
+    if ((st = launch_sweep<T, double, T, true>(c, r, nullptr, w1))) return st;
+    for (int i = 1; i < c->opt.n_pre; ++i) {
+      if ((st = launch_sweep<T, double, T, false>(c, r, w1, w2))) return st;
+      T *t = w1; w1 = w2; w2 = t;
+    }
+  } else {
+    HMG_CUDA(c, cudaMemsetAsync(w1, 0, sizeof(T) * f.ntrace, c->stream));
+  }
+  // lines 3-5: R = r - S lambda; bbar = Gamma P^T R
+  T *cb = static_cast<T *>(c->cb);
+  {
+    Prof pr(c, kCompResidual, 2);
+    residual_kernel<T, double><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
+        Prec<T>::S(c), r, w1, w2, d, f.edge_stencil, f.col_edges);
+    restrict_kernel<T><<<grid_for(f.ncell, 256), 256, 0, c->stream>>>(w2, Prec<T>::gamma(c), cb, d,
+                                                                      f.ncell, f.col_edges);
+  }
+  HMG_CUDA(c, cudaGetLastError());
+  // line 6: one V-cycle of the pressure multigrid
+  T *dpi = nullptr;
+  {
+    const int nl = c->nmg - 1;
+    Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * c->opt.mg_npost);
+    if ((st = vcycle<T>(c, cb, &dpi))) return st;
+  }
+  // line 7: lambda += P dPi
+  {
+    Prof pp(c, kCompProlong);
+    prolong_kernel<T><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(w1, dpi, w2, d, f.edge_stencil);
+  }
+  HMG_CUDA(c, cudaGetLastError());
+  // line 8: postsmooth
+  const int np = c->opt.n_post;
+  if (np == 0) {
+    convert_kernel<T, double><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(w2, z, f.ntrace);
+    HMG_CUDA(c, cudaGetLastError());
+    return HMG_OK;
+  }
+  T *cur = w2, *nxt = w3;
+  for (int i = 0; i < np - 1; ++i) {
+    if ((st = launch_sweep<T, double, T, false>(c, r, cur, nxt))) return st;
+    T *t = cur; cur = nxt; nxt = t;
+  }
+  return launch_sweep<T, double, double, false>(c, r, cur, z);
+}
+
+int precond_apply(Ctx *c, const double *r, double *z) {
+  const bool mixed = c->opt.precision == HMG_PRECISION_MIXED;
+  switch (c->opt.precond) {
+    case HMG_PRECOND_NONE:
+      HMG_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * c->lv[0].ntrace, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+      return HMG_OK;
+    case HMG_PRECOND_LINESMOOTH:
+      return mixed ? line_precond<float>(c, r, z) : line_precond<double>(c, r, z);
+    default:
+      return mixed ? two_level<float>(c, r, z) : two_level<double>(c, r, z);
+  }
+}
+
+int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps) {
+  // ping-pong between lam and a work vector; one copy at the end if the count is odd
+  double *cur = lam, *nxt = static_cast<double *>(c->w3);
+  int st;
+  for (int i = 0; i < nsweeps; ++i) {
+    if ((st = launch_sweep<double, double, double, false>(c, b, cur, nxt))) return st;
+    double *t = cur; cur = nxt; nxt = t;
+  }
+  if (cur != lam)
+    HMG_CUDA(c, cudaMemcpyAsync(lam, cur, sizeof(double) * c->lv[0].ntrace,
+                                cudaMemcpyDeviceToDevice, c->stream));
+  return HMG_OK;
+}
+
+}  // namespace hmg

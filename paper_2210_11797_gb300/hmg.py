@@ -1,0 +1,303 @@
+"""Python binding of libhmg.so (C ABI in include/hmg.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library. PyTorch is used for device memory and the
+stream (tensors are passed by data_ptr()). If the library has not been built this module
+raises on first use; there is no CPU fallback.
+
+Low-level functions carry the C names (hmg_create, hmg_solve, ...); `Solver` wraps one
+context for a mesh hierarchy + coefficients produced by `paper_2210_11797_gb300.inputs`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HMG_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "not_ready", 4: "not_converged",
+                5: "breakdown", 6: "nonfinite", 7: "timeout", 8: "out_of_memory"}
+PRECISION = {"fp64": 0, "mixed": 1}
+PRECOND = {"none": 0, "linesmooth": 1, "nonnested": 2}
+MAX_HISTORY = 512
+NCOMP = 8
+COMPONENTS = ["trace_rhs", "trace_apply", "presmooth", "line_sweep", "residual_restrict",
+              "pressure_vcycle", "prolong", "krylov_vectors"]
+
+
+class HmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshLevel(C.Structure):
+    _fields_ = [("geometry", C.c_int32), ("ncol", C.c_int32), ("nlev", C.c_int32), ("nedge", C.c_int32),
+                ("radius", C.c_double), ("corners", C.c_void_p), ("z_levels", C.c_void_p),
+                ("col_edges", C.c_void_p), ("edge_cols", C.c_void_p), ("edge_face", C.c_void_p),
+                ("parent", C.c_void_p)]
+
+
+class Background(C.Structure):
+    _fields_ = [("theta_lev", C.c_void_p), ("exner_lev", C.c_void_p), ("exner", C.c_void_p)]
+
+
+class Scalars(C.Structure):
+    _fields_ = [("dt", C.c_double), ("tau_u", C.c_double), ("tau_rho", C.c_double),
+                ("tau_theta", C.c_double), ("cp", C.c_double), ("kappa", C.c_double),
+                ("preset", C.c_int32), ("sigma", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("precond", C.c_int32), ("n_pre", C.c_int32),
+                ("n_post", C.c_int32), ("n_smooth", C.c_int32), ("omega", C.c_double),
+                ("mg_npre", C.c_int32), ("mg_npost", C.c_int32), ("mg_ncoarse", C.c_int32),
+                ("mg_omega", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("divergence", C.c_double), ("profile", C.c_int32)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("true_rel_residual", C.c_double), ("solve_ms", C.c_double), ("n_history", C.c_int32),
+                ("history", C.c_double * MAX_HISTORY), ("comp_ms", C.c_double * NCOMP),
+                ("comp_calls", C.c_int32 * NCOMP)]
+
+    def as_dict(self):
+        return {"status": STATUS_NAMES.get(self.status, self.status), "iterations": self.iterations,
+                "rel_residual": self.rel_residual, "true_rel_residual": self.true_rel_residual,
+                "solve_ms": self.solve_ms, "history": list(self.history[: self.n_history]),
+                "components": {n: {"ms": self.comp_ms[i], "launches": self.comp_calls[i]}
+                               for i, n in enumerate(COMPONENTS)}}
+
+
+_LIB = None
+_P = C.c_void_p
+_SIGS = {
+    "hmg_default_options": ([C.POINTER(Options)], C.c_int),
+    "hmg_create": ([C.POINTER(_P), C.POINTER(Options), _P], C.c_int),
+    "hmg_set_options": ([_P, C.POINTER(Options)], C.c_int),
+    "hmg_set_mesh": ([_P, C.c_int32, C.POINTER(MeshLevel)], C.c_int),
+    "hmg_set_coefficients": ([_P, C.POINTER(Scalars), C.POINTER(Background)], C.c_int),
+    "hmg_assemble_trace": ([_P], C.c_int),
+    "hmg_sizes": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "hmg_destroy": ([_P], None),
+    "hmg_status_string": ([C.c_int], C.c_char_p),
+    "hmg_last_error": ([_P], C.c_char_p),
+    "hmg_trace_rhs": ([_P, _P, _P, _P], C.c_int),
+    "hmg_solve": ([_P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
+    "hmg_solve_host": ([_P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
+    "hmg_reconstruct": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "hmg_apply_trace": ([_P, _P, _P], C.c_int),
+    "hmg_precond_apply": ([_P, _P, _P], C.c_int),
+    "hmg_line_smooth": ([_P, _P, _P, C.c_int32], C.c_int),
+    "hmg_apply_pressure": ([_P, C.c_int32, _P, _P], C.c_int),
+    "hmg_pressure_vcycle": ([_P, _P, _P], C.c_int),
+    "hmg_get_gamma": ([_P, _P], C.c_int),
+    "hmg_get_trace_operator": ([_P, _P], C.c_int),
+}
+
+
+def header_symbols():
+    """Names of the functions declared in include/hmg.h."""
+    import re
+    path = os.path.join(_build.INCLUDE, "hmg.h")
+    src = open(path).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(hmg_\w+)\s*\(", src, re.M)))
+
+
+def lib():
+    """Load libhmg.so (built in-tree by paper_2210_11797_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2210_11797_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+def _check(ctx, st):
+    if st != HMG_OK:
+        msg = lib().hmg_last_error(ctx).decode() if ctx else lib().hmg_status_string(st).decode()
+        raise HmgError(st, msg)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().hmg_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One library context: mesh hierarchy, coefficients, assembled operators, workspace."""
+
+    def __init__(self, hier, coeffs, stream=None, **options):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.opts = default_options(**options)
+        self.ctx = C.c_void_p()
+        _check(None, lib().hmg_create(C.byref(self.ctx), C.byref(self.opts), C.c_void_p(self.stream.cuda_stream)))
+        self._keep = []
+        self._set_mesh(hier)
+        self._set_coefficients(coeffs)
+        _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+        nc, nt = C.c_int64(), C.c_int64()
+        _check(self.ctx, lib().hmg_sizes(self.ctx, C.byref(nc), C.byref(nt)))
+        self.ncell, self.ntrace = nc.value, nt.value
+        self._keep = []
+
+    def _arr(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self._keep.append(a)
+        return a.ctypes.data_as(C.c_void_p)
+
+    def _set_mesh(self, hier):
+        levels = (MeshLevel * hier.nmg)()
+        for l, m in enumerate(hier.meshes):
+            lv = levels[l]
+            lv.geometry, lv.ncol, lv.nlev, lv.nedge = m.geometry, m.ncol, m.nlev, m.nedge
+            lv.radius = m.radius
+            lv.corners = self._arr(m.corners, np.float64)
+            lv.z_levels = self._arr(m.z_levels, np.float64)
+            lv.col_edges = self._arr(m.col_edges, np.int32)
+            lv.edge_cols = self._arr(m.edge_cols, np.int32)
+            lv.edge_face = self._arr(m.edge_face, np.int8)
+            lv.parent = self._arr(hier.parents[l], np.int32) if l + 1 < hier.nmg else None
+        _check(self.ctx, lib().hmg_set_mesh(self.ctx, hier.nmg, levels))
+        self.nmg = hier.nmg
+        self.level_cells = [m.ncell for m in hier.meshes]
+
+    def _set_coefficients(self, co):
+        sc = Scalars(co.dt, co.tau_u, co.tau_rho, co.tau_theta, co.cp, co.kappa, co.preset, co.sigma)
+        bgs = (Background * len(co.levels))()
+        for l, bg in enumerate(co.levels):
+            bgs[l].theta_lev = self._arr(bg.theta_lev, np.float64)
+            bgs[l].exner_lev = self._arr(bg.exner_lev, np.float64)
+            bgs[l].exner = self._arr(bg.exner, np.float64)
+        _check(self.ctx, lib().hmg_set_coefficients(self.ctx, C.byref(sc), bgs))
+
+    # -- helpers --------------------------------------------------------------------------
+    def _dev(self, t, n, name):
+        torch = self.torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{name}: expected a contiguous float64 CUDA tensor")
+        if t.numel() != n:
+            raise ValueError(f"{name}: expected {n} elements, got {t.numel()}")
+        return _ptr(t)
+
+    def _empty(self, n):
+        return self.torch.empty(n, dtype=self.torch.float64, device=self.device)
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISION[v]
+            if k == "precond" and isinstance(v, str):
+                v = PRECOND[v]
+            setattr(self.opts, k, v)
+        _check(self.ctx, lib().hmg_set_options(self.ctx, C.byref(self.opts)))
+        if self.opts.precision == PRECISION["mixed"]:
+            _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+
+    # -- the calls ------------------------------------------------------------------------
+    def trace_rhs(self, Rub, Rpi):
+        B = self._empty(self.ntrace)
+        _check(self.ctx, lib().hmg_trace_rhs(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"),
+                                             self._dev(Rpi, self.ncell, "Rpi"), _ptr(B)))
+        return B
+
+    def solve(self, Rub, Rpi, lam=None, check=True):
+        lam = self._empty(self.ntrace) if lam is None else lam
+        st = SolveStats()
+        rc = lib().hmg_solve(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"), self._dev(Rpi, self.ncell, "Rpi"),
+                             self._dev(lam, self.ntrace, "lambda"), C.byref(st))
+        if check:
+            _check(self.ctx, rc)
+        return lam, st.as_dict()
+
+    def solve_host(self, Rub, Rpi, check=True):
+        Rub = np.ascontiguousarray(Rub, np.float64)
+        Rpi = np.ascontiguousarray(Rpi, np.float64)
+        if Rub.size != 6 * self.ncell or Rpi.size != self.ncell:
+            raise ValueError("Rub / Rpi size")
+        lam = np.empty(self.ntrace)
+        st = SolveStats()
+        rc = lib().hmg_solve_host(self.ctx, Rub.ctypes.data_as(C.c_void_p), Rpi.ctypes.data_as(C.c_void_p),
+                                  lam.ctypes.data_as(C.c_void_p), C.byref(st))
+        if check:
+            _check(self.ctx, rc)
+        return lam, st.as_dict()
+
+    def reconstruct(self, lam, Rub, Rpi):
+        ub, pi = self._empty(6 * self.ncell), self._empty(self.ncell)
+        _check(self.ctx, lib().hmg_reconstruct(self.ctx, self._dev(lam, self.ntrace, "lambda"),
+                                               self._dev(Rub, 6 * self.ncell, "Rub"),
+                                               self._dev(Rpi, self.ncell, "Rpi"), _ptr(ub), _ptr(pi)))
+        return ub, pi
+
+    def apply_trace(self, x):
+        y = self._empty(self.ntrace)
+        _check(self.ctx, lib().hmg_apply_trace(self.ctx, self._dev(x, self.ntrace, "x"), _ptr(y)))
+        return y
+
+    def precond(self, r):
+        z = self._empty(self.ntrace)
+        _check(self.ctx, lib().hmg_precond_apply(self.ctx, self._dev(r, self.ntrace, "r"), _ptr(z)))
+        return z
+
+    def line_smooth(self, b, lam, nsweeps):
+        _check(self.ctx, lib().hmg_line_smooth(self.ctx, self._dev(b, self.ntrace, "b"),
+                                               self._dev(lam, self.ntrace, "lambda"), nsweeps))
+        return lam
+
+    def apply_pressure(self, level, x):
+        n = self.level_cells[level]
+        y = self._empty(n)
+        _check(self.ctx, lib().hmg_apply_pressure(self.ctx, level, self._dev(x, n, "x"), _ptr(y)))
+        return y
+
+    def vcycle(self, b):
+        x = self._empty(self.ncell)
+        _check(self.ctx, lib().hmg_pressure_vcycle(self.ctx, self._dev(b, self.ncell, "b"), _ptr(x)))
+        return x
+
+    def gamma(self):
+        g = self._empty(self.ncell)
+        _check(self.ctx, lib().hmg_get_gamma(self.ctx, _ptr(g)))
+        return g
+
+    def trace_operator_slots(self):
+        out = self.torch.empty((11, self.ntrace), dtype=self.torch.float64, device=self.device)
+        _check(self.ctx, lib().hmg_get_trace_operator(self.ctx, _ptr(out)))
+        return out
+
+    def close(self):
+        if self.ctx:
+            lib().hmg_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,323 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle, kernel by kernel and
+for whole solves. Needs a GB300 and the built library.
+
+Tolerances (FP64, unit roundoff u = 1.1e-16):
+* a single S or H row (<= 11 products) differs from the oracle's sum by <= ~11 u sum|a_i x_i|;
+  we allow 1e-13 relative to (|S| |x|) row by row;
+* local LU / inverse (7x7, partial pivoting in both): 1e-11 relative per entry block;
+* composite operators (a sweep, a V-cycle, Algorithm 2): 1e-11 in max norm relative to
+  the output's max norm (a few dozen well-conditioned steps);
+* whole solves converged to 1e-12 on both sides: relative 2-norm difference < 1e-9
+  (the FP64 parity target of the method's statement).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import fem
+from oracle.nonnested import HybridSolver, OracleOptions
+from paper_2210_11797_gb300 import inputs as I
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _workloads():
+    yield "planar16", I.planar_helmholtz()
+    yield "sphereC6L5", I.cubed_sphere(6, 5, courant=8.0, nmg=2, seed=4)
+    yield "sphereC12L30", I.cubed_sphere(12, 30)
+
+
+_CACHE = {}
+
+
+def _pair(name):
+    if name not in _CACHE:
+        from paper_2210_11797_gb300.hmg import Solver
+        w = dict(_workloads())[name]
+        ora = HybridSolver(w.hier, w.coeffs)
+        gpu = Solver(w.hier, w.coeffs, tol=w.tol)
+        _CACHE[name] = (w, ora, gpu)
+    return _CACHE[name]
+
+
+NAMES = ["planar16", "sphereC6L5", "sphereC12L30"]
+
+
+def _slots_to_matrix(mesh, slots):
+    """Sparse S from the library's 11 slots per row, with the slot layout documented in
+    include/hmg.h (hmg_get_trace_operator) spelled out independently here."""
+    import scipy.sparse as sp
+    L, NH, T = mesh.nlev, mesh.n_trace_h, mesh.n_trace
+    rows, cols, vals = [], [], []
+    e = np.repeat(np.arange(mesh.nedge), L)
+    k = np.tile(np.arange(L), mesh.nedge)
+    r = e * L + k
+    c1, c2 = mesh.edge_cols[e, 0].astype(np.int64), mesh.edge_cols[e, 1].astype(np.int64)
+    i1, i2 = mesh.edge_face[e, 0].astype(np.int64), mesh.edge_face[e, 1].astype(np.int64)
+    hcols = [r]
+    hcols += [mesh.col_edges[c1, (i1 + m) % 4] * L + k for m in (1, 2, 3)]
+    hcols += [NH + c1 * (L + 1) + k, NH + c1 * (L + 1) + k + 1]
+    hcols += [mesh.col_edges[c2, (i2 + m) % 4] * L + k for m in (1, 2, 3)]
+    hcols += [NH + c2 * (L + 1) + k, NH + c2 * (L + 1) + k + 1]
+    for sl, cc in enumerate(hcols):
+        rows.append(r); cols.append(cc); vals.append(slots[sl, :NH])
+    c = np.repeat(np.arange(mesh.ncol), L + 1)
+    kz = np.tile(np.arange(L + 1), mesh.ncol)
+    rz = NH + c * (L + 1) + kz
+    up, dn = kz < L, kz > 0
+    zc = [(rz, np.ones_like(up))]
+    zc += [(mesh.col_edges[c, i] * L + kz, up) for i in range(4)] + [(rz + 1, up)]
+    zc += [(mesh.col_edges[c, i] * L + kz - 1, dn) for i in range(4)] + [(rz - 1, dn)]
+    for sl, (cc, ok) in enumerate(zc):
+        ok = ok.astype(bool)
+        rows.append(rz[ok]); cols.append(cc[ok]); vals.append(slots[sl, NH:][ok])
+        assert np.all(slots[sl, NH:][~ok] == 0.0)
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(T, T)).tocsr()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_trace_operator_entries_match_oracle(name):
+    """Assembly parity: every entry of S within 1e-13 of its row's largest entry (both sides
+    invert A_K by block elimination, accurate to a few ulps of the row scale)."""
+    w, ora, gpu = _pair(name)
+    Sg = _slots_to_matrix(w.mesh, _np(gpu.trace_operator_slots()))
+    d = abs(Sg - ora.S).tocsr()
+    rowmax = abs(ora.S).max(axis=1).toarray().ravel()
+    assert np.all(d.max(axis=1).toarray().ravel() <= 1e-13 * rowmax)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_trace_apply_matches_assembled_operator(name):
+    """Apply parity: y = S x from the kernel equals the CPU product with the same entries to
+    within 11 roundings of sum |S_ij x_j|."""
+    w, ora, gpu = _pair(name)
+    Sg = _slots_to_matrix(w.mesh, _np(gpu.trace_operator_slots()))
+    x = np.random.default_rng(1).standard_normal(gpu.ntrace)
+    y = _np(gpu.apply_trace(_cuda(x)))
+    scale = abs(Sg) @ np.abs(x)
+    assert np.all(np.abs(y - Sg @ x) <= 2e-15 * 11 * scale)
+    want = ora.S @ x
+    assert np.all(np.abs(y - want) <= 1e-12 * (abs(ora.S) @ np.abs(x)))
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_trace_rhs_and_reconstruct_match_oracle(name):
+    w, ora, gpu = _pair(name)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    B = _np(gpu.trace_rhs(Rub, Rpi))
+    Bo = ora.rhs(w.Rub, w.Rpi)
+    assert np.abs(B - Bo).max() <= 1e-11 * np.abs(Bo).max()
+    lam = np.random.default_rng(2).standard_normal(gpu.ntrace)
+    ub, pi = gpu.reconstruct(_cuda(lam), Rub, Rpi)
+    ubo, pio = ora.reconstruct(lam, w.Rub, w.Rpi)
+    assert np.abs(_np(ub).reshape(-1, 6) - ubo).max() <= 1e-11 * np.abs(ubo).max()
+    assert np.abs(_np(pi) - pio).max() <= 1e-11 * np.abs(pio).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_line_smoother_matches_oracle(name):
+    w, ora, gpu = _pair(name)
+    rng = np.random.default_rng(3)
+    lam, B = rng.standard_normal(gpu.ntrace), ora.S @ rng.standard_normal(gpu.ntrace)
+    got = _np(gpu.line_smooth(_cuda(B), _cuda(lam), 2))
+    want = ora.smoother.smooth(lam, B, 0.6, 2)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_pressure_operator_and_vcycle_match_oracle(name):
+    w, ora, gpu = _pair(name)
+    rng = np.random.default_rng(4)
+    for l in range(w.hier.nmg):
+        x = rng.standard_normal(w.hier.meshes[l].ncell)
+        y = _np(gpu.apply_pressure(l, _cuda(x)))
+        H = ora.mg.H[l]
+        assert np.all(np.abs(y - H @ x) <= 1e-12 * (abs(H) @ np.abs(x)))
+    b = rng.standard_normal(gpu.ncell)
+    got = _np(gpu.vcycle(_cuda(b)))
+    want = ora.mg.vcycle(b)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+    g = _np(gpu.gamma())
+    assert np.abs(g - ora.gamma).max() <= 1e-12 * np.abs(ora.gamma).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_two_level_preconditioner_matches_oracle(name):
+    w, ora, gpu = _pair(name)
+    r = ora.S @ np.random.default_rng(5).standard_normal(gpu.ntrace)
+    got = _np(gpu.precond(_cuda(r)))
+    want = ora.two_level(r)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_matches_oracle(name):
+    w, ora, gpu = _pair(name)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    gpu.set_options(tol=1e-12)
+    try:
+        lam, st = gpu.solve(Rub, Rpi)
+    finally:
+        gpu.set_options(tol=w.tol)
+    lo, hist, sto = ora.solve(w.Rub, w.Rpi, 1e-12)
+    assert st["status"] == "ok" and sto == "ok"
+    lam = _np(lam)
+    assert np.linalg.norm(lam - lo) / np.linalg.norm(lo) < 1e-9
+    assert abs(st["iterations"] - (len(hist) - 1)) <= 1
+    # residual histories agree while they are well above rounding
+    n = min(len(hist), len(st["history"]), 6)
+    np.testing.assert_allclose(st["history"][:n], hist[:n], rtol=1e-7)
+    assert st["true_rel_residual"] <= 1.01e-12 * 10
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_at_method_tolerance_and_host_path(name):
+    w, ora, gpu = _pair(name)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam, st = gpu.solve(Rub, Rpi)
+    assert st["status"] == "ok" and st["rel_residual"] <= w.tol
+    # the oracle's own S certifies the residual of the GPU answer
+    B = ora.rhs(w.Rub, w.Rpi)
+    lam = _np(lam)
+    assert np.linalg.norm(B - ora.S @ lam) / np.linalg.norm(B) <= 1.05 * w.tol
+    lam_h, st_h = gpu.solve_host(w.Rub, w.Rpi)
+    assert np.array_equal(lam_h, lam)                  # deterministic reductions
+    assert st_h["iterations"] == st["iterations"]
+
+
+def test_mixed_precision_preconditioner_reaches_fp64_tolerance():
+    w, ora, gpu = _pair("sphereC12L30")
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    gpu.set_options(precision="mixed")
+    try:
+        lam, st = gpu.solve(Rub, Rpi)
+    finally:
+        gpu.set_options(precision="fp64")
+    assert st["status"] == "ok"
+    B = ora.rhs(w.Rub, w.Rpi)
+    lam = _np(lam)
+    assert np.linalg.norm(B - ora.S @ lam) / np.linalg.norm(B) <= 1.05 * w.tol
+    lo, _h, _s = ora.solve(w.Rub, w.Rpi, 1e-12)
+    # forward error of a 1e-6 residual solve, reported against the converged FP64 oracle
+    assert np.linalg.norm(lam - lo) / np.linalg.norm(lo) < 1e-3
+
+
+def test_configuration2_line_smoother_preconditioner():
+    w, ora, gpu = _pair("planar16")
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    gpu.set_options(precond="linesmooth", n_smooth=2)
+    try:
+        r = ora.S @ np.random.default_rng(6).standard_normal(gpu.ntrace)
+        got = _np(gpu.precond(_cuda(r)))
+        ora.opts = OracleOptions(precond="linesmooth", n_smooth=2)
+        want = ora.precond(r)
+        ora.opts = OracleOptions()
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+        lam, st = gpu.solve(Rub, Rpi)
+        assert st["status"] == "ok"
+    finally:
+        gpu.set_options(precond="nonnested", n_smooth=1)
+
+
+def test_failure_paths_report_status():
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w, ora, gpu = _pair("planar16")
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    gpu.set_options(max_iter=2, tol=1e-14)
+    try:
+        _lam, st = gpu.solve(Rub, Rpi, check=False)
+        assert st["status"] == "not_converged" and st["iterations"] == 2
+    finally:
+        gpu.set_options(max_iter=200, tol=w.tol)
+    bad = w.Rpi.copy()
+    bad[7] = np.nan
+    _lam, st = gpu.solve(Rub, _cuda(bad), check=False)
+    assert st["status"] == "nonfinite"
+    # an inconsistent mesh table is rejected before anything runs on the device
+    h = I.planar_hierarchy(4, 2, 1.0, I.uniform_levels(2, 0.1), 1)
+    h.meshes[0].col_edges[3, 1] = 0
+    with pytest.raises(HmgError) as e:
+        Solver(h, I.Coefficients([I.unit_background(h.meshes[0])], preset=1, sigma=1.0))
+    assert e.value.status == 1
+    # divergence (omega far above the stable range with two post-smooths) is detected
+    gpu.set_options(omega=1.9, max_iter=60)
+    try:
+        _lam, st = gpu.solve(Rub, Rpi, check=False)
+        assert st["status"] != "ok"
+    finally:
+        gpu.set_options(omega=0.6, max_iter=200)
+
+
+def test_full_size_c96_sampled_rows():
+    """C96 x 30 (the paper's mesh, 1.66M cells): sampled rows of S x and of the final
+    residual against the oracle's own cell matrices for the cells touching those rows."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(96, 30)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-6)
+    mesh, bg, co = w.mesh, w.coeffs.levels[0], w.coeffs
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([rng.integers(0, mesh.n_trace_h, 300),
+                                     rng.integers(mesh.n_trace_h, mesh.n_trace, 300),
+                                     [mesh.n_trace_h, mesh.n_trace - 1]]))
+    # cells containing each sampled row
+    g_all = None
+    col, lev = np.divmod(np.arange(mesh.ncell), mesh.nlev)
+    cells = []
+    L = mesh.nlev
+    for r in rows:
+        if r < mesh.n_trace_h:
+            e, k = divmod(int(r), L)
+            cells += [mesh.edge_cols[e, 0] * L + k, mesh.edge_cols[e, 1] * L + k]
+        else:
+            c, k = divmod(int(r) - mesh.n_trace_h, L + 1)
+            if k < L:
+                cells.append(c * L + k)
+            if k > 0:
+                cells.append(c * L + k - 1)
+    cells = np.unique(cells)
+    A, Kd, _cc = fem.cell_system(mesh, bg, co, cells=cells)
+    SK = fem.condense(A, Kd)
+    g = fem.trace_dof_ids(mesh, cells)
+    x = rng.standard_normal(gpu.ntrace)
+    y = _np(gpu.apply_trace(_cuda(x)))
+    want = np.zeros(len(rows))
+    scale = np.zeros(len(rows))
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for ci in range(len(cells)):
+        for i in range(6):
+            j = pos.get(int(g[ci, i]))
+            if j is not None:
+                want[j] += SK[ci, i] @ x[g[ci]]
+                scale[j] += np.abs(SK[ci, i]) @ np.abs(x[g[ci]])
+    assert np.all(np.abs(y[rows] - want) <= 1e-12 * scale)
+    # the solve reaches the tolerance; sampled residual rows recomputed by the oracle agree
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam, st = gpu.solve(Rub, Rpi)
+    assert st["status"] == "ok" and st["true_rel_residual"] <= 1.05e-6
+    lam = _np(lam)
+    B = _np(gpu.trace_rhs(Rub, Rpi))
+    Bo = np.zeros(len(rows))
+    R = np.concatenate([w.Rub[cells], w.Rpi[cells, None]], axis=1)
+    Y = np.linalg.solve(A, R[:, :, None])[:, :, 0]
+    res = np.zeros(len(rows))
+    for ci in range(len(cells)):
+        for i in range(6):
+            j = pos.get(int(g[ci, i]))
+            if j is not None:
+                Bo[j] += Y[ci, i]
+                res[j] += Y[ci, i] - SK[ci, i] @ lam[g[ci]]
+    assert np.abs(B[rows] - Bo).max() <= 1e-11 * np.abs(Bo).max()
+    Slam = _np(gpu.apply_trace(_cuda(lam)))
+    assert np.abs((B - Slam)[rows] - res).max() <= 1e-9 * np.linalg.norm(B) / np.sqrt(len(B)) + \
+        1e-12 * np.abs(Bo).max()
+    gpu.close()

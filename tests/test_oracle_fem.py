@@ -261,3 +261,42 @@ def test_buoyancy_weight_is_tau_squared_dt_squared_n_squared():
     want = co.tau_u * co.tau_theta * co.dt ** 2 * n2
     np.testing.assert_allclose(cc["c22"], want, rtol=1e-4)
     assert (cc["c22"] > 0).all()
+
+
+def test_local_inverse_matches_extended_precision():
+    """A_K^-1 (hence S_K) of physical cubed-sphere cells agrees with a 60-digit inverse to a
+    few ulps of each row's scale, although A_K's entries span ~20 orders of magnitude."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    w = I.cubed_sphere(12, 30)
+    cells = [0, 29, 31, 500, w.mesh.ncell - 1]
+    A, Kd, _cc = fem.cell_system(w.mesh, w.coeffs.levels[0], w.coeffs, cells=cells)
+    Ainv = fem.local_inverse(A)
+    SK = fem.condense(A, Kd)
+    for i in range(len(cells)):
+        ex = mp.matrix(A[i].tolist()) ** -1
+        exn = np.array([[float(ex[r, c]) for c in range(7)] for r in range(7)])
+        scale = np.abs(exn).max(axis=1, keepdims=True)
+        assert (np.abs(Ainv[i] - exn) / scale).max() < 1e-14
+        exs = exn[:6, :6] * Kd[i][None, :]
+        assert (np.abs(SK[i] - exs) / np.abs(exs).max(axis=1, keepdims=True)).max() < 1e-14
+
+
+def test_trace_row_sums_identity():
+    """S 1 = sum_K m_K (A_K^-1)_{u,p} equals the plain row sums of S up to their cancellation
+    error, and equals the 60-digit row sums of S_K on sample cells."""
+    w = I.cubed_sphere(6, 8, nmg=1)
+    A, Kd, _cc = fem.cell_system(w.mesh, w.coeffs.levels[0], w.coeffs)
+    SK = fem.condense(A, Kd)
+    S = fem.assemble_trace_operator(w.mesh, SK)
+    rs = fem.trace_row_sums(w.mesh, A)
+    plain = S @ np.ones(w.mesh.n_trace)
+    cond = abs(S) @ np.ones(w.mesh.n_trace)
+    assert np.all(np.abs(rs - plain) <= 1e-13 * cond)
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    for cell in (0, 17, w.mesh.ncell - 1):
+        ex = mp.matrix(A[cell].tolist()) ** -1
+        exact = [float(sum(ex[i, j] * mp.mpf(Kd[cell, j]) for j in range(6))) for i in range(6)]
+        got = A[cell, 6, 6] * fem.local_inverse(A[cell:cell + 1])[0, :6, 6]
+        np.testing.assert_allclose(got, exact, rtol=1e-12)

@@ -249,3 +249,17 @@ def test_paper_parameters_are_the_oracle_defaults():
     assert I.mg_levels_for(96) == GOLDEN["pressure_mg_levels"]["value"]
     assert len(fem.GAUSS_X) == GOLDEN["gauss_points_per_direction_p0"]["value"]
     assert 6 * 96 * 96 * 30 == GOLDEN["c96_cells"]["value"]
+
+
+def test_pressure_operator_annihilates_constants_up_to_mass_term():
+    """G 1 = 0 exactly on every interior facet (single-valued theta), so H 1 = M3^Pi 1 (the
+    numerator of Gamma), while the plain row sums of H agree only up to their cancellation
+    error. Ground and lid facets carry no velocity dof (inverse lumped mass 0)."""
+    w = I.cubed_sphere(6, 8, nmg=1)
+    s = HybridSolver(w.hier, w.coeffs)
+    Bg, inv_lump, Gg, m = s.mg.parts0
+    one = np.ones(w.mesh.ncell)
+    assert np.all(inv_lump * (Gg @ one) == 0.0)
+    assert np.array_equal(pressure_mg.pressure_operator_times(s.mg.parts0, one), m)
+    H = s.mg.H[0]
+    assert np.all(np.abs(H @ one - m) <= 1e-14 * (abs(H) @ one))
