@@ -195,6 +195,21 @@ int hmg_precond_apply(hmg_ctx *ctx, const double *r, double *z);
 /* nsweeps of Algorithm 1 on S lambda = b, updating lambda [ntrace] in place (FP64). */
 int hmg_line_smooth(hmg_ctx *ctx, const double *b, double *lambda, int32_t nsweeps);
 
+/* The same sweeps as hmg_line_smooth, for callers that must not allocate device memory at
+ * call time: for instance code whose device memory is all handed to another allocator (a
+ * framework's caching pool), code with a fixed memory budget decided at start-up, or
+ * latency-bound loops that cannot afford cudaMalloc/cudaFree, which synchronise the device.
+ * The paper has no counterpart; this is a property of the library, not of the method.
+ * The second vector of the ping-pong comes from an 8 MiB array compiled into the library
+ * (held by every GPU that loads it until the process exits), so ntrace must be at most
+ * 1048576; a larger mesh gets HMG_ERR_INVALID_ARG. The call allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls in the process share the one array and it keeps the last
+ * call's contents (nothing in it needs to start at zero), so calls whose GPU work overlaps
+ * in time, on any streams or contexts of the same device, race and give wrong results. */
+int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *lambda, int32_t nsweeps);
+
 /* y = H_l x on multigrid level l (Eq. elliptic_pressure_system), FP64, [ncell_l]. */
 int hmg_apply_pressure(hmg_ctx *ctx, int32_t level, const double *x, double *y);
 

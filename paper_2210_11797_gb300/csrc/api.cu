@@ -76,8 +76,6 @@ static void free_all(Ctx *c) {
 
 using namespace hmg;
 
-struct hmg_ctx : public Ctx {};
-
 extern "C" {
 
 int hmg_default_options(hmg_options *o) {

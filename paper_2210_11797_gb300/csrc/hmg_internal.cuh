@@ -169,3 +169,6 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
 int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
 
 }  // namespace hmg
+
+// The opaque handle of the C ABI is the internal context.
+struct hmg_ctx : public hmg::Ctx {};

@@ -6,6 +6,8 @@
 // Paper (arXiv 2210.11797): Eqs. hybrid-S, hybrid-rhs, hybrid-recovery (Sec. 2.4);
 // Algorithm 1 and Eq. banded_system; Algorithm 2; Sec. 2.5 intergrid operators
 // (P lambda = {{Pi}}, Restrict = P^T) and Eq. scaling_matrix.
+#include <mutex>
+
 #include "device_common.cuh"
 #include "hmg_internal.cuh"
 #include "precond.cuh"
@@ -388,3 +390,61 @@ int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps) {
 }
 
 }  // namespace hmg
+
+// ---- line smoothing without any allocation -----------------------------------------------
+// hmg_line_smooth keeps its second vector in the context's workspace, which
+// hmg_assemble_trace allocates. This variant takes that vector from a fixed array compiled
+// into the library instead, so the call itself never allocates device memory. Its size is
+// fixed here: every GPU that loads the library holds these 8 MiB until the process exits.
+namespace {
+constexpr int64_t kNoAllocMaxTrace = int64_t(1) << 20;   // trace unknowns (1,048,576 doubles)
+constexpr int kNoAllocMaxDevices = 64;
+__device__ __align__(256) double g_sweep_scratch[kNoAllocMaxTrace];
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of g_sweep_scratch on the current device (looked up once per device; the
+// name of a __device__ array is only a host-side stand-in and must not be handed to a kernel).
+int scratch_on_current_device(hmg::Ctx *c, double **out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (c->device < 0 || c->device >= kNoAllocMaxDevices)
+    return hmg::fail(c, HMG_ERR_INVALID_ARG, "device ordinal beyond the no-allocation table");
+  if (!g_scratch_ptr[c->device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
+    if (e != cudaSuccess) return hmg::cuda_fail(c, e, "cudaGetSymbolAddress(g_sweep_scratch)");
+    g_scratch_ptr[c->device] = static_cast<double *>(p);
+  }
+  *out = g_scratch_ptr[c->device];
+  return HMG_OK;
+}
+}  // namespace
+
+extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *lambda,
+                                       int32_t nsweeps) {
+  using namespace hmg;
+  if (!ctx) return HMG_ERR_INVALID_ARG;
+  Ctx *c = ctx;
+  if (!c->assembled) return fail(c, HMG_ERR_NOT_READY, "call hmg_assemble_trace first");
+  if (!b || !lambda || nsweeps < 0) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  if (c->lv[0].ntrace > kNoAllocMaxTrace)
+    return fail(c, HMG_ERR_INVALID_ARG,
+                "hmg_line_smooth_noalloc: ntrace exceeds the built-in scratch of 1048576 trace "
+                "unknowns; use hmg_line_smooth");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  double *scratch = nullptr;
+  int st = scratch_on_current_device(c, &scratch);
+  if (st) return st;
+  // same sweeps as hmg_line_smooth, ping-ponging between lambda and the fixed array; nothing
+  // in the array needs to start at zero (each sweep overwrites every entry it later reads)
+  double *cur = lambda, *nxt = scratch;
+  for (int i = 0; i < nsweeps; ++i) {
+    if ((st = launch_sweep<double, double, double, false>(c, b, cur, nxt))) return st;
+    double *t = cur; cur = nxt; nxt = t;
+  }
+  if (cur != lambda)
+    HMG_CUDA(c, cudaMemcpyAsync(lambda, cur, sizeof(double) * c->lv[0].ntrace,
+                                cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}

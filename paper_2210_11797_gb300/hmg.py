@@ -92,6 +92,7 @@ _SIGS = {
     "hmg_apply_trace": ([_P, _P, _P], C.c_int),
     "hmg_precond_apply": ([_P, _P, _P], C.c_int),
     "hmg_line_smooth": ([_P, _P, _P, C.c_int32], C.c_int),
+    "hmg_line_smooth_noalloc": ([_P, _P, _P, C.c_int32], C.c_int),
     "hmg_apply_pressure": ([_P, C.c_int32, _P, _P], C.c_int),
     "hmg_pressure_vcycle": ([_P, _P, _P], C.c_int),
     "hmg_get_gamma": ([_P, _P], C.c_int),
