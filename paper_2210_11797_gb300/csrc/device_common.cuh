@@ -68,6 +68,31 @@ __device__ __forceinline__ void grid_reduce(const double (&val)[NV], const int (
   if (threadIdx.x == 0) counter[slot[0]] = 0u;
 }
 
+// Block-level sums of NV per-thread values written to part[slot][blockIdx.x] (no atomics, no
+// fences); finalize_kernel reduces them. For one-row-per-thread kernels with ~10^4-10^5
+// blocks, where a single ticket counter serialises every block on one atomic.
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&val)[NV], const int (&slot)[NV],
+                                               double *part) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double v = warp_sum(val[i]);
+    if (lane == 0) sh[i][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double v = lane < nwarp ? sh[i][lane] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) part[(int64_t)slot[i] * kMaxRedBlocks + blockIdx.x] = v;
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T ld(const T *p) { return __ldg(p); }
 
@@ -83,10 +108,13 @@ struct TraceDims {
   int64_t NT;     // all rows
 };
 
-template <typename TS, typename TX, typename TA>
+// acc + sign * (row of S) . x as a chain of fused multiply-adds, one per coefficient: with
+// acc = 0, sign = +1 it is S x; with acc = b, sign = -1 it is the residual b - S x without a
+// separate subtraction (the FP64 issue rate, not HBM, bounds these kernels on GB300).
+template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row_h(const TS *__restrict__ S, const TX *__restrict__ x,
                                       const int32_t *__restrict__ stencil, const TraceDims d,
-                                      int64_t row) {
+                                      int64_t row, TA acc) {
   const int e = (int)(row / d.L);
   const int k = (int)(row - (int64_t)e * d.L);
   const int32_t *st = stencil + 8 * (int64_t)e;
@@ -94,54 +122,62 @@ __device__ __forceinline__ TA s_row_h(const TS *__restrict__ S, const TX *__rest
   const int64_t z1 = d.NH + (int64_t)c1 * (d.L + 1) + k;
   const int64_t z2 = d.NH + (int64_t)c2 * (d.L + 1) + k;
   const int64_t T = d.NT;
-  TA y = (TA)ld(S + row) * (TA)ld(x + row);
-  y += (TA)ld(S + T + row) * (TA)ld(x + (int64_t)__ldg(st + 2) * d.L + k);
-  y += (TA)ld(S + 2 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 3) * d.L + k);
-  y += (TA)ld(S + 3 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 4) * d.L + k);
-  y += (TA)ld(S + 4 * T + row) * (TA)ld(x + z1);
-  y += (TA)ld(S + 5 * T + row) * (TA)ld(x + z1 + 1);
-  y += (TA)ld(S + 6 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 5) * d.L + k);
-  y += (TA)ld(S + 7 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 6) * d.L + k);
-  y += (TA)ld(S + 8 * T + row) * (TA)ld(x + (int64_t)__ldg(st + 7) * d.L + k);
-  y += (TA)ld(S + 9 * T + row) * (TA)ld(x + z2);
-  y += (TA)ld(S + 10 * T + row) * (TA)ld(x + z2 + 1);
-  return y;
+  auto term = [&](int slot, int64_t col) {
+    const TA a = (TA)ld(S + slot * T + row);
+    acc = fma(NEG ? -a : a, (TA)ld(x + col), acc);
+  };
+  term(0, row);
+  term(1, (int64_t)__ldg(st + 2) * d.L + k);
+  term(2, (int64_t)__ldg(st + 3) * d.L + k);
+  term(3, (int64_t)__ldg(st + 4) * d.L + k);
+  term(4, z1);
+  term(5, z1 + 1);
+  term(6, (int64_t)__ldg(st + 5) * d.L + k);
+  term(7, (int64_t)__ldg(st + 6) * d.L + k);
+  term(8, (int64_t)__ldg(st + 7) * d.L + k);
+  term(9, z2);
+  term(10, z2 + 1);
+  return acc;
 }
 
-template <typename TS, typename TX, typename TA>
+template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row_z(const TS *__restrict__ S, const TX *__restrict__ x,
                                       const int32_t *__restrict__ col_edges, const TraceDims d,
-                                      int64_t row) {
+                                      int64_t row, TA acc) {
   const int64_t zr = row - d.NH;
   const int c = (int)(zr / (d.L + 1));
   const int k = (int)(zr - (int64_t)c * (d.L + 1));
   const int64_t T = d.NT;
   const int32_t *ce = col_edges + 4 * (int64_t)c;
-  TA y = (TA)ld(S + row) * (TA)ld(x + row);
+  auto term = [&](int slot, int64_t col) {
+    const TA a = (TA)ld(S + slot * T + row);
+    acc = fma(NEG ? -a : a, (TA)ld(x + col), acc);
+  };
+  term(0, row);
   if (k < d.L) {
-    y += (TA)ld(S + T + row) * (TA)ld(x + (int64_t)__ldg(ce + 0) * d.L + k);
-    y += (TA)ld(S + 2 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 1) * d.L + k);
-    y += (TA)ld(S + 3 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 2) * d.L + k);
-    y += (TA)ld(S + 4 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 3) * d.L + k);
-    y += (TA)ld(S + 5 * T + row) * (TA)ld(x + row + 1);
+    term(1, (int64_t)__ldg(ce + 0) * d.L + k);
+    term(2, (int64_t)__ldg(ce + 1) * d.L + k);
+    term(3, (int64_t)__ldg(ce + 2) * d.L + k);
+    term(4, (int64_t)__ldg(ce + 3) * d.L + k);
+    term(5, row + 1);
   }
   if (k > 0) {
-    y += (TA)ld(S + 6 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 0) * d.L + k - 1);
-    y += (TA)ld(S + 7 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 1) * d.L + k - 1);
-    y += (TA)ld(S + 8 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 2) * d.L + k - 1);
-    y += (TA)ld(S + 9 * T + row) * (TA)ld(x + (int64_t)__ldg(ce + 3) * d.L + k - 1);
-    y += (TA)ld(S + 10 * T + row) * (TA)ld(x + row - 1);
+    term(6, (int64_t)__ldg(ce + 0) * d.L + k - 1);
+    term(7, (int64_t)__ldg(ce + 1) * d.L + k - 1);
+    term(8, (int64_t)__ldg(ce + 2) * d.L + k - 1);
+    term(9, (int64_t)__ldg(ce + 3) * d.L + k - 1);
+    term(10, row - 1);
   }
-  return y;
+  return acc;
 }
 
-template <typename TS, typename TX, typename TA>
+template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row(const TS *__restrict__ S, const TX *__restrict__ x,
                                     const int32_t *__restrict__ stencil,
                                     const int32_t *__restrict__ col_edges, const TraceDims d,
-                                    int64_t row) {
-  return row < d.NH ? s_row_h<TS, TX, TA>(S, x, stencil, d, row)
-                    : s_row_z<TS, TX, TA>(S, x, col_edges, d, row);
+                                    int64_t row, TA acc) {
+  return row < d.NH ? s_row_h<TS, TX, TA, NEG>(S, x, stencil, d, row, acc)
+                    : s_row_z<TS, TX, TA, NEG>(S, x, col_edges, d, row, acc);
 }
 
 }  // namespace hmg

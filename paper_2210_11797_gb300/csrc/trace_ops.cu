@@ -26,24 +26,53 @@ __global__ void __launch_bounds__(kRedThreads)
   double a0 = 0.0, a1 = 0.0;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row < d.NT) {
-    double v = s_row<double, double, double>(S, x, stencil, col_edges, d, row);
     if (MODE == 3) {
-      v = __ldg(w + row) - v;
-      a0 += v * v;
+      const double v = s_row<double, double, double, true>(S, x, stencil, col_edges, d, row, __ldg(w + row));
+      a0 = v * v;
     } else {
+      const double v = s_row<double, double, double, false>(S, x, stencil, col_edges, d, row, 0.0);
       y[row] = v;
-      if (MODE == 1) a0 += __ldg(w + row) * v;
-      if (MODE == 2) { a0 += v * __ldg(w + row); a1 += v * v; }
+      if (MODE == 1) a0 = __ldg(w + row) * v;
+      if (MODE == 2) { a0 = v * __ldg(w + row); a1 = v * v; }
     }
   }
   if (MODE == 1 || MODE == 3) {
     const double val[1] = {a0};
     const int sl[1] = {slot0};
-    grid_reduce<1>(val, sl, part, counter, scal);
+    block_partials<1>(val, sl, part);
   } else if (MODE == 2) {
     const double val[2] = {a0, a1};
     const int sl[2] = {slot0, slot1};
-    grid_reduce<2>(val, sl, part, counter, scal);
+    block_partials<2>(val, sl, part);
+  }
+}
+
+// Sum of the per-block partials of slots s0 (and s1) into scal, in a fixed order.
+__global__ void __launch_bounds__(1024)
+    finalize_kernel(const double *__restrict__ part, int nblocks, int s0, int s1, double *scal) {
+  __shared__ double sh[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < 2; ++q) {
+    const int slot = q == 0 ? s0 : s1;
+    if (slot < 0) break;
+    const double *p = part + (int64_t)slot * kMaxRedBlocks;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int b = threadIdx.x;
+    for (; b + 3 * 1024 < nblocks; b += 4 * 1024) {
+      acc[0] += p[b];
+      acc[1] += p[b + 1024];
+      acc[2] += p[b + 2048];
+      acc[3] += p[b + 3072];
+    }
+    for (; b < nblocks; b += 1024) acc[0] += p[b];
+    double v = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    if (lane == 0) sh[q][warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < 32; ++i) s += sh[q][i];
+      scal[slot] = s;
+    }
   }
 }
 
@@ -60,6 +89,8 @@ int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, i
     case 2: spmv_kernel<2><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
     default: spmv_kernel<3><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
   }
+  if (mode != 0)
+    finalize_kernel<<<1, 1024, 0, c->stream>>>(c->part, (int)g, slot0, mode == 2 ? slot1 : -1, c->scal);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -174,7 +205,7 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
-      if (!ZERO) r -= s_row_z<T, T, T>(S, lam_in, a.col_edges, d, row);
+      if (!ZERO) r = s_row_z<T, T, T, true>(S, lam_in, a.col_edges, d, row, r);
       const int k = i % L1;
       sr[i] = r;
       ssub[i] = k > 0 ? __ldg(S + 10 * d.NT + row) : (T)0;
@@ -206,7 +237,7 @@ __global__ void __launch_bounds__(256)
     const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
     if (row >= d.NH) return;
     T r = (T)__ldg(b + row);
-    if (!ZERO) r -= s_row_h<T, T, T>(S, lam_in, a.stencil, d, row);
+    if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
     const T old = ZERO ? (T)0 : lam_in[row];
     lam_out[row] = (Tout)(old + omega * r * __ldg(hinv + row));
   }
@@ -240,7 +271,7 @@ __global__ void __launch_bounds__(256)
                     const int32_t *__restrict__ col_edges) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= d.NT) return;
-  R[row] = (T)__ldg(b + row) - s_row<T, T, T>(S, lam, stencil, col_edges, d, row);
+  R[row] = s_row<T, T, T, true>(S, lam, stencil, col_edges, d, row, (T)__ldg(b + row));
 }
 
 // ---- bbar = Gamma P^T R (Algorithm 2 lines 4-5) -----------------------------------------
