@@ -106,6 +106,9 @@ typedef struct {
   double divergence;    /* stop with NOT_CONVERGED if ||r|| > divergence * ||B|| (1e3) */
   int32_t profile;      /* 1: time every solver component with CUDA events (see
                            hmg_solve_stats.comp_ms); 0: no events (default) */
+  int32_t graph;        /* 1 (default): the whole solve is one CUDA graph whose BiCGStab loop
+                           is a device-side WHILE node (no host round trip per iteration);
+                           0: the host drives the loop (always so when profile = 1) */
 } hmg_options;
 
 #define HMG_MAX_HISTORY 512
@@ -173,6 +176,21 @@ int hmg_trace_rhs(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *B)
  * stop reason (HMG_OK when converged). */
 int hmg_solve(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *lambda,
               hmg_solve_stats *stats);
+
+/* n independent solves (a batch of contexts, all assembled, on the current device, each with
+ * its own mesh and options) in ONE CUDA graph launch: one branch per context, each branch
+ * B_lambda -> a device-side WHILE loop of BiCGStab iterations -> the final residual, the
+ * branches running concurrently. Rub[i], Rpi[i], lambda[i] are device pointers of context
+ * i; stats (host, may be NULL) has n entries. Returns the first non-OK status of any solve
+ * (details in that solve's stats). The graph runs on ctxs[0]'s stream. */
+int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
+                      const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats);
+
+/* Time the candidate launch shapes of the line sweep and of the pressure smoother on each
+ * level (columns of a column block per thread block) on this context's mesh and keep the
+ * fastest; later launches of this context use them. Needs an assembled context; the sweep
+ * timings overwrite the context's work vectors. */
+int hmg_autotune(hmg_ctx *ctx);
 
 /* The same solve with HOST buffers: the inputs are copied to the device, the result back. */
 int hmg_solve_host(hmg_ctx *ctx, const double *Rub_host, const double *Rpi_host,

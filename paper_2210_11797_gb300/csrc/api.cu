@@ -64,12 +64,17 @@ Prof::~Prof() {
 }
 
 static void free_all(Ctx *c) {
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
   for (void *p : c->owned) cudaFree(p);
   c->owned.clear();
   if (c->scal_host) cudaFreeHost(c->scal_host);
   c->scal_host = nullptr;
+  if (c->state_host) cudaFreeHost(c->state_host);
+  c->state_host = nullptr;
 }
 
 }  // namespace hmg
@@ -94,6 +99,8 @@ int hmg_default_options(hmg_options *o) {
   o->tol = 1e-6;
   o->max_iter = 200;
   o->divergence = 1e3;
+  o->profile = 0;
+  o->graph = 1;
   return HMG_OK;
 }
 
@@ -111,11 +118,15 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(double) * Scal::N);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->state_host, sizeof(int) * 4);
   if (e != cudaSuccess) {
+    free_all(c);
     delete c;
     return HMG_ERR_CUDA;
   }
   int st = dev_alloc(c, &c->scal, Scal::N);
+  if (!st) st = dev_alloc(c, &c->state, 4);
+  if (!st) st = dev_alloc(c, &c->hist, HMG_MAX_HISTORY);
   if (!st) st = dev_alloc(c, &c->part, (size_t)Scal::N * kMaxRedBlocks);
   if (!st) st = dev_alloc(c, &c->counter, Scal::N);
   if (!st && cudaMemset(c->counter, 0, sizeof(unsigned int) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
@@ -435,6 +446,32 @@ int hmg_get_gamma(hmg_ctx *c, double *gamma) {
   if (!gamma) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
   HMG_CUDA(c, cudaMemcpyAsync(gamma, c->gamma, sizeof(double) * c->lv[0].ncell, cudaMemcpyDeviceToDevice, c->stream));
   return finish(c, HMG_OK);
+}
+
+int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
+                      const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats) {
+  if (!ctxs || n < 1 || !Rub || !Rpi || !lambda) return HMG_ERR_INVALID_ARG;
+  hmg_ctx *c0 = ctxs[0];
+  if (!c0) return HMG_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    hmg_ctx *c = ctxs[i];
+    if (!c) return fail(c0, HMG_ERR_INVALID_ARG, "null context in the batch");
+    if (!c->assembled) return fail(c0, HMG_ERR_NOT_READY, "a context of the batch is not assembled");
+    if (c->device != c0->device) return fail(c0, HMG_ERR_INVALID_ARG, "batched contexts must share a device");
+    if (!Rub[i] || !Rpi[i] || !lambda[i]) return fail(c0, HMG_ERR_INVALID_ARG, "null pointer in the batch");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(c0, HMG_ERR_INVALID_ARG, "a context appears twice in the batch");
+  }
+  HMG_CUDA(c0, cudaSetDevice(c0->device));
+  // the batch graph reads inputs that may have been written on the contexts' own streams
+  for (int i = 0; i < n; ++i) HMG_CUDA(c0, cudaStreamSynchronize(ctxs[i]->stream));
+  return krylov_solve_batched(ctxs, n, Rub, Rpi, lambda, stats);
+}
+
+int hmg_autotune(hmg_ctx *c) {
+  int st = ready(c);
+  if (st) return st;
+  return finish(c, autotune(c));
 }
 
 int hmg_get_trace_operator(hmg_ctx *c, double *slots) {

@@ -99,6 +99,23 @@ struct Ctx {
   unsigned int *counter = nullptr;  // device [Scal::N] tickets of the last-block reductions
   double *scal_host = nullptr; // pinned [Scal::N]
   double *host_in = nullptr;   // device staging for hmg_solve_host (Rub | Rpi | lambda)
+  // device-side iteration state of the Krylov loop: [0] completed iterations, [1] status;
+  // hist[i] = ||r_i|| / ||B|| (i = 0 .. iterations)
+  int *state = nullptr;
+  double *hist = nullptr;
+  int *state_host = nullptr;   // pinned [2]
+  // whole-solve CUDA graph (B_lambda, a WHILE node over BiCGStab iterations, final residual)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  struct GraphKey {
+    const void *Rub, *Rpi, *lam;
+    hmg_options opt;
+  } graph_key{};
+  // autotuned launch shapes (0 = default): columns per block of the line sweep and of the
+  // pressure smoother on each level
+  int tune_sweep_cpb = 0;
+  int tune_mg_cpb[kMaxLevels] = {0};
   std::vector<void *> owned;   // every device allocation, freed by hmg_destroy
   // component timing (hmg_options.profile): event pool and (component, start, end) marks
   std::vector<cudaEvent_t> ev_pool;
@@ -167,6 +184,16 @@ int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
                  hmg_solve_stats *st);
 int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
+// Batched solves: one CUDA graph with one branch per context (contexts on one device).
+int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
+                         const double *const *Rpi, double *const *lambda, hmg_solve_stats *st);
+// Releases the context's cached solve graph.
+void drop_graph(Ctx *c);
+// Launch-shape autotuning of one context (columns per block of the sweep and MG smoother).
+int autotune(Ctx *c);
+// Sweep launch with explicit columns per block (autotuner).
+int time_sweep_cpb(Ctx *c, int cpb, float *ms);
+int time_mg_cpb(Ctx *c, int level, int cpb, float *ms);
 
 }  // namespace hmg
 

@@ -3,11 +3,16 @@
 // the recurrence residual satisfies ||r_i|| <= tol ||B_lambda|| (Sec. 3.1 of arXiv
 // 2210.11797: BiCGStab reducing the residual two-norm by the tolerance).
 //
-// Scalars live on the device: every inner product is a deterministic grid reduction into
-// ctx->scal, and the vector kernels compute alpha, beta and omega from those sums
-// themselves, so an iteration needs one 8-word device-to-host read (for the stopping test).
-#include <chrono>
+// Everything the loop decides lives on the device: the inner products are deterministic
+// reductions into ctx->scal, the vector kernels compute alpha, beta and omega from them,
+// and a check kernel appends ||r_i|| / ||B|| to a history array and decides whether to go
+// on. With hmg_options.graph the whole solve is one CUDA graph in which a WHILE conditional
+// node repeats the iteration body until the check kernel clears its condition, so a solve
+// costs one graph launch and one synchronisation. Batched solves put one such branch per
+// context into a single graph. With graph = 0 (or profile = 1) the host drives the loop.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "device_common.cuh"
 #include "hmg_internal.cuh"
@@ -19,12 +24,14 @@ static unsigned red_grid(int64_t n) {
   return g < (unsigned)kRedBlocks ? g : (unsigned)kRedBlocks;
 }
 
+enum { kIt = 0, kStatus = 1, kContinue = 2 };
+
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *part,
                unsigned int *counter, double *scal, int slot) {
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s += a[i] * b[i];
+    s = fma(a[i], b[i], s);
   const double v[1] = {s};
   const int sl[1] = {slot};
   grid_reduce<1>(v, sl, part, counter, scal);
@@ -36,8 +43,7 @@ int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot) {
   return HMG_OK;
 }
 
-// Start: x = 0, r = rhat = B, p = v = 0, scal[RHO_cur] = (B, B), scal[RHO_prev] = 1,
-// alpha = omega = 1.
+// x = 0, r = rhat = B, p = v = 0
 __global__ void bicg_init_kernel(const double *__restrict__ B, double *__restrict__ x,
                                  double *__restrict__ r, double *__restrict__ rhat,
                                  double *__restrict__ p, double *__restrict__ v, int64_t n) {
@@ -51,30 +57,52 @@ __global__ void bicg_init_kernel(const double *__restrict__ B, double *__restric
   }
 }
 
-__global__ void bicg_scalars_init_kernel(double *scal) {
-  scal[Scal::RHO0] = scal[Scal::BB];
+struct LoopParams {
+  double tol, divergence;
+  int max_iter;
+};
+
+// rho_0 = (B, B), rho_-1 = alpha = omega = 1; iteration state and history[0]; the loop runs
+// while B != 0 is finite, the tolerance is not met and iterations are allowed.
+template <bool GRAPH>
+__global__ void bicg_start_kernel(double *scal, int *state, double *hist, LoopParams lp,
+                                  cudaGraphConditionalHandle handle) {
+  const double bb = scal[Scal::BB];
+  scal[Scal::RHO0] = bb;
   scal[Scal::RHO1] = 1.0;
   scal[Scal::ALPHA] = 1.0;
   scal[Scal::OMEGA] = 1.0;
+  int status = isfinite(bb) ? HMG_OK : HMG_ERR_NONFINITE;
+  const bool work = status == HMG_OK && bb > 0.0 && 1.0 > lp.tol;
+  if (work && lp.max_iter <= 0) status = HMG_ERR_NOT_CONVERGED;
+  const int cont = work && lp.max_iter > 0;
+  state[kIt] = 0;
+  state[kStatus] = status;
+  state[kContinue] = cont;
+  hist[0] = bb > 0.0 ? 1.0 : 0.0;
+  if (GRAPH) cudaGraphSetConditional(handle, cont);
 }
 
 // p = r + beta (p - omega v), beta = (rho_i / rho_{i-1}) (alpha / omega)
 __global__ void bicg_p_kernel(const double *__restrict__ r, double *__restrict__ p,
                               const double *__restrict__ v, const double *__restrict__ scal,
-                              int par, int64_t n) {
+                              const int *__restrict__ state, int64_t n) {
+  const int par = state[kIt] & 1;
   const double rho = scal[par], rho_prev = scal[1 - par];
   const double alpha = scal[Scal::ALPHA], omega = scal[Scal::OMEGA];
   const double beta = (rho / rho_prev) * (alpha / omega);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
 }
 
 // alpha = rho_i / (rhat, v); s = r - alpha v
 __global__ void bicg_s_kernel(const double *__restrict__ r, const double *__restrict__ v,
-                              double *__restrict__ s, double *scal, int par, int64_t n) {
+                              double *__restrict__ s, double *scal, const int *__restrict__ state,
+                              int64_t n) {
+  const int par = state[kIt] & 1;
   const double alpha = scal[par] / scal[Scal::RV];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s[i] = r[i] - alpha * v[i];
+    s[i] = fma(-alpha, v[i], r[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[Scal::ALPHA] = alpha;
 }
 
@@ -84,16 +112,17 @@ __global__ void __launch_bounds__(kRedThreads)
     bicg_xr_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ s,
                    const double *__restrict__ t, const double *__restrict__ phat,
                    const double *__restrict__ shat, const double *__restrict__ rhat, double *scal,
-                   double *part, unsigned int *counter, int par, int64_t n) {
+                   double *part, unsigned int *counter, const int *__restrict__ state, int64_t n) {
+  const int par = state[kIt] & 1;
   const double alpha = scal[Scal::ALPHA];
   const double omega = scal[Scal::TS] / scal[Scal::TT];
   double a0 = 0.0, a1 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = x[i] + alpha * phat[i] + omega * shat[i];
-    const double ri = s[i] - omega * t[i];
+    x[i] = fma(omega, shat[i], fma(alpha, phat[i], x[i]));
+    const double ri = fma(-omega, t[i], s[i]);
     r[i] = ri;
-    a0 += rhat[i] * ri;
-    a1 += ri * ri;
+    a0 = fma(rhat[i], ri, a0);
+    a1 = fma(ri, ri, a1);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[Scal::OMEGA] = omega;
   const double val[2] = {a0, a1};
@@ -101,86 +130,191 @@ __global__ void __launch_bounds__(kRedThreads)
   grid_reduce<2>(val, sl, part, counter, scal);
 }
 
-int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st) {
+// End of an iteration: record ||r_i|| / ||B||, decide the status, continue or stop.
+template <bool GRAPH>
+__global__ void bicg_check_kernel(const double *scal, int *state, double *hist, LoopParams lp,
+                                  cudaGraphConditionalHandle handle) {
+  const int it = state[kIt] + 1;        // iterations completed after this one
+  const int par_next = it & 1;          // slot holding rho_{i+1}
+  const double bnorm = sqrt(scal[Scal::BB]);
+  const double rel = sqrt(scal[Scal::RR]) / bnorm;
+  hist[it < HMG_MAX_HISTORY ? it : HMG_MAX_HISTORY - 1] = rel;
+  int status = HMG_OK, cont = 0;
+  if (!isfinite(rel) || !isfinite(scal[Scal::ALPHA]) || !isfinite(scal[Scal::OMEGA])) {
+    status = HMG_ERR_NONFINITE;
+  } else if (rel <= lp.tol) {
+    status = HMG_OK;
+  } else if (scal[Scal::RV] == 0.0 || scal[Scal::TT] == 0.0 || scal[par_next] == 0.0) {
+    status = HMG_ERR_BREAKDOWN;
+  } else if (rel > lp.divergence || it >= lp.max_iter) {
+    status = HMG_ERR_NOT_CONVERGED;
+  } else {
+    cont = 1;
+  }
+  state[kIt] = it;
+  state[kStatus] = status;
+  state[kContinue] = cont;
+  if (GRAPH) cudaGraphSetConditional(handle, cont);
+}
+
+static LoopParams loop_params(const Ctx *c) {
+  return LoopParams{c->opt.tol, c->opt.divergence, c->opt.max_iter};
+}
+
+// B_lambda, (B, B), x = 0, r = rhat = B, loop state
+static int solve_head(Ctx *c, const double *Rub, const double *Rpi, double *x, bool graph,
+                      cudaGraphConditionalHandle h) {
   const int64_t n = c->lv[0].ntrace;
-  c->marks.clear();
-  c->ev_next = 0;
-  cudaEvent_t e0, e1;
-  HMG_CUDA(c, cudaEventCreate(&e0));
-  HMG_CUDA(c, cudaEventCreate(&e1));
-  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
   int s;
   if ((s = launch_trace_rhs(c, Rub, Rpi, c->B))) return s;
+  Prof pk(c, kCompKrylov, 3);
+  if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
+  bicg_init_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, x, c->r, c->rhat, c->p, c->v, n);
+  if (graph) bicg_start_kernel<true><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
+  else bicg_start_kernel<false><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// one BiCGStab iteration and its check
+static int solve_body(Ctx *c, double *x, bool graph, cudaGraphConditionalHandle h) {
+  const int64_t n = c->lv[0].ntrace;
   const unsigned vg = red_grid(n);
-  double *x = lambda;
+  int s;
   {
-    Prof pk(c, kCompKrylov, 3);
-    if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
-    bicg_init_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->B, x, c->r, c->rhat, c->p, c->v, n);
-    bicg_scalars_init_kernel<<<1, 1, 0, c->stream>>>(c->scal);
+    Prof pk(c, kCompKrylov);
+    bicg_p_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->p, c->v, c->scal, c->state, n);
     HMG_CUDA(c, cudaGetLastError());
   }
-  HMG_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal, sizeof(double) * Scal::N, cudaMemcpyDeviceToHost, c->stream));
-  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  const double bb = c->scal_host[Scal::BB];
-  const double bnorm = std::sqrt(bb);
-  int status = HMG_OK, it = 0;
-  double rel = bnorm > 0.0 ? 1.0 : 0.0;
-  if (st) {
-    st->n_history = 0;
-    st->history[st->n_history++] = rel;
+  if ((s = precond_apply(c, c->p, c->phat))) return s;
+  if ((s = launch_spmv(c, c->phat, c->v, 1, c->rhat, Scal::RV, 0))) return s;
+  {
+    Prof pk(c, kCompKrylov);
+    bicg_s_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->v, c->s, c->scal, c->state, n);
+    HMG_CUDA(c, cudaGetLastError());
   }
-  if (!std::isfinite(bb)) status = HMG_ERR_NONFINITE;
-  const double tol = c->opt.tol;
-  while (status == HMG_OK && bnorm > 0.0 && rel > tol) {
-    if (it >= c->opt.max_iter) { status = HMG_ERR_NOT_CONVERGED; break; }
-    const int par = it & 1;
-    {
-      Prof pk(c, kCompKrylov);
-      bicg_p_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->p, c->v, c->scal, par, n);
-      HMG_CUDA(c, cudaGetLastError());
-    }
-    if ((s = precond_apply(c, c->p, c->phat))) return s;
-    if ((s = launch_spmv(c, c->phat, c->v, 1, c->rhat, Scal::RV, 0))) return s;
-    {
-      Prof pk(c, kCompKrylov);
-      bicg_s_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->v, c->s, c->scal, par, n);
-      HMG_CUDA(c, cudaGetLastError());
-    }
-    if ((s = precond_apply(c, c->s, c->shat))) return s;
-    if ((s = launch_spmv(c, c->shat, c->t, 2, c->s, Scal::TS, Scal::TT))) return s;
-    {
-      Prof pk(c, kCompKrylov);
-      bicg_xr_kernel<<<vg, kRedThreads, 0, c->stream>>>(x, c->r, c->s, c->t, c->phat, c->shat,
-                                                        c->rhat, c->scal, c->part, c->counter, par, n);
-      HMG_CUDA(c, cudaGetLastError());
-    }
-    HMG_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal, sizeof(double) * Scal::N, cudaMemcpyDeviceToHost, c->stream));
-    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-    ++it;
-    const double *h = c->scal_host;
-    rel = std::sqrt(h[Scal::RR]) / bnorm;
-    if (st && st->n_history < HMG_MAX_HISTORY) st->history[st->n_history++] = rel;
-    if (rel > tol && (h[Scal::RV] == 0.0 || h[Scal::TT] == 0.0 || h[1 - par] == 0.0)) {
-      status = HMG_ERR_BREAKDOWN;
-      break;
-    }
-    if (!std::isfinite(rel) || !std::isfinite(h[Scal::ALPHA]) || !std::isfinite(h[Scal::OMEGA])) {
-      status = HMG_ERR_NONFINITE;
-      break;
-    }
-    if (rel > c->opt.divergence) { status = HMG_ERR_NOT_CONVERGED; break; }
+  if ((s = precond_apply(c, c->s, c->shat))) return s;
+  if ((s = launch_spmv(c, c->shat, c->t, 2, c->s, Scal::TS, Scal::TT))) return s;
+  {
+    Prof pk(c, kCompKrylov, 2);
+    bicg_xr_kernel<<<vg, kRedThreads, 0, c->stream>>>(x, c->r, c->s, c->t, c->phat, c->shat, c->rhat,
+                                                      c->scal, c->part, c->counter, c->state, n);
+    if (graph) bicg_check_kernel<true><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
+    else bicg_check_kernel<false><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
+    HMG_CUDA(c, cudaGetLastError());
   }
-  // final FP64 residual ||B - S lambda|| recomputed from the iterate
-  if ((s = launch_spmv(c, x, nullptr, 3, c->B, Scal::AUX, 0))) return s;
-  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  return HMG_OK;
+}
+
+// ||B - S x||^2 recomputed in FP64 from the final iterate
+static int solve_tail(Ctx *c, const double *x) { return launch_spmv(c, x, nullptr, 3, c->B, Scal::AUX, 0); }
+
+// ---- graph construction ------------------------------------------------------------------
+// Adds one solve (head -> WHILE(body) -> tail) to graph g, without dependencies on other
+// nodes of g: the head is captured into g, the WHILE node is added after the head's last
+// nodes, the body is captured into the WHILE node's graph on a second stream, and the tail
+// is captured after the WHILE node.
+static int add_solve_branch(Ctx *c, cudaGraph_t g, const double *Rub, const double *Rpi, double *x) {
+  if (!c->cap_stream) HMG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaGraphConditionalHandle h;
+  HMG_CUDA(c, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  cudaStream_t saved = c->stream;
+  HMG_CUDA(c, cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  int st = solve_head(c, Rub, Rpi, x, true, h);
+  if (!st) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t wnode = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, deps, nullptr, nd, &p);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(c->cap_stream, &wnode, nullptr, 1,
+                                                                 cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "graph conditional node");
+    if (!st) {
+      cudaGraph_t body = p.conditional.phGraph_out[0];
+      cudaStream_t s2 = nullptr;
+      e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        st = cuda_fail(c, e, "capture of the iteration body");
+      } else {
+        c->stream = s2;
+        st = solve_body(c, x, true, h);
+        cudaGraph_t tmp;
+        e = cudaStreamEndCapture(s2, &tmp);
+        if (!st && e != cudaSuccess) st = cuda_fail(c, e, "end of the body capture");
+      }
+      if (s2) cudaStreamDestroy(s2);
+      c->stream = c->cap_stream;
+      if (!st) st = solve_tail(c, x);
+    }
+  }
+  c->stream = saved;
+  cudaGraph_t out;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &out);
+  if (st) return st;
+  HMG_CUDA(c, e);
+  return HMG_OK;
+}
+
+static bool same_key(const Ctx::GraphKey &k, const double *Rub, const double *Rpi, const double *lam,
+                     const hmg_options &o) {
+  return k.Rub == Rub && k.Rpi == Rpi && k.lam == lam && std::memcmp(&k.opt, &o, sizeof(o)) == 0;
+}
+
+void drop_graph(Ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
+static int ensure_solve_graph(Ctx *c, const double *Rub, const double *Rpi, double *x) {
+  if (c->graph_exec && same_key(c->graph_key, Rub, Rpi, x, c->opt)) return HMG_OK;
+  drop_graph(c);
+  HMG_CUDA(c, cudaGraphCreate(&c->graph, 0));
+  int st = add_solve_branch(c, c->graph, Rub, Rpi, x);
+  if (st) { drop_graph(c); return st; }
+  cudaError_t e = cudaGraphInstantiate(&c->graph_exec, c->graph, 0);
+  if (e != cudaSuccess) { drop_graph(c); return cuda_fail(c, e, "cudaGraphInstantiate"); }
+  c->graph_key = Ctx::GraphKey{Rub, Rpi, x, c->opt};
+  return HMG_OK;
+}
+
+// ---- results --------------------------------------------------------------------------------
+static int status_message(Ctx *c, int status) {
+  if (status == HMG_OK) return HMG_OK;
+  const char *why = status == HMG_ERR_NOT_CONVERGED ? "BiCGStab did not converge"
+                    : status == HMG_ERR_BREAKDOWN  ? "BiCGStab breakdown"
+                                                   : "non-finite value in BiCGStab";
+  return fail(c, status, why);
+}
+
+// Copies the loop state, history and scalars to the host (stream-ordered) and fills stats.
+static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
   HMG_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal, sizeof(double) * Scal::N, cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+  if (st) HMG_CUDA(c, cudaMemcpyAsync(st->history, c->hist, sizeof(double) * HMG_MAX_HISTORY, cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  const int it = c->state_host[kIt], status = c->state_host[kStatus];
   if (st) {
+    const double bb = c->scal_host[Scal::BB];
+    const double bnorm = std::sqrt(bb);
+    st->status = status;
+    st->iterations = it;
+    st->n_history = it + 1 < HMG_MAX_HISTORY ? it + 1 : HMG_MAX_HISTORY;
+    st->rel_residual = st->history[st->n_history - 1];
+    st->true_rel_residual = bnorm > 0.0 ? std::sqrt(c->scal_host[Scal::AUX]) / bnorm : 0.0;
+    st->solve_ms = ms;
     for (int q = 0; q < HMG_NCOMP; ++q) { st->comp_ms[q] = 0.0; st->comp_calls[q] = 0; }
     for (const Ctx::Mark &m : c->marks) {
       float t = 0.f;
@@ -189,19 +323,91 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
         st->comp_calls[m.comp] += m.launches;
       }
     }
-    st->status = status;
-    st->iterations = it;
-    st->rel_residual = rel;
-    st->true_rel_residual = bnorm > 0.0 ? std::sqrt(c->scal_host[Scal::AUX]) / bnorm : 0.0;
-    st->solve_ms = ms;
   }
-  if (status != HMG_OK) {
-    const char *why = status == HMG_ERR_NOT_CONVERGED ? "BiCGStab did not converge"
-                      : status == HMG_ERR_BREAKDOWN  ? "BiCGStab breakdown"
-                                                     : "non-finite value in BiCGStab";
-    return fail(c, status, why);
+  return status_message(c, status);
+}
+
+int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st) {
+  c->marks.clear();
+  c->ev_next = 0;
+  cudaEvent_t e0, e1;
+  HMG_CUDA(c, cudaEventCreate(&e0));
+  HMG_CUDA(c, cudaEventCreate(&e1));
+  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  int s;
+  if (c->opt.graph && !c->opt.profile) {
+    if ((s = ensure_solve_graph(c, Rub, Rpi, lambda))) return s;
+    HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  } else {
+    cudaGraphConditionalHandle none = 0;
+    if ((s = solve_head(c, Rub, Rpi, lambda, false, none))) return s;
+    for (;;) {
+      HMG_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+      HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (!c->state_host[kContinue]) break;
+      if ((s = solve_body(c, lambda, false, none))) return s;
+    }
+    if ((s = solve_tail(c, lambda))) return s;
   }
-  return HMG_OK;
+  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  HMG_CUDA(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return collect(c, st, ms);
+}
+
+// All contexts on one device; each branch of the graph is one context's whole solve, and
+// the branches have no dependencies on one another, so they run concurrently.
+int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
+                         const double *const *Rpi, double *const *lambda, hmg_solve_stats *st) {
+  Ctx *c0 = ctxs[0];
+  cudaGraph_t g = nullptr;
+  HMG_CUDA(c0, cudaGraphCreate(&g, 0));
+  int s = HMG_OK;
+  for (int i = 0; i < n && !s; ++i) {
+    Ctx *c = ctxs[i];
+    c->marks.clear();
+    c->ev_next = 0;
+    s = add_solve_branch(c, g, Rub[i], Rpi[i], lambda[i]);
+    if (s && c != c0) c0->err = c->err;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (!s) {
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) s = cuda_fail(c0, e, "cudaGraphInstantiate (batched)");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!s) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c0->stream);
+    cudaError_t e = cudaGraphLaunch(ex, c0->stream);
+    if (e != cudaSuccess) s = cuda_fail(c0, e, "cudaGraphLaunch (batched)");
+    cudaEventRecord(e1, c0->stream);
+    cudaEventSynchronize(e1);
+  }
+  float ms = 0.f;
+  if (!s) cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ex) cudaGraphExecDestroy(ex);
+  cudaGraphDestroy(g);
+  if (s) return s;
+  int worst = HMG_OK;
+  for (int i = 0; i < n; ++i) {
+    Ctx *c = ctxs[i];
+    cudaStream_t saved = c->stream;
+    c->stream = c0->stream;
+    const int r = collect(c, st ? &st[i] : nullptr, ms);
+    c->stream = saved;
+    if (r != HMG_OK && worst == HMG_OK) {
+      worst = r;
+      c0->err = c->err;
+    }
+  }
+  return worst;
 }
 
 }  // namespace hmg

@@ -25,17 +25,21 @@ __device__ __forceinline__ T xin(const T *__restrict__ x, const T *__restrict__ 
   return v;
 }
 
-template <typename T, int MODE>
+// acc + sign * (row K of H) . x' as one FMA per coefficient (acc = b, sign = -1: the residual).
+template <typename T, int MODE, bool NEG>
 __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x,
-                                     const T *__restrict__ e, const MGArgs &a, int c, int k) {
+                                     const T *__restrict__ e, const MGArgs &a, int c, int k, T acc) {
   const int64_t C = a.ncell, K = (int64_t)c * a.L + k;
-  T y = __ldg(H + K) * xin<T, MODE>(x, e, a.parent, c, k, a.L);
+  auto term = [&](int slot, int col, int kk) {
+    const T h = __ldg(H + slot * C + K);
+    acc = fma(NEG ? -h : h, xin<T, MODE>(x, e, a.parent, col, kk, a.L), acc);
+  };
+  term(0, c, k);
 #pragma unroll
-  for (int f = 0; f < 4; ++f)
-    y += __ldg(H + (1 + f) * C + K) * xin<T, MODE>(x, e, a.parent, __ldg(a.col_nbr + 4 * (int64_t)c + f), k, a.L);
-  if (k > 0) y += __ldg(H + 5 * C + K) * xin<T, MODE>(x, e, a.parent, c, k - 1, a.L);
-  if (k < a.L - 1) y += __ldg(H + 6 * C + K) * xin<T, MODE>(x, e, a.parent, c, k + 1, a.L);
-  return y;
+  for (int f = 0; f < 4; ++f) term(1 + f, __ldg(a.col_nbr + 4 * (int64_t)c + f), k);
+  if (k > 0) term(5, c, k - 1);
+  if (k < a.L - 1) term(6, c, k + 1);
+  return acc;
 }
 
 // MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x);
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(256)
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
     T r = b[K];
-    if (MODE != 0) r -= h_apply<T, MODE>(H, x, e, a, c, k);
+    if (MODE != 0) r = h_apply<T, MODE, true>(H, x, e, a, c, k, r);
     sr[i] = r;
     ssub[i] = k > 0 ? __ldg(H + 5 * C + K) : (T)0;
     sinv[i] = __ldg(hinv + K);
@@ -100,7 +104,7 @@ __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict_
   for (int i = 0; i < 4; ++i) {
     const int ch = __ldg(children + 4 * (int64_t)cc + i);
     T r = b[(int64_t)ch * a.L + k];
-    if (x != nullptr) r -= h_apply<T, 1>(H, x, nullptr, a, ch, k);
+    if (x != nullptr) r = h_apply<T, 1, true>(H, x, nullptr, a, ch, k, r);
     s += r;
   }
   bc[Kc] = s;
@@ -112,7 +116,7 @@ __global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= a.ncell) return;
   const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
-  y[K] = h_apply<T, 1>(H, x, nullptr, a, c, k);
+  y[K] = h_apply<T, 1, false>(H, x, nullptr, a, c, k, (T)0);
 }
 
 static MGArgs mg_args(const Ctx *c, int l) {
@@ -120,7 +124,8 @@ static MGArgs mg_args(const Ctx *c, int l) {
   MGArgs a;
   a.L = lv.nlev;
   a.ncol = lv.ncol;
-  a.cpb = 256 / lv.nlev > 0 ? 256 / lv.nlev : 1;
+  const int cmax = 256 / lv.nlev > 0 ? 256 / lv.nlev : 1;
+  a.cpb = c->tune_mg_cpb[l] > 0 && c->tune_mg_cpb[l] <= cmax ? c->tune_mg_cpb[l] : cmax;
   a.ncell = lv.ncell;
   a.col_nbr = lv.col_nbr;
   a.parent = lv.parent;
@@ -128,16 +133,40 @@ static MGArgs mg_args(const Ctx *c, int l) {
 }
 
 template <typename T, int MODE>
-static int smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
+static int smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out, int cpb_override = 0) {
   const Level &lv = c->lv[l];
   MGArgs a = mg_args(c, l);
+  if (cpb_override > 0 && cpb_override * lv.nlev <= 256) a.cpb = cpb_override;
   const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
   const size_t smem = (size_t)4 * a.cpb * lv.nlev * sizeof(T);
-  mg_smooth_kernel<T, MODE><<<g, 256, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_inv(lv),
-                                                         Prec<T>::Hz_cp(lv), b, x, e, out,
-                                                         (T)c->opt.mg_omega);
+  int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
+  if (threads > 256) threads = 256;
+  mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_inv(lv),
+                                                             Prec<T>::Hz_cp(lv), b, x, e, out,
+                                                             (T)c->opt.mg_omega);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
+}
+
+// Average time of 5 FP64 smoothing sweeps on level l with `cpb` columns per block.
+int time_mg_cpb(Ctx *c, int l, int cpb, float *ms) {
+  Level &lv = c->lv[l];
+  double *b = static_cast<double *>(lv.vb), *x = static_cast<double *>(lv.vx), *y = static_cast<double *>(lv.vy);
+  HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * lv.ncell, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * lv.ncell, c->stream));
+  int st = smooth<double, 1>(c, l, b, x, nullptr, y, cpb);
+  cudaEvent_t e0, e1;
+  HMG_CUDA(c, cudaEventCreate(&e0));
+  HMG_CUDA(c, cudaEventCreate(&e1));
+  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  for (int i = 0; i < 5 && !st; ++i) st = smooth<double, 1>(c, l, b, x, nullptr, y, cpb);
+  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  HMG_CUDA(c, cudaEventSynchronize(e1));
+  cudaEventElapsedTime(ms, e0, e1);
+  *ms /= 5.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 // n sweeps on level l from zero (n >= 1); the result ends in *cur (one of lv.vx / lv.vy).

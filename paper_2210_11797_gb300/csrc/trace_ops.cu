@@ -16,6 +16,8 @@ namespace hmg {
 
 static TraceDims dims_of(const Level &f) { return TraceDims{f.nlev, f.nth, f.ntrace}; }
 
+constexpr int kSpmvRows = 4;   // rows of S per thread in the S apply with fused reductions
+
 // ---- y = S x with optional fused inner products -----------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kRedThreads)
@@ -23,17 +25,23 @@ __global__ void __launch_bounds__(kRedThreads)
                 const double *__restrict__ w, const TraceDims d, const int32_t *__restrict__ stencil,
                 const int32_t *__restrict__ col_edges, double *part, unsigned int *counter,
                 double *scal, int slot0, int slot1) {
+  // kSpmvRows rows per thread (block-strided, so each pass stays coalesced): the block's
+  // shuffle reduction, 5 FP64 adds per value and thread, is paid once per kSpmvRows rows
   double a0 = 0.0, a1 = 0.0;
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row < d.NT) {
-    if (MODE == 3) {
-      const double v = s_row<double, double, double, true>(S, x, stencil, col_edges, d, row, __ldg(w + row));
-      a0 = v * v;
-    } else {
-      const double v = s_row<double, double, double, false>(S, x, stencil, col_edges, d, row, 0.0);
-      y[row] = v;
-      if (MODE == 1) a0 = __ldg(w + row) * v;
-      if (MODE == 2) { a0 = v * __ldg(w + row); a1 = v * v; }
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kSpmvRows + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kSpmvRows; ++j) {
+    const int64_t row = base + (int64_t)j * blockDim.x;
+    if (row < d.NT) {
+      if (MODE == 3) {
+        const double v = s_row<double, double, double, true>(S, x, stencil, col_edges, d, row, __ldg(w + row));
+        a0 = fma(v, v, a0);
+      } else {
+        const double v = s_row<double, double, double, false>(S, x, stencil, col_edges, d, row, 0.0);
+        y[row] = v;
+        if (MODE == 1) a0 = fma(__ldg(w + row), v, a0);
+        if (MODE == 2) { a0 = fma(v, __ldg(w + row), a0); a1 = fma(v, v, a1); }
+      }
     }
   }
   if (MODE == 1 || MODE == 3) {
@@ -80,7 +88,7 @@ int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, i
                 int slot1) {
   const Level &f = c->lv[0];
   const TraceDims d = dims_of(f);
-  const unsigned g = grid_for(f.ntrace, kRedThreads);   // one row per thread
+  const unsigned g = grid_for(f.ntrace, kRedThreads * kSpmvRows);
   if (g > (unsigned)kMaxRedBlocks) return fail(c, HMG_ERR_INVALID_ARG, "too many rows for one reduction");
   Prof prof(c, kCompApply);
   switch (mode) {
@@ -239,24 +247,29 @@ __global__ void __launch_bounds__(256)
     T r = (T)__ldg(b + row);
     if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
     const T old = ZERO ? (T)0 : lam_in[row];
-    lam_out[row] = (Tout)(old + omega * r * __ldg(hinv + row));
+    lam_out[row] = (Tout)fma(r * __ldg(hinv + row), omega, old);
   }
 }
 
 template <typename T, typename Tb, typename Tout, bool ZERO>
-static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out) {
+static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int cpb_override = 0) {
   const Level &f = c->lv[0];
   SweepArgs a;
   a.d = dims_of(f);
   a.ncol = f.ncol;
-  a.cpb = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
+  const int cpb_max = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
+  a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb > 0 ? c->tune_sweep_cpb : cpb_max);
+  if (a.cpb > cpb_max) a.cpb = cpb_max;
   a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
   a.stencil = f.edge_stencil;
   a.col_edges = f.col_edges;
-  const unsigned nhb = grid_for(f.nth, 256);
+  // threads: the column block's rows rounded up to whole warps (at most 256)
+  int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
+  if (threads > 256) threads = 256;
+  const unsigned nhb = grid_for(f.nth, threads);
   const size_t smem = (size_t)4 * a.cpb * (f.nlev + 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
-  sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, 256, smem, c->stream>>>(
+  sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
       a, Prec<T>::S(c), Prec<T>::Sz_inv(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_inv(c), b, lam_in,
       lam_out, (T)c->opt.omega);
   HMG_CUDA(c, cudaGetLastError());
@@ -479,3 +492,62 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
   return HMG_OK;
 }
+
+// ---- launch-shape autotuning ---------------------------------------------------------------
+namespace hmg {
+
+// Average time of 5 full FP64 sweeps with `cpb` columns per z-block (work vectors as data).
+int time_sweep_cpb(Ctx *c, int cpb, float *ms) {
+  const int64_t T = c->lv[0].ntrace;
+  double *b = static_cast<double *>(c->w1), *x = static_cast<double *>(c->w2), *y = static_cast<double *>(c->w3);
+  HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * T, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * T, c->stream));
+  int st;
+  if ((st = launch_sweep<double, double, double, false>(c, b, x, y, cpb))) return st;   // warm-up
+  cudaEvent_t e0, e1;
+  HMG_CUDA(c, cudaEventCreate(&e0));
+  HMG_CUDA(c, cudaEventCreate(&e1));
+  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  for (int i = 0; i < 5 && !st; ++i) st = launch_sweep<double, double, double, false>(c, b, x, y, cpb);
+  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  HMG_CUDA(c, cudaEventSynchronize(e1));
+  cudaEventElapsedTime(ms, e0, e1);
+  *ms /= 5.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+int autotune(Ctx *c) {
+  const Level &f = c->lv[0];
+  const int cmax = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
+  int best = cmax;
+  float best_ms = 1e30f;
+  const int profile = c->opt.profile;
+  c->opt.profile = 0;
+  int st = HMG_OK;
+  for (int cand : {cmax, cmax / 2, cmax / 4, 2, 1}) {
+    if (cand < 1 || cand > cmax) continue;
+    float ms = 0.f;
+    if ((st = time_sweep_cpb(c, cand, &ms))) break;
+    if (ms < best_ms) { best_ms = ms; best = cand; }
+  }
+  if (!st) c->tune_sweep_cpb = best;
+  for (int l = 0; l < c->nmg && !st; ++l) {
+    const int L = c->lv[l].nlev;
+    const int mmax = 256 / L > 0 ? 256 / L : 1;
+    int mbest = mmax;
+    float mbest_ms = 1e30f;
+    for (int cand : {mmax, mmax / 2, mmax / 4, 2, 1}) {
+      if (cand < 1 || cand > mmax) continue;
+      float ms = 0.f;
+      if ((st = time_mg_cpb(c, l, cand, &ms))) break;
+      if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; }
+    }
+    if (!st) c->tune_mg_cpb[l] = mbest;
+  }
+  c->opt.profile = profile;
+  return st;
+}
+
+}  // namespace hmg

@@ -55,7 +55,7 @@ class Options(C.Structure):
                 ("n_post", C.c_int32), ("n_smooth", C.c_int32), ("omega", C.c_double),
                 ("mg_npre", C.c_int32), ("mg_npost", C.c_int32), ("mg_ncoarse", C.c_int32),
                 ("mg_omega", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("divergence", C.c_double), ("profile", C.c_int32)]
+                ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -97,7 +97,27 @@ _SIGS = {
     "hmg_pressure_vcycle": ([_P, _P, _P], C.c_int),
     "hmg_get_gamma": ([_P, _P], C.c_int),
     "hmg_get_trace_operator": ([_P, _P], C.c_int),
+    "hmg_solve_batched": ([C.POINTER(_P), C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                           C.POINTER(SolveStats)], C.c_int),
+    "hmg_autotune": ([_P], C.c_int),
 }
+
+
+def solve_batched(solvers, Rubs, Rpis, lams=None, check=True):
+    """n independent solves (one per Solver, each with its own mesh) in one graph launch.
+    Returns (list of lambda tensors, list of stats dicts)."""
+    n = len(solvers)
+    lams = lams or [s._empty(s.ntrace) for s in solvers]
+    P = C.c_void_p
+    ctxs = (P * n)(*[s.ctx.value for s in solvers])
+    rub = (P * n)(*[s._dev(r, 6 * s.ncell, "Rub").value for s, r in zip(solvers, Rubs)])
+    rpi = (P * n)(*[s._dev(r, s.ncell, "Rpi").value for s, r in zip(solvers, Rpis)])
+    lam = (P * n)(*[s._dev(l, s.ntrace, "lambda").value for s, l in zip(solvers, lams)])
+    stats = (SolveStats * n)()
+    rc = lib().hmg_solve_batched(ctxs, n, rub, rpi, lam, stats)
+    if check:
+        _check(solvers[0].ctx, rc)
+    return lams, [st.as_dict() for st in stats]
 
 
 def header_symbols():
@@ -286,6 +306,9 @@ class Solver:
         g = self._empty(self.ncell)
         _check(self.ctx, lib().hmg_get_gamma(self.ctx, _ptr(g)))
         return g
+
+    def autotune(self):
+        _check(self.ctx, lib().hmg_autotune(self.ctx))
 
     def trace_operator_slots(self):
         out = self.torch.empty((11, self.ntrace), dtype=self.torch.float64, device=self.device)

@@ -1,0 +1,73 @@
+"""Device-side iteration (CUDA graph with a WHILE node), batched solves in one graph launch,
+and launch-shape autotuning: each must give what the host-driven single solve gives."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.nonnested import HybridSolver
+from paper_2210_11797_gb300 import inputs as I
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def _workloads():
+    return [I.planar_helmholtz(), I.cubed_sphere(6, 5, nmg=2, seed=4), I.cubed_sphere(12, 10, seed=5),
+            I.cubed_sphere(8, 7, seed=6)]
+
+
+def test_graph_loop_equals_host_loop():
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(12, 30)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-8)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    gpu.set_options(graph=0)
+    lam0, st0 = gpu.solve(Rub, Rpi)
+    gpu.set_options(graph=1)
+    lam1, st1 = gpu.solve(Rub, Rpi)
+    lam2, st2 = gpu.solve(Rub, Rpi)            # cached graph, replayed
+    assert st0["status"] == st1["status"] == "ok"
+    assert st0["iterations"] == st1["iterations"] == st2["iterations"]
+    assert torch.equal(lam0, lam1) and torch.equal(lam1, lam2)
+    assert st0["history"] == st1["history"]
+    # a changed option rebuilds the graph
+    gpu.set_options(max_iter=2, tol=1e-14)
+    _l, st3 = gpu.solve(Rub, Rpi, check=False)
+    assert st3["status"] == "not_converged" and st3["iterations"] == 2
+    gpu.close()
+
+
+def test_batched_solves_equal_single_solves():
+    from paper_2210_11797_gb300.hmg import Solver, solve_batched
+    ws = _workloads()
+    solvers = [Solver(w.hier, w.coeffs, tol=1e-9, precision="mixed") for w in ws]
+    Rubs = [_cuda(w.Rub.ravel()) for w in ws]
+    Rpis = [_cuda(w.Rpi) for w in ws]
+    lams, stats = solve_batched(solvers, Rubs, Rpis)
+    for s, w, r, p, lam, st in zip(solvers, ws, Rubs, Rpis, lams, stats):
+        single, st1 = s.solve(r, p)
+        assert st["status"] == "ok" and st["iterations"] == st1["iterations"]
+        assert torch.equal(lam, single)
+        ora = HybridSolver(w.hier, w.coeffs)
+        B = ora.rhs(w.Rub, w.Rpi)
+        lo = lam.cpu().numpy()
+        assert np.linalg.norm(B - ora.S @ lo) / np.linalg.norm(B) <= 1.05e-9
+    for s in solvers:
+        s.close()
+
+
+def test_autotuned_shapes_keep_results():
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(12, 30)
+    gpu = Solver(w.hier, w.coeffs)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam0, st0 = gpu.solve(Rub, Rpi)
+    gpu.autotune()
+    lam1, st1 = gpu.solve(Rub, Rpi)
+    # the column-block shape changes which block solves which columns, not the arithmetic
+    assert torch.equal(lam0, lam1) and st0["iterations"] == st1["iterations"]
+    gpu.close()
