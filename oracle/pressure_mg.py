@@ -114,9 +114,10 @@ class PressureMultigrid:
         fine, coarse = self.hier.meshes[l], self.hier.meshes[l + 1]
         return e.reshape(coarse.ncol, coarse.nlev)[self.hier.parents[l]].ravel()
 
-    def vcycle(self, b, l=0):
-        """One V-cycle for H_l x = b from a zero initial guess."""
-        x = np.zeros_like(b)
+    def vcycle(self, b, l=0, x0=None):
+        """One V-cycle for H_l x = b from a zero initial guess, or from x0 (the first
+        smoothing sweep of level l then starts from x0)."""
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
         if l == self.hier.nmg - 1:
             for _ in range(self.ncoarse):
                 x = self.block_jacobi(l, x, b)

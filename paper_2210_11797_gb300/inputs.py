@@ -400,3 +400,53 @@ def batched_sizes(count: int = 64, seed: int = 3):
     u = uniform01(seed, 2 * count)
     ns, ls = (12, 24, 32, 48), (10, 30, 50, 70)
     return [(ns[int(u[2 * i] * 4)], ls[int(u[2 * i + 1] * 4)]) for i in range(count)]
+
+
+# --------------------------------------------------------------------------------------
+# Initial weights of the learned coarse model
+# --------------------------------------------------------------------------------------
+COARSE_MODEL_CHANNELS = 32
+COARSE_MODEL_SHAPES = (("W1", (32, 1, 3)), ("W2", (32, 32, 3)), ("M", (32, 3)), ("W3", (1, 32, 3)))
+
+
+def coarse_model_init(seed: int = 0) -> dict:
+    """He-scaled SplitMix64 normals for the convolutions; the horizontal mix starts as the
+    identity plus a small positive share of the neighbours (w_c, w_e, w_d) = (1, 0.1, 0.05)."""
+    ch = COARSE_MODEL_CHANNELS
+    z = normal(seed, ch * 3 + ch * ch * 3 + ch * 3)
+    n1, n2 = ch * 3, ch * ch * 3
+    return {
+        "W1": z[:n1].reshape(ch, 1, 3) * math.sqrt(2.0 / 3.0),
+        "W2": z[n1:n1 + n2].reshape(ch, ch, 3) * math.sqrt(2.0 / (3.0 * ch)),
+        "M": np.tile(np.array([1.0, 0.1, 0.05]), (ch, 1)),
+        "W3": z[n1 + n2:].reshape(1, ch, 3) * math.sqrt(1.0 / (3.0 * ch)),
+    }
+
+
+def flatten_coarse_model(params: dict) -> np.ndarray:
+    """The flat FP32 parameter vector of the C ABI: W1, W2, M, W3 in that order."""
+    return np.concatenate([np.asarray(params[k], np.float64).reshape(-1) for k, _ in COARSE_MODEL_SHAPES]
+                          ).astype(np.float32)
+
+
+def unflatten_coarse_model(v) -> dict:
+    out, o = {}, 0
+    for k, shp in COARSE_MODEL_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(v[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
+
+
+def panel_patch_columns(n: int, npanel: int, nx: int, ny: int, stride: int | None = None) -> np.ndarray:
+    """Column ids of nx x ny patches cut from the regular n x n grid of each panel (column
+    p n^2 + j n + i; the planar mesh is one panel): [npatch][nx ny], patch column q = jj nx + ii,
+    patch origins every `stride` columns (default: non-overlapping)."""
+    sx, sy = (stride or nx), (stride or ny)
+    out = []
+    for p in range(npanel):
+        for j0 in range(0, n - ny + 1, sy):
+            for i0 in range(0, n - nx + 1, sx):
+                jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+                out.append((p * n * n + (j0 + jj) * n + (i0 + ii)).reshape(-1))
+    return np.asarray(out, np.int32)

@@ -263,3 +263,16 @@ def test_pressure_operator_annihilates_constants_up_to_mass_term():
     assert np.array_equal(pressure_mg.pressure_operator_times(s.mg.parts0, one), m)
     H = s.mg.H[0]
     assert np.all(np.abs(H @ one - m) <= 1e-14 * (abs(H) @ one))
+
+
+def test_vcycle_from_the_exact_solution_stays_there(config1):
+    """Started from x0 = H^-1 b every residual is zero, so the V-cycle returns x0 (this pins
+    the initial-guess form used by the learned coarse solve)."""
+    import scipy.sparse.linalg as spla
+    w, s = config1
+    H = s.mg.H[0].tocsc()
+    b = np.random.default_rng(9).standard_normal(H.shape[0])
+    x0 = spla.spsolve(H, b)
+    np.testing.assert_allclose(s.mg.vcycle(b, x0=x0), x0, rtol=1e-10, atol=1e-12 * np.abs(x0).max())
+    # and from a zero guess it is the plain V-cycle
+    np.testing.assert_array_equal(s.mg.vcycle(b, x0=np.zeros_like(b)), s.mg.vcycle(b))
