@@ -149,6 +149,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     stats = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # profiler range = the timed steps (ncu --profile-from-start off captures only these)
+    torch.cuda.cudart().cudaProfilerStart()
     with ClockSampler(dev) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -156,6 +158,7 @@ def run_ours(args, rank, world):
             stats.append(st)
         e1.record(stream)
         torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
     if world > 1:
         torch.distributed.barrier()
     ms_total = e0.elapsed_time(e1)

@@ -109,7 +109,19 @@ typedef struct {
   int32_t graph;        /* 1 (default): the whole solve is one CUDA graph whose BiCGStab loop
                            is a device-side WHILE node (no host round trip per iteration);
                            0: the host drives the loop (always so when profile = 1) */
+  int32_t coarse;       /* coarse solve of Algorithm 2 line 6: HMG_COARSE_* */
+  int32_t krylov;       /* HMG_KRYLOV_BICGSTAB (default) or HMG_KRYLOV_FGMRES */
+  int32_t restart;      /* FGMRES restart length (30) */
+  double stall_ratio;   /* FGMRES with a learned coarse solve falls back to the V-cycle for the
+                           rest of the solve after two consecutive steps that each reduce the
+                           residual estimate by less than this factor (0.9) */
 } hmg_options;
+
+#define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
+#define HMG_COARSE_LEARNED 1        /* the learned model f ~ H^-1 alone */
+#define HMG_COARSE_LEARNED_VCYCLE 2 /* the model's output as the V-cycle's initial guess */
+#define HMG_KRYLOV_BICGSTAB 0
+#define HMG_KRYLOV_FGMRES 1
 
 #define HMG_MAX_HISTORY 512
 /* Solver components timed when hmg_options.profile = 1 (cf. Table time_in_components):
@@ -120,7 +132,8 @@ typedef struct {
 #define HMG_NCOMP 8
 typedef struct {
   int32_t status;            /* HMG_OK or the reason the iteration stopped */
-  int32_t iterations;        /* completed BiCGStab iterations */
+  int32_t iterations;        /* completed BiCGStab iterations (FGMRES: steps, i.e.
+                                preconditioner applications) */
   double rel_residual;       /* recurrence residual ||r_i|| / ||B|| at exit */
   double true_rel_residual;  /* ||B - S lambda|| / ||B|| recomputed in FP64 at exit */
   double solve_ms;           /* device time of the call (CUDA events on the stream) */
@@ -245,6 +258,61 @@ int hmg_get_gamma(hmg_ctx *ctx, double *gamma);
  * 1-4 faces e0..e3 of the cell above (c, k); 5 its top; 6-9 faces e0..e3 of the cell
  * below (c, k-1); 10 its bottom. Slots of a missing cell (ground, lid) hold 0. */
 int hmg_get_trace_operator(hmg_ctx *ctx, double *slots);
+
+/* ---- learned coarse correction ------------------------------------------------------ */
+/* The paper has no learned component. These calls replace (HMG_COARSE_LEARNED) or seed
+ * (HMG_COARSE_LEARNED_VCYCLE) the coarse solve H dPi = bbar of Algorithm 2 line 6 with a
+ * small network f: dPi = D^-1/2 f(D^-1/2 bbar), D = diag(H_0). f acts per column over the
+ * levels (zero padding at ground and lid), bias-free:
+ *   h1 = relu(conv(1 -> 32, 3)), h2 = relu(conv(32 -> 32, 3)),
+ *   h3 = relu(w_c h2 + w_e * (sum of the 4 edge neighbours) + w_d * (sum of the 4 corner
+ *        neighbours)) per channel, y = conv(32 -> 1, 3); conv(a -> b, 3): y[o][k] =
+ *   sum_i sum_d W[o][i][d] x[i][k + d - 1].
+ * Parameters (FP32, flat): W1 [32][1][3] at 0, W2 [32][32][3] at 96, (w_c, w_e, w_d) [32][3]
+ * at 3168, W3 [1][32][3] at 3264; 3360 in all. Inference and training store weights and
+ * activations in BF16 and accumulate in FP32 (fp32 = 1 keeps them in FP32, for checks).
+ * Use it with HMG_KRYLOV_FGMRES (the map is not linear). Corner neighbours: across local
+ * face i to column n, then across the face of n that follows the shared one (mod 4). */
+
+/* Number of parameters (3360). */
+int32_t hmg_coarse_model_size(void);
+
+/* Set / read the parameters (host arrays of n = hmg_coarse_model_size() floats). Needs the
+ * mesh (at most 128 levels); the first call allocates the model's device buffers. */
+int hmg_set_coarse_model(hmg_ctx *ctx, const float *params, int32_t n);
+int hmg_get_coarse_model(hmg_ctx *ctx, float *params, int32_t n);
+
+/* out = D^-1/2 f(D^-1/2 bbar) on the finest mesh; bbar, out [ncell] device FP64. */
+int hmg_apply_coarse_model(hmg_ctx *ctx, const double *bbar, double *out, int32_t fp32);
+
+/* Training samples are nx x ny patches of columns (column q = j nx + i of a patch, the
+ * regular grid's edge and corner neighbours, zero outside the patch): x, t [nsamp][nx ny]
+ * [nlev] device FP32, with t the target of f(x). Loss = mean over the samples of
+ * ||f(x_s) - t_s||^2 / ||t_s||^2. hmg_coarse_model_grad writes that loss (host) and its
+ * gradient (host, [3360]); hmg_train_coarse_model runs `epochs` passes of Adam
+ * (beta 0.9 / 0.999, eps 1e-8, learning rate lr) over minibatches of `batch` samples in an
+ * order shuffled per epoch by SplitMix64(seed), updating the model in place, and writes the
+ * mean loss of each epoch to loss_hist (host [epochs], may be NULL). */
+int hmg_coarse_model_grad(hmg_ctx *ctx, const float *x, const float *t, int32_t nsamp, int32_t nx,
+                          int32_t ny, int32_t fp32, float *grad, double *loss);
+int hmg_train_coarse_model(hmg_ctx *ctx, const float *x, const float *t, int32_t nsamp, int32_t nx,
+                           int32_t ny, int32_t batch, int32_t epochs, double lr, uint64_t seed,
+                           double *loss_hist);
+
+/* One solve (FP64, HMG_PRECOND_NONNESTED, host-driven loop) that also records, at each of its
+ * first max_pairs preconditioner applications, the pair x = D^-1/2 bbar and
+ * t = D^1/2 H^-1 bbar, with H^-1 bbar from pressure V-cycles iterated to a relative residual
+ * of 1e-12 (at most 80): x_out, t_out [max_pairs][ncell] device FP32; *n_out = pairs taken. */
+int hmg_collect_coarse_pairs(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *lambda,
+                             int32_t max_pairs, float *x_out, float *t_out, int32_t *n_out,
+                             hmg_solve_stats *stats);
+
+/* Cut training patches out of collected pairs: patch p takes the columns cols[p][0..P) of pair
+ * pair[p] (device int32 arrays, checked on the host), scaling x and t by 1 / rms(x patch):
+ * xo, to [npatch][P][nlev] device FP32. xs, ts [npairs][ncell]. */
+int hmg_extract_patches(hmg_ctx *ctx, const float *xs, const float *ts, int32_t npairs,
+                        const int32_t *pair, const int32_t *cols, int32_t npatch, int32_t patch_cols,
+                        float *xo, float *to);
 
 #ifdef __cplusplus
 }

@@ -37,6 +37,10 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_npre < 1 || o.mg_npost < 1 || o.mg_ncoarse < 1) return bad("multigrid sweep counts must be >= 1");
   if (!std::isfinite(o.omega) || !std::isfinite(o.mg_omega)) return bad("relaxation factors");
   if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.divergence > 0.0)) return bad("tol / max_iter / divergence");
+  if (o.coarse < HMG_COARSE_VCYCLE || o.coarse > HMG_COARSE_LEARNED_VCYCLE) return bad("coarse");
+  if (o.krylov != HMG_KRYLOV_BICGSTAB && o.krylov != HMG_KRYLOV_FGMRES) return bad("krylov");
+  if (o.restart < 1 || o.restart > 64) return bad("restart must be in 1..64");
+  if (!(o.stall_ratio > 0.0)) return bad("stall_ratio");
   return HMG_OK;
 }
 
@@ -101,6 +105,10 @@ int hmg_default_options(hmg_options *o) {
   o->divergence = 1e3;
   o->profile = 0;
   o->graph = 1;
+  o->coarse = HMG_COARSE_VCYCLE;
+  o->krylov = HMG_KRYLOV_BICGSTAB;
+  o->restart = 30;
+  o->stall_ratio = 0.9;
   return HMG_OK;
 }
 
@@ -481,6 +489,104 @@ int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
   HMG_CUDA(c, cudaMemcpyAsync(slots, c->S, sizeof(double) * kSlots * c->lv[0].ntrace,
                               cudaMemcpyDeviceToDevice, c->stream));
   return finish(c, HMG_OK);
+}
+
+// ---- learned coarse correction -------------------------------------------------------------
+static int mesh_ready(hmg_ctx *c) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, HMG_ERR_NOT_READY, "call hmg_set_mesh first");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  return HMG_OK;
+}
+
+int32_t hmg_coarse_model_size(void) { return kCoarseParams; }
+
+int hmg_set_coarse_model(hmg_ctx *c, const float *params, int32_t n) {
+  int st = mesh_ready(c);
+  if (st) return st;
+  if (!params || n != kCoarseParams) return fail(c, HMG_ERR_INVALID_ARG, "params must hold hmg_coarse_model_size() floats");
+  if ((st = nn_setup(c))) return st;
+  HMG_CUDA(c, cudaMemcpyAsync(c->nn_w, params, sizeof(float) * kCoarseParams, cudaMemcpyHostToDevice, c->stream));
+  return finish(c, HMG_OK);
+}
+
+int hmg_get_coarse_model(hmg_ctx *c, float *params, int32_t n) {
+  int st = mesh_ready(c);
+  if (st) return st;
+  if (!params || n != kCoarseParams) return fail(c, HMG_ERR_INVALID_ARG, "params must hold hmg_coarse_model_size() floats");
+  if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
+  HMG_CUDA(c, cudaMemcpyAsync(params, c->nn_w, sizeof(float) * kCoarseParams, cudaMemcpyDeviceToHost, c->stream));
+  return finish(c, HMG_OK);
+}
+
+int hmg_apply_coarse_model(hmg_ctx *c, const double *bbar, double *out, int32_t fp32) {
+  int st = ready(c);
+  if (st) return st;
+  if (!bbar || !out || bbar == out) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
+  return finish(c, apply_coarse_model(c, bbar, out, fp32 ? 1 : 0));
+}
+
+static int check_patches(hmg_ctx *c, const float *x, const float *t, int32_t nsamp, int32_t nx, int32_t ny) {
+  if (!x || !t) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if (nsamp < 1 || nx < 1 || ny < 1 || (int64_t)nsamp * nx * ny > (1 << 26))
+    return fail(c, HMG_ERR_INVALID_ARG, "bad patch batch shape");
+  if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
+  return HMG_OK;
+}
+
+int hmg_coarse_model_grad(hmg_ctx *c, const float *x, const float *t, int32_t nsamp, int32_t nx, int32_t ny,
+                          int32_t fp32, float *grad, double *loss) {
+  int st = mesh_ready(c);
+  if (st) return st;
+  if ((st = check_patches(c, x, t, nsamp, nx, ny))) return st;
+  if (!grad || !loss) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  return coarse_model_grad(c, x, t, nsamp, nx, ny, fp32 ? 1 : 0, grad, loss);
+}
+
+int hmg_train_coarse_model(hmg_ctx *c, const float *x, const float *t, int32_t nsamp, int32_t nx, int32_t ny,
+                           int32_t batch, int32_t epochs, double lr, uint64_t seed, double *loss_hist) {
+  int st = mesh_ready(c);
+  if (st) return st;
+  if ((st = check_patches(c, x, t, nsamp, nx, ny))) return st;
+  if (batch < 1 || batch > nsamp || epochs < 0 || !(lr > 0.0)) return fail(c, HMG_ERR_INVALID_ARG, "bad training settings");
+  return train_coarse_model(c, x, t, nsamp, nx, ny, batch, epochs, lr, seed, loss_hist);
+}
+
+int hmg_collect_coarse_pairs(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, int32_t max_pairs,
+                             float *x_out, float *t_out, int32_t *n_out, hmg_solve_stats *stats) {
+  int st = ready(c);
+  if (st) return st;
+  if (!Rub || !Rpi || !lambda || !x_out || !t_out || !n_out || max_pairs < 1)
+    return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  if (c->opt.precision != HMG_PRECISION_FP64 || c->opt.precond != HMG_PRECOND_NONNESTED)
+    return fail(c, HMG_ERR_INVALID_ARG, "pairs are collected from the FP64 non-nested preconditioner");
+  c->collect_x = x_out;
+  c->collect_t = t_out;
+  c->collect_max = max_pairs;
+  c->collect_n = 0;
+  st = krylov_solve(c, Rub, Rpi, lambda, stats);
+  *n_out = c->collect_n;
+  c->collect_x = c->collect_t = nullptr;
+  c->collect_max = c->collect_n = 0;
+  return st;
+}
+
+int hmg_extract_patches(hmg_ctx *c, const float *xs, const float *ts, int32_t npairs, const int32_t *pair,
+                        const int32_t *cols, int32_t npatch, int32_t patch_cols, float *xo, float *to) {
+  int st = ready(c);
+  if (st) return st;
+  if (!xs || !ts || !pair || !cols || !xo || !to || npairs < 1 || npatch < 1 || patch_cols < 1)
+    return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  // the gather's indices are checked on the host before the kernel reads through them
+  std::vector<int32_t> hp(npatch), hc((size_t)npatch * patch_cols);
+  HMG_CUDA(c, cudaMemcpy(hp.data(), pair, sizeof(int32_t) * hp.size(), cudaMemcpyDeviceToHost));
+  HMG_CUDA(c, cudaMemcpy(hc.data(), cols, sizeof(int32_t) * hc.size(), cudaMemcpyDeviceToHost));
+  for (int32_t v : hp)
+    if (v < 0 || v >= npairs) return fail(c, HMG_ERR_INVALID_ARG, "pair index out of range");
+  for (int32_t v : hc)
+    if (v < 0 || v >= c->lv[0].ncol) return fail(c, HMG_ERR_INVALID_ARG, "column index out of range");
+  return extract_patches(c, xs, ts, c->lv[0].ncell, pair, cols, npatch, patch_cols, xo, to);
 }
 
 }  // extern "C"

@@ -68,6 +68,16 @@ struct Level {
   void *vb = nullptr, *vx = nullptr, *vy = nullptr;
 };
 
+// Work buffers of the coarse-model training (learned.cu).
+struct TrainBufs {
+  int64_t cap_cells = 0;
+  void *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;   // activations (BF16 or FP32)
+  float *ga3 = nullptr, *ga2 = nullptr, *gy = nullptr;
+  double *loss_part = nullptr, *loss = nullptr;
+  float *part3 = nullptr, *partM = nullptr, *part2 = nullptr, *part1 = nullptr;
+  float *grad = nullptr, *m = nullptr, *v = nullptr, *tn = nullptr;
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -116,6 +126,19 @@ struct Ctx {
   // pressure smoother on each level
   int tune_sweep_cpb = 0;
   int tune_mg_cpb[kMaxLevels] = {0};
+  // learned coarse correction: FP32 master weights, one activation buffer, corner neighbours
+  float *nn_w = nullptr;
+  void *nn_act = nullptr;
+  int32_t *nn_diag = nullptr;
+  TrainBufs train;
+  bool coarse_fallback = false;   // set by the flexible Krylov loop when it stalls
+  // collection of (scaled bbar, scaled H^-1 bbar) pairs at the preconditioner calls
+  float *collect_x = nullptr, *collect_t = nullptr;
+  int collect_max = 0, collect_n = 0;
+  double *collect_r = nullptr, *collect_e = nullptr, *collect_y = nullptr;
+  // flexible GMRES basis: V [restart+1][ntrace], Z [restart][ntrace], Hessenberg column
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
+  int gm_restart = 0;
   std::vector<void *> owned;   // every device allocation, freed by hmg_destroy
   // component timing (hmg_options.profile): event pool and (component, start, end) marks
   std::vector<cudaEvent_t> ev_pool;
@@ -189,6 +212,25 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
                          const double *const *Rpi, double *const *lambda, hmg_solve_stats *st);
 // Releases the context's cached solve graph.
 void drop_graph(Ctx *c);
+
+// ---- learned coarse correction (learned.cu) ---------------------------------------------
+constexpr int kCoarseParams = 3360;
+int nn_setup(Ctx *c);
+template <typename T>
+int learned_coarse(Ctx *c, const T *bbar, T *out);
+int apply_coarse_model(Ctx *c, const double *bbar, double *out, int fp32);
+int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int fp32,
+                      float *grad_host, double *loss_host);
+int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int batch,
+                       int epochs, double lr, uint64_t seed, double *loss_hist);
+int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, const int32_t *pair,
+                    const int32_t *cols, int npatch, int P, float *xo, float *to);
+// records (D^-1/2 bbar, D^1/2 H^-1 bbar) for the current preconditioner call (FP64 path)
+int collect_pair(Ctx *c, const double *bbar);
+// r = b - H_l x (FP64) on level l
+int pressure_residual_fp64(Ctx *c, int level, const double *b, const double *x, double *r);
+// flexible GMRES(restart) driver (krylov.cu)
+int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st);
 // Launch-shape autotuning of one context (columns per block of the sweep and MG smoother).
 int autotune(Ctx *c);
 // Sweep launch with explicit columns per block (autotuner).

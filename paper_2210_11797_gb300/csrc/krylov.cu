@@ -293,9 +293,10 @@ static int ensure_solve_graph(Ctx *c, const double *Rub, const double *Rpi, doub
 // ---- results --------------------------------------------------------------------------------
 static int status_message(Ctx *c, int status) {
   if (status == HMG_OK) return HMG_OK;
-  const char *why = status == HMG_ERR_NOT_CONVERGED ? "BiCGStab did not converge"
-                    : status == HMG_ERR_BREAKDOWN  ? "BiCGStab breakdown"
-                                                   : "non-finite value in BiCGStab";
+  const std::string name = c->opt.krylov == HMG_KRYLOV_FGMRES ? "FGMRES" : "BiCGStab";
+  const std::string why = status == HMG_ERR_NOT_CONVERGED ? name + " did not converge"
+                          : status == HMG_ERR_BREAKDOWN  ? name + " breakdown"
+                                                         : "non-finite value in " + name;
   return fail(c, status, why);
 }
 
@@ -330,12 +331,14 @@ static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st) {
   c->marks.clear();
   c->ev_next = 0;
+  c->coarse_fallback = false;
+  if (c->opt.krylov == HMG_KRYLOV_FGMRES) return fgmres_solve(c, Rub, Rpi, lambda, st);
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
   int s;
-  if (c->opt.graph && !c->opt.profile) {
+  if (c->opt.graph && !c->opt.profile && !c->collect_x) {
     if ((s = ensure_solve_graph(c, Rub, Rpi, lambda))) return s;
     HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
   } else {
@@ -363,6 +366,9 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
 int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
                          const double *const *Rpi, double *const *lambda, hmg_solve_stats *st) {
   Ctx *c0 = ctxs[0];
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->opt.krylov != HMG_KRYLOV_BICGSTAB || ctxs[i]->collect_x)
+      return fail(c0, HMG_ERR_INVALID_ARG, "batched solves take BiCGStab contexts without pair collection");
   cudaGraph_t g = nullptr;
   HMG_CUDA(c0, cudaGraphCreate(&g, 0));
   int s = HMG_OK;
@@ -370,6 +376,7 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
     Ctx *c = ctxs[i];
     c->marks.clear();
     c->ev_next = 0;
+    c->coarse_fallback = false;
     s = add_solve_branch(c, g, Rub[i], Rpi[i], lambda[i]);
     if (s && c != c0) c0->err = c->err;
   }
@@ -408,6 +415,286 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
     }
   }
   return worst;
+}
+
+// ---- flexible GMRES(m) ----------------------------------------------------------------------
+// Right-preconditioned flexible GMRES (Saad 2003 Alg. 9.6) from lambda = 0: z_j = M_j^-1 v_j may
+// change from step to step (a learned coarse solve is not a fixed linear map) and the update is
+// x += Z_m y_m. The new basis vector is orthogonalised by classical Gram-Schmidt applied twice
+// (equal to modified Gram-Schmidt in exact arithmetic and as robust in practice, Giraud et al.
+// 2005), so a step costs two multi-vector dot kernels instead of j + 1 dependent reductions.
+// The Hessenberg column (j + 2 numbers) goes to the host, which holds the Givens rotations and
+// solves the small triangular system: one synchronisation per step, against a preconditioner
+// application of about a millisecond. max_iter counts steps (preconditioner applications).
+//
+// Fallback: with a learned coarse solve, two consecutive steps that each reduce the residual
+// estimate by less than the factor stall_ratio, or a step whose Hessenberg column is not
+// finite (that step is dropped and the cycle restarts), switch the coarse solve to the
+// pressure V-cycle for the rest of the solve.
+constexpr int kMaxRestart = 64;
+constexpr unsigned kGmBlocks = 608;   // blocks per dot of the multi-vector dot kernel (4 per SM)
+
+__global__ void __launch_bounds__(kRedThreads)
+    mdot_kernel(const double *__restrict__ V, int64_t n, const double *__restrict__ w, double *__restrict__ part) {
+  const double *v = V + (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(v[i], w[i], s);
+  s = warp_sum(s);
+  __shared__ double sh[kRedThreads / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kRedThreads / 32; ++q) t += sh[q];
+    part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// h[k] = the partials of dot k summed in block order (one block per k); hacc[k] += h[k]
+__global__ void mdot_finalize_kernel(const double *__restrict__ part, int nb, double *__restrict__ h,
+                                     double *__restrict__ hacc) {
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)k * nb + b];
+  s = warp_sum(s);
+  __shared__ double sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    h[k] = t;
+    if (hacc) hacc[k] += t;
+  }
+}
+
+// w += sign * sum_{k < nk} h[k] V[k]
+__global__ void __launch_bounds__(kRedThreads)
+    mcomb_kernel(double *__restrict__ w, const double *__restrict__ V, int64_t n, const double *__restrict__ h,
+                 int nk, double sign) {
+  __shared__ double hs[kMaxRestart + 1];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = sign * h[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int k = 0; k < nk; ++k) s = fma(hs[k], V[(int64_t)k * n + i], s);
+    w[i] = s;
+  }
+}
+
+// w /= sqrt(nn) (w = 0 when nn = 0); *hout = sqrt(nn)
+__global__ void gm_normalize_kernel(double *__restrict__ w, int64_t n, const double *nn, double *hout) {
+  const double s = sqrt(*nn);
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] *= inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = s;
+}
+
+// r = B - y
+__global__ void gm_sub_kernel(const double *__restrict__ B, const double *__restrict__ y, double *__restrict__ r,
+                              int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = B[i] - y[i];
+}
+
+static void dev_release(Ctx *c, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->owned.size(); ++i)
+    if (c->owned[i] == p) {
+      c->owned.erase(c->owned.begin() + (long)i);
+      break;
+    }
+  cudaFree(p);
+}
+
+static int gm_buffers(Ctx *c, int m) {
+  if (c->gm_V && c->gm_restart >= m) return HMG_OK;
+  const int64_t n = c->lv[0].ntrace;
+  dev_release(c, c->gm_V);
+  dev_release(c, c->gm_Z);
+  c->gm_V = c->gm_Z = nullptr;
+  c->gm_restart = 0;
+  int s;
+  if ((s = dev_alloc(c, &c->gm_V, (size_t)(m + 1) * n))) return s;
+  if ((s = dev_alloc(c, &c->gm_Z, (size_t)m * n))) return s;
+  if (!c->gm_h) {
+    if ((s = dev_alloc(c, &c->gm_h, (size_t)3 * (kMaxRestart + 2)))) return s;
+    if ((s = dev_alloc(c, &c->gm_part, (size_t)(kMaxRestart + 1) * kGmBlocks))) return s;
+    if ((s = dev_alloc(c, &c->gm_y, (size_t)kMaxRestart))) return s;
+  }
+  c->gm_restart = m;
+  return HMG_OK;
+}
+
+static unsigned gm_grid(int64_t n) {
+  const unsigned g = grid_for(n, kRedThreads);
+  return g < kGmBlocks ? g : kGmBlocks;
+}
+
+// h[k] = (V_k, w), k < nk (and hacc[k] += h[k])
+static int mdot(Ctx *c, const double *V, int nk, const double *w, double *h, double *hacc) {
+  const int64_t n = c->lv[0].ntrace;
+  const unsigned nb = gm_grid(n);
+  mdot_kernel<<<dim3(nb, (unsigned)nk), kRedThreads, 0, c->stream>>>(V, n, w, c->gm_part);
+  mdot_finalize_kernel<<<(unsigned)nk, 256, 0, c->stream>>>(c->gm_part, (int)nb, h, hacc);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+static int mcomb(Ctx *c, double *w, const double *V, const double *h, int nk, double sign) {
+  const int64_t n = c->lv[0].ntrace;
+  mcomb_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(w, V, n, h, nk, sign);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// v = v / ||v||, *beta_host = ||v||
+static int normalize(Ctx *c, double *v, double *nn_slot, double *h_slot, double *beta_host) {
+  const int64_t n = c->lv[0].ntrace;
+  int s;
+  if ((s = mdot(c, v, 1, v, nn_slot, nullptr))) return s;
+  gm_normalize_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(v, n, nn_slot, h_slot);
+  HMG_CUDA(c, cudaGetLastError());
+  if (beta_host) {
+    HMG_CUDA(c, cudaMemcpyAsync(beta_host, h_slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return HMG_OK;
+}
+
+int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_solve_stats *st) {
+  const int64_t n = c->lv[0].ntrace;
+  const int m = c->opt.restart;
+  const bool learned = c->opt.precond == HMG_PRECOND_NONNESTED && c->opt.coarse != HMG_COARSE_VCYCLE;
+  int s;
+  if ((s = gm_buffers(c, m))) return s;
+  double *hd = c->gm_h, *h2 = hd + (kMaxRestart + 2), *sc = h2 + (kMaxRestart + 2);
+  double *V = c->gm_V, *Z = c->gm_Z;
+  cudaEvent_t e0, e1;
+  HMG_CUDA(c, cudaEventCreate(&e0));
+  HMG_CUDA(c, cudaEventCreate(&e1));
+  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  if ((s = launch_trace_rhs(c, Rub, Rpi, c->B))) return s;
+  double beta = 0.0;
+  {
+    Prof pk(c, kCompKrylov, 6);
+    if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
+    HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+    HMG_CUDA(c, cudaMemcpyAsync(V, c->B, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = normalize(c, V, sc, sc + 1, &beta))) return s;
+  }
+  const double bnorm = beta;
+  std::vector<double> hist{bnorm > 0.0 ? 1.0 : 0.0};
+  const int kRunning = -1;
+  int status = !std::isfinite(bnorm) ? HMG_ERR_NONFINITE : (bnorm == 0.0 || 1.0 <= c->opt.tol) ? HMG_OK : kRunning;
+  if (status == kRunning && c->opt.max_iter <= 0) status = HMG_ERR_NOT_CONVERGED;
+  std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
+  int steps = 0, slow = 0;
+  double prev_rel = 1.0;
+  while (status == kRunning) {
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
+      if ((s = precond_apply(c, vj, zj))) return s;
+      if ((s = launch_spmv(c, zj, w, 0, nullptr, 0, 0))) return s;
+      {
+        Prof pk(c, kCompKrylov, 12);
+        if ((s = mdot(c, V, j + 1, w, hd, nullptr))) return s;
+        if ((s = mcomb(c, w, V, hd, j + 1, -1.0))) return s;
+        if ((s = mdot(c, V, j + 1, w, h2, hd))) return s;
+        if ((s = mcomb(c, w, V, h2, j + 1, -1.0))) return s;
+        if ((s = normalize(c, w, sc, hd + j + 1, nullptr))) return s;
+        HMG_CUDA(c, cudaMemcpyAsync(col.data(), hd, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->stream));
+        HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+      }
+      bool finite = true;
+      for (int i = 0; i <= j + 1; ++i) finite = finite && std::isfinite(col[i]);
+      if (!finite) {
+        if (learned && !c->coarse_fallback) {
+          c->coarse_fallback = true;   // drop the step, keep the cycle's first jd steps, restart
+          break;
+        }
+        status = HMG_ERR_NONFINITE;
+        break;
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      if (den == 0.0) {
+        status = HMG_ERR_BREAKDOWN;
+        break;
+      }
+      cs[j] = col[j] / den;
+      sn[j] = col[j + 1] / den;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = col[i];
+      ++steps;
+      jd = j + 1;
+      const double rel = std::fabs(g[j + 1]) / bnorm;
+      hist.push_back(rel);
+      if (learned && !c->coarse_fallback) {
+        slow = rel > c->opt.stall_ratio * prev_rel ? slow + 1 : 0;
+        if (slow >= 2) c->coarse_fallback = true;
+      }
+      prev_rel = rel;
+      if (rel <= c->opt.tol) break;
+      if (!(rel <= c->opt.divergence) || steps >= c->opt.max_iter) {
+        status = HMG_ERR_NOT_CONVERGED;
+        break;
+      }
+    }
+    // x += Z y, y = R^-1 g over the cycle's completed steps
+    if (jd > 0) {
+      for (int i = jd - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < jd; ++k) t -= Hm[(size_t)i * m + k] * y[k];
+        y[i] = t / Hm[(size_t)i * m + i];
+      }
+      Prof pk(c, kCompKrylov);
+      HMG_CUDA(c, cudaMemcpyAsync(c->gm_y, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, c->stream));
+      if ((s = mcomb(c, x, Z, c->gm_y, jd, 1.0))) return s;
+      HMG_CUDA(c, cudaStreamSynchronize(c->stream));   // y (host) is reused by the next cycle
+    }
+    if (status != kRunning) break;
+    if (hist.back() <= c->opt.tol) {
+      status = HMG_OK;
+      break;
+    }
+    // restart from the true residual
+    if ((s = launch_spmv(c, x, c->t, 0, nullptr, 0, 0))) return s;
+    {
+      Prof pk(c, kCompKrylov, 4);
+      gm_sub_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, c->t, V, n);
+      HMG_CUDA(c, cudaGetLastError());
+      if ((s = normalize(c, V, sc, sc + 1, &beta))) return s;
+    }
+    if (!std::isfinite(beta)) status = HMG_ERR_NONFINITE;
+  }
+  if ((s = solve_tail(c, x))) return s;
+  const int nh = (int)hist.size() < HMG_MAX_HISTORY ? (int)hist.size() : HMG_MAX_HISTORY;
+  if ((int)hist.size() > HMG_MAX_HISTORY) hist[HMG_MAX_HISTORY - 1] = hist.back();
+  c->state_host[kIt] = steps;
+  c->state_host[kStatus] = status;
+  c->state_host[kContinue] = 0;
+  HMG_CUDA(c, cudaMemcpyAsync(c->hist, hist.data(), sizeof(double) * nh, cudaMemcpyHostToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(int) * 3, cudaMemcpyHostToDevice, c->stream));
+  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+  HMG_CUDA(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return collect(c, st, ms);
 }
 
 }  // namespace hmg

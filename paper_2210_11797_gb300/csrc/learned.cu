@@ -1,0 +1,736 @@
+// Learned coarse-level correction: a small network f ~ H^-1 used at Algorithm 2 line 6
+// (instead of, or as the initial guess of, the pressure V-cycle), its training on the GPU
+// (forward, backward, Adam) and the collection of training pairs from the solver itself.
+// The paper has no learned component; this is the growth axis of the hot path.
+//
+// Network per column over the levels (zero padding at ground and lid), bias-free:
+//   h1 = relu(conv(1 -> 32, 3)(x)); h2 = relu(conv(32 -> 32, 3)(h1));
+//   h3 = relu(w_c h2 + w_e sum(4 edge neighbours) + w_d sum(4 corner neighbours));
+//   y  = conv(32 -> 1, 3)(h3); conv(a -> b, 3): y[o,k] = sum_i sum_d W[o,i,d] x[i,k+d-1].
+// Around it the diagonal of H scales input and output: dPi = D^-1/2 f(D^-1/2 bbar).
+// Storage: BF16 weights and activations (or FP32 for gradient checks), FP32 accumulation,
+// FP32 master weights for Adam. Parameters, flat: W1 [32][1][3], W2 [32][32][3],
+// M [32][3] (w_c, w_e, w_d), W3 [1][32][3].
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+#include "hmg_internal.cuh"
+#include "precond.cuh"
+
+namespace hmg {
+
+constexpr int kCh = 32;
+constexpr int kOffW1 = 0, kOffW2 = 96, kOffM = 96 + 3072, kOffW3 = 96 + 3072 + 96;
+constexpr int kNParams = kOffW3 + 96;   // 3360
+static_assert(kNParams == kCoarseParams, "parameter count");
+constexpr int kMaxL = 128;              // levels a column may have for the network kernels
+
+template <typename A>
+__device__ __forceinline__ float to_f(A v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename A>
+__device__ __forceinline__ A from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16(v); }
+// value as it is stored (rounded to the storage type), back in FP32
+template <typename A>
+__device__ __forceinline__ float rnd(float v) { return to_f<A>(from_f<A>(v)); }
+
+// ---- neighbour access -----------------------------------------------------------------------
+// On the mesh: edge and corner neighbours from tables. On a training patch (nx x ny columns,
+// column j*nx + i of sample s): the regular grid, -1 outside the patch (zero padding).
+struct Nbrs {
+  const int32_t *edge, *diag;   // mesh tables [ncol][4]; null on patches
+  int nx, ny;                   // patch shape
+  __device__ __forceinline__ void get(int col, int out_e[4], int out_d[4]) const {
+    if (edge) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) { out_e[s] = edge[4 * col + s]; out_d[s] = diag[4 * col + s]; }
+      return;
+    }
+    const int P = nx * ny, s0 = (col / P) * P, q = col - s0, i = q % nx, j = q / nx;
+    auto at = [&](int di, int dj) {
+      const int i2 = i + di, j2 = j + dj;
+      return (i2 >= 0 && i2 < nx && j2 >= 0 && j2 < ny) ? s0 + j2 * nx + i2 : -1;
+    };
+    out_e[0] = at(0, -1); out_e[1] = at(1, 0); out_e[2] = at(0, 1); out_e[3] = at(-1, 0);
+    out_d[0] = at(1, -1); out_d[1] = at(1, 1); out_d[2] = at(-1, 1); out_d[3] = at(-1, -1);
+  }
+};
+
+// ---- forward, column-local layers: x -> h1 -> h2 ---------------------------------------------
+// One block per CPB columns; weights and one column block of activations in shared memory.
+// x = xin[K] * xscale(K) with xscale = 1/sqrt(diag H) (mesh) or 1 (patches). Stores h2 (and h1
+// when training) in A, channel-major [32][ncells].
+template <typename A, typename Tin>
+__global__ void __launch_bounds__(128)
+    nn_front_kernel(const float *__restrict__ wts, const Tin *__restrict__ xin,
+                    const double *__restrict__ diagH, const float *__restrict__ diagH32, int ncol,
+                    int L, int cpb, A *__restrict__ h1_out, A *__restrict__ h2_out) {
+  extern __shared__ float sm[];
+  float *W1 = sm, *W2 = W1 + 96;
+  float *xs = W2 + 3072;                       // [cpb][L+2]
+  float *h1 = xs + cpb * (L + 2);              // [cpb][32][L+2]
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) W1[i] = rnd<A>(wts[kOffW1 + i]);
+  for (int i = threadIdx.x; i < 3072; i += blockDim.x) W2[i] = rnd<A>(wts[kOffW2 + i]);
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  const int64_t C = (int64_t)ncol * L;
+  for (int i = threadIdx.x; i < cpb * (L + 2); i += blockDim.x) {
+    const int cc = i / (L + 2), k = i % (L + 2) - 1;
+    float v = 0.f;
+    if (cc < nc && k >= 0 && k < L) {
+      const int64_t K = (int64_t)(c0 + cc) * L + k;
+      float s = 1.f;
+      if (diagH) s = (float)(1.0 / sqrt(diagH[K]));
+      else if (diagH32) s = rsqrtf(diagH32[K]);
+      v = rnd<A>((float)xin[K] * s);
+    }
+    xs[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cpb * kCh * (L + 2); i += blockDim.x) {
+    const int cc = i / (kCh * (L + 2)), r = i % (kCh * (L + 2)), o = r / (L + 2), k = r % (L + 2) - 1;
+    float v = 0.f;
+    if (cc < nc && k >= 0 && k < L) {
+      const float *x = xs + cc * (L + 2) + k;    // x[k-1..k+1] at x[0..2]
+      v = fmaxf(fmaf(W1[3 * o], x[0], fmaf(W1[3 * o + 1], x[1], W1[3 * o + 2] * x[2])), 0.f);
+      v = rnd<A>(v);
+      if (h1_out) h1_out[(int64_t)o * C + (int64_t)(c0 + cc) * L + k] = from_f<A>(v);
+    }
+    h1[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc * kCh * L; i += blockDim.x) {
+    const int cc = i / (kCh * L), r = i % (kCh * L), o = r / L, k = r % L;
+    const float *hb = h1 + cc * kCh * (L + 2) + k;   // channel i at hb + i*(L+2), taps 0..2
+    const float *w = W2 + o * 96;
+    float acc = 0.f;
+#pragma unroll 8
+    for (int ci = 0; ci < kCh; ++ci) {
+      const float *hc = hb + ci * (L + 2);
+      acc = fmaf(w[3 * ci], hc[0], acc);
+      acc = fmaf(w[3 * ci + 1], hc[1], acc);
+      acc = fmaf(w[3 * ci + 2], hc[2], acc);
+    }
+    h2_out[(int64_t)o * C + (int64_t)(c0 + cc) * L + k] = from_f<A>(fmaxf(acc, 0.f));
+  }
+}
+
+// ---- forward, horizontal mix and output layer: h2 -> h3 -> y ---------------------------------
+// mesh: out[K] = y * yscale(K) (yscale = 1/sqrt(diag H)) written as Tout.
+// training: also stores h3 and, for the loss, gy = 2 (y - t) / (||t_s||^2 B) and the per-block
+// sums of (y - t)^2 / ||t_s||^2 (sample s of the block's columns).
+template <typename A, typename Tout>
+__global__ void __launch_bounds__(128)
+    nn_back_kernel(const float *__restrict__ wts, const A *__restrict__ h2, Nbrs nb, int ncol, int L,
+                   int cpb, const double *__restrict__ diagH, const float *__restrict__ diagH32,
+                   Tout *__restrict__ out, A *__restrict__ h3_out, const float *__restrict__ target,
+                   const float *__restrict__ tnorm2, int patch_cols, float inv_batch,
+                   float *__restrict__ gy_out, double *__restrict__ loss_part) {
+  extern __shared__ float sm[];
+  float *Mw = sm, *W3 = Mw + 96;
+  float *h3 = W3 + 96;                          // [cpb][32][L+2]
+  __shared__ double red[4];
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) {
+    Mw[i] = rnd<A>(wts[kOffM + i]);
+    W3[i] = rnd<A>(wts[kOffW3 + i]);
+  }
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  const int64_t C = (int64_t)ncol * L;
+  __syncthreads();
+  for (int i = threadIdx.x; i < cpb * kCh * (L + 2); i += blockDim.x) {
+    const int cc = i / (kCh * (L + 2)), r = i % (kCh * (L + 2)), ch = r / (L + 2), k = r % (L + 2) - 1;
+    float v = 0.f;
+    if (cc < nc && k >= 0 && k < L) {
+      const int col = c0 + cc;
+      int e[4], d[4];
+      nb.get(col, e, d);
+      const A *hc = h2 + (int64_t)ch * C;
+      float se = 0.f, sd = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (e[s] >= 0) se += to_f<A>(hc[(int64_t)e[s] * L + k]);
+        if (d[s] >= 0) sd += to_f<A>(hc[(int64_t)d[s] * L + k]);
+      }
+      const float a = fmaf(Mw[3 * ch], to_f<A>(hc[(int64_t)col * L + k]), fmaf(Mw[3 * ch + 1], se, Mw[3 * ch + 2] * sd));
+      v = rnd<A>(fmaxf(a, 0.f));
+      if (h3_out) h3_out[(int64_t)ch * C + (int64_t)col * L + k] = from_f<A>(v);
+    }
+    h3[i] = v;
+  }
+  __syncthreads();
+  double lsum = 0.0;
+  for (int i = threadIdx.x; i < nc * L; i += blockDim.x) {
+    const int cc = i / L, k = i % L;
+    const float *hb = h3 + cc * kCh * (L + 2) + k;
+    float y = 0.f;
+#pragma unroll 8
+    for (int ch = 0; ch < kCh; ++ch) {
+      const float *hc = hb + ch * (L + 2);
+      y = fmaf(W3[3 * ch], hc[0], fmaf(W3[3 * ch + 1], hc[1], fmaf(W3[3 * ch + 2], hc[2], y)));
+    }
+    const int64_t K = (int64_t)(c0 + cc) * L + k;
+    if (out) {
+      double s = 1.0;
+      if (diagH) s = 1.0 / sqrt(diagH[K]);
+      else if (diagH32) s = (double)rsqrtf(diagH32[K]);
+      out[K] = (Tout)((double)y * s);
+    }
+    if (gy_out) {
+      const int sample = (c0 + cc) / patch_cols;
+      const float r = y - target[K];
+      const float w = 1.0f / tnorm2[sample];
+      gy_out[K] = 2.0f * r * w * inv_batch;
+      lsum += (double)(r * r * w);
+    }
+  }
+  if (loss_part) {
+    lsum = warp_sum(lsum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      loss_part[blockIdx.x] = s;
+    }
+  }
+}
+
+// ---- backward ---------------------------------------------------------------------------------
+// B3: gh3 = conv^T(W3, gy), ga3 = gh3 [h3 > 0]; partial gW3[ch][d] = sum gy[k] h3[ch][k+d-1].
+// One block per CPB columns; the partial sums of its columns go to part[block][96].
+template <typename A>
+__global__ void __launch_bounds__(128)
+    nn_bwd3_kernel(const float *__restrict__ wts, const A *__restrict__ h3, const float *__restrict__ gy,
+                   int ncol, int L, int cpb, float *__restrict__ ga3, float *__restrict__ part) {
+  extern __shared__ float sm[];
+  float *W3 = sm, *gys = W3 + 96;               // gys [cpb][L+2]
+  float *acc = gys + cpb * (L + 2);             // [96] per-block partials
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) { W3[i] = rnd<A>(wts[kOffW3 + i]); acc[i] = 0.f; }
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  const int64_t C = (int64_t)ncol * L;
+  for (int i = threadIdx.x; i < cpb * (L + 2); i += blockDim.x) {
+    const int cc = i / (L + 2), k = i % (L + 2) - 1;
+    gys[i] = (cc < nc && k >= 0 && k < L) ? gy[(int64_t)(c0 + cc) * L + k] : 0.f;
+  }
+  __syncthreads();
+  // ga3 (one thread per (column, channel, level))
+  for (int i = threadIdx.x; i < nc * kCh * L; i += blockDim.x) {
+    const int cc = i / (kCh * L), r = i % (kCh * L), ch = r / L, k = r % L;
+    const float *g = gys + cc * (L + 2) + k;    // gy[k-1..k+1] at g[0..2]
+    // y[k'] += W3[ch][d] h3[ch][k'+d-1]  =>  gh3[ch][k] = sum_d W3[ch][d] gy[k-d+1]
+    const float gh = fmaf(W3[3 * ch], g[2], fmaf(W3[3 * ch + 1], g[1], W3[3 * ch + 2] * g[0]));
+    const int64_t idx = (int64_t)ch * C + (int64_t)(c0 + cc) * L + k;
+    ga3[idx] = to_f<A>(h3[idx]) > 0.f ? gh : 0.f;
+  }
+  // gW3 partials: thread per (ch, d), loop over the block's positions
+  for (int w = threadIdx.x; w < 96; w += blockDim.x) {
+    const int ch = w / 3, d = w % 3;
+    float s = 0.f;
+    for (int cc = 0; cc < nc; ++cc)
+      for (int k = 0; k < L; ++k) {
+        const int kk = k + d - 1;
+        if (kk < 0 || kk >= L) continue;
+        s = fmaf(gys[cc * (L + 2) + k + 1], to_f<A>(h3[(int64_t)ch * C + (int64_t)(c0 + cc) * L + kk]), s);
+      }
+    acc[w] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) part[(int64_t)blockIdx.x * 96 + i] = acc[i];
+}
+
+// B2: gh2 = w_c ga3 + w_e sum(edge nbrs of ga3) + w_d sum(corner nbrs) (the neighbour relation is
+// symmetric on a patch), ga2 = gh2 [h2 > 0]; partials of gM: (ga3 . h2, ga3 . sum_e h2,
+// ga3 . sum_d h2) per channel. Thread per (column, channel) over the levels.
+template <typename A>
+__global__ void __launch_bounds__(128)
+    nn_bwd2_kernel(const float *__restrict__ wts, const A *__restrict__ h2, const float *__restrict__ ga3,
+                   Nbrs nb, int ncol, int L, int cpb, float *__restrict__ ga2, float *__restrict__ part) {
+  __shared__ float Mw[96], acc[96 * 4];
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) Mw[i] = rnd<A>(wts[kOffM + i]);
+  for (int i = threadIdx.x; i < 96 * 4; i += blockDim.x) acc[i] = 0.f;
+  __syncthreads();
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  const int64_t C = (int64_t)ncol * L;
+  // per-thread gM partials (channel, kind) accumulated, then combined through shared memory
+  for (int i = threadIdx.x; i < nc * kCh; i += blockDim.x) {
+    const int cc = i / kCh, ch = i % kCh, col = c0 + cc;
+    int e[4], d[4];
+    nb.get(col, e, d);
+    const float *g = ga3 + (int64_t)ch * C;
+    const A *h = h2 + (int64_t)ch * C;
+    float sc = 0.f, se = 0.f, sd = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float gk = g[(int64_t)col * L + k];
+      float ge = 0.f, gd = 0.f, he = 0.f, hd = 0.f;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (e[s] >= 0) { ge += g[(int64_t)e[s] * L + k]; he += to_f<A>(h[(int64_t)e[s] * L + k]); }
+        if (d[s] >= 0) { gd += g[(int64_t)d[s] * L + k]; hd += to_f<A>(h[(int64_t)d[s] * L + k]); }
+      }
+      const float hk = to_f<A>(h[(int64_t)col * L + k]);
+      const float gh = fmaf(Mw[3 * ch], gk, fmaf(Mw[3 * ch + 1], ge, Mw[3 * ch + 2] * gd));
+      ga2[(int64_t)ch * C + (int64_t)col * L + k] = hk > 0.f ? gh : 0.f;
+      sc = fmaf(gk, hk, sc);
+      se = fmaf(gk, he, se);
+      sd = fmaf(gk, hd, sd);
+    }
+    // deterministic: each (column, channel) owns one slot of acc; sum the block's columns below
+    if (cc < 4) { acc[(cc * kCh + ch) * 3 + 0] = sc; acc[(cc * kCh + ch) * 3 + 1] = se; acc[(cc * kCh + ch) * 3 + 2] = sd; }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < 96; w += blockDim.x) {
+    float s = 0.f;
+    for (int cc = 0; cc < min(nc, 4); ++cc) s += acc[cc * 96 + w];
+    part[(int64_t)blockIdx.x * 96 + w] = s;
+  }
+}
+
+// B1: gh1 = conv^T(W2, ga2), ga1 = gh1 [h1 > 0]; partials of gW2 = sum ga2[o][k] h1[i][k+d-1]
+// and gW1 = sum ga1[o][k] x[k+d-1]. One block per CPB columns; thread-owned weight slots.
+template <typename A>
+__global__ void __launch_bounds__(256)
+    nn_bwd1_kernel(const float *__restrict__ wts, const A *__restrict__ h1, const float *__restrict__ ga2,
+                   const float *__restrict__ xin, int ncol, int L, int cpb, float *__restrict__ part2,
+                   float *__restrict__ part1) {
+  extern __shared__ float sm[];
+  float *W2 = sm;                                   // [32][32][3]
+  float *g2 = W2 + 3072;                            // [32][L+2] one column of ga2
+  float *h1s = g2 + kCh * (L + 2);                  // [32][L+2]
+  float *g1 = h1s + kCh * (L + 2);                  // [32][L+2]
+  float *xs = g1 + kCh * (L + 2);                   // [L+2]
+  for (int i = threadIdx.x; i < 3072; i += blockDim.x) W2[i] = rnd<A>(wts[kOffW2 + i]);
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  const int64_t C = (int64_t)ncol * L;
+  float a2[12], a1 = 0.f;                           // thread-owned gW2 slots w = tid + 256 j
+#pragma unroll
+  for (int j = 0; j < 12; ++j) a2[j] = 0.f;
+  for (int cc = 0; cc < nc; ++cc) {
+    const int col = c0 + cc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kCh * (L + 2); i += blockDim.x) {
+      const int ch = i / (L + 2), k = i % (L + 2) - 1;
+      const bool in = k >= 0 && k < L;
+      g2[i] = in ? ga2[(int64_t)ch * C + (int64_t)col * L + k] : 0.f;
+      h1s[i] = in ? to_f<A>(h1[(int64_t)ch * C + (int64_t)col * L + k]) : 0.f;
+    }
+    for (int i = threadIdx.x; i < L + 2; i += blockDim.x) {
+      const int k = i - 1;
+      xs[i] = (k >= 0 && k < L) ? rnd<A>(xin[(int64_t)col * L + k]) : 0.f;
+    }
+    __syncthreads();
+    // ga1 = (W2^T conv ga2) [h1 > 0]
+    for (int i = threadIdx.x; i < kCh * L; i += blockDim.x) {
+      const int ci = i / L, k = i % L;
+      float s = 0.f;
+      for (int o = 0; o < kCh; ++o) {
+        const float *g = g2 + o * (L + 2) + k;     // ga2[o][k-1..k+1]
+        const float *w = W2 + o * 96 + 3 * ci;
+        s = fmaf(w[0], g[2], fmaf(w[1], g[1], fmaf(w[2], g[0], s)));
+      }
+      g1[ci * (L + 2) + k + 1] = h1s[ci * (L + 2) + k + 1] > 0.f ? s : 0.f;
+    }
+    for (int i = threadIdx.x; i < kCh; i += blockDim.x) { g1[i * (L + 2)] = 0.f; g1[i * (L + 2) + L + 1] = 0.f; }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const int w = threadIdx.x + 256 * j;        // (o, i, d)
+      const int o = w / 96, ci = (w % 96) / 3, d = w % 3;
+      float s = a2[j];
+      for (int k = 0; k < L; ++k) s = fmaf(g2[o * (L + 2) + k + 1], h1s[ci * (L + 2) + k + d], s);
+      a2[j] = s;
+    }
+    if (threadIdx.x < 96) {
+      const int o = threadIdx.x / 3, d = threadIdx.x % 3;
+      float s = a1;
+      for (int k = 0; k < L; ++k) s = fmaf(g1[o * (L + 2) + k + 1], xs[k + d], s);
+      a1 = s;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 12; ++j) part2[(int64_t)blockIdx.x * 3072 + threadIdx.x + 256 * j] = a2[j];
+  if (threadIdx.x < 96) part1[(int64_t)blockIdx.x * 96 + threadIdx.x] = a1;
+}
+
+// Sum of per-block partials [nblocks][n] into out[n] (fixed order), one thread per entry.
+__global__ void sum_partials_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * n + i];
+  out[i] = (float)s;
+}
+
+__global__ void sum_loss_kernel(const double *__restrict__ part, int n, double *out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+// Adam (Kingma & Ba 2015) with bias correction on the FP32 master weights.
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int n, float lr, float b1, float b2, float eps, int t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float mh = mi / (1.f - powf(b1, (float)t));
+  const float vh = vi / (1.f - powf(b2, (float)t));
+  w[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// per-sample ||t_s||^2 of the training targets
+__global__ void tnorm_kernel(const float *__restrict__ t, int64_t per_sample, float *__restrict__ out) {
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < per_sample; i += blockDim.x) {
+    const double v = t[(int64_t)s * per_sample + i];
+    acc += v * v;
+  }
+  acc = warp_sum(acc);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    out[s] = (float)(a > 0.0 ? a : 1.0);
+  }
+}
+
+// gather patches: out[p][q][k] = src[pair(p)][cols[p][q]][k] for x and t, then both scaled by
+// 1 / rms(x patch) (the network is positively homogeneous, so the pair stays consistent)
+__global__ void extract_patches_kernel(const float *__restrict__ xs, const float *__restrict__ ts,
+                                       int64_t ncell, const int32_t *__restrict__ pair,
+                                       const int32_t *__restrict__ cols, int P, int L,
+                                       float *__restrict__ xo, float *__restrict__ to) {
+  const int p = blockIdx.x;
+  const int64_t n = (int64_t)P * L;
+  const float *xsrc = xs + (int64_t)pair[p] * ncell, *tsrc = ts + (int64_t)pair[p] * ncell;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int q = (int)(i / L), k = (int)(i % L);
+    const float v = xsrc[(int64_t)cols[(int64_t)p * P + q] * L + k];
+    acc += (double)v * v;
+  }
+  acc = warp_sum(acc);
+  __shared__ double red[32];
+  __shared__ float scale;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    const double rms = sqrt(a / (double)n);
+    scale = rms > 0.0 ? (float)(1.0 / rms) : 1.f;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int q = (int)(i / L), k = (int)(i % L);
+    const int64_t src = (int64_t)cols[(int64_t)p * P + q] * L + k;
+    xo[(int64_t)p * n + i] = xsrc[src] * scale;
+    to[(int64_t)p * n + i] = tsrc[src] * scale;
+  }
+}
+
+// gathers the samples order[b0 .. b0+batch) of (x, t, ||t||^2) into contiguous batch buffers
+__global__ void gather_samples_kernel(const float *__restrict__ x, const float *__restrict__ t,
+                                      const float *__restrict__ tn, const int32_t *__restrict__ order,
+                                      int b0, int batch, int64_t per, float *__restrict__ xb,
+                                      float *__restrict__ tb, float *__restrict__ tnb) {
+  const int q = blockIdx.y;
+  const int64_t src = (int64_t)order[b0 + q] * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+    xb[(int64_t)q * per + i] = x[src + i];
+    tb[(int64_t)q * per + i] = t[src + i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tnb[q] = tn[order[b0 + q]];
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+static int front_smem(int cpb, int L) { return (96 + 3072 + cpb * (L + 2) + cpb * kCh * (L + 2)) * 4; }
+static int back_smem(int cpb, int L) { return (96 + 96 + cpb * kCh * (L + 2)) * 4; }
+static int bwd1_smem(int L) { return (3072 + 3 * kCh * (L + 2) + (L + 2)) * 4; }
+constexpr int kNnCpb = 4;
+
+// Allows the column-block kernels the dynamic shared memory of their largest use (128 levels).
+template <typename A, typename Tin, typename Tout>
+static int nn_attrs(Ctx *c) {
+  const int big = 200 * 1024;
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_front_kernel<A, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_back_kernel<A, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  return HMG_OK;
+}
+
+template <typename A, typename Tin, typename Tout>
+static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH, const float *dH32) {
+  const Level &f = c->lv[0];
+  const int L = f.nlev;
+  A *h2 = reinterpret_cast<A *>(c->nn_act);
+  const unsigned g = (unsigned)((f.ncol + kNnCpb - 1) / kNnCpb);
+  nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
+                                                                        kNnCpb, nullptr, h2);
+  Nbrs nb{f.col_nbr, c->nn_diag, 0, 0};
+  nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
+      c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// dPi = D^-1/2 f(D^-1/2 bbar) on the finest mesh, in the preconditioner's precision.
+template <typename T>
+int learned_coarse(Ctx *c, const T *bbar, T *out) {
+  if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
+  const double *dH = nullptr;
+  const float *dH32 = nullptr;
+  if (sizeof(T) == 8) dH = c->lv[0].H; else dH32 = c->lv[0].H32;   // row 0 of H = its diagonal
+  return nn_forward_mesh<__nv_bfloat16, T, T>(c, bbar, out, dH, dH32);
+}
+template int learned_coarse<double>(Ctx *, const double *, double *);
+template int learned_coarse<float>(Ctx *, const float *, float *);
+
+int nn_setup(Ctx *c) {
+  if (c->nn_w) return HMG_OK;
+  const Level &f = c->lv[0];
+  if (f.nlev > kMaxL) return fail(c, HMG_ERR_INVALID_ARG, "the network kernels take at most 128 levels");
+  int st;
+  if ((st = nn_attrs<__nv_bfloat16, double, double>(c))) return st;
+  if ((st = nn_attrs<__nv_bfloat16, float, float>(c))) return st;
+  if ((st = nn_attrs<float, double, double>(c))) return st;
+  if ((st = nn_attrs<float, float, float>(c))) return st;
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  if ((st = dev_alloc(c, &c->nn_w, kNParams))) return st;
+  float *tmp;
+  if ((st = dev_alloc(c, &tmp, (size_t)kCh * f.ncell))) return st;   // BF16 h2 fits in half
+  c->nn_act = tmp;
+  // corner neighbours: across face f to n, then across the face of n after the shared one
+  std::vector<int32_t> nbr(4 * (size_t)f.ncol), nbf(4 * (size_t)f.ncol), diag(4 * (size_t)f.ncol);
+  HMG_CUDA(c, cudaMemcpy(nbr.data(), f.col_nbr, nbr.size() * 4, cudaMemcpyDeviceToHost));
+  HMG_CUDA(c, cudaMemcpy(nbf.data(), f.col_nbr_face, nbf.size() * 4, cudaMemcpyDeviceToHost));
+  for (int col = 0; col < f.ncol; ++col)
+    for (int s = 0; s < 4; ++s) {
+      const int n = nbr[4 * col + s], g = (nbf[4 * col + s] + 1) & 3;
+      diag[4 * col + s] = nbr[4 * n + g];
+    }
+  if ((st = dev_alloc(c, &c->nn_diag, diag.size()))) return st;
+  HMG_CUDA(c, cudaMemcpy(c->nn_diag, diag.data(), diag.size() * 4, cudaMemcpyHostToDevice));
+  return HMG_OK;
+}
+
+// One training batch on patches: forward, loss, backward into grad [kNParams] (FP32).
+template <typename A>
+static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn, int nsamp, int nx, int ny,
+                         int L, float *grad, double *loss_dev) {
+  TrainBufs &tb = c->train;
+  const int P = nx * ny, ncol = nsamp * P;
+  const int64_t C = (int64_t)ncol * L;
+  if (C > tb.cap_cells) return fail(c, HMG_ERR_INVALID_ARG, "training batch larger than the buffers");
+  A *h1 = reinterpret_cast<A *>(tb.h1), *h2 = reinterpret_cast<A *>(tb.h2), *h3 = reinterpret_cast<A *>(tb.h3);
+  const unsigned g = (unsigned)((ncol + kNnCpb - 1) / kNnCpb);
+  Nbrs nb{nullptr, nullptr, nx, ny};
+  nn_front_kernel<A, float><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, x, nullptr, nullptr, ncol, L,
+                                                                          kNnCpb, h1, h2);
+  nn_back_kernel<A, float><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
+      c->nn_w, h2, nb, ncol, L, kNnCpb, nullptr, nullptr, nullptr, h3, t, tn, P, 1.f / (float)nsamp, tb.gy,
+      tb.loss_part);
+  sum_loss_kernel<<<1, 256, 0, c->stream>>>(tb.loss_part, (int)g, loss_dev);
+  nn_bwd3_kernel<A><<<g, 128, (96 + kNnCpb * (L + 2) + 96) * 4, c->stream>>>(c->nn_w, h3, tb.gy, ncol, L, kNnCpb,
+                                                                             tb.ga3, tb.part3);
+  nn_bwd2_kernel<A><<<g, 128, 0, c->stream>>>(c->nn_w, h2, tb.ga3, nb, ncol, L, kNnCpb, tb.ga2, tb.partM);
+  const int cpb1 = 64;
+  const unsigned g1 = (unsigned)((ncol + cpb1 - 1) / cpb1);
+  nn_bwd1_kernel<A><<<g1, 256, bwd1_smem(L), c->stream>>>(c->nn_w, h1, tb.ga2, x, ncol, L, cpb1, tb.part2, tb.part1);
+  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.part1, (int)g1, 96, grad + kOffW1);
+  sum_partials_kernel<<<grid_for(3072, 256), 256, 0, c->stream>>>(tb.part2, (int)g1, 3072, grad + kOffW2);
+  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.partM, (int)g, 96, grad + kOffM);
+  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.part3, (int)g, 96, grad + kOffW3);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+int train_buffers(Ctx *c, int64_t cells, int nblocks_max) {
+  TrainBufs &tb = c->train;
+  if (tb.cap_cells >= cells) return HMG_OK;
+  int st;
+  float *f;
+  // storage for FP32 activations (BF16 uses half of it)
+  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h1 = f;
+  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h2 = f;
+  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h3 = f;
+  if ((st = dev_alloc(c, &tb.ga3, (size_t)kCh * cells))) return st;
+  if ((st = dev_alloc(c, &tb.ga2, (size_t)kCh * cells))) return st;
+  if ((st = dev_alloc(c, &tb.gy, (size_t)cells))) return st;
+  if ((st = dev_alloc(c, &tb.loss_part, (size_t)nblocks_max))) return st;
+  if ((st = dev_alloc(c, &tb.part3, (size_t)nblocks_max * 96))) return st;
+  if ((st = dev_alloc(c, &tb.partM, (size_t)nblocks_max * 96))) return st;
+  if ((st = dev_alloc(c, &tb.part2, (size_t)nblocks_max * 3072))) return st;
+  if ((st = dev_alloc(c, &tb.part1, (size_t)nblocks_max * 96))) return st;
+  if ((st = dev_alloc(c, &tb.grad, (size_t)kNParams))) return st;
+  if ((st = dev_alloc(c, &tb.m, (size_t)kNParams))) return st;
+  if ((st = dev_alloc(c, &tb.v, (size_t)kNParams))) return st;
+  if ((st = dev_alloc(c, &tb.loss, 1))) return st;
+  if ((st = dev_alloc(c, &tb.tn, (size_t)1))) return st;
+  tb.cap_cells = cells;
+  return HMG_OK;
+}
+
+int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int fp32,
+                      float *grad_host, double *loss_host) {
+  const int L = c->lv[0].nlev;
+  const int64_t cells = (int64_t)nsamp * nx * ny * L;
+  int st;
+  if ((st = nn_setup(c))) return st;
+  if ((st = train_buffers(c, cells, (int)(nsamp * nx * ny + kNnCpb - 1) / kNnCpb + 1))) return st;
+  float *tn;
+  if ((st = dev_alloc(c, &tn, (size_t)nsamp))) return st;
+  tnorm_kernel<<<nsamp, 256, 0, c->stream>>>(t, (int64_t)nx * ny * L, tn);
+  if (fp32) st = nn_batch_grad<float>(c, x, t, tn, nsamp, nx, ny, L, c->train.grad, c->train.loss);
+  else st = nn_batch_grad<__nv_bfloat16>(c, x, t, tn, nsamp, nx, ny, L, c->train.grad, c->train.loss);
+  if (st) return st;
+  HMG_CUDA(c, cudaMemcpyAsync(grad_host, c->train.grad, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(loss_host, c->train.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) for the epoch shuffles of the training samples.
+static uint64_t splitmix64_next(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int batch, int epochs,
+                       double lr, uint64_t seed, double *loss_hist) {
+  const int L = c->lv[0].nlev, P = nx * ny;
+  const int64_t per = (int64_t)P * L;
+  int st;
+  if ((st = nn_setup(c))) return st;
+  if (batch < 1 || batch > nsamp) return fail(c, HMG_ERR_INVALID_ARG, "bad batch size");
+  if ((st = train_buffers(c, (int64_t)batch * per, (batch * P + kNnCpb - 1) / kNnCpb + 1))) return st;
+  float *tn_all, *xb, *tb_, *tnb;
+  int32_t *order_dev;
+  if ((st = dev_alloc(c, &tn_all, (size_t)nsamp))) return st;
+  if ((st = dev_alloc(c, &xb, (size_t)batch * per))) return st;
+  if ((st = dev_alloc(c, &tb_, (size_t)batch * per))) return st;
+  if ((st = dev_alloc(c, &tnb, (size_t)batch))) return st;
+  if ((st = dev_alloc(c, &order_dev, (size_t)nsamp))) return st;
+  tnorm_kernel<<<nsamp, 256, 0, c->stream>>>(t, per, tn_all);
+  HMG_CUDA(c, cudaMemsetAsync(c->train.m, 0, sizeof(float) * kNParams, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(c->train.v, 0, sizeof(float) * kNParams, c->stream));
+  std::vector<int32_t> order(nsamp);
+  uint64_t s = seed;
+  int step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = 0; i < nsamp; ++i) order[i] = i;
+    for (int i = nsamp - 1; i > 0; --i) {           // Fisher-Yates
+      const int j = (int)(splitmix64_next(s) % (uint64_t)(i + 1));
+      std::swap(order[i], order[j]);
+    }
+    HMG_CUDA(c, cudaMemcpyAsync(order_dev, order.data(), sizeof(int32_t) * nsamp, cudaMemcpyHostToDevice, c->stream));
+    double ep_loss = 0.0;
+    int nb = 0;
+    for (int b0 = 0; b0 + batch <= nsamp; b0 += batch) {
+      gather_samples_kernel<<<dim3(grid_for(per, 256) < 64 ? grid_for(per, 256) : 64, batch), 256, 0, c->stream>>>(
+          x, t, tn_all, order_dev, b0, batch, per, xb, tb_, tnb);
+      if ((st = nn_batch_grad<__nv_bfloat16>(c, xb, tb_, tnb, batch, nx, ny, L, c->train.grad, c->train.loss))) return st;
+      ++step;
+      adam_kernel<<<grid_for(kNParams, 256), 256, 0, c->stream>>>(c->nn_w, c->train.grad, c->train.m, c->train.v,
+                                                                  kNParams, (float)lr, 0.9f, 0.999f, 1e-8f, step);
+      double l = 0.0;
+      HMG_CUDA(c, cudaMemcpyAsync(&l, c->train.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+      ep_loss += l / batch;
+      ++nb;
+    }
+    if (loss_hist) loss_hist[ep] = nb ? ep_loss / nb : 0.0;
+  }
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
+int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, const int32_t *pair,
+                    const int32_t *cols, int npatch, int P, float *xo, float *to) {
+  extract_patches_kernel<<<npatch, 256, 0, c->stream>>>(xs, ts, ncell, pair, cols, P, c->lv[0].nlev, xo, to);
+  HMG_CUDA(c, cudaGetLastError());
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
+int apply_coarse_model(Ctx *c, const double *bbar, double *out, int fp32) {
+  int st = nn_setup(c);
+  if (st) return st;
+  if (fp32) return nn_forward_mesh<float, double, double>(c, bbar, out, c->lv[0].H, nullptr);
+  return nn_forward_mesh<__nv_bfloat16, double, double>(c, bbar, out, c->lv[0].H, nullptr);
+}
+
+// ---- training pairs from the solver itself -----------------------------------------------------
+// out = v D^(+-1/2) in FP32 (up: D^1/2, else D^-1/2)
+__global__ void scale_to_float_kernel(const double *__restrict__ v, const double *__restrict__ diagH, bool up,
+                                      float *__restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)(up ? v[i] * sqrt(diagH[i]) : v[i] / sqrt(diagH[i]));
+}
+
+__global__ void add_kernel(double *__restrict__ x, const double *__restrict__ e, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += e[i];
+}
+
+// For the current preconditioner call: x = D^-1/2 bbar and t = D^1/2 H^-1 bbar, with H^-1 bbar
+// from pressure-multigrid V-cycles iterated until ||bbar - H y|| <= 1e-12 ||bbar|| (at most 80).
+int collect_pair(Ctx *c, const double *bbar) {
+  if (c->collect_n >= c->collect_max) return HMG_OK;
+  const Level &f = c->lv[0];
+  const int64_t C = f.ncell;
+  int st;
+  if (!c->collect_r) {
+    if ((st = dev_alloc(c, &c->collect_r, (size_t)C))) return st;
+    if ((st = dev_alloc(c, &c->collect_y, (size_t)C))) return st;
+  }
+  const double *dH = f.H;   // row 0 of H: its diagonal
+  scale_to_float_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(bbar, dH, false, c->collect_x + c->collect_n * C, C);
+  HMG_CUDA(c, cudaMemsetAsync(c->collect_y, 0, sizeof(double) * C, c->stream));
+  if ((st = launch_dot(c, bbar, bbar, C, 10))) return st;
+  double bb = 0.0;
+  HMG_CUDA(c, cudaMemcpyAsync(&bb, c->scal + 10, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int it = 0; it < 80 && bb > 0.0; ++it) {
+    if ((st = pressure_residual_fp64(c, 0, bbar, c->collect_y, c->collect_r))) return st;
+    if ((st = launch_dot(c, c->collect_r, c->collect_r, C, 11))) return st;
+    double rr = 0.0;
+    HMG_CUDA(c, cudaMemcpyAsync(&rr, c->scal + 11, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (rr <= 1e-24 * bb) break;
+    double *e = nullptr;
+    if ((st = vcycle<double>(c, c->collect_r, &e))) return st;
+    add_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(c->collect_y, e, C);
+  }
+  scale_to_float_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(c->collect_y, dH, true, c->collect_t + c->collect_n * C, C);
+  HMG_CUDA(c, cudaGetLastError());
+  ++c->collect_n;
+  return HMG_OK;
+}
+
+}  // namespace hmg

@@ -8,8 +8,9 @@ namespace hmg {
 // One pressure-multigrid V-cycle for H_0 x = b from a zero initial guess (Sec. 2.3), in
 // precision T (double: FP64 operator; float: the FP32 copies). b [ncell] in T. On return
 // *x points at the level-0 work vector holding the result (valid until the next V-cycle).
+// With x0, the finest level starts from x0 instead of zero (its first sweep smooths x0).
 template <typename T>
-int vcycle(Ctx *c, const T *b, T **x);
+int vcycle(Ctx *c, const T *b, T **x, const T *x0 = nullptr);
 
 template <typename T>
 struct Prec;

@@ -111,6 +111,15 @@ __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict_
 }
 
 template <typename T>
+__global__ void mg_residual_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ b,
+                                   const T *__restrict__ x, T *__restrict__ r) {
+  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (K >= a.ncell) return;
+  const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
+  r[K] = h_apply<T, 1, true>(H, x, nullptr, a, c, k, b[K]);
+}
+
+template <typename T>
 __global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ x,
                                 T *__restrict__ y) {
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -169,13 +178,16 @@ int time_mg_cpb(Ctx *c, int l, int cpb, float *ms) {
   return st;
 }
 
-// n sweeps on level l from zero (n >= 1); the result ends in *cur (one of lv.vx / lv.vy).
+// n sweeps on level l from zero, or from x0 (n >= 1); the result ends in *cur (one of
+// lv.vx / lv.vy; x0 must be neither).
 template <typename T>
-static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur) {
+static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur, const T *x0 = nullptr) {
   Level &lv = c->lv[l];
   T *x = static_cast<T *>(lv.vx), *y = static_cast<T *>(lv.vy);
   int st;
-  if ((st = smooth<T, 0>(c, l, b, nullptr, nullptr, x))) return st;
+  if (x0) st = smooth<T, 1>(c, l, b, x0, nullptr, x);
+  else st = smooth<T, 0>(c, l, b, nullptr, nullptr, x);
+  if (st) return st;
   for (int i = 1; i < n; ++i) {
     if ((st = smooth<T, 1>(c, l, b, x, nullptr, y))) return st;
     T *t = x; x = y; y = t;
@@ -185,14 +197,14 @@ static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur) {
 }
 
 template <typename T>
-int vcycle(Ctx *c, const T *b0, T **x_out) {
+int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
   const int nmg = c->nmg;
   const T *b[kMaxLevels];
   T *x[kMaxLevels];
   int st;
   b[0] = b0;
   for (int l = 0; l < nmg - 1; ++l) {
-    if ((st = sweeps_from_zero<T>(c, l, b[l], c->opt.mg_npre, &x[l]))) return st;
+    if ((st = sweeps_from_zero<T>(c, l, b[l], c->opt.mg_npre, &x[l], l == 0 ? x0 : nullptr))) return st;
     const Level &coarse = c->lv[l + 1];
     MGArgs a = mg_args(c, l);
     T *bc = static_cast<T *>(coarse.vb);
@@ -202,7 +214,7 @@ int vcycle(Ctx *c, const T *b0, T **x_out) {
     b[l + 1] = bc;
   }
   const int lc = nmg - 1;
-  if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc]))) return st;
+  if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc], lc == 0 ? x0 : nullptr))) return st;
   // options are validated to mg_npre >= 1 and mg_npost >= 1
   for (int l = nmg - 2; l >= 0; --l) {
     Level &lv = c->lv[l];
@@ -219,8 +231,8 @@ int vcycle(Ctx *c, const T *b0, T **x_out) {
   return HMG_OK;
 }
 
-template int vcycle<double>(Ctx *, const double *, double **);
-template int vcycle<float>(Ctx *, const float *, float **);
+template int vcycle<double>(Ctx *, const double *, double **, const double *);
+template int vcycle<float>(Ctx *, const float *, float **, const float *);
 
 int pressure_vcycle_fp64(Ctx *c, const double *b, double *x) {
   double *res = nullptr;
@@ -228,6 +240,14 @@ int pressure_vcycle_fp64(Ctx *c, const double *b, double *x) {
   if (st) return st;
   HMG_CUDA(c, cudaMemcpyAsync(x, res, sizeof(double) * c->lv[0].ncell, cudaMemcpyDeviceToDevice,
                               c->stream));
+  return HMG_OK;
+}
+
+int pressure_residual_fp64(Ctx *c, int l, const double *b, const double *x, double *r) {
+  const Level &lv = c->lv[l];
+  MGArgs a = mg_args(c, l);
+  mg_residual_kernel<double><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(a, lv.H, b, x, r);
+  HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
 

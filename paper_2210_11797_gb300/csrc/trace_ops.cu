@@ -377,12 +377,24 @@ static int two_level(Ctx *c, const double *r, double *z) {
                                                                       f.ncell, f.col_edges);
   }
   HMG_CUDA(c, cudaGetLastError());
-  // line 6: one V-cycle of the pressure multigrid
+  // (training pairs for the learned coarse solve, FP64 path only)
+  if (c->collect_x && sizeof(T) == 8 && (st = collect_pair(c, reinterpret_cast<const double *>(cb)))) return st;
+  // line 6: the coarse solve H dPi = bbar: one V-cycle of the pressure multigrid, the learned
+  // model, or the model's output as the V-cycle's initial guess
   T *dpi = nullptr;
   {
     const int nl = c->nmg - 1;
     Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * c->opt.mg_npost);
-    if ((st = vcycle<T>(c, cb, &dpi))) return st;
+    const bool learned = c->opt.coarse != HMG_COARSE_VCYCLE && !c->coarse_fallback;
+    if (learned && c->opt.coarse == HMG_COARSE_LEARNED) {
+      dpi = w3;
+      if ((st = learned_coarse<T>(c, cb, dpi))) return st;
+    } else if (learned) {
+      if ((st = learned_coarse<T>(c, cb, w3))) return st;
+      if ((st = vcycle<T>(c, cb, &dpi, w3))) return st;
+    } else {
+      if ((st = vcycle<T>(c, cb, &dpi))) return st;
+    }
   }
   // line 7: lambda += P dPi
   {

@@ -21,6 +21,9 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "not_ready", 4: "not_co
                 5: "breakdown", 6: "nonfinite", 7: "timeout", 8: "out_of_memory"}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "linesmooth": 1, "nonnested": 2}
+COARSE = {"vcycle": 0, "learned": 1, "learned_vcycle": 2}
+KRYLOV = {"bicgstab": 0, "fgmres": 1}
+_NAMED = {"precision": PRECISION, "precond": PRECOND, "coarse": COARSE, "krylov": KRYLOV}
 MAX_HISTORY = 512
 NCOMP = 8
 COMPONENTS = ["trace_rhs", "trace_apply", "presmooth", "line_sweep", "residual_restrict",
@@ -55,7 +58,9 @@ class Options(C.Structure):
                 ("n_post", C.c_int32), ("n_smooth", C.c_int32), ("omega", C.c_double),
                 ("mg_npre", C.c_int32), ("mg_npost", C.c_int32), ("mg_ncoarse", C.c_int32),
                 ("mg_omega", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32)]
+                ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
+                ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
+                ("stall_ratio", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -100,6 +105,17 @@ _SIGS = {
     "hmg_solve_batched": ([C.POINTER(_P), C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                            C.POINTER(SolveStats)], C.c_int),
     "hmg_autotune": ([_P], C.c_int),
+    "hmg_coarse_model_size": ([], C.c_int32),
+    "hmg_set_coarse_model": ([_P, _P, C.c_int32], C.c_int),
+    "hmg_get_coarse_model": ([_P, _P, C.c_int32], C.c_int),
+    "hmg_apply_coarse_model": ([_P, _P, _P, C.c_int32], C.c_int),
+    "hmg_coarse_model_grad": ([_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P,
+                               C.POINTER(C.c_double)], C.c_int),
+    "hmg_train_coarse_model": ([_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                C.c_double, C.c_uint64, _P], C.c_int),
+    "hmg_collect_coarse_pairs": ([_P, _P, _P, _P, C.c_int32, _P, _P, C.POINTER(C.c_int32),
+                                  C.POINTER(SolveStats)], C.c_int),
+    "hmg_extract_patches": ([_P, _P, _P, C.c_int32, _P, _P, C.c_int32, C.c_int32, _P, _P], C.c_int),
 }
 
 
@@ -125,7 +141,7 @@ def header_symbols():
     import re
     path = os.path.join(_build.INCLUDE, "hmg.h")
     src = open(path).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(hmg_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int32_t|void|const char \*)\s*(hmg_\w+)\s*\(", src, re.M)))
 
 
 def lib():
@@ -155,15 +171,15 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _option_value(k, v):
+    return _NAMED[k][v] if k in _NAMED and isinstance(v, str) else v
+
+
 def default_options(**kw) -> Options:
     o = Options()
     lib().hmg_default_options(C.byref(o))
     for k, v in kw.items():
-        if k == "precision" and isinstance(v, str):
-            v = PRECISION[v]
-        if k == "precond" and isinstance(v, str):
-            v = PRECOND[v]
-        setattr(o, k, v)
+        setattr(o, k, _option_value(k, v))
     return o
 
 
@@ -206,6 +222,7 @@ class Solver:
             lv.parent = self._arr(hier.parents[l], np.int32) if l + 1 < hier.nmg else None
         _check(self.ctx, lib().hmg_set_mesh(self.ctx, hier.nmg, levels))
         self.nmg = hier.nmg
+        self.ncol, self.nlev = hier.meshes[0].ncol, hier.meshes[0].nlev
         self.level_cells = [m.ncell for m in hier.meshes]
 
     def _set_coefficients(self, co):
@@ -231,11 +248,7 @@ class Solver:
 
     def set_options(self, **kw):
         for k, v in kw.items():
-            if k == "precision" and isinstance(v, str):
-                v = PRECISION[v]
-            if k == "precond" and isinstance(v, str):
-                v = PRECOND[v]
-            setattr(self.opts, k, v)
+            setattr(self.opts, k, _option_value(k, v))
         _check(self.ctx, lib().hmg_set_options(self.ctx, C.byref(self.opts)))
         if self.opts.precision == PRECISION["mixed"]:
             _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
@@ -314,6 +327,75 @@ class Solver:
         out = self.torch.empty((11, self.ntrace), dtype=self.torch.float64, device=self.device)
         _check(self.ctx, lib().hmg_get_trace_operator(self.ctx, _ptr(out)))
         return out
+
+    # -- learned coarse correction ----------------------------------------------------------
+    def _f32(self, t, name):
+        torch = self.torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError(f"{name}: expected a contiguous float32 CUDA tensor")
+        return _ptr(t)
+
+    def set_coarse_model(self, params):
+        p = np.ascontiguousarray(params, np.float32).ravel()
+        _check(self.ctx, lib().hmg_set_coarse_model(self.ctx, p.ctypes.data_as(C.c_void_p), p.size))
+
+    def get_coarse_model(self):
+        p = np.empty(lib().hmg_coarse_model_size(), np.float32)
+        _check(self.ctx, lib().hmg_get_coarse_model(self.ctx, p.ctypes.data_as(C.c_void_p), p.size))
+        return p
+
+    def apply_coarse_model(self, bbar, fp32=False):
+        out = self._empty(self.ncell)
+        _check(self.ctx, lib().hmg_apply_coarse_model(self.ctx, self._dev(bbar, self.ncell, "bbar"), _ptr(out),
+                                                      1 if fp32 else 0))
+        return out
+
+    def _patches(self, x, t, nx, ny):
+        if x.shape != t.shape or x.ndim != 3 or x.shape[1] != nx * ny:
+            raise ValueError("x, t: expected [nsamp, nx*ny, nlev]")
+        return self._f32(x, "x"), self._f32(t, "t"), x.shape[0]
+
+    def coarse_model_grad(self, x, t, nx, ny, fp32=False):
+        px, pt, ns = self._patches(x, t, nx, ny)
+        g = np.empty(lib().hmg_coarse_model_size(), np.float32)
+        loss = C.c_double()
+        _check(self.ctx, lib().hmg_coarse_model_grad(self.ctx, px, pt, ns, nx, ny, 1 if fp32 else 0,
+                                                     g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return loss.value, g
+
+    def train_coarse_model(self, x, t, nx, ny, batch, epochs, lr, seed=0):
+        px, pt, ns = self._patches(x, t, nx, ny)
+        hist = np.zeros(max(epochs, 1))
+        _check(self.ctx, lib().hmg_train_coarse_model(self.ctx, px, pt, ns, nx, ny, batch, epochs, lr, seed,
+                                                      hist.ctypes.data_as(C.c_void_p)))
+        return hist[:epochs]
+
+    def collect_coarse_pairs(self, Rub, Rpi, max_pairs, check=True):
+        torch = self.torch
+        xs = torch.empty((max_pairs, self.ncell), dtype=torch.float32, device=self.device)
+        ts = torch.empty_like(xs)
+        lam = self._empty(self.ntrace)
+        n = C.c_int32()
+        st = SolveStats()
+        rc = lib().hmg_collect_coarse_pairs(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"),
+                                            self._dev(Rpi, self.ncell, "Rpi"), _ptr(lam), max_pairs,
+                                            _ptr(xs), _ptr(ts), C.byref(n), C.byref(st))
+        if check:
+            _check(self.ctx, rc)
+        return xs[: n.value], ts[: n.value], lam, st.as_dict()
+
+    def extract_patches(self, xs, ts, pair, cols):
+        """pair [npatch], cols [npatch, P] (int32 CUDA tensors) -> x, t [npatch, P, nlev]."""
+        torch = self.torch
+        npatch, P = cols.shape
+        xo = torch.empty((npatch, P, self.nlev), dtype=torch.float32, device=self.device)
+        to = torch.empty_like(xo)
+        for a, nm in ((pair, "pair"), (cols, "cols")):
+            if not (a.is_cuda and a.dtype == torch.int32 and a.is_contiguous()):
+                raise TypeError(f"{nm}: expected a contiguous int32 CUDA tensor")
+        _check(self.ctx, lib().hmg_extract_patches(self.ctx, self._f32(xs, "xs"), self._f32(ts, "ts"), xs.shape[0],
+                                                   _ptr(pair), _ptr(cols), npatch, P, _ptr(xo), _ptr(to)))
+        return xo, to
 
     def close(self):
         if self.ctx:

@@ -52,4 +52,26 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hmg.Background) == 3 * 8
     assert ctypes.sizeof(hmg.Scalars) == 6 * 8 + 8 + 8
     assert ctypes.sizeof(hmg.SolveStats) == 4 + 4 + 3 * 8 + 8 + hmg.MAX_HISTORY * 8 + 8 * 8 + 8 * 4
-    assert ctypes.sizeof(hmg.Options) == 8 * 4 + 3 * 8 + 4 * 4 + 8 + 4 + 4
+    assert ctypes.sizeof(hmg.Options) == 112
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every field offset of the ctypes mirrors equals the C compiler's offsetof."""
+    structs = {"hmg_mesh_level": hmg.MeshLevel, "hmg_background": hmg.Background,
+               "hmg_scalars": hmg.Scalars, "hmg_options": hmg.Options, "hmg_solve_stats": hmg.SolveStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hmg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, field, value = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if field == "sizeof" else getattr(py, field).offset
+        assert got == int(value), (cname, field, got, value)

@@ -1,0 +1,217 @@
+"""The learned coarse correction on the GPU (through the C ABI) against the oracle: the
+network's forward map on the mesh, its gradient on training patches, training with Adam,
+flexible GMRES, and the coarse modes of Algorithm 2 line 6 inside whole solves.
+
+Tolerances:
+* FP32 network (fp32 = 1): FP32 storage and accumulation of at most 3 x 32 + 9 products per
+  output of a layer, four layers: a few hundred FP32 roundings (u = 6e-8) relative to the
+  magnitudes summed, so 1e-4 relative to the output's max norm (and to the gradient's);
+* BF16 network (the solver's): weights and activations rounded to BF16 (u = 3.9e-3) at
+  every layer, so 5e-2 in relative 2-norm;
+* flexible GMRES against the oracle's, both converged to 1e-12 with the same FP64
+  preconditioner: relative 2-norm difference < 1e-9, as for BiCGStab.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import learned as N
+from oracle.nonnested import HybridSolver
+from paper_2210_11797_gb300 import inputs as I
+
+
+def _cuda(a, dtype=np.float64):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+_CACHE = {}
+
+
+def _setup(name):
+    if name not in _CACHE:
+        from paper_2210_11797_gb300.hmg import Solver
+        w = {"planar16": lambda: I.planar_helmholtz(),
+             "sphereC12L30": lambda: I.cubed_sphere(12, 30)}[name]()
+        ora = HybridSolver(w.hier, w.coeffs)
+        gpu = Solver(w.hier, w.coeffs, tol=w.tol)
+        _CACHE[name] = (w, ora, gpu)
+    w, ora, gpu = _CACHE[name]
+    gpu.set_options(tol=w.tol, krylov="bicgstab", coarse="vcycle", restart=30, max_iter=200,
+                    stall_ratio=0.9, graph=1)
+    return w, ora, gpu
+
+
+def _rounded(params):
+    """The FP32 weights the library holds, back in FP64."""
+    return I.unflatten_coarse_model(I.flatten_coarse_model(params))
+
+
+def _oracle_coarse_model(ora, params):
+    mesh = ora.mesh
+    d = ora.mg.H[0].diagonal()
+    edge, diag = N.mesh_neighbours(mesh)
+
+    def apply(bbar):
+        x = (bbar / np.sqrt(d)).reshape(mesh.ncol, mesh.nlev)
+        return N.forward(params, x, edge, diag).reshape(-1) / np.sqrt(d)
+    return apply
+
+
+@pytest.mark.parametrize("name", ["planar16", "sphereC12L30"])
+def test_forward_matches_oracle(name):
+    _w, ora, gpu = _setup(name)
+    params = I.coarse_model_init(5)
+    gpu.set_coarse_model(I.flatten_coarse_model(params))
+    b = I.normal(11, gpu.ncell)
+    ref = _oracle_coarse_model(ora, _rounded(params))(b)
+    out32 = _np(gpu.apply_coarse_model(_cuda(b), fp32=True))
+    assert np.abs(out32 - ref).max() / np.abs(ref).max() < 1e-4
+    out16 = _np(gpu.apply_coarse_model(_cuda(b), fp32=False))
+    assert np.linalg.norm(out16 - ref) / np.linalg.norm(ref) < 5e-2
+    # the model round-trips through the ABI unchanged
+    np.testing.assert_array_equal(gpu.get_coarse_model(), I.flatten_coarse_model(params))
+
+
+def test_gradient_matches_oracle():
+    _w, _ora, gpu = _setup("planar16")
+    params = I.coarse_model_init(7)
+    gpu.set_coarse_model(I.flatten_coarse_model(params))
+    p = _rounded(params)
+    nx, ny, ns, L = 5, 4, 3, gpu.nlev
+    x = I.normal(21, ns * nx * ny * L).reshape(ns, nx * ny, L).astype(np.float32)
+    t = I.normal(22, ns * nx * ny * L).reshape(ns, nx * ny, L).astype(np.float32)
+    edge, diag = N.grid_neighbours(nx, ny)
+    loss_ref, g_ref = 0.0, {k: 0.0 for k in p}
+    for s in range(ns):
+        l, g = N.loss_and_grad(p, x[s].astype(np.float64), t[s].astype(np.float64), edge, diag)
+        loss_ref += l / ns
+        for k in g:
+            g_ref[k] = g_ref[k] + g[k] / ns
+    loss, g = gpu.coarse_model_grad(_cuda(x, np.float32), _cuda(t, np.float32), nx, ny, fp32=True)
+    assert abs(loss - loss_ref) / loss_ref < 1e-5
+    gd = I.unflatten_coarse_model(g)
+    for k in g_ref:
+        err = np.abs(gd[k] - g_ref[k]).max() / np.abs(g_ref[k]).max()
+        assert err < 1e-4, (k, err)
+    # BF16 storage: same direction, a few per cent off
+    _l16, g16 = gpu.coarse_model_grad(_cuda(x, np.float32), _cuda(t, np.float32), nx, ny, fp32=False)
+    gf = I.flatten_coarse_model(g_ref).astype(np.float64)
+    cos = g16 @ gf / (np.linalg.norm(g16) * np.linalg.norm(gf))
+    assert cos > 0.99
+
+
+def _pairs_and_patches(gpu, w, npairs, nx, stride):
+    xs, ts, _lam, st = gpu.collect_coarse_pairs(_cuda(w.Rub), _cuda(w.Rpi), npairs)
+    assert st["status"] == "ok" and xs.shape[0] == npairs
+    m = w.hier.meshes[0]
+    npanel = 1 if m.geometry == 0 else 6
+    n = int(round(np.sqrt(m.ncol / npanel)))
+    cols = I.panel_patch_columns(n, npanel, nx, nx, stride)
+    pair = np.repeat(np.arange(npairs, dtype=np.int32), len(cols))
+    allcols = np.tile(cols, (npairs, 1))
+    xo, to = gpu.extract_patches(xs, ts, _cuda(pair, np.int32), _cuda(allcols, np.int32))
+    return xs, ts, xo, to
+
+
+def test_collected_pairs_are_coarse_solves():
+    """t = D^1/2 H^-1 bbar for x = D^-1/2 bbar: H (D^-1/2 t) = D^1/2 x to FP32 accuracy."""
+    w, ora, gpu = _setup("planar16")
+    xs, ts, _xo, _to = _pairs_and_patches(gpu, w, 4, 8, 8)
+    d = ora.mg.H[0].diagonal()
+    H = ora.mg.H[0]
+    for q in range(xs.shape[0]):
+        x, t = _np(xs[q]), _np(ts[q])
+        lhs = H @ (t / np.sqrt(d))
+        rhs = x * np.sqrt(d)
+        assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-5
+
+
+def test_training_reduces_the_loss():
+    w, _ora, gpu = _setup("planar16")
+    gpu.set_coarse_model(I.flatten_coarse_model(I.coarse_model_init(0)))
+    _xs, _ts, xo, to = _pairs_and_patches(gpu, w, 16, 8, 4)
+    hist = gpu.train_coarse_model(xo, to, 8, 8, batch=16, epochs=30, lr=3e-3, seed=1)
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 0.7 * hist[0], hist
+    # the trained model generalises to pairs of another right-hand side
+    w2 = I.planar_helmholtz(seed=9)
+    _a, _b, xo2, to2 = _pairs_and_patches(gpu, w2, 4, 8, 8)
+    trained, _g = gpu.coarse_model_grad(xo2, to2, 8, 8)
+    gpu.set_coarse_model(I.flatten_coarse_model(I.coarse_model_init(0)))
+    initial, _g = gpu.coarse_model_grad(xo2, to2, 8, 8)
+    assert trained < 0.8 * initial
+
+
+@pytest.mark.parametrize("name", ["planar16", "sphereC12L30"])
+def test_fgmres_matches_oracle(name):
+    w, ora, gpu = _setup(name)
+    gpu.set_options(krylov="fgmres", tol=1e-12, restart=30, max_iter=300)
+    lam, st = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-11
+    B = ora.rhs(w.Rub, w.Rpi)
+    ref, hist, status = N.fgmres(lambda v: ora.S @ v, B, lambda v, _k: ora.precond(v), 1e-12, restart=30,
+                                 maxit=300)
+    assert status == "ok"
+    assert abs(st["iterations"] - (len(hist) - 1)) <= 1
+    np.testing.assert_allclose(st["history"][:5], hist[:5], rtol=1e-6)
+    assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-9
+
+
+@pytest.mark.parametrize("coarse", ["learned", "learned_vcycle"])
+def test_learned_coarse_solve_matches_oracle_solution(coarse):
+    w, ora, gpu = _setup("sphereC12L30")
+    params = I.coarse_model_init(3)
+    gpu.set_coarse_model(I.flatten_coarse_model(params))
+    gpu.set_options(krylov="fgmres", coarse=coarse, tol=1e-10, max_iter=400)
+    lam, st = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9
+    # the oracle's flexible GMRES with the oracle network at the same place of Algorithm 2
+    model = _oracle_coarse_model(ora, _rounded(params))
+    if coarse == "learned":
+        ora.coarse_solve = model
+    else:
+        ora.coarse_solve = lambda b: ora.mg.vcycle(b, x0=model(b))
+    try:
+        B = ora.rhs(w.Rub, w.Rpi)
+        ref, _h, status = N.fgmres(lambda v: ora.S @ v, B, lambda v, _k: ora.precond(v), 1e-10, restart=30,
+                                   maxit=400)
+    finally:
+        del ora.coarse_solve
+    assert status == "ok"
+    assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-7
+
+
+def test_corrupted_model_falls_back_to_the_vcycle():
+    """NaN weights: the first flexible step is not finite, is dropped, and the solve finishes
+    with the pressure V-cycle as coarse solve (the same answer as the plain configuration)."""
+    w, _ora, gpu = _setup("planar16")
+    gpu.set_coarse_model(np.full(3360, np.nan, np.float32))
+    gpu.set_options(krylov="fgmres", coarse="learned", tol=1e-10)
+    lam, st = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9
+    gpu.set_options(krylov="fgmres", coarse="vcycle", tol=1e-10)
+    ref, st2 = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert st["iterations"] == st2["iterations"]
+    assert np.linalg.norm(_np(lam) - _np(ref)) / np.linalg.norm(_np(ref)) < 1e-12
+    # BiCGStab cannot drop a step: a NaN model is reported, not hidden
+    gpu.set_options(krylov="bicgstab", coarse="learned", tol=1e-10)
+    _lam, st3 = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi), check=False)
+    assert st3["status"] in ("nonfinite", "breakdown")
+
+
+def test_learned_mode_without_a_model_is_an_error():
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w = I.planar_helmholtz()
+    s = Solver(w.hier, w.coeffs, tol=w.tol, krylov="fgmres", coarse="learned")
+    with pytest.raises(HmgError):
+        s.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    with pytest.raises(HmgError):
+        s.apply_coarse_model(_cuda(np.ones(s.ncell)))
+    s.close()
