@@ -610,6 +610,7 @@ int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx,
   HMG_CUDA(c, cudaMemcpyAsync(grad_host, c->train.grad, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaMemcpyAsync(loss_host, c->train.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  *loss_host /= nsamp;   // the kernels sum the per-sample losses; the gradient is of the mean
   return HMG_OK;
 }
 

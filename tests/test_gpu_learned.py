@@ -215,3 +215,40 @@ def test_learned_mode_without_a_model_is_an_error():
     with pytest.raises(HmgError):
         s.apply_coarse_model(_cuda(np.ones(s.ncell)))
     s.close()
+
+
+def test_trained_network_gain():
+    """What training buys: the network trained on pairs from the solver's own preconditioner
+    calls, as the whole coarse solve of Algorithm 2 line 6 (no V-cycle, fallback disabled),
+    needs fewer flexible GMRES steps than the untrained network and than the preconditioner
+    with no coarse correction at all (configuration 2, the line smoother alone)."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(12, 30, seed=0)
+    s = Solver(w.hier, w.coeffs, tol=1e-6)
+    s.set_coarse_model(I.flatten_coarse_model(I.coarse_model_init(0)))
+    xs, ts = [], []
+    for seed in range(4):
+        ww = I.cubed_sphere(12, 30, seed=1000 + seed)
+        x, t, _lam, st = s.collect_coarse_pairs(_cuda(ww.Rub), _cuda(ww.Rpi), 16)
+        xs.append(x)
+        ts.append(t)
+    xs, ts = torch.cat(xs), torch.cat(ts)
+    cols = I.panel_patch_columns(12, 6, 6, 6, 3)
+    pair = np.repeat(np.arange(xs.shape[0], dtype=np.int32), len(cols))
+    xo, to = s.extract_patches(xs, ts, _cuda(pair, np.int32), _cuda(np.tile(cols, (xs.shape[0], 1)), np.int32))
+    test = I.cubed_sphere(12, 30, seed=99)
+    Rub, Rpi = _cuda(test.Rub), _cuda(test.Rpi)
+
+    def steps(**opt):
+        s.set_options(krylov="fgmres", tol=1e-6, max_iter=400, stall_ratio=1e30, **opt)
+        _lam, st = s.solve(Rub, Rpi)
+        assert st["status"] == "ok" and st["true_rel_residual"] < 2e-6
+        return st["iterations"]
+
+    untrained = steps(coarse="learned")
+    hist = s.train_coarse_model(xo, to, 6, 6, batch=32, epochs=20, lr=2e-3, seed=1)
+    assert hist[-1] < hist[0]
+    trained = steps(coarse="learned")
+    line_only = steps(precond="linesmooth", coarse="vcycle")
+    assert trained < untrained and trained < line_only, (trained, untrained, line_only)
+    s.close()
