@@ -13,26 +13,16 @@ struct MGArgs {
   int L, ncol, cpb;
   int64_t ncell;
   const int32_t *col_nbr;
-  const int32_t *parent;   // MODE 2: column of the next coarser level
 };
 
-// x'(K) of the smoother input: x, or x + injected coarse correction e (MODE 2).
-template <typename T, int MODE>
-__device__ __forceinline__ T xin(const T *__restrict__ x, const T *__restrict__ e,
-                                 const int32_t *__restrict__ parent, int col, int k, int L) {
-  T v = x[(int64_t)col * L + k];
-  if (MODE == 2) v += e[(int64_t)__ldg(parent + col) * L + k];
-  return v;
-}
-
-// acc + sign * (row K of H) . x' as one FMA per coefficient (acc = b, sign = -1: the residual).
-template <typename T, int MODE, bool NEG>
-__device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x,
-                                     const T *__restrict__ e, const MGArgs &a, int c, int k, T acc) {
+// acc + sign * (row K of H) . x as one FMA per coefficient (acc = b, sign = -1: the residual).
+template <typename T, bool NEG>
+__device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x, const MGArgs &a,
+                                     int c, int k, T acc) {
   const int64_t C = a.ncell, K = (int64_t)c * a.L + k;
   auto term = [&](int slot, int col, int kk) {
     const T h = __ldg(H + slot * C + K);
-    acc = fma(NEG ? -h : h, xin<T, MODE>(x, e, a.parent, col, kk, a.L), acc);
+    acc = fma(NEG ? -h : h, x[(int64_t)col * a.L + kk], acc);
   };
   term(0, c, k);
 #pragma unroll
@@ -42,52 +32,62 @@ __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restric
   return acc;
 }
 
-// MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x);
-// 2: as 1 with x replaced by x + P e (injection of the coarse correction e).
+// MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
     mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hinv,
                      const T *__restrict__ hcp, const T *__restrict__ b, const T *__restrict__ x,
-                     const T *__restrict__ e, T *__restrict__ x_out, T omega) {
+                     T *__restrict__ x_out, T omega) {
   extern __shared__ unsigned char smem_raw[];
   T *sr = reinterpret_cast<T *>(smem_raw);
-  T *ssub = sr + a.cpb * a.L, *sinv = ssub + a.cpb * a.L, *scp = sinv + a.cpb * a.L;
+  T *sl = sr + a.cpb * a.L, *scp = sl + a.cpb * a.L;
   const int c0 = blockIdx.x * a.cpb;
   const int nc = min(a.cpb, a.ncol - c0);
   const int n = nc * a.L;
   const int64_t base = (int64_t)c0 * a.L;
   const int64_t C = a.ncell;
+  // all threads: r, then r / pivot and sub / pivot, so that the serial Thomas recurrences
+  // below are one FMA per row each
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
     T r = b[K];
-    if (MODE != 0) r = h_apply<T, MODE, true>(H, x, e, a, c, k, r);
-    sr[i] = r;
-    ssub[i] = k > 0 ? __ldg(H + 5 * C + K) : (T)0;
-    sinv[i] = __ldg(hinv + K);
+    if (MODE != 0) r = h_apply<T, true>(H, x, a, c, k, r);
+    const T inv = __ldg(hinv + K);
+    sr[i] = r * inv;
+    sl[i] = k > 0 ? __ldg(H + 5 * C + K) * inv : (T)0;
     scp[i] = __ldg(hcp + K);
   }
   __syncthreads();
   if ((int)threadIdx.x < nc) {
     const int o = threadIdx.x * a.L;
-    T y = sr[o] * sinv[o];
-    sr[o] = y;
+    T y = sr[o];
     for (int k = 1; k < a.L; ++k) {
-      y = (sr[o + k] - ssub[o + k] * y) * sinv[o + k];
+      y = fma(-sl[o + k], y, sr[o + k]);
       sr[o + k] = y;
     }
-    T xk = sr[o + a.L - 1];
+    T xk = y;
     for (int k = a.L - 2; k >= 0; --k) {
-      xk = sr[o + k] - scp[o + k] * xk;
+      xk = fma(-scp[o + k], xk, sr[o + k]);
       sr[o + k] = xk;
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int c = c0 + i / a.L, k = i % a.L;
-    const T old = MODE == 0 ? (T)0 : xin<T, MODE>(x, e, a.parent, c, k, a.L);
-    x_out[base + i] = old + omega * sr[i];
+    const T old = MODE == 0 ? (T)0 : x[base + i];
+    x_out[base + i] = fma(omega, sr[i], old);
   }
+}
+
+// x_out = x + P e: injection of the coarse-level correction e (prolongation, Sec. 2.3).
+template <typename T>
+__global__ void mg_inject_kernel(const T *__restrict__ x, const T *__restrict__ e,
+                                 const int32_t *__restrict__ parent, int L, int64_t ncell,
+                                 T *__restrict__ x_out) {
+  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (K >= ncell) return;
+  const int c = (int)(K / L), k = (int)(K - (int64_t)c * L);
+  x_out[K] = x[K] + e[(int64_t)__ldg(parent + c) * L + k];
 }
 
 // b_coarse(cc, k) = sum over the four children ch of (b - H x)(ch, k); x == nullptr means 0.
@@ -104,7 +104,7 @@ __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict_
   for (int i = 0; i < 4; ++i) {
     const int ch = __ldg(children + 4 * (int64_t)cc + i);
     T r = b[(int64_t)ch * a.L + k];
-    if (x != nullptr) r = h_apply<T, 1, true>(H, x, nullptr, a, ch, k, r);
+    if (x != nullptr) r = h_apply<T, true>(H, x, a, ch, k, r);
     s += r;
   }
   bc[Kc] = s;
@@ -116,7 +116,7 @@ __global__ void mg_residual_kernel(const MGArgs a, const T *__restrict__ H, cons
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= a.ncell) return;
   const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
-  r[K] = h_apply<T, 1, true>(H, x, nullptr, a, c, k, b[K]);
+  r[K] = h_apply<T, true>(H, x, a, c, k, b[K]);
 }
 
 template <typename T>
@@ -125,7 +125,7 @@ __global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= a.ncell) return;
   const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
-  y[K] = h_apply<T, 1, false>(H, x, nullptr, a, c, k, (T)0);
+  y[K] = h_apply<T, false>(H, x, a, c, k, (T)0);
 }
 
 static MGArgs mg_args(const Ctx *c, int l) {
@@ -137,21 +137,20 @@ static MGArgs mg_args(const Ctx *c, int l) {
   a.cpb = c->tune_mg_cpb[l] > 0 && c->tune_mg_cpb[l] <= cmax ? c->tune_mg_cpb[l] : cmax;
   a.ncell = lv.ncell;
   a.col_nbr = lv.col_nbr;
-  a.parent = lv.parent;
   return a;
 }
 
 template <typename T, int MODE>
-static int smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out, int cpb_override = 0) {
+static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0) {
   const Level &lv = c->lv[l];
   MGArgs a = mg_args(c, l);
   if (cpb_override > 0 && cpb_override * lv.nlev <= 256) a.cpb = cpb_override;
   const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
-  const size_t smem = (size_t)4 * a.cpb * lv.nlev * sizeof(T);
+  const size_t smem = (size_t)3 * a.cpb * lv.nlev * sizeof(T);
   int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > 256) threads = 256;
   mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_inv(lv),
-                                                             Prec<T>::Hz_cp(lv), b, x, e, out,
+                                                             Prec<T>::Hz_cp(lv), b, x, out,
                                                              (T)c->opt.mg_omega);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
@@ -163,12 +162,12 @@ int time_mg_cpb(Ctx *c, int l, int cpb, float *ms) {
   double *b = static_cast<double *>(lv.vb), *x = static_cast<double *>(lv.vx), *y = static_cast<double *>(lv.vy);
   HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * lv.ncell, c->stream));
   HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * lv.ncell, c->stream));
-  int st = smooth<double, 1>(c, l, b, x, nullptr, y, cpb);
+  int st = smooth<double, 1>(c, l, b, x, y, cpb);
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-  for (int i = 0; i < 5 && !st; ++i) st = smooth<double, 1>(c, l, b, x, nullptr, y, cpb);
+  for (int i = 0; i < 5 && !st; ++i) st = smooth<double, 1>(c, l, b, x, y, cpb);
   HMG_CUDA(c, cudaEventRecord(e1, c->stream));
   HMG_CUDA(c, cudaEventSynchronize(e1));
   cudaEventElapsedTime(ms, e0, e1);
@@ -185,11 +184,11 @@ static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur, const T *
   Level &lv = c->lv[l];
   T *x = static_cast<T *>(lv.vx), *y = static_cast<T *>(lv.vy);
   int st;
-  if (x0) st = smooth<T, 1>(c, l, b, x0, nullptr, x);
-  else st = smooth<T, 0>(c, l, b, nullptr, nullptr, x);
+  if (x0) st = smooth<T, 1>(c, l, b, x0, x);
+  else st = smooth<T, 0>(c, l, b, nullptr, x);
   if (st) return st;
   for (int i = 1; i < n; ++i) {
-    if ((st = smooth<T, 1>(c, l, b, x, nullptr, y))) return st;
+    if ((st = smooth<T, 1>(c, l, b, x, y))) return st;
     T *t = x; x = y; y = t;
   }
   *cur = x;
@@ -219,10 +218,12 @@ int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
   for (int l = nmg - 2; l >= 0; --l) {
     Level &lv = c->lv[l];
     T *other = x[l] == static_cast<T *>(lv.vx) ? static_cast<T *>(lv.vy) : static_cast<T *>(lv.vx);
-    if ((st = smooth<T, 2>(c, l, b[l], x[l], x[l + 1], other))) return st;
+    mg_inject_kernel<T><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,
+                                                                        lv.ncell, other);
+    HMG_CUDA(c, cudaGetLastError());
     T *cur = other, *nxt = x[l];
-    for (int i = 1; i < c->opt.mg_npost; ++i) {
-      if ((st = smooth<T, 1>(c, l, b[l], cur, nullptr, nxt))) return st;
+    for (int i = 0; i < c->opt.mg_npost; ++i) {
+      if ((st = smooth<T, 1>(c, l, b[l], cur, nxt))) return st;
       T *t = cur; cur = nxt; nxt = t;
     }
     x[l] = cur;

@@ -208,30 +208,31 @@ __global__ void __launch_bounds__(256)
     const int c0 = blockIdx.x * a.cpb;
     const int nc = min(a.cpb, a.ncol - c0);
     const int nrow = nc * L1;
-    T *ssub = sr + a.cpb * L1, *sinv = ssub + a.cpb * L1, *scp = sinv + a.cpb * L1;
+    T *sl = sr + a.cpb * L1, *scp = sl + a.cpb * L1;
     const int64_t base = d.NH + (int64_t)c0 * L1;
+    // all threads: r, then r / pivot and sub / pivot, so that the serial Thomas recurrences
+    // below are one FMA per row each
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
       if (!ZERO) r = s_row_z<T, T, T, true>(S, lam_in, a.col_edges, d, row, r);
       const int k = i % L1;
-      sr[i] = r;
-      ssub[i] = k > 0 ? __ldg(S + 10 * d.NT + row) : (T)0;
-      sinv[i] = __ldg(zinv + (row - d.NH));
+      const T inv = __ldg(zinv + (row - d.NH));
+      sr[i] = r * inv;
+      sl[i] = k > 0 ? __ldg(S + 10 * d.NT + row) * inv : (T)0;
       scp[i] = __ldg(zcp + (row - d.NH));
     }
     __syncthreads();
     if ((int)threadIdx.x < nc) {
       const int o = threadIdx.x * L1;
-      T y = sr[o] * sinv[o];
-      sr[o] = y;
+      T y = sr[o];
       for (int k = 1; k < L1; ++k) {
-        y = (sr[o + k] - ssub[o + k] * y) * sinv[o + k];
+        y = fma(-sl[o + k], y, sr[o + k]);
         sr[o + k] = y;
       }
-      T xk = sr[o + L1 - 1];
+      T xk = y;
       for (int k = L1 - 2; k >= 0; --k) {
-        xk = sr[o + k] - scp[o + k] * xk;
+        xk = fma(-scp[o + k], xk, sr[o + k]);
         sr[o + k] = xk;
       }
     }
@@ -267,7 +268,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
   if (threads > 256) threads = 256;
   const unsigned nhb = grid_for(f.nth, threads);
-  const size_t smem = (size_t)4 * a.cpb * (f.nlev + 1) * sizeof(T);
+  const size_t smem = (size_t)3 * a.cpb * (f.nlev + 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
   sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
       a, Prec<T>::S(c), Prec<T>::Sz_inv(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_inv(c), b, lam_in,
@@ -384,7 +385,7 @@ static int two_level(Ctx *c, const double *r, double *z) {
   T *dpi = nullptr;
   {
     const int nl = c->nmg - 1;
-    Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * c->opt.mg_npost);
+    Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1));
     const bool learned = c->opt.coarse != HMG_COARSE_VCYCLE && !c->coarse_fallback;
     if (learned && c->opt.coarse == HMG_COARSE_LEARNED) {
       dpi = w3;
