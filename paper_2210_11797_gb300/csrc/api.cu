@@ -155,6 +155,11 @@ int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
   c->opt = *opt;
   if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32)
     c->assembled = false;  // the FP32 copies are built by hmg_assemble_trace
+  if (c->assembled && (c->opt.omega != c->factor_omega || c->opt.mg_omega != c->factor_mg_omega)) {
+    HMG_CUDA(c, cudaSetDevice(c->device));
+    if ((st = build_factors(c))) return st;
+    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   return HMG_OK;
 }
 

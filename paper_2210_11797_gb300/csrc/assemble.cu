@@ -342,9 +342,14 @@ __global__ void trace_rows_kernel(const RowArgs a, const double *__restrict__ SK
 
 // Thomas factors of S^zz_c (rows k = 0..L of column c: sub = slot 10, diag = slot 0,
 // sup = slot 5) and 1 / diag(S^hh).
-__global__ void trace_factor_kernel(const RowArgs a, int ncol, const double *__restrict__ S,
-                                    double *__restrict__ zinv, double *__restrict__ zcp,
-                                    double *__restrict__ hinv) {
+// Thomas factors of every S^zz_j (Algorithm 1) with the relaxation folded in: for pivot
+// p_k = d_k - s_k cp_{k-1}, zw = omega / p_k, zl = s_k / p_k (s_k the sub-diagonal) and
+// zcp = u_k / p_k (u_k the super-diagonal); and hw = omega / diag(S^hh). The sweeps then do
+// y_k = r_k zw_k - zl_k y_{k-1}, x_k = y_k - zcp_k x_{k+1} (one FMA per row each) and
+// lambda += x, which is lambda + omega (S^zz)^-1 r.
+__global__ void trace_factor_kernel(const RowArgs a, int ncol, const double *__restrict__ S, double omega,
+                                    double *__restrict__ zw, double *__restrict__ zl,
+                                    double *__restrict__ zcp, double *__restrict__ hw) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t T = a.NT;
   if (i < ncol) {
@@ -355,11 +360,12 @@ __global__ void trace_factor_kernel(const RowArgs a, int ncol, const double *__r
       const double sub = k > 0 ? S[10 * T + row] : 0.0;
       const double inv = 1.0 / (S[row] - sub * cp);
       cp = S[5 * T + row] * inv;
-      zinv[row - a.NH] = inv;
+      zw[row - a.NH] = omega * inv;
+      zl[row - a.NH] = sub * inv;
       zcp[row - a.NH] = cp;
     }
   }
-  for (int64_t row = i; row < a.NH; row += (int64_t)gridDim.x * blockDim.x) hinv[row] = 1.0 / S[row];
+  for (int64_t row = i; row < a.NH; row += (int64_t)gridDim.x * blockDim.x) hw[row] = omega / S[row];
 }
 
 struct HArgs {
@@ -406,9 +412,12 @@ __global__ void pressure_rows_kernel(const HArgs a, const double *__restrict__ r
   H[K] = diag;
 }
 
-// Thomas factors of H_z per column (sub = below, diag, sup = above).
-__global__ void pressure_factor_kernel(const HArgs a, const double *__restrict__ H,
-                                       double *__restrict__ inv_out, double *__restrict__ cp_out) {
+// Thomas factors of H_z per column (sub = below, diag, sup = above) with the block-Jacobi
+// relaxation omega folded in, in the form of trace_factor_kernel: w = omega / p_k,
+// l = sub / p_k, cp = sup / p_k.
+__global__ void pressure_factor_kernel(const HArgs a, const double *__restrict__ H, double omega,
+                                       double *__restrict__ w_out, double *__restrict__ l_out,
+                                       double *__restrict__ cp_out) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= a.ncol) return;
   const int64_t C = a.ncell;
@@ -418,7 +427,8 @@ __global__ void pressure_factor_kernel(const HArgs a, const double *__restrict__
     const double sub = k > 0 ? H[5 * C + K] : 0.0;
     const double inv = 1.0 / (H[K] - sub * cp);
     cp = H[6 * C + K] * inv;
-    inv_out[K] = inv;
+    w_out[K] = omega * inv;
+    l_out[K] = sub * inv;
     cp_out[K] = cp;
   }
 }
@@ -452,10 +462,46 @@ __global__ void to_float_kernel(const double *__restrict__ in, float *__restrict
 }
 
 static int to_float(Ctx *c, const double *in, float **out, int64_t n) {
-  int st = dev_alloc(c, out, (size_t)n);
-  if (st) return st;
+  if (!*out) {
+    int st = dev_alloc(c, out, (size_t)n);
+    if (st) return st;
+  }
   to_float_kernel<<<grid_for(n, 256) > 4096 ? 4096 : grid_for(n, 256), 256, 0, c->stream>>>(in, *out, n);
   HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// Relaxation-weighted Thomas factors of S^zz, 1/diag S^hh and H_z on every level for the
+// current omega and mg_omega (and their FP32 copies when those exist). Rebuilt whenever
+// either relaxation weight changes.
+int build_factors(Ctx *c) {
+  const Level &f = c->lv[0];
+  RowArgs ra{f.nlev, f.nth, f.ntrace, f.ncell, f.edge_stencil, f.edge_fc, f.col_edges, f.col_nbr, f.col_nbr_face};
+  trace_factor_kernel<<<grid_for(f.ncol, 128), 128, 0, c->stream>>>(ra, f.ncol, c->S, c->opt.omega, c->Sz_w,
+                                                                    c->Sz_l, c->Sz_cp, c->Sh_w);
+  HMG_CUDA(c, cudaGetLastError());
+  for (int l = 0; l < c->nmg; ++l) {
+    Level &lv = c->lv[l];
+    HArgs ha{lv.nlev, lv.ncol, lv.ncell, lv.col_nbr, lv.col_nbr_face};
+    pressure_factor_kernel<<<grid_for(lv.ncol, 128), 128, 0, c->stream>>>(ha, lv.H, c->opt.mg_omega, lv.Hz_w,
+                                                                           lv.Hz_l, lv.Hz_cp);
+    HMG_CUDA(c, cudaGetLastError());
+  }
+  int st;
+  if (c->have_fp32) {
+    if ((st = to_float(c, c->Sz_w, &c->Sz_w32, f.ntz))) return st;
+    if ((st = to_float(c, c->Sz_l, &c->Sz_l32, f.ntz))) return st;
+    if ((st = to_float(c, c->Sz_cp, &c->Sz_cp32, f.ntz))) return st;
+    if ((st = to_float(c, c->Sh_w, &c->Sh_w32, f.nth))) return st;
+    for (int l = 0; l < c->nmg; ++l) {
+      Level &lv = c->lv[l];
+      if ((st = to_float(c, lv.Hz_w, &lv.Hz_w32, lv.ncell))) return st;
+      if ((st = to_float(c, lv.Hz_l, &lv.Hz_l32, lv.ncell))) return st;
+      if ((st = to_float(c, lv.Hz_cp, &lv.Hz_cp32, lv.ncell))) return st;
+    }
+  }
+  c->factor_omega = c->opt.omega;
+  c->factor_mg_omega = c->opt.mg_omega;
   return HMG_OK;
 }
 
@@ -476,9 +522,10 @@ int assemble_all(Ctx *c) {
   int st;
   if (!c->S) {
     if ((st = dev_alloc(c, &c->S, (size_t)kSlots * T))) return st;
-    if ((st = dev_alloc(c, &c->Sz_inv, (size_t)f.ntz))) return st;
+    if ((st = dev_alloc(c, &c->Sz_w, (size_t)f.ntz))) return st;
+    if ((st = dev_alloc(c, &c->Sz_l, (size_t)f.ntz))) return st;
     if ((st = dev_alloc(c, &c->Sz_cp, (size_t)f.ntz))) return st;
-    if ((st = dev_alloc(c, &c->Sh_inv, (size_t)f.nth))) return st;
+    if ((st = dev_alloc(c, &c->Sh_w, (size_t)f.nth))) return st;
     if ((st = dev_alloc(c, &c->Ainv, (size_t)49 * C))) return st;
     if ((st = dev_alloc(c, &c->kth, (size_t)6 * C))) return st;
     if ((st = dev_alloc(c, &c->gamma, (size_t)C))) return st;
@@ -494,38 +541,30 @@ int assemble_all(Ctx *c) {
   RowArgs ra{f.nlev, f.nth, T, C, f.edge_stencil, f.edge_fc, f.col_edges, f.col_nbr, f.col_nbr_face};
   trace_rows_kernel<<<grid_for(T, 256), 256, 0, c->stream>>>(ra, SK, c->S);
   HMG_CUDA(c, cudaGetLastError());
-  trace_factor_kernel<<<grid_for(f.ncol, 128), 128, 0, c->stream>>>(ra, f.ncol, c->S, c->Sz_inv,
-                                                                    c->Sz_cp, c->Sh_inv);
-  HMG_CUDA(c, cudaGetLastError());
   for (int l = 0; l < c->nmg; ++l) {
     Level &lv = c->lv[l];
     if (!lv.H) {
       if ((st = dev_alloc(c, &lv.H, (size_t)kHCoef * lv.ncell))) return st;
-      if ((st = dev_alloc(c, &lv.Hz_inv, (size_t)lv.ncell))) return st;
+      if ((st = dev_alloc(c, &lv.Hz_w, (size_t)lv.ncell))) return st;
+      if ((st = dev_alloc(c, &lv.Hz_l, (size_t)lv.ncell))) return st;
       if ((st = dev_alloc(c, &lv.Hz_cp, (size_t)lv.ncell))) return st;
     }
     HArgs ha{lv.nlev, lv.ncol, lv.ncell, lv.col_nbr, lv.col_nbr_face};
     pressure_rows_kernel<<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(ha, rec[l], lv.H);
-    HMG_CUDA(c, cudaGetLastError());
-    pressure_factor_kernel<<<grid_for(lv.ncol, 128), 128, 0, c->stream>>>(ha, lv.H, lv.Hz_inv, lv.Hz_cp);
     HMG_CUDA(c, cudaGetLastError());
   }
   gamma_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(ra, sk1, rec[0], c->gamma);
   HMG_CUDA(c, cudaGetLastError());
   if (c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32) {
     if ((st = to_float(c, c->S, &c->S32, (int64_t)kSlots * T))) return st;
-    if ((st = to_float(c, c->Sz_inv, &c->Sz_inv32, f.ntz))) return st;
-    if ((st = to_float(c, c->Sz_cp, &c->Sz_cp32, f.ntz))) return st;
-    if ((st = to_float(c, c->Sh_inv, &c->Sh_inv32, f.nth))) return st;
     if ((st = to_float(c, c->gamma, &c->gamma32, C))) return st;
     for (int l = 0; l < c->nmg; ++l) {
       Level &lv = c->lv[l];
       if ((st = to_float(c, lv.H, &lv.H32, (int64_t)kHCoef * lv.ncell))) return st;
-      if ((st = to_float(c, lv.Hz_inv, &lv.Hz_inv32, lv.ncell))) return st;
-      if ((st = to_float(c, lv.Hz_cp, &lv.Hz_cp32, lv.ncell))) return st;
     }
     c->have_fp32 = true;
   }
+  if ((st = build_factors(c))) return st;
   int sing = 0;
   HMG_CUDA(c, cudaMemcpyAsync(&sing, singular, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));

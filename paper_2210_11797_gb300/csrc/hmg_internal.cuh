@@ -61,9 +61,10 @@ struct Level {
   double *theta_lev = nullptr, *exner_lev = nullptr, *exner = nullptr;
   // assembled pressure operator (device)
   double *H = nullptr;              // [7][ncell]
-  double *Hz_inv = nullptr;         // [ncell] Thomas reciprocal pivots of H_z
-  double *Hz_cp = nullptr;          // [ncell] Thomas modified super-diagonal of H_z
-  float *H32 = nullptr, *Hz_inv32 = nullptr, *Hz_cp32 = nullptr;
+  // Thomas factors of H_z with the relaxation mg_omega folded in (pivot p_k): omega / p_k,
+  // sub_k / p_k and sup_k / p_k, [ncell] each
+  double *Hz_w = nullptr, *Hz_l = nullptr, *Hz_cp = nullptr;
+  float *H32 = nullptr, *Hz_w32 = nullptr, *Hz_l32 = nullptr, *Hz_cp32 = nullptr;
   // multigrid work vectors, sized for doubles (used as float in the mixed path)
   void *vb = nullptr, *vx = nullptr, *vy = nullptr;
 };
@@ -89,13 +90,14 @@ struct Ctx {
   bool have_mesh = false, have_coeffs = false, assembled = false, have_fp32 = false;
   // finest-level trace system (device)
   double *S = nullptr;        // [11][ntrace]
-  double *Sz_inv = nullptr;   // [ntz] Thomas reciprocal pivots of S^zz
-  double *Sz_cp = nullptr;    // [ntz] Thomas modified super-diagonals
-  double *Sh_inv = nullptr;   // [nth] 1 / diag(S^hh)
+  // Thomas factors of S^zz with omega folded in (pivot p_k): omega / p_k, sub_k / p_k,
+  // sup_k / p_k, [ntz] each; and omega / diag(S^hh) [nth]
+  double *Sz_w = nullptr, *Sz_l = nullptr, *Sz_cp = nullptr, *Sh_w = nullptr;
+  double factor_omega = 0.0, factor_mg_omega = 0.0;   // the weights the factors were built with
   double *Ainv = nullptr;     // [49][ncell] A_K^-1, entry (i, j) at (7 i + j) * ncell + K
   double *kth = nullptr;      // [6][ncell] diagonal of K_K (k theta on each local face)
   double *gamma = nullptr;    // [ncell]
-  float *S32 = nullptr, *Sz_inv32 = nullptr, *Sz_cp32 = nullptr, *Sh_inv32 = nullptr,
+  float *S32 = nullptr, *Sz_w32 = nullptr, *Sz_l32 = nullptr, *Sz_cp32 = nullptr, *Sh_w32 = nullptr,
         *gamma32 = nullptr;
   // Krylov workspace (FP64, [ntrace] each)
   double *B = nullptr, *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr,
@@ -188,6 +190,8 @@ inline unsigned grid_for(int64_t n, int threads) {
 
 // ---- assembly (assemble.cu) -----------------------------------------------------------
 int assemble_all(Ctx *c);
+// (Re)builds the relaxation-weighted Thomas factors for the context's omega and mg_omega.
+int build_factors(Ctx *c);
 
 // ---- trace-space kernels (trace_ops.cu) -----------------------------------------------
 // y = S x (FP64). mode 0: plain; 1: also (w, y) -> scal[slot0]; 2: also (y, w) -> slot0 and

@@ -17,23 +17,27 @@ struct Prec;
 template <>
 struct Prec<double> {
   static const double *S(const Ctx *c) { return c->S; }
-  static const double *Sz_inv(const Ctx *c) { return c->Sz_inv; }
+  static const double *Sz_w(const Ctx *c) { return c->Sz_w; }
+  static const double *Sz_l(const Ctx *c) { return c->Sz_l; }
   static const double *Sz_cp(const Ctx *c) { return c->Sz_cp; }
-  static const double *Sh_inv(const Ctx *c) { return c->Sh_inv; }
+  static const double *Sh_w(const Ctx *c) { return c->Sh_w; }
   static const double *gamma(const Ctx *c) { return c->gamma; }
   static const double *H(const Level &l) { return l.H; }
-  static const double *Hz_inv(const Level &l) { return l.Hz_inv; }
+  static const double *Hz_w(const Level &l) { return l.Hz_w; }
+  static const double *Hz_l(const Level &l) { return l.Hz_l; }
   static const double *Hz_cp(const Level &l) { return l.Hz_cp; }
 };
 template <>
 struct Prec<float> {
   static const float *S(const Ctx *c) { return c->S32; }
-  static const float *Sz_inv(const Ctx *c) { return c->Sz_inv32; }
+  static const float *Sz_w(const Ctx *c) { return c->Sz_w32; }
+  static const float *Sz_l(const Ctx *c) { return c->Sz_l32; }
   static const float *Sz_cp(const Ctx *c) { return c->Sz_cp32; }
-  static const float *Sh_inv(const Ctx *c) { return c->Sh_inv32; }
+  static const float *Sh_w(const Ctx *c) { return c->Sh_w32; }
   static const float *gamma(const Ctx *c) { return c->gamma32; }
   static const float *H(const Level &l) { return l.H32; }
-  static const float *Hz_inv(const Level &l) { return l.Hz_inv32; }
+  static const float *Hz_w(const Level &l) { return l.Hz_w32; }
+  static const float *Hz_l(const Level &l) { return l.Hz_l32; }
   static const float *Hz_cp(const Level &l) { return l.Hz_cp32; }
 };
 

@@ -35,9 +35,9 @@ __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restric
 // MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
-    mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hinv,
-                     const T *__restrict__ hcp, const T *__restrict__ b, const T *__restrict__ x,
-                     T *__restrict__ x_out, T omega) {
+    mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hw,
+                     const T *__restrict__ hl, const T *__restrict__ hcp, const T *__restrict__ b,
+                     const T *__restrict__ x, T *__restrict__ x_out) {
   extern __shared__ unsigned char smem_raw[];
   T *sr = reinterpret_cast<T *>(smem_raw);
   T *sl = sr + a.cpb * a.L, *scp = sl + a.cpb * a.L;
@@ -45,17 +45,15 @@ __global__ void __launch_bounds__(256)
   const int nc = min(a.cpb, a.ncol - c0);
   const int n = nc * a.L;
   const int64_t base = (int64_t)c0 * a.L;
-  const int64_t C = a.ncell;
-  // all threads: r, then r / pivot and sub / pivot, so that the serial Thomas recurrences
-  // below are one FMA per row each
+  // all threads: r omega / pivot and the factors, so that the serial Thomas recurrences
+  // below are one FMA per row each (factors from pressure_factor_kernel)
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
     T r = b[K];
     if (MODE != 0) r = h_apply<T, true>(H, x, a, c, k, r);
-    const T inv = __ldg(hinv + K);
-    sr[i] = r * inv;
-    sl[i] = k > 0 ? __ldg(H + 5 * C + K) * inv : (T)0;
+    sr[i] = r * __ldg(hw + K);
+    sl[i] = __ldg(hl + K);
     scp[i] = __ldg(hcp + K);
   }
   __syncthreads();
@@ -73,10 +71,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const T old = MODE == 0 ? (T)0 : x[base + i];
-    x_out[base + i] = fma(omega, sr[i], old);
-  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x_out[base + i] = MODE == 0 ? sr[i] : x[base + i] + sr[i];
 }
 
 // x_out = x + P e: injection of the coarse-level correction e (prolongation, Sec. 2.3).
@@ -149,9 +144,9 @@ static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_overrid
   const size_t smem = (size_t)3 * a.cpb * lv.nlev * sizeof(T);
   int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > 256) threads = 256;
-  mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_inv(lv),
-                                                             Prec<T>::Hz_cp(lv), b, x, out,
-                                                             (T)c->opt.mg_omega);
+  mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_w(lv),
+                                                             Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x,
+                                                             out);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }

@@ -197,9 +197,9 @@ struct SweepArgs {
 
 template <typename T, typename Tb, typename Tout, bool ZERO>
 __global__ void __launch_bounds__(256)
-    sweep_kernel(const SweepArgs a, const T *__restrict__ S, const T *__restrict__ zinv,
-                 const T *__restrict__ zcp, const T *__restrict__ hinv, const Tb *__restrict__ b,
-                 const T *__restrict__ lam_in, Tout *__restrict__ lam_out, T omega) {
+    sweep_kernel(const SweepArgs a, const T *__restrict__ S, const T *__restrict__ zw,
+                 const T *__restrict__ zl, const T *__restrict__ zcp, const T *__restrict__ hw,
+                 const Tb *__restrict__ b, const T *__restrict__ lam_in, Tout *__restrict__ lam_out) {
   extern __shared__ unsigned char smem_raw[];
   const TraceDims &d = a.d;
   if ((int)blockIdx.x < a.nzb) {
@@ -210,16 +210,14 @@ __global__ void __launch_bounds__(256)
     const int nrow = nc * L1;
     T *sl = sr + a.cpb * L1, *scp = sl + a.cpb * L1;
     const int64_t base = d.NH + (int64_t)c0 * L1;
-    // all threads: r, then r / pivot and sub / pivot, so that the serial Thomas recurrences
-    // below are one FMA per row each
+    // all threads: r omega / pivot and the factors, so that the serial Thomas recurrences
+    // below are one FMA per row each (factors from trace_factor_kernel)
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
       if (!ZERO) r = s_row_z<T, T, T, true>(S, lam_in, a.col_edges, d, row, r);
-      const int k = i % L1;
-      const T inv = __ldg(zinv + (row - d.NH));
-      sr[i] = r * inv;
-      sl[i] = k > 0 ? __ldg(S + 10 * d.NT + row) * inv : (T)0;
+      sr[i] = r * __ldg(zw + (row - d.NH));
+      sl[i] = __ldg(zl + (row - d.NH));
       scp[i] = __ldg(zcp + (row - d.NH));
     }
     __syncthreads();
@@ -239,16 +237,14 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
-      const T old = ZERO ? (T)0 : lam_in[row];
-      lam_out[row] = (Tout)(old + omega * sr[i]);
+      lam_out[row] = (Tout)(ZERO ? sr[i] : lam_in[row] + sr[i]);
     }
   } else {
     const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
     if (row >= d.NH) return;
     T r = (T)__ldg(b + row);
     if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
-    const T old = ZERO ? (T)0 : lam_in[row];
-    lam_out[row] = (Tout)fma(r * __ldg(hinv + row), omega, old);
+    lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
   }
 }
 
@@ -271,8 +267,8 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   const size_t smem = (size_t)3 * a.cpb * (f.nlev + 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
   sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
-      a, Prec<T>::S(c), Prec<T>::Sz_inv(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_inv(c), b, lam_in,
-      lam_out, (T)c->opt.omega);
+      a, Prec<T>::S(c), Prec<T>::Sz_w(c), Prec<T>::Sz_l(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_w(c), b,
+      lam_in, lam_out);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }

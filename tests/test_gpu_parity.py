@@ -134,6 +134,30 @@ def test_line_smoother_matches_oracle(name):
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
 
 
+def test_changed_relaxation_weights_rebuild_the_factors():
+    """omega and mg_omega are folded into the Thomas factors; changing them through the
+    options rebuilds the factors (the oracle takes the weights as arguments)."""
+    from oracle.pressure_mg import PressureMultigrid
+    w, ora, gpu = _pair("planar16")
+    rng = np.random.default_rng(13)
+    lam, B = rng.standard_normal(gpu.ntrace), ora.S @ rng.standard_normal(gpu.ntrace)
+    b = rng.standard_normal(gpu.ncell)
+    try:
+        gpu.set_options(omega=0.8, mg_omega=0.7)
+        got = _np(gpu.line_smooth(_cuda(B), _cuda(lam), 2))
+        want = ora.smoother.smooth(lam, B, 0.8, 2)
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+        mg = PressureMultigrid(w.hier, w.coeffs, 0.7, ora.mg.npre, ora.mg.npost, ora.mg.ncoarse)
+        got = _np(gpu.vcycle(_cuda(b)))
+        want = mg.vcycle(b)
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+    finally:
+        gpu.set_options(omega=0.6, mg_omega=0.9)
+    got = _np(gpu.line_smooth(_cuda(B), _cuda(lam), 2))
+    want = ora.smoother.smooth(lam, B, 0.6, 2)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("name", NAMES)
 def test_pressure_operator_and_vcycle_match_oracle(name):
     w, ora, gpu = _pair(name)
