@@ -240,6 +240,12 @@ int autotune(Ctx *c);
 // Sweep launch with explicit columns per block (autotuner).
 int time_sweep_cpb(Ctx *c, int cpb, float *ms);
 int time_mg_cpb(Ctx *c, int level, int cpb, float *ms);
+// Columns per block of the pressure smoother: at most 64, and its three shared-memory arrays
+// (column stride nlev rounded up to odd) within the default 48 KB (FP64).
+inline int mg_cpb_limit(int nlev) {
+  const int m = 2048 / (nlev | 1);
+  return m < 1 ? 1 : (m > 64 ? 64 : m);
+}
 
 }  // namespace hmg
 

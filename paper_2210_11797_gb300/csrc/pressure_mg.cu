@@ -39,8 +39,11 @@ __global__ void __launch_bounds__(256)
                      const T *__restrict__ hl, const T *__restrict__ hcp, const T *__restrict__ b,
                      const T *__restrict__ x, T *__restrict__ x_out) {
   extern __shared__ unsigned char smem_raw[];
+  // one column per lane in the serial phase: column j at j * ld, ld = L rounded up to odd so
+  // that the lanes of a half-warp hit distinct banks
+  const int ld = a.L | 1;
   T *sr = reinterpret_cast<T *>(smem_raw);
-  T *sl = sr + a.cpb * a.L, *scp = sl + a.cpb * a.L;
+  T *sl = sr + a.cpb * ld, *scp = sl + a.cpb * ld;
   const int c0 = blockIdx.x * a.cpb;
   const int nc = min(a.cpb, a.ncol - c0);
   const int n = nc * a.L;
@@ -52,13 +55,14 @@ __global__ void __launch_bounds__(256)
     const int64_t K = base + i;
     T r = b[K];
     if (MODE != 0) r = h_apply<T, true>(H, x, a, c, k, r);
-    sr[i] = r * __ldg(hw + K);
-    sl[i] = __ldg(hl + K);
-    scp[i] = __ldg(hcp + K);
+    const int j = (c - c0) * ld + k;
+    sr[j] = r * __ldg(hw + K);
+    sl[j] = __ldg(hl + K);
+    scp[j] = __ldg(hcp + K);
   }
   __syncthreads();
   if ((int)threadIdx.x < nc) {
-    const int o = threadIdx.x * a.L;
+    const int o = threadIdx.x * ld;
     T y = sr[o];
     for (int k = 1; k < a.L; ++k) {
       y = fma(-sl[o + k], y, sr[o + k]);
@@ -71,7 +75,10 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x_out[base + i] = MODE == 0 ? sr[i] : x[base + i] + sr[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const T v = sr[(i / a.L) * ld + i % a.L];
+    x_out[base + i] = MODE == 0 ? v : x[base + i] + v;
+  }
 }
 
 // x_out = x + P e: injection of the coarse-level correction e (prolongation, Sec. 2.3).
@@ -128,8 +135,8 @@ static MGArgs mg_args(const Ctx *c, int l) {
   MGArgs a;
   a.L = lv.nlev;
   a.ncol = lv.ncol;
-  const int cmax = 256 / lv.nlev > 0 ? 256 / lv.nlev : 1;
-  a.cpb = c->tune_mg_cpb[l] > 0 && c->tune_mg_cpb[l] <= cmax ? c->tune_mg_cpb[l] : cmax;
+  const int cdef = mg_cpb_limit(lv.nlev) < 32 ? mg_cpb_limit(lv.nlev) : 32;
+  a.cpb = c->tune_mg_cpb[l] > 0 && c->tune_mg_cpb[l] <= mg_cpb_limit(lv.nlev) ? c->tune_mg_cpb[l] : cdef;
   a.ncell = lv.ncell;
   a.col_nbr = lv.col_nbr;
   return a;
@@ -139,9 +146,9 @@ template <typename T, int MODE>
 static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0) {
   const Level &lv = c->lv[l];
   MGArgs a = mg_args(c, l);
-  if (cpb_override > 0 && cpb_override * lv.nlev <= 256) a.cpb = cpb_override;
+  if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) a.cpb = cpb_override;
   const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
-  const size_t smem = (size_t)3 * a.cpb * lv.nlev * sizeof(T);
+  const size_t smem = (size_t)3 * a.cpb * (lv.nlev | 1) * sizeof(T);
   int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > 256) threads = 256;
   mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_w(lv),

@@ -205,10 +205,11 @@ __global__ void __launch_bounds__(256)
   if ((int)blockIdx.x < a.nzb) {
     T *sr = reinterpret_cast<T *>(smem_raw);
     const int L1 = d.L + 1;
+    const int ld = L1 | 1;   // column stride in shared memory, odd: conflict-free lanes
     const int c0 = blockIdx.x * a.cpb;
     const int nc = min(a.cpb, a.ncol - c0);
     const int nrow = nc * L1;
-    T *sl = sr + a.cpb * L1, *scp = sl + a.cpb * L1;
+    T *sl = sr + a.cpb * ld, *scp = sl + a.cpb * ld;
     const int64_t base = d.NH + (int64_t)c0 * L1;
     // all threads: r omega / pivot and the factors, so that the serial Thomas recurrences
     // below are one FMA per row each (factors from trace_factor_kernel)
@@ -216,13 +217,14 @@ __global__ void __launch_bounds__(256)
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
       if (!ZERO) r = s_row_z<T, T, T, true>(S, lam_in, a.col_edges, d, row, r);
-      sr[i] = r * __ldg(zw + (row - d.NH));
-      sl[i] = __ldg(zl + (row - d.NH));
-      scp[i] = __ldg(zcp + (row - d.NH));
+      const int j = (i / L1) * ld + i % L1;
+      sr[j] = r * __ldg(zw + (row - d.NH));
+      sl[j] = __ldg(zl + (row - d.NH));
+      scp[j] = __ldg(zcp + (row - d.NH));
     }
     __syncthreads();
     if ((int)threadIdx.x < nc) {
-      const int o = threadIdx.x * L1;
+      const int o = threadIdx.x * ld;
       T y = sr[o];
       for (int k = 1; k < L1; ++k) {
         y = fma(-sl[o + k], y, sr[o + k]);
@@ -237,7 +239,8 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
-      lam_out[row] = (Tout)(ZERO ? sr[i] : lam_in[row] + sr[i]);
+      const T v = sr[(i / L1) * ld + i % L1];
+      lam_out[row] = (Tout)(ZERO ? v : lam_in[row] + v);
     }
   } else {
     const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
@@ -248,14 +251,22 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Columns per block of the sweep: at most 64, and the three shared-memory arrays of the
+// block's column rows within the default 48 KB (FP64).
+static int sweep_cpb_limit(int nlev) {
+  const int m = 2048 / ((nlev + 1) | 1);
+  return m < 1 ? 1 : (m > 64 ? 64 : m);
+}
+
 template <typename T, typename Tb, typename Tout, bool ZERO>
 static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int cpb_override = 0) {
   const Level &f = c->lv[0];
   SweepArgs a;
   a.d = dims_of(f);
   a.ncol = f.ncol;
-  const int cpb_max = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
-  a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb > 0 ? c->tune_sweep_cpb : cpb_max);
+  const int cpb_max = sweep_cpb_limit(f.nlev);
+  const int cpb_def = cpb_max < 32 ? cpb_max : 32;
+  a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb > 0 ? c->tune_sweep_cpb : cpb_def);
   if (a.cpb > cpb_max) a.cpb = cpb_max;
   a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
   a.stencil = f.edge_stencil;
@@ -264,7 +275,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
   if (threads > 256) threads = 256;
   const unsigned nhb = grid_for(f.nth, threads);
-  const size_t smem = (size_t)3 * a.cpb * (f.nlev + 1) * sizeof(T);
+  const size_t smem = (size_t)3 * a.cpb * ((f.nlev + 1) | 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
   sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
       a, Prec<T>::S(c), Prec<T>::Sz_w(c), Prec<T>::Sz_l(c), Prec<T>::Sz_cp(c), Prec<T>::Sh_w(c), b,
@@ -529,13 +540,14 @@ int time_sweep_cpb(Ctx *c, int cpb, float *ms) {
 
 int autotune(Ctx *c) {
   const Level &f = c->lv[0];
-  const int cmax = 256 / (f.nlev + 1) > 0 ? 256 / (f.nlev + 1) : 1;
-  int best = cmax;
+  const int cmax = sweep_cpb_limit(f.nlev);
+  const int cdef = cmax < 32 ? cmax : 32;
+  int best = cdef;
   float best_ms = 1e30f;
   const int profile = c->opt.profile;
   c->opt.profile = 0;
   int st = HMG_OK;
-  for (int cand : {cmax, cmax / 2, cmax / 4, 2, 1}) {
+  for (int cand : {32, 64, 16, 8, 4, 2, 1}) {
     if (cand < 1 || cand > cmax) continue;
     float ms = 0.f;
     if ((st = time_sweep_cpb(c, cand, &ms))) break;
@@ -544,10 +556,11 @@ int autotune(Ctx *c) {
   if (!st) c->tune_sweep_cpb = best;
   for (int l = 0; l < c->nmg && !st; ++l) {
     const int L = c->lv[l].nlev;
-    const int mmax = 256 / L > 0 ? 256 / L : 1;
-    int mbest = mmax;
+    const int mmax = mg_cpb_limit(L);
+    const int mdef = mmax < 32 ? mmax : 32;
+    int mbest = mdef;
     float mbest_ms = 1e30f;
-    for (int cand : {mmax, mmax / 2, mmax / 4, 2, 1}) {
+    for (int cand : {32, 64, 16, 8, 4, 2, 1}) {
       if (cand < 1 || cand > mmax) continue;
       float ms = 0.f;
       if ((st = time_mg_cpb(c, l, cand, &ms))) break;
