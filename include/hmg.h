@@ -200,8 +200,8 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
                       const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats);
 
 /* Time the candidate launch shapes of the line sweep and of the pressure smoother on each
- * level (columns of a column block per thread block) on this context's mesh and keep the
- * fastest; later launches of this context use them. Needs an assembled context; the sweep
+ * level (columns per thread block: 1-64; threads per block: 128 or 256) on this context's
+ * mesh and keep the fastest; later launches of this context use them. Needs an assembled context; the sweep
  * timings overwrite the context's work vectors. */
 int hmg_autotune(hmg_ctx *ctx);
 

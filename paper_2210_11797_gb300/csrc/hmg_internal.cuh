@@ -126,8 +126,8 @@ struct Ctx {
   } graph_key{};
   // autotuned launch shapes (0 = default): columns per block of the line sweep and of the
   // pressure smoother on each level
-  int tune_sweep_cpb = 0;
-  int tune_mg_cpb[kMaxLevels] = {0};
+  int tune_sweep_cpb = 0, tune_sweep_threads = 0;
+  int tune_mg_cpb[kMaxLevels] = {0}, tune_mg_threads[kMaxLevels] = {0};
   // learned coarse correction: FP32 master weights, one activation buffer, corner neighbours
   float *nn_w = nullptr;
   void *nn_act = nullptr;
@@ -237,9 +237,9 @@ int pressure_residual_fp64(Ctx *c, int level, const double *b, const double *x, 
 int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st);
 // Launch-shape autotuning of one context (columns per block of the sweep and MG smoother).
 int autotune(Ctx *c);
-// Sweep launch with explicit columns per block (autotuner).
-int time_sweep_cpb(Ctx *c, int cpb, float *ms);
-int time_mg_cpb(Ctx *c, int level, int cpb, float *ms);
+// Sweep / smoother launches with explicit columns and threads per block (autotuner).
+int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms);
+int time_mg_cpb(Ctx *c, int level, int cpb, int threads, float *ms);
 // Columns per block of the pressure smoother: at most 64, and its three shared-memory arrays
 // (column stride nlev rounded up to odd) within the default 48 KB (FP64).
 inline int mg_cpb_limit(int nlev) {

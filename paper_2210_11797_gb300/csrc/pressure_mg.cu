@@ -143,14 +143,16 @@ static MGArgs mg_args(const Ctx *c, int l) {
 }
 
 template <typename T, int MODE>
-static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0) {
+static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0, int threads_override = 0) {
   const Level &lv = c->lv[l];
   MGArgs a = mg_args(c, l);
   if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) a.cpb = cpb_override;
   const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
   const size_t smem = (size_t)3 * a.cpb * (lv.nlev | 1) * sizeof(T);
+  const int tmax = threads_override > 0 ? threads_override : (c->tune_mg_threads[l] > 0 ? c->tune_mg_threads[l] : 256);
   int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
-  if (threads > 256) threads = 256;
+  if (threads > tmax) threads = tmax;
+  if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
   mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_w(lv),
                                                              Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x,
                                                              out);
@@ -159,17 +161,17 @@ static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_overrid
 }
 
 // Average time of 5 FP64 smoothing sweeps on level l with `cpb` columns per block.
-int time_mg_cpb(Ctx *c, int l, int cpb, float *ms) {
+int time_mg_cpb(Ctx *c, int l, int cpb, int threads, float *ms) {
   Level &lv = c->lv[l];
   double *b = static_cast<double *>(lv.vb), *x = static_cast<double *>(lv.vx), *y = static_cast<double *>(lv.vy);
   HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * lv.ncell, c->stream));
   HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * lv.ncell, c->stream));
-  int st = smooth<double, 1>(c, l, b, x, y, cpb);
+  int st = smooth<double, 1>(c, l, b, x, y, cpb, threads);
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-  for (int i = 0; i < 5 && !st; ++i) st = smooth<double, 1>(c, l, b, x, y, cpb);
+  for (int i = 0; i < 5 && !st; ++i) st = smooth<double, 1>(c, l, b, x, y, cpb, threads);
   HMG_CUDA(c, cudaEventRecord(e1, c->stream));
   HMG_CUDA(c, cudaEventSynchronize(e1));
   cudaEventElapsedTime(ms, e0, e1);

@@ -259,7 +259,8 @@ static int sweep_cpb_limit(int nlev) {
 }
 
 template <typename T, typename Tb, typename Tout, bool ZERO>
-static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int cpb_override = 0) {
+static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int cpb_override = 0,
+                        int threads_override = 0) {
   const Level &f = c->lv[0];
   SweepArgs a;
   a.d = dims_of(f);
@@ -272,8 +273,10 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   a.stencil = f.edge_stencil;
   a.col_edges = f.col_edges;
   // threads: the column block's rows rounded up to whole warps (at most 256)
+  const int tmax = threads_override > 0 ? threads_override : (c->tune_sweep_threads > 0 ? c->tune_sweep_threads : 256);
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
-  if (threads > 256) threads = 256;
+  if (threads > tmax) threads = tmax;
+  if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
   const unsigned nhb = grid_for(f.nth, threads);
   const size_t smem = (size_t)3 * a.cpb * ((f.nlev + 1) | 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
@@ -517,18 +520,18 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
 namespace hmg {
 
 // Average time of 5 full FP64 sweeps with `cpb` columns per z-block (work vectors as data).
-int time_sweep_cpb(Ctx *c, int cpb, float *ms) {
+int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms) {
   const int64_t T = c->lv[0].ntrace;
   double *b = static_cast<double *>(c->w1), *x = static_cast<double *>(c->w2), *y = static_cast<double *>(c->w3);
   HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * T, c->stream));
   HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * T, c->stream));
   int st;
-  if ((st = launch_sweep<double, double, double, false>(c, b, x, y, cpb))) return st;   // warm-up
+  if ((st = launch_sweep<double, double, double, false>(c, b, x, y, cpb, threads))) return st;   // warm-up
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-  for (int i = 0; i < 5 && !st; ++i) st = launch_sweep<double, double, double, false>(c, b, x, y, cpb);
+  for (int i = 0; i < 5 && !st; ++i) st = launch_sweep<double, double, double, false>(c, b, x, y, cpb, threads);
   HMG_CUDA(c, cudaEventRecord(e1, c->stream));
   HMG_CUDA(c, cudaEventSynchronize(e1));
   cudaEventElapsedTime(ms, e0, e1);
@@ -541,32 +544,31 @@ int time_sweep_cpb(Ctx *c, int cpb, float *ms) {
 int autotune(Ctx *c) {
   const Level &f = c->lv[0];
   const int cmax = sweep_cpb_limit(f.nlev);
-  const int cdef = cmax < 32 ? cmax : 32;
-  int best = cdef;
+  int best = cmax < 32 ? cmax : 32, best_t = 256;
   float best_ms = 1e30f;
   const int profile = c->opt.profile;
   c->opt.profile = 0;
   int st = HMG_OK;
-  for (int cand : {32, 64, 16, 8, 4, 2, 1}) {
-    if (cand < 1 || cand > cmax) continue;
-    float ms = 0.f;
-    if ((st = time_sweep_cpb(c, cand, &ms))) break;
-    if (ms < best_ms) { best_ms = ms; best = cand; }
-  }
-  if (!st) c->tune_sweep_cpb = best;
-  for (int l = 0; l < c->nmg && !st; ++l) {
-    const int L = c->lv[l].nlev;
-    const int mmax = mg_cpb_limit(L);
-    const int mdef = mmax < 32 ? mmax : 32;
-    int mbest = mdef;
-    float mbest_ms = 1e30f;
-    for (int cand : {32, 64, 16, 8, 4, 2, 1}) {
-      if (cand < 1 || cand > mmax) continue;
+  for (int cand : {32, 64, 16, 8, 4, 2, 1})
+    for (int thr : {256, 128}) {
+      if (cand > cmax || st) continue;
       float ms = 0.f;
-      if ((st = time_mg_cpb(c, l, cand, &ms))) break;
-      if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; }
+      if ((st = time_sweep_cpb(c, cand, thr, &ms))) break;
+      if (ms < best_ms) { best_ms = ms; best = cand; best_t = thr; }
     }
-    if (!st) c->tune_mg_cpb[l] = mbest;
+  if (!st) { c->tune_sweep_cpb = best; c->tune_sweep_threads = best_t; }
+  for (int l = 0; l < c->nmg && !st; ++l) {
+    const int mmax = mg_cpb_limit(c->lv[l].nlev);
+    int mbest = mmax < 32 ? mmax : 32, mbest_t = 256;
+    float mbest_ms = 1e30f;
+    for (int cand : {32, 64, 16, 8, 4, 2, 1})
+      for (int thr : {256, 128}) {
+        if (cand > mmax || st) continue;
+        float ms = 0.f;
+        if ((st = time_mg_cpb(c, l, cand, thr, &ms))) break;
+        if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; mbest_t = thr; }
+      }
+    if (!st) { c->tune_mg_cpb[l] = mbest; c->tune_mg_threads[l] = mbest_t; }
   }
   c->opt.profile = profile;
   return st;
