@@ -370,6 +370,17 @@ def run_batched(args, rank, world):
         ms_total = float(t.item())
     ms_step = ms_total / args.steps
     T = sum(s.ntrace for s in solvers)
+    # the same solves one after another (each its own graph launch), for comparison
+    for s_, r1, r2, l_ in zip(solvers, Rubs, Rpis, lams):
+        s_.solve(r1, r2, l_)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for s_, r1, r2, l_ in zip(solvers, Rubs, Rpis, lams):
+        s_.solve(r1, r2, l_)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    ms_sequential = q0.elapsed_time(q1)
     out = {
         "metric": METRIC, "value": round(world * T / (ms_step / 1e3), 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
@@ -381,6 +392,7 @@ def run_batched(args, rank, world):
                    "iterations": [st["iterations"] for st in stats],
                    "max_true_rel_residual": max(st["true_rel_residual"] for st in stats),
                    "launch": "one CUDA graph per step, one WHILE-loop branch per solve",
+                   "sequential_ms": round(ms_sequential, 3),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "gpu_launches": None, "roofline": None,
         "clocks": clk.summary(),
