@@ -282,8 +282,11 @@ int32_t hmg_coarse_model_size(void);
 int hmg_set_coarse_model(hmg_ctx *ctx, const float *params, int32_t n);
 int hmg_get_coarse_model(hmg_ctx *ctx, float *params, int32_t n);
 
-/* out = D^-1/2 f(D^-1/2 bbar) on the finest mesh; bbar, out [ncell] device FP64. */
-int hmg_apply_coarse_model(hmg_ctx *ctx, const double *bbar, double *out, int32_t fp32);
+/* out = D^-1/2 f(D^-1/2 bbar) on the finest mesh; bbar, out [ncell] device FP64. mode 0: the
+ * solver's form, the 32 -> 32 convolution on the tensor cores (tcgen05.mma, BF16 operands,
+ * FP32 accumulator in tensor memory); 1: FP32 on the CUDA cores; 2: BF16 storage on the CUDA
+ * cores. Returns HMG_ERR_TIMEOUT if a bounded wait for the tensor cores ran out. */
+int hmg_apply_coarse_model(hmg_ctx *ctx, const double *bbar, double *out, int32_t mode);
 
 /* Training samples are nx x ny patches of columns (column q = j nx + i of a patch, the
  * regular grid's edge and corner neighbours, zero outside the patch): x, t [nsamp][nx ny]

@@ -139,6 +139,7 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   if (!st) st = dev_alloc(c, &c->counter, Scal::N);
   if (!st && cudaMemset(c->counter, 0, sizeof(unsigned int) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
   if (!st && cudaMemset(c->scal, 0, sizeof(double) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
+  if (!st && cudaMemset(c->state, 0, sizeof(int) * 4) != cudaSuccess) st = HMG_ERR_CUDA;
   if (st) {
     free_all(c);
     delete c;
@@ -497,6 +498,15 @@ int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
 }
 
 // ---- learned coarse correction -------------------------------------------------------------
+// A kernel whose bounded wait on the tensor cores ran out sets state[3] (the context stays usable).
+static int check_wait_flag(hmg_ctx *c) {
+  int flag = 0;
+  HMG_CUDA(c, cudaMemcpy(&flag, c->state + 3, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return HMG_OK;
+  HMG_CUDA(c, cudaMemset(c->state + 3, 0, sizeof(int)));
+  return fail(c, HMG_ERR_TIMEOUT, "a tensor-core wait of the coarse model ran out");
+}
+
 static int mesh_ready(hmg_ctx *c) {
   if (!c) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh) return fail(c, HMG_ERR_NOT_READY, "call hmg_set_mesh first");
@@ -524,12 +534,13 @@ int hmg_get_coarse_model(hmg_ctx *c, float *params, int32_t n) {
   return finish(c, HMG_OK);
 }
 
-int hmg_apply_coarse_model(hmg_ctx *c, const double *bbar, double *out, int32_t fp32) {
+int hmg_apply_coarse_model(hmg_ctx *c, const double *bbar, double *out, int32_t mode) {
   int st = ready(c);
   if (st) return st;
-  if (!bbar || !out || bbar == out) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  if (!bbar || !out || bbar == out || mode < 0 || mode > 2) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
   if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
-  return finish(c, apply_coarse_model(c, bbar, out, fp32 ? 1 : 0));
+  if ((st = finish(c, apply_coarse_model(c, bbar, out, mode)))) return st;
+  return check_wait_flag(c);
 }
 
 static int check_patches(hmg_ctx *c, const float *x, const float *t, int32_t nsamp, int32_t nx, int32_t ny) {

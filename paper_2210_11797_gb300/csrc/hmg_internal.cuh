@@ -111,11 +111,12 @@ struct Ctx {
   unsigned int *counter = nullptr;  // device [Scal::N] tickets of the last-block reductions
   double *scal_host = nullptr; // pinned [Scal::N]
   double *host_in = nullptr;   // device staging for hmg_solve_host (Rub | Rpi | lambda)
-  // device-side iteration state of the Krylov loop: [0] completed iterations, [1] status;
+  // device-side iteration state of the Krylov loop: [0] completed iterations, [1] status,
+  // [2] continue flag, [3] set by a kernel whose bounded wait ran out;
   // hist[i] = ||r_i|| / ||B|| (i = 0 .. iterations)
   int *state = nullptr;
   double *hist = nullptr;
-  int *state_host = nullptr;   // pinned [2]
+  int *state_host = nullptr;   // pinned [4]
   // whole-solve CUDA graph (B_lambda, a WHILE node over BiCGStab iterations, final residual)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -222,7 +223,8 @@ constexpr int kCoarseParams = 3360;
 int nn_setup(Ctx *c);
 template <typename T>
 int learned_coarse(Ctx *c, const T *bbar, T *out);
-int apply_coarse_model(Ctx *c, const double *bbar, double *out, int fp32);
+// mode 0: BF16 on the tensor cores (the solver's form); 1: FP32 and 2: BF16 on the CUDA cores
+int apply_coarse_model(Ctx *c, const double *bbar, double *out, int mode);
 int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int fp32,
                       float *grad_host, double *loss_host);
 int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int batch,

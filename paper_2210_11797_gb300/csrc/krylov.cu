@@ -24,7 +24,7 @@ static unsigned red_grid(int64_t n) {
   return g < (unsigned)kRedBlocks ? g : (unsigned)kRedBlocks;
 }
 
-enum { kIt = 0, kStatus = 1, kContinue = 2 };
+enum { kIt = 0, kStatus = 1, kContinue = 2, kWaitFlag = 3 };
 
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *part,
@@ -296,6 +296,7 @@ static int status_message(Ctx *c, int status) {
   const std::string name = c->opt.krylov == HMG_KRYLOV_FGMRES ? "FGMRES" : "BiCGStab";
   const std::string why = status == HMG_ERR_NOT_CONVERGED ? name + " did not converge"
                           : status == HMG_ERR_BREAKDOWN  ? name + " breakdown"
+                          : status == HMG_ERR_TIMEOUT    ? "a bounded device-side wait ran out"
                                                          : "non-finite value in " + name;
   return fail(c, status, why);
 }
@@ -303,10 +304,15 @@ static int status_message(Ctx *c, int status) {
 // Copies the loop state, history and scalars to the host (stream-ordered) and fills stats.
 static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
   HMG_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal, sizeof(double) * Scal::N, cudaMemcpyDeviceToHost, c->stream));
-  HMG_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
   if (st) HMG_CUDA(c, cudaMemcpyAsync(st->history, c->hist, sizeof(double) * HMG_MAX_HISTORY, cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  const int it = c->state_host[kIt], status = c->state_host[kStatus];
+  const int it = c->state_host[kIt];
+  int status = c->state_host[kStatus];
+  if (c->state_host[kWaitFlag]) {   // a bounded device-side wait ran out during the solve
+    HMG_CUDA(c, cudaMemsetAsync(c->state + kWaitFlag, 0, sizeof(int), c->stream));
+    status = HMG_ERR_TIMEOUT;
+  }
   if (st) {
     const double bb = c->scal_host[Scal::BB];
     const double bnorm = std::sqrt(bb);

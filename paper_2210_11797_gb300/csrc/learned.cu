@@ -124,6 +124,149 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// ---- forward, column-local layers on the tensor cores (inference, BF16) ---------------------
+// h2 = relu(conv(32 -> 32, 3)(h1)) as a GEMM per tile of 128 consecutive cells:
+//   H2[m][o] = sum_kk A[m][kk] B[o][kk],  kk = d * 32 + i,  A[m][kk] = h1[i](cell m + d - 1),
+//   B[o][kk] = W2[o][i][d],
+// with A (128 x 96) and B (32 x 96) in BF16 in shared memory, K-major without swizzle (8 x 16 B
+// core matrices: along M/N every 128 B, along K every (rows / 8) * 128 B), one
+// tcgen05.mma (M 128, N 32, K 16) per 16 columns of K issued by one thread, the FP32
+// accumulator in 32 TMEM columns, read back by the four warps (warp w owns lanes 32w..32w+31).
+// h1 = relu(conv(1 -> 32, 3)(x)) is computed on the fly while A is written (3 FMAs per entry).
+constexpr int kTcM = 128;
+constexpr int kTcAWindow = 64 * 1024;     // A region: 24 KB used, the rest keeps any descriptor
+constexpr int kTcB = kTcAWindow;          // stride within the CTA's shared memory
+constexpr int kTcBWindow = 8 * 1024;      // B region: 6 KB used
+constexpr int kTcX = kTcB + kTcBWindow;   // x staging: 132 floats
+constexpr int kTcBar = kTcX + 1024;       // mbarrier (8 B) and the TMEM address (4 B)
+constexpr int kTcSmem = kTcBar + 64;
+constexpr uint32_t kTcWaitLimit = 1u << 24;   // mbarrier polls before the kernel gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+  return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(128)
+    nn_front_tc_kernel(const float *__restrict__ wts, const Tin *__restrict__ xin,
+                       const double *__restrict__ diagH, const float *__restrict__ diagH32, int64_t ncell,
+                       int L, __nv_bfloat16 *__restrict__ h2_out, int *__restrict__ wait_flag) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
+  float *xs = reinterpret_cast<float *>(tc_smem + kTcX);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + kTcBar);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + kTcBar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+
+  if (warp == 0) {   // 32 TMEM columns for the 128 x 32 FP32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // x on cells m0-2 .. m0+129 (scaled by diag(H)^-1/2 and rounded to BF16), 0 outside the mesh
+  for (int j = tid; j < kTcM + 4; j += blockDim.x) {
+    const int64_t q = m0 - 2 + j;
+    float v = 0.f;
+    if (q >= 0 && q < ncell) {
+      float sc = 1.f;
+      if (diagH) sc = (float)(1.0 / sqrt(diagH[q]));
+      else if (diagH32) sc = rsqrtf(diagH32[q]);
+      v = rnd<__nv_bfloat16>((float)xin[q] * sc);
+    }
+    xs[j] = v;
+  }
+  // B = W2 as [o][d * 32 + i] in core-matrix order (N = 32 rows: 4 row groups)
+  for (int e = tid; e < 32 * 96; e += blockDim.x) {
+    const int o = e / 96, kk = e % 96, d = kk / 32, i = kk % 32;
+    const uint32_t off = (uint32_t)(((kk >> 3) * 4 + (o >> 3)) * 128 + (o & 7) * 16 + (kk & 7) * 2);
+    *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16(wts[kOffW2 + (o * 32 + i) * 3 + d]);
+  }
+  __syncthreads();
+  // A: im2col of h1 (M = 128 rows: 16 row groups)
+  for (int e = tid; e < kTcM * 96; e += blockDim.x) {
+    const int m = e / 96, kk = e % 96, d = kk / 32, i = kk % 32;
+    const int64_t cell = m0 + m;
+    float h = 0.f;
+    if (cell < ncell) {
+      const int k = (int)(cell % L), kd = k + d - 1;     // level of the tap, same column
+      if (kd >= 0 && kd < L) {
+        const int j = m + d + 1;                          // xs index of cell + d - 1
+        const float xm = kd - 1 >= 0 ? xs[j - 1] : 0.f, x0 = xs[j], xp = kd + 1 < L ? xs[j + 1] : 0.f;
+        const float *w1 = wts + kOffW1 + 3 * i;
+        const float w0 = rnd<__nv_bfloat16>(w1[0]), wc = rnd<__nv_bfloat16>(w1[1]), wp = rnd<__nv_bfloat16>(w1[2]);
+        h = rnd<__nv_bfloat16>(fmaxf(fmaf(w0, xm, fmaf(wc, x0, wp * xp)), 0.f));
+      }
+    }
+    const uint32_t off = (uint32_t)(((kk >> 3) * (kTcM / 8) + (m >> 3)) * 128 + (m & 7) * 16 + (kk & 7) * 2);
+    *reinterpret_cast<__nv_bfloat16 *>(sA + off) = __float2bfloat16(h);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    const uint32_t idesc = umma_idesc_bf16(kTcM, 32);
+    for (int s = 0; s < 6; ++s) {   // K = 96 in steps of 16 (two core matrices along K)
+      const uint64_t ad = umma_desc(a0 + s * 2 * (kTcM / 8) * 128, (kTcM / 8) * 128, 128);
+      const uint64_t bd = umma_desc(b0 + s * 2 * 4 * 128, 4 * 128, 128);
+      const uint32_t acc = s > 0 ? 1u : 0u;
+      asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+  }
+  // wait for the MMAs (bounded)
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+  }
+  if (!done) atomicExch(wait_flag, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done) {
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int64_t cell = m0 + warp * 32 + lane;
+    if (cell < ncell) {
+#pragma unroll
+      for (int o = 0; o < 32; ++o)
+        h2_out[(int64_t)o * ncell + cell] = __float2bfloat16(fmaxf(__uint_as_float(r[o]), 0.f));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
 // ---- forward, horizontal mix and output layer: h2 -> h3 -> y ---------------------------------
 // mesh: out[K] = y * yscale(K) (yscale = 1/sqrt(diag H)) written as Tout.
 // training: also stores h3 and, for the loss, gy = 2 (y - t) / (||t_s||^2 B) and the per-block
@@ -481,14 +624,21 @@ static int nn_attrs(Ctx *c) {
   return HMG_OK;
 }
 
-template <typename A, typename Tin, typename Tout>
+// TC: the column-local layers on the tensor cores (A must be BF16), else on the CUDA cores.
+template <typename A, typename Tin, typename Tout, bool TC>
 static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH, const float *dH32) {
   const Level &f = c->lv[0];
   const int L = f.nlev;
   A *h2 = reinterpret_cast<A *>(c->nn_act);
   const unsigned g = (unsigned)((f.ncol + kNnCpb - 1) / kNnCpb);
-  nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
-                                                                        kNnCpb, nullptr, h2);
+  if (TC) {
+    static_assert(!TC || sizeof(A) == 2, "the tensor-core layers store BF16");
+    nn_front_tc_kernel<Tin><<<grid_for(f.ncell, kTcM), 128, kTcSmem, c->stream>>>(
+        c->nn_w, bbar, dH, dH32, f.ncell, L, reinterpret_cast<__nv_bfloat16 *>(h2), c->state + 3);
+  } else {
+    nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
+                                                                          kNnCpb, nullptr, h2);
+  }
   Nbrs nb{f.col_nbr, c->nn_diag, 0, 0};
   nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
       c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
@@ -503,7 +653,7 @@ int learned_coarse(Ctx *c, const T *bbar, T *out) {
   const double *dH = nullptr;
   const float *dH32 = nullptr;
   if (sizeof(T) == 8) dH = c->lv[0].H; else dH32 = c->lv[0].H32;   // row 0 of H = its diagonal
-  return nn_forward_mesh<__nv_bfloat16, T, T>(c, bbar, out, dH, dH32);
+  return nn_forward_mesh<__nv_bfloat16, T, T, true>(c, bbar, out, dH, dH32);
 }
 template int learned_coarse<double>(Ctx *, const double *, double *);
 template int learned_coarse<float>(Ctx *, const float *, float *);
@@ -518,6 +668,8 @@ int nn_setup(Ctx *c) {
   if ((st = nn_attrs<float, double, double>(c))) return st;
   if ((st = nn_attrs<float, float, float>(c))) return st;
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   if ((st = dev_alloc(c, &c->nn_w, kNParams))) return st;
   float *tmp;
@@ -679,11 +831,12 @@ int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, con
   return HMG_OK;
 }
 
-int apply_coarse_model(Ctx *c, const double *bbar, double *out, int fp32) {
+int apply_coarse_model(Ctx *c, const double *bbar, double *out, int mode) {
   int st = nn_setup(c);
   if (st) return st;
-  if (fp32) return nn_forward_mesh<float, double, double>(c, bbar, out, c->lv[0].H, nullptr);
-  return nn_forward_mesh<__nv_bfloat16, double, double>(c, bbar, out, c->lv[0].H, nullptr);
+  if (mode == 1) return nn_forward_mesh<float, double, double, false>(c, bbar, out, c->lv[0].H, nullptr);
+  if (mode == 2) return nn_forward_mesh<__nv_bfloat16, double, double, false>(c, bbar, out, c->lv[0].H, nullptr);
+  return nn_forward_mesh<__nv_bfloat16, double, double, true>(c, bbar, out, c->lv[0].H, nullptr);
 }
 
 // ---- training pairs from the solver itself -----------------------------------------------------

@@ -344,10 +344,13 @@ class Solver:
         _check(self.ctx, lib().hmg_get_coarse_model(self.ctx, p.ctypes.data_as(C.c_void_p), p.size))
         return p
 
-    def apply_coarse_model(self, bbar, fp32=False):
+    MODEL_MODES = {"tensor": 0, "fp32": 1, "bf16": 2}
+
+    def apply_coarse_model(self, bbar, mode="tensor"):
+        """mode: "tensor" (BF16 on the tensor cores, the solver's form), "fp32" or "bf16" (CUDA cores)."""
         out = self._empty(self.ncell)
         _check(self.ctx, lib().hmg_apply_coarse_model(self.ctx, self._dev(bbar, self.ncell, "bbar"), _ptr(out),
-                                                      1 if fp32 else 0))
+                                                      self.MODEL_MODES[mode]))
         return out
 
     def _patches(self, x, t, nx, ny):

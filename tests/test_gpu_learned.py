@@ -71,10 +71,15 @@ def test_forward_matches_oracle(name):
     gpu.set_coarse_model(I.flatten_coarse_model(params))
     b = I.normal(11, gpu.ncell)
     ref = _oracle_coarse_model(ora, _rounded(params))(b)
-    out32 = _np(gpu.apply_coarse_model(_cuda(b), fp32=True))
+    out32 = _np(gpu.apply_coarse_model(_cuda(b), mode="fp32"))
     assert np.abs(out32 - ref).max() / np.abs(ref).max() < 1e-4
-    out16 = _np(gpu.apply_coarse_model(_cuda(b), fp32=False))
+    out16 = _np(gpu.apply_coarse_model(_cuda(b), mode="bf16"))
     assert np.linalg.norm(out16 - ref) / np.linalg.norm(ref) < 5e-2
+    # the tensor-core form (tcgen05, BF16 in, FP32 accumulate): the same BF16 arithmetic up to
+    # the order of the 96-term sums, so it stays within a few BF16 roundings of the CUDA-core form
+    outtc = _np(gpu.apply_coarse_model(_cuda(b), mode="tensor"))
+    assert np.linalg.norm(outtc - ref) / np.linalg.norm(ref) < 5e-2
+    assert np.linalg.norm(outtc - out16) / np.linalg.norm(out16) < 1e-2
     # the model round-trips through the ABI unchanged
     np.testing.assert_array_equal(gpu.get_coarse_model(), I.flatten_coarse_model(params))
 
