@@ -133,6 +133,7 @@ struct Ctx {
   float *nn_w = nullptr;
   void *nn_act = nullptr;
   int32_t *nn_diag = nullptr;
+  void *nn_bimg = nullptr;        // W2 as the BF16 B operand image of the tensor-core layer (6 KB)
   TrainBufs train;
   bool coarse_fallback = false;   // set by the flexible Krylov loop when it stalls
   // collection of (scaled bbar, scaled H^-1 bbar) pairs at the preconditioner calls

@@ -27,6 +27,7 @@ constexpr int kOffW1 = 0, kOffW2 = 96, kOffM = 96 + 3072, kOffW3 = 96 + 3072 + 9
 constexpr int kNParams = kOffW3 + 96;   // 3360
 static_assert(kNParams == kCoarseParams, "parameter count");
 constexpr int kMaxL = 128;              // levels a column may have for the network kernels
+constexpr int kMaxNnCpb = 16;           // columns per block of the horizontal-mix kernel (at most)
 
 template <typename A>
 __device__ __forceinline__ float to_f(A v);
@@ -137,8 +138,8 @@ constexpr int kTcM = 128;
 constexpr int kTcAWindow = 64 * 1024;     // A region: 24 KB used, the rest keeps any descriptor
 constexpr int kTcB = kTcAWindow;          // stride within the CTA's shared memory
 constexpr int kTcBWindow = 8 * 1024;      // B region: 6 KB used
-constexpr int kTcX = kTcB + kTcBWindow;   // x staging: 132 floats
-constexpr int kTcBar = kTcX + 1024;       // mbarrier (8 B) and the TMEM address (4 B)
+constexpr int kTcX = kTcB + kTcBWindow;   // x (132 floats), W1 (96 floats), row levels (128 ints)
+constexpr int kTcBar = kTcX + 2048;       // two mbarriers (16 B) and the TMEM address (4 B)
 constexpr int kTcSmem = kTcBar + 64;
 constexpr uint32_t kTcWaitLimit = 1u << 24;   // mbarrier polls before the kernel gives up
 
@@ -160,16 +161,36 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// W2 -> the B operand image: B[o][d * 32 + i] in BF16, core-matrix order (N = 32: 4 row groups)
+__global__ void nn_pack_b_kernel(const float *__restrict__ wts, __nv_bfloat16 *__restrict__ bimg) {
+  for (int e = threadIdx.x; e < 32 * 96; e += blockDim.x) {
+    const int o = e / 96, kk = e % 96, d = kk / 32, i = kk % 32;
+    const int off = ((kk >> 3) * 4 + (o >> 3)) * 64 + (o & 7) * 8 + (kk & 7);   // in elements
+    bimg[off] = __float2bfloat16(wts[kOffW2 + (o * 32 + i) * 3 + d]);
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(128)
-    nn_front_tc_kernel(const float *__restrict__ wts, const Tin *__restrict__ xin,
-                       const double *__restrict__ diagH, const float *__restrict__ diagH32, int64_t ncell,
-                       int L, __nv_bfloat16 *__restrict__ h2_out, int *__restrict__ wait_flag) {
+    nn_front_tc_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ bimg,
+                       const Tin *__restrict__ xin, const double *__restrict__ diagH,
+                       const float *__restrict__ diagH32, int64_t ncell, int L,
+                       __nv_bfloat16 *__restrict__ h2_out, int *__restrict__ wait_flag) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
-  float *xs = reinterpret_cast<float *>(tc_smem + kTcX);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + kTcBar);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + kTcBar + 8);
+  float *xs = reinterpret_cast<float *>(tc_smem + kTcX);            // 132 floats
+  float *w1s = xs + kTcM + 4;                                        // 96 floats
+  int *lev = reinterpret_cast<int *>(w1s + 96);                      // 128 ints: level of row m
+  uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + kTcBar);   // [0] MMA done, [1] B loaded
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + kTcBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * kTcM;
 
@@ -179,9 +200,14 @@ __global__ void __launch_bounds__(128)
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    // B (6 KB) by the bulk-copy engine
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar + 1)), "r"(6144));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(sB)), "l"(bimg), "r"(6144), "r"(smem_u32(bar + 1)) : "memory");
   }
-  // x on cells m0-2 .. m0+129 (scaled by diag(H)^-1/2 and rounded to BF16), 0 outside the mesh
+  // x on cells m0-2 .. m0+129 (scaled by diag(H)^-1/2, rounded to BF16), 0 outside the mesh
   for (int j = tid; j < kTcM + 4; j += blockDim.x) {
     const int64_t q = m0 - 2 + j;
     float v = 0.f;
@@ -193,30 +219,36 @@ __global__ void __launch_bounds__(128)
     }
     xs[j] = v;
   }
-  // B = W2 as [o][d * 32 + i] in core-matrix order (N = 32 rows: 4 row groups)
-  for (int e = tid; e < 32 * 96; e += blockDim.x) {
-    const int o = e / 96, kk = e % 96, d = kk / 32, i = kk % 32;
-    const uint32_t off = (uint32_t)(((kk >> 3) * 4 + (o >> 3)) * 128 + (o & 7) * 16 + (kk & 7) * 2);
-    *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16(wts[kOffW2 + (o * 32 + i) * 3 + d]);
+  if (tid < 96) w1s[tid] = rnd<__nv_bfloat16>(wts[kOffW1 + tid]);
+  {
+    const int64_t cell = m0 + tid;   // 128 threads, one row each
+    lev[tid] = cell < ncell ? (int)(cell % L) : -1;
   }
   __syncthreads();
-  // A: im2col of h1 (M = 128 rows: 16 row groups)
-  for (int e = tid; e < kTcM * 96; e += blockDim.x) {
-    const int m = e / 96, kk = e % 96, d = kk / 32, i = kk % 32;
-    const int64_t cell = m0 + m;
-    float h = 0.f;
-    if (cell < ncell) {
-      const int k = (int)(cell % L), kd = k + d - 1;     // level of the tap, same column
-      if (kd >= 0 && kd < L) {
-        const int j = m + d + 1;                          // xs index of cell + d - 1
-        const float xm = kd - 1 >= 0 ? xs[j - 1] : 0.f, x0 = xs[j], xp = kd + 1 < L ? xs[j + 1] : 0.f;
-        const float *w1 = wts + kOffW1 + 3 * i;
-        const float w0 = rnd<__nv_bfloat16>(w1[0]), wc = rnd<__nv_bfloat16>(w1[1]), wp = rnd<__nv_bfloat16>(w1[2]);
-        h = rnd<__nv_bfloat16>(fmaxf(fmaf(w0, xm, fmaf(wc, x0, wp * xp)), 0.f));
+  // A: im2col of h1, 16 B (8 channels of one tap of one row) per store: (m, d, g) items
+  for (int e = tid; e < kTcM * 12; e += blockDim.x) {
+    const int m = e / 12, r = e % 12, d = r >> 2, g = r & 3;
+    const int k = lev[m], kd = k + d - 1;
+    uint4 pack = make_uint4(0u, 0u, 0u, 0u);
+    if (k >= 0 && kd >= 0 && kd < L) {
+      const int j = m + d + 1;                       // xs index of the tap cell
+      const float xm = kd > 0 ? xs[j - 1] : 0.f, x0 = xs[j], xp = kd + 1 < L ? xs[j + 1] : 0.f;
+      uint32_t wds[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float hv[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const float *w = w1s + 3 * (g * 8 + 2 * q + t);
+          hv[t] = fmaxf(fmaf(w[0], xm, fmaf(w[1], x0, w[2] * xp)), 0.f);
+        }
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(hv[0], hv[1]);
+        wds[q] = *reinterpret_cast<const uint32_t *>(&b2);
       }
+      pack = make_uint4(wds[0], wds[1], wds[2], wds[3]);
     }
-    const uint32_t off = (uint32_t)(((kk >> 3) * (kTcM / 8) + (m >> 3)) * 128 + (m & 7) * 16 + (kk & 7) * 2);
-    *reinterpret_cast<__nv_bfloat16 *>(sA + off) = __float2bfloat16(h);
+    const uint32_t off = (uint32_t)(((d * 4 + g) * (kTcM / 8) + (m >> 3)) * 128 + (m & 7) * 16);
+    *reinterpret_cast<uint4 *>(sA + off) = pack;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -224,24 +256,24 @@ __global__ void __launch_bounds__(128)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   if (tid == 0) {
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-    const uint32_t idesc = umma_idesc_bf16(kTcM, 32);
-    for (int s = 0; s < 6; ++s) {   // K = 96 in steps of 16 (two core matrices along K)
-      const uint64_t ad = umma_desc(a0 + s * 2 * (kTcM / 8) * 128, (kTcM / 8) * 128, 128);
-      const uint64_t bd = umma_desc(b0 + s * 2 * 4 * 128, 4 * 128, 128);
-      const uint32_t acc = s > 0 ? 1u : 0u;
-      asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    if (mbar_wait(bar + 1, 0)) {
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t idesc = umma_idesc_bf16(kTcM, 32);
+      for (int s = 0; s < 6; ++s) {   // K = 96 in steps of 16 (two core matrices along K)
+        const uint64_t ad = umma_desc(a0 + s * 2 * (kTcM / 8) * 128, (kTcM / 8) * 128, 128);
+        const uint64_t bd = umma_desc(b0 + s * 2 * 4 * 128, 4 * 128, 128);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+    } else {
+      atomicExch(wait_flag, 1);
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)));   // release the waiters
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
   }
-  // wait for the MMAs (bounded)
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(smem_u32(bar)) : "memory");
-  }
+  const bool done = mbar_wait(bar, 0);
   if (!done) atomicExch(wait_flag, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
@@ -282,20 +314,26 @@ __global__ void __launch_bounds__(128)
   float *Mw = sm, *W3 = Mw + 96;
   float *h3 = W3 + 96;                          // [cpb][32][L+2]
   __shared__ double red[4];
+  __shared__ int snb[kMaxNnCpb][8];             // edge and corner neighbours of the block's columns
   for (int i = threadIdx.x; i < 96; i += blockDim.x) {
     Mw[i] = rnd<A>(wts[kOffM + i]);
     W3[i] = rnd<A>(wts[kOffW3 + i]);
   }
   const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
   const int64_t C = (int64_t)ncol * L;
+  if ((int)threadIdx.x < nc) {
+    int e[4], d[4];
+    nb.get(c0 + threadIdx.x, e, d);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { snb[threadIdx.x][q] = e[q]; snb[threadIdx.x][4 + q] = d[q]; }
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < cpb * kCh * (L + 2); i += blockDim.x) {
     const int cc = i / (kCh * (L + 2)), r = i % (kCh * (L + 2)), ch = r / (L + 2), k = r % (L + 2) - 1;
     float v = 0.f;
     if (cc < nc && k >= 0 && k < L) {
       const int col = c0 + cc;
-      int e[4], d[4];
-      nb.get(col, e, d);
+      const int *e = snb[cc], *d = snb[cc] + 4;
       const A *hc = h2 + (int64_t)ch * C;
       float se = 0.f, sd = 0.f;
 #pragma unroll
@@ -633,8 +671,10 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
   const unsigned g = (unsigned)((f.ncol + kNnCpb - 1) / kNnCpb);
   if (TC) {
     static_assert(!TC || sizeof(A) == 2, "the tensor-core layers store BF16");
+    nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
     nn_front_tc_kernel<Tin><<<grid_for(f.ncell, kTcM), 128, kTcSmem, c->stream>>>(
-        c->nn_w, bbar, dH, dH32, f.ncell, L, reinterpret_cast<__nv_bfloat16 *>(h2), c->state + 3);
+        c->nn_w, static_cast<const __nv_bfloat16 *>(c->nn_bimg), bbar, dH, dH32, f.ncell, L,
+        reinterpret_cast<__nv_bfloat16 *>(h2), c->state + 3);
   } else {
     nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
                                                                           kNnCpb, nullptr, h2);
@@ -672,6 +712,11 @@ int nn_setup(Ctx *c) {
   HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   if ((st = dev_alloc(c, &c->nn_w, kNParams))) return st;
+  {
+    __nv_bfloat16 *bimg;
+    if ((st = dev_alloc(c, &bimg, (size_t)32 * 96))) return st;   // cudaMalloc: 256-B aligned
+    c->nn_bimg = bimg;
+  }
   float *tmp;
   if ((st = dev_alloc(c, &tmp, (size_t)kCh * f.ncell))) return st;   // BF16 h2 fits in half
   c->nn_act = tmp;
