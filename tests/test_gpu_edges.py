@@ -1,0 +1,125 @@
+"""Edge cases of the CUDA path against the FP64 oracle: ragged sizes (column counts and level
+counts that fill no launch shape evenly), a single layer, a single multigrid level, an odd
+cubed-sphere panel, a zero right-hand side, and the largest workload (C192 x 30, sampled
+rows). Tolerances as in test_gpu_parity: whole solves converged to 1e-12 on both sides agree
+to a relative 2-norm difference below 1e-9."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import fem
+from oracle.nonnested import HybridSolver
+from paper_2210_11797_gb300 import inputs as I
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+CASES = {
+    "planar6x6x7": lambda: I.planar_helmholtz(n=6, nlev=7, nmg=2, seed=1),
+    "planar8x8x1": lambda: I.planar_helmholtz(n=8, nlev=1, nmg=2, seed=2),
+    "planar8x8x5_one_mg_level": lambda: I.planar_helmholtz(n=8, nlev=5, nmg=1, seed=3),
+    "sphereC3L4": lambda: I.cubed_sphere(3, 4, seed=4),
+    "sphereC10L9": lambda: I.cubed_sphere(10, 9, seed=5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("krylov", ["bicgstab", "fgmres"])
+def test_small_and_ragged_solves_match_oracle(name, krylov):
+    from paper_2210_11797_gb300.hmg import Solver
+    w = CASES[name]()
+    ora = HybridSolver(w.hier, w.coeffs)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-12, max_iter=400, krylov=krylov)
+    gpu.autotune()
+    lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-11
+    ref, _hist, status = ora.solve(w.Rub, w.Rpi, 1e-12, maxit=400)
+    assert status == "ok"
+    assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-9
+    # the host-buffer path gives the same lambda
+    lam_h, st_h = gpu.solve_host(w.Rub.ravel(), w.Rpi)
+    np.testing.assert_array_equal(lam_h, _np(lam))
+    # and the recovered (u, Pi) satisfies the cell equations as the oracle's does
+    ub, pi = gpu.reconstruct(lam, _cuda(w.Rub.ravel()), _cuda(w.Rpi))
+    ub_o, pi_o = ora.reconstruct(ref, w.Rub, w.Rpi)
+    assert np.linalg.norm(_np(pi) - pi_o.ravel()) <= 1e-8 * np.linalg.norm(pi_o)
+    assert np.linalg.norm(_np(ub) - ub_o.ravel()) <= 1e-8 * np.linalg.norm(ub_o)
+    gpu.close()
+
+
+@pytest.mark.parametrize("krylov", ["bicgstab", "fgmres"])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_zero_right_hand_side(krylov, graph):
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz()
+    gpu = Solver(w.hier, w.coeffs, tol=1e-10, krylov=krylov, graph=graph)
+    lam = _cuda(np.full(gpu.ntrace, 7.0))       # overwritten: the iteration starts from zero
+    lam, st = gpu.solve(_cuda(np.zeros(6 * gpu.ncell)), _cuda(np.zeros(gpu.ncell)), lam)
+    assert st["status"] == "ok" and st["iterations"] == 0
+    assert not np.any(_np(lam))
+    gpu.close()
+
+
+def test_tolerance_one_and_zero_iterations():
+    """tol >= 1 is met by lambda = 0 before any iteration; max_iter = 0 below it is reported."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz()
+    gpu = Solver(w.hier, w.coeffs, tol=1.0)
+    lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["iterations"] == 0 and not np.any(_np(lam))
+    gpu.set_options(tol=1e-6, max_iter=0)
+    _lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi), check=False)
+    assert st["status"] == "not_converged" and st["iterations"] == 0
+    gpu.close()
+
+
+def test_largest_workload_c192_sampled_rows():
+    """C192 x 30 (6.6M cells, 20.1M trace unknowns): sampled rows of S x against the
+    oracle's cell matrices of the cells touching them, and the solve to 1e-6."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(192, 30)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-6)
+    mesh, bg, co = w.mesh, w.coeffs.levels[0], w.coeffs
+    rng = np.random.default_rng(11)
+    L = mesh.nlev
+    rows = np.unique(np.concatenate([rng.integers(0, mesh.n_trace_h, 200),
+                                     rng.integers(mesh.n_trace_h, mesh.n_trace, 200),
+                                     [0, mesh.n_trace_h - 1, mesh.n_trace_h, mesh.n_trace - 1]]))
+    cells = []
+    for r in rows:
+        if r < mesh.n_trace_h:
+            e, k = divmod(int(r), L)
+            cells += [mesh.edge_cols[e, 0] * L + k, mesh.edge_cols[e, 1] * L + k]
+        else:
+            c, k = divmod(int(r) - mesh.n_trace_h, L + 1)
+            if k < L:
+                cells.append(c * L + k)
+            if k > 0:
+                cells.append(c * L + k - 1)
+    cells = np.unique(cells)
+    A, Kd, _cc = fem.cell_system(mesh, bg, co, cells=cells)
+    SK = fem.condense(A, Kd)
+    g = fem.trace_dof_ids(mesh, cells)
+    x = rng.standard_normal(gpu.ntrace)
+    y = _np(gpu.apply_trace(_cuda(x)))
+    want, scale = np.zeros(len(rows)), np.zeros(len(rows))
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for ci in range(len(cells)):
+        for i in range(6):
+            j = pos.get(int(g[ci, i]))
+            if j is not None:
+                want[j] += SK[ci, i] @ x[g[ci]]
+                scale[j] += np.abs(SK[ci, i]) @ np.abs(x[g[ci]])
+    assert np.all(np.abs(y[rows] - want) <= 1e-12 * scale)
+    _lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] <= 1.05e-6
+    gpu.close()
