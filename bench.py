@@ -120,6 +120,22 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job is done when every replica is): an all-reduce MAX of
+    one number over the process group (NCCL on the GPUs; gloo in the CPU tests)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rhs_seed(rank: int) -> int:
+    """Rank r > 0 solves its own right-hand side (seed r); rank 0 the workload's (seed 0)."""
+    return rank
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -138,7 +154,7 @@ def run_ours(args, rank, world):
     w = workload_spec(args.workload)
     if rank:                                   # replicas: independent right-hand sides
         from paper_2210_11797_gb300 import inputs as I
-        w.Rub, w.Rpi = I.draw_rhs(w.mesh.ncell, rank, "normal")
+        w.Rub, w.Rpi = I.draw_rhs(w.mesh.ncell, replica_rhs_seed(rank), "normal")
     stream = torch.cuda.current_stream()
     # the solve runs as one CUDA graph (device-side BiCGStab loop); the component timers need
     # host-recorded events, so they run in a second timed pass of the same steps (host loop)
@@ -167,11 +183,7 @@ def run_ours(args, rank, world):
     torch.cuda.cudart().cudaProfilerStop()
     if world > 1:
         torch.distributed.barrier()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ms_step = ms_total / args.steps
     T = solver.ntrace
     value = world * T / (ms_step / 1e3)
@@ -363,11 +375,7 @@ def run_batched(args, rank, world):
             _l, stats = solve_batched(solvers, Rubs, Rpis, lams)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ms_step = ms_total / args.steps
     T = sum(s.ntrace for s in solvers)
     # the same solves one after another (each its own graph launch), for comparison
