@@ -263,12 +263,12 @@ def _timed_solves(solver, Rub, Rpi, stream, steps):
     import torch
     lam = torch.empty(solver.ntrace, dtype=torch.float64, device="cuda")
     for _ in range(2):
-        solver.solve(Rub, Rpi, lam)
+        solver.solve(Rub, Rpi, lam, check=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        _l, st = solver.solve(Rub, Rpi, lam)
+        _l, st = solver.solve(Rub, Rpi, lam, check=False)
     e1.record(stream)
     torch.cuda.synchronize()
     return lam, st, e0.elapsed_time(e1) / steps
@@ -338,7 +338,20 @@ def run_variants(args, w, solver, Rub, Rpi, lam_ref, stream):
     solver.set_options(coarse="learned")
     lam, st, ms = _timed_solves(solver, Rub, Rpi, stream, steps)
     record("fp64_fgmres_learned_only", lam, st, ms, note="falls back to the V-cycle when steps stall")
-    solver.set_options(krylov="bicgstab", coarse="vcycle", precision="fp64")
+    # the paper's other configurations on the same solve (Sec. 3.2): 3a / 3b (coarse solve by
+    # V-cycle-preconditioned BiCGStab to 1e-14 / 1e-2) and 2 (the line smoother alone, n sweeps)
+    solver.set_options(krylov="bicgstab", coarse="exact")
+    lam, st, ms = _timed_solves(solver, Rub, Rpi, stream, 2)
+    record("fp64_bicgstab_3a", lam, st, ms, note="host-driven inner BiCGStab on H")
+    solver.set_options(coarse="approx")
+    lam, st, ms = _timed_solves(solver, Rub, Rpi, stream, 2)
+    record("fp64_bicgstab_3b", lam, st, ms, note="host-driven inner BiCGStab on H")
+    for nsm in (1, 2, 3):
+        solver.set_options(coarse="vcycle", precond="linesmooth", n_smooth=nsm, max_iter=400)
+        lam, st, ms = _timed_solves(solver, Rub, Rpi, stream, 2)
+        record(f"fp64_bicgstab_config2_n{nsm}", lam, st, ms)
+    solver.set_options(krylov="bicgstab", coarse="vcycle", precision="fp64", precond="nonnested", n_smooth=1,
+                       max_iter=200)
     return out
 
 

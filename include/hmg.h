@@ -120,6 +120,10 @@ typedef struct {
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
 #define HMG_COARSE_LEARNED 1        /* the learned model f ~ H^-1 alone */
 #define HMG_COARSE_LEARNED_VCYCLE 2 /* the model's output as the V-cycle's initial guess */
+#define HMG_COARSE_KRYLOV_EXACT 3   /* configuration 3a (Sec. 3.2): H dPi = bbar by BiCGStab
+                                       preconditioned with the V-cycle, to 1e-14 (FP64 only;
+                                       the host drives the inner loop) */
+#define HMG_COARSE_KRYLOV_APPROX 4  /* configuration 3b: the same to 1e-2 */
 #define HMG_KRYLOV_BICGSTAB 0
 #define HMG_KRYLOV_FGMRES 1
 

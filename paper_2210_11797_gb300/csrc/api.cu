@@ -37,7 +37,10 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_npre < 1 || o.mg_npost < 1 || o.mg_ncoarse < 1) return bad("multigrid sweep counts must be >= 1");
   if (!std::isfinite(o.omega) || !std::isfinite(o.mg_omega)) return bad("relaxation factors");
   if (!(o.tol > 0.0) || o.max_iter < 0 || !(o.divergence > 0.0)) return bad("tol / max_iter / divergence");
-  if (o.coarse < HMG_COARSE_VCYCLE || o.coarse > HMG_COARSE_LEARNED_VCYCLE) return bad("coarse");
+  if (o.coarse < HMG_COARSE_VCYCLE || o.coarse > HMG_COARSE_KRYLOV_APPROX) return bad("coarse");
+  if ((o.coarse == HMG_COARSE_KRYLOV_EXACT || o.coarse == HMG_COARSE_KRYLOV_APPROX) &&
+      o.precision != HMG_PRECISION_FP64)
+    return bad("the Krylov coarse solves (configurations 3a, 3b) run in FP64");
   if (o.krylov != HMG_KRYLOV_BICGSTAB && o.krylov != HMG_KRYLOV_FGMRES) return bad("krylov");
   if (o.restart < 1 || o.restart > 64) return bad("restart must be in 1..64");
   if (!(o.stall_ratio > 0.0)) return bad("stall_ratio");

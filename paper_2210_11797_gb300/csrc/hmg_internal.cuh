@@ -140,6 +140,7 @@ struct Ctx {
   float *collect_x = nullptr, *collect_t = nullptr;
   int collect_max = 0, collect_n = 0;
   double *collect_r = nullptr, *collect_e = nullptr, *collect_y = nullptr;
+  double *ck = nullptr;           // [9][ncell] work vectors of the Krylov coarse solve
   // flexible GMRES basis: V [restart+1][ntrace], Z [restart][ntrace], Hessenberg column
   double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
   int gm_restart = 0;
@@ -236,6 +237,8 @@ int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, con
 int collect_pair(Ctx *c, const double *bbar);
 // r = b - H_l x (FP64) on level l
 int pressure_residual_fp64(Ctx *c, int level, const double *b, const double *x, double *r);
+// x = H_0^-1 b by V-cycle-preconditioned BiCGStab to tol (configurations 3a / 3b), host-driven
+int coarse_krylov(Ctx *c, const double *b, double *x, double tol, int maxit);
 // flexible GMRES(restart) driver (krylov.cu)
 int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st);
 // Launch-shape autotuning of one context (columns per block of the sweep and MG smoother).

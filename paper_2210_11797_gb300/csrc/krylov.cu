@@ -344,7 +344,9 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
   int s;
-  if (c->opt.graph && !c->opt.profile && !c->collect_x) {
+  const bool host_coarse = c->opt.precond == HMG_PRECOND_NONNESTED &&
+                           (c->opt.coarse == HMG_COARSE_KRYLOV_EXACT || c->opt.coarse == HMG_COARSE_KRYLOV_APPROX);
+  if (c->opt.graph && !c->opt.profile && !c->collect_x && !host_coarse) {
     if ((s = ensure_solve_graph(c, Rub, Rpi, lambda))) return s;
     HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
   } else {
@@ -373,7 +375,8 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
                          const double *const *Rpi, double *const *lambda, hmg_solve_stats *st) {
   Ctx *c0 = ctxs[0];
   for (int i = 0; i < n; ++i)
-    if (ctxs[i]->opt.krylov != HMG_KRYLOV_BICGSTAB || ctxs[i]->collect_x)
+    if (ctxs[i]->opt.krylov != HMG_KRYLOV_BICGSTAB || ctxs[i]->collect_x ||
+        ctxs[i]->opt.coarse == HMG_COARSE_KRYLOV_EXACT || ctxs[i]->opt.coarse == HMG_COARSE_KRYLOV_APPROX)
       return fail(c0, HMG_ERR_INVALID_ARG, "batched solves take BiCGStab contexts without pair collection");
   cudaGraph_t g = nullptr;
   HMG_CUDA(c0, cudaGraphCreate(&g, 0));

@@ -3,6 +3,8 @@
 // (Eq. pressure_block_jacobi, Thomas algorithm per column), residual + restriction (sum over
 // the four horizontal children) and prolongation (injection), in one V-cycle with
 // mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level.
+#include <cmath>
+
 #include "device_common.cuh"
 #include "hmg_internal.cuh"
 #include "precond.cuh"
@@ -261,6 +263,90 @@ int apply_pressure_fp64(Ctx *c, int l, const double *x, double *y) {
   MGArgs a = mg_args(c, l);
   mg_apply_kernel<double><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(a, lv.H, x, y);
   HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+
+// ---- configurations 3a / 3b: the coarse solve by Krylov iteration ---------------------------
+// Right-preconditioned BiCGStab (van der Vorst 1992) on H_0 x = b from x = 0, the pressure
+// V-cycle as preconditioner, stopping when ||r|| <= tol ||b|| (Sec. 3.2: 1e-14 for 3a, 1e-2
+// for 3b) or after maxit iterations (the approximation is used either way, as for a fixed
+// number of V-cycles). The host reads the inner products (one synchronisation each).
+__global__ void ck_p_kernel(double *__restrict__ p, const double *__restrict__ r, const double *__restrict__ v,
+                            double beta, double omega, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+// y = x + a z
+__global__ void ck_axpy_kernel(double *__restrict__ y, const double *__restrict__ x, double a,
+                               const double *__restrict__ z, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] + a * z[i];
+}
+// x += alpha phat + omega shat
+__global__ void ck_x_kernel(double *__restrict__ x, const double *__restrict__ ph, const double *__restrict__ sh,
+                            double alpha, double omega, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = x[i] + alpha * ph[i] + omega * sh[i];
+}
+
+int coarse_krylov(Ctx *c, const double *b, double *x, double tol, int maxit) {
+  const Level &f = c->lv[0];
+  const int64_t n = f.ncell;
+  int st;
+  if (!c->ck && (st = dev_alloc(c, &c->ck, (size_t)8 * n))) return st;
+  double *r = c->ck, *rh = r + n, *p = rh + n, *v = p + n, *s = v + n, *t = s + n, *ph = t + n, *sh = ph + n;
+  const unsigned g = grid_for(n, 256);
+  constexpr int kSlot = 12;
+  auto dot = [&](const double *a, const double *bb, double *out) -> int {
+    int e = launch_dot(c, a, bb, n, kSlot);
+    if (e) return e;
+    HMG_CUDA(c, cudaMemcpyAsync(out, c->scal + kSlot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HMG_OK;
+  };
+  HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(rh, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(p, 0, sizeof(double) * n, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(v, 0, sizeof(double) * n, c->stream));
+  double bb = 0.0;
+  if ((st = dot(b, b, &bb))) return st;
+  const double bnorm = std::sqrt(bb);
+  if (!(bnorm > 0.0)) return HMG_OK;
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  for (int it = 0; it < maxit; ++it) {
+    double rho = 0.0, rv = 0.0, tt = 0.0, ts = 0.0, rr = 0.0;
+    if ((st = dot(rh, r, &rho))) return st;
+    if (rho == 0.0 || !std::isfinite(rho)) break;
+    const double beta = (rho / rho_old) * (alpha / omega);
+    ck_p_kernel<<<g, 256, 0, c->stream>>>(p, r, v, beta, omega, n);
+    HMG_CUDA(c, cudaGetLastError());
+    if ((st = pressure_vcycle_fp64(c, p, ph))) return st;
+    if ((st = apply_pressure_fp64(c, 0, ph, v))) return st;
+    if ((st = dot(rh, v, &rv))) return st;
+    if (rv == 0.0 || !std::isfinite(rv)) break;
+    alpha = rho / rv;
+    ck_axpy_kernel<<<g, 256, 0, c->stream>>>(s, r, -alpha, v, n);
+    HMG_CUDA(c, cudaGetLastError());
+    if ((st = pressure_vcycle_fp64(c, s, sh))) return st;
+    if ((st = apply_pressure_fp64(c, 0, sh, t))) return st;
+    if ((st = dot(t, t, &tt))) return st;
+    if (tt == 0.0 || !std::isfinite(tt)) {   // s = 0: x += alpha phat is exact
+      ck_x_kernel<<<g, 256, 0, c->stream>>>(x, ph, sh, alpha, 0.0, n);
+      HMG_CUDA(c, cudaGetLastError());
+      break;
+    }
+    if ((st = dot(t, s, &ts))) return st;
+    omega = ts / tt;
+    ck_x_kernel<<<g, 256, 0, c->stream>>>(x, ph, sh, alpha, omega, n);
+    ck_axpy_kernel<<<g, 256, 0, c->stream>>>(r, s, -omega, t, n);
+    HMG_CUDA(c, cudaGetLastError());
+    rho_old = rho;
+    if ((st = dot(r, r, &rr))) return st;
+    const double rel = std::sqrt(rr) / bnorm;
+    if (!std::isfinite(rel) || rel <= tol) break;
+  }
   return HMG_OK;
 }
 

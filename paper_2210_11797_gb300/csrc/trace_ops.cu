@@ -396,8 +396,15 @@ static int two_level(Ctx *c, const double *r, double *z) {
   {
     const int nl = c->nmg - 1;
     Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1));
-    const bool learned = c->opt.coarse != HMG_COARSE_VCYCLE && !c->coarse_fallback;
-    if (learned && c->opt.coarse == HMG_COARSE_LEARNED) {
+    const int cm = c->opt.coarse;
+    const bool learned = (cm == HMG_COARSE_LEARNED || cm == HMG_COARSE_LEARNED_VCYCLE) && !c->coarse_fallback;
+    if (cm == HMG_COARSE_KRYLOV_EXACT || cm == HMG_COARSE_KRYLOV_APPROX) {
+      if (sizeof(T) != 8) return fail(c, HMG_ERR_INVALID_ARG, "the Krylov coarse solves run in FP64");
+      dpi = w3;
+      if ((st = coarse_krylov(c, reinterpret_cast<const double *>(cb), reinterpret_cast<double *>(dpi),
+                              cm == HMG_COARSE_KRYLOV_EXACT ? 1e-14 : 1e-2, 500)))
+        return st;
+    } else if (learned && cm == HMG_COARSE_LEARNED) {
       dpi = w3;
       if ((st = learned_coarse<T>(c, cb, dpi))) return st;
     } else if (learned) {

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "not_ready", 4: "not_co
                 5: "breakdown", 6: "nonfinite", 7: "timeout", 8: "out_of_memory"}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"none": 0, "linesmooth": 1, "nonnested": 2}
-COARSE = {"vcycle": 0, "learned": 1, "learned_vcycle": 2}
+COARSE = {"vcycle": 0, "learned": 1, "learned_vcycle": 2, "exact": 3, "approx": 4}
 KRYLOV = {"bicgstab": 0, "fgmres": 1}
 _NAMED = {"precision": PRECISION, "precond": PRECOND, "coarse": COARSE, "krylov": KRYLOV}
 MAX_HISTORY = 512

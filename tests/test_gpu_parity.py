@@ -134,6 +134,24 @@ def test_line_smoother_matches_oracle(name):
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("coarse", ["exact", "approx"])
+@pytest.mark.parametrize("name", ["planar16", "sphereC6L5"])
+def test_krylov_coarse_configurations_match_oracle(name, coarse):
+    """Configurations 3a / 3b: the coarse solve by V-cycle-preconditioned BiCGStab to 1e-14 /
+    1e-2 inside Algorithm 2, against the oracle's same configuration."""
+    w, _ora, gpu = _pair(name)
+    ora = HybridSolver(w.hier, w.coeffs, OracleOptions(coarse=coarse))
+    try:
+        gpu.set_options(coarse=coarse, tol=1e-10, max_iter=200)
+        lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
+        assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9
+        ref, hist, status = ora.solve(w.Rub, w.Rpi, 1e-10)
+        assert status == "ok" and abs(st["iterations"] - (len(hist) - 1)) <= 1
+        assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-8
+    finally:
+        gpu.set_options(coarse="vcycle", tol=w.tol, max_iter=200)
+
+
 def test_changed_relaxation_weights_rebuild_the_factors():
     """omega and mg_omega are folded into the Thomas factors; changing them through the
     options rebuilds the factors (the oracle takes the weights as arguments)."""
