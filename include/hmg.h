@@ -92,6 +92,9 @@ typedef struct {
 #define HMG_PRECOND_NONE 0
 #define HMG_PRECOND_LINESMOOTH 1 /* configuration 2: Algorithm 1 from zero, n_smooth sweeps */
 #define HMG_PRECOND_NONNESTED 2  /* configuration 3c: Algorithm 2 with one pressure V-cycle */
+#define HMG_PRECOND_SCHUR 3      /* configuration 1: the unhybridised 2x2 system (Eq. 2x2system)
+                                    with the approximate Schur complement (Sec. 2.3); solved by
+                                    hmg_solve_mixed; set before hmg_assemble_trace; FP64 */
 
 typedef struct {
   int32_t precision;    /* HMG_PRECISION_* */
@@ -209,6 +212,22 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
  * timings overwrite the context's work vectors. */
 int hmg_autotune(hmg_ctx *ctx);
 
+/* Configuration 1 (Sec. 2.3, Sec. 3.2): BiCGStab on the unhybridised 2x2 system for the
+ * continuous normal velocity u and the Exner increment Pi (Eq. 2x2system), preconditioned by
+ * the approximate Schur complement: lumped velocity mass, Step 1 (Eq. pressure_rhs), one
+ * pressure-multigrid V-cycle on Eq. elliptic_pressure_system, Step 3 (Eq. velocity_recovery).
+ * Needs a context assembled with precond = HMG_PRECOND_SCHUR. Rub, Rpi as for hmg_solve (the
+ * continuous residual of facet f is the sum of its cells' oriented broken residuals). u
+ * [ntrace] device: the normal velocity per facet in the trace numbering, oriented out of
+ * edge_cols[e][0] on vertical facets and upwards on horizontal ones, 0 on ground and lid;
+ * pi [ncell] device. The Krylov vectors are [u | Pi]; stats as for hmg_solve. */
+int hmg_solve_mixed(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *u, double *pi,
+                    hmg_solve_stats *stats);
+
+/* y = (2x2 operator) x on [u | Pi] vectors of ntrace + ncell values (device; configuration 1
+ * contexts; ground and lid rows are the identity). */
+int hmg_apply_mixed(hmg_ctx *ctx, const double *x, double *y);
+
 /* The same solve with HOST buffers: the inputs are copied to the device, the result back. */
 int hmg_solve_host(hmg_ctx *ctx, const double *Rub_host, const double *Rpi_host,
                    double *lambda_host, hmg_solve_stats *stats);
@@ -224,7 +243,8 @@ int hmg_reconstruct(hmg_ctx *ctx, const double *lambda, const double *Rub, const
 int hmg_apply_trace(hmg_ctx *ctx, const double *x, double *y);
 
 /* z = M^-1 r: one application of the configured preconditioner (Algorithm 2 for
- * HMG_PRECOND_NONNESTED) in the configured precision. r, z [ntrace], no overlap. */
+ * HMG_PRECOND_NONNESTED) in the configured precision. r, z [ntrace] (HMG_PRECOND_SCHUR:
+ * [ntrace + ncell], the approximate Schur complement of configuration 1), no overlap. */
 int hmg_precond_apply(hmg_ctx *ctx, const double *r, double *z);
 
 /* nsweeps of Algorithm 1 on S lambda = b, updating lambda [ntrace] in place (FP64). */

@@ -32,7 +32,9 @@ static int upload(Ctx *c, T **dst, const T *src, size_t n) {
 static int check_options(Ctx *c, const hmg_options &o) {
   auto bad = [&](const char *m) { return fail(c, HMG_ERR_INVALID_ARG, std::string("options: ") + m); };
   if (o.precision != HMG_PRECISION_FP64 && o.precision != HMG_PRECISION_MIXED) return bad("precision");
-  if (o.precond < HMG_PRECOND_NONE || o.precond > HMG_PRECOND_NONNESTED) return bad("precond");
+  if (o.precond < HMG_PRECOND_NONE || o.precond > HMG_PRECOND_SCHUR) return bad("precond");
+  if (o.precond == HMG_PRECOND_SCHUR && o.precision != HMG_PRECISION_FP64)
+    return bad("configuration 1 (HMG_PRECOND_SCHUR) runs in FP64");
   if (o.n_pre < 0 || o.n_post < 0 || o.n_smooth < 1) return bad("trace smoother sweep counts");
   if (o.mg_npre < 1 || o.mg_npost < 1 || o.mg_ncoarse < 1) return bad("multigrid sweep counts must be >= 1");
   if (!std::isfinite(o.omega) || !std::isfinite(o.mg_omega)) return bad("relaxation factors");
@@ -320,9 +322,10 @@ int hmg_assemble_trace(hmg_ctx *c) {
   const Level &f = c->lv[0];
   const size_t T = (size_t)f.ntrace;
   if (!c->B) {
+    // Krylov vectors long enough for the 2x2 system of configuration 1 ([u | Pi])
     double **vecs[] = {&c->B, &c->r, &c->rhat, &c->p, &c->v, &c->s, &c->t, &c->phat, &c->shat};
     for (double **v : vecs)
-      if ((st = dev_alloc(c, v, T))) return st;
+      if ((st = dev_alloc(c, v, T + (size_t)f.ncell))) return st;
     double *tmp;
     if ((st = dev_alloc(c, &tmp, T))) return st;
     c->w1 = tmp;
@@ -391,17 +394,48 @@ int hmg_trace_rhs(hmg_ctx *c, const double *Rub, const double *Rpi, double *B) {
   return finish(c, launch_trace_rhs(c, Rub, Rpi, B));
 }
 
+static int reject_schur(hmg_ctx *c) {
+  return mixed_system(c) ? fail(c, HMG_ERR_INVALID_ARG, "configuration 1 solves the 2x2 system: use hmg_solve_mixed")
+                         : HMG_OK;
+}
+
 int hmg_solve(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *stats) {
   int st = ready(c);
   if (st) return st;
   if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if ((st = reject_schur(c))) return st;
   return krylov_solve(c, Rub, Rpi, lambda, stats);
+}
+
+int hmg_solve_mixed(hmg_ctx *c, const double *Rub, const double *Rpi, double *u, double *pi, hmg_solve_stats *stats) {
+  int st = ready(c);
+  if (st) return st;
+  if (!Rub || !Rpi || !u || !pi) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if (!mixed_system(c) || !c->have_mixed)
+    return fail(c, HMG_ERR_NOT_READY, "configuration 1 needs precond = HMG_PRECOND_SCHUR before hmg_assemble_trace");
+  const int solve_st = krylov_solve(c, Rub, Rpi, c->mx_x, stats);
+  if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
+      solve_st != HMG_ERR_NONFINITE && solve_st != HMG_ERR_TIMEOUT)
+    return solve_st;
+  const Level &f = c->lv[0];
+  HMG_CUDA(c, cudaMemcpyAsync(u, c->mx_x, sizeof(double) * f.ntrace, cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(pi, c->mx_x + f.ntrace, sizeof(double) * f.ncell, cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return solve_st;
+}
+
+int hmg_apply_mixed(hmg_ctx *c, const double *x, double *y) {
+  int st = ready(c);
+  if (st) return st;
+  if (!x || !y || x == y) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  return finish(c, launch_mixed_apply(c, x, y, 0, nullptr, 0, 0));
 }
 
 int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *stats) {
   int st = ready(c);
   if (st) return st;
   if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if ((st = reject_schur(c))) return st;
   const Level &f = c->lv[0];
   double *dRub = c->host_in, *dRpi = dRub + 6 * f.ncell, *dlam = dRpi + f.ncell;
   HMG_CUDA(c, cudaMemcpyAsync(dRub, Rub, sizeof(double) * 6 * f.ncell, cudaMemcpyHostToDevice, c->stream));
@@ -476,6 +510,7 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
     if (!c->assembled) return fail(c0, HMG_ERR_NOT_READY, "a context of the batch is not assembled");
     if (c->device != c0->device) return fail(c0, HMG_ERR_INVALID_ARG, "batched contexts must share a device");
     if (!Rub[i] || !Rpi[i] || !lambda[i]) return fail(c0, HMG_ERR_INVALID_ARG, "null pointer in the batch");
+    if (mixed_system(c)) return fail(c0, HMG_ERR_INVALID_ARG, "batched solves are hybridised solves");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return fail(c0, HMG_ERR_INVALID_ARG, "a context appears twice in the batch");
   }

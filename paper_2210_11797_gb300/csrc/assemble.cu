@@ -555,6 +555,7 @@ int assemble_all(Ctx *c) {
   }
   gamma_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(ra, sk1, rec[0], c->gamma);
   HMG_CUDA(c, cudaGetLastError());
+  if (c->opt.precond == HMG_PRECOND_SCHUR && (st = build_mixed(c, rec[0]))) return st;
   if (c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32) {
     if ((st = to_float(c, c->S, &c->S32, (int64_t)kSlots * T))) return st;
     if ((st = to_float(c, c->gamma, &c->gamma32, C))) return st;

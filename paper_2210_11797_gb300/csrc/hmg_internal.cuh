@@ -141,6 +141,12 @@ struct Ctx {
   int collect_max = 0, collect_n = 0;
   double *collect_r = nullptr, *collect_e = nullptr, *collect_y = nullptr;
   double *ck = nullptr;           // [9][ncell] work vectors of the Krylov coarse solve
+  // configuration 1 (mixed.cu): the 2x2 operator (velocity block in the 11-slot layout of S,
+  // G couplings [2][ntrace], B couplings and M3^Pi [7][ncell]), 1 / lumped mass [ntrace], the
+  // solution [ntrace + ncell] and the Step-1 right-hand side [ncell]
+  double *mx_Mu = nullptr, *mx_Gx = nullptr, *mx_Bx = nullptr, *mx_ilump = nullptr, *mx_x = nullptr,
+         *mx_bp = nullptr;
+  bool have_mixed = false;
   // flexible GMRES basis: V [restart+1][ntrace], Z [restart][ntrace], Hessenberg column
   double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
   int gm_restart = 0;
@@ -214,6 +220,19 @@ int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
                  hmg_solve_stats *st);
 int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
+// sums the per-block partials of slots s0 (and s1 >= 0) into scal (fixed order)
+int launch_finalize(Ctx *c, int nblocks, int s0, int s1);
+
+// ---- configuration 1: the unhybridised 2x2 system (mixed.cu) ------------------------------
+int build_mixed(Ctx *c, const double *rec0);
+// y = Mx x on [u | Pi] vectors (ntrace + ncell), with the fused products of launch_spmv's modes
+int launch_mixed_apply(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1);
+int launch_mixed_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B);
+// z = approximate-Schur preconditioner applied to r (Steps 1-3, one pressure V-cycle)
+int schur_precond(Ctx *c, const double *r, double *z);
+// the Krylov system of the context's configuration: its length, operator and right-hand side
+inline bool mixed_system(const Ctx *c) { return c->opt.precond == HMG_PRECOND_SCHUR; }
+inline int64_t sys_n(const Ctx *c) { return c->lv[0].ntrace + (mixed_system(c) ? c->lv[0].ncell : 0); }
 // Batched solves: one CUDA graph with one branch per context (contexts on one device).
 int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
                          const double *const *Rpi, double *const *lambda, hmg_solve_stats *st);

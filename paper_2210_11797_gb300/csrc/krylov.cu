@@ -26,6 +26,15 @@ static unsigned red_grid(int64_t n) {
 
 enum { kIt = 0, kStatus = 1, kContinue = 2, kWaitFlag = 3 };
 
+// The system the Krylov loop iterates on: S lambda = B_lambda (hybridised configurations) or
+// the 2x2 system on [u | Pi] (configuration 1).
+static int sys_apply(Ctx *c, const double *x, double *y, int mode, const double *w, int s0, int s1) {
+  return mixed_system(c) ? launch_mixed_apply(c, x, y, mode, w, s0, s1) : launch_spmv(c, x, y, mode, w, s0, s1);
+}
+static int sys_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B) {
+  return mixed_system(c) ? launch_mixed_rhs(c, Rub, Rpi, B) : launch_trace_rhs(c, Rub, Rpi, B);
+}
+
 __global__ void __launch_bounds__(kRedThreads)
     dot_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *part,
                unsigned int *counter, double *scal, int slot) {
@@ -164,9 +173,9 @@ static LoopParams loop_params(const Ctx *c) {
 // B_lambda, (B, B), x = 0, r = rhat = B, loop state
 static int solve_head(Ctx *c, const double *Rub, const double *Rpi, double *x, bool graph,
                       cudaGraphConditionalHandle h) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   int s;
-  if ((s = launch_trace_rhs(c, Rub, Rpi, c->B))) return s;
+  if ((s = sys_rhs(c, Rub, Rpi, c->B))) return s;
   Prof pk(c, kCompKrylov, 3);
   if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
   bicg_init_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, x, c->r, c->rhat, c->p, c->v, n);
@@ -178,7 +187,7 @@ static int solve_head(Ctx *c, const double *Rub, const double *Rpi, double *x, b
 
 // one BiCGStab iteration and its check
 static int solve_body(Ctx *c, double *x, bool graph, cudaGraphConditionalHandle h) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   const unsigned vg = red_grid(n);
   int s;
   {
@@ -187,14 +196,14 @@ static int solve_body(Ctx *c, double *x, bool graph, cudaGraphConditionalHandle 
     HMG_CUDA(c, cudaGetLastError());
   }
   if ((s = precond_apply(c, c->p, c->phat))) return s;
-  if ((s = launch_spmv(c, c->phat, c->v, 1, c->rhat, Scal::RV, 0))) return s;
+  if ((s = sys_apply(c, c->phat, c->v, 1, c->rhat, Scal::RV, 0))) return s;
   {
     Prof pk(c, kCompKrylov);
     bicg_s_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->v, c->s, c->scal, c->state, n);
     HMG_CUDA(c, cudaGetLastError());
   }
   if ((s = precond_apply(c, c->s, c->shat))) return s;
-  if ((s = launch_spmv(c, c->shat, c->t, 2, c->s, Scal::TS, Scal::TT))) return s;
+  if ((s = sys_apply(c, c->shat, c->t, 2, c->s, Scal::TS, Scal::TT))) return s;
   {
     Prof pk(c, kCompKrylov, 2);
     bicg_xr_kernel<<<vg, kRedThreads, 0, c->stream>>>(x, c->r, c->s, c->t, c->phat, c->shat, c->rhat,
@@ -207,7 +216,7 @@ static int solve_body(Ctx *c, double *x, bool graph, cudaGraphConditionalHandle 
 }
 
 // ||B - S x||^2 recomputed in FP64 from the final iterate
-static int solve_tail(Ctx *c, const double *x) { return launch_spmv(c, x, nullptr, 3, c->B, Scal::AUX, 0); }
+static int solve_tail(Ctx *c, const double *x) { return sys_apply(c, x, nullptr, 3, c->B, Scal::AUX, 0); }
 
 // ---- graph construction ------------------------------------------------------------------
 // Adds one solve (head -> WHILE(body) -> tail) to graph g, without dependencies on other
@@ -520,7 +529,7 @@ static void dev_release(Ctx *c, void *p) {
 
 static int gm_buffers(Ctx *c, int m) {
   if (c->gm_V && c->gm_restart >= m) return HMG_OK;
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = c->lv[0].ntrace + c->lv[0].ncell;   // the longer of the two systems
   dev_release(c, c->gm_V);
   dev_release(c, c->gm_Z);
   c->gm_V = c->gm_Z = nullptr;
@@ -544,7 +553,7 @@ static unsigned gm_grid(int64_t n) {
 
 // h[k] = (V_k, w), k < nk (and hacc[k] += h[k])
 static int mdot(Ctx *c, const double *V, int nk, const double *w, double *h, double *hacc) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   const unsigned nb = gm_grid(n);
   mdot_kernel<<<dim3(nb, (unsigned)nk), kRedThreads, 0, c->stream>>>(V, n, w, c->gm_part);
   mdot_finalize_kernel<<<(unsigned)nk, 256, 0, c->stream>>>(c->gm_part, (int)nb, h, hacc);
@@ -553,7 +562,7 @@ static int mdot(Ctx *c, const double *V, int nk, const double *w, double *h, dou
 }
 
 static int mcomb(Ctx *c, double *w, const double *V, const double *h, int nk, double sign) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   mcomb_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(w, V, n, h, nk, sign);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
@@ -561,7 +570,7 @@ static int mcomb(Ctx *c, double *w, const double *V, const double *h, int nk, do
 
 // v = v / ||v||, *beta_host = ||v||
 static int normalize(Ctx *c, double *v, double *nn_slot, double *h_slot, double *beta_host) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   int s;
   if ((s = mdot(c, v, 1, v, nn_slot, nullptr))) return s;
   gm_normalize_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(v, n, nn_slot, h_slot);
@@ -574,7 +583,7 @@ static int normalize(Ctx *c, double *v, double *nn_slot, double *h_slot, double 
 }
 
 int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_solve_stats *st) {
-  const int64_t n = c->lv[0].ntrace;
+  const int64_t n = sys_n(c);
   const int m = c->opt.restart;
   const bool learned = c->opt.precond == HMG_PRECOND_NONNESTED && c->opt.coarse != HMG_COARSE_VCYCLE;
   int s;
@@ -585,7 +594,7 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
   HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-  if ((s = launch_trace_rhs(c, Rub, Rpi, c->B))) return s;
+  if ((s = sys_rhs(c, Rub, Rpi, c->B))) return s;
   double beta = 0.0;
   {
     Prof pk(c, kCompKrylov, 6);
@@ -609,7 +618,7 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
     for (int j = 0; j < m; ++j) {
       double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
       if ((s = precond_apply(c, vj, zj))) return s;
-      if ((s = launch_spmv(c, zj, w, 0, nullptr, 0, 0))) return s;
+      if ((s = sys_apply(c, zj, w, 0, nullptr, 0, 0))) return s;
       {
         Prof pk(c, kCompKrylov, 12);
         if ((s = mdot(c, V, j + 1, w, hd, nullptr))) return s;
@@ -680,7 +689,7 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
       break;
     }
     // restart from the true residual
-    if ((s = launch_spmv(c, x, c->t, 0, nullptr, 0, 0))) return s;
+    if ((s = sys_apply(c, x, c->t, 0, nullptr, 0, 0))) return s;
     {
       Prof pk(c, kCompKrylov, 4);
       gm_sub_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, c->t, V, n);

@@ -84,6 +84,12 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+int launch_finalize(Ctx *c, int nblocks, int s0, int s1) {
+  finalize_kernel<<<1, 1024, 0, c->stream>>>(c->part, nblocks, s0, s1, c->scal);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
 int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0,
                 int slot1) {
   const Level &f = c->lv[0];
@@ -438,8 +444,10 @@ static int two_level(Ctx *c, const double *r, double *z) {
 int precond_apply(Ctx *c, const double *r, double *z) {
   const bool mixed = c->opt.precision == HMG_PRECISION_MIXED;
   switch (c->opt.precond) {
+    case HMG_PRECOND_SCHUR:
+      return schur_precond(c, r, z);
     case HMG_PRECOND_NONE:
-      HMG_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * c->lv[0].ntrace, cudaMemcpyDeviceToDevice,
+      HMG_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * sys_n(c), cudaMemcpyDeviceToDevice,
                                   c->stream));
       return HMG_OK;
     case HMG_PRECOND_LINESMOOTH:

@@ -20,7 +20,7 @@ HMG_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "not_ready", 4: "not_converged",
                 5: "breakdown", 6: "nonfinite", 7: "timeout", 8: "out_of_memory"}
 PRECISION = {"fp64": 0, "mixed": 1}
-PRECOND = {"none": 0, "linesmooth": 1, "nonnested": 2}
+PRECOND = {"none": 0, "linesmooth": 1, "nonnested": 2, "schur": 3}
 COARSE = {"vcycle": 0, "learned": 1, "learned_vcycle": 2, "exact": 3, "approx": 4}
 KRYLOV = {"bicgstab": 0, "fgmres": 1}
 _NAMED = {"precision": PRECISION, "precond": PRECOND, "coarse": COARSE, "krylov": KRYLOV}
@@ -105,6 +105,8 @@ _SIGS = {
     "hmg_solve_batched": ([C.POINTER(_P), C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                            C.POINTER(SolveStats)], C.c_int),
     "hmg_autotune": ([_P], C.c_int),
+    "hmg_solve_mixed": ([_P, _P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
+    "hmg_apply_mixed": ([_P, _P, _P], C.c_int),
     "hmg_coarse_model_size": ([], C.c_int32),
     "hmg_set_coarse_model": ([_P, _P, C.c_int32], C.c_int),
     "hmg_get_coarse_model": ([_P, _P, C.c_int32], C.c_int),
@@ -269,6 +271,22 @@ class Solver:
             _check(self.ctx, rc)
         return lam, st.as_dict()
 
+    def solve_mixed(self, Rub, Rpi, check=True):
+        """Configuration 1: returns (u [ntrace], Pi [ncell], stats)."""
+        u, pi = self._empty(self.ntrace), self._empty(self.ncell)
+        st = SolveStats()
+        rc = lib().hmg_solve_mixed(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"), self._dev(Rpi, self.ncell, "Rpi"),
+                                   _ptr(u), _ptr(pi), C.byref(st))
+        if check:
+            _check(self.ctx, rc)
+        return u, pi, st.as_dict()
+
+    def apply_mixed(self, x):
+        n = self.ntrace + self.ncell
+        y = self._empty(n)
+        _check(self.ctx, lib().hmg_apply_mixed(self.ctx, self._dev(x, n, "x"), _ptr(y)))
+        return y
+
     def solve_host(self, Rub, Rpi, check=True):
         Rub = np.ascontiguousarray(Rub, np.float64)
         Rpi = np.ascontiguousarray(Rpi, np.float64)
@@ -295,8 +313,9 @@ class Solver:
         return y
 
     def precond(self, r):
-        z = self._empty(self.ntrace)
-        _check(self.ctx, lib().hmg_precond_apply(self.ctx, self._dev(r, self.ntrace, "r"), _ptr(z)))
+        n = self.ntrace + (self.ncell if self.opts.precond == PRECOND["schur"] else 0)
+        z = self._empty(n)
+        _check(self.ctx, lib().hmg_precond_apply(self.ctx, self._dev(r, n, "r"), _ptr(z)))
         return z
 
     def line_smooth(self, b, lam, nsweeps):
