@@ -62,10 +62,11 @@ __global__ void mixed_rows_kernel(const MixedArgs a, const double *__restrict__ 
       v[m] = face_sign(a, c1, j1) * rec_m(r1, i1, j1);
       v[5 + m] = -face_sign(a, c2, j2) * rec_m(r2, i2, j2);
     }
-    v[4] = -rec_m(r1, i1, 4);
-    v[5] = rec_m(r1, i1, 5);
-    v[9] = rec_m(r2, i2, 4);
-    v[10] = -rec_m(r2, i2, 5);
+    // the bottom / top faces at k = 0 / L-1 are ground / lid facets (u = 0): no coupling
+    v[4] = k > 0 ? -rec_m(r1, i1, 4) : 0.0;
+    v[5] = k < a.L - 1 ? rec_m(r1, i1, 5) : 0.0;
+    v[9] = k > 0 ? rec_m(r2, i2, 4) : 0.0;
+    v[10] = k < a.L - 1 ? -rec_m(r2, i2, 5) : 0.0;
     g0 = -r1[CellRec::KTH + i1];          // s A(i, 6) with A(i, 6) = -k theta
     g1 = r2[CellRec::KTH + i2];
     il = 1.0 / (r1[CellRec::LUMP + i1] + r2[CellRec::LUMP + i2]);
@@ -81,8 +82,8 @@ __global__ void mixed_rows_kernel(const MixedArgs a, const double *__restrict__ 
         v[1 + i] = -si * rec_m(ra, 4, i);
         v[6 + i] = si * rec_m(rb, 5, i);
       }
-      v[5] = -rec_m(ra, 4, 5);
-      v[10] = -rec_m(rb, 5, 4);
+      v[5] = k + 1 < a.L ? -rec_m(ra, 4, 5) : 0.0;   // the lid above, the ground below: u = 0
+      v[10] = k - 1 > 0 ? -rec_m(rb, 5, 4) : 0.0;
       g0 = ra[CellRec::KTH + 4];
       g1 = -rb[CellRec::KTH + 5];
       il = 1.0 / (ra[CellRec::LUMP + 4] + rb[CellRec::LUMP + 5]);
@@ -98,10 +99,12 @@ __global__ void mixed_rows_kernel(const MixedArgs a, const double *__restrict__ 
 __global__ void mixed_cell_rows_kernel(const MixedArgs a, const double *__restrict__ rec, double *__restrict__ Bx) {
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= a.ncell) return;
-  const int c = (int)(K / a.L);
+  const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
   const double *r = rec + K * kCellData;
 #pragma unroll
   for (int i = 0; i < 6; ++i) Bx[(int64_t)i * a.ncell + K] = face_sign(a, c, i) * r[CellRec::B + i];
+  if (k == 0) Bx[4 * a.ncell + K] = 0.0;            // ground facet: u = 0
+  if (k == a.L - 1) Bx[5 * a.ncell + K] = 0.0;      // lid facet
   Bx[6 * a.ncell + K] = r[CellRec::MPI];
 }
 
