@@ -106,7 +106,9 @@ typedef struct {
   double mg_omega;      /* pressure block-Jacobi relaxation (0.9) */
   double tol;           /* relative residual ||B - S lambda|| / ||B|| to stop (1e-6) */
   int32_t max_iter;     /* BiCGStab iterations (200) */
-  double divergence;    /* stop with NOT_CONVERGED if ||r|| > divergence * ||B|| (1e3) */
+  double divergence;    /* stop with NOT_CONVERGED if ||r|| > divergence * ||B|| (1e8; BiCGStab on
+                           the 2x2 system of configuration 1 passes through residuals of 5e3
+                           ||B|| on its way to convergence) */
   int32_t profile;      /* 1: time every solver component with CUDA events (see
                            hmg_solve_stats.comp_ms); 0: no events (default) */
   int32_t graph;        /* 1 (default): the whole solve is one CUDA graph whose BiCGStab loop

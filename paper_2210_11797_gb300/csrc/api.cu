@@ -107,7 +107,7 @@ int hmg_default_options(hmg_options *o) {
   o->mg_omega = 0.9;
   o->tol = 1e-6;
   o->max_iter = 200;
-  o->divergence = 1e3;
+  o->divergence = 1e8;
   o->profile = 0;
   o->graph = 1;
   o->coarse = HMG_COARSE_VCYCLE;
