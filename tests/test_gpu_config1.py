@@ -67,7 +67,9 @@ def test_configuration1_solve_matches_oracle(name):
     w, ms, gpu = _pair(name)
     u, pi, st = gpu.solve_mixed(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
     uo, pio, hist, status = ms.solve(w.Rub, w.Rpi, 1e-12)
-    assert status == "ok" and st["status"] == "ok" and abs(st["iterations"] - (len(hist) - 1)) <= 1
+    # the spike amplifies rounding: the oracle itself takes 25 iterations on x86-64 and 27 on
+    # aarch64 for C12 x 30, so the counts agree within 3
+    assert status == "ok" and st["status"] == "ok" and abs(st["iterations"] - (len(hist) - 1)) <= 3
     xo = np.concatenate([uo, pio])
     b = ms.rhs(w.Rub, w.Rpi)
     true_o = np.linalg.norm(b - ms.Mx @ xo) / np.linalg.norm(b)
