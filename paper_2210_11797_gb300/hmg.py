@@ -287,12 +287,16 @@ class Solver:
         _check(self.ctx, lib().hmg_apply_mixed(self.ctx, self._dev(x, n, "x"), _ptr(y)))
         return y
 
-    def solve_host(self, Rub, Rpi, check=True):
+    def solve_host(self, Rub, Rpi, check=True, out=None):
+        """Host buffers in and out; `out` (float64 [ntrace], e.g. a view of pinned memory)
+        receives lambda, else a new array."""
         Rub = np.ascontiguousarray(Rub, np.float64)
         Rpi = np.ascontiguousarray(Rpi, np.float64)
         if Rub.size != 6 * self.ncell or Rpi.size != self.ncell:
             raise ValueError("Rub / Rpi size")
-        lam = np.empty(self.ntrace)
+        lam = np.empty(self.ntrace) if out is None else out
+        if lam.dtype != np.float64 or lam.size != self.ntrace or not lam.flags.c_contiguous:
+            raise ValueError("out: contiguous float64 [ntrace]")
         st = SolveStats()
         rc = lib().hmg_solve_host(self.ctx, Rub.ctypes.data_as(C.c_void_p), Rpi.ctypes.data_as(C.c_void_p),
                                   lam.ctypes.data_as(C.c_void_p), C.byref(st))
