@@ -214,6 +214,14 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
  * timings overwrite the context's work vectors. */
 int hmg_autotune(hmg_ctx *ctx);
 
+/* Read / set the launch shapes of a context (host int32 arrays): sweep[2] = {columns per
+ * block, threads per block} of the line sweep; mg[2 * nmg] = the same for the pressure
+ * smoother on each level. 0 means the default (32 columns, 256 threads, within the shared
+ * memory limit); hmg_set_launch_shapes rejects columns outside 1..64 and threads other than
+ * 0, 128 and 256. */
+int hmg_get_launch_shapes(hmg_ctx *ctx, int32_t *sweep, int32_t *mg, int32_t nmg);
+int hmg_set_launch_shapes(hmg_ctx *ctx, const int32_t *sweep, const int32_t *mg, int32_t nmg);
+
 /* Configuration 1 (Sec. 2.3, Sec. 3.2): BiCGStab on the unhybridised 2x2 system for the
  * continuous normal velocity u and the Exner increment Pi (Eq. 2x2system), preconditioned by
  * the approximate Schur complement: lumped velocity mass, Step 1 (Eq. pressure_rhs), one

@@ -526,6 +526,35 @@ int hmg_autotune(hmg_ctx *c) {
   return finish(c, autotune(c));
 }
 
+int hmg_get_launch_shapes(hmg_ctx *c, int32_t *sweep, int32_t *mg, int32_t nmg) {
+  if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
+  if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
+  sweep[0] = c->tune_sweep_cpb;
+  sweep[1] = c->tune_sweep_threads;
+  for (int l = 0; l < nmg; ++l) {
+    mg[2 * l] = c->tune_mg_cpb[l];
+    mg[2 * l + 1] = c->tune_mg_threads[l];
+  }
+  return HMG_OK;
+}
+
+int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, int32_t nmg) {
+  if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
+  if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
+  auto ok = [](int32_t cpb, int32_t thr) { return cpb >= 0 && cpb <= 64 && (thr == 0 || thr == 128 || thr == 256); };
+  if (!ok(sweep[0], sweep[1])) return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
+  for (int l = 0; l < nmg; ++l)
+    if (!ok(mg[2 * l], mg[2 * l + 1])) return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
+  drop_graph(c);   // captured launches carry the old shapes
+  c->tune_sweep_cpb = sweep[0];
+  c->tune_sweep_threads = sweep[1];
+  for (int l = 0; l < nmg; ++l) {
+    c->tune_mg_cpb[l] = mg[2 * l];
+    c->tune_mg_threads[l] = mg[2 * l + 1];
+  }
+  return HMG_OK;
+}
+
 int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
   int st = ready(c);
   if (st) return st;

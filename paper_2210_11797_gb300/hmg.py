@@ -105,6 +105,8 @@ _SIGS = {
     "hmg_solve_batched": ([C.POINTER(_P), C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                            C.POINTER(SolveStats)], C.c_int),
     "hmg_autotune": ([_P], C.c_int),
+    "hmg_get_launch_shapes": ([_P, _P, _P, C.c_int32], C.c_int),
+    "hmg_set_launch_shapes": ([_P, _P, _P, C.c_int32], C.c_int),
     "hmg_solve_mixed": ([_P, _P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
     "hmg_apply_mixed": ([_P, _P, _P], C.c_int),
     "hmg_coarse_model_size": ([], C.c_int32),
@@ -345,6 +347,20 @@ class Solver:
 
     def autotune(self):
         _check(self.ctx, lib().hmg_autotune(self.ctx))
+
+    def launch_shapes(self):
+        """((sweep columns, threads), [(smoother columns, threads) per level]); 0 = default."""
+        sw = np.zeros(2, np.int32)
+        mg = np.zeros(2 * self.nmg, np.int32)
+        _check(self.ctx, lib().hmg_get_launch_shapes(self.ctx, sw.ctypes.data_as(C.c_void_p),
+                                                     mg.ctypes.data_as(C.c_void_p), self.nmg))
+        return (int(sw[0]), int(sw[1])), [(int(mg[2 * l]), int(mg[2 * l + 1])) for l in range(self.nmg)]
+
+    def set_launch_shapes(self, sweep, mg):
+        sw = np.asarray(sweep, np.int32).ravel()
+        mgs = np.asarray(mg, np.int32).ravel()
+        _check(self.ctx, lib().hmg_set_launch_shapes(self.ctx, sw.ctypes.data_as(C.c_void_p),
+                                                     mgs.ctypes.data_as(C.c_void_p), self.nmg))
 
     def trace_operator_slots(self):
         out = self.torch.empty((11, self.ntrace), dtype=self.torch.float64, device=self.device)
