@@ -336,6 +336,31 @@ def isothermal_background(mesh: ExtrudedMesh, temperature: float = 250.0) -> Lev
     return LevelBackground(ones * (temperature / pi_lev), ones * pi_lev, ones * pi_c)
 
 
+def stratified_background(mesh: ExtrudedMesh, brunt: float = 0.012, theta_surface: float = 290.0,
+                          theta_amp: float = 20.0) -> LevelBackground:
+    """Hydrostatic atmosphere of constant Brunt-Vaisala frequency N over a horizontally varying
+    surface: theta*(z) = theta_s exp(N^2 z / g), Pi*(z) = 1 - g^2 / (c_p theta_s N^2)
+    (1 - exp(-N^2 z / g)), with theta_s = theta_surface - theta_amp sin^2(latitude) on the
+    sphere (latitude of the column centre) and theta_surface - theta_amp (1 + cos 2 pi x
+    cos 2 pi y) / 2 on the unit plane."""
+    z = mesh.z_levels
+    zc = 0.5 * (z[1:] + z[:-1])
+    centre = mesh.corners.mean(axis=1)
+    if mesh.geometry == 1:
+        s = centre[:, 2] / np.linalg.norm(centre, axis=1)
+        ts = theta_surface - theta_amp * s * s
+    else:
+        ts = theta_surface - theta_amp * 0.5 * (1.0 + np.cos(2 * math.pi * centre[:, 0]) *
+                                                 np.cos(2 * math.pi * centre[:, 1]))
+    n2g = brunt * brunt / GRAVITY
+    ts = ts[:, None]
+
+    def exner(height):
+        return 1.0 - GRAVITY * GRAVITY / (CP * ts * brunt * brunt) * (1.0 - np.exp(-n2g * height[None, :]))
+
+    return LevelBackground(ts * np.exp(n2g * z[None, :]), exner(z), exner(zc))
+
+
 def unit_background(mesh: ExtrudedMesh) -> LevelBackground:
     ones_l = np.ones((mesh.ncol, mesh.nlev + 1))
     return LevelBackground(ones_l.copy(), ones_l.copy(), np.ones((mesh.ncol, mesh.nlev)))
@@ -384,15 +409,21 @@ def planar_helmholtz(n: int = 16, nlev: int = 8, length: float = 1.0, top: float
 
 def cubed_sphere(n: int, nlev: int = 30, top: float = 30000.0, courant: float = 8.0,
                  temperature: float = 250.0, nmg: int | None = None, seed: int = 0,
-                 tol: float = 1e-6, radius: float = EARTH_RADIUS) -> Workload:
-    """Isothermal atmosphere on C_n x nlev quadratically stretched levels, N(0,1) RHS."""
+                 tol: float = 1e-6, radius: float = EARTH_RADIUS,
+                 background: str = "isothermal") -> Workload:
+    """Isothermal (or, with background="stratified", constant-N over a latitude-dependent
+    surface temperature) atmosphere on C_n x nlev quadratically stretched levels, N(0,1) RHS."""
     if nmg is None:
         nmg = mg_levels_for(n)
     hier = sphere_hierarchy(n, nlev, quadratic_levels(nlev, top), nmg, radius)
-    co = Coefficients([isothermal_background(m, temperature) for m in hier.meshes],
-                      dt=acoustic_dt(n, courant, temperature, radius), preset=0)
+    if background == "stratified":
+        bgs = [stratified_background(m) for m in hier.meshes]
+    else:
+        bgs = [isothermal_background(m, temperature) for m in hier.meshes]
+    co = Coefficients(bgs, dt=acoustic_dt(n, courant, temperature, radius), preset=0)
     rub, rpi = draw_rhs(hier.meshes[0].ncell, seed, "normal")
-    return Workload(f"cubed_sphere_C{n}_L{nlev}", hier, co, rub, rpi, tol)
+    suffix = "" if background == "isothermal" else f"_{background}"
+    return Workload(f"cubed_sphere_C{n}_L{nlev}{suffix}", hier, co, rub, rpi, tol)
 
 
 def batched_sizes(count: int = 64, seed: int = 3):

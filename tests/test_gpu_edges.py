@@ -1,7 +1,7 @@
 """Edge cases of the CUDA path against the FP64 oracle: ragged sizes (column counts and level
 counts that fill no launch shape evenly), a single layer, a single multigrid level, an odd
-cubed-sphere panel, a zero right-hand side, and the largest workload (C192 x 30, sampled
-rows). Tolerances as in test_gpu_parity: whole solves converged to 1e-12 on both sides agree
+cubed-sphere panel, a non-isothermal, horizontally varying background, a zero right-hand
+side, and the largest workload (C192 x 30, sampled rows). Tolerances as in test_gpu_parity: whole solves converged to 1e-12 on both sides agree
 to a relative 2-norm difference below 1e-9."""
 import numpy as np
 import pytest
@@ -29,6 +29,8 @@ CASES = {
     "planar8x8x5_one_mg_level": lambda: I.planar_helmholtz(n=8, nlev=5, nmg=1, seed=3),
     "sphereC3L4": lambda: I.cubed_sphere(3, 4, seed=4),
     "sphereC10L9": lambda: I.cubed_sphere(10, 9, seed=5),
+    # a general background: constant N over a latitude-dependent surface temperature
+    "sphereC8L12_stratified": lambda: I.cubed_sphere(8, 12, seed=6, background="stratified"),
 }
 
 

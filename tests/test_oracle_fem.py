@@ -263,6 +263,25 @@ def test_buoyancy_weight_is_tau_squared_dt_squared_n_squared():
     assert (cc["c22"] > 0).all()
 
 
+def test_buoyancy_weight_of_a_constant_n_background_varies_only_with_n():
+    """Over a horizontally varying surface temperature, a constant-N hydrostatic background
+    still gives -c_p d_z Pi* d_z theta* = N^2 in every cell (theta_s cancels), so the vertical
+    weight is tau_u tau_theta dt^2 N^2 everywhere, up to O(dz^2)."""
+    N = 0.012
+    hier = I.planar_hierarchy(3, 40, 1.0, I.uniform_levels(40, 2000.0), 1)
+    mesh = hier.meshes[0]
+    bg = I.stratified_background(mesh, brunt=N)
+    assert np.ptp(bg.theta_lev[:, 0]) > 5.0                 # the surface really varies
+    co = I.Coefficients([bg], dt=900.0)
+    cc = fem.cell_coefficients(mesh, bg, co)
+    np.testing.assert_allclose(cc["c22"], co.tau_u * co.tau_theta * co.dt ** 2 * N ** 2, rtol=1e-4)
+    # and the background is hydrostatic: c_p d_z Pi* = -g / theta* at the level midpoints
+    z = mesh.z_levels
+    dpi = np.diff(bg.exner_lev, axis=1) / np.diff(z)[None, :]
+    theta_mid = np.sqrt(bg.theta_lev[:, 1:] * bg.theta_lev[:, :-1])
+    np.testing.assert_allclose(I.CP * dpi, -I.GRAVITY / theta_mid, rtol=1e-4)
+
+
 def test_local_inverse_matches_extended_precision():
     """A_K^-1 (hence S_K) of physical cubed-sphere cells agrees with a 60-digit inverse to a
     few ulps of each row's scale, although A_K's entries span ~20 orders of magnitude."""
