@@ -87,12 +87,13 @@ def _vertical_unit(x: np.ndarray, geometry: int) -> np.ndarray:
     return r
 
 
-def local_mass(verts: np.ndarray, c22: np.ndarray, geometry: int):
+def local_mass(verts: np.ndarray, c22: np.ndarray, geometry: int, coriolis=None):
     """Velocity block of A_K and the volumes, by 3x3x3 Gauss quadrature (Sec. 2.2).
 
-    M_K(f,g) = int_K [v_f.v_g + c22 (zhat.v_f)(zhat.v_g)] dx with the contravariant Piola
-    map v = J vhat / det J; c22 is the vertical weight of -Q22 (reading of the mu term
-    in the design doc). Returns M [n,6,6], |K| (Gauss) [n], |K|_1 (one-point) [n] and
+    M_K(f,g) = int_K [v_f.v_g + c22 (zhat.v_f)(zhat.v_g) + v_f.(c x v_g)] dx with the
+    contravariant Piola map v = J vhat / det J; c22 is the vertical weight of -Q22 (reading
+    of the mu term in the design doc) and c = tau_u dt 2 Omega the Coriolis vector of Eq. gh-u
+    (None: no rotation). Returns M [n,6,6], |K| (Gauss) [n], |K|_1 (one-point) [n] and
     (zhat . v_f) at the cell centre [n,6].
     """
     n = verts.shape[0]
@@ -112,6 +113,9 @@ def local_mass(verts: np.ndarray, c22: np.ndarray, geometry: int):
                 M += (w / det)[:, None, None] * (
                     np.matmul(Jv.transpose(0, 2, 1), Jv)
                     + c22[:, None, None] * np.matmul(rv.transpose(0, 2, 1), rv))
+                if coriolis is not None:
+                    cxv = np.cross(np.asarray(coriolis, np.float64)[None, :, None], Jv, axis=1)   # c x (J vhat_g)
+                    M += (w / det)[:, None, None] * np.matmul(Jv.transpose(0, 2, 1), cxv)
                 vol += w * det
     N, dN = trilinear_shape(0.5, 0.5, 0.5)
     xc = N @ verts
@@ -154,7 +158,11 @@ def cell_coefficients(mesh, bg, co, cells=None):
     else:
         # -Q22 weight: -tau_u tau_theta dt^2 c_p (d_z hatPi*)(d_z theta*), constant per cell
         c22 = -co.tau_u * co.tau_theta * co.dt ** 2 * co.cp * ((pi1 - pi0) / dz) * ((th1 - th0) / dz)
-    M, vol, vol1, zv = local_mass(verts, c22, mesh.geometry)
+    omega = getattr(co, "omega", 0.0)
+    # Coriolis (Eq. gh-u): tau_u dt 2 Omega, the rotation axis being the sphere's polar axis
+    # (z of the Earth-centred frame) or the vertical of the plane (an f-plane)
+    cor = None if (co.preset == 1 or omega == 0.0) else (0.0, 0.0, co.tau_u * co.dt * 2.0 * omega)
+    M, vol, vol1, zv = local_mass(verts, c22, mesh.geometry, cor)
     theta = np.zeros((len(cells), 6))
     mean_own = 0.5 * (th0 + th1)
     for f in range(4):

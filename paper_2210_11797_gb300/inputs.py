@@ -37,6 +37,7 @@ GRAVITY = 9.80616
 CP = 1004.5
 R_DRY = 287.05
 KAPPA = R_DRY / CP
+EARTH_OMEGA = 7.292e-5   # rad/s
 EARTH_RADIUS = 6.371e6
 
 
@@ -324,6 +325,7 @@ class Coefficients:
     kappa: float = KAPPA
     preset: int = 0          # 0 physical, 1 constant-coefficient Helmholtz
     sigma: float = 0.0       # preset 1 shift: m_K = sigma |K|
+    omega: float = 0.0       # rotation rate (rad/s) about the polar axis / the vertical
 
 
 def isothermal_background(mesh: ExtrudedMesh, temperature: float = 250.0) -> LevelBackground:
@@ -410,7 +412,7 @@ def planar_helmholtz(n: int = 16, nlev: int = 8, length: float = 1.0, top: float
 def cubed_sphere(n: int, nlev: int = 30, top: float = 30000.0, courant: float = 8.0,
                  temperature: float = 250.0, nmg: int | None = None, seed: int = 0,
                  tol: float = 1e-6, radius: float = EARTH_RADIUS,
-                 background: str = "isothermal") -> Workload:
+                 background: str = "isothermal", omega: float = 0.0) -> Workload:
     """Isothermal (or, with background="stratified", constant-N over a latitude-dependent
     surface temperature) atmosphere on C_n x nlev quadratically stretched levels, N(0,1) RHS."""
     if nmg is None:
@@ -420,9 +422,9 @@ def cubed_sphere(n: int, nlev: int = 30, top: float = 30000.0, courant: float = 
         bgs = [stratified_background(m) for m in hier.meshes]
     else:
         bgs = [isothermal_background(m, temperature) for m in hier.meshes]
-    co = Coefficients(bgs, dt=acoustic_dt(n, courant, temperature, radius), preset=0)
+    co = Coefficients(bgs, dt=acoustic_dt(n, courant, temperature, radius), preset=0, omega=omega)
     rub, rpi = draw_rhs(hier.meshes[0].ncell, seed, "normal")
-    suffix = "" if background == "isothermal" else f"_{background}"
+    suffix = ("" if background == "isothermal" else f"_{background}") + ("" if omega == 0.0 else "_rotating")
     return Workload(f"cubed_sphere_C{n}_L{nlev}{suffix}", hier, co, rub, rpi, tol)
 
 

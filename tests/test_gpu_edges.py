@@ -1,7 +1,8 @@
 """Edge cases of the CUDA path against the FP64 oracle: ragged sizes (column counts and level
 counts that fill no launch shape evenly), a single layer, a single multigrid level, an odd
 cubed-sphere panel, a non-isothermal, horizontally varying background, a zero right-hand
-side, and the largest workload (C192 x 30, sampled rows). Tolerances as in test_gpu_parity: whole solves converged to 1e-12 on both sides agree
+side, and the largest workload (C192 x 30, sampled rows). Tolerances as in test_gpu_parity:
+whole solves converged to 1e-12 on both sides agree
 to a relative 2-norm difference below 1e-9."""
 import numpy as np
 import pytest

@@ -319,3 +319,61 @@ def test_trace_row_sums_identity():
         exact = [float(sum(ex[i, j] * mp.mpf(Kd[cell, j]) for j in range(6))) for i in range(6)]
         got = A[cell, 6, 6] * fem.local_inverse(A[cell:cell + 1])[0, :6, 6]
         np.testing.assert_allclose(got, exact, rtol=1e-12)
+
+
+def test_coriolis_block_on_a_box_closed_form():
+    """f-plane box, c = tau_u dt 2 Omega zhat: v_f.(c x v_g) couples only the x faces with the
+    y faces, C(f,g) = -c/hz * A_f * B_g with A, B = +1/2 on the faces at 1 and -1/2 at 0,
+    antisymmetric; rows and columns of the vertical faces stay untouched."""
+    hx, hy, hz, c = 0.7, 0.3, 0.05, 2.5
+    verts = np.zeros((1, 8, 3))
+    for v in range(8):
+        verts[0, v] = ((v & 1) * hx, ((v >> 1) & 1) * hy, ((v >> 2) & 1) * hz)
+    M0 = fem.local_mass(verts, np.zeros(1), 0)[0][0]
+    M1 = fem.local_mass(verts, np.zeros(1), 0, (0.0, 0.0, c))[0][0]
+    C = M1 - M0
+    half = {0: -0.5, 1: 0.5, 2: 0.5, 3: -0.5}      # local faces: 0 y=0, 1 x=1, 2 y=1, 3 x=0
+    want = np.zeros((6, 6))
+    for f in (1, 3):
+        for g in (0, 2):
+            want[f, g] = -c / hz * half[f] * half[g]
+            want[g, f] = -want[f, g]
+    np.testing.assert_allclose(C, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_rotation_adds_an_antisymmetric_block_and_keeps_the_pressure_operator():
+    """On curved sphere cells the Coriolis part of M_K is antisymmetric and the symmetric part
+    is the non-rotating M_K; the lumped mass (diagonal and opposite-face entries) and so H
+    do not see the rotation."""
+    from oracle.pressure_mg import pressure_operator
+    w0 = I.cubed_sphere(4, 3, seed=1)
+    w1 = I.cubed_sphere(4, 3, seed=1, omega=10 * I.EARTH_OMEGA)
+    cells = [0, 5, 40, w0.mesh.ncell - 1]
+    M0 = fem.cell_coefficients(w0.mesh, w0.coeffs.levels[0], w0.coeffs, cells)["M"]
+    M1 = fem.cell_coefficients(w1.mesh, w1.coeffs.levels[0], w1.coeffs, cells)["M"]
+    C = M1 - M0
+    assert np.abs(C).max() > 1e-6 * np.abs(M0).max()
+    np.testing.assert_allclose(C + C.transpose(0, 2, 1), 0.0, atol=1e-13 * np.abs(M0).max())
+    H0 = pressure_operator(w0.mesh, w0.coeffs.levels[0], w0.coeffs)
+    H1 = pressure_operator(w1.mesh, w1.coeffs.levels[0], w1.coeffs)
+    assert abs(H1 - H0).max() <= 1e-12 * abs(H0).max()
+
+
+def test_rotating_hybridised_solution_equals_mixed_solution():
+    """With Coriolis the cell matrices are not symmetric; hybridise-then-recover still equals
+    the dense direct solve of the unhybridised 2x2 system."""
+    w = I.cubed_sphere(2, 3, seed=3, omega=20 * I.EARTH_OMEGA)
+    Mx, rhs, interior = fem.mixed_system(w.mesh, w.coeffs.levels[0], w.coeffs, w.Rub, w.Rpi)
+    x = np.linalg.solve(Mx, rhs)
+    nf = len(interior)
+    hs = HybridSolver(w.hier, w.coeffs)
+    S = hs.S.toarray()
+    assert np.abs(S - S.T).max() > 1e-8 * np.abs(S).max()          # really non-symmetric
+    lam = np.linalg.solve(S, hs.rhs(w.Rub, w.Rpi))
+    ub, pi = hs.reconstruct(lam, w.Rub, w.Rpi)
+    np.testing.assert_allclose(pi, x[nf:], rtol=1e-9, atol=1e-10 * np.abs(x[nf:]).max())
+    s = fem.face_orientation(w.mesh)
+    g = fem.trace_dof_ids(w.mesh)
+    u = np.zeros(w.mesh.n_trace)
+    u[interior] = x[:nf]
+    np.testing.assert_allclose(ub, s * u[g], rtol=1e-9, atol=1e-10 * np.abs(ub).max())
