@@ -84,6 +84,9 @@ typedef struct {
   double dt, tau_u, tau_rho, tau_theta, cp, kappa;
   int32_t preset;
   double sigma;
+  double omega;  /* rotation rate (rad/s) of the Coriolis term 2 Omega x u of Eq. gh-u (preset
+                    0), about the z axis of the sphere's Earth-centred frame or the vertical of
+                    the plane (an f-plane); 0: no rotation. Makes A_K non-symmetric. */
 } hmg_scalars;
 
 /* ---- options ----------------------------------------------------------------------- */

@@ -281,6 +281,7 @@ int hmg_set_coefficients(hmg_ctx *c, const hmg_scalars *sc, const hmg_background
   if (!c->have_mesh) return fail(c, HMG_ERR_NOT_READY, "set the mesh first");
   if (sc->preset != 0 && sc->preset != 1) return fail(c, HMG_ERR_INVALID_ARG, "preset must be 0 or 1");
   if (sc->preset == 1 && !(sc->sigma >= 0.0)) return fail(c, HMG_ERR_INVALID_ARG, "sigma must be >= 0");
+  if (!std::isfinite(sc->omega)) return fail(c, HMG_ERR_INVALID_ARG, "omega must be finite");
   if (sc->preset == 0 && !(sc->dt > 0.0 && sc->cp > 0.0 && sc->kappa > 0.0 && sc->kappa < 1.0))
     return fail(c, HMG_ERR_INVALID_ARG, "dt, cp > 0 and 0 < kappa < 1 required");
   HMG_CUDA(c, cudaSetDevice(c->device));

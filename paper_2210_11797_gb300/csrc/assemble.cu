@@ -61,9 +61,13 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
   const double gq = sqrt(15.0) / 10.0;
   const double gx[3] = {0.5 - gq, 0.5, 0.5 + gq};
   const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-  double M[21];
+  double M[21], Cor[15];
 #pragma unroll
   for (int i = 0; i < 21; ++i) M[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) Cor[i] = 0.0;
+  // Coriolis vector tau_u dt 2 Omega about z (Eq. gh-u); none for the Helmholtz preset
+  const double cz = helm ? 0.0 : a.sc.tau_u * a.sc.dt * 2.0 * a.sc.omega;
   double vol = 0.0;
   for (int q = 0; q < 27; ++q) {
     const int qi = q % 3, qj = (q / 3) % 3, qk = q / 9;
@@ -110,6 +114,20 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
         M[idx] += wd * s[f] * s[g] * (G[dir[f]][dir[g]] + c22 * rJ[dir[f]] * rJ[dir[g]]);
         ++idx;
       }
+    }
+    if (cz != 0.0) {
+      // v_f . (c x v_g) = s_f s_g c . (J_dg x J_df) / det^2: X[d][e] = (c x-products of the
+      // columns of J), antisymmetric; c = (0, 0, cz)
+      double X[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) X[d][e] = cz * (J[0][e] * J[1][d] - J[1][e] * J[0][d]);
+      int ci = 0;
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int g = f + 1; g < 6; ++g) Cor[ci++] += wd * s[f] * s[g] * X[dir[f]][dir[g]];
     }
     vol += w * det;
   }
@@ -170,6 +188,8 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
 #pragma unroll
   for (int i = 0; i < 21; ++i) out[CellRec::M + i] = M[i];
 #pragma unroll
+  for (int i = 0; i < 15; ++i) out[CellRec::CORI + i] = Cor[i];
+#pragma unroll
   for (int f = 0; f < 6; ++f) {
     out[CellRec::B + f] = b[f];
     out[CellRec::KTH + f] = kk * theta[f];
@@ -188,9 +208,10 @@ __device__ __forceinline__ double mget(const double *M, int f, int g) {
 }
 
 // A_K = [[M, g], [b^T, m]] with g = -KTH (Eq. hybrid-A). A_K^-1 by block elimination:
-// M^-1 from the Cholesky factor of the equilibrated velocity block D M D (D = diag(M)^-1/2,
-// symmetric positive definite), y = M^-1 g, z = M^-1 b, pressure Schur complement
-// s = m - b.y, then A^-1 = [[M^-1 + y z^T / s, -y / s], [-z^T / s, 1 / s]]. The rows of
+// M^-1 from the LU factors of the equilibrated velocity block D M D (D = diag(M)^-1/2; its
+// symmetric part is positive definite, the Coriolis part antisymmetric), y = M^-1 g,
+// z = M^-T b, pressure Schur complement s = m - b.y, then
+// A^-1 = [[M^-1 + y z^T / s, -y / s], [-z^T / s, 1 / s]]. The rows of
 // A_K span ~20 orders of magnitude on the sphere; this form keeps every entry within a few
 // ulps of its row's scale, where pivoting on A_K itself can lose 1e-12.
 // Outputs: Ainv entry-major ((7 i + j) * ncell + K), S_K = (A^-1)_uu diag(KTH) entry-major,
@@ -204,54 +225,59 @@ __global__ void __launch_bounds__(128) condense_kernel(int64_t ncell, const doub
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= ncell) return;
   const double *r = rec + K * kCellData;
-  double d[6], L[6][6], Li[6][6];
+  // M_K = symmetric part (21 stored) + Coriolis part (antisymmetric, 15 stored)
+  auto mfull = [&](int f, int g) {
+    double v = mget(r + CellRec::M, f, g);
+    if (f < g) v += r[CellRec::CORI + f * 6 - f * (f + 1) / 2 + (g - f - 1)];
+    else if (f > g) v -= r[CellRec::CORI + g * 6 - g * (g + 1) / 2 + (f - g - 1)];
+    return v;
+  };
+  double d[6], A[6][6];
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const double mff = fabs(mget(r + CellRec::M, f, f));
     if (!(mff > 0.0)) { atomicExch(singular, 1); return; }
     d[f] = 1.0 / sqrt(mff);
   }
-  // Cholesky of Ms = D M D
 #pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    double s = d[j] * mget(r + CellRec::M, j, j) * d[j];
+  for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int q = 0; q < j; ++q) s -= L[j][q] * L[j][q];
-    if (!(s > 0.0)) { atomicExch(singular, 1); return; }
-    L[j][j] = sqrt(s);
-    const double inv = 1.0 / L[j][j];
+    for (int j = 0; j < 6; ++j) A[i][j] = d[i] * mfull(i, j) * d[j];
+  // LU of the equilibrated D M D without pivoting (its symmetric part is positive definite,
+  // so every pivot is positive; with no rotation this is the symmetric case), in place
 #pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      double t = d[i] * mget(r + CellRec::M, i, j) * d[j];
+  for (int k = 0; k < 6; ++k) {
+    if (!(A[k][k] > 0.0)) { atomicExch(singular, 1); return; }
+    const double inv = 1.0 / A[k][k];
 #pragma unroll
-      for (int q = 0; q < j; ++q) t -= L[i][q] * L[j][q];
-      L[i][j] = t * inv;
+    for (int i = k + 1; i < 6; ++i) {
+      const double l = A[i][k] * inv;
+      A[i][k] = l;
+#pragma unroll
+      for (int j = k + 1; j < 6; ++j) A[i][j] -= l * A[k][j];
     }
   }
-  // Li = L^-1 (lower triangular)
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    Li[j][j] = 1.0 / L[j][j];
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      double t = 0.0;
-#pragma unroll
-      for (int q = j; q < i; ++q) t += L[i][q] * Li[q][j];
-      Li[i][j] = -t / L[i][i];
-    }
-  }
-  // M^-1 = D Li^T Li D (symmetric)
+  // M^-1 = D (LU)^-1 D, column by column
   double Mi[6][6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  for (int c = 0; c < 6; ++c) {
+    double y[6];
 #pragma unroll
-    for (int j = i; j < 6; ++j) {
-      double t = 0.0;
+    for (int i = 0; i < 6; ++i) {
+      double t = i == c ? 1.0 : 0.0;
 #pragma unroll
-      for (int q = j; q < 6; ++q) t += Li[q][i] * Li[q][j];
-      Mi[i][j] = d[i] * t * d[j];
-      Mi[j][i] = Mi[i][j];
+      for (int q = 0; q < i; ++q) t -= A[i][q] * y[q];
+      y[i] = t;
     }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+      double t = y[i];
+#pragma unroll
+      for (int q = i + 1; q < 6; ++q) t -= A[i][q] * y[q];
+      y[i] = t / A[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) Mi[i][c] = d[i] * y[i] * d[c];
   }
   double kth[6], g[6], b[6], y[6], z[6];
 #pragma unroll
@@ -265,7 +291,7 @@ __global__ void __launch_bounds__(128) condense_kernel(int64_t ncell, const doub
   for (int i = 0; i < 6; ++i) {
     double ty = 0.0, tz = 0.0;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) { ty += Mi[i][j] * g[j]; tz += Mi[i][j] * b[j]; }
+    for (int j = 0; j < 6; ++j) { ty += Mi[i][j] * g[j]; tz += Mi[j][i] * b[j]; }   // y = M^-1 g, z = M^-T b
     y[i] = ty;
     z[i] = tz;
   }

@@ -15,7 +15,7 @@ namespace hmg {
 constexpr int kMaxLevels = 8;
 constexpr int kSlots = 11;      // coefficients per trace row of S
 constexpr int kHCoef = 7;       // coefficients per cell of H: diag, e0..e3, below, above
-constexpr int kCellData = 40;   // per-cell assembly record (see CellRec)
+constexpr int kCellData = 55;   // per-cell assembly record (see CellRec)
 constexpr int kRedBlocks = 1216;  // blocks of the grid-stride vector reductions (8 per SM)
 constexpr int kMaxRedBlocks = 1 << 18;  // partial-sum slots per reduction (one row per thread)
 constexpr int kRedThreads = 256;
@@ -28,6 +28,7 @@ struct CellRec {
   static constexpr int KTH = 27;   // 6: k * theta_f (diagonal of K_K; G_K = -KTH)
   static constexpr int MPI = 33;   // 1: M3^Pi
   static constexpr int LUMP = 34;  // 6: this cell's share of the lumped mass of each face
+  static constexpr int CORI = 40;  // 15: Coriolis part of M_K (antisymmetric), f < g row-major
 };
 
 // Reduction slots of the scalar block kept on the device.

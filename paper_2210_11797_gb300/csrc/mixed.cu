@@ -34,10 +34,16 @@ __device__ __forceinline__ double face_sign(const MixedArgs &a, int c, int f) {
   return (__ldg(a.stencil + 8 * (int64_t)e) == c && __ldg(a.edge_fc + 2 * (int64_t)e) == f) ? 1.0 : -1.0;
 }
 
-// upper-triangular M_K (21 entries, f <= g, row-major) of a cell record
+// M_K(f, g) of a cell record: the symmetric part (21 entries, f <= g, row-major) plus the
+// antisymmetric Coriolis part (15 entries, f < g, row-major)
 __device__ __forceinline__ double rec_m(const double *r, int f, int g) {
-  if (f > g) { const int t = f; f = g; g = t; }
-  return r[CellRec::M + f * 6 - f * (f - 1) / 2 + (g - f)];
+  const int a = f < g ? f : g, b = f < g ? g : f;
+  double v = r[CellRec::M + a * 6 - a * (a - 1) / 2 + (b - a)];
+  if (a != b) {
+    const double c = r[CellRec::CORI + a * 6 - a * (a + 1) / 2 + (b - a - 1)];
+    v += f < g ? c : -c;
+  }
+  return v;
 }
 
 // Facet rows: velocity block (11 slots, sign-applied M_K summed over the facet's cells), the

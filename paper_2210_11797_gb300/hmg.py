@@ -50,7 +50,7 @@ class Background(C.Structure):
 class Scalars(C.Structure):
     _fields_ = [("dt", C.c_double), ("tau_u", C.c_double), ("tau_rho", C.c_double),
                 ("tau_theta", C.c_double), ("cp", C.c_double), ("kappa", C.c_double),
-                ("preset", C.c_int32), ("sigma", C.c_double)]
+                ("preset", C.c_int32), ("sigma", C.c_double), ("omega", C.c_double)]
 
 
 class Options(C.Structure):
@@ -230,7 +230,8 @@ class Solver:
         self.level_cells = [m.ncell for m in hier.meshes]
 
     def _set_coefficients(self, co):
-        sc = Scalars(co.dt, co.tau_u, co.tau_rho, co.tau_theta, co.cp, co.kappa, co.preset, co.sigma)
+        sc = Scalars(co.dt, co.tau_u, co.tau_rho, co.tau_theta, co.cp, co.kappa, co.preset, co.sigma,
+                     getattr(co, "omega", 0.0))
         bgs = (Background * len(co.levels))()
         for l, bg in enumerate(co.levels):
             bgs[l].theta_lev = self._arr(bg.theta_lev, np.float64)

@@ -50,7 +50,7 @@ def test_struct_layouts_match_header():
     # sizes follow from the C declarations in include/hmg.h (x86-64 and aarch64 LP64 ABIs)
     assert ctypes.sizeof(hmg.MeshLevel) == 4 * 4 + 8 + 6 * 8
     assert ctypes.sizeof(hmg.Background) == 3 * 8
-    assert ctypes.sizeof(hmg.Scalars) == 6 * 8 + 8 + 8
+    assert ctypes.sizeof(hmg.Scalars) == 6 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(hmg.SolveStats) == 4 + 4 + 3 * 8 + 8 + hmg.MAX_HISTORY * 8 + 8 * 8 + 8 * 4
     assert ctypes.sizeof(hmg.Options) == 112
 

@@ -26,6 +26,7 @@ WORKLOADS = {
     "planar16": lambda: I.planar_helmholtz(),
     "sphereC6L5": lambda: I.cubed_sphere(6, 5, courant=8.0, nmg=2, seed=4),
     "sphereC12L30": lambda: I.cubed_sphere(12, 30),
+    "sphereC6L5_rotating": lambda: I.cubed_sphere(6, 5, courant=8.0, nmg=2, seed=4, omega=10 * I.EARTH_OMEGA),
 }
 _CACHE = {}
 

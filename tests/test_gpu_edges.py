@@ -1,6 +1,7 @@
 """Edge cases of the CUDA path against the FP64 oracle: ragged sizes (column counts and level
 counts that fill no launch shape evenly), a single layer, a single multigrid level, an odd
-cubed-sphere panel, a non-isothermal, horizontally varying background, a zero right-hand
+cubed-sphere panel, a non-isothermal, horizontally varying background, a rotating planet
+(Coriolis: non-symmetric cell matrices), a zero right-hand
 side, and the largest workload (C192 x 30, sampled rows). Tolerances as in test_gpu_parity:
 whole solves converged to 1e-12 on both sides agree
 to a relative 2-norm difference below 1e-9."""
@@ -32,6 +33,8 @@ CASES = {
     "sphereC10L9": lambda: I.cubed_sphere(10, 9, seed=5),
     # a general background: constant N over a latitude-dependent surface temperature
     "sphereC8L12_stratified": lambda: I.cubed_sphere(8, 12, seed=6, background="stratified"),
+    # Coriolis (10x the Earth's rate): non-symmetric cell matrices and trace operator
+    "sphereC8L12_rotating": lambda: I.cubed_sphere(8, 12, seed=7, omega=10 * I.EARTH_OMEGA),
 }
 
 
