@@ -123,6 +123,10 @@ typedef struct {
   double stall_ratio;   /* FGMRES with a learned coarse solve falls back to the V-cycle for the
                            rest of the solve after two consecutive steps that each reduce the
                            residual estimate by less than this factor (0.9) */
+  int32_t warm_start;   /* 0 (default, the paper): the Krylov iteration starts from zero;
+                           1: from the lambda (hmg_solve) or [u | Pi] (hmg_solve_mixed, its
+                           internal copy of the last solution) passed in, r_0 = B - S lambda_0
+                           (resuming a solve, or a previous time step's solution) */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
@@ -153,6 +157,7 @@ typedef struct {
   double history[HMG_MAX_HISTORY];
   double comp_ms[HMG_NCOMP]; /* device time per component (profile = 1), else 0 */
   int32_t comp_calls[HMG_NCOMP]; /* kernel launches per component (profile = 1) */
+  int32_t coarse_fallback;   /* 1 if a learned coarse solve was replaced by the V-cycle */
 } hmg_solve_stats;
 
 /* ---- lifecycle --------------------------------------------------------------------- */
@@ -310,6 +315,12 @@ int hmg_get_trace_operator(hmg_ctx *ctx, double *slots);
  * activations in BF16 and accumulate in FP32 (fp32 = 1 keeps them in FP32, for checks).
  * Use it with HMG_KRYLOV_FGMRES (the map is not linear). Corner neighbours: across local
  * face i to column n, then across the face of n that follows the shared one (mod 4). */
+
+/* Self-test of the bounded device-side waits of the tensor-core kernels: one kernel waits
+ * on an mbarrier that nothing arrives on, gives up after `polls` polls (1..2^24), records
+ * the expiry in a device flag and returns; the call then reports HMG_ERR_TIMEOUT (the
+ * expected result) and leaves the context usable. Anything else is a failure. */
+int hmg_check_device_wait(hmg_ctx *ctx, int32_t polls);
 
 /* Number of parameters (3360). */
 int32_t hmg_coarse_model_size(void);

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hmg_internal.cuh"
 
 namespace hmg {
@@ -46,6 +48,7 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.krylov != HMG_KRYLOV_BICGSTAB && o.krylov != HMG_KRYLOV_FGMRES) return bad("krylov");
   if (o.restart < 1 || o.restart > 64) return bad("restart must be in 1..64");
   if (!(o.stall_ratio > 0.0)) return bad("stall_ratio");
+  if (o.warm_start != 0 && o.warm_start != 1) return bad("warm_start must be 0 or 1");
   return HMG_OK;
 }
 
@@ -58,13 +61,21 @@ static int next_event(Ctx *c) {
   return c->ev_next++;
 }
 
+// NVTX range names of the components (the names of hmg_solve_stats.comp_ms)
+static const char *const kCompNames[HMG_NCOMP] = {"trace_rhs", "trace_apply", "presmooth", "line_sweep",
+                                                  "residual_restrict", "pressure_vcycle", "prolong",
+                                                  "krylov_vectors"};
+
 Prof::Prof(Ctx *c, int comp, int launches) : c_(c), comp_(comp), launches_(launches) {
   if (!c_->opt.profile) return;
+  nvtxRangePushA(kCompNames[comp_]);   // visible to a profiler attached to the process
   e0_ = next_event(c_);
   if (e0_ >= 0) cudaEventRecord(c_->ev_pool[e0_], c_->stream);
 }
 
 Prof::~Prof() {
+  if (!c_->opt.profile) return;
+  nvtxRangePop();
   if (e0_ < 0) return;
   const int e1 = next_event(c_);
   if (e1 < 0) return;
@@ -441,6 +452,8 @@ int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lam
   double *dRub = c->host_in, *dRpi = dRub + 6 * f.ncell, *dlam = dRpi + f.ncell;
   HMG_CUDA(c, cudaMemcpyAsync(dRub, Rub, sizeof(double) * 6 * f.ncell, cudaMemcpyHostToDevice, c->stream));
   HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * f.ncell, cudaMemcpyHostToDevice, c->stream));
+  if (c->opt.warm_start)   // the initial lambda comes from the host buffer too
+    HMG_CUDA(c, cudaMemcpyAsync(dlam, lambda, sizeof(double) * f.ntrace, cudaMemcpyHostToDevice, c->stream));
   const int solve_st = krylov_solve(c, dRub, dRpi, dlam, stats);
   if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
       solve_st != HMG_ERR_NONFINITE)
@@ -583,6 +596,15 @@ static int mesh_ready(hmg_ctx *c) {
 }
 
 int32_t hmg_coarse_model_size(void) { return kCoarseParams; }
+
+int hmg_check_device_wait(hmg_ctx *c, int32_t polls) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (polls < 1 || polls > (1 << 24)) return fail(c, HMG_ERR_INVALID_ARG, "polls must be in 1..2^24");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  int st = wait_selftest(c, (uint32_t)polls);
+  if (st) return st;
+  return check_wait_flag(c);
+}
 
 int hmg_set_coarse_model(hmg_ctx *c, const float *params, int32_t n) {
   int st = mesh_ready(c);

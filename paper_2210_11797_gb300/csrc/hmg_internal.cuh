@@ -253,6 +253,8 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
                        int epochs, double lr, uint64_t seed, double *loss_hist);
 int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, const int32_t *pair,
                     const int32_t *cols, int npatch, int P, float *xo, float *to);
+// launches a kernel whose bounded mbarrier wait must run out (sets state[3])
+int wait_selftest(Ctx *c, uint32_t limit);
 // records (D^-1/2 bbar, D^1/2 H^-1 bbar) for the current preconditioner call (FP64 path)
 int collect_pair(Ctx *c, const double *bbar);
 // r = b - H_l x (FP64) on level l

@@ -69,7 +69,21 @@ __global__ void bicg_init_kernel(const double *__restrict__ B, double *__restric
 struct LoopParams {
   double tol, divergence;
   int max_iter;
+  int warm;   // the iteration starts from the lambda passed in (r_0 = B - S lambda_0)
 };
+
+// warm start: r = B - y (y = S x_0 on entry in r), rhat = r, p = v = 0; x is kept
+__global__ void bicg_init_warm_kernel(const double *__restrict__ B, double *__restrict__ r,
+                                      double *__restrict__ rhat, double *__restrict__ p,
+                                      double *__restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = B[i] - r[i];
+    r[i] = ri;
+    rhat[i] = ri;
+    p[i] = 0.0;
+    v[i] = 0.0;
+  }
+}
 
 // rho_0 = (B, B), rho_-1 = alpha = omega = 1; iteration state and history[0]; the loop runs
 // while B != 0 is finite, the tolerance is not met and iterations are allowed.
@@ -77,18 +91,20 @@ template <bool GRAPH>
 __global__ void bicg_start_kernel(double *scal, int *state, double *hist, LoopParams lp,
                                   cudaGraphConditionalHandle handle) {
   const double bb = scal[Scal::BB];
-  scal[Scal::RHO0] = bb;
+  const double rr0 = lp.warm ? scal[Scal::RR] : bb;   // (rhat, r_0) = ||r_0||^2
+  scal[Scal::RHO0] = rr0;
   scal[Scal::RHO1] = 1.0;
   scal[Scal::ALPHA] = 1.0;
   scal[Scal::OMEGA] = 1.0;
-  int status = isfinite(bb) ? HMG_OK : HMG_ERR_NONFINITE;
-  const bool work = status == HMG_OK && bb > 0.0 && 1.0 > lp.tol;
+  const double rel0 = bb > 0.0 ? sqrt(rr0 / bb) : 0.0;
+  int status = isfinite(bb) && isfinite(rr0) ? HMG_OK : HMG_ERR_NONFINITE;
+  const bool work = status == HMG_OK && bb > 0.0 && rel0 > lp.tol;
   if (work && lp.max_iter <= 0) status = HMG_ERR_NOT_CONVERGED;
   const int cont = work && lp.max_iter > 0;
   state[kIt] = 0;
   state[kStatus] = status;
   state[kContinue] = cont;
-  hist[0] = bb > 0.0 ? 1.0 : 0.0;
+  hist[0] = rel0;
   if (GRAPH) cudaGraphSetConditional(handle, cont);
 }
 
@@ -167,7 +183,7 @@ __global__ void bicg_check_kernel(const double *scal, int *state, double *hist, 
 }
 
 static LoopParams loop_params(const Ctx *c) {
-  return LoopParams{c->opt.tol, c->opt.divergence, c->opt.max_iter};
+  return LoopParams{c->opt.tol, c->opt.divergence, c->opt.max_iter, c->opt.warm_start ? 1 : 0};
 }
 
 // B_lambda, (B, B), x = 0, r = rhat = B, loop state
@@ -178,7 +194,13 @@ static int solve_head(Ctx *c, const double *Rub, const double *Rpi, double *x, b
   if ((s = sys_rhs(c, Rub, Rpi, c->B))) return s;
   Prof pk(c, kCompKrylov, 3);
   if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
-  bicg_init_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, x, c->r, c->rhat, c->p, c->v, n);
+  if (c->opt.warm_start) {
+    if ((s = sys_apply(c, x, c->r, 0, nullptr, 0, 0))) return s;
+    bicg_init_warm_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, c->r, c->rhat, c->p, c->v, n);
+    if ((s = launch_dot(c, c->r, c->r, n, Scal::RR))) return s;
+  } else {
+    bicg_init_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, x, c->r, c->rhat, c->p, c->v, n);
+  }
   if (graph) bicg_start_kernel<true><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
   else bicg_start_kernel<false><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
   HMG_CUDA(c, cudaGetLastError());
@@ -331,6 +353,7 @@ static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
     st->rel_residual = st->history[st->n_history - 1];
     st->true_rel_residual = bnorm > 0.0 ? std::sqrt(c->scal_host[Scal::AUX]) / bnorm : 0.0;
     st->solve_ms = ms;
+    st->coarse_fallback = c->coarse_fallback ? 1 : 0;
     for (int q = 0; q < HMG_NCOMP; ++q) { st->comp_ms[q] = 0.0; st->comp_calls[q] = 0; }
     for (const Ctx::Mark &m : c->marks) {
       float t = 0.f;
@@ -599,18 +622,28 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
   {
     Prof pk(c, kCompKrylov, 6);
     if ((s = launch_dot(c, c->B, c->B, n, Scal::BB))) return s;
-    HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
-    HMG_CUDA(c, cudaMemcpyAsync(V, c->B, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->opt.warm_start) {   // r_0 = B - S lambda_0
+      if ((s = sys_apply(c, x, c->t, 0, nullptr, 0, 0))) return s;
+      gm_sub_kernel<<<red_grid(n), kRedThreads, 0, c->stream>>>(c->B, c->t, V, n);
+      HMG_CUDA(c, cudaGetLastError());
+    } else {
+      HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+      HMG_CUDA(c, cudaMemcpyAsync(V, c->B, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
     if ((s = normalize(c, V, sc, sc + 1, &beta))) return s;
   }
-  const double bnorm = beta;
-  std::vector<double> hist{bnorm > 0.0 ? 1.0 : 0.0};
+  double bb_host = 0.0;
+  HMG_CUDA(c, cudaMemcpyAsync(&bb_host, c->scal + Scal::BB, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double bnorm = std::sqrt(bb_host);
+  std::vector<double> hist{bnorm > 0.0 ? beta / bnorm : 0.0};
   const int kRunning = -1;
-  int status = !std::isfinite(bnorm) ? HMG_ERR_NONFINITE : (bnorm == 0.0 || 1.0 <= c->opt.tol) ? HMG_OK : kRunning;
+  int status = !std::isfinite(bnorm) || !std::isfinite(beta) ? HMG_ERR_NONFINITE
+               : (bnorm == 0.0 || hist[0] <= c->opt.tol) ? HMG_OK : kRunning;
   if (status == kRunning && c->opt.max_iter <= 0) status = HMG_ERR_NOT_CONVERGED;
   std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), col(m + 2), y(m);
   int steps = 0, slow = 0;
-  double prev_rel = 1.0;
+  double prev_rel = hist[0];
   while (status == kRunning) {
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;

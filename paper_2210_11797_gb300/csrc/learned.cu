@@ -141,7 +141,7 @@ constexpr int kTcBWindow = 8 * 1024;      // B region: 6 KB used
 constexpr int kTcX = kTcB + kTcBWindow;   // x (132 floats), W1 (96 floats), row levels (128 ints)
 constexpr int kTcBar = kTcX + 2048;       // two mbarriers (16 B) and the TMEM address (4 B)
 constexpr int kTcSmem = kTcBar + 64;
-constexpr uint32_t kTcWaitLimit = 1u << 24;   // mbarrier polls before the kernel gives up
+constexpr uint32_t kTcWaitLimit = 1u << 20;   // mbarrier polls before the kernel gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -170,9 +170,9 @@ __global__ void nn_pack_b_kernel(const float *__restrict__ wts, __nv_bfloat16 *_
   }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kTcWaitLimit) {
   uint32_t done = 0;
-  for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+  for (uint32_t it = 0; it < limit && !done; ++it)
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return done != 0;
@@ -871,6 +871,26 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
 int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, const int32_t *pair,
                     const int32_t *cols, int npatch, int P, float *xo, float *to) {
   extract_patches_kernel<<<npatch, 256, 0, c->stream>>>(xs, ts, ncell, pair, cols, P, c->lv[0].nlev, xo, to);
+  HMG_CUDA(c, cudaGetLastError());
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
+// Self-test of the bounded wait: one CTA waits on an mbarrier that nothing arrives on, gives up
+// after `limit` polls, records that in *flag and returns (the context stays usable).
+__global__ void wait_selftest_kernel(uint32_t limit, int *flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const bool done = mbar_wait(&bar, 0, limit);
+  if (!done && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+int wait_selftest(Ctx *c, uint32_t limit) {
+  wait_selftest_kernel<<<1, 32, 0, c->stream>>>(limit, c->state + 3);
   HMG_CUDA(c, cudaGetLastError());
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
   return HMG_OK;

@@ -60,19 +60,20 @@ class Options(C.Structure):
                 ("mg_omega", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
                 ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
-                ("stall_ratio", C.c_double)]
+                ("stall_ratio", C.c_double), ("warm_start", C.c_int32)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("rel_residual", C.c_double),
                 ("true_rel_residual", C.c_double), ("solve_ms", C.c_double), ("n_history", C.c_int32),
                 ("history", C.c_double * MAX_HISTORY), ("comp_ms", C.c_double * NCOMP),
-                ("comp_calls", C.c_int32 * NCOMP)]
+                ("comp_calls", C.c_int32 * NCOMP), ("coarse_fallback", C.c_int32)]
 
     def as_dict(self):
         return {"status": STATUS_NAMES.get(self.status, self.status), "iterations": self.iterations,
                 "rel_residual": self.rel_residual, "true_rel_residual": self.true_rel_residual,
                 "solve_ms": self.solve_ms, "history": list(self.history[: self.n_history]),
+                "coarse_fallback": bool(self.coarse_fallback),
                 "components": {n: {"ms": self.comp_ms[i], "launches": self.comp_calls[i]}
                                for i, n in enumerate(COMPONENTS)}}
 
@@ -110,6 +111,7 @@ _SIGS = {
     "hmg_solve_mixed": ([_P, _P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
     "hmg_apply_mixed": ([_P, _P, _P], C.c_int),
     "hmg_coarse_model_size": ([], C.c_int32),
+    "hmg_check_device_wait": ([_P, C.c_int32], C.c_int),
     "hmg_set_coarse_model": ([_P, _P, C.c_int32], C.c_int),
     "hmg_get_coarse_model": ([_P, _P, C.c_int32], C.c_int),
     "hmg_apply_coarse_model": ([_P, _P, _P, C.c_int32], C.c_int),
@@ -374,6 +376,10 @@ class Solver:
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
             raise TypeError(f"{name}: expected a contiguous float32 CUDA tensor")
         return _ptr(t)
+
+    def check_device_wait(self, polls=1000):
+        """Status of the bounded-wait self-test (expected: 7, HMG_ERR_TIMEOUT)."""
+        return lib().hmg_check_device_wait(self.ctx, polls)
 
     def set_coarse_model(self, params):
         p = np.ascontiguousarray(params, np.float32).ravel()

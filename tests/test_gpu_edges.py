@@ -129,3 +129,33 @@ def test_largest_workload_c192_sampled_rows():
     _lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
     assert st["status"] == "ok" and st["true_rel_residual"] <= 1.05e-6
     gpu.close()
+
+
+@pytest.mark.parametrize("krylov", ["bicgstab", "fgmres"])
+def test_warm_start_resumes_a_solve(krylov):
+    """warm_start = 1 starts from the lambda passed in: resuming from a solution converged to
+    1e-4 reaches 1e-10 in fewer iterations than from zero, with the same answer; the oracle's
+    BiCGStab from the same start agrees; starting from the exact answer needs no iteration."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(6, 5, courant=8.0, nmg=2, seed=4)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-4, krylov=krylov)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam0, _st = gpu.solve(Rub, Rpi)
+    gpu.set_options(tol=1e-10)
+    cold, st_cold = gpu.solve(Rub, Rpi)
+    gpu.set_options(warm_start=1)
+    warm = lam0.clone()
+    warm, st_warm = gpu.solve(Rub, Rpi, warm)
+    assert st_warm["status"] == "ok" and st_warm["iterations"] < st_cold["iterations"]
+    assert st_warm["history"][0] < 1e-3                    # ||B - S lambda_0|| / ||B||
+    assert np.linalg.norm(_np(warm) - _np(cold)) / np.linalg.norm(_np(cold)) < 1e-8
+    if krylov == "bicgstab":
+        ora = HybridSolver(w.hier, w.coeffs)
+        from oracle.nonnested import bicgstab
+        B = ora.rhs(w.Rub, w.Rpi)
+        ref, hist, status = bicgstab(lambda v: ora.S @ v, B, ora.precond, 1e-10, 200, x0=_np(lam0))
+        assert status == "ok" and abs(st_warm["iterations"] - (len(hist) - 1)) <= 1
+        assert np.linalg.norm(_np(warm) - ref) / np.linalg.norm(ref) < 1e-9
+    again, st_again = gpu.solve(Rub, Rpi, warm.clone())
+    assert st_again["iterations"] <= 1
+    gpu.close()

@@ -200,9 +200,10 @@ def test_corrupted_model_falls_back_to_the_vcycle():
     gpu.set_coarse_model(np.full(3360, np.nan, np.float32))
     gpu.set_options(krylov="fgmres", coarse="learned", tol=1e-10)
     lam, st = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
-    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9
+    assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9 and st["coarse_fallback"]
     gpu.set_options(krylov="fgmres", coarse="vcycle", tol=1e-10)
     ref, st2 = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert not st2["coarse_fallback"]
     assert st["iterations"] == st2["iterations"]
     assert np.linalg.norm(_np(lam) - _np(ref)) / np.linalg.norm(_np(ref)) < 1e-12
     # BiCGStab cannot drop a step: a NaN model is reported, not hidden
@@ -258,3 +259,16 @@ def test_trained_network_in_the_solve():
     assert steps(coarse="learned_vcycle") <= plain + 1
     steps(coarse="learned", stall_ratio=0.9)
     s.close()
+
+
+def test_bounded_device_wait_reports_a_timeout_and_keeps_the_context():
+    """The tensor-core kernels wait on mbarriers with a bounded number of polls. A wait on a
+    barrier that nothing arrives on must end with HMG_ERR_TIMEOUT (no hang, no fault), and
+    the context must keep working afterwards."""
+    w, _ora, gpu = _setup("planar16")
+    assert gpu.check_device_wait(1000) == 7
+    gpu.set_coarse_model(I.flatten_coarse_model(I.coarse_model_init(1)))
+    out = _np(gpu.apply_coarse_model(_cuda(I.normal(3, gpu.ncell))))
+    assert np.all(np.isfinite(out))
+    _lam, st = gpu.solve(_cuda(w.Rub), _cuda(w.Rpi))
+    assert st["status"] == "ok"
