@@ -70,14 +70,18 @@ struct Level {
   void *vb = nullptr, *vx = nullptr, *vy = nullptr;
 };
 
-// Work buffers of the coarse-model training (learned.cu).
+// Work buffers of the coarse-model training (learned.cu), grown on demand and reused.
 struct TrainBufs {
-  int64_t cap_cells = 0;
+  int64_t cap_cells = 0, cap_blocks = 0;
   void *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;   // activations (BF16 or FP32)
   float *ga3 = nullptr, *ga2 = nullptr, *gy = nullptr;
   double *loss_part = nullptr, *loss = nullptr;
   float *part3 = nullptr, *partM = nullptr, *part2 = nullptr, *part1 = nullptr;
-  float *grad = nullptr, *m = nullptr, *v = nullptr, *tn = nullptr;
+  float *grad = nullptr, *m = nullptr, *v = nullptr;
+  // per-call data (with their capacities): sample norms, the current minibatch, the epoch order
+  float *tn = nullptr, *tnb = nullptr, *xb = nullptr, *tb = nullptr;
+  int32_t *order = nullptr;
+  size_t cap_tn = 0, cap_tnb = 0, cap_xb = 0, cap_tb = 0, cap_order = 0;
 };
 
 struct Ctx {
@@ -191,6 +195,29 @@ int dev_alloc(Ctx *c, T **p, size_t n) {
   c->owned.push_back(q);
   *p = static_cast<T *>(q);
   return HMG_OK;
+}
+
+// Releases one device allocation of the context (and forgets it).
+inline void dev_free(Ctx *c, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->owned.size(); ++i)
+    if (c->owned[i] == p) {
+      c->owned.erase(c->owned.begin() + (long)i);
+      break;
+    }
+  cudaFree(p);
+}
+
+// (Re)allocates *p to hold at least n elements (contents not kept); *cap tracks the size.
+template <typename T>
+int dev_grow(Ctx *c, T **p, size_t *cap, size_t n) {
+  if (*p && *cap >= n) return HMG_OK;
+  dev_free(c, *p);
+  *p = nullptr;
+  *cap = 0;
+  const int st = dev_alloc(c, p, n);
+  if (!st) *cap = n;
+  return st;
 }
 
 inline unsigned grid_for(int64_t n, int threads) {

@@ -540,21 +540,11 @@ __global__ void gm_sub_kernel(const double *__restrict__ B, const double *__rest
     r[i] = B[i] - y[i];
 }
 
-static void dev_release(Ctx *c, void *p) {
-  if (!p) return;
-  for (size_t i = 0; i < c->owned.size(); ++i)
-    if (c->owned[i] == p) {
-      c->owned.erase(c->owned.begin() + (long)i);
-      break;
-    }
-  cudaFree(p);
-}
-
 static int gm_buffers(Ctx *c, int m) {
   if (c->gm_V && c->gm_restart >= m) return HMG_OK;
   const int64_t n = c->lv[0].ntrace + c->lv[0].ncell;   // the longer of the two systems
-  dev_release(c, c->gm_V);
-  dev_release(c, c->gm_Z);
+  dev_free(c, c->gm_V);
+  dev_free(c, c->gm_Z);
   c->gm_V = c->gm_Z = nullptr;
   c->gm_restart = 0;
   int s;

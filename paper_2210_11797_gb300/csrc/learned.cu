@@ -767,27 +767,42 @@ static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn
 
 int train_buffers(Ctx *c, int64_t cells, int nblocks_max) {
   TrainBufs &tb = c->train;
-  if (tb.cap_cells >= cells) return HMG_OK;
   int st;
-  float *f;
-  // storage for FP32 activations (BF16 uses half of it)
-  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h1 = f;
-  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h2 = f;
-  if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st; tb.h3 = f;
-  if ((st = dev_alloc(c, &tb.ga3, (size_t)kCh * cells))) return st;
-  if ((st = dev_alloc(c, &tb.ga2, (size_t)kCh * cells))) return st;
-  if ((st = dev_alloc(c, &tb.gy, (size_t)cells))) return st;
-  if ((st = dev_alloc(c, &tb.loss_part, (size_t)nblocks_max))) return st;
-  if ((st = dev_alloc(c, &tb.part3, (size_t)nblocks_max * 96))) return st;
-  if ((st = dev_alloc(c, &tb.partM, (size_t)nblocks_max * 96))) return st;
-  if ((st = dev_alloc(c, &tb.part2, (size_t)nblocks_max * 3072))) return st;
-  if ((st = dev_alloc(c, &tb.part1, (size_t)nblocks_max * 96))) return st;
-  if ((st = dev_alloc(c, &tb.grad, (size_t)kNParams))) return st;
-  if ((st = dev_alloc(c, &tb.m, (size_t)kNParams))) return st;
-  if ((st = dev_alloc(c, &tb.v, (size_t)kNParams))) return st;
-  if ((st = dev_alloc(c, &tb.loss, 1))) return st;
-  if ((st = dev_alloc(c, &tb.tn, (size_t)1))) return st;
-  tb.cap_cells = cells;
+  if (tb.cap_cells < cells) {
+    void **acts[] = {&tb.h1, &tb.h2, &tb.h3};
+    for (void **a : acts) {   // storage for FP32 activations (BF16 uses half of it)
+      dev_free(c, *a);
+      float *f;
+      if ((st = dev_alloc(c, &f, (size_t)kCh * cells))) return st;
+      *a = f;
+    }
+    float **grads[] = {&tb.ga3, &tb.ga2};
+    for (float **g : grads) {
+      dev_free(c, *g);
+      if ((st = dev_alloc(c, g, (size_t)kCh * cells))) return st;
+    }
+    dev_free(c, tb.gy);
+    if ((st = dev_alloc(c, &tb.gy, (size_t)cells))) return st;
+    tb.cap_cells = cells;
+  }
+  if (tb.cap_blocks < nblocks_max) {
+    dev_free(c, tb.loss_part);
+    if ((st = dev_alloc(c, &tb.loss_part, (size_t)nblocks_max))) return st;
+    float **parts[] = {&tb.part3, &tb.partM, &tb.part1};
+    for (float **q : parts) {
+      dev_free(c, *q);
+      if ((st = dev_alloc(c, q, (size_t)nblocks_max * 96))) return st;
+    }
+    dev_free(c, tb.part2);
+    if ((st = dev_alloc(c, &tb.part2, (size_t)nblocks_max * 3072))) return st;
+    tb.cap_blocks = nblocks_max;
+  }
+  if (!tb.grad) {
+    if ((st = dev_alloc(c, &tb.grad, (size_t)kNParams))) return st;
+    if ((st = dev_alloc(c, &tb.m, (size_t)kNParams))) return st;
+    if ((st = dev_alloc(c, &tb.v, (size_t)kNParams))) return st;
+    if ((st = dev_alloc(c, &tb.loss, 1))) return st;
+  }
   return HMG_OK;
 }
 
@@ -798,8 +813,8 @@ int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx,
   int st;
   if ((st = nn_setup(c))) return st;
   if ((st = train_buffers(c, cells, (int)(nsamp * nx * ny + kNnCpb - 1) / kNnCpb + 1))) return st;
-  float *tn;
-  if ((st = dev_alloc(c, &tn, (size_t)nsamp))) return st;
+  if ((st = dev_grow(c, &c->train.tn, &c->train.cap_tn, (size_t)nsamp))) return st;
+  float *tn = c->train.tn;
   tnorm_kernel<<<nsamp, 256, 0, c->stream>>>(t, (int64_t)nx * ny * L, tn);
   if (fp32) st = nn_batch_grad<float>(c, x, t, tn, nsamp, nx, ny, L, c->train.grad, c->train.loss);
   else st = nn_batch_grad<__nv_bfloat16>(c, x, t, tn, nsamp, nx, ny, L, c->train.grad, c->train.loss);
@@ -827,13 +842,14 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
   if ((st = nn_setup(c))) return st;
   if (batch < 1 || batch > nsamp) return fail(c, HMG_ERR_INVALID_ARG, "bad batch size");
   if ((st = train_buffers(c, (int64_t)batch * per, (batch * P + kNnCpb - 1) / kNnCpb + 1))) return st;
-  float *tn_all, *xb, *tb_, *tnb;
-  int32_t *order_dev;
-  if ((st = dev_alloc(c, &tn_all, (size_t)nsamp))) return st;
-  if ((st = dev_alloc(c, &xb, (size_t)batch * per))) return st;
-  if ((st = dev_alloc(c, &tb_, (size_t)batch * per))) return st;
-  if ((st = dev_alloc(c, &tnb, (size_t)batch))) return st;
-  if ((st = dev_alloc(c, &order_dev, (size_t)nsamp))) return st;
+  TrainBufs &T = c->train;
+  if ((st = dev_grow(c, &T.tn, &T.cap_tn, (size_t)nsamp))) return st;
+  if ((st = dev_grow(c, &T.order, &T.cap_order, (size_t)nsamp))) return st;
+  if ((st = dev_grow(c, &T.xb, &T.cap_xb, (size_t)batch * per))) return st;
+  if ((st = dev_grow(c, &T.tb, &T.cap_tb, (size_t)batch * per))) return st;
+  if ((st = dev_grow(c, &T.tnb, &T.cap_tnb, (size_t)batch))) return st;
+  float *tn_all = T.tn, *xb = T.xb, *tb_ = T.tb, *tnb = T.tnb;
+  int32_t *order_dev = T.order;
   tnorm_kernel<<<nsamp, 256, 0, c->stream>>>(t, per, tn_all);
   HMG_CUDA(c, cudaMemsetAsync(c->train.m, 0, sizeof(float) * kNParams, c->stream));
   HMG_CUDA(c, cudaMemsetAsync(c->train.v, 0, sizeof(float) * kNParams, c->stream));
