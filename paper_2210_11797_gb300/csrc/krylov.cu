@@ -19,6 +19,28 @@
 
 namespace hmg {
 
+// Two CUDA events around a solve on the context's stream, destroyed on every return path.
+struct SolveTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~SolveTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  int start(Ctx *c) {
+    HMG_CUDA(c, cudaEventCreate(&e0));
+    HMG_CUDA(c, cudaEventCreate(&e1));
+    HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+    return HMG_OK;
+  }
+  int stop(Ctx *c, float *ms) {
+    HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+    HMG_CUDA(c, cudaEventSynchronize(e1));
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, e0, e1);
+    return HMG_OK;
+  }
+};
+
 static unsigned red_grid(int64_t n) {
   unsigned g = grid_for(n, kRedThreads);
   return g < (unsigned)kRedBlocks ? g : (unsigned)kRedBlocks;
@@ -371,11 +393,9 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
   c->ev_next = 0;
   c->coarse_fallback = false;
   if (c->opt.krylov == HMG_KRYLOV_FGMRES) return fgmres_solve(c, Rub, Rpi, lambda, st);
-  cudaEvent_t e0, e1;
-  HMG_CUDA(c, cudaEventCreate(&e0));
-  HMG_CUDA(c, cudaEventCreate(&e1));
-  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  SolveTimer timer;
   int s;
+  if ((s = timer.start(c))) return s;
   const bool host_coarse = c->opt.precond == HMG_PRECOND_NONNESTED &&
                            (c->opt.coarse == HMG_COARSE_KRYLOV_EXACT || c->opt.coarse == HMG_COARSE_KRYLOV_APPROX);
   if (c->opt.graph && !c->opt.profile && !c->collect_x && !host_coarse) {
@@ -392,12 +412,8 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
     }
     if ((s = solve_tail(c, lambda))) return s;
   }
-  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
-  HMG_CUDA(c, cudaEventSynchronize(e1));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if ((s = timer.stop(c, &ms))) return s;
   return collect(c, st, ms);
 }
 
@@ -603,10 +619,8 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
   if ((s = gm_buffers(c, m))) return s;
   double *hd = c->gm_h, *h2 = hd + (kMaxRestart + 2), *sc = h2 + (kMaxRestart + 2);
   double *V = c->gm_V, *Z = c->gm_Z;
-  cudaEvent_t e0, e1;
-  HMG_CUDA(c, cudaEventCreate(&e0));
-  HMG_CUDA(c, cudaEventCreate(&e1));
-  HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+  SolveTimer timer;
+  if ((s = timer.start(c))) return s;
   if ((s = sys_rhs(c, Rub, Rpi, c->B))) return s;
   double beta = 0.0;
   {
@@ -729,12 +743,8 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *x, hmg_so
   c->state_host[kContinue] = 0;
   HMG_CUDA(c, cudaMemcpyAsync(c->hist, hist.data(), sizeof(double) * nh, cudaMemcpyHostToDevice, c->stream));
   HMG_CUDA(c, cudaMemcpyAsync(c->state, c->state_host, sizeof(int) * 3, cudaMemcpyHostToDevice, c->stream));
-  HMG_CUDA(c, cudaEventRecord(e1, c->stream));
-  HMG_CUDA(c, cudaEventSynchronize(e1));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if ((s = timer.stop(c, &ms))) return s;
   return collect(c, st, ms);
 }
 
