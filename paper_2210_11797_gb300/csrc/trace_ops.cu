@@ -201,10 +201,6 @@ struct SweepArgs {
   const int32_t *stencil, *col_edges;
 };
 
-// lambda^h rows per thread of the sweep: 2 in FP32 (memory-latency bound), 1 in FP64
-template <typename T>
-constexpr int kSweepHRows = sizeof(T) == 4 ? 2 : 1;
-
 template <typename T, typename Tb, typename Tout, bool ZERO>
 __global__ void __launch_bounds__(256)
     sweep_kernel(const SweepArgs a, const T *__restrict__ S, const T *__restrict__ zw,
@@ -253,19 +249,11 @@ __global__ void __launch_bounds__(256)
       lam_out[row] = (Tout)(ZERO ? v : lam_in[row] + v);
     }
   } else {
-    // lambda^h rows: point Jacobi; in FP32 two rows per thread (block-strided, coalesced) keep
-    // more gathers in flight, the FP32 form being bound by memory latency, not arithmetic
-    constexpr int HR = kSweepHRows<T>;
-    const int64_t base = (int64_t)(blockIdx.x - a.nzb) * blockDim.x * HR + threadIdx.x;
-#pragma unroll
-    for (int j = 0; j < HR; ++j) {
-      const int64_t row = base + (int64_t)j * blockDim.x;
-      if (row < d.NH) {
-        T r = (T)__ldg(b + row);
-        if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
-        lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
-      }
-    }
+    const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
+    if (row >= d.NH) return;
+    T r = (T)__ldg(b + row);
+    if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
+    lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
   }
 }
 
@@ -295,7 +283,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
   if (threads > tmax) threads = tmax;
   if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
-  const unsigned nhb = grid_for(f.nth, threads * kSweepHRows<T>);
+  const unsigned nhb = grid_for(f.nth, threads);
   const size_t smem = (size_t)3 * a.cpb * ((f.nlev + 1) | 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
   sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
