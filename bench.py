@@ -62,11 +62,38 @@ def kernel_source_hash():
 
 def sweep_bytes(mesh, elem=8):
     """Algorithmic bytes of one full line-smoother sweep (Algorithm 1, fused residual):
-    every nonzero of S once, lambda_in, b and lambda_out once, the two Thomas factors of
-    each lambda^z row, 1/diag of each lambda^h row, and the index tables."""
+    every nonzero of S once, lambda_in, b and lambda_out once, the three Thomas factors of
+    each lambda^z row (omega/pivot, sub/pivot, sup/pivot), omega/diag of each lambda^h row,
+    and the index tables."""
     L, NH, NZ, T = mesh.nlev, mesh.n_trace_h, mesh.n_trace_z, mesh.n_trace
     nnz = 11 * NH + mesh.ncol * (11 * (L - 1) + 2 * 6)
-    return elem * (nnz + 3 * T + 2 * NZ + NH) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
+    return elem * (nnz + 3 * T + 3 * NZ + NH) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
+
+
+def solve_bytes(hier, iterations, elem=8):
+    """Algorithmic bytes of one whole solve (B_lambda, BiCGStab under configuration 3c, the
+    final residual), each kernel's inputs and outputs counted once, the preconditioner's
+    arrays in `elem` bytes (4 with the FP32 preconditioner) and the Krylov vectors in 8:
+      B_lambda: A_K^-1 (49 C) + R (7 C) + B (T); initialisation 6 T;
+      per iteration: 2 S applies, 2 preconditioner applications, 15 T of vector updates;
+      preconditioner: presmooth from zero (b, factors, out), residual (S, lambda, b, R),
+      restriction (R, Gamma, bbar), one V-cycle (per level 42.5 C_l: smoother from zero 5,
+      residual + restriction 9.25, injection 2.25, two smoothers 26; coarsest 5 + 2 x 13),
+      prolongation (2 T + C), two full sweeps; the final residual: nnz + 2 T."""
+    f = hier.meshes[0]
+    L, NH, NZ, T, C = f.nlev, f.n_trace_h, f.n_trace_z, f.n_trace, f.ncell
+    nnz = 11 * NH + f.ncol * (11 * (L - 1) + 2 * 6)
+    tables = 4 * (8 * f.nedge + 4 * f.ncol)
+    cells = [m.ncell for m in hier.meshes]
+    vcycle = elem * (sum(42.5 * c for c in cells[:-1]) + 31.0 * cells[-1])
+    precond = (8 * T + elem * (3 * NZ + NH + T)                 # presmooth from zero
+               + elem * (nnz + 2 * T) + 8 * T + tables          # residual
+               + elem * (T + 2 * C)                             # restriction with Gamma
+               + vcycle
+               + elem * (2 * T + C)                             # prolongation
+               + 2 * sweep_bytes(f, elem))                      # post-smoothing
+    per_it = 2 * spmv_bytes(f) + 2 * precond + 8 * 15 * T
+    return 8 * (49 * C + 7 * C + T) + 8 * 6 * T + iterations * per_it + 8 * (nnz + 2 * T) + tables
 
 
 def spmv_bytes(mesh, elem=8):
@@ -238,6 +265,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     its = [s["iterations"] for s in stats]
+    sb = solve_bytes(w.hier, max(its), 8 if args.precision == "fp64" else 4)
     variants = run_variants(args, w, solver, Rub, Rpi, lam, stream) if (world == 1 and not args.no_variants) else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -256,6 +284,9 @@ def run_ours(args, rank, world):
         "components_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in comp.items()},
         "gpu_launches": launches,
         "roofline": roofline,
+        "solve_roofline": {"algorithmic_bytes": int(sb), "achieved": round(sb / (ms_step / 1e3) / 1e9, 1),
+                           "peak": peak, "unit": "GB/s", "frac": round(sb / (ms_step / 1e3) / 1e9 / peak, 4),
+                           "model": "each kernel's inputs and outputs once (solve_bytes in bench.py)"},
         "e2e": {"value": round(world * T / (e2e_ms / 1e3), 1), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 7 * w.mesh.ncell, "d2h_bytes_per_step": 8 * T,
                 "ms_per_step": round(e2e_ms, 4)},
