@@ -49,6 +49,7 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.restart < 1 || o.restart > 64) return bad("restart must be in 1..64");
   if (!(o.stall_ratio > 0.0)) return bad("stall_ratio");
   if (o.warm_start != 0 && o.warm_start != 1) return bad("warm_start must be 0 or 1");
+  if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
   return HMG_OK;
 }
 
@@ -125,6 +126,7 @@ int hmg_default_options(hmg_options *o) {
   o->krylov = HMG_KRYLOV_BICGSTAB;
   o->restart = 30;
   o->stall_ratio = 0.9;
+  o->mg_fused = 1;
   return HMG_OK;
 }
 
@@ -153,6 +155,9 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   if (!st) st = dev_alloc(c, &c->hist, HMG_MAX_HISTORY);
   if (!st) st = dev_alloc(c, &c->part, (size_t)Scal::N * kMaxRedBlocks);
   if (!st) st = dev_alloc(c, &c->counter, Scal::N);
+  if (!st) st = dev_alloc(c, &c->mg_bar, 2);
+  if (!st && cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    st = HMG_ERR_CUDA;
   if (!st && cudaMemset(c->counter, 0, sizeof(unsigned int) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
   if (!st && cudaMemset(c->scal, 0, sizeof(double) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;
   if (!st && cudaMemset(c->state, 0, sizeof(int) * 4) != cudaSuccess) st = HMG_ERR_CUDA;
@@ -393,6 +398,16 @@ static int ready(hmg_ctx *c) {
   return HMG_OK;
 }
 
+// A kernel whose bounded wait (a tensor-core mbarrier, the grid barrier of the cooperative
+// multigrid kernel) ran out sets state[3]; the context stays usable.
+static int check_wait_flag(hmg_ctx *c) {
+  int flag = 0;
+  HMG_CUDA(c, cudaMemcpy(&flag, c->state + 3, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return HMG_OK;
+  HMG_CUDA(c, cudaMemset(c->state + 3, 0, sizeof(int)));
+  return fail(c, HMG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+}
+
 static int finish(hmg_ctx *c, int st) {
   if (st) return st;
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -481,7 +496,8 @@ int hmg_precond_apply(hmg_ctx *c, const double *r, double *z) {
   int st = ready(c);
   if (st) return st;
   if (!r || !z || r == z) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
-  return finish(c, precond_apply(c, r, z));
+  if ((st = finish(c, precond_apply(c, r, z)))) return st;
+  return check_wait_flag(c);
 }
 
 int hmg_line_smooth(hmg_ctx *c, const double *b, double *lambda, int32_t nsweeps) {
@@ -502,7 +518,8 @@ int hmg_pressure_vcycle(hmg_ctx *c, const double *b, double *x) {
   int st = ready(c);
   if (st) return st;
   if (!b || !x) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
-  return finish(c, pressure_vcycle_fp64(c, b, x));
+  if ((st = finish(c, pressure_vcycle_fp64(c, b, x)))) return st;
+  return check_wait_flag(c);
 }
 
 int hmg_get_gamma(hmg_ctx *c, double *gamma) {
@@ -579,14 +596,6 @@ int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
 }
 
 // ---- learned coarse correction -------------------------------------------------------------
-// A kernel whose bounded wait on the tensor cores ran out sets state[3] (the context stays usable).
-static int check_wait_flag(hmg_ctx *c) {
-  int flag = 0;
-  HMG_CUDA(c, cudaMemcpy(&flag, c->state + 3, sizeof(int), cudaMemcpyDeviceToHost));
-  if (!flag) return HMG_OK;
-  HMG_CUDA(c, cudaMemset(c->state + 3, 0, sizeof(int)));
-  return fail(c, HMG_ERR_TIMEOUT, "a tensor-core wait of the coarse model ran out");
-}
 
 static int mesh_ready(hmg_ctx *c) {
   if (!c) return HMG_ERR_INVALID_ARG;

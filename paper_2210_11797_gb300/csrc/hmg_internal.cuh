@@ -146,6 +146,8 @@ struct Ctx {
   int collect_max = 0, collect_n = 0;
   double *collect_r = nullptr, *collect_e = nullptr, *collect_y = nullptr;
   double *ck = nullptr;           // [9][ncell] work vectors of the Krylov coarse solve
+  unsigned int *mg_bar = nullptr; // grid barrier of the cooperative coarse-level kernel
+  int num_sms = 0;
   // configuration 1 (mixed.cu): the 2x2 operator (velocity block in the 11-slot layout of S,
   // G couplings [2][ntrace], B couplings and M3^Pi [7][ncell]), 1 / lumped mass [ntrace], the
   // solution [ntrace + ncell] and the Step-1 right-hand side [ncell]
@@ -286,6 +288,8 @@ int wait_selftest(Ctx *c, uint32_t limit);
 int collect_pair(Ctx *c, const double *bbar);
 // r = b - H_l x (FP64) on level l
 int pressure_residual_fp64(Ctx *c, int level, const double *b, const double *x, double *r);
+// kernel launches of one V-cycle (for the component timers)
+int vcycle_launches(const Ctx *c);
 // x = H_0^-1 b by V-cycle-preconditioned BiCGStab to tol (configurations 3a / 3b), host-driven
 int coarse_krylov(Ctx *c, const double *b, double *x, double tol, int maxit);
 // flexible GMRES(restart) driver (krylov.cu)

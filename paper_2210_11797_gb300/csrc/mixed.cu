@@ -313,8 +313,7 @@ int schur_precond(Ctx *c, const double *r, double *z) {
   }
   double *pi = nullptr;
   {
-    const int nl = c->nmg - 1;
-    Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1));
+    Prof pv(c, kCompVcycle, vcycle_launches(c));
     if ((st = vcycle<double>(c, c->mx_bp, &pi))) return st;
   }
   Prof pp(c, kCompProlong);

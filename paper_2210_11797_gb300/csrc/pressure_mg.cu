@@ -3,6 +3,7 @@
 // (Eq. pressure_block_jacobi, Thomas algorithm per column), residual + restriction (sum over
 // the four horizontal children) and prolongation (injection), in one V-cycle with
 // mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level.
+#include <algorithm>
 #include <cmath>
 
 #include "device_common.cuh"
@@ -17,14 +18,23 @@ struct MGArgs {
   const int32_t *col_nbr;
 };
 
+// Loads of vectors that other blocks of the same launch wrote (the cooperative coarse-level
+// kernel, COH) bypass L1; coefficient arrays, never written during a solve, go through the
+// read-only path.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+  if (COH) return __ldcg(p);
+  return *p;
+}
+
 // acc + sign * (row K of H) . x as one FMA per coefficient (acc = b, sign = -1: the residual).
-template <typename T, bool NEG>
+template <typename T, bool NEG, bool COH = false>
 __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x, const MGArgs &a,
                                      int c, int k, T acc) {
   const int64_t C = a.ncell, K = (int64_t)c * a.L + k;
   auto term = [&](int slot, int col, int kk) {
     const T h = __ldg(H + slot * C + K);
-    acc = fma(NEG ? -h : h, x[(int64_t)col * a.L + kk], acc);
+    acc = fma(NEG ? -h : h, ldv<COH>(x + (int64_t)col * a.L + kk), acc);
   };
   term(0, c, k);
 #pragma unroll
@@ -34,19 +44,19 @@ __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restric
   return acc;
 }
 
-// MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256)
-    mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hw,
-                     const T *__restrict__ hl, const T *__restrict__ hcp, const T *__restrict__ b,
-                     const T *__restrict__ x, T *__restrict__ x_out) {
-  extern __shared__ unsigned char smem_raw[];
+// One column block (columns blk * cpb ..) of the block-Jacobi smoother, by the whole thread
+// block. MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void smooth_block(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ hw,
+                                             const T *__restrict__ hl, const T *__restrict__ hcp,
+                                             const T *__restrict__ b, const T *__restrict__ x,
+                                             T *__restrict__ x_out, int blk, unsigned char *smem_raw) {
   // one column per lane in the serial phase: column j at j * ld, ld = L rounded up to odd so
   // that the lanes of a half-warp hit distinct banks
   const int ld = a.L | 1;
   T *sr = reinterpret_cast<T *>(smem_raw);
   T *sl = sr + a.cpb * ld, *scp = sl + a.cpb * ld;
-  const int c0 = blockIdx.x * a.cpb;
+  const int c0 = blk * a.cpb;
   const int nc = min(a.cpb, a.ncol - c0);
   const int n = nc * a.L;
   const int64_t base = (int64_t)c0 * a.L;
@@ -55,8 +65,8 @@ __global__ void __launch_bounds__(256)
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
-    T r = b[K];
-    if (MODE != 0) r = h_apply<T, true>(H, x, a, c, k, r);
+    T r = ldv<COH>(b + K);
+    if (MODE != 0) r = h_apply<T, true, COH>(H, x, a, c, k, r);
     const int j = (c - c0) * ld + k;
     sr[j] = r * __ldg(hw + K);
     sl[j] = __ldg(hl + K);
@@ -79,22 +89,54 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const T v = sr[(i / a.L) * ld + i % a.L];
-    x_out[base + i] = MODE == 0 ? v : x[base + i] + v;
+    x_out[base + i] = MODE == 0 ? v : ldv<COH>(x + base + i) + v;
   }
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+    mg_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hw,
+                     const T *__restrict__ hl, const T *__restrict__ hcp, const T *__restrict__ b,
+                     const T *__restrict__ x, T *__restrict__ x_out) {
+  extern __shared__ unsigned char smem_raw[];
+  smooth_block<T, MODE, false>(a, H, hw, hl, hcp, b, x, x_out, blockIdx.x, smem_raw);
+}
+
 // x_out = x + P e: injection of the coarse-level correction e (prolongation, Sec. 2.3).
+template <typename T, bool COH>
+__device__ __forceinline__ void inject_cell(const T *__restrict__ x, const T *__restrict__ e,
+                                            const int32_t *__restrict__ parent, int L, int64_t K,
+                                            T *__restrict__ x_out) {
+  const int c = (int)(K / L), k = (int)(K - (int64_t)c * L);
+  x_out[K] = ldv<COH>(x + K) + ldv<COH>(e + (int64_t)__ldg(parent + c) * L + k);
+}
+
 template <typename T>
 __global__ void mg_inject_kernel(const T *__restrict__ x, const T *__restrict__ e,
                                  const int32_t *__restrict__ parent, int L, int64_t ncell,
                                  T *__restrict__ x_out) {
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= ncell) return;
-  const int c = (int)(K / L), k = (int)(K - (int64_t)c * L);
-  x_out[K] = x[K] + e[(int64_t)__ldg(parent + c) * L + k];
+  inject_cell<T, false>(x, e, parent, L, K, x_out);
 }
 
 // b_coarse(cc, k) = sum over the four children ch of (b - H x)(ch, k); x == nullptr means 0.
+template <typename T, bool COH>
+__device__ __forceinline__ void restrict_cell(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ b,
+                                              const T *__restrict__ x, const int32_t *__restrict__ children,
+                                              int64_t Kc, T *__restrict__ bc) {
+  const int cc = (int)(Kc / a.L), k = (int)(Kc - (int64_t)cc * a.L);
+  T s = (T)0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ch = __ldg(children + 4 * (int64_t)cc + i);
+    T r = ldv<COH>(b + (int64_t)ch * a.L + k);
+    if (x != nullptr) r = h_apply<T, true, COH>(H, x, a, ch, k, r);
+    s += r;
+  }
+  bc[Kc] = s;
+}
+
 template <typename T>
 __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict__ H,
                                             const T *__restrict__ b, const T *__restrict__ x,
@@ -102,16 +144,7 @@ __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict_
                                             T *__restrict__ bc) {
   const int64_t Kc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (Kc >= (int64_t)ncol_c * a.L) return;
-  const int cc = (int)(Kc / a.L), k = (int)(Kc - (int64_t)cc * a.L);
-  T s = (T)0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int ch = __ldg(children + 4 * (int64_t)cc + i);
-    T r = b[(int64_t)ch * a.L + k];
-    if (x != nullptr) r = h_apply<T, true>(H, x, a, ch, k, r);
-    s += r;
-  }
-  bc[Kc] = s;
+  restrict_cell<T, false>(a, H, b, x, children, Kc, bc);
 }
 
 template <typename T>
@@ -130,6 +163,104 @@ __global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T
   if (K >= a.ncell) return;
   const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
   y[K] = h_apply<T, false>(H, x, a, c, k, (T)0);
+}
+
+// ---- the coarse levels of a V-cycle in one cooperative launch ----------------------------------
+// Levels l0 .. nmg-1 (all but the finest) are small and latency-bound as one launch per step;
+// here one co-resident grid runs every step (smoothing sweeps, residual + restriction,
+// injection) with a grid-wide barrier between steps. Same arithmetic as the per-step kernels.
+constexpr uint32_t kGridBarrierLimit = 1u << 22;   // 64 ns sleeps (~0.3 s) before a barrier gives up
+
+struct GridBarrier {
+  unsigned int count, gen;
+};
+
+// All blocks of the co-resident grid meet; a block that waits past the limit records it in
+// *flag (reported as HMG_ERR_TIMEOUT) and goes on.
+__device__ __forceinline__ void grid_barrier(GridBarrier *gb, unsigned int &gen, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicExch(&gb->gen, gen + 1);
+    } else {
+      uint32_t it = 0;
+      while (atomicAdd(&gb->gen, 0u) == gen && it < kGridBarrierLimit) {
+        __nanosleep(64);
+        ++it;
+      }
+      if (it >= kGridBarrierLimit) atomicExch(flag, 1);
+    }
+    __threadfence();
+  }
+  ++gen;
+  __syncthreads();
+}
+
+template <typename T>
+struct CoarseLevel {
+  MGArgs a;
+  const T *H, *hw, *hl, *hcp;
+  T *vb, *vx, *vy;
+  const int32_t *children;   // [ncol][4]: this level's children on the next finer level
+  const int32_t *parent;     // [ncol]: the column containing it on the next coarser level
+  int nblk;                  // column blocks of the smoother
+};
+
+template <typename T>
+struct CoarseArgs {
+  int l0, nmg, npre, npost, ncoarse;
+  CoarseLevel<T> lv[kMaxLevels];
+  GridBarrier *bar;
+  int *flag;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) mg_coarse_kernel(const CoarseArgs<T> p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned int gen = 0;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+  auto smooth_phase = [&](int l, bool zero, const T *xin, T *xout) {
+    const CoarseLevel<T> &q = p.lv[l];
+    for (int blk = blockIdx.x; blk < q.nblk; blk += gridDim.x) {
+      if (zero) smooth_block<T, 0, true>(q.a, q.H, q.hw, q.hl, q.hcp, q.vb, nullptr, xout, blk, smem_raw);
+      else smooth_block<T, 1, true>(q.a, q.H, q.hw, q.hl, q.hcp, q.vb, xin, xout, blk, smem_raw);
+      __syncthreads();   // the next column block reuses the shared memory
+    }
+    grid_barrier(p.bar, gen, p.flag);
+  };
+  auto sweeps_from_zero = [&](int l, int n) {
+    T *cur = p.lv[l].vx, *oth = p.lv[l].vy;
+    smooth_phase(l, true, nullptr, cur);
+    for (int i = 1; i < n; ++i) {
+      smooth_phase(l, false, cur, oth);
+      T *t = cur; cur = oth; oth = t;
+    }
+    return cur;
+  };
+  T *x[kMaxLevels];
+  for (int l = p.l0; l < p.nmg - 1; ++l) {
+    x[l] = sweeps_from_zero(l, p.npre);
+    const CoarseLevel<T> &q = p.lv[l], &cq = p.lv[l + 1];
+    for (int64_t Kc = tid; Kc < cq.a.ncell; Kc += nthr) restrict_cell<T, true>(q.a, q.H, q.vb, x[l], cq.children, Kc, cq.vb);
+    grid_barrier(p.bar, gen, p.flag);
+  }
+  const int lc = p.nmg - 1;
+  x[lc] = sweeps_from_zero(lc, p.ncoarse);
+  for (int l = p.nmg - 2; l >= p.l0; --l) {
+    const CoarseLevel<T> &q = p.lv[l];
+    T *other = x[l] == q.vx ? q.vy : q.vx;
+    for (int64_t K = tid; K < q.a.ncell; K += nthr) inject_cell<T, true>(x[l], x[l + 1], q.parent, q.a.L, K, other);
+    grid_barrier(p.bar, gen, p.flag);
+    T *cur = other, *nxt = x[l];
+    for (int i = 0; i < p.npost; ++i) {
+      smooth_phase(l, false, cur, nxt);
+      T *t = cur; cur = nxt; nxt = t;
+    }
+    x[l] = cur;
+  }
 }
 
 static MGArgs mg_args(const Ctx *c, int l) {
@@ -207,6 +338,79 @@ static int sweeps_from_zero(Ctx *c, int l, const T *b, int n, T **cur, const T *
   return HMG_OK;
 }
 
+// Launches the coarse levels 1 .. nmg-1 of a V-cycle as one cooperative grid; *x1 receives
+// level 1's correction (lv[1].vx or vy, the pointer sequence of the kernel replayed here).
+template <typename T>
+static int launch_coarse(Ctx *c, T **x1) {
+  const int nmg = c->nmg;
+  CoarseArgs<T> p{};
+  p.l0 = 1;
+  p.nmg = nmg;
+  p.npre = c->opt.mg_npre;
+  p.npost = c->opt.mg_npost;
+  p.ncoarse = c->opt.mg_ncoarse;
+  size_t smem = 0;
+  int64_t need = 1;
+  for (int l = 1; l < nmg; ++l) {
+    const Level &lv = c->lv[l];
+    CoarseLevel<T> &q = p.lv[l];
+    q.a = mg_args(c, l);
+    q.H = Prec<T>::H(lv);
+    q.hw = Prec<T>::Hz_w(lv);
+    q.hl = Prec<T>::Hz_l(lv);
+    q.hcp = Prec<T>::Hz_cp(lv);
+    q.vb = static_cast<T *>(lv.vb);
+    q.vx = static_cast<T *>(lv.vx);
+    q.vy = static_cast<T *>(lv.vy);
+    q.children = lv.children;
+    q.parent = lv.parent;
+    q.nblk = (lv.ncol + q.a.cpb - 1) / q.a.cpb;
+    const size_t sm = (size_t)3 * q.a.cpb * (lv.nlev | 1) * sizeof(T);
+    if (sm > smem) smem = sm;
+    need = std::max<int64_t>(need, std::max<int64_t>(q.nblk, (lv.ncell + 255) / 256));
+  }
+  p.bar = reinterpret_cast<GridBarrier *>(c->mg_bar);
+  p.flag = c->state + 3;
+  int per_sm = 0;
+  HMG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mg_coarse_kernel<T>, 256, smem));
+  if (per_sm < 1) return fail(c, HMG_ERR_CUDA, "the coarse-level kernel does not fit on an SM");
+  const int64_t grid = std::min<int64_t>(need, (int64_t)per_sm * c->num_sms);
+  HMG_CUDA(c, cudaMemsetAsync(c->mg_bar, 0, 2 * sizeof(unsigned int), c->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  HMG_CUDA(c, cudaLaunchKernelEx(&cfg, mg_coarse_kernel<T>, p));
+  // replay the kernel's choice of work vectors
+  T *x[kMaxLevels];
+  auto sweeps = [&](int l, int n) {
+    T *cur = p.lv[l].vx, *oth = p.lv[l].vy;
+    for (int i = 1; i < n; ++i) { T *t = cur; cur = oth; oth = t; }
+    return cur;
+  };
+  for (int l = 1; l < nmg - 1; ++l) x[l] = sweeps(l, p.npre);
+  x[nmg - 1] = sweeps(nmg - 1, p.ncoarse);
+  for (int l = nmg - 2; l >= 1; --l) {
+    T *cur = x[l] == p.lv[l].vx ? p.lv[l].vy : p.lv[l].vx, *nxt = x[l];
+    for (int i = 0; i < p.npost; ++i) { T *t = cur; cur = nxt; nxt = t; }
+    x[l] = cur;
+  }
+  *x1 = x[1];
+  return HMG_OK;
+}
+
+int vcycle_launches(const Ctx *c) {
+  const int nl = c->nmg - 1;
+  if (c->opt.mg_fused && c->nmg >= 2) return (c->opt.mg_npre + 1) + 2 + (c->opt.mg_npost + 1);
+  return nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1);
+}
+
 template <typename T>
 int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
   const int nmg = c->nmg;
@@ -214,7 +418,10 @@ int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
   T *x[kMaxLevels];
   int st;
   b[0] = b0;
-  for (int l = 0; l < nmg - 1; ++l) {
+  // with mg_fused, only the finest level runs step by step; levels >= 1 are one launch
+  const bool fused = c->opt.mg_fused && nmg >= 2;
+  const int ldown = fused ? 1 : nmg - 1;
+  for (int l = 0; l < ldown; ++l) {
     if ((st = sweeps_from_zero<T>(c, l, b[l], c->opt.mg_npre, &x[l], l == 0 ? x0 : nullptr))) return st;
     const Level &coarse = c->lv[l + 1];
     MGArgs a = mg_args(c, l);
@@ -224,10 +431,14 @@ int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
     HMG_CUDA(c, cudaGetLastError());
     b[l + 1] = bc;
   }
-  const int lc = nmg - 1;
-  if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc], lc == 0 ? x0 : nullptr))) return st;
+  if (fused) {
+    if ((st = launch_coarse<T>(c, &x[1]))) return st;
+  } else {
+    const int lc = nmg - 1;
+    if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc], lc == 0 ? x0 : nullptr))) return st;
+  }
   // options are validated to mg_npre >= 1 and mg_npost >= 1
-  for (int l = nmg - 2; l >= 0; --l) {
+  for (int l = fused ? 0 : nmg - 2; l >= 0; --l) {
     Level &lv = c->lv[l];
     T *other = x[l] == static_cast<T *>(lv.vx) ? static_cast<T *>(lv.vy) : static_cast<T *>(lv.vx);
     mg_inject_kernel<T><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,

@@ -400,8 +400,7 @@ static int two_level(Ctx *c, const double *r, double *z) {
   // model, or the model's output as the V-cycle's initial guess
   T *dpi = nullptr;
   {
-    const int nl = c->nmg - 1;
-    Prof pv(c, kCompVcycle, nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1));
+    Prof pv(c, kCompVcycle, vcycle_launches(c));
     const int cm = c->opt.coarse;
     const bool learned = (cm == HMG_COARSE_LEARNED || cm == HMG_COARSE_LEARNED_VCYCLE) && !c->coarse_fallback;
     if (cm == HMG_COARSE_KRYLOV_EXACT || cm == HMG_COARSE_KRYLOV_APPROX) {
