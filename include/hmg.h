@@ -123,9 +123,11 @@ typedef struct {
   double stall_ratio;   /* FGMRES with a learned coarse solve falls back to the V-cycle for the
                            rest of the solve after two consecutive steps that each reduce the
                            residual estimate by less than this factor (0.9) */
-  int32_t mg_fused;     /* 1 (default): the coarse levels (all but the finest) of each V-cycle
-                           run as one cooperative launch with grid-wide barriers; 0: one launch
-                           per smoothing sweep, restriction and injection (same arithmetic) */
+  int32_t mg_fused;     /* 0 (default): one launch per smoothing sweep, restriction and
+                           injection; 1: the coarse levels (all but the finest) of each V-cycle
+                           run as one cooperative launch with grid-wide barriers (same
+                           arithmetic, bitwise the same result; slower inside the solve's
+                           CUDA graph on GB300, where launches cost little) */
   int32_t warm_start;   /* 0 (default, the paper): the Krylov iteration starts from zero;
                            1: from the lambda (hmg_solve) or [u | Pi] (hmg_solve_mixed, its
                            internal copy of the last solution) passed in, r_0 = B - S lambda_0

@@ -126,7 +126,7 @@ int hmg_default_options(hmg_options *o) {
   o->krylov = HMG_KRYLOV_BICGSTAB;
   o->restart = 30;
   o->stall_ratio = 0.9;
-  o->mg_fused = 1;
+  o->mg_fused = 0;
   return HMG_OK;
 }
 
@@ -155,7 +155,7 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   if (!st) st = dev_alloc(c, &c->hist, HMG_MAX_HISTORY);
   if (!st) st = dev_alloc(c, &c->part, (size_t)Scal::N * kMaxRedBlocks);
   if (!st) st = dev_alloc(c, &c->counter, Scal::N);
-  if (!st) st = dev_alloc(c, &c->mg_bar, 2);
+  if (!st) st = dev_alloc(c, &c->mg_bar, 64);
   if (!st && cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     st = HMG_ERR_CUDA;
   if (!st && cudaMemset(c->counter, 0, sizeof(unsigned int) * Scal::N) != cudaSuccess) st = HMG_ERR_CUDA;

@@ -169,31 +169,46 @@ __global__ void mg_apply_kernel(const MGArgs a, const T *__restrict__ H, const T
 // Levels l0 .. nmg-1 (all but the finest) are small and latency-bound as one launch per step;
 // here one co-resident grid runs every step (smoothing sweeps, residual + restriction,
 // injection) with a grid-wide barrier between steps. Same arithmetic as the per-step kernels.
-constexpr uint32_t kGridBarrierLimit = 1u << 22;   // 64 ns sleeps (~0.3 s) before a barrier gives up
+constexpr uint64_t kGridBarrierLimitNs = 500000000ull;   // a barrier gives up after 0.5 s
 
+// arrival counter and generation on separate 128-byte lines, so that the polling of the
+// generation does not contend with the arrivals
 struct GridBarrier {
-  unsigned int count, gen;
+  unsigned int count, pad0[31];
+  unsigned int gen, pad1[31];
 };
 
-// All blocks of the co-resident grid meet; a block that waits past the limit records it in
-// *flag (reported as HMG_ERR_TIMEOUT) and goes on.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// All blocks of the co-resident grid meet. Arrival is an acq_rel add at GPU scope (it
+// publishes this block's writes, ordered before it by __syncthreads); the last block resets
+// the counter and releases the next generation, which the others acquire. A block that waits
+// past the limit records it in *flag (reported as HMG_ERR_TIMEOUT) and goes on.
 __device__ __forceinline__ void grid_barrier(GridBarrier *gb, unsigned int &gen, int *flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicExch(&gb->gen, gen + 1);
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+    if (old == gridDim.x - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&gb->count), "r"(0u) : "memory");
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&gb->gen), "r"(gen + 1) : "memory");
     } else {
-      uint32_t it = 0;
-      while (atomicAdd(&gb->gen, 0u) == gen && it < kGridBarrierLimit) {
-        __nanosleep(64);
-        ++it;
+      const uint64_t t0 = global_ns();
+      unsigned int g;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&gb->gen) : "memory");
+        if (g != gen) break;
+        if (global_ns() - t0 > kGridBarrierLimitNs) {
+          atomicExch(flag, 1);
+          break;
+        }
+        __nanosleep(32);
       }
-      if (it >= kGridBarrierLimit) atomicExch(flag, 1);
     }
-    __threadfence();
   }
   ++gen;
   __syncthreads();
@@ -375,7 +390,7 @@ static int launch_coarse(Ctx *c, T **x1) {
   HMG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mg_coarse_kernel<T>, 256, smem));
   if (per_sm < 1) return fail(c, HMG_ERR_CUDA, "the coarse-level kernel does not fit on an SM");
   const int64_t grid = std::min<int64_t>(need, (int64_t)per_sm * c->num_sms);
-  HMG_CUDA(c, cudaMemsetAsync(c->mg_bar, 0, 2 * sizeof(unsigned int), c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(c->mg_bar, 0, sizeof(GridBarrier), c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(256);
