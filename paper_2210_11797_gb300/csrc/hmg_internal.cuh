@@ -148,6 +148,7 @@ struct Ctx {
   double *ck = nullptr;           // [9][ncell] work vectors of the Krylov coarse solve
   unsigned int *mg_bar = nullptr; // grid barrier of the cooperative coarse-level kernel
   int num_sms = 0;
+  int wave_blocks[3] = {0, 0, 0};   // resident blocks (all SMs) of the BiCGStab vector kernels
   // configuration 1 (mixed.cu): the 2x2 operator (velocity block in the 11-slot layout of S,
   // G couplings [2][ntrace], B couplings and M3^Pi [7][ncell]), 1 / lumped mass [ntrace], the
   // solution [ntrace + ncell] and the Step-1 right-hand side [ncell]

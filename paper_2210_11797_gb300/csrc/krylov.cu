@@ -10,6 +10,7 @@
 // node repeats the iteration body until the check kernel clears its condition, so a solve
 // costs one graph launch and one synchronisation. Batched solves put one such branch per
 // context into a single graph. With graph = 0 (or profile = 1) the host drives the loop.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -130,26 +131,63 @@ __global__ void bicg_start_kernel(double *scal, int *state, double *hist, LoopPa
   if (GRAPH) cudaGraphSetConditional(handle, cont);
 }
 
+// Vector updates take kVecUnroll grid-stride elements per pass, loads first, so that each
+// thread keeps several independent loads in flight (HBM latency x bandwidth).
+constexpr int kVecUnroll = 4;
+constexpr int kXrUnroll = 2;   // six input vectors: 2 keeps bicg_xr_kernel at 8 blocks per SM
+
 // p = r + beta (p - omega v), beta = (rho_i / rho_{i-1}) (alpha / omega)
 __global__ void bicg_p_kernel(const double *__restrict__ r, double *__restrict__ p,
                               const double *__restrict__ v, const double *__restrict__ scal,
                               const int *__restrict__ state, int64_t n) {
-  const int par = state[kIt] & 1;
-  const double rho = scal[par], rho_prev = scal[1 - par];
-  const double alpha = scal[Scal::ALPHA], omega = scal[Scal::OMEGA];
-  const double beta = (rho / rho_prev) * (alpha / omega);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+  // the coefficients once per block (FP64 divides are long sequences on the narrow FP64 pipe)
+  __shared__ double coef[2];
+  if (threadIdx.x == 0) {
+    const int par = state[kIt] & 1;
+    const double rho = scal[par], rho_prev = scal[1 - par];
+    const double alpha = scal[Scal::ALPHA], omega = scal[Scal::OMEGA];
+    coef[0] = (rho / rho_prev) * (alpha / omega);
+    coef[1] = omega;
+  }
+  __syncthreads();
+  const double beta = coef[0], omega = coef[1];
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecUnroll - 1) * st < n; i += kVecUnroll * st) {   // all loads of the group first
+    double rr[kVecUnroll], pp[kVecUnroll], vv[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      rr[u] = r[i + u * st];
+      pp[u] = p[i + u * st];
+      vv[u] = v[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) p[i + u * st] = fma(beta, fma(-omega, vv[u], pp[u]), rr[u]);
+  }
+  for (; i < n; i += st) p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
 }
 
 // alpha = rho_i / (rhat, v); s = r - alpha v
 __global__ void bicg_s_kernel(const double *__restrict__ r, const double *__restrict__ v,
                               double *__restrict__ s, double *scal, const int *__restrict__ state,
                               int64_t n) {
-  const int par = state[kIt] & 1;
-  const double alpha = scal[par] / scal[Scal::RV];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s[i] = fma(-alpha, v[i], r[i]);
+  __shared__ double coef;
+  if (threadIdx.x == 0) coef = scal[state[kIt] & 1] / scal[Scal::RV];
+  __syncthreads();
+  const double alpha = coef;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecUnroll - 1) * st < n; i += kVecUnroll * st) {
+    double rr[kVecUnroll], vv[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+      rr[u] = r[i + u * st];
+      vv[u] = v[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) s[i + u * st] = fma(-alpha, vv[u], rr[u]);
+  }
+  for (; i < n; i += st) s[i] = fma(-alpha, v[i], r[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[Scal::ALPHA] = alpha;
 }
 
@@ -162,9 +200,35 @@ __global__ void __launch_bounds__(kRedThreads)
                    double *part, unsigned int *counter, const int *__restrict__ state, int64_t n) {
   const int par = state[kIt] & 1;
   const double alpha = scal[Scal::ALPHA];
-  const double omega = scal[Scal::TS] / scal[Scal::TT];
+  __shared__ double coef;
+  if (threadIdx.x == 0) coef = scal[Scal::TS] / scal[Scal::TT];
+  __syncthreads();
+  const double omega = coef;
   double a0 = 0.0, a1 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // the partial sums accumulate in the same order (i, i + st, ...) as a plain grid-stride loop
+  for (; i + (kXrUnroll - 1) * st < n; i += kXrUnroll * st) {
+    double xx[kXrUnroll], sh[kXrUnroll], ph[kXrUnroll], tt[kXrUnroll], ss[kXrUnroll], rh[kXrUnroll];
+#pragma unroll
+    for (int u = 0; u < kXrUnroll; ++u) {
+      xx[u] = x[i + u * st];
+      sh[u] = shat[i + u * st];
+      ph[u] = phat[i + u * st];
+      tt[u] = t[i + u * st];
+      ss[u] = s[i + u * st];
+      rh[u] = rhat[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < kXrUnroll; ++u) {
+      x[i + u * st] = fma(omega, sh[u], fma(alpha, ph[u], xx[u]));
+      const double ri = fma(-omega, tt[u], ss[u]);
+      r[i + u * st] = ri;
+      a0 = fma(rh[u], ri, a0);
+      a1 = fma(ri, ri, a1);
+    }
+  }
+  for (; i < n; i += st) {
     x[i] = fma(omega, shat[i], fma(alpha, phat[i], x[i]));
     const double ri = fma(-omega, t[i], s[i]);
     r[i] = ri;
@@ -229,28 +293,43 @@ static int solve_head(Ctx *c, const double *Rub, const double *Rpi, double *x, b
   return HMG_OK;
 }
 
+// Blocks of a grid-stride vector kernel: one wave of resident blocks (no partial second
+// wave), at most one row per thread; fixed per device, so the reductions stay deterministic.
+static int wave_grid(Ctx *c, int which, const void *kernel, int64_t n, unsigned *g) {
+  if (!c->wave_blocks[which]) {
+    int per_sm = 0;
+    HMG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRedThreads, 0));
+    c->wave_blocks[which] = std::max(1, std::min(per_sm * c->num_sms, kRedBlocks));
+  }
+  *g = (unsigned)std::min<int64_t>(c->wave_blocks[which], grid_for(n, kRedThreads));
+  return HMG_OK;
+}
+
 // one BiCGStab iteration and its check
 static int solve_body(Ctx *c, double *x, bool graph, cudaGraphConditionalHandle h) {
   const int64_t n = sys_n(c);
-  const unsigned vg = red_grid(n);
+  unsigned gp, gs, gx;
   int s;
+  if ((s = wave_grid(c, 0, (const void *)bicg_p_kernel, n, &gp))) return s;
+  if ((s = wave_grid(c, 1, (const void *)bicg_s_kernel, n, &gs))) return s;
+  if ((s = wave_grid(c, 2, (const void *)bicg_xr_kernel, n, &gx))) return s;
   {
     Prof pk(c, kCompKrylov);
-    bicg_p_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->p, c->v, c->scal, c->state, n);
+    bicg_p_kernel<<<gp, kRedThreads, 0, c->stream>>>(c->r, c->p, c->v, c->scal, c->state, n);
     HMG_CUDA(c, cudaGetLastError());
   }
   if ((s = precond_apply(c, c->p, c->phat))) return s;
   if ((s = sys_apply(c, c->phat, c->v, 1, c->rhat, Scal::RV, 0))) return s;
   {
     Prof pk(c, kCompKrylov);
-    bicg_s_kernel<<<vg, kRedThreads, 0, c->stream>>>(c->r, c->v, c->s, c->scal, c->state, n);
+    bicg_s_kernel<<<gs, kRedThreads, 0, c->stream>>>(c->r, c->v, c->s, c->scal, c->state, n);
     HMG_CUDA(c, cudaGetLastError());
   }
   if ((s = precond_apply(c, c->s, c->shat))) return s;
   if ((s = sys_apply(c, c->shat, c->t, 2, c->s, Scal::TS, Scal::TT))) return s;
   {
     Prof pk(c, kCompKrylov, 2);
-    bicg_xr_kernel<<<vg, kRedThreads, 0, c->stream>>>(x, c->r, c->s, c->t, c->phat, c->shat, c->rhat,
+    bicg_xr_kernel<<<gx, kRedThreads, 0, c->stream>>>(x, c->r, c->s, c->t, c->phat, c->shat, c->rhat,
                                                       c->scal, c->part, c->counter, c->state, n);
     if (graph) bicg_check_kernel<true><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
     else bicg_check_kernel<false><<<1, 1, 0, c->stream>>>(c->scal, c->state, c->hist, loop_params(c), h);
@@ -542,8 +621,13 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // w /= sqrt(nn) (w = 0 when nn = 0); *hout = sqrt(nn)
 __global__ void gm_normalize_kernel(double *__restrict__ w, int64_t n, const double *nn, double *hout) {
-  const double s = sqrt(*nn);
-  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  __shared__ double coef[2];
+  if (threadIdx.x == 0) {
+    coef[0] = sqrt(*nn);
+    coef[1] = coef[0] > 0.0 ? 1.0 / coef[0] : 0.0;
+  }
+  __syncthreads();
+  const double s = coef[0], inv = coef[1];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     w[i] *= inv;
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = s;

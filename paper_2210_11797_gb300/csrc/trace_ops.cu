@@ -312,13 +312,16 @@ __global__ void restrict_kernel(const T *__restrict__ R, const T *__restrict__ g
                                 const int32_t *__restrict__ col_edges) {
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= C) return;
-  const int c = (int)(K / d.L), k = (int)(K - (int64_t)c * d.L);
+  // 32-bit index arithmetic (the mesh limits keep every row index below 2^31)
+  const unsigned Ku = (unsigned)K, Lu = (unsigned)d.L;
+  const int c = (int)(Ku / Lu), k = (int)(Ku - (unsigned)c * Lu);
   const int32_t *ce = col_edges + 4 * (int64_t)c;
   T s = (T)0.5 * (R[(int64_t)__ldg(ce) * d.L + k] + R[(int64_t)__ldg(ce + 1) * d.L + k] +
                   R[(int64_t)__ldg(ce + 2) * d.L + k] + R[(int64_t)__ldg(ce + 3) * d.L + k]);
   const int64_t zb = d.NH + (int64_t)c * (d.L + 1) + k;
-  s += (k == 0 ? (T)1 : (T)0.5) * R[zb];
-  s += (k == d.L - 1 ? (T)1 : (T)0.5) * R[zb + 1];
+  // the weights 1 and 1/2 scale exactly, so each FMA rounds as the product-then-add did
+  s = fma(k == 0 ? (T)1 : (T)0.5, R[zb], s);
+  s = fma(k == d.L - 1 ? (T)1 : (T)0.5, R[zb + 1], s);
   bbar[K] = gamma[K] * s;
 }
 
@@ -329,20 +332,23 @@ __global__ void prolong_kernel(const T *__restrict__ lam_in, const T *__restrict
                                const int32_t *__restrict__ stencil) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= d.NT) return;
-  T p;
-  if (row < d.NH) {
-    const int e = (int)(row / d.L), k = (int)(row - (int64_t)e * d.L);
-    p = (T)0.5 * (dpi[(int64_t)stencil[8 * (int64_t)e] * d.L + k] +
-                  dpi[(int64_t)stencil[8 * (int64_t)e + 1] * d.L + k]);
+  // lam_in + (1/2)(a + b) as one FMA: the halving is exact, so it rounds as the add did
+  const T li = lam_in[row];
+  T out;
+  if (row < d.NH) {   // 32-bit index arithmetic (row indices stay below 2^31)
+    const unsigned ru = (unsigned)row, Lu = (unsigned)d.L;
+    const int e = (int)(ru / Lu), k = (int)(ru - (unsigned)e * Lu);
+    out = fma((T)0.5, dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e) * d.L + k] +
+                          dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e + 1) * d.L + k], li);
   } else {
-    const int64_t zr = row - d.NH;
-    const int c = (int)(zr / (d.L + 1)), k = (int)(zr - (int64_t)c * (d.L + 1));
+    const unsigned zr = (unsigned)(row - d.NH), L1 = (unsigned)d.L + 1u;
+    const int c = (int)(zr / L1), k = (int)(zr - (unsigned)c * L1);
     const int64_t K = (int64_t)c * d.L + k;
-    if (k == 0) p = dpi[K];
-    else if (k == d.L) p = dpi[K - 1];
-    else p = (T)0.5 * (dpi[K - 1] + dpi[K]);
+    if (k == 0) out = li + dpi[K];
+    else if (k == d.L) out = li + dpi[K - 1];
+    else out = fma((T)0.5, dpi[K - 1] + dpi[K], li);
   }
-  lam_out[row] = lam_in[row] + p;
+  lam_out[row] = out;
 }
 
 template <typename Tin, typename Tout>
