@@ -27,14 +27,14 @@ __device__ __forceinline__ T ldv(const T *p) {
   return *p;
 }
 
-// acc + sign * (row K of H) . x as one FMA per coefficient (acc = b, sign = -1: the residual).
-template <typename T, bool NEG, bool COH = false>
-__device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x, const MGArgs &a,
-                                     int c, int k, T acc) {
+// acc + sign * (row K of H) . x as one FMA per coefficient (acc = b, sign = -1: the residual);
+// xv(col, kk) gives x in column col, layer kk.
+template <typename T, bool NEG, typename XV>
+__device__ __forceinline__ T h_apply_f(const T *__restrict__ H, const MGArgs &a, int c, int k, T acc, const XV &xv) {
   const int64_t C = a.ncell, K = (int64_t)c * a.L + k;
   auto term = [&](int slot, int col, int kk) {
     const T h = __ldg(H + slot * C + K);
-    acc = fma(NEG ? -h : h, ldv<COH>(x + (int64_t)col * a.L + kk), acc);
+    acc = fma(NEG ? -h : h, xv(col, kk), acc);
   };
   term(0, c, k);
 #pragma unroll
@@ -44,13 +44,81 @@ __device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restric
   return acc;
 }
 
+template <typename T, bool NEG, bool COH = false>
+__device__ __forceinline__ T h_apply(const T *__restrict__ H, const T *__restrict__ x, const MGArgs &a,
+                                     int c, int k, T acc) {
+  return h_apply_f<T, NEG>(H, a, c, k, acc,
+                           [&](int col, int kk) { return ldv<COH>(x + (int64_t)col * a.L + kk); });
+}
+
+// b_coarse(cc, k) = sum over the four children ch of (b - H x)(ch, k); x == nullptr means 0
+// (a: the fine level).
+template <typename T, bool COH>
+__device__ __forceinline__ T restrict_value(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ b,
+                                            const T *__restrict__ x, const int32_t *__restrict__ children,
+                                            int cc, int k) {
+  T s = (T)0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int ch = __ldg(children + 4 * (int64_t)cc + i);
+    T r = ldv<COH>(b + (int64_t)ch * a.L + k);
+    if (x != nullptr) r = h_apply<T, true, COH>(H, x, a, ch, k, r);
+    s += r;
+  }
+  return s;
+}
+
+// Sources of the smoother's right-hand side per cell: r(c, k, K) is the vector the sweep
+// applies omega H_z^-1 to, out(c, k, K, v) the new iterate from that correction v.
+template <typename T, bool COH>
+struct SrcZero {   // zero start: x_out = omega H_z^-1 b
+  const T *b;
+  __device__ T r(const MGArgs &, int, int, int64_t K) const { return ldv<COH>(b + K); }
+  __device__ T out(const MGArgs &, int, int, int64_t, T v) const { return v; }
+};
+
+template <typename T, bool COH>
+struct SrcIter {   // x_out = x + omega H_z^-1 (b - H x)
+  const T *H, *b, *x;
+  __device__ T r(const MGArgs &a, int c, int k, int64_t K) const {
+    return h_apply<T, true, COH>(H, x, a, c, k, ldv<COH>(b + K));
+  }
+  __device__ T out(const MGArgs &, int, int, int64_t K, T v) const { return ldv<COH>(x + K) + v; }
+};
+
+template <typename T>
+struct SrcRestrict {   // zero start on the coarse level, b = the restricted fine residual (also stored)
+  MGArgs af;           // the fine level
+  const T *Hf, *bf, *xf;
+  const int32_t *children;
+  T *bc;
+  __device__ T r(const MGArgs &, int c, int k, int64_t K) const {
+    const T v = restrict_value<T, false>(af, Hf, bf, xf, children, c, k);
+    bc[K] = v;
+    return v;
+  }
+  __device__ T out(const MGArgs &, int, int, int64_t, T v) const { return v; }
+};
+
+template <typename T>
+struct SrcInject {   // x_in = x + P e (injection), then x_out = x_in + omega H_z^-1 (b - H x_in)
+  const T *H, *b, *x, *e;
+  const int32_t *parent;
+  __device__ T xin(const MGArgs &a, int col, int kk) const {
+    return x[(int64_t)col * a.L + kk] + e[(int64_t)__ldg(parent + col) * a.L + kk];
+  }
+  __device__ T r(const MGArgs &a, int c, int k, int64_t K) const {
+    return h_apply_f<T, true>(H, a, c, k, b[K], [&](int col, int kk) { return xin(a, col, kk); });
+  }
+  __device__ T out(const MGArgs &a, int c, int k, int64_t, T v) const { return xin(a, c, k) + v; }
+};
+
 // One column block (columns blk * cpb ..) of the block-Jacobi smoother, by the whole thread
-// block. MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
-template <typename T, int MODE, bool COH>
-__device__ __forceinline__ void smooth_block(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ hw,
-                                             const T *__restrict__ hl, const T *__restrict__ hcp,
-                                             const T *__restrict__ b, const T *__restrict__ x,
-                                             T *__restrict__ x_out, int blk, unsigned char *smem_raw) {
+// block: x_out = src.out(omega H_z^-1 src.r).
+template <typename T, typename Src>
+__device__ __forceinline__ void smooth_block_src(const MGArgs &a, const T *__restrict__ hw, const T *__restrict__ hl,
+                                                 const T *__restrict__ hcp, const Src &src, T *__restrict__ x_out,
+                                                 int blk, unsigned char *smem_raw) {
   // one column per lane in the serial phase: column j at j * ld, ld = L rounded up to odd so
   // that the lanes of a half-warp hit distinct banks
   const int ld = a.L | 1;
@@ -65,8 +133,7 @@ __device__ __forceinline__ void smooth_block(const MGArgs &a, const T *__restric
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
-    T r = ldv<COH>(b + K);
-    if (MODE != 0) r = h_apply<T, true, COH>(H, x, a, c, k, r);
+    const T r = src.r(a, c, k, K);
     const int j = (c - c0) * ld + k;
     sr[j] = r * __ldg(hw + K);
     sl[j] = __ldg(hl + K);
@@ -88,9 +155,19 @@ __device__ __forceinline__ void smooth_block(const MGArgs &a, const T *__restric
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const T v = sr[(i / a.L) * ld + i % a.L];
-    x_out[base + i] = MODE == 0 ? v : ldv<COH>(x + base + i) + v;
+    const int cl = i / a.L, k = i % a.L;
+    x_out[base + i] = src.out(a, c0 + cl, k, base + i, sr[cl * ld + k]);
   }
+}
+
+// MODE 0: x_out = omega H_z^-1 b (zero start); 1: x_out = x + omega H_z^-1 (b - H x).
+template <typename T, int MODE, bool COH>
+__device__ __forceinline__ void smooth_block(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ hw,
+                                             const T *__restrict__ hl, const T *__restrict__ hcp,
+                                             const T *__restrict__ b, const T *__restrict__ x,
+                                             T *__restrict__ x_out, int blk, unsigned char *smem_raw) {
+  if (MODE == 0) smooth_block_src(a, hw, hl, hcp, SrcZero<T, COH>{b}, x_out, blk, smem_raw);
+  else smooth_block_src(a, hw, hl, hcp, SrcIter<T, COH>{H, b, x}, x_out, blk, smem_raw);
 }
 
 template <typename T, int MODE>
@@ -120,21 +197,12 @@ __global__ void mg_inject_kernel(const T *__restrict__ x, const T *__restrict__ 
   inject_cell<T, false>(x, e, parent, L, K, x_out);
 }
 
-// b_coarse(cc, k) = sum over the four children ch of (b - H x)(ch, k); x == nullptr means 0.
 template <typename T, bool COH>
 __device__ __forceinline__ void restrict_cell(const MGArgs &a, const T *__restrict__ H, const T *__restrict__ b,
                                               const T *__restrict__ x, const int32_t *__restrict__ children,
                                               int64_t Kc, T *__restrict__ bc) {
   const int cc = (int)(Kc / a.L), k = (int)(Kc - (int64_t)cc * a.L);
-  T s = (T)0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int ch = __ldg(children + 4 * (int64_t)cc + i);
-    T r = ldv<COH>(b + (int64_t)ch * a.L + k);
-    if (x != nullptr) r = h_apply<T, true, COH>(H, x, a, ch, k, r);
-    s += r;
-  }
-  bc[Kc] = s;
+  bc[Kc] = restrict_value<T, COH>(a, H, b, x, children, cc, k);
 }
 
 template <typename T>
@@ -145,6 +213,30 @@ __global__ void mg_residual_restrict_kernel(const MGArgs a, const T *__restrict_
   const int64_t Kc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (Kc >= (int64_t)ncol_c * a.L) return;
   restrict_cell<T, false>(a, H, b, x, children, Kc, bc);
+}
+
+// Restriction of the fine residual fused with the coarse level's first, zero-start sweep:
+// bc = P^T (b_f - H_f x_f) (stored for the later sweeps) and x_out = omega H_z^-1 bc.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mg_restrict_smooth_kernel(const MGArgs a, const T *__restrict__ hw, const T *__restrict__ hl,
+                              const T *__restrict__ hcp, const MGArgs af, const T *__restrict__ Hf,
+                              const T *__restrict__ bf, const T *__restrict__ xf,
+                              const int32_t *__restrict__ children, T *__restrict__ bc, T *__restrict__ x_out) {
+  extern __shared__ unsigned char smem_raw[];
+  smooth_block_src(a, hw, hl, hcp, SrcRestrict<T>{af, Hf, bf, xf, children, bc}, x_out, blockIdx.x, smem_raw);
+}
+
+// Injection of the coarse correction e fused with the first post-smoothing sweep:
+// x_in = x + P e, x_out = x_in + omega H_z^-1 (b - H x_in) (x_in is not stored).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mg_inject_smooth_kernel(const MGArgs a, const T *__restrict__ H, const T *__restrict__ hw,
+                            const T *__restrict__ hl, const T *__restrict__ hcp, const T *__restrict__ b,
+                            const T *__restrict__ x, const T *__restrict__ e, const int32_t *__restrict__ parent,
+                            T *__restrict__ x_out) {
+  extern __shared__ unsigned char smem_raw[];
+  smooth_block_src(a, hw, hl, hcp, SrcInject<T>{H, b, x, e, parent}, x_out, blockIdx.x, smem_raw);
 }
 
 template <typename T>
@@ -290,20 +382,61 @@ static MGArgs mg_args(const Ctx *c, int l) {
   return a;
 }
 
+// Launch shape of a smoothing sweep on level l: column blocks of a.cpb columns, threads per
+// block, dynamic shared memory.
+struct SmoothShape {
+  MGArgs a;
+  unsigned grid;
+  int threads;
+  size_t smem;
+};
+
+template <typename T>
+static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int threads_override = 0) {
+  const Level &lv = c->lv[l];
+  SmoothShape sh;
+  sh.a = mg_args(c, l);
+  if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) sh.a.cpb = cpb_override;
+  sh.grid = (unsigned)((lv.ncol + sh.a.cpb - 1) / sh.a.cpb);
+  sh.smem = (size_t)3 * sh.a.cpb * (lv.nlev | 1) * sizeof(T);
+  const int tmax = threads_override > 0 ? threads_override : (c->tune_mg_threads[l] > 0 ? c->tune_mg_threads[l] : 256);
+  int threads = ((sh.a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
+  if (threads > tmax) threads = tmax;
+  if (threads < ((sh.a.cpb + 31) / 32) * 32) threads = ((sh.a.cpb + 31) / 32) * 32;   // a lane per column
+  sh.threads = threads;
+  return sh;
+}
+
 template <typename T, int MODE>
 static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0, int threads_override = 0) {
   const Level &lv = c->lv[l];
-  MGArgs a = mg_args(c, l);
-  if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) a.cpb = cpb_override;
-  const unsigned g = (unsigned)((lv.ncol + a.cpb - 1) / a.cpb);
-  const size_t smem = (size_t)3 * a.cpb * (lv.nlev | 1) * sizeof(T);
-  const int tmax = threads_override > 0 ? threads_override : (c->tune_mg_threads[l] > 0 ? c->tune_mg_threads[l] : 256);
-  int threads = ((a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
-  if (threads > tmax) threads = tmax;
-  if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
-  mg_smooth_kernel<T, MODE><<<g, threads, smem, c->stream>>>(a, Prec<T>::H(lv), Prec<T>::Hz_w(lv),
-                                                             Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x,
-                                                             out);
+  const SmoothShape sh = smooth_shape<T>(c, l, cpb_override, threads_override);
+  mg_smooth_kernel<T, MODE><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
+      sh.a, Prec<T>::H(lv), Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x, out);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// Level l+1's restricted right-hand side (into lv[l+1].vb) and its first zero-start sweep
+// (into out), from level l's b and x, in one launch.
+template <typename T>
+static int restrict_smooth(Ctx *c, int l, const T *bf, const T *xf, T *out) {
+  const Level &fine = c->lv[l], &lv = c->lv[l + 1];
+  const SmoothShape sh = smooth_shape<T>(c, l + 1);
+  mg_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
+      sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), mg_args(c, l), Prec<T>::H(fine), bf, xf,
+      lv.children, static_cast<T *>(lv.vb), out);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// x + P e (e from level l+1) and level l's first post-smoothing sweep from it, in one launch.
+template <typename T>
+static int inject_smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
+  const Level &lv = c->lv[l];
+  const SmoothShape sh = smooth_shape<T>(c, l);
+  mg_inject_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
+      sh.a, Prec<T>::H(lv), Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x, e, lv.parent, out);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -420,47 +553,84 @@ static int launch_coarse(Ctx *c, T **x1) {
   return HMG_OK;
 }
 
+// Levels of at most kFuseMaxCells cells are latency-bound: there the restriction runs inside
+// the level's first (zero-start) sweep and the injection inside its first post-sweep, one
+// launch each instead of two. On larger levels the separate, fully parallel restriction and
+// injection kernels are faster (measured on GB300 at C96 and C192, 30 layers).
+constexpr int64_t kFuseMaxCells = 1 << 18;
+static bool fuse_level(const Ctx *c, int l) { return c->lv[l].ncell <= kFuseMaxCells; }
+
 int vcycle_launches(const Ctx *c) {
-  const int nl = c->nmg - 1;
-  if (c->opt.mg_fused && c->nmg >= 2) return (c->opt.mg_npre + 1) + 2 + (c->opt.mg_npost + 1);
-  return nl * (c->opt.mg_npre + 1) + c->opt.mg_ncoarse + nl * (c->opt.mg_npost + 1);
+  const int nmg = c->nmg, npre = c->opt.mg_npre, npost = c->opt.mg_npost;
+  if (nmg == 1) return c->opt.mg_ncoarse;
+  // finest level: pre-sweeps, restriction, injection and post-sweeps; the coarse levels one launch
+  if (c->opt.mg_fused) return npre + 1 + 1 + 1 + npost;
+  int n = npre + 1 + npost;   // finest level: pre-sweeps, injection, post-sweeps
+  for (int l = 1; l < nmg; ++l) {
+    const bool f = fuse_level(c, l);
+    n += (l == nmg - 1 ? c->opt.mg_ncoarse : npre) + (f ? 0 : 1);   // sweeps (+ restriction)
+    if (l < nmg - 1) n += npost + (f ? 0 : 1);                        // post-sweeps (+ injection)
+  }
+  return n;
 }
 
 template <typename T>
 int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
-  const int nmg = c->nmg;
+  const int nmg = c->nmg, npre = c->opt.mg_npre, npost = c->opt.mg_npost;
   const T *b[kMaxLevels];
   T *x[kMaxLevels];
   int st;
   b[0] = b0;
+  if ((st = sweeps_from_zero<T>(c, 0, b0, nmg == 1 ? c->opt.mg_ncoarse : npre, &x[0], x0))) return st;
   // with mg_fused, only the finest level runs step by step; levels >= 1 are one launch
   const bool fused = c->opt.mg_fused && nmg >= 2;
-  const int ldown = fused ? 1 : nmg - 1;
-  for (int l = 0; l < ldown; ++l) {
-    if ((st = sweeps_from_zero<T>(c, l, b[l], c->opt.mg_npre, &x[l], l == 0 ? x0 : nullptr))) return st;
-    const Level &coarse = c->lv[l + 1];
-    MGArgs a = mg_args(c, l);
+  if (fused) {
+    const Level &coarse = c->lv[1];
     T *bc = static_cast<T *>(coarse.vb);
     mg_residual_restrict_kernel<T><<<grid_for(coarse.ncell, 256), 256, 0, c->stream>>>(
-        a, Prec<T>::H(c->lv[l]), b[l], x[l], coarse.children, coarse.ncol, bc);
+        mg_args(c, 0), Prec<T>::H(c->lv[0]), b[0], x[0], coarse.children, coarse.ncol, bc);
     HMG_CUDA(c, cudaGetLastError());
-    b[l + 1] = bc;
-  }
-  if (fused) {
+    b[1] = bc;
     if ((st = launch_coarse<T>(c, &x[1]))) return st;
   } else {
-    const int lc = nmg - 1;
-    if ((st = sweeps_from_zero<T>(c, lc, b[lc], c->opt.mg_ncoarse, &x[lc], lc == 0 ? x0 : nullptr))) return st;
+    for (int l = 0; l + 1 < nmg; ++l) {
+      // residual + restriction to level l+1, then its first, zero-start sweep (one launch on
+      // small levels)
+      const Level &cl = c->lv[l + 1];
+      T *cur = static_cast<T *>(cl.vx), *oth = static_cast<T *>(cl.vy);
+      if (fuse_level(c, l + 1)) {
+        if ((st = restrict_smooth<T>(c, l, b[l], x[l], cur))) return st;
+      } else {
+        mg_residual_restrict_kernel<T><<<grid_for(cl.ncell, 256), 256, 0, c->stream>>>(
+            mg_args(c, l), Prec<T>::H(c->lv[l]), b[l], x[l], cl.children, cl.ncol, static_cast<T *>(cl.vb));
+        if ((st = smooth<T, 0>(c, l + 1, static_cast<const T *>(cl.vb), nullptr, cur))) return st;
+      }
+      b[l + 1] = static_cast<const T *>(cl.vb);
+      const int n = l + 2 == nmg ? c->opt.mg_ncoarse : npre;
+      for (int i = 1; i < n; ++i) {
+        if ((st = smooth<T, 1>(c, l + 1, b[l + 1], cur, oth))) return st;
+        T *t = cur; cur = oth; oth = t;
+      }
+      x[l + 1] = cur;
+    }
   }
   // options are validated to mg_npre >= 1 and mg_npost >= 1
   for (int l = fused ? 0 : nmg - 2; l >= 0; --l) {
     Level &lv = c->lv[l];
     T *other = x[l] == static_cast<T *>(lv.vx) ? static_cast<T *>(lv.vy) : static_cast<T *>(lv.vx);
-    mg_inject_kernel<T><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,
-                                                                        lv.ncell, other);
-    HMG_CUDA(c, cudaGetLastError());
+    int done = 0;
+    if (l >= 1 && fuse_level(c, l)) {
+      // the injection rides in the first post-sweep (on the finest level it would add 7 FP64
+      // adds per cell to an FP64-bound sweep)
+      if ((st = inject_smooth<T>(c, l, b[l], x[l], x[l + 1], other))) return st;
+      done = 1;
+    } else {
+      mg_inject_kernel<T><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,
+                                                                          lv.ncell, other);
+      HMG_CUDA(c, cudaGetLastError());
+    }
     T *cur = other, *nxt = x[l];
-    for (int i = 0; i < c->opt.mg_npost; ++i) {
+    for (int i = done; i < npost; ++i) {
       if ((st = smooth<T, 1>(c, l, b[l], cur, nxt))) return st;
       T *t = cur; cur = nxt; nxt = t;
     }
