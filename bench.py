@@ -29,11 +29,10 @@ UNIT = "trace unknowns/s"
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture (see profiles/), keyed
 # by the sha256 of the kernel sources it was taken on; a changed source makes it stale (null).
-# The C96 figure is the C64 capture's dram__bytes_read.sum + dram__bytes_write.sum
-# (293.61 MB) scaled by the rows processed (C96 / C64 = 2.25).
+# C96: dram__bytes_read.sum + dram__bytes_write.sum of the full sweep, captured at full size
+# (a one-pass metric set), mean of two launches.
 TRAFFIC = {
-    "line_sweep:c96:fp64:1c3de3ea131409fd": 660622464,
-    "line_sweep:c64:fp64:1c3de3ea131409fd": 293609984,
+    "line_sweep:c96:fp64:b2e8bb9abf308333": 675950080,
 }
 
 

@@ -560,11 +560,11 @@ int hmg_autotune(hmg_ctx *c) {
 int hmg_get_launch_shapes(hmg_ctx *c, int32_t *sweep, int32_t *mg, int32_t nmg) {
   if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
-  sweep[0] = c->tune_sweep_cpb;
-  sweep[1] = c->tune_sweep_threads;
+  sweep[0] = c->tune_sweep_cpb[0];
+  sweep[1] = c->tune_sweep_threads[0];
   for (int l = 0; l < nmg; ++l) {
-    mg[2 * l] = c->tune_mg_cpb[l];
-    mg[2 * l + 1] = c->tune_mg_threads[l];
+    mg[2 * l] = c->tune_mg_cpb[0][l];
+    mg[2 * l + 1] = c->tune_mg_threads[0][l];
   }
   return HMG_OK;
 }
@@ -577,11 +577,15 @@ int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, i
   for (int l = 0; l < nmg; ++l)
     if (!ok(mg[2 * l], mg[2 * l + 1])) return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
   drop_graph(c);   // captured launches carry the old shapes
-  c->tune_sweep_cpb = sweep[0];
-  c->tune_sweep_threads = sweep[1];
+  for (int p = 0; p < 2; ++p) {   // the same shapes for the FP64 and FP32 kernels
+    c->tune_sweep_cpb[p] = sweep[0];
+    c->tune_sweep_threads[p] = sweep[1];
+  }
   for (int l = 0; l < nmg; ++l) {
-    c->tune_mg_cpb[l] = mg[2 * l];
-    c->tune_mg_threads[l] = mg[2 * l + 1];
+    for (int p = 0; p < 2; ++p) {
+      c->tune_mg_cpb[p][l] = mg[2 * l];
+      c->tune_mg_threads[p][l] = mg[2 * l + 1];
+    }
   }
   return HMG_OK;
 }

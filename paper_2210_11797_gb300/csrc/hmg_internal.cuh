@@ -132,8 +132,9 @@ struct Ctx {
   } graph_key{};
   // autotuned launch shapes (0 = default): columns per block of the line sweep and of the
   // pressure smoother on each level
-  int tune_sweep_cpb = 0, tune_sweep_threads = 0;
-  int tune_mg_cpb[kMaxLevels] = {0}, tune_mg_threads[kMaxLevels] = {0};
+  // launch shapes chosen by autotune, [0] for the FP64 kernels, [1] for the FP32 preconditioner's
+  int tune_sweep_cpb[2] = {0, 0}, tune_sweep_threads[2] = {0, 0};
+  int tune_mg_cpb[2][kMaxLevels] = {}, tune_mg_threads[2][kMaxLevels] = {};
   // learned coarse correction: FP32 master weights, one activation buffer, corner neighbours
   float *nn_w = nullptr;
   void *nn_act = nullptr;
@@ -298,8 +299,8 @@ int fgmres_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
 // Launch-shape autotuning of one context (columns per block of the sweep and MG smoother).
 int autotune(Ctx *c);
 // Sweep / smoother launches with explicit columns and threads per block (autotuner).
-int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms);
-int time_mg_cpb(Ctx *c, int level, int cpb, int threads, float *ms);
+int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms);
+int time_mg_cpb(Ctx *c, int level, int cpb, int threads, int fp32, float *ms);
 // Columns per block of the pressure smoother: at most 64, and its three shared-memory arrays
 // (column stride nlev rounded up to odd) within the default 48 KB (FP64).
 inline int mg_cpb_limit(int nlev) {

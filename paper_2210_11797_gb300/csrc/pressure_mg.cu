@@ -370,13 +370,15 @@ __global__ void __launch_bounds__(256) mg_coarse_kernel(const CoarseArgs<T> p) {
   }
 }
 
-static MGArgs mg_args(const Ctx *c, int l) {
+// pm: 0 for the FP64 kernels' tuned shapes, 1 for the FP32 ones
+static MGArgs mg_args(const Ctx *c, int l, int pm = 0) {
   const Level &lv = c->lv[l];
   MGArgs a;
   a.L = lv.nlev;
   a.ncol = lv.ncol;
   const int cdef = mg_cpb_limit(lv.nlev) < 32 ? mg_cpb_limit(lv.nlev) : 32;
-  a.cpb = c->tune_mg_cpb[l] > 0 && c->tune_mg_cpb[l] <= mg_cpb_limit(lv.nlev) ? c->tune_mg_cpb[l] : cdef;
+  const int tc = c->tune_mg_cpb[pm][l];
+  a.cpb = tc > 0 && tc <= mg_cpb_limit(lv.nlev) ? tc : cdef;
   a.ncell = lv.ncell;
   a.col_nbr = lv.col_nbr;
   return a;
@@ -395,11 +397,13 @@ template <typename T>
 static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int threads_override = 0) {
   const Level &lv = c->lv[l];
   SmoothShape sh;
-  sh.a = mg_args(c, l);
+  const int pm = sizeof(T) == 4 ? 1 : 0;
+  sh.a = mg_args(c, l, pm);
   if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) sh.a.cpb = cpb_override;
   sh.grid = (unsigned)((lv.ncol + sh.a.cpb - 1) / sh.a.cpb);
   sh.smem = (size_t)3 * sh.a.cpb * (lv.nlev | 1) * sizeof(T);
-  const int tmax = threads_override > 0 ? threads_override : (c->tune_mg_threads[l] > 0 ? c->tune_mg_threads[l] : 256);
+  const int tt = c->tune_mg_threads[pm][l];
+  const int tmax = threads_override > 0 ? threads_override : (tt > 0 ? tt : 256);
   int threads = ((sh.a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > tmax) threads = tmax;
   if (threads < ((sh.a.cpb + 31) / 32) * 32) threads = ((sh.a.cpb + 31) / 32) * 32;   // a lane per column
@@ -441,13 +445,15 @@ static int inject_smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *o
   return HMG_OK;
 }
 
-// Average time of 5 FP64 smoothing sweeps on level l with `cpb` columns per block.
-int time_mg_cpb(Ctx *c, int l, int cpb, int threads, float *ms) {
+// Best-of-three average time of a smoothing sweep on level l with `cpb` columns per block,
+// in FP64 (fp32 = 0) or FP32.
+template <typename T>
+static int time_mg_cpb_t(Ctx *c, int l, int cpb, int threads, float *ms) {
   Level &lv = c->lv[l];
-  double *b = static_cast<double *>(lv.vb), *x = static_cast<double *>(lv.vx), *y = static_cast<double *>(lv.vy);
-  HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * lv.ncell, c->stream));
-  HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * lv.ncell, c->stream));
-  int st = smooth<double, 1>(c, l, b, x, y, cpb, threads);
+  T *b = static_cast<T *>(lv.vb), *x = static_cast<T *>(lv.vx), *y = static_cast<T *>(lv.vy);
+  HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(T) * lv.ncell, c->stream));
+  HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(T) * lv.ncell, c->stream));
+  int st = smooth<T, 1>(c, l, b, x, y, cpb, threads);
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
@@ -455,7 +461,7 @@ int time_mg_cpb(Ctx *c, int l, int cpb, int threads, float *ms) {
   float best = 1e30f;
   for (int rep = 0; rep < 3 && !st; ++rep) {
     HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < 10 && !st; ++i) st = smooth<double, 1>(c, l, b, x, y, cpb, threads);
+    for (int i = 0; i < 10 && !st; ++i) st = smooth<T, 1>(c, l, b, x, y, cpb, threads);
     HMG_CUDA(c, cudaEventRecord(e1, c->stream));
     HMG_CUDA(c, cudaEventSynchronize(e1));
     float t = 0.f;
@@ -466,6 +472,10 @@ int time_mg_cpb(Ctx *c, int l, int cpb, int threads, float *ms) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
+}
+
+int time_mg_cpb(Ctx *c, int l, int cpb, int threads, int fp32, float *ms) {
+  return fp32 ? time_mg_cpb_t<float>(c, l, cpb, threads, ms) : time_mg_cpb_t<double>(c, l, cpb, threads, ms);
 }
 
 // n sweeps on level l from zero, or from x0 (n >= 1); the result ends in *cur (one of
@@ -502,7 +512,7 @@ static int launch_coarse(Ctx *c, T **x1) {
   for (int l = 1; l < nmg; ++l) {
     const Level &lv = c->lv[l];
     CoarseLevel<T> &q = p.lv[l];
-    q.a = mg_args(c, l);
+    q.a = mg_args(c, l, sizeof(T) == 4 ? 1 : 0);
     q.H = Prec<T>::H(lv);
     q.hw = Prec<T>::Hz_w(lv);
     q.hl = Prec<T>::Hz_l(lv);

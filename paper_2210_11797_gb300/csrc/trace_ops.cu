@@ -273,13 +273,14 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   a.ncol = f.ncol;
   const int cpb_max = sweep_cpb_limit(f.nlev);
   const int cpb_def = cpb_max < 32 ? cpb_max : 32;
-  a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb > 0 ? c->tune_sweep_cpb : cpb_def);
+  const int pm = sizeof(T) == 4 ? 1 : 0;   // FP32 preconditioner kernels have their own tuned shape
+  a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb[pm] > 0 ? c->tune_sweep_cpb[pm] : cpb_def);
   if (a.cpb > cpb_max) a.cpb = cpb_max;
   a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
   a.stencil = f.edge_stencil;
   a.col_edges = f.col_edges;
   // threads: the column block's rows rounded up to whole warps (at most 256)
-  const int tmax = threads_override > 0 ? threads_override : (c->tune_sweep_threads > 0 ? c->tune_sweep_threads : 256);
+  const int tmax = threads_override > 0 ? threads_override : (c->tune_sweep_threads[pm] > 0 ? c->tune_sweep_threads[pm] : 256);
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
   if (threads > tmax) threads = tmax;
   if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
@@ -540,13 +541,19 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
 namespace hmg {
 
 // Average time of 5 full FP64 sweeps with `cpb` columns per z-block (work vectors as data).
-int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms) {
+// Best-of-three average time of a full sweep with `cpb` columns per block, in FP64 or (fp32)
+// with the FP32 preconditioner's types (FP32 S and lambda in, FP64 b and lambda out).
+int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms) {
   const int64_t T = c->lv[0].ntrace;
   double *b = static_cast<double *>(c->w1), *x = static_cast<double *>(c->w2), *y = static_cast<double *>(c->w3);
   HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(double) * T, c->stream));
   HMG_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * T, c->stream));
+  auto run = [&]() {
+    return fp32 ? launch_sweep<float, double, double, false>(c, b, reinterpret_cast<const float *>(x), y, cpb, threads)
+                : launch_sweep<double, double, double, false>(c, b, x, y, cpb, threads);
+  };
   int st;
-  if ((st = launch_sweep<double, double, double, false>(c, b, x, y, cpb, threads))) return st;   // warm-up
+  if ((st = run())) return st;   // warm-up
   cudaEvent_t e0, e1;
   HMG_CUDA(c, cudaEventCreate(&e0));
   HMG_CUDA(c, cudaEventCreate(&e1));
@@ -554,7 +561,7 @@ int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms) {
   float best = 1e30f;
   for (int rep = 0; rep < 3 && !st; ++rep) {
     HMG_CUDA(c, cudaEventRecord(e0, c->stream));
-    for (int i = 0; i < 10 && !st; ++i) st = launch_sweep<double, double, double, false>(c, b, x, y, cpb, threads);
+    for (int i = 0; i < 10 && !st; ++i) st = run();
     HMG_CUDA(c, cudaEventRecord(e1, c->stream));
     HMG_CUDA(c, cudaEventSynchronize(e1));
     float t = 0.f;
@@ -569,32 +576,36 @@ int time_sweep_cpb(Ctx *c, int cpb, int threads, float *ms) {
 
 int autotune(Ctx *c) {
   const Level &f = c->lv[0];
-  const int cmax = sweep_cpb_limit(f.nlev);
-  int best = cmax < 32 ? cmax : 32, best_t = 256;
-  float best_ms = 1e30f;
   const int profile = c->opt.profile;
   c->opt.profile = 0;
   int st = HMG_OK;
-  for (int cand : {32, 64, 16, 8, 4, 2, 1})
-    for (int thr : {256, 128}) {
-      if (cand > cmax || st) continue;
-      float ms = 0.f;
-      if ((st = time_sweep_cpb(c, cand, thr, &ms))) break;
-      if (ms < best_ms) { best_ms = ms; best = cand; best_t = thr; }
-    }
-  if (!st) { c->tune_sweep_cpb = best; c->tune_sweep_threads = best_t; }
-  for (int l = 0; l < c->nmg && !st; ++l) {
-    const int mmax = mg_cpb_limit(c->lv[l].nlev);
-    int mbest = mmax < 32 ? mmax : 32, mbest_t = 256;
-    float mbest_ms = 1e30f;
+  // FP64 shapes always; FP32 ones when the FP32 preconditioner's coefficients exist
+  for (int pm = 0; pm < 2 && !st; ++pm) {
+    if (pm == 1 && (!c->S32 || !c->lv[0].H32)) break;
+    const int cmax = sweep_cpb_limit(f.nlev);
+    int best = cmax < 32 ? cmax : 32, best_t = 256;
+    float best_ms = 1e30f;
     for (int cand : {32, 64, 16, 8, 4, 2, 1})
       for (int thr : {256, 128}) {
-        if (cand > mmax || st) continue;
+        if (cand > cmax || st) continue;
         float ms = 0.f;
-        if ((st = time_mg_cpb(c, l, cand, thr, &ms))) break;
-        if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; mbest_t = thr; }
+        if ((st = time_sweep_cpb(c, cand, thr, pm, &ms))) break;
+        if (ms < best_ms) { best_ms = ms; best = cand; best_t = thr; }
       }
-    if (!st) { c->tune_mg_cpb[l] = mbest; c->tune_mg_threads[l] = mbest_t; }
+    if (!st) { c->tune_sweep_cpb[pm] = best; c->tune_sweep_threads[pm] = best_t; }
+    for (int l = 0; l < c->nmg && !st; ++l) {
+      const int mmax = mg_cpb_limit(c->lv[l].nlev);
+      int mbest = mmax < 32 ? mmax : 32, mbest_t = 256;
+      float mbest_ms = 1e30f;
+      for (int cand : {32, 64, 16, 8, 4, 2, 1})
+        for (int thr : {256, 128}) {
+          if (cand > mmax || st) continue;
+          float ms = 0.f;
+          if ((st = time_mg_cpb(c, l, cand, thr, pm, &ms))) break;
+          if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; mbest_t = thr; }
+        }
+      if (!st) { c->tune_mg_cpb[pm][l] = mbest; c->tune_mg_threads[pm][l] = mbest_t; }
+    }
   }
   c->opt.profile = profile;
   return st;
