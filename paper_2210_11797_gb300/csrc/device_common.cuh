@@ -128,7 +128,9 @@ struct TraceDims {
 
 // acc + sign * (row of S) . x as a chain of fused multiply-adds, one per coefficient: with
 // acc = 0, sign = +1 it is S x; with acc = b, sign = -1 it is the residual b - S x without a
-// separate subtraction (the FP64 issue rate, not HBM, bounds these kernels on GB300).
+// separate subtraction (the FP64 issue rate, not HBM, bounds these kernels on GB300). S is
+// larger than L2 and read once per kernel, so its loads are marked evict-first: the gathered
+// x values and the other vectors stay in L2.
 template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row_h(const TS *__restrict__ S, const TX *__restrict__ x,
                                       const int32_t *__restrict__ stencil, const TraceDims d,
@@ -141,7 +143,7 @@ __device__ __forceinline__ TA s_row_h(const TS *__restrict__ S, const TX *__rest
   const int64_t z2 = d.NH + (int64_t)c2 * (d.L + 1) + k;
   const int64_t T = d.NT;
   auto term = [&](int slot, int64_t col) {
-    const TA a = (TA)ld(S + slot * T + row);
+    const TA a = (TA)__ldcs(S + slot * T + row);   // S streams through once: evict first
     acc = fma(NEG ? -a : a, (TA)ld(x + col), acc);
   };
   term(0, row);
@@ -168,7 +170,7 @@ __device__ __forceinline__ TA s_row_z(const TS *__restrict__ S, const TX *__rest
   const int64_t T = d.NT;
   const int32_t *ce = col_edges + 4 * (int64_t)c;
   auto term = [&](int slot, int64_t col) {
-    const TA a = (TA)ld(S + slot * T + row);
+    const TA a = (TA)__ldcs(S + slot * T + row);   // S streams through once: evict first
     acc = fma(NEG ? -a : a, (TA)ld(x + col), acc);
   };
   term(0, row);
