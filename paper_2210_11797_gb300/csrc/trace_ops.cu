@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(256)
     T *sl = sr + a.cpb * ld, *scp = sl + a.cpb * ld;
     const int64_t base = d.NH + (int64_t)c0 * L1;
     // all threads: r omega / pivot and the factors, so that the serial Thomas recurrences
-    // below are one FMA per row each (factors from trace_factor_kernel)
+    // below are one FMA per row each (factors from trace_factor_kernel); two rows per pass
+    // keep twice the gathers in flight
+#pragma unroll 2
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
