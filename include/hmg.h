@@ -132,6 +132,10 @@ typedef struct {
                            1: from the lambda (hmg_solve) or [u | Pi] (hmg_solve_mixed, its
                            internal copy of the last solution) passed in, r_0 = B - S lambda_0
                            (resuming a solve, or a previous time step's solution) */
+  int32_t mg_fuse_cells; /* coarse levels of at most this many cells (default 262144) run the
+                           restriction inside their first sweep and the injection inside their
+                           first post-sweep, one launch instead of two (same arithmetic,
+                           bitwise the same result); 0: never. Must be >= 0 */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */

@@ -50,6 +50,7 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (!(o.stall_ratio > 0.0)) return bad("stall_ratio");
   if (o.warm_start != 0 && o.warm_start != 1) return bad("warm_start must be 0 or 1");
   if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
+  if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
   return HMG_OK;
 }
 
@@ -127,6 +128,7 @@ int hmg_default_options(hmg_options *o) {
   o->restart = 30;
   o->stall_ratio = 0.9;
   o->mg_fused = 0;
+  o->mg_fuse_cells = 1 << 18;
   return HMG_OK;
 }
 

@@ -563,12 +563,12 @@ static int launch_coarse(Ctx *c, T **x1) {
   return HMG_OK;
 }
 
-// Levels of at most kFuseMaxCells cells are latency-bound: there the restriction runs inside
-// the level's first (zero-start) sweep and the injection inside its first post-sweep, one
-// launch each instead of two. On larger levels the separate, fully parallel restriction and
-// injection kernels are faster (measured on GB300 at C96 and C192, 30 layers).
-constexpr int64_t kFuseMaxCells = 1 << 18;
-static bool fuse_level(const Ctx *c, int l) { return c->lv[l].ncell <= kFuseMaxCells; }
+// Levels of at most opt.mg_fuse_cells cells (2^18 by default) are latency-bound: there the
+// restriction runs inside the level's first (zero-start) sweep and the injection inside its
+// first post-sweep, one launch each instead of two. On larger levels the separate, fully
+// parallel restriction and injection kernels are faster (measured on GB300 at C96 and C192,
+// 30 layers).
+static bool fuse_level(const Ctx *c, int l) { return c->lv[l].ncell <= (int64_t)c->opt.mg_fuse_cells; }
 
 int vcycle_launches(const Ctx *c) {
   const int nmg = c->nmg, npre = c->opt.mg_npre, npost = c->opt.mg_npost;

@@ -60,7 +60,8 @@ class Options(C.Structure):
                 ("mg_omega", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
                 ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
-                ("stall_ratio", C.c_double), ("mg_fused", C.c_int32), ("warm_start", C.c_int32)]
+                ("stall_ratio", C.c_double), ("mg_fused", C.c_int32), ("warm_start", C.c_int32),
+                ("mg_fuse_cells", C.c_int32)]
 
 
 class SolveStats(C.Structure):

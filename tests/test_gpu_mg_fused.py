@@ -1,9 +1,10 @@
 """The coarse levels of the pressure V-cycle (Sec. 2.3) as one cooperative launch (mg_fused = 1)
-against one launch per smoothing sweep, restriction and injection (mg_fused = 0). The two run
-the same arithmetic in the same order, so their outputs agree bit for bit: the V-cycle in FP64
-and FP32, the non-nested preconditioner, whole solves (with and without the CUDA graph), and
-the mixed system with the Schur preconditioner. The V-cycle is also checked against the
-oracle's."""
+against one launch per smoothing sweep, restriction and injection (mg_fused = 0), and the
+restriction / injection run inside the neighbouring sweep on small levels (mg_fuse_cells)
+against separate kernels. All forms run the same arithmetic in the same order, so their
+outputs agree bit for bit: the V-cycle in FP64 and FP32, the non-nested preconditioner, whole
+solves (with and without the CUDA graph), and the mixed system with the Schur
+preconditioner. The V-cycle is also checked against the oracle's."""
 import numpy as np
 import pytest
 
@@ -92,4 +93,44 @@ def test_fused_vcycle_with_tuned_launch_shapes():
     gpu.autotune()
     gpu.set_options(mg_fused=1)
     np.testing.assert_array_equal(_np(gpu.vcycle(b)), ref)
+    gpu.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_restriction_and_injection_inside_the_sweeps_are_bitwise_the_separate_kernels(name):
+    from paper_2210_11797_gb300.hmg import Solver
+    w = CASES[name]()
+    gpu = Solver(w.hier, w.coeffs, tol=1e-10, mg_fuse_cells=0)   # separate kernels everywhere
+    rng = np.random.default_rng(6)
+    b = _cuda(rng.standard_normal(gpu.ncell))
+    r = _cuda(rng.standard_normal(gpu.ntrace))
+    ref_v, ref_z = _np(gpu.vcycle(b)), _np(gpu.precond(r))
+    gpu.set_options(mg_fuse_cells=1 << 30)                          # fused on every coarse level
+    np.testing.assert_array_equal(_np(gpu.vcycle(b)), ref_v)
+    np.testing.assert_array_equal(_np(gpu.precond(r)), ref_z)
+    gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solves_with_and_without_the_fused_steps_agree_bitwise(precision):
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(24, 30, seed=11)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    out = []
+    for cells in (0, 1 << 30):
+        gpu = Solver(w.hier, w.coeffs, tol=1e-8, precision=precision, mg_fuse_cells=cells)
+        lam, st = gpu.solve(Rub, Rpi)
+        assert st["status"] == "ok"
+        out.append((_np(lam), st["iterations"]))
+        gpu.close()
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    assert out[1][1] == out[0][1]
+
+
+def test_fuse_threshold_must_not_be_negative():
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w = I.planar_helmholtz()
+    gpu = Solver(w.hier, w.coeffs)
+    with pytest.raises(HmgError):
+        gpu.set_options(mg_fuse_cells=-1)
     gpu.close()
