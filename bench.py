@@ -512,7 +512,7 @@ def oracle_sample(workload: str, steps: int, warmup: int, seconds: float | None,
         _lam, hist, _st = s.solve_trace(B, w.tol)
         its_needed = len(hist) - 1
     step_s = statistics.median(t_rhs) + its_needed * statistics.median(t_it)
-    return {"workload": w.name, "T": w.mesh.n_trace, "setup_s": setup_s, "rhs_s": statistics.median(t_rhs),
+    return {"workload": w.name, "T": w.mesh.n_trace, "tol": w.tol, "setup_s": setup_s, "rhs_s": statistics.median(t_rhs),
             "iter_s": statistics.median(t_it), "its": its_needed, "step_s": step_s,
             "samples": len(t_it), "value": w.mesh.n_trace / step_s}
 
@@ -563,7 +563,7 @@ def main():
                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(r["step_s"] * 1e3, 2), "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": r["workload"], "ntrace": r["T"], "tol": 1e-6},
+               "config": {"workload": r["workload"], "ntrace": r["T"], "tol": r["tol"]},
                "cpu_baseline": {"value": round(r["value"], 1), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"B_lambda + 1 of {r['its']} BiCGStab iterations per step "
                                           f"({r['samples']} steps; setup {r['setup_s']:.0f} s untimed)"},
