@@ -489,7 +489,7 @@ int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps) {
 namespace {
 constexpr int64_t kNoAllocMaxTrace = int64_t(1) << 20;   // trace unknowns (1,048,576 doubles)
 constexpr int kNoAllocMaxDevices = 64;
-__device__ __align__(256) double g_sweep_scratch[kNoAllocMaxTrace];
+static __device__ __align__(256) double g_sweep_scratch[kNoAllocMaxTrace];
 std::mutex g_scratch_mu;
 double *g_scratch_ptr[kNoAllocMaxDevices] = {nullptr};
 
