@@ -2,7 +2,10 @@
 // operator H, the column block-Jacobi smoother x <- x + omega H_z^-1 (b - H x)
 // (Eq. pressure_block_jacobi, Thomas algorithm per column), residual + restriction (sum over
 // the four horizontal children) and prolongation (injection), in one V-cycle with
-// mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level.
+// mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level. On small
+// (latency-bound) levels the restriction runs inside the level's first sweep and the
+// injection inside its first post-sweep; with option mg_fused all coarse levels run as one
+// cooperative launch. Every form does the same arithmetic in the same order.
 #include <algorithm>
 #include <cmath>
 
