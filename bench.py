@@ -413,6 +413,62 @@ def run_variants(args, w, solver, Rub, Rpi, lam_ref, stream):
     return out
 
 
+def run_param_sweep(args):
+    """The parameter studies of the paper's Appendix B, on the GPU: solve time, iterations and
+    status as functions of the relaxation factors and smoothing-step counts, for
+    configuration 3c (omega of Algorithm 1 inside Algorithm 2, n_pre / n_post), configuration
+    2 (omega, n_smooth) and configuration 1 (omega_pressure, pressure-multigrid pre / post
+    sweeps). The other settings stay at the paper's values."""
+    import torch
+    from paper_2210_11797_gb300.hmg import Solver
+    w = workload_spec(args.workload)
+    Rub = torch.as_tensor(w.Rub.ravel()).cuda()
+    Rpi = torch.as_tensor(w.Rpi).cuda()
+    stream = torch.cuda.current_stream()
+    omegas = (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
+
+    def row(st, ms):
+        return {"ms": round(ms, 3), "iterations": st["iterations"], "status": st["status"]}
+
+    out = {"mode": "appendix_b_parameter_sweep", "workload": w.name, "tol": w.tol, "omegas": omegas}
+    solver = Solver(w.hier, w.coeffs, tol=w.tol, max_iter=200)
+    solver.autotune()
+    c3 = {}
+    for npre, npost in ((1, 1), (1, 2), (2, 2), (3, 2)):
+        for om in omegas:
+            solver.set_options(n_pre=npre, n_post=npost, omega=om)
+            _l, st, ms = _timed_solves(solver, Rub, Rpi, stream, 1)
+            c3[f"pre{npre}_post{npost}_omega{om}"] = row(st, ms)
+    out["config3c"] = c3
+    c2 = {}
+    solver.set_options(n_pre=1, n_post=2, precond="linesmooth", max_iter=400)
+    for nsm in (1, 2, 3):
+        for om in omegas:
+            solver.set_options(n_smooth=nsm, omega=om)
+            _l, st, ms = _timed_solves(solver, Rub, Rpi, stream, 1)
+            c2[f"nsmooth{nsm}_omega{om}"] = row(st, ms)
+    out["config2"] = c2
+    solver.close()
+    s1 = Solver(w.hier, w.coeffs, tol=w.tol, precond="schur", max_iter=200)
+    s1.autotune()
+    c1 = {}
+    for npre, npost in ((1, 1), (1, 2), (2, 1), (2, 2)):
+        for om in omegas:
+            s1.set_options(mg_npre=npre, mg_npost=npost, mg_omega=om)
+            for _ in range(2):
+                s1.solve_mixed(Rub, Rpi, check=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _u, _pi, st = s1.solve_mixed(Rub, Rpi, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c1[f"mgpre{npre}_mgpost{npost}_omegap{om}"] = row(st, e0.elapsed_time(e1))
+    out["config1"] = c1
+    s1.close()
+    return out
+
+
 def run_batched(args, rank, world):
     """64 independent cubed-sphere solves (N in {12,24,32,48}, L in {10,30,50,70}, drawn by
     SplitMix64 seed 3), each context autotuned, all solved in one graph launch per step."""
@@ -544,6 +600,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven Krylov loop in the timed region (profilers cannot look inside the "
                          "solve graph's conditional node)")
+    ap.add_argument("--param-sweep", action="store_true",
+                    help="the paper's Appendix B parameter studies (relaxation factors, smoothing "
+                         "steps) on the workload instead of the benchmark line")
     ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--_seconds", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_its", type=int, default=None, help=argparse.SUPPRESS)
@@ -575,6 +634,10 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.param_sweep:
+        if rank == 0:
+            print(json.dumps(run_param_sweep(args)))
+        return
     if args.workload.startswith("batch"):
         out = run_batched(args, rank, world)
         if rank == 0:
