@@ -32,7 +32,7 @@ UNIT = "trace unknowns/s"
 # C96: dram__bytes_read.sum + dram__bytes_write.sum of the full sweep, captured at full size
 # (a one-pass metric set), mean of two launches.
 TRAFFIC = {
-    "line_sweep:c96:fp64:25b3f241e61d8785": 656224000,
+    "line_sweep:c96:fp64:ed4bc81c8a240f39": 656322688,
 }
 
 
@@ -77,7 +77,9 @@ def solve_bytes(hier, iterations, elem=8):
       per iteration: 2 S applies, 2 preconditioner applications, 15 T of vector updates;
       preconditioner: presmooth from zero (b, factors, out), residual (S, lambda, b, R),
       restriction (R, Gamma, bbar), one V-cycle (per level 42.5 C_l: smoother from zero 5,
-      residual + restriction 9.25, injection 2.25, two smoothers 26; coarsest 5 + 2 x 13),
+      residual + restriction 9.25, injection 2.25, two smoothers 26; coarsest 5 + 2 x 13; the
+      finest level's zero-start sweep runs inside the restriction kernel, so bbar is not
+      read back: minus C),
       prolongation (2 T + C), two full sweeps; the final residual: nnz + 2 T."""
     f = hier.meshes[0]
     L, NH, NZ, T, C = f.nlev, f.n_trace_h, f.n_trace_z, f.n_trace, f.ncell
@@ -88,7 +90,7 @@ def solve_bytes(hier, iterations, elem=8):
     precond = (8 * T + elem * (3 * NZ + NH + T)                 # presmooth from zero
                + elem * (nnz + 2 * T) + 8 * T + tables          # residual
                + elem * (T + 2 * C)                             # restriction with Gamma
-               + vcycle
+               + vcycle - elem * C
                + elem * (2 * T + C)                             # prolongation
                + 2 * sweep_bytes(f, elem))                      # post-smoothing
     per_it = 2 * spmv_bytes(f) + 2 * precond + 8 * 15 * T

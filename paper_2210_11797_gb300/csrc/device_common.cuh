@@ -126,6 +126,22 @@ struct TraceDims {
   int64_t NT;     // all rows
 };
 
+// bbar_K = Gamma_K (P^T R)_K for cell K = (column c, layer k) (Algorithm 2 lines 4-5). P^T
+// weights: 1/2 on interior faces (both neighbours share the facet), 1 on ground and lid; the
+// weights scale exactly, so each FMA rounds as a product-then-add would.
+template <typename T>
+__device__ __forceinline__ T trace_restrict_cell(const T *__restrict__ R, const T *__restrict__ gamma,
+                                                 const int32_t *__restrict__ col_edges, const TraceDims &d,
+                                                 int c, int k, int64_t K) {
+  const int32_t *ce = col_edges + 4 * (int64_t)c;
+  T s = (T)0.5 * (R[(int64_t)__ldg(ce) * d.L + k] + R[(int64_t)__ldg(ce + 1) * d.L + k] +
+                  R[(int64_t)__ldg(ce + 2) * d.L + k] + R[(int64_t)__ldg(ce + 3) * d.L + k]);
+  const int64_t zb = d.NH + (int64_t)c * (d.L + 1) + k;
+  s = fma(k == 0 ? (T)1 : (T)0.5, R[zb], s);
+  s = fma(k == d.L - 1 ? (T)1 : (T)0.5, R[zb + 1], s);
+  return gamma[K] * s;
+}
+
 // acc + sign * (row of S) . x as a chain of fused multiply-adds, one per coefficient: with
 // acc = 0, sign = +1 it is S x; with acc = b, sign = -1 it is the residual b - S x without a
 // separate subtraction (the FP64 issue rate, not HBM, bounds these kernels on GB300). S is

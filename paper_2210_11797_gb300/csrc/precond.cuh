@@ -12,6 +12,11 @@ namespace hmg {
 template <typename T>
 int vcycle(Ctx *c, const T *b, T **x, const T *x0 = nullptr);
 
+// The same V-cycle with b = Gamma P^T R (Algorithm 2 lines 4-5) computed inside its first
+// sweep from the trace residual R [ntrace]; b is also stored in cb [ncell] (in T).
+template <typename T>
+int vcycle_trace(Ctx *c, const T *R, T *cb, T **x);
+
 template <typename T>
 struct Prec;
 template <>

@@ -116,6 +116,20 @@ struct SrcInject {   // x_in = x + P e (injection), then x_out = x_in + omega H_
   __device__ T out(const MGArgs &a, int c, int k, int64_t, T v) const { return xin(a, c, k) + v; }
 };
 
+template <typename T>
+struct SrcTraceRestrict {   // zero start on the finest level, b = Gamma P^T R from the trace residual (also stored)
+  const T *R, *gamma;
+  const int32_t *col_edges;
+  TraceDims d;
+  T *bc;
+  __device__ T r(const MGArgs &, int c, int k, int64_t K) const {
+    const T v = trace_restrict_cell(R, gamma, col_edges, d, c, k, K);
+    bc[K] = v;
+    return v;
+  }
+  __device__ T out(const MGArgs &, int, int, int64_t, T v) const { return v; }
+};
+
 // One column block (columns blk * cpb ..) of the block-Jacobi smoother, by the whole thread
 // block: x_out = src.out(omega H_z^-1 src.r).
 template <typename T, typename Src>
@@ -228,6 +242,18 @@ __global__ void __launch_bounds__(256)
                               const int32_t *__restrict__ children, T *__restrict__ bc, T *__restrict__ x_out) {
   extern __shared__ unsigned char smem_raw[];
   smooth_block_src(a, hw, hl, hcp, SrcRestrict<T>{af, Hf, bf, xf, children, bc}, x_out, blockIdx.x, smem_raw);
+}
+
+// Algorithm 2 lines 4-5 fused with the V-cycle's first, zero-start sweep on the finest level:
+// bc = Gamma P^T R (stored for the later sweeps) and x_out = omega H_z^-1 bc.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    mg_trace_restrict_smooth_kernel(const MGArgs a, const T *__restrict__ hw, const T *__restrict__ hl,
+                                    const T *__restrict__ hcp, const T *__restrict__ R,
+                                    const T *__restrict__ gamma, const int32_t *__restrict__ col_edges,
+                                    const TraceDims d, T *__restrict__ bc, T *__restrict__ x_out) {
+  extern __shared__ unsigned char smem_raw[];
+  smooth_block_src(a, hw, hl, hcp, SrcTraceRestrict<T>{R, gamma, col_edges, d, bc}, x_out, blockIdx.x, smem_raw);
 }
 
 // Injection of the coarse correction e fused with the first post-smoothing sweep:
@@ -437,6 +463,19 @@ static int restrict_smooth(Ctx *c, int l, const T *bf, const T *xf, T *out) {
   return HMG_OK;
 }
 
+// Gamma P^T R into cb and the finest level's first zero-start sweep (into out), in one launch.
+template <typename T>
+static int trace_restrict_smooth(Ctx *c, const T *R, T *cb, T *out) {
+  const Level &lv = c->lv[0];
+  const SmoothShape sh = smooth_shape<T>(c, 0);
+  const TraceDims d{lv.nlev, lv.nth, lv.ntrace};
+  mg_trace_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
+      sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), R, Prec<T>::gamma(c), lv.col_edges, d,
+      cb, out);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
 // x + P e (e from level l+1) and level l's first post-smoothing sweep from it, in one launch.
 template <typename T>
 static int inject_smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
@@ -587,14 +626,27 @@ int vcycle_launches(const Ctx *c) {
   return n;
 }
 
+// With R (the trace residual), b0 = Gamma P^T R is computed into cb inside the first sweep.
 template <typename T>
-int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
+static int vcycle_impl(Ctx *c, const T *b0, T **x_out, const T *x0, const T *R, T *cb) {
   const int nmg = c->nmg, npre = c->opt.mg_npre, npost = c->opt.mg_npost;
   const T *b[kMaxLevels];
   T *x[kMaxLevels];
   int st;
-  b[0] = b0;
-  if ((st = sweeps_from_zero<T>(c, 0, b0, nmg == 1 ? c->opt.mg_ncoarse : npre, &x[0], x0))) return st;
+  const int n0 = nmg == 1 ? c->opt.mg_ncoarse : npre;
+  if (R) {
+    b[0] = cb;
+    T *cur = static_cast<T *>(c->lv[0].vx), *oth = static_cast<T *>(c->lv[0].vy);
+    if ((st = trace_restrict_smooth<T>(c, R, cb, cur))) return st;
+    for (int i = 1; i < n0; ++i) {
+      if ((st = smooth<T, 1>(c, 0, cb, cur, oth))) return st;
+      T *t = cur; cur = oth; oth = t;
+    }
+    x[0] = cur;
+  } else {
+    b[0] = b0;
+    if ((st = sweeps_from_zero<T>(c, 0, b0, n0, &x[0], x0))) return st;
+  }
   // with mg_fused, only the finest level runs step by step; levels >= 1 are one launch
   const bool fused = c->opt.mg_fused && nmg >= 2;
   if (fused) {
@@ -653,8 +705,20 @@ int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
   return HMG_OK;
 }
 
+template <typename T>
+int vcycle(Ctx *c, const T *b0, T **x_out, const T *x0) {
+  return vcycle_impl<T>(c, b0, x_out, x0, nullptr, nullptr);
+}
+
+template <typename T>
+int vcycle_trace(Ctx *c, const T *R, T *cb, T **x_out) {
+  return vcycle_impl<T>(c, nullptr, x_out, nullptr, R, cb);
+}
+
 template int vcycle<double>(Ctx *, const double *, double **, const double *);
 template int vcycle<float>(Ctx *, const float *, float **, const float *);
+template int vcycle_trace<double>(Ctx *, const double *, double *, double **);
+template int vcycle_trace<float>(Ctx *, const float *, float *, float **);
 
 int pressure_vcycle_fp64(Ctx *c, const double *b, double *x) {
   double *res = nullptr;

@@ -308,7 +308,6 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---- bbar = Gamma P^T R (Algorithm 2 lines 4-5) -----------------------------------------
-// P^T weights: 1/2 on interior faces (both neighbours share the facet), 1 on ground and lid.
 template <typename T>
 __global__ void restrict_kernel(const T *__restrict__ R, const T *__restrict__ gamma,
                                 T *__restrict__ bbar, const TraceDims d, int64_t C,
@@ -318,14 +317,7 @@ __global__ void restrict_kernel(const T *__restrict__ R, const T *__restrict__ g
   // 32-bit index arithmetic (the mesh limits keep every row index below 2^31)
   const unsigned Ku = (unsigned)K, Lu = (unsigned)d.L;
   const int c = (int)(Ku / Lu), k = (int)(Ku - (unsigned)c * Lu);
-  const int32_t *ce = col_edges + 4 * (int64_t)c;
-  T s = (T)0.5 * (R[(int64_t)__ldg(ce) * d.L + k] + R[(int64_t)__ldg(ce + 1) * d.L + k] +
-                  R[(int64_t)__ldg(ce + 2) * d.L + k] + R[(int64_t)__ldg(ce + 3) * d.L + k]);
-  const int64_t zb = d.NH + (int64_t)c * (d.L + 1) + k;
-  // the weights 1 and 1/2 scale exactly, so each FMA rounds as the product-then-add did
-  s = fma(k == 0 ? (T)1 : (T)0.5, R[zb], s);
-  s = fma(k == d.L - 1 ? (T)1 : (T)0.5, R[zb + 1], s);
-  bbar[K] = gamma[K] * s;
+  bbar[K] = trace_restrict_cell(R, gamma, col_edges, d, c, k, K);
 }
 
 // ---- lam_out = lam_in + P dPi (Algorithm 2 line 7) ---------------------------------------
@@ -393,14 +385,20 @@ static int two_level(Ctx *c, const double *r, double *z) {
   } else {
     HMG_CUDA(c, cudaMemsetAsync(w1, 0, sizeof(T) * f.ntrace, c->stream));
   }
-  // lines 3-5: R = r - S lambda; bbar = Gamma P^T R
+  // lines 3-5: R = r - S lambda; bbar = Gamma P^T R (with a plain V-cycle as the coarse solve,
+  // the restriction runs inside the V-cycle's first sweep)
   T *cb = static_cast<T *>(c->cb);
+  const int cm = c->opt.coarse;
+  const bool plain_vcycle =
+      !c->collect_x && (cm == HMG_COARSE_VCYCLE ||
+                        ((cm == HMG_COARSE_LEARNED || cm == HMG_COARSE_LEARNED_VCYCLE) && c->coarse_fallback));
   {
-    Prof pr(c, kCompResidual, 2);
+    Prof pr(c, kCompResidual, plain_vcycle ? 1 : 2);
     residual_kernel<T, double><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
         Prec<T>::S(c), r, w1, w2, d, f.edge_stencil, f.col_edges);
-    restrict_kernel<T><<<grid_for(f.ncell, 256), 256, 0, c->stream>>>(w2, Prec<T>::gamma(c), cb, d,
-                                                                      f.ncell, f.col_edges);
+    if (!plain_vcycle)
+      restrict_kernel<T><<<grid_for(f.ncell, 256), 256, 0, c->stream>>>(w2, Prec<T>::gamma(c), cb, d,
+                                                                        f.ncell, f.col_edges);
   }
   HMG_CUDA(c, cudaGetLastError());
   // (training pairs for the learned coarse solve, FP64 path only)
@@ -410,9 +408,10 @@ static int two_level(Ctx *c, const double *r, double *z) {
   T *dpi = nullptr;
   {
     Prof pv(c, kCompVcycle, vcycle_launches(c));
-    const int cm = c->opt.coarse;
     const bool learned = (cm == HMG_COARSE_LEARNED || cm == HMG_COARSE_LEARNED_VCYCLE) && !c->coarse_fallback;
-    if (cm == HMG_COARSE_KRYLOV_EXACT || cm == HMG_COARSE_KRYLOV_APPROX) {
+    if (plain_vcycle) {
+      if ((st = vcycle_trace<T>(c, w2, cb, &dpi))) return st;
+    } else if (cm == HMG_COARSE_KRYLOV_EXACT || cm == HMG_COARSE_KRYLOV_APPROX) {
       if (sizeof(T) != 8) return fail(c, HMG_ERR_INVALID_ARG, "the Krylov coarse solves run in FP64");
       dpi = w3;
       if ((st = coarse_krylov(c, reinterpret_cast<const double *>(cb), reinterpret_cast<double *>(dpi),
