@@ -136,6 +136,14 @@ typedef struct {
                            restriction inside their first sweep and the injection inside their
                            first post-sweep, one launch instead of two (same arithmetic,
                            bitwise the same result); 0: never. Must be >= 0 */
+  int32_t async_stats;  /* 0 (default): hmg_solve synchronises once, to fill its stats.
+                           1: a graph-launched BiCGStab solve (graph = 1, profile = 0, no
+                           Krylov coarse solve) is only enqueued on the context's stream;
+                           hmg_solve returns HMG_OK at once with stats->status set to
+                           HMG_ERR_NOT_READY (nothing else filled), and hmg_solve_stats_get
+                           gives the stats and the stop reason later.
+                           Host-driven and FGMRES solves, hmg_solve_host, hmg_solve_mixed
+                           and batched solves stay synchronous */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
@@ -215,6 +223,13 @@ int hmg_trace_rhs(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *B)
  * stop reason (HMG_OK when converged). */
 int hmg_solve(hmg_ctx *ctx, const double *Rub, const double *Rpi, double *lambda,
               hmg_solve_stats *stats);
+
+/* With async_stats = 1: waits for the last enqueued solve of this context (its end event,
+ * not the whole stream), fills stats (host, may be NULL) and returns that solve's stop
+ * reason. HMG_ERR_NOT_READY when no asynchronous solve is pending. The results of an
+ * enqueued solve live in pinned host buffers of the context: a second hmg_solve before this
+ * call replaces them, so only the latest solve's stats can be read. */
+int hmg_solve_stats_get(hmg_ctx *ctx, hmg_solve_stats *stats);
 
 /* n independent solves (a batch of contexts, all assembled, on the current device, each with
  * its own mesh and options) in ONE CUDA graph launch: one branch per context, each branch

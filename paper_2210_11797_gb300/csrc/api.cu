@@ -51,6 +51,7 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.warm_start != 0 && o.warm_start != 1) return bad("warm_start must be 0 or 1");
   if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
   if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
+  if (o.async_stats != 0 && o.async_stats != 1) return bad("async_stats must be 0 or 1");
   return HMG_OK;
 }
 
@@ -97,6 +98,11 @@ static void free_all(Ctx *c) {
   c->scal_host = nullptr;
   if (c->state_host) cudaFreeHost(c->state_host);
   c->state_host = nullptr;
+  if (c->hist_host) cudaFreeHost(c->hist_host);
+  c->hist_host = nullptr;
+  if (c->as_e0) cudaEventDestroy(c->as_e0);
+  if (c->as_e1) cudaEventDestroy(c->as_e1);
+  c->as_e0 = c->as_e1 = nullptr;
 }
 
 }  // namespace hmg
@@ -147,6 +153,9 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaMallocHost(&c->scal_host, sizeof(double) * Scal::N);
   if (e == cudaSuccess) e = cudaMallocHost(&c->state_host, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->hist_host, sizeof(double) * HMG_MAX_HISTORY);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->as_e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->as_e1);
   if (e != cudaSuccess) {
     free_all(c);
     delete c;
@@ -433,7 +442,12 @@ int hmg_solve(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, 
   if (st) return st;
   if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
   if ((st = reject_schur(c))) return st;
-  return krylov_solve(c, Rub, Rpi, lambda, stats);
+  return krylov_solve(c, Rub, Rpi, lambda, stats, true);
+}
+
+int hmg_solve_stats_get(hmg_ctx *c, hmg_solve_stats *stats) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  return solve_stats_get(c, stats);
 }
 
 int hmg_solve_mixed(hmg_ctx *c, const double *Rub, const double *Rpi, double *u, double *pi, hmg_solve_stats *stats) {
@@ -442,7 +456,7 @@ int hmg_solve_mixed(hmg_ctx *c, const double *Rub, const double *Rpi, double *u,
   if (!Rub || !Rpi || !u || !pi) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
   if (!mixed_system(c) || !c->have_mixed)
     return fail(c, HMG_ERR_NOT_READY, "configuration 1 needs precond = HMG_PRECOND_SCHUR before hmg_assemble_trace");
-  const int solve_st = krylov_solve(c, Rub, Rpi, c->mx_x, stats);
+  const int solve_st = krylov_solve(c, Rub, Rpi, c->mx_x, stats, false);
   if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
       solve_st != HMG_ERR_NONFINITE && solve_st != HMG_ERR_TIMEOUT)
     return solve_st;
@@ -471,7 +485,7 @@ int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lam
   HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * f.ncell, cudaMemcpyHostToDevice, c->stream));
   if (c->opt.warm_start)   // the initial lambda comes from the host buffer too
     HMG_CUDA(c, cudaMemcpyAsync(dlam, lambda, sizeof(double) * f.ntrace, cudaMemcpyHostToDevice, c->stream));
-  const int solve_st = krylov_solve(c, dRub, dRpi, dlam, stats);
+  const int solve_st = krylov_solve(c, dRub, dRpi, dlam, stats, false);
   if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
       solve_st != HMG_ERR_NONFINITE)
     return solve_st;
@@ -686,7 +700,7 @@ int hmg_collect_coarse_pairs(hmg_ctx *c, const double *Rub, const double *Rpi, d
   c->collect_t = t_out;
   c->collect_max = max_pairs;
   c->collect_n = 0;
-  st = krylov_solve(c, Rub, Rpi, lambda, stats);
+  st = krylov_solve(c, Rub, Rpi, lambda, stats, false);
   *n_out = c->collect_n;
   c->collect_x = c->collect_t = nullptr;
   c->collect_max = c->collect_n = 0;

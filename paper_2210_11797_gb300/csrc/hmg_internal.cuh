@@ -122,6 +122,9 @@ struct Ctx {
   int *state = nullptr;
   double *hist = nullptr;
   int *state_host = nullptr;   // pinned [4]
+  double *hist_host = nullptr; // pinned [HMG_MAX_HISTORY]
+  cudaEvent_t as_e0 = nullptr, as_e1 = nullptr;   // start / end of an enqueued (async) solve
+  bool stats_pending = false;  // an async solve's results are on their way to the host
   // whole-solve CUDA graph (B_lambda, a WHILE node over BiCGStab iterations, final residual)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -249,8 +252,11 @@ int pressure_vcycle_fp64(Ctx *c, const double *b, double *x);
 int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
 
 // ---- Krylov (krylov.cu) ------------------------------------------------------------------
+// allow_async: with opt.async_stats, a graph-launched solve is only enqueued (stats later
+// through solve_stats_get)
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
-                 hmg_solve_stats *st);
+                 hmg_solve_stats *st, bool allow_async);
+int solve_stats_get(Ctx *c, hmg_solve_stats *st);
 int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
 // sums the per-block partials of slots s0 (and s1 >= 0) into scal (fixed order)
 int launch_finalize(Ctx *c, int nblocks, int s0, int s1);

@@ -404,6 +404,8 @@ static bool same_key(const Ctx::GraphKey &k, const double *Rub, const double *Rp
 }
 
 void drop_graph(Ctx *c) {
+  // an enqueued (async_stats) solve may still be running the graph: let it finish first
+  if (c->graph_exec && c->stats_pending) cudaEventSynchronize(c->as_e1);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
@@ -434,11 +436,16 @@ static int status_message(Ctx *c, int status) {
 }
 
 // Copies the loop state, history and scalars to the host (stream-ordered) and fills stats.
-static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
+// Enqueues the copies of the loop state, history and scalars into the pinned host buffers.
+static int enqueue_results(Ctx *c) {
   HMG_CUDA(c, cudaMemcpyAsync(c->scal_host, c->scal, sizeof(double) * Scal::N, cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaMemcpyAsync(c->state_host, c->state, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
-  if (st) HMG_CUDA(c, cudaMemcpyAsync(st->history, c->hist, sizeof(double) * HMG_MAX_HISTORY, cudaMemcpyDeviceToHost, c->stream));
-  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(c->hist_host, c->hist, sizeof(double) * HMG_MAX_HISTORY, cudaMemcpyDeviceToHost, c->stream));
+  return HMG_OK;
+}
+
+// Stats from the host buffers (the copies have completed) and the solve's stop reason.
+static int fill_stats(Ctx *c, hmg_solve_stats *st, float ms) {
   const int it = c->state_host[kIt];
   int status = c->state_host[kStatus];
   if (c->state_host[kWaitFlag]) {   // a bounded device-side wait ran out during the solve
@@ -448,6 +455,7 @@ static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
   if (st) {
     const double bb = c->scal_host[Scal::BB];
     const double bnorm = std::sqrt(bb);
+    std::memcpy(st->history, c->hist_host, sizeof(double) * HMG_MAX_HISTORY);
     st->status = status;
     st->iterations = it;
     st->n_history = it + 1 < HMG_MAX_HISTORY ? it + 1 : HMG_MAX_HISTORY;
@@ -467,11 +475,32 @@ static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
   return status_message(c, status);
 }
 
-int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st) {
+static int collect(Ctx *c, hmg_solve_stats *st, float ms) {
+  int s;
+  if ((s = enqueue_results(c))) return s;
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return fill_stats(c, st, ms);
+}
+
+int solve_stats_get(Ctx *c, hmg_solve_stats *st) {
+  if (!c->stats_pending) return fail(c, HMG_ERR_NOT_READY, "no asynchronous solve is pending");
+  c->stats_pending = false;
+  HMG_CUDA(c, cudaEventSynchronize(c->as_e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->as_e0, c->as_e1);
+  c->marks.clear();   // no component timers in a graph-launched solve
+  return fill_stats(c, st, ms);
+}
+
+int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st,
+                 bool allow_async) {
   c->marks.clear();
   c->ev_next = 0;
   c->coarse_fallback = false;
-  if (c->opt.krylov == HMG_KRYLOV_FGMRES) return fgmres_solve(c, Rub, Rpi, lambda, st);
+  if (c->opt.krylov == HMG_KRYLOV_FGMRES) {
+    c->stats_pending = false;   // its results replace an uncollected enqueued solve's
+    return fgmres_solve(c, Rub, Rpi, lambda, st);
+  }
   SolveTimer timer;
   int s;
   if ((s = timer.start(c))) return s;
@@ -479,6 +508,16 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
                            (c->opt.coarse == HMG_COARSE_KRYLOV_EXACT || c->opt.coarse == HMG_COARSE_KRYLOV_APPROX);
   if (c->opt.graph && !c->opt.profile && !c->collect_x && !host_coarse) {
     if ((s = ensure_solve_graph(c, Rub, Rpi, lambda))) return s;
+    if (allow_async && c->opt.async_stats) {
+      // enqueue only: the results travel to the pinned buffers behind the solve
+      HMG_CUDA(c, cudaEventRecord(c->as_e0, c->stream));
+      HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+      HMG_CUDA(c, cudaEventRecord(c->as_e1, c->stream));
+      if ((s = enqueue_results(c))) return s;
+      c->stats_pending = true;
+      if (st) st->status = HMG_ERR_NOT_READY;   // the stats come from hmg_solve_stats_get
+      return HMG_OK;
+    }
     HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
   } else {
     cudaGraphConditionalHandle none = 0;
@@ -493,6 +532,7 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
   }
   float ms = 0.f;
   if ((s = timer.stop(c, &ms))) return s;
+  c->stats_pending = false;   // these results replace an uncollected enqueued solve's
   return collect(c, st, ms);
 }
 
@@ -513,6 +553,10 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
     c->marks.clear();
     c->ev_next = 0;
     c->coarse_fallback = false;
+    if (c->stats_pending) {   // an enqueued solve of this context runs on its own stream
+      cudaEventSynchronize(c->as_e1);
+      c->stats_pending = false;
+    }
     s = add_solve_branch(c, g, Rub[i], Rpi[i], lambda[i]);
     if (s && c != c0) c0->err = c->err;
   }

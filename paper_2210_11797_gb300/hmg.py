@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
                 ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
                 ("stall_ratio", C.c_double), ("mg_fused", C.c_int32), ("warm_start", C.c_int32),
-                ("mg_fuse_cells", C.c_int32)]
+                ("mg_fuse_cells", C.c_int32), ("async_stats", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -94,6 +94,7 @@ _SIGS = {
     "hmg_last_error": ([_P], C.c_char_p),
     "hmg_trace_rhs": ([_P, _P, _P, _P], C.c_int),
     "hmg_solve": ([_P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
+    "hmg_solve_stats_get": ([_P, C.POINTER(SolveStats)], C.c_int),
     "hmg_solve_host": ([_P, _P, _P, _P, C.POINTER(SolveStats)], C.c_int),
     "hmg_reconstruct": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "hmg_apply_trace": ([_P, _P, _P], C.c_int),
@@ -275,7 +276,17 @@ class Solver:
                              self._dev(lam, self.ntrace, "lambda"), C.byref(st))
         if check:
             _check(self.ctx, rc)
+        if rc == HMG_OK and st.status == 3:   # async_stats: enqueued, stats from solve_stats()
+            return lam, None
         return lam, st.as_dict()
+
+    def solve_stats(self, check=True):
+        """Stats of the last solve enqueued with async_stats = 1 (waits for it)."""
+        st = SolveStats()
+        rc = lib().hmg_solve_stats_get(self.ctx, C.byref(st))
+        if check:
+            _check(self.ctx, rc)
+        return st.as_dict()
 
     def solve_mixed(self, Rub, Rpi, check=True):
         """Configuration 1: returns (u [ntrace], Pi [ncell], stats)."""

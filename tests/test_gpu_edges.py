@@ -159,3 +159,39 @@ def test_warm_start_resumes_a_solve(krylov):
     again, st_again = gpu.solve(Rub, Rpi, warm.clone())
     assert st_again["iterations"] <= 1
     gpu.close()
+
+
+def test_async_stats_enqueue_the_solve_and_report_later():
+    """async_stats = 1: hmg_solve only enqueues the graph-launched solve; hmg_solve_stats_get
+    then gives the same stats as a synchronous solve (same lambda, iterations and history,
+    bit for bit); nothing pending is NOT_READY; the host-buffer and host-driven solves stay
+    synchronous."""
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w = I.cubed_sphere(12, 10, seed=3)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-8)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam_s, st_s = gpu.solve(Rub, Rpi)
+    gpu.set_options(async_stats=1)
+    lam_a = torch.empty_like(lam_s)
+    lam_a, st = gpu.solve(Rub, Rpi, lam_a)
+    assert st is None
+    st_a = gpu.solve_stats()
+    assert st_a["status"] == "ok" and st_a["iterations"] == st_s["iterations"]
+    np.testing.assert_array_equal(st_a["history"], st_s["history"])
+    assert st_a["true_rel_residual"] == st_s["true_rel_residual"] and st_a["solve_ms"] > 0
+    np.testing.assert_array_equal(_np(lam_a), _np(lam_s))
+    with pytest.raises(HmgError):
+        gpu.solve_stats()
+    # two enqueued solves: the stats are the second's
+    gpu.set_options(tol=1e-4)
+    lam_a, st = gpu.solve(Rub, Rpi, lam_a)
+    gpu.set_options(tol=1e-8)
+    lam_a, st = gpu.solve(Rub, Rpi, lam_a)
+    assert st is None and gpu.solve_stats()["iterations"] == st_s["iterations"]
+    # host buffers and the host-driven loop ignore async_stats
+    lam_h, st_h = gpu.solve_host(w.Rub.ravel(), w.Rpi)
+    assert st_h["iterations"] == st_s["iterations"]
+    gpu.set_options(graph=0)
+    _l, st_g = gpu.solve(Rub, Rpi)
+    assert st_g is not None and st_g["iterations"] == st_s["iterations"]
+    gpu.close()
