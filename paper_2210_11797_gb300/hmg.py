@@ -270,6 +270,8 @@ class Solver:
         return B
 
     def solve(self, Rub, Rpi, lam=None, check=True):
+        """(lambda, stats dict). With async_stats = 1 a graph-launched solve is only enqueued:
+        stats is None and solve_stats() gives them later."""
         lam = self._empty(self.ntrace) if lam is None else lam
         st = SolveStats()
         rc = lib().hmg_solve(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"), self._dev(Rpi, self.ncell, "Rpi"),
