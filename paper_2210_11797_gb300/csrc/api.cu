@@ -570,6 +570,7 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
 int hmg_autotune(hmg_ctx *c) {
   int st = ready(c);
   if (st) return st;
+  drop_graph(c);   // captured launches carry the old shapes
   return finish(c, autotune(c));
 }
 

@@ -307,6 +307,8 @@ int autotune(Ctx *c);
 // Sweep / smoother launches with explicit columns and threads per block (autotuner).
 int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms);
 int time_mg_cpb(Ctx *c, int level, int cpb, int threads, int fp32, float *ms);
+// Best-of-three average time of one whole V-cycle (FP64 or FP32) with the current shapes.
+int time_vcycle(Ctx *c, int fp32, float *ms);
 // Columns per block of the pressure smoother: at most 64, and its three shared-memory arrays
 // (column stride nlev rounded up to odd) within the default 48 KB (FP64).
 inline int mg_cpb_limit(int nlev) {

@@ -512,8 +512,10 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
       // enqueue only: the results travel to the pinned buffers behind the solve
       HMG_CUDA(c, cudaEventRecord(c->as_e0, c->stream));
       HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
-      HMG_CUDA(c, cudaEventRecord(c->as_e1, c->stream));
       if ((s = enqueue_results(c))) return s;
+      // the end event follows the copies: once it completes, the host buffers hold this solve's
+      // results (solve_ms includes the few-microsecond copies)
+      HMG_CUDA(c, cudaEventRecord(c->as_e1, c->stream));
       c->stats_pending = true;
       if (st) st->status = HMG_ERR_NOT_READY;   // the stats come from hmg_solve_stats_get
       return HMG_OK;

@@ -715,6 +715,35 @@ int vcycle_trace(Ctx *c, const T *R, T *cb, T **x_out) {
   return vcycle_impl<T>(c, nullptr, x_out, nullptr, R, cb);
 }
 
+template <typename T>
+static int time_vcycle_t(Ctx *c, float *ms) {
+  T *b = static_cast<T *>(c->lv[0].vb);   // level 0's own b vector is free outside a solve
+  HMG_CUDA(c, cudaMemsetAsync(b, 0, sizeof(T) * c->lv[0].ncell, c->stream));
+  T *x = nullptr;
+  int st = vcycle<T>(c, b, &x);
+  cudaEvent_t e0, e1;
+  HMG_CUDA(c, cudaEventCreate(&e0));
+  HMG_CUDA(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3 && !st; ++rep) {
+    HMG_CUDA(c, cudaEventRecord(e0, c->stream));
+    for (int i = 0; i < 10 && !st; ++i) st = vcycle<T>(c, b, &x);
+    HMG_CUDA(c, cudaEventRecord(e1, c->stream));
+    HMG_CUDA(c, cudaEventSynchronize(e1));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (t < best) best = t;
+  }
+  *ms = best / 10.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+int time_vcycle(Ctx *c, int fp32, float *ms) {
+  return fp32 ? time_vcycle_t<float>(c, ms) : time_vcycle_t<double>(c, ms);
+}
+
 template int vcycle<double>(Ctx *, const double *, double **, const double *);
 template int vcycle<float>(Ctx *, const float *, float **, const float *);
 template int vcycle_trace<double>(Ctx *, const double *, double *, double **);

@@ -607,6 +607,26 @@ int autotune(Ctx *c) {
         }
       if (!st) { c->tune_mg_cpb[pm][l] = mbest; c->tune_mg_threads[pm][l] = mbest_t; }
     }
+    // then one coordinate-descent pass over the levels, coarsest first, timing whole
+    // V-cycles: the fused restriction / injection sweeps of the small levels take the level's
+    // shape too, and a shape that suits the plain smoother can starve them of blocks
+    for (int l = c->nmg - 1; l >= 0 && !st; --l) {
+      const int mmax = mg_cpb_limit(c->lv[l].nlev);
+      int bc = c->tune_mg_cpb[pm][l], bt = c->tune_mg_threads[pm][l];
+      float bms = 1e30f;
+      if ((st = time_vcycle(c, pm, &bms))) break;
+      for (int cand : {32, 64, 16, 8, 4, 2, 1})
+        for (int thr : {256, 128}) {
+          if (cand > mmax || st || (cand == bc && thr == bt)) continue;
+          c->tune_mg_cpb[pm][l] = cand;
+          c->tune_mg_threads[pm][l] = thr;
+          float ms = 0.f;
+          if ((st = time_vcycle(c, pm, &ms))) break;
+          if (ms < 0.98f * bms) { bms = ms; bc = cand; bt = thr; }   // 2%: beyond the timing noise
+        }
+      c->tune_mg_cpb[pm][l] = bc;
+      c->tune_mg_threads[pm][l] = bt;
+    }
   }
   c->opt.profile = profile;
   return st;
