@@ -485,13 +485,8 @@ int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lam
   HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * f.ncell, cudaMemcpyHostToDevice, c->stream));
   if (c->opt.warm_start)   // the initial lambda comes from the host buffer too
     HMG_CUDA(c, cudaMemcpyAsync(dlam, lambda, sizeof(double) * f.ntrace, cudaMemcpyHostToDevice, c->stream));
-  const int solve_st = krylov_solve(c, dRub, dRpi, dlam, stats, false);
-  if (solve_st != HMG_OK && solve_st != HMG_ERR_NOT_CONVERGED && solve_st != HMG_ERR_BREAKDOWN &&
-      solve_st != HMG_ERR_NONFINITE)
-    return solve_st;
-  HMG_CUDA(c, cudaMemcpyAsync(lambda, dlam, sizeof(double) * f.ntrace, cudaMemcpyDeviceToHost, c->stream));
-  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  return solve_st;
+  // lambda comes back to the host behind the solve, under the same synchronisation
+  return krylov_solve(c, dRub, dRpi, dlam, stats, false, lambda);
 }
 
 int hmg_reconstruct(hmg_ctx *c, const double *lambda, const double *Rub, const double *Rpi, double *ub, double *pi) {

@@ -254,8 +254,10 @@ int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
 // ---- Krylov (krylov.cu) ------------------------------------------------------------------
 // allow_async: with opt.async_stats, a graph-launched solve is only enqueued (stats later
 // through solve_stats_get)
+// host_out (may be null): lambda is also copied into this host buffer, enqueued right behind
+// the solve so that one synchronisation covers the solve, the copy and the stats.
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda,
-                 hmg_solve_stats *st, bool allow_async);
+                 hmg_solve_stats *st, bool allow_async, double *host_out = nullptr);
 int solve_stats_get(Ctx *c, hmg_solve_stats *st);
 int launch_dot(Ctx *c, const double *a, const double *b, int64_t n, int slot);
 // sums the per-block partials of slots s0 (and s1 >= 0) into scal (fixed order)

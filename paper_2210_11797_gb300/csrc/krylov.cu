@@ -22,14 +22,16 @@ namespace hmg {
 
 // Two CUDA events around a solve on the context's stream, destroyed on every return path.
 struct SolveTimer {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   ~SolveTimer() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
   }
   int start(Ctx *c) {
     HMG_CUDA(c, cudaEventCreate(&e0));
     HMG_CUDA(c, cudaEventCreate(&e1));
+    HMG_CUDA(c, cudaEventCreate(&e2));
     HMG_CUDA(c, cudaEventRecord(e0, c->stream));
     return HMG_OK;
   }
@@ -492,14 +494,29 @@ int solve_stats_get(Ctx *c, hmg_solve_stats *st) {
   return fill_stats(c, st, ms);
 }
 
+// A stop reason of the iteration itself (lambda is then the last iterate), not a failure.
+static bool solve_outcome(int r) {
+  return r == HMG_OK || r == HMG_ERR_NOT_CONVERGED || r == HMG_ERR_BREAKDOWN || r == HMG_ERR_NONFINITE ||
+         r == HMG_ERR_TIMEOUT;
+}
+
+static int copy_to_host(Ctx *c, double *host_out, const double *lambda) {
+  HMG_CUDA(c, cudaMemcpyAsync(host_out, lambda, sizeof(double) * sys_n(c), cudaMemcpyDeviceToHost, c->stream));
+  HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HMG_OK;
+}
+
 int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, hmg_solve_stats *st,
-                 bool allow_async) {
+                 bool allow_async, double *host_out) {
   c->marks.clear();
   c->ev_next = 0;
   c->coarse_fallback = false;
   if (c->opt.krylov == HMG_KRYLOV_FGMRES) {
     c->stats_pending = false;   // its results replace an uncollected enqueued solve's
-    return fgmres_solve(c, Rub, Rpi, lambda, st);
+    const int r = fgmres_solve(c, Rub, Rpi, lambda, st);
+    int s2;
+    if (host_out && solve_outcome(r) && (s2 = copy_to_host(c, host_out, lambda))) return s2;
+    return r;
   }
   SolveTimer timer;
   int s;
@@ -521,6 +538,17 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
       return HMG_OK;
     }
     HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    // one synchronisation: the solve's end, the copy of lambda to the host, the results
+    HMG_CUDA(c, cudaEventRecord(timer.e1, c->stream));
+    if (host_out)
+      HMG_CUDA(c, cudaMemcpyAsync(host_out, lambda, sizeof(double) * sys_n(c), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = enqueue_results(c))) return s;
+    HMG_CUDA(c, cudaEventRecord(timer.e2, c->stream));
+    HMG_CUDA(c, cudaEventSynchronize(timer.e2));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, timer.e0, timer.e1);
+    c->stats_pending = false;   // these results replace an uncollected enqueued solve's
+    return fill_stats(c, st, ms);
   } else {
     cudaGraphConditionalHandle none = 0;
     if ((s = solve_head(c, Rub, Rpi, lambda, false, none))) return s;
@@ -535,7 +563,9 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
   float ms = 0.f;
   if ((s = timer.stop(c, &ms))) return s;
   c->stats_pending = false;   // these results replace an uncollected enqueued solve's
-  return collect(c, st, ms);
+  const int r = collect(c, st, ms);
+  if (host_out && solve_outcome(r) && (s = copy_to_host(c, host_out, lambda))) return s;
+  return r;
 }
 
 // All contexts on one device; each branch of the graph is one context's whole solve, and
