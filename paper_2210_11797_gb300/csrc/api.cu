@@ -103,6 +103,11 @@ static void free_all(Ctx *c) {
   if (c->as_e0) cudaEventDestroy(c->as_e0);
   if (c->as_e1) cudaEventDestroy(c->as_e1);
   c->as_e0 = c->as_e1 = nullptr;
+  if (c->loop_done) cudaEventDestroy(c->loop_done);
+  if (c->copy_done) cudaEventDestroy(c->copy_done);
+  c->loop_done = c->copy_done = nullptr;
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
 }
 
 }  // namespace hmg
@@ -156,6 +161,9 @@ int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaMallocHost(&c->hist_host, sizeof(double) * HMG_MAX_HISTORY);
   if (e == cudaSuccess) e = cudaEventCreate(&c->as_e0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->as_e1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->loop_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_all(c);
     delete c;

@@ -124,6 +124,9 @@ struct Ctx {
   int *state_host = nullptr;   // pinned [4]
   double *hist_host = nullptr; // pinned [HMG_MAX_HISTORY]
   cudaEvent_t as_e0 = nullptr, as_e1 = nullptr;   // start / end of an enqueued (async) solve
+  cudaEvent_t loop_done = nullptr;   // recorded by the solve graph when its Krylov loop ends
+  cudaEvent_t copy_done = nullptr;   // end of the copy of lambda to the host
+  cudaStream_t copy_stream = nullptr;   // that copy, overlapping the final residual
   bool stats_pending = false;  // an async solve's results are on their way to the host
   // whole-solve CUDA graph (B_lambda, a WHILE node over BiCGStab iterations, final residual)
   cudaStream_t cap_stream = nullptr;

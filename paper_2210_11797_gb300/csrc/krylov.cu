@@ -389,6 +389,11 @@ static int add_solve_branch(Ctx *c, cudaGraph_t g, const double *Rub, const doub
       }
       if (s2) cudaStreamDestroy(s2);
       c->stream = c->cap_stream;
+      // an event node after the loop: a copy of lambda to the host can overlap the tail
+      if (!st) {
+        e = cudaEventRecordWithFlags(c->loop_done, c->cap_stream, cudaEventRecordExternal);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "loop-end event node");
+      }
       if (!st) st = solve_tail(c, x);
     }
   }
@@ -538,10 +543,16 @@ int krylov_solve(Ctx *c, const double *Rub, const double *Rpi, double *lambda, h
       return HMG_OK;
     }
     HMG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
-    // one synchronisation: the solve's end, the copy of lambda to the host, the results
+    // one synchronisation: the solve's end, the copy of lambda to the host (on its own stream,
+    // from the end of the Krylov loop, so it overlaps the final residual), the results
     HMG_CUDA(c, cudaEventRecord(timer.e1, c->stream));
-    if (host_out)
-      HMG_CUDA(c, cudaMemcpyAsync(host_out, lambda, sizeof(double) * sys_n(c), cudaMemcpyDeviceToHost, c->stream));
+    if (host_out) {
+      HMG_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->loop_done, 0));
+      HMG_CUDA(c, cudaMemcpyAsync(host_out, lambda, sizeof(double) * sys_n(c), cudaMemcpyDeviceToHost,
+                                  c->copy_stream));
+      HMG_CUDA(c, cudaEventRecord(c->copy_done, c->copy_stream));
+      HMG_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_done, 0));
+    }
     if ((s = enqueue_results(c))) return s;
     HMG_CUDA(c, cudaEventRecord(timer.e2, c->stream));
     HMG_CUDA(c, cudaEventSynchronize(timer.e2));
