@@ -195,3 +195,24 @@ def test_async_stats_enqueue_the_solve_and_report_later():
     _l, st_g = gpu.solve(Rub, Rpi)
     assert st_g is not None and st_g["iterations"] == st_s["iterations"]
     gpu.close()
+
+
+def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
+    """Launch shapes change no arithmetic: a solve captured before hmg_autotune and the solve
+    re-captured after it (autotune drops the old graph) give the same lambda bit for bit."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(16, 12, seed=12)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-8)
+    Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam0, st0 = gpu.solve(Rub, Rpi)
+    before = gpu.launch_shapes()
+    gpu.autotune()
+    lam1, st1 = gpu.solve(Rub, Rpi, torch.empty_like(lam0))
+    assert st1["iterations"] == st0["iterations"]
+    np.testing.assert_array_equal(_np(lam1), _np(lam0))
+    sw, mg = gpu.launch_shapes()
+    assert sw[0] > 0 and all(c > 0 for c, _t in mg)      # tuned shapes are recorded
+    gpu.set_launch_shapes(*before)                          # and can be reset
+    lam2, _st = gpu.solve(Rub, Rpi, torch.empty_like(lam0))
+    np.testing.assert_array_equal(_np(lam2), _np(lam0))
+    gpu.close()
