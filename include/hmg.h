@@ -58,7 +58,7 @@ typedef struct hmg_ctx hmg_ctx; /* opaque, owned by the library */
 typedef struct {
   int32_t geometry;          /* 0: planar, corners are (x, y, 0); 1: sphere, corners are
                                 unit vectors and a vertex at height z is corner*(radius+z) */
-  int32_t ncol, nlev, nedge; /* columns, layers, vertical edges (faces between columns) */
+  int32_t ncol, nlev, nedge; /* columns, layers (1..2045), vertical edges (faces between columns) */
   double radius;             /* sphere radius (geometry 1) */
   const double *corners;     /* [ncol][4][3] column corners, counter-clockwise from above */
   const double *z_levels;    /* [nlev+1] level heights, strictly increasing */

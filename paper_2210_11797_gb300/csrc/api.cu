@@ -219,6 +219,8 @@ int hmg_set_mesh(hmg_ctx *c, int32_t nmg, const hmg_mesh_level *levels) {
       return fail(c, HMG_ERR_INVALID_ARG, buf);
     };
     if (m.ncol < 1 || m.nlev < 1 || m.nedge < 1) return bad("empty mesh");
+    // one column's three Thomas arrays (FP64, L + 1 rows) must fit a block's 48 KB of shared memory
+    if (m.nlev > kMaxLayers) return bad("more than 2045 layers");
     if (m.nlev != L) return bad("every level needs the same nlev");
     if (m.geometry != 0 && m.geometry != 1) return bad("geometry must be 0 or 1");
     if (m.geometry == 1 && !(m.radius > 0.0)) return bad("radius must be > 0");

@@ -216,3 +216,23 @@ def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
     lam2, _st = gpu.solve(Rub, Rpi, torch.empty_like(lam0))
     np.testing.assert_array_equal(_np(lam2), _np(lam0))
     gpu.close()
+
+
+def test_tallest_columns_solve_and_one_more_layer_is_rejected():
+    """The layer limit (2045: one column's three Thomas arrays fill a block's 48 KB of shared
+    memory): a 4 x 4 x 2045 Helmholtz box solves (one column per block in the sweep and the
+    smoother; the oracle's S certifies the residual), and 2046 layers are refused before
+    anything runs on the device."""
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w = I.planar_helmholtz(n=4, nlev=2045, top=100.0, nmg=2, seed=9, tol=1e-8)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-8, max_iter=400)
+    lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
+    assert st["status"] == "ok" and st["true_rel_residual"] <= 1.05e-8
+    ora = HybridSolver(w.hier, w.coeffs)
+    B = ora.rhs(w.Rub, w.Rpi)
+    assert np.linalg.norm(B - ora.S @ _np(lam)) / np.linalg.norm(B) <= 1.05e-8
+    gpu.close()
+    h = I.planar_hierarchy(4, 2046, 1.0, I.uniform_levels(2046, 100.0), 1)
+    with pytest.raises(HmgError) as e:
+        Solver(h, I.Coefficients([I.unit_background(h.meshes[0])], preset=1, sigma=1.0))
+    assert e.value.status == 1
