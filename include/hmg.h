@@ -144,11 +144,6 @@ typedef struct {
                            gives the stats and the stop reason later.
                            Host-driven and FGMRES solves, hmg_solve_host, hmg_solve_mixed
                            and batched solves stay synchronous */
-  int32_t mg_twisted;   /* the pressure smoother's column solves: 0: Thomas, one lane per column;
-                           1: twisted elimination, two lanes per column, each running half the
-                           serial chain (the same FP64 work, rounded differently); 2 (default):
-                           Thomas until hmg_autotune picks the faster of the two on whole
-                           V-cycles */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */

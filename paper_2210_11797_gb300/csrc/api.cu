@@ -52,7 +52,6 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
   if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
   if (o.async_stats != 0 && o.async_stats != 1) return bad("async_stats must be 0 or 1");
-  if (o.mg_twisted < 0 || o.mg_twisted > 2) return bad("mg_twisted must be 0, 1 or 2");
   return HMG_OK;
 }
 
@@ -141,7 +140,6 @@ int hmg_default_options(hmg_options *o) {
   o->stall_ratio = 0.9;
   o->mg_fused = 0;
   o->mg_fuse_cells = 1 << 18;
-  o->mg_twisted = 2;
   return HMG_OK;
 }
 
@@ -198,8 +196,7 @@ int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
   c->opt = *opt;
   if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32)
     c->assembled = false;  // the FP32 copies are built by hmg_assemble_trace
-  if (c->assembled && (c->opt.omega != c->factor_omega || c->opt.mg_omega != c->factor_mg_omega ||
-                       mg_twisted(c) != c->factor_twisted)) {
+  if (c->assembled && (c->opt.omega != c->factor_omega || c->opt.mg_omega != c->factor_mg_omega)) {
     HMG_CUDA(c, cudaSetDevice(c->device));
     if ((st = build_factors(c))) return st;
     HMG_CUDA(c, cudaStreamSynchronize(c->stream));

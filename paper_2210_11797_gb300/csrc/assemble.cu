@@ -442,34 +442,14 @@ __global__ void pressure_rows_kernel(const HArgs a, const double *__restrict__ r
 // relaxation omega folded in, in the form of trace_factor_kernel: w = omega / p_k,
 // l = sub / p_k, cp = sup / p_k.
 __global__ void pressure_factor_kernel(const HArgs a, const double *__restrict__ H, double omega,
-                                       int twisted, double *__restrict__ w_out, double *__restrict__ l_out,
+                                       double *__restrict__ w_out, double *__restrict__ l_out,
                                        double *__restrict__ cp_out) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= a.ncol) return;
-  if (!twisted) {   // one-lane Thomas: w = omega / pivot, l = sub / pivot, cp = sup / pivot
-    const int64_t C = a.ncell;
-    double cp = 0.0;
-    for (int k = 0; k < a.L; ++k) {
-      const int64_t K = c * a.L + k;
-      const double sub = k > 0 ? H[5 * C + K] : 0.0;
-      const double inv = 1.0 / (H[K] - sub * cp);
-      cp = H[6 * C + K] * inv;
-      w_out[K] = omega * inv;
-      l_out[K] = sub * inv;
-      cp_out[K] = cp;
-    }
-    return;
-  }
-  // Twisted (two-sided) elimination of the column's tridiagonal H_z: rows 0..m-1 from the top,
-  // rows L-1..m+1 from the bottom, row m last, so that the smoother runs the two halves on two
-  // lanes (half the serial chain). Per row: w = omega / pivot, l = elimination coefficient,
-  // u = back-substitution coefficient; row m keeps a_m / p_m in l and c_m / p_m in u.
   const int64_t C = a.ncell;
-  const int L = a.L, m = L >> 1;
-  const int64_t K0 = c * L;
-  double cp = 0.0;   // c_{k-1} / p_{k-1} of the top part
-  for (int k = 0; k < m; ++k) {
-    const int64_t K = K0 + k;
+  double cp = 0.0;
+  for (int k = 0; k < a.L; ++k) {
+    const int64_t K = c * a.L + k;
     const double sub = k > 0 ? H[5 * C + K] : 0.0;
     const double inv = 1.0 / (H[K] - sub * cp);
     cp = H[6 * C + K] * inv;
@@ -477,22 +457,6 @@ __global__ void pressure_factor_kernel(const HArgs a, const double *__restrict__
     l_out[K] = sub * inv;
     cp_out[K] = cp;
   }
-  double ap = 0.0;   // a_{k+1} / q_{k+1} of the bottom part
-  for (int k = L - 1; k > m; --k) {
-    const int64_t K = K0 + k;
-    const double sup = k < L - 1 ? H[6 * C + K] : 0.0;
-    const double inv = 1.0 / (H[K] - sup * ap);
-    ap = H[5 * C + K] * inv;
-    w_out[K] = omega * inv;
-    l_out[K] = sup * inv;
-    cp_out[K] = ap;
-  }
-  const int64_t K = K0 + m;
-  const double sub = m > 0 ? H[5 * C + K] : 0.0, sup = m < L - 1 ? H[6 * C + K] : 0.0;
-  const double inv = 1.0 / (H[K] - sub * cp - sup * ap);
-  w_out[K] = omega * inv;
-  l_out[K] = sub * inv;
-  cp_out[K] = sup * inv;
 }
 
 // Gamma_K = (H 1)_K / (P^T S P 1)_K (Eq. scaling_matrix). H 1 = M3^Pi 1: G annihilates
@@ -545,8 +509,8 @@ int build_factors(Ctx *c) {
   for (int l = 0; l < c->nmg; ++l) {
     Level &lv = c->lv[l];
     HArgs ha{lv.nlev, lv.ncol, lv.ncell, lv.col_nbr, lv.col_nbr_face};
-    pressure_factor_kernel<<<grid_for(lv.ncol, 128), 128, 0, c->stream>>>(
-        ha, lv.H, c->opt.mg_omega, mg_twisted(c) ? 1 : 0, lv.Hz_w, lv.Hz_l, lv.Hz_cp);
+    pressure_factor_kernel<<<grid_for(lv.ncol, 128), 128, 0, c->stream>>>(ha, lv.H, c->opt.mg_omega, lv.Hz_w,
+                                                                           lv.Hz_l, lv.Hz_cp);
     HMG_CUDA(c, cudaGetLastError());
   }
   int st;
@@ -563,7 +527,6 @@ int build_factors(Ctx *c) {
     }
   }
   c->factor_omega = c->opt.omega;
-  c->factor_twisted = mg_twisted(c);
   c->factor_mg_omega = c->opt.mg_omega;
   return HMG_OK;
 }

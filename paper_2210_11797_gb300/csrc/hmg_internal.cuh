@@ -99,8 +99,6 @@ struct Ctx {
   // sup_k / p_k, [ntz] each; and omega / diag(S^hh) [nth]
   double *Sz_w = nullptr, *Sz_l = nullptr, *Sz_cp = nullptr, *Sh_w = nullptr;
   double factor_omega = 0.0, factor_mg_omega = 0.0;   // the weights the factors were built with
-  bool factor_twisted = false;   // the pressure smoother's factors are the twisted (two-lane) ones
-  bool tuned_twisted = false;    // hmg_autotune chose the twisted column solve (mg_twisted = 2)
   double *Ainv = nullptr;     // [49][ncell] A_K^-1, entry (i, j) at (7 i + j) * ncell + K
   double *kth = nullptr;      // [6][ncell] diagonal of K_K (k theta on each local face)
   double *gamma = nullptr;    // [ncell]
@@ -321,12 +319,6 @@ int time_vcycle(Ctx *c, int fp32, float *ms);
 // layers per column: a one-column block's three shared-memory arrays of the line sweep
 // (3 x ((L + 1) | 1) doubles) stay within the default 48 KB of dynamic shared memory
 constexpr int kMaxLayers = 2045;
-
-// The pressure smoother's column solve: one-lane Thomas, or the two-lane twisted elimination
-// (option mg_twisted: 0, 1, or 2 = as hmg_autotune chose).
-inline bool mg_twisted(const Ctx *c) {
-  return c->opt.mg_twisted == 1 || (c->opt.mg_twisted == 2 && c->tuned_twisted);
-}
 
 inline int mg_cpb_limit(int nlev) {
   const int m = 2048 / (nlev | 1);

@@ -17,7 +17,6 @@ namespace hmg {
 
 struct MGArgs {
   int L, ncol, cpb;
-  int twisted;   // columns solved by the two-lane twisted elimination (factors to match)
   int64_t ncell;
   const int32_t *col_nbr;
 };
@@ -158,59 +157,18 @@ __device__ __forceinline__ void smooth_block_src(const MGArgs &a, const T *__res
     scp[j] = __ldg(hcp + K);
   }
   __syncthreads();
-  if (!a.twisted) {   // one lane per column: Thomas forward and backward
-    if ((int)threadIdx.x < nc) {
-      const int o = threadIdx.x * ld;
-      T y = sr[o];
-      for (int k = 1; k < a.L; ++k) {
-        y = fma(-sl[o + k], y, sr[o + k]);
-        sr[o + k] = y;
-      }
-      T xk = y;
-      for (int k = a.L - 2; k >= 0; --k) {
-        xk = fma(-scp[o + k], xk, sr[o + k]);
-        sr[o + k] = xk;
-      }
+  if ((int)threadIdx.x < nc) {
+    const int o = threadIdx.x * ld;
+    T y = sr[o];
+    for (int k = 1; k < a.L; ++k) {
+      y = fma(-sl[o + k], y, sr[o + k]);
+      sr[o + k] = y;
     }
-  } else {
-  // twisted solve (factors from pressure_factor_kernel), two lanes per column: the even lane
-  // eliminates rows 0..m-1 downwards, the odd lane rows L-1..m+1 upwards, they swap their
-  // last values, each forms row m, then back-substitutes its own half
-  {
-    const int t = threadIdx.x;
-    const bool act = t < 2 * nc;
-    const unsigned mask = __ballot_sync(0xffffffffu, act);
-    if (act) {
-      const int o = (t >> 1) * ld, m = a.L >> 1;
-      const bool top = (t & 1) == 0;
-      // both lanes run the same instruction stream on mirrored rows (no divergence): the top
-      // lane rows 0, 1, .., m-1, the bottom lane rows L-1, L-2, .., m+1 (one fewer when L is
-      // even, its last step predicated off)
-      const int cnt = top ? m : a.L - 1 - m, k0 = top ? 0 : a.L - 1, dk = top ? 1 : -1;
-      T v = (T)0;
-      for (int i = 0; i < m; ++i) {
-        if (i < cnt) {
-          const int k = k0 + dk * i;
-          v = fma(-sl[o + k], v, sr[o + k]);
-          sr[o + k] = v;
-        }
-      }
-      const T w = __shfl_xor_sync(mask, v, 1);
-      const T ym = top ? v : w, zp = top ? w : v;   // Y_{m-1}, Z_{m+1} (0 where absent)
-      const T xm = fma(-sl[o + m], ym, fma(-scp[o + m], zp, sr[o + m]));
-      __syncwarp(mask);   // both lanes have read row m before it is overwritten
-      if (top) sr[o + m] = xm;
-      T x = xm;
-      const int k1 = top ? m - 1 : m + 1;
-      for (int i = 0; i < m; ++i) {
-        if (i < cnt) {
-          const int k = k1 - dk * i;
-          x = fma(-scp[o + k], x, sr[o + k]);
-          sr[o + k] = x;
-        }
-      }
+    T xk = y;
+    for (int k = a.L - 2; k >= 0; --k) {
+      xk = fma(-scp[o + k], xk, sr[o + k]);
+      sr[o + k] = xk;
     }
-  }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -452,7 +410,6 @@ static MGArgs mg_args(const Ctx *c, int l, int pm = 0) {
   a.cpb = tc > 0 && tc <= mg_cpb_limit(lv.nlev) ? tc : cdef;
   a.ncell = lv.ncell;
   a.col_nbr = lv.col_nbr;
-  a.twisted = c->factor_twisted ? 1 : 0;   // as the factors were built
   return a;
 }
 
@@ -478,8 +435,7 @@ static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int t
   const int tmax = threads_override > 0 ? threads_override : (tt > 0 ? tt : 256);
   int threads = ((sh.a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > tmax) threads = tmax;
-  const int lanes = (sh.a.twisted ? 2 : 1) * sh.a.cpb;   // one or two lanes per column
-  if (threads < ((lanes + 31) / 32) * 32) threads = ((lanes + 31) / 32) * 32;
+  if (threads < ((sh.a.cpb + 31) / 32) * 32) threads = ((sh.a.cpb + 31) / 32) * 32;   // a lane per column
   sh.threads = threads;
   return sh;
 }

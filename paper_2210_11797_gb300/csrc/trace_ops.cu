@@ -6,7 +6,6 @@
 // Paper (arXiv 2210.11797): Eqs. hybrid-S, hybrid-rhs, hybrid-recovery (Sec. 2.4);
 // Algorithm 1 and Eq. banded_system; Algorithm 2; Sec. 2.5 intergrid operators
 // (P lambda = {{Pi}}, Restrict = P^T) and Eq. scaling_matrix.
-#include <cstring>
 #include <mutex>
 
 #include "device_common.cuh"
@@ -576,40 +575,14 @@ int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms) {
   return st;
 }
 
-// One coordinate-descent pass over the multigrid levels, coarsest first, timing whole
-// V-cycles: the fused restriction / injection sweeps of the small levels take the level's
-// shape too, and a shape that suits the plain smoother can starve them of blocks.
-static int descend_levels(Ctx *c, int pm) {
-  int st = HMG_OK;
-  for (int l = c->nmg - 1; l >= 0 && !st; --l) {
-    const int mmax = mg_cpb_limit(c->lv[l].nlev);
-    int bc = c->tune_mg_cpb[pm][l], bt = c->tune_mg_threads[pm][l];
-    float bms = 1e30f;
-    if ((st = time_vcycle(c, pm, &bms))) break;
-    for (int cand : {32, 64, 16, 8, 4, 2, 1})
-      for (int thr : {256, 128}) {
-        if (cand > mmax || st || (cand == bc && thr == bt)) continue;
-        c->tune_mg_cpb[pm][l] = cand;
-        c->tune_mg_threads[pm][l] = thr;
-        float ms = 0.f;
-        if ((st = time_vcycle(c, pm, &ms))) break;
-        if (ms < 0.98f * bms) { bms = ms; bc = cand; bt = thr; }   // 2%: beyond the timing noise
-      }
-    c->tune_mg_cpb[pm][l] = bc;
-    c->tune_mg_threads[pm][l] = bt;
-  }
-  return st;
-}
-
 int autotune(Ctx *c) {
   const Level &f = c->lv[0];
   const int profile = c->opt.profile;
   c->opt.profile = 0;
   int st = HMG_OK;
-  const bool fp32 = c->S32 && c->lv[0].H32;
   // FP64 shapes always; FP32 ones when the FP32 preconditioner's coefficients exist
   for (int pm = 0; pm < 2 && !st; ++pm) {
-    if (pm == 1 && !fp32) break;
+    if (pm == 1 && (!c->S32 || !c->lv[0].H32)) break;
     const int cmax = sweep_cpb_limit(f.nlev);
     int best = cmax < 32 ? cmax : 32, best_t = 256;
     float best_ms = 1e30f;
@@ -634,28 +607,25 @@ int autotune(Ctx *c) {
         }
       if (!st) { c->tune_mg_cpb[pm][l] = mbest; c->tune_mg_threads[pm][l] = mbest_t; }
     }
-    if (!st) st = descend_levels(c, pm);
-  }
-  // the smoother's column solve (mg_twisted = 2): one-lane Thomas or the two-lane twisted
-  // elimination, whichever runs the whole V-cycle of the configured precision faster
-  if (!st && c->opt.mg_twisted == 2) {
-    const int pd = c->opt.precision == HMG_PRECISION_MIXED && fp32 ? 1 : 0;
-    int save_cpb[2][kMaxLevels], save_thr[2][kMaxLevels];
-    std::memcpy(save_cpb, c->tune_mg_cpb, sizeof(save_cpb));
-    std::memcpy(save_thr, c->tune_mg_threads, sizeof(save_thr));
-    const bool cur = c->tuned_twisted;
-    float t_cur = 0.f, t_alt = 0.f;
-    if (!(st = time_vcycle(c, pd, &t_cur))) {
-      c->tuned_twisted = !cur;
-      st = build_factors(c);
-      for (int pm = 0; pm < (fp32 ? 2 : 1) && !st; ++pm) st = descend_levels(c, pm);
-      if (!st) st = time_vcycle(c, pd, &t_alt);
-      if (!st && !(t_alt < 0.98f * t_cur)) {   // keep the first form unless clearly faster
-        c->tuned_twisted = cur;
-        std::memcpy(c->tune_mg_cpb, save_cpb, sizeof(save_cpb));
-        std::memcpy(c->tune_mg_threads, save_thr, sizeof(save_thr));
-        st = build_factors(c);
-      }
+    // then one coordinate-descent pass over the levels, coarsest first, timing whole
+    // V-cycles: the fused restriction / injection sweeps of the small levels take the level's
+    // shape too, and a shape that suits the plain smoother can starve them of blocks
+    for (int l = c->nmg - 1; l >= 0 && !st; --l) {
+      const int mmax = mg_cpb_limit(c->lv[l].nlev);
+      int bc = c->tune_mg_cpb[pm][l], bt = c->tune_mg_threads[pm][l];
+      float bms = 1e30f;
+      if ((st = time_vcycle(c, pm, &bms))) break;
+      for (int cand : {32, 64, 16, 8, 4, 2, 1})
+        for (int thr : {256, 128}) {
+          if (cand > mmax || st || (cand == bc && thr == bt)) continue;
+          c->tune_mg_cpb[pm][l] = cand;
+          c->tune_mg_threads[pm][l] = thr;
+          float ms = 0.f;
+          if ((st = time_vcycle(c, pm, &ms))) break;
+          if (ms < 0.98f * bms) { bms = ms; bc = cand; bt = thr; }   // 2%: beyond the timing noise
+        }
+      c->tune_mg_cpb[pm][l] = bc;
+      c->tune_mg_threads[pm][l] = bt;
     }
   }
   c->opt.profile = profile;

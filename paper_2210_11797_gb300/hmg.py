@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
                 ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
                 ("stall_ratio", C.c_double), ("mg_fused", C.c_int32), ("warm_start", C.c_int32),
-                ("mg_fuse_cells", C.c_int32), ("async_stats", C.c_int32), ("mg_twisted", C.c_int32)]
+                ("mg_fuse_cells", C.c_int32), ("async_stats", C.c_int32)]
 
 
 class SolveStats(C.Structure):

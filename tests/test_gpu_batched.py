@@ -63,7 +63,7 @@ def test_batched_solves_equal_single_solves():
 def test_autotuned_shapes_keep_results():
     from paper_2210_11797_gb300.hmg import Solver
     w = I.cubed_sphere(12, 30)
-    gpu = Solver(w.hier, w.coeffs, mg_twisted=0)   # the column-solve form stays fixed
+    gpu = Solver(w.hier, w.coeffs)
     Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
     lam0, st0 = gpu.solve(Rub, Rpi)
     gpu.autotune()

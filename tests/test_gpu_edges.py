@@ -199,11 +199,10 @@ def test_async_stats_enqueue_the_solve_and_report_later():
 
 def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
     """Launch shapes change no arithmetic: a solve captured before hmg_autotune and the solve
-    re-captured after it (autotune drops the old graph) give the same lambda bit for bit
-    (with the column-solve form fixed: mg_twisted = 0)."""
+    re-captured after it (autotune drops the old graph) give the same lambda bit for bit."""
     from paper_2210_11797_gb300.hmg import Solver
     w = I.cubed_sphere(16, 12, seed=12)
-    gpu = Solver(w.hier, w.coeffs, tol=1e-8, mg_twisted=0)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-8)
     Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
     lam0, st0 = gpu.solve(Rub, Rpi)
     before = gpu.launch_shapes()
