@@ -206,6 +206,7 @@ class Solver:
         self._set_mesh(hier)
         self._set_coefficients(coeffs)
         _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+        self._fp32_built = self.opts.precision == PRECISION["mixed"]   # FP32 operator copies exist
         nc, nt = C.c_int64(), C.c_int64()
         _check(self.ctx, lib().hmg_sizes(self.ctx, C.byref(nc), C.byref(nt)))
         self.ncell, self.ntrace = nc.value, nt.value
@@ -259,8 +260,11 @@ class Solver:
         for k, v in kw.items():
             setattr(self.opts, k, _option_value(k, v))
         _check(self.ctx, lib().hmg_set_options(self.ctx, C.byref(self.opts)))
-        if self.opts.precision == PRECISION["mixed"]:
+        # the FP32 copies of the operators are built by assembly, once; later changes of the
+        # relaxation weights rebuild them inside hmg_set_options
+        if self.opts.precision == PRECISION["mixed"] and not self._fp32_built:
             _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+            self._fp32_built = True
 
     # -- the calls ------------------------------------------------------------------------
     def trace_rhs(self, Rub, Rpi):
