@@ -21,8 +21,8 @@ preconditioners for a compatible finite element dynamical core" (arXiv 2210.1179
                  the non-nested two-level cycle (Algorithm 2) and right-preconditioned
                  BiCGStab (Sec. 3.2).
 
-Readings of passages the paper leaves open are listed in the design doc and repeated where
-they are used. Pins (tests/test_oracle_*.py, marker "not gpu") tie each function to
+Where the paper leaves a passage open, the reading taken is stated in the docstring of the
+function that uses it. Pins (tests/test_oracle_*.py, marker "not gpu") tie each function to
 something other than itself: closed forms on boxes, the divergence theorem, the
 hybrid = mixed identity against a dense direct solve, Thomas vs dense LU, and the
 convergence behaviour the paper reports.

@@ -91,8 +91,10 @@ def local_mass(verts: np.ndarray, c22: np.ndarray, geometry: int, coriolis=None)
     """Velocity block of A_K and the volumes, by 3x3x3 Gauss quadrature (Sec. 2.2).
 
     M_K(f,g) = int_K [v_f.v_g + c22 (zhat.v_f)(zhat.v_g) + v_f.(c x v_g)] dx with the
-    contravariant Piola map v = J vhat / det J; c22 is the vertical weight of -Q22 (reading
-    of the mu term in the design doc) and c = tau_u dt 2 Omega the Coriolis vector of Eq. gh-u
+    contravariant Piola map v = J vhat / det J; c22 is the vertical weight of -Q22 (the
+    dimensionally inconsistent mu term of Eq. gh-u is dropped: buoyancy enters through -Q22
+    only, whose weight tau_u tau_theta dt^2 N^2 makes 1 + c22 the paper's mu) and
+    c = tau_u dt 2 Omega the Coriolis vector of Eq. gh-u
     (None: no rotation). Returns M [n,6,6], |K| (Gauss) [n], |K|_1 (one-point) [n] and
     (zhat . v_f) at the cell centre [n,6].
     """

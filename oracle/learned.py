@@ -14,8 +14,10 @@ f(a x) = a f(x) for a > 0:
     y  = conv1d(C -> 1, 3)(h3)
 conv1d(a -> b, 3): y[o, k] = sum_i sum_{d=-1..1} W[o, i, d+1] x[i, k+d].
 The horizontal mix is depthwise (one (w_c, w_e, w_d) per channel) and isotropic.
-Input and output are scaled by diag(H)^-1/2 around the network (reading in the design doc), so
-the learned map is f_H(b) = D^-1/2 f(D^-1/2 b) with D = diag(H).
+Input and output are scaled by diag(H)^-1/2 around the network (a choice of this project:
+the paper has no learned part; H's diagonal varies by orders of magnitude with height, and
+the bias-free network is positively homogeneous, so the scaling gives it a dimensionless
+problem), so the learned map is f_H(b) = D^-1/2 f(D^-1/2 b) with D = diag(H).
 
 Flexible GMRES (Saad 2003 Alg. 9.6, restart m) allows the preconditioner to change between
 steps (a network is not a fixed linear operator).

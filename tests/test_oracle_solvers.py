@@ -58,7 +58,8 @@ def test_column_blocks_of_S_are_tridiagonal_and_match_dense(config1):
 
 def test_line_sweep_formula_against_dense_algebra(config1):
     """One sweep of Algorithm 1 equals lambda + omega D^-1 (B - S lambda) with D the block
-    diagonal [diag(S^hh), S^zz] formed densely (update sign +omega)."""
+    diagonal [diag(S^hh), S^zz] formed densely (update sign +omega: Algorithm 1 prints a
+    minus sign with R = B - S lambda, which diverges)."""
     w, s = config1
     mesh = w.mesh
     S = s.S.toarray()
