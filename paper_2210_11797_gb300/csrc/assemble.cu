@@ -24,6 +24,33 @@ struct CellArgs {
   hmg_scalars sc;
 };
 
+// Trilinear shape function values and derivatives at the 27 Gauss points (3 per direction):
+// [q][v] = {N_v, dN_v/dxi, dN_v/deta, dN_v/dzeta}, q = qi + 3 qj + 9 qk, vertex v = (v&1,
+// v>>1&1, v>>2). They depend on the point only, so they are formed once on the host (with the
+// same expressions and order of operations a per-cell evaluation would use) instead of in
+// every cell.
+__constant__ double c_shape[27][8][4];
+
+static int upload_shape_functions(Ctx *c) {
+  static thread_local double h[27][8][4];
+  const double gq = std::sqrt(15.0) / 10.0;
+  const double gx[3] = {0.5 - gq, 0.5, 0.5 + gq};
+  for (int q = 0; q < 27; ++q) {
+    const double xi = gx[q % 3], eta = gx[(q / 3) % 3], zeta = gx[q / 9];
+    for (int v = 0; v < 8; ++v) {
+      const int av = v & 1, bv = (v >> 1) & 1, cv = (v >> 2) & 1;
+      const double fx = av ? xi : 1.0 - xi, fy = bv ? eta : 1.0 - eta, fz = cv ? zeta : 1.0 - zeta;
+      const double sx = av ? 1.0 : -1.0, sy = bv ? 1.0 : -1.0, sz = cv ? 1.0 : -1.0;
+      h[q][v][0] = fx * fy * fz;
+      h[q][v][1] = sx * fy * fz;
+      h[q][v][2] = fx * sy * fz;
+      h[q][v][3] = fx * fy * sz;
+    }
+  }
+  HMG_CUDA(c, cudaMemcpyToSymbol(c_shape, h, sizeof(h)));
+  return HMG_OK;
+}
+
 // Corner of the column at reference (xi, eta) in {0,1}^2: (0,0)->0, (1,0)->1, (1,1)->2, (0,1)->3.
 __device__ __forceinline__ int corner_of(int a, int b) { return b ? (a ? 2 : 3) : (a ? 1 : 0); }
 
@@ -77,11 +104,8 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
     double x[3] = {0, 0, 0};
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      const int av = v & 1, bv = (v >> 1) & 1, cv = (v >> 2) & 1;
-      const double fx = av ? xi : 1.0 - xi, fy = bv ? eta : 1.0 - eta, fz = cv ? zeta : 1.0 - zeta;
-      const double sx = av ? 1.0 : -1.0, sy = bv ? 1.0 : -1.0, sz = cv ? 1.0 : -1.0;
-      const double n = fx * fy * fz;
-      const double d0 = sx * fy * fz, d1 = fx * sy * fz, d2 = fx * fy * sz;
+      const double n = c_shape[q][v][0];
+      const double d0 = c_shape[q][v][1], d1 = c_shape[q][v][2], d2 = c_shape[q][v][3];
       x[0] += n * vx[v]; x[1] += n * vy[v]; x[2] += n * vz[v];
       J[0][0] += vx[v] * d0; J[0][1] += vx[v] * d1; J[0][2] += vx[v] * d2;
       J[1][0] += vy[v] * d0; J[1][1] += vy[v] * d1; J[1][2] += vy[v] * d2;
@@ -97,21 +121,26 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
     } else {
       r[0] = 0.0; r[1] = 0.0; r[2] = 1.0;
     }
-    double G[3][3], rJ[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      rJ[d] = r[0] * J[0][d] + r[1] * J[1][d] + r[2] * J[2][d];
-#pragma unroll
-      for (int e = 0; e < 3; ++e) G[d][e] = J[0][d] * J[0][e] + J[1][d] * J[1][e] + J[2][d] * J[2][e];
-    }
-    const double s[6] = {eta - 1.0, xi, eta, xi - 1.0, zeta - 1.0, zeta};
     const double wd = w / det;
+    // H[d][e] = w / det * (G[d][e] + c22 (r.J)_d (r.J)_e), G = J^T J: 6 distinct entries,
+    // formed once per point; each of the 21 entries of M then costs a multiply and an FMA
+    double rJ[3], H[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rJ[d] = r[0] * J[0][d] + r[1] * J[1][d] + r[2] * J[2][d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int e = d; e < 3; ++e) {
+        const double g = J[0][d] * J[0][e] + J[1][d] * J[1][e] + J[2][d] * J[2][e];
+        H[d][e] = H[e][d] = wd * fma(c22 * rJ[d], rJ[e], g);
+      }
+    const double s[6] = {eta - 1.0, xi, eta, xi - 1.0, zeta - 1.0, zeta};
     int idx = 0;
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
 #pragma unroll
       for (int g = f; g < 6; ++g) {
-        M[idx] += wd * s[f] * s[g] * (G[dir[f]][dir[g]] + c22 * rJ[dir[f]] * rJ[dir[g]]);
+        M[idx] = fma(s[f], s[g] * H[dir[f]][dir[g]], M[idx]);
         ++idx;
       }
     }
@@ -122,12 +151,15 @@ __global__ void __launch_bounds__(128) cell_kernel(const CellArgs a, double *__r
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int e = 0; e < 3; ++e) X[d][e] = cz * (J[0][e] * J[1][d] - J[1][e] * J[0][d]);
+        for (int e = 0; e < 3; ++e) X[d][e] = wd * cz * (J[0][e] * J[1][d] - J[1][e] * J[0][d]);
       int ci = 0;
 #pragma unroll
       for (int f = 0; f < 6; ++f)
 #pragma unroll
-        for (int g = f + 1; g < 6; ++g) Cor[ci++] += wd * s[f] * s[g] * X[dir[f]][dir[g]];
+        for (int g = f + 1; g < 6; ++g) {
+          Cor[ci] = fma(s[f], s[g] * X[dir[f]][dir[g]], Cor[ci]);
+          ++ci;
+        }
     }
     vol += w * det;
   }
@@ -535,6 +567,8 @@ int assemble_all(Ctx *c) {
   if (!c->have_mesh || !c->have_coeffs) return fail(c, HMG_ERR_NOT_READY, "mesh or coefficients not set");
   // per-level cell records
   double *rec[kMaxLevels] = {nullptr};
+  int st0;
+  if ((st0 = upload_shape_functions(c))) return st0;
   for (int l = 0; l < c->nmg; ++l) {
     Level &lv = c->lv[l];
     HMG_CUDA(c, cudaMalloc(&rec[l], (size_t)lv.ncell * kCellData * sizeof(double)));

@@ -327,6 +327,12 @@ class Solver:
             _check(self.ctx, rc)
         return lam, st.as_dict()
 
+    def assemble(self):
+        """Rebuild the operators (cell matrices, S, factors, H per level, Gamma) from the
+        coefficients on the device (hmg_assemble_trace)."""
+        _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+        self._fp32_built = self.opts.precision == PRECISION["mixed"] or self._fp32_built
+
     def reconstruct(self, lam, Rub, Rpi):
         ub, pi = self._empty(6 * self.ncell), self._empty(self.ncell)
         _check(self.ctx, lib().hmg_reconstruct(self.ctx, self._dev(lam, self.ntrace, "lambda"),
