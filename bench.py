@@ -490,6 +490,60 @@ def run_param_sweep(args):
     return out
 
 
+def coarse_map_bytes(ncell, elem=8):
+    """Algorithmic bytes of one application of the learned coarse map, per cell: the front
+    kernel reads bbar and diag(H) (elem each) and writes the 32 BF16 channels of the second
+    layer (64 B); the back kernel reads those channels (its columns' neighbours come from
+    cache), diag(H) again and writes the output (elem)."""
+    return ncell * ((2 * elem + 64) + (64 + 2 * elem))
+
+
+def run_coarse_map(args):
+    """The learned coarse map (growth axis: the network that may replace or seed the pressure
+    V-cycle) timed at the workload's size beside the V-cycle it stands in for. Each forward is
+    timed alone with CUDA events after an L2 flush (a 256 MB write); weights are a seeded
+    random draw (the time does not depend on their values)."""
+    import numpy as np
+    import torch
+    from paper_2210_11797_gb300 import inputs as I
+    from paper_2210_11797_gb300.hmg import Solver, lib
+    w = workload_spec(args.workload)
+    solver = Solver(w.hier, w.coeffs, tol=w.tol)
+    stream = torch.cuda.current_stream()
+    npar = lib().hmg_coarse_model_size()
+    solver.set_coarse_model((0.2 * I.normal(11, npar)).astype(np.float32))
+    bbar = torch.as_tensor(I.normal(12, solver.ncell)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    ms = {m: timed(lambda m=m: solver.apply_coarse_model(bbar, m)) for m in ("tensor", "fp32", "bf16")}
+    ms["pressure_vcycle"] = timed(lambda: solver.vcycle(bbar))
+    peak, kind = measured_peaks()
+    nbytes = coarse_map_bytes(solver.ncell)
+    gbs = nbytes / (ms["tensor"] * 1e-3) / 1e9
+    out = {"mode": "coarse_map", "workload": w.name, "ncell": solver.ncell, "steps": args.steps,
+           "warmup": args.warmup, "l2": "flushed before each timed forward (256 MB write)",
+           "ms": {k: round(v, 4) for k, v in ms.items()},
+           "roofline": {"bound": "hbm", "kernel": "coarse_map (nn_front_tc_kernel + nn_back_kernel)",
+                        "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "peak_kind": kind, "algorithmic_bytes": nbytes}}
+    solver.close()
+    return out
+
+
 def run_batched(args, rank, world):
     """64 independent cubed-sphere solves (N in {12,24,32,48}, L in {10,30,50,70}, drawn by
     SplitMix64 seed 3), each context autotuned, all solved in one graph launch per step."""
@@ -624,6 +678,9 @@ def main():
     ap.add_argument("--param-sweep", action="store_true",
                     help="the paper's Appendix B parameter studies (relaxation factors, smoothing "
                          "steps) on the workload instead of the benchmark line")
+    ap.add_argument("--coarse-map", action="store_true",
+                    help="time the learned coarse map (tensor-core and CUDA-core forms) and the "
+                         "pressure V-cycle at the workload's size instead of the benchmark line")
     ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--_seconds", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_its", type=int, default=None, help=argparse.SUPPRESS)
@@ -658,6 +715,10 @@ def main():
     if args.param_sweep:
         if rank == 0:
             print(json.dumps(run_param_sweep(args)))
+        return
+    if args.coarse_map:
+        if rank == 0:
+            print(json.dumps(run_coarse_map(args)))
         return
     if args.workload.startswith("batch"):
         out = run_batched(args, rank, world)

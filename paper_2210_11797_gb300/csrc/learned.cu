@@ -126,20 +126,25 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---- forward, column-local layers on the tensor cores (inference, BF16) ---------------------
-// h2 = relu(conv(32 -> 32, 3)(h1)) as a GEMM per tile of 128 consecutive cells:
-//   H2[m][o] = sum_kk A[m][kk] B[o][kk],  kk = d * 32 + i,  A[m][kk] = h1[i](cell m + d - 1),
-//   B[o][kk] = W2[o][i][d],
-// with A (128 x 96) and B (32 x 96) in BF16 in shared memory, K-major without swizzle (8 x 16 B
-// core matrices: along M/N every 128 B, along K every (rows / 8) * 128 B), one
-// tcgen05.mma (M 128, N 32, K 16) per 16 columns of K issued by one thread, the FP32
-// accumulator in 32 TMEM columns, read back by the four warps (warp w owns lanes 32w..32w+31).
-// h1 = relu(conv(1 -> 32, 3)(x)) is computed on the fly while A is written (3 FMAs per entry).
+// The cells are laid out in padded rows, R = col (L + 2) + k + 1, with an empty row below and
+// above every column (levels -1 and L). Per tile of 128 padded rows,
+// h2 = relu(conv(32 -> 32, 3)(h1)) is a GEMM
+//   H2[m][o] = sum_d sum_i h1[i](row m + d - 1) W2[o][i][d]
+// issued as six tcgen05.mma (M 128, N 32, K 16; K = d * 32 + i): the A operand of tap d is the
+// tile's h1 rows shifted by d - 1, i.e. the same shared-memory buffer read from a start address
+// d rows further on. h1 is zero on the padded rows, which is the convolution's zero padding at
+// ground and lid, so A needs no im2col copy. A: h1 on the tile's rows -1 .. 128 in BF16,
+// K-major without swizzle ([8-channel group][row][8 channels]: rows every 16 B, core matrices
+// along M every 128 B, along K every 130 x 16 B); B (32 x 96 BF16) in the same core-matrix form.
+// The FP32 accumulator lives in 32 TMEM columns and is read back by the four warps (warp w owns
+// lanes 32w..32w+31); the results of padded rows are dropped. h2 leaves cell-major, [ncell][32]
+// BF16, for nn_mix_out_kernel.
 constexpr int kTcM = 128;
-constexpr int kTcAWindow = 64 * 1024;     // A region: 24 KB used, the rest keeps any descriptor
-constexpr int kTcB = kTcAWindow;          // stride within the CTA's shared memory
-constexpr int kTcBWindow = 8 * 1024;      // B region: 6 KB used
-constexpr int kTcX = kTcB + kTcBWindow;   // x (132 floats), W1 (96 floats), row levels (128 ints)
-constexpr int kTcBar = kTcX + 2048;       // two mbarriers (16 B) and the TMEM address (4 B)
+constexpr int kTcRows = kTcM + 2;                      // h1 rows of a tile: -1 .. 128
+constexpr int kTcLbo = kTcRows * 16;                   // bytes between 8-channel groups
+constexpr int kTcB = (4 * kTcLbo + 1023) / 1024 * 1024;   // A: 8,320 B; B from here (6 KB)
+constexpr int kTcX = kTcB + 6 * 1024;                  // x (132 floats), W1 (96 floats)
+constexpr int kTcBar = kTcX + 1024;                    // two mbarriers (16 B), TMEM address (4 B)
 constexpr int kTcSmem = kTcBar + 64;
 constexpr uint32_t kTcWaitLimit = 1u << 20;   // mbarrier polls before the kernel gives up
 
@@ -182,17 +187,23 @@ template <typename Tin>
 __global__ void __launch_bounds__(128)
     nn_front_tc_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ bimg,
                        const Tin *__restrict__ xin, const double *__restrict__ diagH,
-                       const float *__restrict__ diagH32, int64_t ncell, int L,
+                       const float *__restrict__ diagH32, int ncol, int L,
                        __nv_bfloat16 *__restrict__ h2_out, int *__restrict__ wait_flag) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
   float *xs = reinterpret_cast<float *>(tc_smem + kTcX);            // 132 floats
   float *w1s = xs + kTcM + 4;                                        // 96 floats
-  int *lev = reinterpret_cast<int *>(w1s + 96);                      // 128 ints: level of row m
   uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + kTcBar);   // [0] MMA done, [1] B loaded
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + kTcBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+  const int P = L + 2, nrows = ncol * P;     // padded rows (the host checks that they fit an int)
+  const int R0 = blockIdx.x * kTcM;
+  // level of padded row R, or -1 on a pad row or past the mesh
+  auto level = [&](int R) {
+    if (R < 0 || R >= nrows) return -1;
+    const int k = R % P - 1;
+    return k < L ? k : -1;
+  };
 
   if (warp == 0) {   // 32 TMEM columns for the 128 x 32 FP32 accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot)));
@@ -207,32 +218,27 @@ __global__ void __launch_bounds__(128)
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(sB)), "l"(bimg), "r"(6144), "r"(smem_u32(bar + 1)) : "memory");
   }
-  // x on cells m0-2 .. m0+129 (scaled by diag(H)^-1/2, rounded to BF16), 0 outside the mesh
+  // x on padded rows R0-2 .. R0+129 (scaled by diag(H)^-1/2 in FP32, rounded to BF16), 0 on pad
+  // rows and outside the mesh
   for (int j = tid; j < kTcM + 4; j += blockDim.x) {
-    const int64_t q = m0 - 2 + j;
+    const int R = R0 - 2 + j, k = level(R);
     float v = 0.f;
-    if (q >= 0 && q < ncell) {
-      float sc = 1.f;
-      if (diagH) sc = (float)(1.0 / sqrt(diagH[q]));
-      else if (diagH32) sc = rsqrtf(diagH32[q]);
+    if (k >= 0) {
+      const int64_t q = (int64_t)(R / P) * L + k;
+      const float sc = rsqrtf(diagH ? (float)diagH[q] : diagH32 ? diagH32[q] : 1.f);
       v = rnd<__nv_bfloat16>((float)xin[q] * sc);
     }
     xs[j] = v;
   }
   if (tid < 96) w1s[tid] = rnd<__nv_bfloat16>(wts[kOffW1 + tid]);
-  {
-    const int64_t cell = m0 + tid;   // 128 threads, one row each
-    lev[tid] = cell < ncell ? (int)(cell % L) : -1;
-  }
   __syncthreads();
-  // A: im2col of h1, 16 B (8 channels of one tap of one row) per store: (m, d, g) items
-  for (int e = tid; e < kTcM * 12; e += blockDim.x) {
-    const int m = e / 12, r = e % 12, d = r >> 2, g = r & 3;
-    const int k = lev[m], kd = k + d - 1;
+  // A: h1 = relu(conv(1 -> 32, 3)(x)) on tile rows -1..128 (buffer rows 0..129), 16 B (8 channels
+  // of one row) per store, rows fastest (consecutive 16-byte slots, no bank conflicts)
+  for (int e = tid; e < 4 * kTcRows; e += blockDim.x) {
+    const int row = e % kTcRows, g = e / kTcRows;
     uint4 pack = make_uint4(0u, 0u, 0u, 0u);
-    if (k >= 0 && kd >= 0 && kd < L) {
-      const int j = m + d + 1;                       // xs index of the tap cell
-      const float xm = kd > 0 ? xs[j - 1] : 0.f, x0 = xs[j], xp = kd + 1 < L ? xs[j + 1] : 0.f;
+    if (level(R0 - 1 + row) >= 0) {
+      const float xm = xs[row], x0 = xs[row + 1], xp = xs[row + 2];   // zero on pad rows
       uint32_t wds[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -247,8 +253,7 @@ __global__ void __launch_bounds__(128)
       }
       pack = make_uint4(wds[0], wds[1], wds[2], wds[3]);
     }
-    const uint32_t off = (uint32_t)(((d * 4 + g) * (kTcM / 8) + (m >> 3)) * 128 + (m & 7) * 16);
-    *reinterpret_cast<uint4 *>(sA + off) = pack;
+    *reinterpret_cast<uint4 *>(sA + g * kTcLbo + row * 16) = pack;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -259,8 +264,9 @@ __global__ void __launch_bounds__(128)
     if (mbar_wait(bar + 1, 0)) {
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
       const uint32_t idesc = umma_idesc_bf16(kTcM, 32);
-      for (int s = 0; s < 6; ++s) {   // K = 96 in steps of 16 (two core matrices along K)
-        const uint64_t ad = umma_desc(a0 + s * 2 * (kTcM / 8) * 128, (kTcM / 8) * 128, 128);
+      for (int s = 0; s < 6; ++s) {   // tap d = s / 2, channels 16 (s % 2) .. + 15
+        const int d = s >> 1, h = s & 1;
+        const uint64_t ad = umma_desc(a0 + 2 * h * kTcLbo + d * 16, kTcLbo, 128);
         const uint64_t bd = umma_desc(b0 + s * 2 * 4 * 128, 4 * 128, 128);
         const uint32_t acc = s > 0 ? 1u : 0u;
         asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -287,16 +293,117 @@ __global__ void __launch_bounds__(128)
                    "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int64_t cell = m0 + warp * 32 + lane;
-    if (cell < ncell) {
+    const int R = R0 + warp * 32 + lane, k = level(R);
+    if (k >= 0) {   // cell-major: the 32 channels of a cell in 64 contiguous bytes
+      const int64_t cell = (int64_t)(R / P) * L + k;
+      uint32_t wd[16];
 #pragma unroll
-      for (int o = 0; o < 32; ++o)
-        h2_out[(int64_t)o * ncell + cell] = __float2bfloat16(fmaxf(__uint_as_float(r[o]), 0.f));
+      for (int p = 0; p < 16; ++p) {
+        const __nv_bfloat162 b2 =
+            __floats2bfloat162_rn(fmaxf(__uint_as_float(r[2 * p]), 0.f), fmaxf(__uint_as_float(r[2 * p + 1]), 0.f));
+        wd[p] = *reinterpret_cast<const uint32_t *>(&b2);
+      }
+      uint4 *dst = reinterpret_cast<uint4 *>(h2_out + cell * kCh);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) dst[g] = make_uint4(wd[4 * g], wd[4 * g + 1], wd[4 * g + 2], wd[4 * g + 3]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+// ---- inference: horizontal mix and output layer after the tensor-core layers -----------------
+// h2 cell-major [ncell][32] BF16. Four threads per cell, thread q owning channels 8q..8q+7, so
+// that one 16-byte load brings a neighbour's share and a warp reads 512 contiguous bytes per
+// neighbour. A block holds whole columns: h3 goes to shared memory ([cell][33], conflict-free)
+// and the output convolution reads levels k-1..k+1 there; the four partial sums of a cell are
+// added by shuffles. Same arithmetic as nn_back_kernel's mesh form up to the order of the
+// 96-term output sum. out[K] = y * diag(H)^-1/2 (the scale in FP32).
+template <typename Tout>
+__global__ void __launch_bounds__(512)
+    nn_mix_out_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ h2, Nbrs nb, int ncol,
+                      int L, int cpb, const double *__restrict__ diagH, const float *__restrict__ diagH32,
+                      Tout *__restrict__ out) {
+  extern __shared__ float sm[];
+  float *Mw = sm, *W3 = Mw + 96;
+  int *snb = reinterpret_cast<int *>(W3 + 96);           // [cpb][8] edge, corner neighbours
+  float *h3 = reinterpret_cast<float *>(snb + 8 * cpb);  // [cpb * L][33]
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) {
+    Mw[i] = rnd<__nv_bfloat16>(wts[kOffM + i]);
+    W3[i] = rnd<__nv_bfloat16>(wts[kOffW3 + i]);
+  }
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0), ncl = nc * L;
+  if ((int)threadIdx.x < nc) {
+    int e[4], d[4];
+    nb.get(c0 + threadIdx.x, e, d);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { snb[8 * threadIdx.x + q] = e[q]; snb[8 * threadIdx.x + 4 + q] = d[q]; }
+  }
+  __syncthreads();
+  const uint4 *hv = reinterpret_cast<const uint4 *>(h2);   // [ncell][4]
+  auto add8 = [](float *acc, uint4 u) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[p]));
+      acc[2 * p] += f.x;
+      acc[2 * p + 1] += f.y;
+    }
+  };
+  // warp-uniform passes (the shuffles below need every lane)
+  for (int base = 0; base < 4 * ncl; base += blockDim.x) {
+    const int i = base + threadIdx.x, j = i >> 2, q = i & 3;
+    if (j < ncl) {
+      const int cc = j / L, k = j - cc * L;
+      const int *nbr = snb + 8 * cc;
+      // all nine loads issued before any use (a missing neighbour reads the cell itself and is
+      // dropped below), so that they are in flight together
+      const int own = c0 + cc;
+      uint4 v[9];
+      v[0] = hv[((int64_t)own * L + k) * 4 + q];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) v[1 + s] = hv[((int64_t)(nbr[s] >= 0 ? nbr[s] : own) * L + k) * 4 + q];
+      float self[8], se[8], sd[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) self[t] = se[t] = sd[t] = 0.f;
+      add8(self, v[0]);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (nbr[s] >= 0) add8(se, v[1 + s]);
+        if (nbr[4 + s] >= 0) add8(sd, v[5 + s]);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int ch = 8 * q + t;
+        const float a = fmaf(Mw[3 * ch], self[t], fmaf(Mw[3 * ch + 1], se[t], Mw[3 * ch + 2] * sd[t]));
+        h3[j * 33 + ch] = rnd<__nv_bfloat16>(fmaxf(a, 0.f));
+      }
+    }
+  }
+  __syncthreads();
+  for (int base = 0; base < 4 * ncl; base += blockDim.x) {
+    const int i = base + threadIdx.x, j = i >> 2, q = i & 3;
+    float y = 0.f;
+    int k = 0;
+    if (j < ncl) {
+      k = j % L;
+      const float *hm = h3 + max(j - 1, 0) * 33, *h0 = h3 + j * 33, *hp = h3 + min(j + 1, ncl - 1) * 33;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int ch = 8 * q + t;
+        const float xm = k > 0 ? hm[ch] : 0.f, xp = k + 1 < L ? hp[ch] : 0.f;
+        y = fmaf(W3[3 * ch], xm, fmaf(W3[3 * ch + 1], h0[ch], fmaf(W3[3 * ch + 2], xp, y)));
+      }
+    }
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    if (j < ncl && q == 0) {
+      const int64_t K = (int64_t)c0 * L + j;
+      const float s = rsqrtf(diagH ? (float)diagH[K] : diagH32 ? diagH32[K] : 1.f);
+      out[K] = (Tout)((double)y * (double)s);
+    }
+  }
 }
 
 // ---- forward, horizontal mix and output layer: h2 -> h3 -> y ---------------------------------
@@ -650,6 +757,7 @@ __global__ void gather_samples_kernel(const float *__restrict__ x, const float *
 // ---- host side ---------------------------------------------------------------------------------
 static int front_smem(int cpb, int L) { return (96 + 3072 + cpb * (L + 2) + cpb * kCh * (L + 2)) * 4; }
 static int back_smem(int cpb, int L) { return (96 + 96 + cpb * kCh * (L + 2)) * 4; }
+static int mix_smem(int cpb, int L) { return (96 + 96 + 8 * cpb + cpb * L * 33) * 4; }
 static int bwd1_smem(int L) { return (3072 + 3 * kCh * (L + 2) + (L + 2)) * 4; }
 constexpr int kNnCpb = 4;
 
@@ -672,16 +780,25 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
   if (TC) {
     static_assert(!TC || sizeof(A) == 2, "the tensor-core layers store BF16");
     nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
-    nn_front_tc_kernel<Tin><<<grid_for(f.ncell, kTcM), 128, kTcSmem, c->stream>>>(
-        c->nn_w, static_cast<const __nv_bfloat16 *>(c->nn_bimg), bbar, dH, dH32, f.ncell, L,
+    const int64_t nrows = (int64_t)f.ncol * (L + 2);   // padded rows
+    if (nrows > INT32_MAX - 2 * kTcM) return fail(c, HMG_ERR_INVALID_ARG, "mesh too large for the tensor-core layer");
+    nn_front_tc_kernel<Tin><<<grid_for(nrows, kTcM), 128, kTcSmem, c->stream>>>(
+        c->nn_w, static_cast<const __nv_bfloat16 *>(c->nn_bimg), bbar, dH, dH32, f.ncol, L,
         reinterpret_cast<__nv_bfloat16 *>(h2), c->state + 3);
   } else {
     nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
                                                                           kNnCpb, nullptr, h2);
   }
   Nbrs nb{f.col_nbr, c->nn_diag, 0, 0};
-  nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
-      c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
+  if (TC) {   // whole columns per block, about 64 cells, four threads per cell
+    const int cpb = std::max(1, 64 / L), thr = (4 * cpb * L + 31) / 32 * 32;
+    const unsigned gm = (unsigned)((f.ncol + cpb - 1) / cpb);
+    nn_mix_out_kernel<Tout><<<gm, thr, mix_smem(cpb, L), c->stream>>>(
+        c->nn_w, reinterpret_cast<const __nv_bfloat16 *>(h2), nb, f.ncol, L, cpb, dH, dH32, out);
+  } else {
+    nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
+        c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
+  }
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
