@@ -491,11 +491,11 @@ def run_param_sweep(args):
 
 
 def coarse_map_bytes(ncell, elem=8):
-    """Algorithmic bytes of one application of the learned coarse map, per cell: the front
-    kernel reads bbar and diag(H) (elem each) and writes the 32 BF16 channels of the second
-    layer (64 B); the back kernel reads those channels (its columns' neighbours come from
-    cache), diag(H) again and writes the output (elem)."""
-    return ncell * ((2 * elem + 64) + (64 + 2 * elem))
+    """Algorithmic bytes of one application of the learned coarse map, per cell: the
+    tensor-core kernel reads bbar and diag(H) (elem each) and writes the 32 BF16 channels of
+    the second layer (64 B); the mix/output kernel reads those channels once (its columns'
+    neighbours come from cache) and writes the output (elem)."""
+    return ncell * ((2 * elem + 64) + (64 + elem))
 
 
 def run_coarse_map(args):
@@ -537,7 +537,7 @@ def run_coarse_map(args):
     out = {"mode": "coarse_map", "workload": w.name, "ncell": solver.ncell, "steps": args.steps,
            "warmup": args.warmup, "l2": "flushed before each timed forward (256 MB write)",
            "ms": {k: round(v, 4) for k, v in ms.items()},
-           "roofline": {"bound": "hbm", "kernel": "coarse_map (nn_front_tc_kernel + nn_back_kernel)",
+           "roofline": {"bound": "hbm", "kernel": "coarse_map (nn_front_tc_kernel + nn_mix_out_kernel)",
                         "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "peak_kind": kind, "algorithmic_bytes": nbytes}}
     solver.close()

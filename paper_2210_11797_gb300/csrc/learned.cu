@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(128)
     nn_front_tc_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ bimg,
                        const Tin *__restrict__ xin, const double *__restrict__ diagH,
                        const float *__restrict__ diagH32, int ncol, int L,
-                       __nv_bfloat16 *__restrict__ h2_out, int *__restrict__ wait_flag) {
+                       __nv_bfloat16 *__restrict__ h2_out, float *__restrict__ dscale_out,
+                       int *__restrict__ wait_flag) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
   float *xs = reinterpret_cast<float *>(tc_smem + kTcX);            // 132 floats
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(128)
                  ::"r"(smem_u32(sB)), "l"(bimg), "r"(6144), "r"(smem_u32(bar + 1)) : "memory");
   }
   // x on padded rows R0-2 .. R0+129 (scaled by diag(H)^-1/2 in FP32, rounded to BF16), 0 on pad
-  // rows and outside the mesh
+  // rows and outside the mesh; the scale of the tile's own rows is kept for the output layer
   for (int j = tid; j < kTcM + 4; j += blockDim.x) {
     const int R = R0 - 2 + j, k = level(R);
     float v = 0.f;
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(128)
       const int64_t q = (int64_t)(R / P) * L + k;
       const float sc = rsqrtf(diagH ? (float)diagH[q] : diagH32 ? diagH32[q] : 1.f);
       v = rnd<__nv_bfloat16>((float)xin[q] * sc);
+      if (j >= 2 && j < kTcM + 2) dscale_out[q] = sc;
     }
     xs[j] = v;
   }
@@ -316,94 +318,101 @@ __global__ void __launch_bounds__(128)
 // ---- inference: horizontal mix and output layer after the tensor-core layers -----------------
 // h2 cell-major [ncell][32] BF16. Four threads per cell, thread q owning channels 8q..8q+7, so
 // that one 16-byte load brings a neighbour's share and a warp reads 512 contiguous bytes per
-// neighbour. A block holds whole columns: h3 goes to shared memory ([cell][33], conflict-free)
-// and the output convolution reads levels k-1..k+1 there; the four partial sums of a cell are
-// added by shuffles. Same arithmetic as nn_back_kernel's mesh form up to the order of the
-// 96-term output sum. out[K] = y * diag(H)^-1/2 (the scale in FP32).
+// neighbour; the nine loads are issued before any use. Sums in FP32, two channels per packed
+// instruction. A block holds whole columns: h3 goes to shared memory in padded rows ([column]
+// [L + 2][36 floats], zero rows at levels -1 and L, so the output convolution needs no edge
+// test), and the four partial sums of the output convolution are added by shuffles. The same
+// arithmetic as nn_back_kernel's mesh form up to the order of the 96-term output sum.
+// out[K] = y * dscale[K], dscale = diag(H)^-1/2 in FP32 as the front kernel computed it.
 template <typename Tout>
 __global__ void __launch_bounds__(512)
     nn_mix_out_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ h2, Nbrs nb, int ncol,
-                      int L, int cpb, const double *__restrict__ diagH, const float *__restrict__ diagH32,
-                      Tout *__restrict__ out) {
-  extern __shared__ float sm[];
-  float *Mw = sm, *W3 = Mw + 96;
-  int *snb = reinterpret_cast<int *>(W3 + 96);           // [cpb][8] edge, corner neighbours
-  float *h3 = reinterpret_cast<float *>(snb + 8 * cpb);  // [cpb * L][33]
-  for (int i = threadIdx.x; i < 96; i += blockDim.x) {
-    Mw[i] = rnd<__nv_bfloat16>(wts[kOffM + i]);
-    W3[i] = rnd<__nv_bfloat16>(wts[kOffW3 + i]);
+                      int L, int cpb, const float *__restrict__ dscale, Tout *__restrict__ out) {
+  extern __shared__ __align__(16) float sm[];
+  // weights per channel as float4, channel 8q + t at 9q + t (no bank conflicts across q)
+  float4 *Mw4 = reinterpret_cast<float4 *>(sm);          // (w_c, w_e, w_d, 0)
+  float4 *W34 = Mw4 + 36;                                // (W3[0][ch][0..2], 0)
+  int *snb = reinterpret_cast<int *>(W34 + 36);          // [cpb][8] edge, corner neighbours
+  float *h3 = reinterpret_cast<float *>(snb + 8 * cpb);  // [cpb][L + 2][36]
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const int w = 9 * (tid >> 3) + (tid & 7);
+    const float *m = wts + kOffM + 3 * tid, *w3 = wts + kOffW3 + 3 * tid;
+    Mw4[w] = make_float4(rnd<__nv_bfloat16>(m[0]), rnd<__nv_bfloat16>(m[1]), rnd<__nv_bfloat16>(m[2]), 0.f);
+    W34[w] = make_float4(rnd<__nv_bfloat16>(w3[0]), rnd<__nv_bfloat16>(w3[1]), rnd<__nv_bfloat16>(w3[2]), 0.f);
   }
-  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0), ncl = nc * L;
-  if ((int)threadIdx.x < nc) {
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+  if (tid < nc) {
     int e[4], d[4];
-    nb.get(c0 + threadIdx.x, e, d);
+    nb.get(c0 + tid, e, d);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { snb[8 * threadIdx.x + q] = e[q]; snb[8 * threadIdx.x + 4 + q] = d[q]; }
+    for (int q = 0; q < 4; ++q) { snb[8 * tid + q] = e[q]; snb[8 * tid + 4 + q] = d[q]; }
   }
+  for (int e = tid; e < cpb * 72; e += blockDim.x) {   // the pad rows
+    const int cc = e / 72, r = e % 72;
+    h3[(cc * (L + 2) + (r < 36 ? 0 : L + 1)) * 36 + r % 36] = 0.f;
+  }
+  // one (cell, channel group) per thread: the host launches at least 4 L cpb threads
+  const int j = tid >> 2, q = tid & 3;
+  const bool act = j < nc * L;
+  const int cc = act ? j / L : 0, k = j - cc * L;
   __syncthreads();
-  const uint4 *hv = reinterpret_cast<const uint4 *>(h2);   // [ncell][4]
-  auto add8 = [](float *acc, uint4 u) {
-    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+  float *row = h3 + (cc * (L + 2) + k + 1) * 36 + 8 * q;
+  if (act) {
+    const int *nbr = snb + 8 * cc;
+    const unsigned own = (unsigned)(c0 + cc), L4 = 4u * (unsigned)L;
+    const uint4 *hv = reinterpret_cast<const uint4 *>(h2) + (4u * (unsigned)k + q);   // + column * 4 L
+    uint4 v[9];
+    v[0] = hv[own * L4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[p]));
-      acc[2 * p] += f.x;
-      acc[2 * p + 1] += f.y;
-    }
-  };
-  // warp-uniform passes (the shuffles below need every lane)
-  for (int base = 0; base < 4 * ncl; base += blockDim.x) {
-    const int i = base + threadIdx.x, j = i >> 2, q = i & 3;
-    if (j < ncl) {
-      const int cc = j / L, k = j - cc * L;
-      const int *nbr = snb + 8 * cc;
-      // all nine loads issued before any use (a missing neighbour reads the cell itself and is
-      // dropped below), so that they are in flight together
-      const int own = c0 + cc;
-      uint4 v[9];
-      v[0] = hv[((int64_t)own * L + k) * 4 + q];
+    for (int s = 0; s < 8; ++s) v[1 + s] = hv[(nbr[s] >= 0 ? (unsigned)nbr[s] : own) * L4];
+    auto pair = [](const uint4 &u, int p) {
+      const uint32_t w = p == 0 ? u.x : p == 1 ? u.y : p == 2 ? u.z : u.w;
+      return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+    };
+    float hq[8];
 #pragma unroll
-      for (int s = 0; s < 8; ++s) v[1 + s] = hv[((int64_t)(nbr[s] >= 0 ? nbr[s] : own) * L + k) * 4 + q];
-      float self[8], se[8], sd[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) self[t] = se[t] = sd[t] = 0.f;
-      add8(self, v[0]);
+    for (int p = 0; p < 4; ++p) {   // channels 8q + 2p, 8q + 2p + 1
+      float2 se = make_float2(0.f, 0.f), sd = make_float2(0.f, 0.f);
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        if (nbr[s] >= 0) add8(se, v[1 + s]);
-        if (nbr[4 + s] >= 0) add8(sd, v[5 + s]);
+        if (nbr[s] >= 0) se = __fadd2_rn(se, pair(v[1 + s], p));
+        if (nbr[4 + s] >= 0) sd = __fadd2_rn(sd, pair(v[5 + s], p));
       }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int ch = 8 * q + t;
-        const float a = fmaf(Mw[3 * ch], self[t], fmaf(Mw[3 * ch + 1], se[t], Mw[3 * ch + 2] * sd[t]));
-        h3[j * 33 + ch] = rnd<__nv_bfloat16>(fmaxf(a, 0.f));
-      }
+      const float4 ma = Mw4[9 * q + 2 * p], mb = Mw4[9 * q + 2 * p + 1];
+      float2 a = __fmul2_rn(make_float2(ma.z, mb.z), sd);
+      a = __ffma2_rn(make_float2(ma.y, mb.y), se, a);
+      a = __ffma2_rn(make_float2(ma.x, mb.x), pair(v[0], p), a);
+      const float2 r = __bfloat1622float2(__floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)));
+      hq[2 * p] = r.x;
+      hq[2 * p + 1] = r.y;
     }
+    reinterpret_cast<float4 *>(row)[0] = make_float4(hq[0], hq[1], hq[2], hq[3]);
+    reinterpret_cast<float4 *>(row)[1] = make_float4(hq[4], hq[5], hq[6], hq[7]);
   }
+  const float dsc = act && q == 0 ? dscale[(int64_t)c0 * L + j] : 0.f;   // in flight across the barrier
   __syncthreads();
-  for (int base = 0; base < 4 * ncl; base += blockDim.x) {
-    const int i = base + threadIdx.x, j = i >> 2, q = i & 3;
-    float y = 0.f;
-    int k = 0;
-    if (j < ncl) {
-      k = j % L;
-      const float *hm = h3 + max(j - 1, 0) * 33, *h0 = h3 + j * 33, *hp = h3 + min(j + 1, ncl - 1) * 33;
+  float y = 0.f;
+  if (act) {
+    float xm[8], x0[8], xp[8];
+    const float4 *rm = reinterpret_cast<const float4 *>(row - 36), *r0 = reinterpret_cast<const float4 *>(row),
+                 *rp = reinterpret_cast<const float4 *>(row + 36);
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int ch = 8 * q + t;
-        const float xm = k > 0 ? hm[ch] : 0.f, xp = k + 1 < L ? hp[ch] : 0.f;
-        y = fmaf(W3[3 * ch], xm, fmaf(W3[3 * ch + 1], h0[ch], fmaf(W3[3 * ch + 2], xp, y)));
-      }
+    for (int h = 0; h < 2; ++h) {
+      const float4 a = rm[h], b = r0[h], c = rp[h];
+      xm[4 * h] = a.x; xm[4 * h + 1] = a.y; xm[4 * h + 2] = a.z; xm[4 * h + 3] = a.w;
+      x0[4 * h] = b.x; x0[4 * h + 1] = b.y; x0[4 * h + 2] = b.z; x0[4 * h + 3] = b.w;
+      xp[4 * h] = c.x; xp[4 * h + 1] = c.y; xp[4 * h + 2] = c.z; xp[4 * h + 3] = c.w;
     }
-    y += __shfl_xor_sync(0xffffffffu, y, 1);
-    y += __shfl_xor_sync(0xffffffffu, y, 2);
-    if (j < ncl && q == 0) {
-      const int64_t K = (int64_t)c0 * L + j;
-      const float s = rsqrtf(diagH ? (float)diagH[K] : diagH32 ? diagH32[K] : 1.f);
-      out[K] = (Tout)((double)y * (double)s);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const float4 w = W34[9 * q + t];
+      y = fmaf(w.x, xm[t], fmaf(w.y, x0[t], fmaf(w.z, xp[t], y)));
     }
   }
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  if (act && q == 0) out[(int64_t)c0 * L + j] = (Tout)(y * dsc);
 }
 
 // ---- forward, horizontal mix and output layer: h2 -> h3 -> y ---------------------------------
@@ -757,7 +766,12 @@ __global__ void gather_samples_kernel(const float *__restrict__ x, const float *
 // ---- host side ---------------------------------------------------------------------------------
 static int front_smem(int cpb, int L) { return (96 + 3072 + cpb * (L + 2) + cpb * kCh * (L + 2)) * 4; }
 static int back_smem(int cpb, int L) { return (96 + 96 + cpb * kCh * (L + 2)) * 4; }
-static int mix_smem(int cpb, int L) { return (96 + 96 + 8 * cpb + cpb * L * 33) * 4; }
+static int mix_smem(int cpb, int L) { return (2 * 36 * 4 + 8 * cpb + cpb * (L + 2) * 36) * 4; }
+// diag(H)^-1/2 in FP32 per cell, passed from the tensor-core front kernel to the output layer:
+// the activation buffer (sized for 32 FP32 channels) after the 32 BF16 channels of h2
+static float *tc_dscale(Ctx *c) {
+  return reinterpret_cast<float *>(static_cast<char *>(c->nn_act) + (size_t)64 * c->lv[0].ncell);
+}
 static int bwd1_smem(int L) { return (3072 + 3 * kCh * (L + 2) + (L + 2)) * 4; }
 constexpr int kNnCpb = 4;
 
@@ -781,10 +795,11 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
     static_assert(!TC || sizeof(A) == 2, "the tensor-core layers store BF16");
     nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
     const int64_t nrows = (int64_t)f.ncol * (L + 2);   // padded rows
-    if (nrows > INT32_MAX - 2 * kTcM) return fail(c, HMG_ERR_INVALID_ARG, "mesh too large for the tensor-core layer");
+    if (nrows > INT32_MAX - 2 * kTcM || 4 * f.ncell >= (int64_t)UINT32_MAX)
+      return fail(c, HMG_ERR_INVALID_ARG, "mesh too large for the tensor-core layers");
     nn_front_tc_kernel<Tin><<<grid_for(nrows, kTcM), 128, kTcSmem, c->stream>>>(
         c->nn_w, static_cast<const __nv_bfloat16 *>(c->nn_bimg), bbar, dH, dH32, f.ncol, L,
-        reinterpret_cast<__nv_bfloat16 *>(h2), c->state + 3);
+        reinterpret_cast<__nv_bfloat16 *>(h2), tc_dscale(c), c->state + 3);
   } else {
     nn_front_kernel<A, Tin><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, bbar, dH, dH32, f.ncol, L,
                                                                           kNnCpb, nullptr, h2);
@@ -794,7 +809,7 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
     const int cpb = std::max(1, 64 / L), thr = (4 * cpb * L + 31) / 32 * 32;
     const unsigned gm = (unsigned)((f.ncol + cpb - 1) / cpb);
     nn_mix_out_kernel<Tout><<<gm, thr, mix_smem(cpb, L), c->stream>>>(
-        c->nn_w, reinterpret_cast<const __nv_bfloat16 *>(h2), nb, f.ncol, L, cpb, dH, dH32, out);
+        c->nn_w, reinterpret_cast<const __nv_bfloat16 *>(h2), nb, f.ncol, L, cpb, tc_dscale(c), out);
   } else {
     nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
         c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
