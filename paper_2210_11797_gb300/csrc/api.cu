@@ -647,6 +647,7 @@ int hmg_set_coarse_model(hmg_ctx *c, const float *params, int32_t n) {
   if (!params || n != kCoarseParams) return fail(c, HMG_ERR_INVALID_ARG, "params must hold hmg_coarse_model_size() floats");
   if ((st = nn_setup(c))) return st;
   HMG_CUDA(c, cudaMemcpyAsync(c->nn_w, params, sizeof(float) * kCoarseParams, cudaMemcpyHostToDevice, c->stream));
+  if ((st = nn_pack_weights(c))) return st;
   return finish(c, HMG_OK);
 }
 

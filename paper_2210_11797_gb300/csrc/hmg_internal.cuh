@@ -285,6 +285,7 @@ void drop_graph(Ctx *c);
 // ---- learned coarse correction (learned.cu) ---------------------------------------------
 constexpr int kCoarseParams = 3360;
 int nn_setup(Ctx *c);
+int nn_pack_weights(Ctx *c);
 template <typename T>
 int learned_coarse(Ctx *c, const T *bbar, T *out);
 // mode 0: BF16 on the tensor cores (the solver's form); 1: FP32 and 2: BF16 on the CUDA cores

@@ -793,7 +793,6 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
   const unsigned g = (unsigned)((f.ncol + kNnCpb - 1) / kNnCpb);
   if (TC) {
     static_assert(!TC || sizeof(A) == 2, "the tensor-core layers store BF16");
-    nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
     const int64_t nrows = (int64_t)f.ncol * (L + 2);   // padded rows
     if (nrows > INT32_MAX - 2 * kTcM || 4 * f.ncell >= (int64_t)UINT32_MAX)
       return fail(c, HMG_ERR_INVALID_ARG, "mesh too large for the tensor-core layers");
@@ -814,6 +813,15 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
     nn_back_kernel<A, Tout><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
         c->nn_w, h2, nb, f.ncol, L, kNnCpb, dH, dH32, out, nullptr, nullptr, nullptr, 1, 1.f, nullptr, nullptr);
   }
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
+// The tensor-core layer's B operand from the FP32 weights; run wherever the weights change
+// (set, or an optimiser step), so that the forward pass, also when captured in a graph, reads
+// an image that matches them.
+int nn_pack_weights(Ctx *c) {
+  nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -1004,6 +1012,7 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
       ++step;
       adam_kernel<<<grid_for(kNParams, 256), 256, 0, c->stream>>>(c->nn_w, c->train.grad, c->train.m, c->train.v,
                                                                   kNParams, (float)lr, 0.9f, 0.999f, 1e-8f, step);
+      if ((st = nn_pack_weights(c))) return st;
       double l = 0.0;
       HMG_CUDA(c, cudaMemcpyAsync(&l, c->train.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       HMG_CUDA(c, cudaStreamSynchronize(c->stream));
