@@ -84,6 +84,30 @@ def test_forward_matches_oracle(name):
     np.testing.assert_array_equal(gpu.get_coarse_model(), I.flatten_coarse_model(params))
 
 
+@pytest.mark.parametrize("n,nlev", [(5, 7), (6, 1), (3, 45)])
+def test_tensor_core_forward_ragged_tiles(n, nlev):
+    """The tensor-core layer tiles the padded rows (L + 2 per column) by 128, and the mix
+    kernel takes whole columns per block: a last tile cut short, columns straddling tiles,
+    a ragged last block, a single level and a column longer than a third of a tile, against
+    the oracle and the BF16 CUDA-core form."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz(n=n, nlev=nlev, nmg=1)
+    ora = HybridSolver(w.hier, w.coeffs)
+    gpu = Solver(w.hier, w.coeffs, tol=w.tol)
+    try:
+        params = I.coarse_model_init(9)
+        gpu.set_coarse_model(I.flatten_coarse_model(params))
+        b = I.normal(13, gpu.ncell)
+        ref = _oracle_coarse_model(ora, _rounded(params))(b)
+        outtc = _np(gpu.apply_coarse_model(_cuda(b), mode="tensor"))
+        out16 = _np(gpu.apply_coarse_model(_cuda(b), mode="bf16"))
+        assert np.isfinite(outtc).all()
+        assert np.linalg.norm(outtc - ref) / np.linalg.norm(ref) < 5e-2
+        assert np.linalg.norm(outtc - out16) / np.linalg.norm(out16) < 1e-2
+    finally:
+        gpu.close()
+
+
 def test_gradient_matches_oracle():
     _w, _ora, gpu = _setup("planar16")
     params = I.coarse_model_init(7)
