@@ -143,8 +143,8 @@ constexpr int kTcM = 128;
 constexpr int kTcRows = kTcM + 2;                      // h1 rows of a tile: -1 .. 128
 constexpr int kTcLbo = kTcRows * 16;                   // bytes between 8-channel groups
 constexpr int kTcB = (4 * kTcLbo + 1023) / 1024 * 1024;   // A: 8,320 B; B from here (6 KB)
-constexpr int kTcX = kTcB + 6 * 1024;                  // x (132 floats), W1 (96 floats)
-constexpr int kTcBar = kTcX + 1024;                    // two mbarriers (16 B), TMEM address (4 B)
+constexpr int kTcX = kTcB + 6 * 1024;                  // x (132 floats), W1 (96), levels (132 ints)
+constexpr int kTcBar = kTcX + 1536;                    // two mbarriers (16 B), TMEM address (4 B)
 constexpr int kTcSmem = kTcBar + 64;
 constexpr uint32_t kTcWaitLimit = 1u << 20;   // mbarrier polls before the kernel gives up
 
@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(128)
   unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
   float *xs = reinterpret_cast<float *>(tc_smem + kTcX);            // 132 floats
   float *w1s = xs + kTcM + 4;                                        // 96 floats
+  int *lev = reinterpret_cast<int *>(w1s + 96);                      // 132 ints: level of x's rows
   uint64_t *bar = reinterpret_cast<uint64_t *>(tc_smem + kTcBar);   // [0] MMA done, [1] B loaded
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tc_smem + kTcBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(128)
   // rows and outside the mesh; the scale of the tile's own rows is kept for the output layer
   for (int j = tid; j < kTcM + 4; j += blockDim.x) {
     const int R = R0 - 2 + j, k = level(R);
+    lev[j] = k;
     float v = 0.f;
     if (k >= 0) {
       const int64_t q = (int64_t)(R / P) * L + k;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(128)
   for (int e = tid; e < 4 * kTcRows; e += blockDim.x) {
     const int row = e % kTcRows, g = e / kTcRows;
     uint4 pack = make_uint4(0u, 0u, 0u, 0u);
-    if (level(R0 - 1 + row) >= 0) {
+    if (lev[row + 1] >= 0) {
       const float xm = xs[row], x0 = xs[row + 1], xp = xs[row + 2];   // zero on pad rows
       uint32_t wds[4];
 #pragma unroll
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(128)
                    "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int R = R0 + warp * 32 + lane, k = level(R);
+    const int R = R0 + warp * 32 + lane, k = lev[warp * 32 + lane + 2];
     if (k >= 0) {   // cell-major: the 32 channels of a cell in 64 contiguous bytes
       const int64_t cell = (int64_t)(R / P) * L + k;
       uint32_t wd[16];
