@@ -60,14 +60,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def sweep_coeffs(mesh):
+    """Coefficients of S one full line-smoother sweep reads: all 11 of a lambda^h row; on a
+    lambda^z row only the 8 couplings outside its column's tridiagonal block S^zz (4 on the
+    ground and lid rows), whose inverse enters through the Thomas factors."""
+    return 11 * mesh.n_trace_h + 8 * mesh.nlev * mesh.ncol
+
+
 def sweep_bytes(mesh, elem=8):
-    """Algorithmic bytes of one full line-smoother sweep (Algorithm 1, fused residual):
-    every nonzero of S once, lambda_in, b and lambda_out once, the three Thomas factors of
-    each lambda^z row (omega/pivot, sub/pivot, sup/pivot), omega/diag of each lambda^h row,
-    and the index tables."""
-    L, NH, NZ, T = mesh.nlev, mesh.n_trace_h, mesh.n_trace_z, mesh.n_trace
-    nnz = 11 * NH + mesh.ncol * (11 * (L - 1) + 2 * 6)
-    return elem * (nnz + 3 * T + 3 * NZ + NH) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
+    """Algorithmic bytes of one full line-smoother sweep (Algorithm 1, fused residual): the
+    coefficients of S it reads (sweep_coeffs), lambda_in, b and lambda_out once, the three
+    Thomas factors of each lambda^z row (omega/pivot, sub/pivot, sup/pivot), omega/diag of each
+    lambda^h row, and the index tables."""
+    NH, NZ, T = mesh.n_trace_h, mesh.n_trace_z, mesh.n_trace
+    return elem * (sweep_coeffs(mesh) + 3 * T + 3 * NZ + NH) + 4 * (8 * mesh.nedge + 4 * mesh.ncol)
 
 
 def solve_bytes(hier, iterations, elem=8):
@@ -76,20 +82,22 @@ def solve_bytes(hier, iterations, elem=8):
     arrays in `elem` bytes (4 with the FP32 preconditioner) and the Krylov vectors in 8:
       B_lambda: A_K^-1 (49 C) + R (7 C) + B (T); initialisation 6 T;
       per iteration: 2 S applies, 2 preconditioner applications, 15 T of vector updates;
-      preconditioner: presmooth from zero (b, factors, out), residual (S, lambda, b, R),
-      restriction (R, Gamma, bbar), one V-cycle (per level 42.5 C_l: smoother from zero 5,
-      residual + restriction 9.25, injection 2.25, two smoothers 26; coarsest 5 + 2 x 13; the
-      finest level's zero-start sweep runs inside the restriction kernel, so bbar is not
-      read back: minus C),
+      preconditioner: presmooth from zero (b, factors, out), residual after it (the
+      couplings of S outside the smoother's diagonal blocks, lambda, b, R), restriction
+      (R, Gamma, bbar), one V-cycle (per level 33.5 C_l: smoother from zero 5, residual
+      (horizontal part of H) + restriction 6.25, injection 2.25, two smoothers 20 (horizontal
+      part of H, b, x, three factors, out); coarsest 5 + 2 x 10; the finest level's
+      zero-start sweep runs inside the restriction kernel, so bbar is not read back: minus C),
       prolongation (2 T + C), two full sweeps; the final residual: nnz + 2 T."""
     f = hier.meshes[0]
     L, NH, NZ, T, C = f.nlev, f.n_trace_h, f.n_trace_z, f.n_trace, f.ncell
     nnz = 11 * NH + f.ncol * (11 * (L - 1) + 2 * 6)
+    off = 10 * NH + 8 * L * f.ncol                              # S minus the smoother's blocks
     tables = 4 * (8 * f.nedge + 4 * f.ncol)
     cells = [m.ncell for m in hier.meshes]
-    vcycle = elem * (sum(42.5 * c for c in cells[:-1]) + 31.0 * cells[-1])
+    vcycle = elem * (sum(33.5 * c for c in cells[:-1]) + 25.0 * cells[-1])
     precond = (8 * T + elem * (3 * NZ + NH + T)                 # presmooth from zero
-               + elem * (nnz + 2 * T) + 8 * T + tables          # residual
+               + elem * (off + 2 * T) + 8 * T + tables          # residual
                + elem * (T + 2 * C)                             # restriction with Gamma
                + vcycle - elem * C
                + elem * (2 * T + C)                             # prolongation

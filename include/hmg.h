@@ -300,11 +300,14 @@ int hmg_line_smooth(hmg_ctx *ctx, const double *b, double *lambda, int32_t nswee
  * The second vector of the ping-pong comes from an 8 MiB array compiled into the library
  * (held by every GPU that loads it until the process exits), so ntrace must be at most
  * 1048576; a larger mesh gets HMG_ERR_INVALID_ARG. The call allocates nothing: no
- * cudaMalloc, cudaFree or allocating library routine. The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. All calls in the process share the one array and it keeps the last
- * call's contents (nothing in it needs to start at zero), so calls whose GPU work overlaps
- * in time, on any streams or contexts of the same device, race and give wrong results. */
+ * cudaMalloc, cudaFree or allocating library routine. hmg_assemble_trace (set-up, with the
+ * context's device current) looks up the array's device address with cudaGetSymbolAddress
+ * and keeps it in the context; that lookup also loads the library code holding the array, so
+ * the array's memory is taken then, not during a call of this function. The address is as
+ * valid as the context's own buffers: after a cudaDeviceReset, destroy the context and build
+ * a new one. All calls in the process share the one array and it keeps the last call's
+ * contents (nothing in it needs to start at zero), so calls whose GPU work overlaps in time,
+ * on any streams or contexts of the same device, race and give wrong results. */
 int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *lambda, int32_t nsweeps);
 
 /* y = H_l x on multigrid level l (Eq. elliptic_pressure_system), FP64, [ncell_l]. */
@@ -357,7 +360,10 @@ int hmg_get_coarse_model(hmg_ctx *ctx, float *params, int32_t n);
 /* out = D^-1/2 f(D^-1/2 bbar) on the finest mesh; bbar, out [ncell] device FP64. mode 0: the
  * solver's form, the 32 -> 32 convolution on the tensor cores (tcgen05.mma, BF16 operands,
  * FP32 accumulator in tensor memory); 1: FP32 on the CUDA cores; 2: BF16 storage on the CUDA
- * cores. Returns HMG_ERR_TIMEOUT if a bounded wait for the tensor cores ran out. */
+ * cores. Returns HMG_ERR_TIMEOUT if a bounded wait for the tensor cores ran out; the output
+ * of that call (or of the solve in which it happened) is then undefined, and the context runs
+ * the network's column layers in the mode-2 form (BF16 on the CUDA cores) for the rest of its
+ * life, in this call's mode 0 and inside solves alike. */
 int hmg_apply_coarse_model(hmg_ctx *ctx, const double *bbar, double *out, int32_t mode);
 
 /* Training samples are nx x ny patches of columns (column q = j nx + i of a patch, the
@@ -373,6 +379,16 @@ int hmg_coarse_model_grad(hmg_ctx *ctx, const float *x, const float *t, int32_t 
 int hmg_train_coarse_model(hmg_ctx *ctx, const float *x, const float *t, int32_t nsamp, int32_t nx,
                            int32_t ny, int32_t batch, int32_t epochs, double lr, uint64_t seed,
                            double *loss_hist);
+
+/* One step of Adam (Kingma & Ba 2015, with bias correction) on n FP32 values, by the same
+ * kernel hmg_train_coarse_model runs after each minibatch: m = beta1 m + (1 - beta1) g,
+ * v = beta2 v + (1 - beta2) g^2, w -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step))
+ * + eps) in FP32, with 1 - beta1, 1 - beta2 and the two bias corrections 1 / (1 - beta^step)
+ * formed on the host in FP64 and rounded once. w, m, v (updated in place) and grad are device arrays of n floats on
+ * the context's device; step >= 1 is the step number after this update. For checking the
+ * optimiser against a reference (the training itself keeps its moments internally). */
+int hmg_adam_step(hmg_ctx *ctx, float *w, const float *grad, float *m, float *v, int32_t n, int32_t step,
+                  double lr, double beta1, double beta2, double eps);
 
 /* One solve (FP64, HMG_PRECOND_NONNESTED, host-driven loop) that also records, at each of its
  * first max_pairs preconditioner applications, the pair x = D^-1/2 bbar and

@@ -21,6 +21,14 @@ problem), so the learned map is f_H(b) = D^-1/2 f(D^-1/2 b) with D = diag(H).
 
 Flexible GMRES (Saad 2003 Alg. 9.6, restart m) allows the preconditioner to change between
 steps (a network is not a fixed linear operator).
+
+Storage precision: the network is specified with BF16 weights and activations and FP32
+accumulation. `forward` and `loss_and_grad` take quant="bf16" to round, to the nearest BF16
+value (ties to even), exactly the quantities that are stored in that format: the weights,
+the input and the activations h1, h2, h3 after their ReLU. Everything else stays FP64, so
+the result is the exact gradient of the network whose stored values are BF16; a BF16
+implementation that accumulates in FP32 differs from it only by its FP32 roundings (and
+the few stored values those move across a BF16 rounding boundary).
 """
 from __future__ import annotations
 
@@ -39,6 +47,24 @@ def init_params(seed: int = 0, ch: int = CHANNELS) -> dict:
         "M": np.stack([np.ones(ch), 0.1 * np.ones(ch), 0.05 * np.ones(ch)], axis=1),  # (w_c, w_e, w_d)
         "W3": rng.standard_normal((1, ch, 3)) * np.sqrt(1.0 / (3.0 * ch)),
     }
+
+
+def round_bf16(a) -> np.ndarray:
+    """Round to the nearest BF16 value (8 significant bits, the exponent range of FP32), ties
+    to even, returned in FP64. The value is first rounded to FP32 (the accumulation format),
+    then the low 16 bits of its FP32 pattern are rounded away. Finite inputs only."""
+    f = np.ascontiguousarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _storage(quant):
+    if quant is None:
+        return lambda a: a
+    if quant == "bf16":
+        return round_bf16
+    raise ValueError(quant)
 
 
 def conv1d(W: np.ndarray, x: np.ndarray) -> np.ndarray:
@@ -95,36 +121,43 @@ def hmix_backward(M, h, edge, diag, gout):
     return gM, gh
 
 
-def forward(params: dict, x: np.ndarray, edge: np.ndarray, diag: np.ndarray, keep: bool = False):
-    """x [ncol, L] -> y [ncol, L]."""
-    a1 = conv1d(params["W1"], x[:, None, :])
-    h1 = np.maximum(a1, 0.0)
-    a2 = conv1d(params["W2"], h1)
-    h2 = np.maximum(a2, 0.0)
-    a3 = hmix(params["M"], h2, edge, diag)
-    h3 = np.maximum(a3, 0.0)
-    y = conv1d(params["W3"], h3)[:, 0, :]
+def forward(params: dict, x: np.ndarray, edge: np.ndarray, diag: np.ndarray, keep: bool = False,
+            quant=None):
+    """x [ncol, L] -> y [ncol, L]. quant="bf16": weights, input and activations stored in
+    BF16 (see the module docstring)."""
+    q = _storage(quant)
+    W = {k: q(v) for k, v in params.items()}
+    x = q(x)
+    a1 = conv1d(W["W1"], x[:, None, :])
+    h1 = q(np.maximum(a1, 0.0))
+    a2 = conv1d(W["W2"], h1)
+    h2 = q(np.maximum(a2, 0.0))
+    a3 = hmix(W["M"], h2, edge, diag)
+    h3 = q(np.maximum(a3, 0.0))
+    y = conv1d(W["W3"], h3)[:, 0, :]
     if keep:
-        return y, dict(x=x, a1=a1, h1=h1, a2=a2, h2=h2, a3=a3, h3=h3)
+        return y, dict(x=x, a1=a1, h1=h1, a2=a2, h2=h2, a3=a3, h3=h3, W=W)
     return y
 
 
-def loss_and_grad(params, x, target, edge, diag):
+def loss_and_grad(params, x, target, edge, diag, quant=None):
     """Relative squared error per sample summed: sum_s ||f(x_s) - t_s||^2 / ||t_s||^2 over the
     samples (the columns of one sample share a sample id in `sample`). Here one call is one
-    sample: x, target [ncol, L]."""
-    y, t = forward(params, x, edge, diag, keep=True)
+    sample: x, target [ncol, L]. With quant="bf16" the gradient is that of the network with
+    BF16 storage, taken at the stored (rounded) weights and activations."""
+    y, t = forward(params, x, edge, diag, keep=True, quant=quant)
+    W = t["W"]
     denom = np.sum(target * target)
     r = y - target
     loss = np.sum(r * r) / denom
     gy = 2.0 * r / denom
-    gW3, gh3 = conv1d_backward(params["W3"], t["h3"], gy[:, None, :])
+    gW3, gh3 = conv1d_backward(W["W3"], t["h3"], gy[:, None, :])
     ga3 = gh3 * (t["a3"] > 0)
-    gM, gh2 = hmix_backward(params["M"], t["h2"], edge, diag, ga3)
+    gM, gh2 = hmix_backward(W["M"], t["h2"], edge, diag, ga3)
     ga2 = gh2 * (t["a2"] > 0)
-    gW2, gh1 = conv1d_backward(params["W2"], t["h1"], ga2)
+    gW2, gh1 = conv1d_backward(W["W2"], t["h1"], ga2)
     ga1 = gh1 * (t["a1"] > 0)
-    gW1, _gx = conv1d_backward(params["W1"], x[:, None, :], ga1)
+    gW1, _gx = conv1d_backward(W["W1"], t["x"][:, None, :], ga1)
     return loss, {"W1": gW1, "W2": gW2, "M": gM, "W3": gW3}
 
 

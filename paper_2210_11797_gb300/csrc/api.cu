@@ -375,6 +375,7 @@ int hmg_assemble_trace(hmg_ctx *c) {
     c->cb = tmp;
     if ((st = dev_alloc(c, &c->host_in, (size_t)7 * f.ncell + T))) return st;
   }
+  if (!c->noalloc_scratch && (st = noalloc_setup(c))) return st;
   c->assembled = true;
   return HMG_OK;
 }
@@ -666,7 +667,9 @@ int hmg_apply_coarse_model(hmg_ctx *c, const double *bbar, double *out, int32_t 
   if (!bbar || !out || bbar == out || mode < 0 || mode > 2) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
   if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
   if ((st = finish(c, apply_coarse_model(c, bbar, out, mode)))) return st;
-  return check_wait_flag(c);
+  st = check_wait_flag(c);
+  if (st == HMG_ERR_TIMEOUT && mode == 0) c->nn_tc_off = true;   // see hmg_apply_coarse_model
+  return st;
 }
 
 static int check_patches(hmg_ctx *c, const float *x, const float *t, int32_t nsamp, int32_t nx, int32_t ny) {
@@ -693,6 +696,16 @@ int hmg_train_coarse_model(hmg_ctx *c, const float *x, const float *t, int32_t n
   if ((st = check_patches(c, x, t, nsamp, nx, ny))) return st;
   if (batch < 1 || batch > nsamp || epochs < 0 || !(lr > 0.0)) return fail(c, HMG_ERR_INVALID_ARG, "bad training settings");
   return train_coarse_model(c, x, t, nsamp, nx, ny, batch, epochs, lr, seed, loss_hist);
+}
+
+int hmg_adam_step(hmg_ctx *c, float *w, const float *grad, float *m, float *v, int32_t n, int32_t step,
+                  double lr, double beta1, double beta2, double eps) {
+  if (!c) return HMG_ERR_INVALID_ARG;
+  if (!w || !grad || !m || !v || n < 1 || step < 1 || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) ||
+      !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return fail(c, HMG_ERR_INVALID_ARG, "bad Adam arguments");
+  HMG_CUDA(c, cudaSetDevice(c->device));
+  return finish(c, adam_update(c, w, grad, m, v, n, step, lr, beta1, beta2, eps));
 }
 
 int hmg_collect_coarse_pairs(hmg_ctx *c, const double *Rub, const double *Rpi, double *lambda, int32_t max_pairs,

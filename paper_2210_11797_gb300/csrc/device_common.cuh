@@ -207,6 +207,65 @@ __device__ __forceinline__ TA s_row_z(const TS *__restrict__ S, const TX *__rest
   return acc;
 }
 
+// The same rows without the couplings of the smoother's diagonal block D (Algorithm 1:
+// D = [diag(S^hh), blockdiag(S^zz_c)]): an h-row without its diagonal (slots 1-10), a z-row
+// without the diagonal and its vertical neighbours (slots 1-4 and 6-9), acc - (S - D) x.
+template <typename TS, typename TX, typename TA>
+__device__ __forceinline__ TA s_row_h_off(const TS *__restrict__ S, const TX *__restrict__ x,
+                                          const int32_t *__restrict__ stencil, const TraceDims d,
+                                          int64_t row, TA acc) {
+  const int e = (int)(row / d.L);
+  const int k = (int)(row - (int64_t)e * d.L);
+  const int32_t *st = stencil + 8 * (int64_t)e;
+  const int c1 = __ldg(st + 0), c2 = __ldg(st + 1);
+  const int64_t z1 = d.NH + (int64_t)c1 * (d.L + 1) + k;
+  const int64_t z2 = d.NH + (int64_t)c2 * (d.L + 1) + k;
+  const int64_t T = d.NT;
+  auto term = [&](int slot, int64_t col) {
+    const TA a = (TA)__ldcs(S + slot * T + row);
+    acc = fma(-a, (TA)ld(x + col), acc);
+  };
+  term(1, (int64_t)__ldg(st + 2) * d.L + k);
+  term(2, (int64_t)__ldg(st + 3) * d.L + k);
+  term(3, (int64_t)__ldg(st + 4) * d.L + k);
+  term(4, z1);
+  term(5, z1 + 1);
+  term(6, (int64_t)__ldg(st + 5) * d.L + k);
+  term(7, (int64_t)__ldg(st + 6) * d.L + k);
+  term(8, (int64_t)__ldg(st + 7) * d.L + k);
+  term(9, z2);
+  term(10, z2 + 1);
+  return acc;
+}
+
+template <typename TS, typename TX, typename TA>
+__device__ __forceinline__ TA s_row_z_off(const TS *__restrict__ S, const TX *__restrict__ x,
+                                          const int32_t *__restrict__ col_edges, const TraceDims d,
+                                          int64_t row, TA acc) {
+  const int64_t zr = row - d.NH;
+  const int c = (int)(zr / (d.L + 1));
+  const int k = (int)(zr - (int64_t)c * (d.L + 1));
+  const int64_t T = d.NT;
+  const int32_t *ce = col_edges + 4 * (int64_t)c;
+  auto term = [&](int slot, int64_t col) {
+    const TA a = (TA)__ldcs(S + slot * T + row);
+    acc = fma(-a, (TA)ld(x + col), acc);
+  };
+  if (k < d.L) {
+    term(1, (int64_t)__ldg(ce + 0) * d.L + k);
+    term(2, (int64_t)__ldg(ce + 1) * d.L + k);
+    term(3, (int64_t)__ldg(ce + 2) * d.L + k);
+    term(4, (int64_t)__ldg(ce + 3) * d.L + k);
+  }
+  if (k > 0) {
+    term(6, (int64_t)__ldg(ce + 0) * d.L + k - 1);
+    term(7, (int64_t)__ldg(ce + 1) * d.L + k - 1);
+    term(8, (int64_t)__ldg(ce + 2) * d.L + k - 1);
+    term(9, (int64_t)__ldg(ce + 3) * d.L + k - 1);
+  }
+  return acc;
+}
+
 template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row(const TS *__restrict__ S, const TX *__restrict__ x,
                                     const int32_t *__restrict__ stencil,

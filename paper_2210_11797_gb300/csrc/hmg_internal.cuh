@@ -148,12 +148,18 @@ struct Ctx {
   void *nn_bimg = nullptr;        // W2 as the BF16 B operand image of the tensor-core layer (6 KB)
   TrainBufs train;
   bool coarse_fallback = false;   // set by the flexible Krylov loop when it stalls
+  // set when a bounded wait of the tensor-core network layer ran out: from then on the
+  // context runs those layers in BF16 on the CUDA cores (same arithmetic up to summation order)
+  bool nn_tc_off = false;
   // collection of (scaled bbar, scaled H^-1 bbar) pairs at the preconditioner calls
   float *collect_x = nullptr, *collect_t = nullptr;
   int collect_max = 0, collect_n = 0;
   double *collect_r = nullptr, *collect_e = nullptr, *collect_y = nullptr;
   double *ck = nullptr;           // [9][ncell] work vectors of the Krylov coarse solve
   unsigned int *mg_bar = nullptr; // grid barrier of the cooperative coarse-level kernel
+  // device address of the allocation-free sweep's built-in scratch array (trace_ops.cu),
+  // looked up once by hmg_assemble_trace
+  double *noalloc_scratch = nullptr;
   int num_sms = 0;
   int wave_blocks[3] = {0, 0, 0};   // resident blocks (all SMs) of the BiCGStab vector kernels
   // configuration 1 (mixed.cu): the 2x2 operator (velocity block in the 11-slot layout of S,
@@ -251,6 +257,8 @@ int launch_reconstruct(Ctx *c, const double *lam, const double *Rub, const doubl
 // preconditioners: z = M^-1 r, r and z FP64 Krylov vectors
 int precond_apply(Ctx *c, const double *r, double *z);
 int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps);
+// looks up the device address of the allocation-free sweep's scratch array (set-up)
+int noalloc_setup(Ctx *c);
 int pressure_vcycle_fp64(Ctx *c, const double *b, double *x);
 int apply_pressure_fp64(Ctx *c, int level, const double *x, double *y);
 
@@ -294,6 +302,9 @@ int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx,
                       float *grad_host, double *loss_host);
 int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx, int ny, int batch,
                        int epochs, double lr, uint64_t seed, double *loss_hist);
+// one Adam step (the training's own kernel) on n FP32 weights: w, m, v updated in place
+int adam_update(Ctx *c, float *w, const float *g, float *m, float *v, int n, int step, double lr, double b1,
+                double b2, double eps);
 int extract_patches(Ctx *c, const float *xs, const float *ts, int64_t ncell, const int32_t *pair,
                     const int32_t *cols, int npatch, int P, float *xo, float *to);
 // launches a kernel whose bounded mbarrier wait must run out (sets state[3])

@@ -458,6 +458,9 @@ static int fill_stats(Ctx *c, hmg_solve_stats *st, float ms) {
   if (c->state_host[kWaitFlag]) {   // a bounded device-side wait ran out during the solve
     HMG_CUDA(c, cudaMemsetAsync(c->state + kWaitFlag, 0, sizeof(int), c->stream));
     status = HMG_ERR_TIMEOUT;
+    // with a learned coarse solve the wait may have been the tensor-core layer's: the context
+    // runs the network on the CUDA cores from now on
+    if (c->opt.coarse == HMG_COARSE_LEARNED || c->opt.coarse == HMG_COARSE_LEARNED_VCYCLE) c->nn_tc_off = true;
   }
   if (st) {
     const double bb = c->scal_host[Scal::BB];

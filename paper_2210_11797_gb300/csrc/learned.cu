@@ -280,11 +280,23 @@ __global__ void __launch_bounds__(128)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
     } else {
       atomicExch(wait_flag, 1);
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)));   // release the waiters
+      // the bulk copy of B may still be in flight: wait for it once more (bounded) before the
+      // block releases its shared memory, then release the waiters without any MMA
+      mbar_wait(bar + 1, 0);
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)));
     }
   }
-  const bool done = mbar_wait(bar, 0);
-  if (!done) atomicExch(wait_flag, 1);
+  // one decision for the whole block, so that the warp-collective loads below never diverge
+  const bool done = __syncthreads_and(mbar_wait(bar, 0) ? 1 : 0) != 0;
+  if (!done) {
+    // MMAs may still be writing the accumulator: one more bounded wait for their commit before
+    // the tensor memory is freed (the launch's outputs are undefined either way)
+    if (tid == 0) {
+      atomicExch(wait_flag, 1);
+      mbar_wait(bar, 0);
+    }
+    __syncthreads();
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
     uint32_t r[32];
@@ -682,19 +694,37 @@ __global__ void sum_loss_kernel(const double *__restrict__ part, int n, double *
   }
 }
 
-// Adam (Kingma & Ba 2015) with bias correction on the FP32 master weights.
+// Adam (Kingma & Ba 2015) with bias correction on the FP32 master weights. The scalars that
+// depend only on the hyper-parameters and the step (1 - beta, 1 / (1 - beta^t)) come from the
+// host in FP64, rounded once: formed in FP32 from a rounded beta2 = 0.999, 1 - beta2^t would
+// be off by about 1e-5 relative.
+struct AdamScalars {
+  float lr, b1, b2, omb1, omb2, bc1, bc2, eps;
+};
+
+static AdamScalars adam_scalars(double lr, double b1, double b2, double eps, int t) {
+  return AdamScalars{(float)lr, (float)b1, (float)b2, (float)(1.0 - b1), (float)(1.0 - b2),
+                     (float)(1.0 / (1.0 - std::pow(b1, (double)t))), (float)(1.0 / (1.0 - std::pow(b2, (double)t))),
+                     (float)eps};
+}
+
 __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
-                            float *__restrict__ v, int n, float lr, float b1, float b2, float eps, int t) {
+                            float *__restrict__ v, int n, const AdamScalars a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  const float mi = fmaf(a.b1, m[i], a.omb1 * gi);
+  const float vi = fmaf(a.b2, v[i], a.omb2 * gi * gi);
   m[i] = mi;
   v[i] = vi;
-  const float mh = mi / (1.f - powf(b1, (float)t));
-  const float vh = vi / (1.f - powf(b2, (float)t));
-  w[i] -= lr * mh / (sqrtf(vh) + eps);
+  w[i] -= a.lr * (mi * a.bc1) / (sqrtf(vi * a.bc2) + a.eps);
+}
+
+int adam_update(Ctx *c, float *w, const float *g, float *m, float *v, int n, int step, double lr, double b1,
+                double b2, double eps) {
+  adam_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(w, g, m, v, n, adam_scalars(lr, b1, b2, eps, step));
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
 }
 
 // per-sample ||t_s||^2 of the training targets
@@ -835,6 +865,8 @@ int learned_coarse(Ctx *c, const T *bbar, T *out) {
   const double *dH = nullptr;
   const float *dH32 = nullptr;
   if (sizeof(T) == 8) dH = c->lv[0].H; else dH32 = c->lv[0].H32;   // row 0 of H = its diagonal
+  if (c->nn_tc_off)   // a bounded tensor-core wait ran out earlier: BF16 on the CUDA cores
+    return nn_forward_mesh<__nv_bfloat16, T, T, false>(c, bbar, out, dH, dH32);
   return nn_forward_mesh<__nv_bfloat16, T, T, true>(c, bbar, out, dH, dH32);
 }
 template int learned_coarse<double>(Ctx *, const double *, double *);
@@ -1013,7 +1045,7 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
       if ((st = nn_batch_grad<__nv_bfloat16>(c, xb, tb_, tnb, batch, nx, ny, L, c->train.grad, c->train.loss))) return st;
       ++step;
       adam_kernel<<<grid_for(kNParams, 256), 256, 0, c->stream>>>(c->nn_w, c->train.grad, c->train.m, c->train.v,
-                                                                  kNParams, (float)lr, 0.9f, 0.999f, 1e-8f, step);
+                                                                  kNParams, adam_scalars(lr, 0.9, 0.999, 1e-8, step));
       if ((st = nn_pack_weights(c))) return st;
       double l = 0.0;
       HMG_CUDA(c, cudaMemcpyAsync(&l, c->train.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1059,7 +1091,7 @@ int apply_coarse_model(Ctx *c, const double *bbar, double *out, int mode) {
   int st = nn_setup(c);
   if (st) return st;
   if (mode == 1) return nn_forward_mesh<float, double, double, false>(c, bbar, out, c->lv[0].H, nullptr);
-  if (mode == 2) return nn_forward_mesh<__nv_bfloat16, double, double, false>(c, bbar, out, c->lv[0].H, nullptr);
+  if (mode == 2 || c->nn_tc_off) return nn_forward_mesh<__nv_bfloat16, double, double, false>(c, bbar, out, c->lv[0].H, nullptr);
   return nn_forward_mesh<__nv_bfloat16, double, double, true>(c, bbar, out, c->lv[0].H, nullptr);
 }
 

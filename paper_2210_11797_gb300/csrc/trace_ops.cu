@@ -6,8 +6,6 @@
 // Paper (arXiv 2210.11797): Eqs. hybrid-S, hybrid-rhs, hybrid-recovery (Sec. 2.4);
 // Algorithm 1 and Eq. banded_system; Algorithm 2; Sec. 2.5 intergrid operators
 // (P lambda = {{Pi}}, Restrict = P^T) and Eq. scaling_matrix.
-#include <mutex>
-
 #include "device_common.cuh"
 #include "hmg_internal.cuh"
 #include "precond.cuh"
@@ -23,10 +21,11 @@ template <int MODE>
 __global__ void __launch_bounds__(kRedThreads)
     spmv_kernel(const double *__restrict__ S, const double *__restrict__ x, double *__restrict__ y,
                 const double *__restrict__ w, const TraceDims d, const int32_t *__restrict__ stencil,
-                const int32_t *__restrict__ col_edges, double *part, unsigned int *counter,
-                double *scal, int slot0, int slot1) {
-  // kSpmvRows rows per thread (block-strided, so each pass stays coalesced): the block's
-  // shuffle reduction, 5 FP64 adds per value and thread, is paid once per kSpmvRows rows
+                const int32_t *__restrict__ col_edges, double *part, int slot0, int slot1) {
+  // kSpmvRows rows per thread (block-strided, so each pass stays coalesced, and four rows'
+  // gathers in flight per thread): the block's reduction is paid once per kSpmvRows rows.
+  // (A persistent grid striding one row per pass, with the partial sums added by the last
+  // block, measured 33% slower at C96.)
   double a0 = 0.0, a1 = 0.0;
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * kSpmvRows + threadIdx.x;
 #pragma unroll
@@ -98,10 +97,10 @@ int launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, i
   if (g > (unsigned)kMaxRedBlocks) return fail(c, HMG_ERR_INVALID_ARG, "too many rows for one reduction");
   Prof prof(c, kCompApply);
   switch (mode) {
-    case 0: spmv_kernel<0><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
-    case 1: spmv_kernel<1><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
-    case 2: spmv_kernel<2><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
-    default: spmv_kernel<3><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, c->counter, c->scal, slot0, slot1); break;
+    case 0: spmv_kernel<0><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, slot0, slot1); break;
+    case 1: spmv_kernel<1><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, slot0, slot1); break;
+    case 2: spmv_kernel<2><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, slot0, slot1); break;
+    default: spmv_kernel<3><<<g, kRedThreads, 0, c->stream>>>(c->S, x, y, w, d, f.edge_stencil, f.col_edges, c->part, slot0, slot1); break;
   }
   if (mode != 0)
     finalize_kernel<<<1, 1024, 0, c->stream>>>(c->part, (int)g, slot0, mode == 2 ? slot1 : -1, c->scal);
@@ -195,10 +194,14 @@ int launch_reconstruct(Ctx *c, const double *lam, const double *Rub, const doubl
 // ZERO, lam_in = 0 and the sweep needs no S apply. Blocks [0, nzb) take CPB columns of
 // lambda^z each (residual rows staged in shared memory, one thread per column runs the
 // Thomas solve with the precomputed factors); the remaining blocks take lambda^h rows.
+// On the lambda^z rows the update is evaluated as (1 - omega) lam_in + omega (S^zz_c)^-1
+// (b - (S - D) lam_in), equal in exact arithmetic: eight couplings instead of eleven in the
+// residual (the sweep is bound by the FP64 issue rate) and three fewer coefficients read.
 struct SweepArgs {
   TraceDims d;
   int ncol, cpb, nzb;
   const int32_t *stencil, *col_edges;
+  double keep;   // 1 - omega
 };
 
 template <typename T, typename Tb, typename Tout, bool ZERO>
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       T r = (T)__ldg(b + row);
-      if (!ZERO) r = s_row_z<T, T, T, true>(S, lam_in, a.col_edges, d, row, r);
+      if (!ZERO) r = s_row_z_off<T, T, T>(S, lam_in, a.col_edges, d, row, r);
       const int j = (i / L1) * ld + i % L1;
       sr[j] = r * __ldg(zw + (row - d.NH));
       sl[j] = __ldg(zl + (row - d.NH));
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
       const T v = sr[(i / L1) * ld + i % L1];
-      lam_out[row] = (Tout)(ZERO ? v : lam_in[row] + v);
+      lam_out[row] = (Tout)(ZERO ? v : fma((T)a.keep, lam_in[row], v));
     }
   } else {
     const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
@@ -281,6 +284,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
   a.stencil = f.edge_stencil;
   a.col_edges = f.col_edges;
+  a.keep = 1.0 - c->factor_omega;   // the omega folded into the factors
   // threads: the column block's rows rounded up to whole warps (at most 256)
   const int tmax = threads_override > 0 ? threads_override : (c->tune_sweep_threads[pm] > 0 ? c->tune_sweep_threads[pm] : 256);
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
@@ -297,14 +301,23 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
 }
 
 // ---- R = b - S lam (Algorithm 2 line 3) ------------------------------------------------------
-template <typename T, typename Tb>
+// ZSWEEP: lam is one line-smoother sweep from zero, lam = omega D^-1 b, so D lam = omega b and
+// R = (1 - omega) b - (S - D) lam (equal in exact arithmetic; ten couplings on a lambda^h row
+// and eight on a lambda^z row instead of eleven).
+template <typename T, typename Tb, bool ZSWEEP>
 __global__ void __launch_bounds__(256)
     residual_kernel(const T *__restrict__ S, const Tb *__restrict__ b, const T *__restrict__ lam,
                     T *__restrict__ R, const TraceDims d, const int32_t *__restrict__ stencil,
-                    const int32_t *__restrict__ col_edges) {
+                    const int32_t *__restrict__ col_edges, double keep) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= d.NT) return;
-  R[row] = s_row<T, T, T, true>(S, lam, stencil, col_edges, d, row, (T)__ldg(b + row));
+  if (ZSWEEP) {
+    const T acc = (T)keep * (T)__ldg(b + row);
+    R[row] = row < d.NH ? s_row_h_off<T, T, T>(S, lam, stencil, d, row, acc)
+                        : s_row_z_off<T, T, T>(S, lam, col_edges, d, row, acc);
+  } else {
+    R[row] = s_row<T, T, T, true>(S, lam, stencil, col_edges, d, row, (T)__ldg(b + row));
+  }
 }
 
 // ---- bbar = Gamma P^T R (Algorithm 2 lines 4-5) -----------------------------------------
@@ -394,8 +407,12 @@ static int two_level(Ctx *c, const double *r, double *z) {
                         ((cm == HMG_COARSE_LEARNED || cm == HMG_COARSE_LEARNED_VCYCLE) && c->coarse_fallback));
   {
     Prof pr(c, kCompResidual, plain_vcycle ? 1 : 2);
-    residual_kernel<T, double><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
-        Prec<T>::S(c), r, w1, w2, d, f.edge_stencil, f.col_edges);
+    if (c->opt.n_pre == 1)   // w1 is one sweep from zero
+      residual_kernel<T, double, true><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
+          Prec<T>::S(c), r, w1, w2, d, f.edge_stencil, f.col_edges, 1.0 - c->factor_omega);
+    else
+      residual_kernel<T, double, false><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(
+          Prec<T>::S(c), r, w1, w2, d, f.edge_stencil, f.col_edges, 0.0);
     if (!plain_vcycle)
       restrict_kernel<T><<<grid_for(f.ncell, 256), 256, 0, c->stream>>>(w2, Prec<T>::gamma(c), cb, d,
                                                                         f.ncell, f.col_edges);
@@ -487,27 +504,24 @@ int line_smooth_fp64(Ctx *c, const double *b, double *lam, int nsweeps) {
 // fixed here: every GPU that loads the library holds these 8 MiB until the process exits.
 namespace {
 constexpr int64_t kNoAllocMaxTrace = int64_t(1) << 20;   // trace unknowns (1,048,576 doubles)
-constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) double g_sweep_scratch[kNoAllocMaxTrace];
-std::mutex g_scratch_mu;
-double *g_scratch_ptr[kNoAllocMaxDevices] = {nullptr};
+}  // namespace
 
-// Device address of g_sweep_scratch on the current device (looked up once per device; the
-// name of a __device__ array is only a host-side stand-in and must not be handed to a kernel).
-int scratch_on_current_device(hmg::Ctx *c, double **out) {
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (c->device < 0 || c->device >= kNoAllocMaxDevices)
-    return hmg::fail(c, HMG_ERR_INVALID_ARG, "device ordinal beyond the no-allocation table");
-  if (!g_scratch_ptr[c->device]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
-    if (e != cudaSuccess) return hmg::cuda_fail(c, e, "cudaGetSymbolAddress(g_sweep_scratch)");
-    g_scratch_ptr[c->device] = static_cast<double *>(p);
-  }
-  *out = g_scratch_ptr[c->device];
+namespace hmg {
+// Device address of g_sweep_scratch in the current device's context, kept in the library
+// context. Called by hmg_assemble_trace (set-up, with the context's device current): the
+// lookup loads this file's module, and with it the array, at set-up rather than inside the
+// first allocation-free call. The name of a __device__ array is only a host-side stand-in
+// and must never be handed to a kernel; this address is what the kernels get. It is as
+// valid as the context's own device buffers (a cudaDeviceReset invalidates both).
+int noalloc_setup(Ctx *c) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_scratch);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_sweep_scratch)");
+  c->noalloc_scratch = static_cast<double *>(p);
   return HMG_OK;
 }
-}  // namespace
+}  // namespace hmg
 
 extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *lambda,
                                        int32_t nsweeps) {
@@ -521,11 +535,11 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
                 "hmg_line_smooth_noalloc: ntrace exceeds the built-in scratch of 1048576 trace "
                 "unknowns; use hmg_line_smooth");
   HMG_CUDA(c, cudaSetDevice(c->device));
-  double *scratch = nullptr;
-  int st = scratch_on_current_device(c, &scratch);
-  if (st) return st;
+  double *scratch = c->noalloc_scratch;   // looked up by hmg_assemble_trace
+  if (!scratch) return fail(c, HMG_ERR_NOT_READY, "the scratch address was not set up; call hmg_assemble_trace");
   // same sweeps as hmg_line_smooth, ping-ponging between lambda and the fixed array; nothing
   // in the array needs to start at zero (each sweep overwrites every entry it later reads)
+  int st;
   double *cur = lambda, *nxt = scratch;
   for (int i = 0; i < nsweeps; ++i) {
     if ((st = launch_sweep<double, double, double, false>(c, b, cur, nxt))) return st;

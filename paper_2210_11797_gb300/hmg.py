@@ -121,6 +121,8 @@ _SIGS = {
                                C.POINTER(C.c_double)], C.c_int),
     "hmg_train_coarse_model": ([_P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                 C.c_double, C.c_uint64, _P], C.c_int),
+    "hmg_adam_step": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                       C.c_double], C.c_int),
     "hmg_collect_coarse_pairs": ([_P, _P, _P, _P, C.c_int32, _P, _P, C.POINTER(C.c_int32),
                                   C.POINTER(SolveStats)], C.c_int),
     "hmg_extract_patches": ([_P, _P, _P, C.c_int32, _P, _P, C.c_int32, C.c_int32, _P, _P], C.c_int),
@@ -442,6 +444,15 @@ class Solver:
         _check(self.ctx, lib().hmg_train_coarse_model(self.ctx, px, pt, ns, nx, ny, batch, epochs, lr, seed,
                                                       hist.ctypes.data_as(C.c_void_p)))
         return hist[:epochs]
+
+    def adam_step(self, w, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        """One Adam update of the FP32 device tensors w, m, v (in place) with gradient g."""
+        n = w.numel()
+        for name, t in (("w", w), ("g", g), ("m", m), ("v", v)):
+            if t.dtype != self.torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{name}: a contiguous CUDA float32 tensor of {n} values is required")
+        _check(self.ctx, lib().hmg_adam_step(self.ctx, _ptr(w), _ptr(g), _ptr(m), _ptr(v), n, step, lr, beta1,
+                                             beta2, eps))
 
     def collect_coarse_pairs(self, Rub, Rpi, max_pairs, check=True):
         torch = self.torch

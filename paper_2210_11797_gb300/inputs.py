@@ -483,3 +483,18 @@ def panel_patch_columns(n: int, npanel: int, nx: int, ny: int, stride: int | Non
                 jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
                 out.append((p * n * n + (j0 + jj) * n + (i0 + ii)).reshape(-1))
     return np.asarray(out, np.int32)
+
+
+def random_panel_patches(n: int, npanel: int, nx: int, ny: int, count: int, npairs: int, seed: int):
+    """`count` random nx x ny patches inside a panel of the regular n x n grid (as in
+    panel_patch_columns): per patch a pair index in [0, npairs), a panel, and an origin
+    (i0, j0) with the whole patch inside the panel, drawn in that order from one
+    SplitMix64(seed) stream. Returns (pair [count] int32, cols [count][nx ny] int32)."""
+    u = uniform01(seed, 4 * count)
+    pair = np.minimum((u[0::4] * npairs).astype(np.int64), npairs - 1)
+    panel = np.minimum((u[1::4] * npanel).astype(np.int64), npanel - 1)
+    i0 = np.minimum((u[2::4] * (n - nx + 1)).astype(np.int64), n - nx)
+    j0 = np.minimum((u[3::4] * (n - ny + 1)).astype(np.int64), n - ny)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    cols = (panel[:, None] * n * n + (j0[:, None] + jj.reshape(1, -1)) * n + (i0[:, None] + ii.reshape(1, -1)))
+    return pair.astype(np.int32), cols.astype(np.int32)

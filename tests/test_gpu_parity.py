@@ -138,16 +138,17 @@ def test_line_smoother_matches_oracle(name):
 @pytest.mark.parametrize("name", ["planar16", "sphereC6L5"])
 def test_krylov_coarse_configurations_match_oracle(name, coarse):
     """Configurations 3a / 3b: the coarse solve by V-cycle-preconditioned BiCGStab to 1e-14 /
-    1e-2 inside Algorithm 2, against the oracle's same configuration."""
+    1e-2 inside Algorithm 2, against the oracle's same configuration; both solved to 1e-12 and
+    held to the FP64 path's 1e-9 relative 2-norm agreement."""
     w, _ora, gpu = _pair(name)
     ora = HybridSolver(w.hier, w.coeffs, OracleOptions(coarse=coarse))
     try:
-        gpu.set_options(coarse=coarse, tol=1e-10, max_iter=200)
+        gpu.set_options(coarse=coarse, tol=1e-12, max_iter=200)
         lam, st = gpu.solve(_cuda(w.Rub.ravel()), _cuda(w.Rpi))
-        assert st["status"] == "ok" and st["true_rel_residual"] < 1e-9
-        ref, hist, status = ora.solve(w.Rub, w.Rpi, 1e-10)
+        assert st["status"] == "ok" and st["true_rel_residual"] < 1e-11
+        ref, hist, status = ora.solve(w.Rub, w.Rpi, 1e-12)
         assert status == "ok" and abs(st["iterations"] - (len(hist) - 1)) <= 1
-        assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-8
+        assert np.linalg.norm(_np(lam) - ref) / np.linalg.norm(ref) < 1e-9
     finally:
         gpu.set_options(coarse="vcycle", tol=w.tol, max_iter=200)
 
@@ -238,29 +239,41 @@ def test_solve_at_method_tolerance_and_host_path(name):
 
 
 def test_mixed_precision_preconditioner_reaches_fp64_tolerance():
+    """The FP32 preconditioner inside FP64 BiCGStab: the oracle's S certifies the FP64 residual
+    of the answer, and its forward error against the converged FP64 oracle solution is that of
+    the plain FP64 solve at the same tolerance (the FP32 preconditioner changes the iterates
+    by far less than the 1e-6 stopping test does). Measured on C12 x 30: forward errors 1.8e-4
+    (mixed) and 1.9e-4 (FP64), the two answers 9.6e-6 apart (2e-10 at C96); the bound on the
+    latter is 3x that."""
     w, ora, gpu = _pair("sphereC12L30")
     Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+    lam64, st64 = gpu.solve(Rub, Rpi)
+    lam64 = _np(lam64)
     gpu.set_options(precision="mixed")
     try:
         lam, st = gpu.solve(Rub, Rpi)
     finally:
         gpu.set_options(precision="fp64")
-    assert st["status"] == "ok"
+    assert st["status"] == "ok" and st["iterations"] == st64["iterations"]
     B = ora.rhs(w.Rub, w.Rpi)
     lam = _np(lam)
     assert np.linalg.norm(B - ora.S @ lam) / np.linalg.norm(B) <= 1.05 * w.tol
     lo, _h, _s = ora.solve(w.Rub, w.Rpi, 1e-12)
-    # forward error of a 1e-6 residual solve, reported against the converged FP64 oracle
-    assert np.linalg.norm(lam - lo) / np.linalg.norm(lo) < 1e-3
+    fwd = np.linalg.norm(lam - lo) / np.linalg.norm(lo)
+    fwd64 = np.linalg.norm(lam64 - lo) / np.linalg.norm(lo)
+    diff = np.linalg.norm(lam - lam64) / np.linalg.norm(lam64)
+    print(f"forward error vs the FP64 oracle: mixed {fwd:.2e}, FP64 {fwd64:.2e}; mixed vs FP64 {diff:.2e}")
+    assert fwd <= 1.05 * fwd64
+    assert diff < 3e-5
 
 
-@pytest.mark.parametrize("name", ["planar16", "sphereC12L30"])
-def test_fp32_preconditioner_against_the_fp64_oracle(name):
+@pytest.mark.parametrize("name,bound", [("planar16", 1.5e-6), ("sphereC12L30", 6e-5)])
+def test_fp32_preconditioner_against_the_fp64_oracle(name, bound):
     """One application of Algorithm 2 with the FP32 coefficients and arithmetic against the
     oracle's FP64 application on the same residual. FP32 rounds each coefficient and each
     operation to 6e-8 relative; the line and column solves amplify that by the conditioning of
-    the vertical blocks (aspect ratios up to ~10^3 here), so the bound is 1e-4 relative in the
-    2-norm (measured: 3e-7 on the plane, 2e-5 on the C12 sphere)."""
+    the vertical blocks (aspect ratios up to ~10^3 here). Measured: 3e-7 on the plane, 2e-5 on
+    the C12 sphere; the bounds are 5x and 3x those."""
     w, ora, gpu = _pair(name)
     r = ora.S @ np.random.default_rng(17).standard_normal(gpu.ntrace)
     gpu.set_options(precision="mixed")
@@ -271,7 +284,7 @@ def test_fp32_preconditioner_against_the_fp64_oracle(name):
     want = ora.precond(r)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     print(f"{name}: FP32 preconditioner vs FP64 oracle, relative 2-norm difference {err:.2e}")
-    assert err < 1e-4
+    assert err < bound
 
 
 def test_configuration2_line_smoother_preconditioner():

@@ -92,3 +92,81 @@ def test_fgmres_solves_and_is_flexible():
     x, hist, st = N.fgmres(lambda v: A @ v, b, lambda v, k: v * (1.0 + (k % 2)), 1e-10, restart=20)
     assert st == "ok"
     np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-7)
+
+
+def test_bf16_rounding_matches_torch_and_ties_go_to_even():
+    """round_bf16 against PyTorch's float32 -> bfloat16 conversion (round to nearest even) on
+    values spread over the FP32 range, and against hand-made ties: 1 + 2^-8 lies halfway
+    between 1 and 1 + 2^-7 and rounds to the even 1; 1 + 3 * 2^-8 rounds up to 1 + 2^-6."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    v = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000)).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(N.round_bf16(v), ref)
+    ties = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 2.0 ** -7 * (1 + 2.0 ** -8)])
+    np.testing.assert_array_equal(N.round_bf16(ties), [1.0, 1 + 2.0 ** -6, -1.0, 2.0 ** -7])
+
+
+def test_bf16_forward_stores_rounded_values():
+    """With BF16 storage every stored activation is a BF16 value and the output equals the FP64
+    network applied to the rounded weights and input up to the rounding of the activations
+    (relative effect of order 2^-8 per layer)."""
+    p = N.init_params(2, ch=8)
+    edge, diag = N.grid_neighbours(4, 3)
+    x = np.random.default_rng(9).standard_normal((12, 7))
+    y16, t = N.forward(p, x, edge, diag, keep=True, quant="bf16")
+    for k in ("x", "h1", "h2", "h3"):
+        np.testing.assert_array_equal(t[k], N.round_bf16(t[k]))
+    for k in p:
+        np.testing.assert_array_equal(t["W"][k], N.round_bf16(p[k]))
+    y = N.forward({k: N.round_bf16(v) for k, v in p.items()}, N.round_bf16(x), edge, diag)
+    assert np.linalg.norm(y16 - y) / np.linalg.norm(y) < 3 * 2.0 ** -8
+    assert np.linalg.norm(y16 - y) > 0          # the activations were rounded
+
+
+def test_bf16_gradient_matches_central_differences_of_the_rounded_network():
+    """The BF16-storage gradient is the derivative of the loss with the activations held at
+    their stored (rounded) values: in the last layer that is exact, so W3's gradient equals a
+    central difference of the loss in W3 with h3 frozen (a linear layer, so the difference is
+    exact up to FP64 rounding)."""
+    p = N.init_params(5, ch=6)
+    edge, diag = N.grid_neighbours(3, 3)
+    rng = np.random.default_rng(10)
+    x, tgt = rng.standard_normal((9, 5)), rng.standard_normal((9, 5))
+    _loss, g = N.loss_and_grad(p, x, tgt, edge, diag, quant="bf16")
+    _y, t = N.forward(p, x, edge, diag, keep=True, quant="bf16")
+    W3 = t["W"]["W3"]
+    denom = np.sum(tgt * tgt)
+
+    def loss_w3(w):
+        y = N.conv1d(w, t["h3"])[:, 0, :]
+        return np.sum((y - tgt) ** 2) / denom
+    h = 1e-5
+    for idx in np.ndindex(W3.shape):
+        wp, wm = W3.copy(), W3.copy()
+        wp[idx] += h
+        wm[idx] -= h
+        fd = (loss_w3(wp) - loss_w3(wm)) / (2 * h)
+        assert g["W3"][idx] == pytest.approx(fd, rel=1e-7, abs=1e-10)
+    # and the full gradient with quant=None is the FP64 network's (the BF16 one differs)
+    _l, g64 = N.loss_and_grad(p, x, tgt, edge, diag)
+    assert not np.allclose(g64["W2"], g["W2"], rtol=1e-6)
+
+
+def test_adam_three_steps_from_nonzero_moments_closed_form():
+    """Three Adam steps continuing from step 4 with given moments, against the update written
+    out from Kingma & Ba's definition for a scalar weight."""
+    w0, m0, v0 = 0.7, 0.02, 3e-4
+    gs = [0.1, -0.05, 0.2]
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    p = {"w": np.array([w0])}
+    st = {"t": 4, "m_w": np.array([m0]), "v_w": np.array([v0])}
+    w, m, v = w0, m0, v0
+    for k, g in enumerate(gs):
+        p = N.adam_step(p, {"w": np.array([g])}, st, lr=lr, b1=b1, b2=b2, eps=eps)
+        t = 5 + k
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        w = w - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+    assert p["w"][0] == pytest.approx(w, rel=1e-15)
+    assert st["t"] == 7 and st["m_w"][0] == pytest.approx(m, rel=1e-15)

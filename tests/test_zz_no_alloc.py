@@ -35,11 +35,16 @@ def test_noalloc_line_smooth_matches_line_smooth(nsweeps):
     ref = _cuda(lam0)
     gpu.line_smooth(b, ref, nsweeps)              # the existing entry point
     ref = ref.cpu().numpy()
-    for _call in range(2):                        # two calls in a row share the built-in array
+    for call in range(2):                         # two calls in a row share the built-in array
         lam = _cuda(lam0)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = L.hmg_line_smooth_noalloc(gpu.ctx, ctypes.c_void_p(b.data_ptr()),
                                        ctypes.c_void_p(lam.data_ptr()), nsweeps)
         assert st == 0, L.hmg_last_error(gpu.ctx).decode()
+        # the array was placed when hmg_assemble_trace looked up its address, so the call
+        # itself takes no device memory, the first call included
+        assert torch.cuda.mem_get_info()[0] == free_before, call
         got = lam.cpu().numpy()
         # same kernels in the same order: equal to the tolerance of the line-smoother parity test
         assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
