@@ -1,6 +1,8 @@
 """bench.py's reference arm (the FP64 oracle timed on the host cores) on the small planar
 workload, on CPU: one JSON line with the contract's keys, impl "reference", the workload's
-own tolerance, and e2e / cpu_baseline describing the same run."""
+own tolerance and the same config dict as the GPU arm's, full solves counted honestly (at
+most one warm-up), and e2e / cpu_baseline describing the same run. Also the multi-core leg of
+the oracle on the batch (processes started together at a barrier)."""
 import json
 import os
 import subprocess
@@ -15,7 +17,7 @@ def test_reference_arm_prints_one_contract_line(repo_root):
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
     for k in ("metric", "value", "unit", "n_gpus", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
@@ -23,3 +25,16 @@ def test_reference_arm_prints_one_contract_line(repo_root):
     assert d["config"]["tol"] == 1e-10 and d["config"]["ntrace"] == 6400
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    sys.path.insert(0, repo_root)
+    import bench
+    assert d["config"] == bench.workload_config(bench.workload_spec("planar16"))
+    assert "full solves" in d["cpu_baseline"]["sample"] and d["iterations"] > 0
+
+
+def test_oracle_batch_leg_on_two_cores(repo_root):
+    sys.path.insert(0, repo_root)
+    import bench
+    r = bench.oracle_batch_multicore(2)
+    assert r["cores"] == 2 and r["all_ok"] and r["sample"] == ["C12xL50", "C32xL10"]
+    assert r["value"] > 0 and r["wall_s"] > 0 and len(r["iterations"]) == 2
+    assert all(i > 0 for i in r["iterations"])

@@ -71,3 +71,34 @@ def test_autotuned_shapes_keep_results():
     # the column-block shape changes which block solves which columns, not the arithmetic
     assert torch.equal(lam0, lam1) and st0["iterations"] == st1["iterations"]
     gpu.close()
+
+
+def test_batch_of_the_seed3_draw():
+    """Members of the batched workload itself (sizes from SplitMix64 seed 3, right-hand sides
+    seed 3 + i, FP32 preconditioner, tol 1e-6): 12 columns per panel edge (three multigrid
+    levels, the coarsest 3 x 3 per panel), 50 and 70 levels, 10 levels, and the largest panels
+    (48 x 48, 70 levels) next to the smallest, all in one graph launch. Each answer equals its
+    single solve bit for bit and the oracle's own S certifies its FP64 residual."""
+    from paper_2210_11797_gb300.hmg import Solver, solve_batched
+    sizes = I.batched_sizes(64, 3)
+    pick = [0, 3, 4, 1, 10, 13]                    # C12xL50, C12xL70, C24xL70, C32xL10, C48xL70, C12xL10
+    assert [sizes[i] for i in pick] == [(12, 50), (12, 70), (24, 70), (32, 10), (48, 70), (12, 10)]
+    ws = [I.cubed_sphere(n, L, seed=3 + i, tol=1e-6) for i, (n, L) in ((i, sizes[i]) for i in pick)]
+    assert ws[0].hier.nmg == 3 and ws[4].hier.nmg == 4
+    solvers = [Solver(w.hier, w.coeffs, tol=w.tol, precision="mixed") for w in ws]
+    for s in solvers:
+        s.autotune()
+    Rubs = [_cuda(w.Rub.ravel()) for w in ws]
+    Rpis = [_cuda(w.Rpi) for w in ws]
+    lams, stats = solve_batched(solvers, Rubs, Rpis)
+    for s, w, r, p, lam, st in zip(solvers, ws, Rubs, Rpis, lams, stats):
+        single, st1 = s.solve(r, p)
+        assert st["status"] == "ok" and st["iterations"] == st1["iterations"]
+        assert torch.equal(lam, single)
+        if w.mesh.ncell <= 300_000:                # the oracle's setup stays within seconds
+            ora = HybridSolver(w.hier, w.coeffs)
+            B = ora.rhs(w.Rub, w.Rpi)
+            lo = lam.cpu().numpy()
+            assert np.linalg.norm(B - ora.S @ lo) / np.linalg.norm(B) <= 1.05e-6
+    for s in solvers:
+        s.close()
