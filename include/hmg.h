@@ -144,6 +144,24 @@ typedef struct {
                            gives the stats and the stop reason later.
                            Host-driven and FGMRES solves, hmg_solve_host, hmg_solve_mixed
                            and batched solves stay synchronous */
+  int32_t degree;       /* polynomial degree p of the discretisation (Sec. 2.2; the paper's runs and
+                           the default: 0, broken RT0 / DG0 / one trace unknown per facet).
+                           1: broken RT1 (36 dofs per cell, 24 of them on the facets), DG1 (8) and
+                           Q1 trace multipliers (4 per facet), the 44 x 44 cell matrices
+                           condensed to 24 x 24 (the paper's table of unknowns per cell), for the
+                           Helmholtz preset (hmg_scalars.preset = 1) in FP64, with Algorithm 1 on
+                           facet blocks and Algorithm 2 on the DG0 coarse space and the
+                           lowest-order pressure multigrid. Set before hmg_assemble_trace (a
+                           change needs a new assembly). With degree 1 every call that takes cell
+                           residuals takes Rub [ncell][36] (the cell's RT1 dofs: the 24 outward
+                           facet fluxes, face by face e0..e3, bottom, top, node (s, t) at
+                           4 f + 2 s + t, then 12 interior dofs) and Rpi [ncell][8] (DG1, node
+                           (i, j, k) at 4 i + 2 j + k), and lambda has hmg_sizes' ntrace entries:
+                           four per facet, facet by facet in the order of the lowest-order
+                           numbering, node (s, t) at + 2 s + t (s along a vertical facet in the
+                           traversal of the column that owns its edge, t upwards; on a horizontal
+                           facet the xi and eta nodes). Batched, mixed-precision, learned,
+                           configuration-1 and allocation-free calls stay degree 0 */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
@@ -206,7 +224,8 @@ int hmg_set_coefficients(hmg_ctx *ctx, const hmg_scalars *scalars, const hmg_bac
  * Gamma = (H 1) / (P^T S P 1). Allocates the solver workspace. */
 int hmg_assemble_trace(hmg_ctx *ctx);
 
-/* Sizes: cells and trace unknowns of the finest level (either pointer may be NULL). */
+/* Sizes: cells and trace unknowns of the finest level (either pointer may be NULL); with
+ * degree 1 (assembled) ntrace counts the four unknowns of every facet. */
 int hmg_sizes(const hmg_ctx *ctx, int64_t *ncell, int64_t *ntrace);
 
 void hmg_destroy(hmg_ctx *ctx);

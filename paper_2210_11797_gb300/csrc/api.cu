@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/hmg.h): validation of the caller's tables,
 // upload of the mesh hierarchy and coefficients, allocation of the solver workspace, and
 // the entry points of the solve.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -52,6 +53,10 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
   if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
   if (o.async_stats != 0 && o.async_stats != 1) return bad("async_stats must be 0 or 1");
+  if (o.degree != 0 && o.degree != 1) return bad("degree must be 0 or 1");
+  if (o.degree == 1 && (o.precision != HMG_PRECISION_FP64 || o.precond == HMG_PRECOND_SCHUR ||
+                        o.coarse != HMG_COARSE_VCYCLE))
+    return bad("degree 1 runs in FP64 with the trace preconditioners and the V-cycle coarse solve");
   return HMG_OK;
 }
 
@@ -196,10 +201,15 @@ int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
   c->opt = *opt;
   if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32)
     c->assembled = false;  // the FP32 copies are built by hmg_assemble_trace
+  if (c->assembled && c->opt.degree != c->degree) c->assembled = false;   // a new discretisation
   if (c->assembled && (c->opt.omega != c->factor_omega || c->opt.mg_omega != c->factor_mg_omega)) {
     HMG_CUDA(c, cudaSetDevice(c->device));
     if ((st = build_factors(c))) return st;
     HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  if (c->assembled && c->degree == 1) {   // (outside any stream capture: the solve graph replays them)
+    HMG_CUDA(c, cudaSetDevice(c->device));
+    if ((st = ho_refactor_if_needed(c))) return st;
   }
   return HMG_OK;
 }
@@ -358,22 +368,49 @@ int hmg_assemble_trace(hmg_ctx *c) {
   int st = assemble_all(c);
   if (st) return st;
   const Level &f = c->lv[0];
-  const size_t T = (size_t)f.ntrace;
-  if (!c->B) {
-    // Krylov vectors long enough for the 2x2 system of configuration 1 ([u | Pi])
+  const int64_t T = f.ntrace, C = f.ncell;
+  const int64_t T1 = c->opt.degree == 1 ? ho_trace_size(c) : 0;
+  // Krylov vectors long enough for the 2x2 system of configuration 1 ([u | Pi]) and for the
+  // degree-1 trace system; work vectors for the longer trace system; the host-copy staging area
+  // for the cell residuals and lambda of either degree
+  const int64_t nvec = std::max(T + C, T1), nwork = std::max(T, T1);
+  const int64_t nhost = std::max(7 * C + T, T1 ? 44 * C + T1 : 0);
+  if (c->vec_cap < nvec) {
     double **vecs[] = {&c->B, &c->r, &c->rhat, &c->p, &c->v, &c->s, &c->t, &c->phat, &c->shat};
-    for (double **v : vecs)
-      if ((st = dev_alloc(c, v, T + (size_t)f.ncell))) return st;
+    for (double **v : vecs) {
+      dev_free(c, *v);
+      *v = nullptr;
+      if ((st = dev_alloc(c, v, (size_t)nvec))) return st;
+    }
+    c->vec_cap = nvec;
+    drop_graph(c);   // a cached solve graph holds the old vectors
+  }
+  if (c->work_cap < nwork) {
+    void **ws[] = {&c->w1, &c->w2, &c->w3};
+    for (void **w : ws) {
+      dev_free(c, *w);
+      double *tmp = nullptr;
+      if ((st = dev_alloc(c, &tmp, (size_t)nwork))) return st;
+      *w = tmp;
+    }
+    c->work_cap = nwork;
+    drop_graph(c);
+  }
+  if (!c->cb) {
     double *tmp;
-    if ((st = dev_alloc(c, &tmp, T))) return st;
-    c->w1 = tmp;
-    if ((st = dev_alloc(c, &tmp, T))) return st;
-    c->w2 = tmp;
-    if ((st = dev_alloc(c, &tmp, T))) return st;
-    c->w3 = tmp;
-    if ((st = dev_alloc(c, &tmp, (size_t)f.ncell))) return st;
+    if ((st = dev_alloc(c, &tmp, (size_t)C))) return st;
     c->cb = tmp;
-    if ((st = dev_alloc(c, &c->host_in, (size_t)7 * f.ncell + T))) return st;
+  }
+  if (c->host_cap < nhost) {
+    dev_free(c, c->host_in);
+    c->host_in = nullptr;
+    if ((st = dev_alloc(c, &c->host_in, (size_t)nhost))) return st;
+    c->host_cap = nhost;
+  }
+  c->degree = c->opt.degree;
+  if (c->degree == 1 && (st = ho_assemble(c))) {
+    c->degree = 0;
+    return st;
   }
   if (!c->noalloc_scratch && (st = noalloc_setup(c))) return st;
   c->assembled = true;
@@ -384,7 +421,7 @@ int hmg_sizes(const hmg_ctx *c, int64_t *ncell, int64_t *ntrace) {
   if (!c) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh) return HMG_ERR_NOT_READY;
   if (ncell) *ncell = c->lv[0].ncell;
-  if (ntrace) *ntrace = c->lv[0].ntrace;
+  if (ntrace) *ntrace = c->assembled && c->degree == 1 ? c->ho.T : c->lv[0].ntrace;
   return HMG_OK;
 }
 
@@ -440,6 +477,7 @@ int hmg_trace_rhs(hmg_ctx *c, const double *Rub, const double *Rpi, double *B) {
   int st = ready(c);
   if (st) return st;
   if (!Rub || !Rpi || !B) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if (c->degree == 1) return finish(c, ho_trace_rhs(c, Rub, Rpi, B));
   return finish(c, launch_trace_rhs(c, Rub, Rpi, B));
 }
 
@@ -491,11 +529,12 @@ int hmg_solve_host(hmg_ctx *c, const double *Rub, const double *Rpi, double *lam
   if (!Rub || !Rpi || !lambda) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
   if ((st = reject_schur(c))) return st;
   const Level &f = c->lv[0];
-  double *dRub = c->host_in, *dRpi = dRub + 6 * f.ncell, *dlam = dRpi + f.ncell;
-  HMG_CUDA(c, cudaMemcpyAsync(dRub, Rub, sizeof(double) * 6 * f.ncell, cudaMemcpyHostToDevice, c->stream));
-  HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * f.ncell, cudaMemcpyHostToDevice, c->stream));
+  const int64_t nu = cell_nu(c), np = cell_np(c);
+  double *dRub = c->host_in, *dRpi = dRub + nu * f.ncell, *dlam = dRpi + np * f.ncell;
+  HMG_CUDA(c, cudaMemcpyAsync(dRub, Rub, sizeof(double) * nu * f.ncell, cudaMemcpyHostToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(dRpi, Rpi, sizeof(double) * np * f.ncell, cudaMemcpyHostToDevice, c->stream));
   if (c->opt.warm_start)   // the initial lambda comes from the host buffer too
-    HMG_CUDA(c, cudaMemcpyAsync(dlam, lambda, sizeof(double) * f.ntrace, cudaMemcpyHostToDevice, c->stream));
+    HMG_CUDA(c, cudaMemcpyAsync(dlam, lambda, sizeof(double) * sys_n(c), cudaMemcpyHostToDevice, c->stream));
   // lambda comes back to the host behind the solve, under the same synchronisation
   return krylov_solve(c, dRub, dRpi, dlam, stats, false, lambda);
 }
@@ -504,6 +543,7 @@ int hmg_reconstruct(hmg_ctx *c, const double *lambda, const double *Rub, const d
   int st = ready(c);
   if (st) return st;
   if (!lambda || !Rub || !Rpi || !ub || !pi) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if (c->degree == 1) return finish(c, ho_reconstruct(c, lambda, Rub, Rpi, ub, pi));
   return finish(c, launch_reconstruct(c, lambda, Rub, Rpi, ub, pi));
 }
 
@@ -511,6 +551,7 @@ int hmg_apply_trace(hmg_ctx *c, const double *x, double *y) {
   int st = ready(c);
   if (st) return st;
   if (!x || !y || x == y) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
+  if (c->degree == 1) return finish(c, ho_launch_spmv(c, x, y, 0, nullptr, 0, 0));
   return finish(c, launch_spmv(c, x, y, 0, nullptr, 0, 0));
 }
 
@@ -526,6 +567,7 @@ int hmg_line_smooth(hmg_ctx *c, const double *b, double *lambda, int32_t nsweeps
   int st = ready(c);
   if (st) return st;
   if (!b || !lambda || nsweeps < 0) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  if (c->degree == 1) return finish(c, ho_line_smooth(c, b, lambda, nsweeps));
   return finish(c, line_smooth_fp64(c, b, lambda, nsweeps));
 }
 
@@ -548,7 +590,8 @@ int hmg_get_gamma(hmg_ctx *c, double *gamma) {
   int st = ready(c);
   if (st) return st;
   if (!gamma) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
-  HMG_CUDA(c, cudaMemcpyAsync(gamma, c->gamma, sizeof(double) * c->lv[0].ncell, cudaMemcpyDeviceToDevice, c->stream));
+  HMG_CUDA(c, cudaMemcpyAsync(gamma, c->degree == 1 ? c->ho.gamma : c->gamma, sizeof(double) * c->lv[0].ncell,
+                              cudaMemcpyDeviceToDevice, c->stream));
   return finish(c, HMG_OK);
 }
 
@@ -564,6 +607,7 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
     if (c->device != c0->device) return fail(c0, HMG_ERR_INVALID_ARG, "batched contexts must share a device");
     if (!Rub[i] || !Rpi[i] || !lambda[i]) return fail(c0, HMG_ERR_INVALID_ARG, "null pointer in the batch");
     if (mixed_system(c)) return fail(c0, HMG_ERR_INVALID_ARG, "batched solves are hybridised solves");
+    if (c->degree != 0) return fail(c0, HMG_ERR_INVALID_ARG, "batched solves are degree 0");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return fail(c0, HMG_ERR_INVALID_ARG, "a context appears twice in the batch");
   }
@@ -617,6 +661,7 @@ int hmg_get_trace_operator(hmg_ctx *c, double *slots) {
   int st = ready(c);
   if (st) return st;
   if (!slots) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
+  if (c->degree != 0) return fail(c, HMG_ERR_INVALID_ARG, "the slot layout is that of degree 0");
   HMG_CUDA(c, cudaMemcpyAsync(slots, c->S, sizeof(double) * kSlots * c->lv[0].ntrace,
                               cudaMemcpyDeviceToDevice, c->stream));
   return finish(c, HMG_OK);
@@ -714,8 +759,8 @@ int hmg_collect_coarse_pairs(hmg_ctx *c, const double *Rub, const double *Rpi, d
   if (st) return st;
   if (!Rub || !Rpi || !lambda || !x_out || !t_out || !n_out || max_pairs < 1)
     return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
-  if (c->opt.precision != HMG_PRECISION_FP64 || c->opt.precond != HMG_PRECOND_NONNESTED)
-    return fail(c, HMG_ERR_INVALID_ARG, "pairs are collected from the FP64 non-nested preconditioner");
+  if (c->opt.precision != HMG_PRECISION_FP64 || c->opt.precond != HMG_PRECOND_NONNESTED || c->degree != 0)
+    return fail(c, HMG_ERR_INVALID_ARG, "pairs are collected from the FP64 non-nested preconditioner of degree 0");
   c->collect_x = x_out;
   c->collect_t = t_out;
   c->collect_max = max_pairs;

@@ -84,6 +84,21 @@ struct TrainBufs {
   size_t cap_tn = 0, cap_tnb = 0, cap_xb = 0, cap_tb = 0, cap_order = 0;
 };
 
+// The degree-1 trace system (higher_order.cu), finest level only.
+struct HoData {
+  int64_t T = 0;               // trace rows: four per facet
+  double *S = nullptr;         // [48][T] two cells x 24 facet-dof coefficients per row
+  double *Ainv = nullptr;      // [ncell][44][44] A_K^-1
+  double *hw = nullptr;        // [16][vertical facets] omega (facet block of S)^-1
+  double *zf = nullptr;        // [48][horizontal facets] block Thomas factors of S^zz
+  double *gamma = nullptr;     // [ncell] Gamma of Eq. scaling_matrix
+  double *m = nullptr;         // [ncell] sigma |K|_1 = (H 1)_K
+  int8_t *own = nullptr;       // [ncol][4] 1 where the column owns the edge of its face
+  double *tab = nullptr;       // reference-element tables
+  int *flag = nullptr;         // singular-matrix flag of the assembly
+  double factor_omega = 0.0;   // the omega the smoother factors hold
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -93,6 +108,8 @@ struct Ctx {
   int nmg = 0;
   Level lv[kMaxLevels];
   bool have_mesh = false, have_coeffs = false, assembled = false, have_fp32 = false;
+  int degree = 0;              // polynomial degree of the assembled system (0 or 1)
+  HoData ho;
   // finest-level trace system (device)
   double *S = nullptr;        // [11][ntrace]
   // Thomas factors of S^zz with omega folded in (pivot p_k): omega / p_k, sub_k / p_k,
@@ -171,6 +188,8 @@ struct Ctx {
   // flexible GMRES basis: V [restart+1][ntrace], Z [restart][ntrace], Hessenberg column
   double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
   int gm_restart = 0;
+  int64_t gm_n = 0;            // length of the basis vectors
+  int64_t vec_cap = 0, work_cap = 0, host_cap = 0;   // capacities of the solver workspace (doubles)
   std::vector<void *> owned;   // every device allocation, freed by hmg_destroy
   // component timing (hmg_options.profile): event pool and (component, start, end) marks
   std::vector<cudaEvent_t> ev_pool;
@@ -283,12 +302,29 @@ int launch_mixed_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B);
 int schur_precond(Ctx *c, const double *r, double *z);
 // the Krylov system of the context's configuration: its length, operator and right-hand side
 inline bool mixed_system(const Ctx *c) { return c->opt.precond == HMG_PRECOND_SCHUR; }
-inline int64_t sys_n(const Ctx *c) { return c->lv[0].ntrace + (mixed_system(c) ? c->lv[0].ncell : 0); }
+inline int64_t sys_n(const Ctx *c) {
+  if (c->degree == 1) return c->ho.T;
+  return c->lv[0].ntrace + (mixed_system(c) ? c->lv[0].ncell : 0);
+}
 // Batched solves: one CUDA graph with one branch per context (contexts on one device).
 int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
                          const double *const *Rpi, double *const *lambda, hmg_solve_stats *st);
 // Releases the context's cached solve graph.
 void drop_graph(Ctx *c);
+
+// ---- degree 1 (higher_order.cu) ----------------------------------------------------------
+int64_t ho_trace_size(const Ctx *c);
+int ho_assemble(Ctx *c);                                   // needs w1, w2 of ho_trace_size doubles
+int ho_launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1);
+int ho_trace_rhs(Ctx *c, const double *Ru, const double *Rp, double *B);
+int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi);
+int ho_precond(Ctx *c, const double *r, double *z);
+int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps);
+// rebuilds the degree-1 smoother factors when omega changed since they were built (synchronises)
+int ho_refactor_if_needed(Ctx *c);
+// cell residual sizes of the assembled degree: velocity and pressure dofs per cell
+inline int cell_nu(const Ctx *c) { return c->degree == 1 ? 36 : 6; }
+inline int cell_np(const Ctx *c) { return c->degree == 1 ? 8 : 1; }
 
 // ---- learned coarse correction (learned.cu) ---------------------------------------------
 constexpr int kCoarseParams = 3360;

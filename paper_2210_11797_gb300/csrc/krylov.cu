@@ -54,9 +54,11 @@ enum { kIt = 0, kStatus = 1, kContinue = 2, kWaitFlag = 3 };
 // The system the Krylov loop iterates on: S lambda = B_lambda (hybridised configurations) or
 // the 2x2 system on [u | Pi] (configuration 1).
 static int sys_apply(Ctx *c, const double *x, double *y, int mode, const double *w, int s0, int s1) {
+  if (c->degree == 1) return ho_launch_spmv(c, x, y, mode, w, s0, s1);
   return mixed_system(c) ? launch_mixed_apply(c, x, y, mode, w, s0, s1) : launch_spmv(c, x, y, mode, w, s0, s1);
 }
 static int sys_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B) {
+  if (c->degree == 1) return ho_trace_rhs(c, Rub, Rpi, B);
   return mixed_system(c) ? launch_mixed_rhs(c, Rub, Rpi, B) : launch_trace_rhs(c, Rub, Rpi, B);
 }
 
@@ -731,8 +733,8 @@ __global__ void gm_sub_kernel(const double *__restrict__ B, const double *__rest
 }
 
 static int gm_buffers(Ctx *c, int m) {
-  if (c->gm_V && c->gm_restart >= m) return HMG_OK;
-  const int64_t n = c->lv[0].ntrace + c->lv[0].ncell;   // the longer of the two systems
+  const int64_t n = std::max<int64_t>(c->lv[0].ntrace + c->lv[0].ncell, sys_n(c));   // the longest system
+  if (c->gm_V && c->gm_restart >= m && c->gm_n >= n) return HMG_OK;
   dev_free(c, c->gm_V);
   dev_free(c, c->gm_Z);
   c->gm_V = c->gm_Z = nullptr;
@@ -746,6 +748,7 @@ static int gm_buffers(Ctx *c, int m) {
     if ((s = dev_alloc(c, &c->gm_y, (size_t)kMaxRestart))) return s;
   }
   c->gm_restart = m;
+  c->gm_n = n;
   return HMG_OK;
 }
 

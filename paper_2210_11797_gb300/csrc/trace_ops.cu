@@ -466,6 +466,7 @@ static int two_level(Ctx *c, const double *r, double *z) {
 }
 
 int precond_apply(Ctx *c, const double *r, double *z) {
+  if (c->degree == 1) return ho_precond(c, r, z);
   const bool mixed = c->opt.precision == HMG_PRECISION_MIXED;
   switch (c->opt.precond) {
     case HMG_PRECOND_SCHUR:
@@ -530,6 +531,7 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
   Ctx *c = ctx;
   if (!c->assembled) return fail(c, HMG_ERR_NOT_READY, "call hmg_assemble_trace first");
   if (!b || !lambda || nsweeps < 0) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
+  if (c->degree != 0) return fail(c, HMG_ERR_INVALID_ARG, "hmg_line_smooth_noalloc sweeps the degree-0 system");
   if (c->lv[0].ntrace > kNoAllocMaxTrace)
     return fail(c, HMG_ERR_INVALID_ARG,
                 "hmg_line_smooth_noalloc: ntrace exceeds the built-in scratch of 1048576 trace "

@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("divergence", C.c_double), ("profile", C.c_int32), ("graph", C.c_int32),
                 ("coarse", C.c_int32), ("krylov", C.c_int32), ("restart", C.c_int32),
                 ("stall_ratio", C.c_double), ("mg_fused", C.c_int32), ("warm_start", C.c_int32),
-                ("mg_fuse_cells", C.c_int32), ("async_stats", C.c_int32)]
+                ("mg_fuse_cells", C.c_int32), ("async_stats", C.c_int32), ("degree", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -209,10 +209,17 @@ class Solver:
         self._set_coefficients(coeffs)
         _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
         self._fp32_built = self.opts.precision == PRECISION["mixed"]   # FP32 operator copies exist
+        self._sizes()
+        self._keep = []
+
+    def _sizes(self):
+        """Cells, trace unknowns and the cell residual dofs of the assembled degree (velocity:
+        6 at degree 0, 36 at degree 1; pressure: 1, 8)."""
         nc, nt = C.c_int64(), C.c_int64()
         _check(self.ctx, lib().hmg_sizes(self.ctx, C.byref(nc), C.byref(nt)))
         self.ncell, self.ntrace = nc.value, nt.value
-        self._keep = []
+        self.degree = self.opts.degree
+        self.nu, self.npr = (36, 8) if self.degree == 1 else (6, 1)
 
     def _arr(self, a, dtype):
         a = np.ascontiguousarray(a, dtype=dtype)
@@ -267,12 +274,15 @@ class Solver:
         if self.opts.precision == PRECISION["mixed"] and not self._fp32_built:
             _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
             self._fp32_built = True
+        if self.opts.degree != self.degree:       # a new discretisation: assemble it
+            _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+            self._sizes()
 
     # -- the calls ------------------------------------------------------------------------
     def trace_rhs(self, Rub, Rpi):
         B = self._empty(self.ntrace)
-        _check(self.ctx, lib().hmg_trace_rhs(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"),
-                                             self._dev(Rpi, self.ncell, "Rpi"), _ptr(B)))
+        _check(self.ctx, lib().hmg_trace_rhs(self.ctx, self._dev(Rub, self.nu * self.ncell, "Rub"),
+                                             self._dev(Rpi, self.npr * self.ncell, "Rpi"), _ptr(B)))
         return B
 
     def solve(self, Rub, Rpi, lam=None, check=True):
@@ -280,7 +290,8 @@ class Solver:
         stats is None and solve_stats() gives them later."""
         lam = self._empty(self.ntrace) if lam is None else lam
         st = SolveStats()
-        rc = lib().hmg_solve(self.ctx, self._dev(Rub, 6 * self.ncell, "Rub"), self._dev(Rpi, self.ncell, "Rpi"),
+        rc = lib().hmg_solve(self.ctx, self._dev(Rub, self.nu * self.ncell, "Rub"),
+                             self._dev(Rpi, self.npr * self.ncell, "Rpi"),
                              self._dev(lam, self.ntrace, "lambda"), C.byref(st))
         if check:
             _check(self.ctx, rc)
@@ -317,7 +328,7 @@ class Solver:
         receives lambda, else a new array."""
         Rub = np.ascontiguousarray(Rub, np.float64)
         Rpi = np.ascontiguousarray(Rpi, np.float64)
-        if Rub.size != 6 * self.ncell or Rpi.size != self.ncell:
+        if Rub.size != self.nu * self.ncell or Rpi.size != self.npr * self.ncell:
             raise ValueError("Rub / Rpi size")
         lam = np.empty(self.ntrace) if out is None else out
         if lam.dtype != np.float64 or lam.size != self.ntrace or not lam.flags.c_contiguous:
@@ -336,10 +347,10 @@ class Solver:
         self._fp32_built = self.opts.precision == PRECISION["mixed"] or self._fp32_built
 
     def reconstruct(self, lam, Rub, Rpi):
-        ub, pi = self._empty(6 * self.ncell), self._empty(self.ncell)
+        ub, pi = self._empty(self.nu * self.ncell), self._empty(self.npr * self.ncell)
         _check(self.ctx, lib().hmg_reconstruct(self.ctx, self._dev(lam, self.ntrace, "lambda"),
-                                               self._dev(Rub, 6 * self.ncell, "Rub"),
-                                               self._dev(Rpi, self.ncell, "Rpi"), _ptr(ub), _ptr(pi)))
+                                               self._dev(Rub, self.nu * self.ncell, "Rub"),
+                                               self._dev(Rpi, self.npr * self.ncell, "Rpi"), _ptr(ub), _ptr(pi)))
         return ub, pi
 
     def apply_trace(self, x):

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(hmg.Background) == 3 * 8
     assert ctypes.sizeof(hmg.Scalars) == 6 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(hmg.SolveStats) == 4 + 4 + 3 * 8 + 8 + hmg.MAX_HISTORY * 8 + 8 * 8 + 8 * 4 + 8
-    assert ctypes.sizeof(hmg.Options) == 128
+    assert ctypes.sizeof(hmg.Options) == 136
 
 
 def test_struct_offsets_match_the_c_compiler(tmp_path):

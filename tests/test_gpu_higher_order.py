@@ -1,0 +1,170 @@
+"""Degree 1 on the GPU (hmg_options.degree = 1, through the C ABI) against the degree-p oracle
+(oracle/higher_order.py): the trace operator, B_lambda, recovery, Gamma, the line smoother
+(facet blocks and block-tridiagonal columns), Algorithm 2 with the DG0 coarse space, and whole
+solves, on the periodic plane and on curved cubed-sphere cells, plus a one-layer mesh and a
+ragged column block.
+
+Tolerances (FP64 on both sides, different summation orders): single operator applications and
+right-hand sides within 1e-13 of the row scale; sweeps, the two-level cycle and recovery
+within 1e-11 of the result's magnitude (as for degree 0); whole solves converged to 1e-12 on
+both sides agree to 1e-9 in the relative 2-norm."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import higher_order as HO
+from paper_2210_11797_gb300 import inputs as I
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _sphere(n=4, nlev=5, nmg=2):
+    hier = I.sphere_hierarchy(n, nlev, I.quadratic_levels(nlev, 0.3), nmg, radius=1.0)
+    co = I.Coefficients([I.unit_background(m) for m in hier.meshes], dt=1.0, preset=1, sigma=10.0)
+    return hier, co
+
+
+_CACHE = {}
+
+
+def _pair(name):
+    if name not in _CACHE:
+        from paper_2210_11797_gb300.hmg import Solver
+        if name == "planar8":
+            w = I.planar_helmholtz(n=8, nlev=4, nmg=2)
+            hier, co = w.hier, w.coeffs
+        elif name == "sphereC4L5":
+            hier, co = _sphere()
+        elif name == "planar5L1":                 # one layer, odd columns: a ragged column block
+            w = I.planar_helmholtz(n=5, nlev=1, nmg=1)
+            hier, co = w.hier, w.coeffs
+        else:
+            raise KeyError(name)
+        ora = HO.HigherOrderHybrid(hier, co, 1)
+        gpu = Solver(hier, co, tol=1e-12, degree=1)
+        _CACHE[name] = (ora, gpu)
+    ora, gpu = _CACHE[name]
+    gpu.set_options(tol=1e-12, max_iter=200, precond="nonnested", n_smooth=1, krylov="bicgstab")
+    return ora, gpu
+
+
+def _rhs(ora, seed):
+    rng = np.random.default_rng(seed)
+    C = ora.mesh.ncell
+    return rng.standard_normal((C, ora.el.nu)), rng.standard_normal((C, ora.el.npr))
+
+
+NAMES = ["planar8", "sphereC4L5", "planar5L1"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_sizes_and_trace_operator(name):
+    ora, gpu = _pair(name)
+    assert gpu.ntrace == ora.T and gpu.degree == 1 and (gpu.nu, gpu.npr) == (36, 8)
+    x = np.random.default_rng(1).standard_normal(ora.T)
+    y = _np(gpu.apply_trace(_cuda(x)))
+    ref = ora.S @ x
+    scale = abs(ora.S) @ np.abs(x)
+    assert np.all(np.abs(y - ref) <= 1e-13 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_rhs_gamma_and_recovery(name):
+    ora, gpu = _pair(name)
+    Ru, Rpi = _rhs(ora, 2)
+    B = _np(gpu.trace_rhs(_cuda(Ru), _cuda(Rpi)))
+    Bo = ora.rhs(Ru, Rpi)
+    assert np.abs(B - Bo).max() <= 1e-13 * np.abs(Bo).max()
+    g = _np(gpu.gamma())
+    assert np.abs(g - ora.gamma).max() <= 1e-12 * np.abs(ora.gamma).max()
+    lam = np.random.default_rng(3).standard_normal(ora.T)
+    u, pi = gpu.reconstruct(_cuda(lam), _cuda(Ru), _cuda(Rpi))
+    uo, pio = ora.reconstruct(lam, Ru, Rpi)
+    assert np.abs(_np(u).reshape(uo.shape) - uo).max() <= 1e-11 * np.abs(uo).max()
+    assert np.abs(_np(pi).reshape(pio.shape) - pio).max() <= 1e-11 * np.abs(pio).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_line_smoother_and_two_level_cycle(name):
+    ora, gpu = _pair(name)
+    rng = np.random.default_rng(4)
+    lam, b = rng.standard_normal(ora.T), ora.S @ rng.standard_normal(ora.T)
+    got = _np(gpu.line_smooth(_cuda(b), _cuda(lam), 2))
+    want = ora.smooth(lam, b, 2)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+    r = ora.S @ rng.standard_normal(ora.T)
+    got = _np(gpu.precond(_cuda(r)))
+    want = ora.two_level(r)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_matches_oracle(name):
+    ora, gpu = _pair(name)
+    Ru, Rpi = _rhs(ora, 5)
+    lam, st = gpu.solve(_cuda(Ru), _cuda(Rpi))
+    lo, hist, sto = ora.solve(Ru, Rpi, 1e-12)
+    assert st["status"] == "ok" and sto == "ok"
+    assert np.linalg.norm(_np(lam) - lo) / np.linalg.norm(lo) < 1e-9
+    assert abs(st["iterations"] - (len(hist) - 1)) <= 1
+    n = min(len(hist), len(st["history"]), 5)
+    np.testing.assert_allclose(st["history"][:n], hist[:n], rtol=1e-7)
+    # host-driven loop and host buffers give the same answer bit for bit
+    gpu.set_options(graph=0)
+    lam2, st2 = gpu.solve(_cuda(Ru), _cuda(Rpi))
+    gpu.set_options(graph=1)
+    assert torch.equal(lam, lam2) and st2["iterations"] == st["iterations"]
+    lam_h, _sth = gpu.solve_host(Ru, Rpi)
+    assert np.array_equal(lam_h, _np(lam))
+
+
+def test_solve_at_degree_one_with_a_smooth_solution():
+    """The manufactured solution of the oracle's convergence pin, solved on the GPU: the same
+    discrete pressure, hence the same L2 error."""
+    H = 0.1
+
+    def pi_exact(x):
+        return np.sin(2 * np.pi * x[:, 0]) * np.cos(2 * np.pi * x[:, 1]) * np.cos(np.pi * x[:, 2] / H)
+
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz(n=8, nlev=8, nmg=2, top=H)
+    sigma = w.coeffs.sigma
+    ora = HO.HigherOrderHybrid(w.hier, w.coeffs, 1)
+    Ru, Rpi, l2 = HO.manufactured_rhs(ora, pi_exact, lambda x: (sigma + 8 * np.pi ** 2 + (np.pi / H) ** 2) * pi_exact(x))
+    gpu = Solver(w.hier, w.coeffs, tol=1e-12, degree=1)
+    try:
+        lam, st = gpu.solve(_cuda(Ru), _cuda(Rpi))
+        assert st["status"] == "ok"
+        _u, pi = gpu.reconstruct(lam, _cuda(Ru), _cuda(Rpi))
+        lo, _h, _s = ora.solve(Ru, Rpi, 1e-12)
+        _uo, pio = ora.reconstruct(lo, Ru, Rpi)
+        e_gpu, e_ora = l2(_np(pi).reshape(pio.shape)), l2(pio)
+        assert abs(e_gpu - e_ora) <= 1e-9 * e_ora
+    finally:
+        gpu.close()
+
+
+def test_degree_one_options_are_checked():
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    w = I.planar_helmholtz(n=4, nlev=2, nmg=1)
+    with pytest.raises(HmgError):
+        Solver(w.hier, w.coeffs, degree=1, precision="mixed")
+    ws = I.cubed_sphere(4, 3, nmg=1)            # the physical preset: degree 1 covers preset 1 only
+    with pytest.raises(HmgError):
+        Solver(ws.hier, ws.coeffs, degree=1)
+    s = Solver(w.hier, w.coeffs)                # degree 0 first, then switched to degree 1
+    n0 = s.ntrace
+    s.set_options(degree=1)
+    assert s.ntrace == 4 * n0 and s.nu == 36
+    s.set_options(degree=0)
+    assert s.ntrace == n0 and s.nu == 6
+    s.close()
