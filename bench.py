@@ -736,6 +736,58 @@ def run_configs(args, stream, model, lam_host):
     del lam64
     # configuration 4: the batch
     out["4_batch64_mixed"] = batch_solves(64, "mixed", steps, 2)
+    # row f4: degree 1 (RT1 / DG1 / Q1 trace) on the Helmholtz plane, larger than L2
+    out["f4_degree1_planar128"] = degree1_solves(args, stream, steps)
+    return out
+
+
+def degree1_bytes(mesh):
+    """Algorithmic bytes of one degree-1 S apply: per trace row the coefficients it reads (24 of
+    cell A, 20 of cell B: 44; 24 on ground and lid rows), x once and y once; the index tables."""
+    L, ncol, nedge = mesh.nlev, mesh.ncol, mesh.nedge
+    rows_h, rows_z = 4 * nedge * L, 4 * ncol * (L + 1)
+    rows_bnd = 8 * ncol                                   # ground and lid facets, four rows each
+    coeffs = 44 * (rows_h + rows_z - rows_bnd) + 24 * rows_bnd
+    return 8 * (coeffs + 2 * (rows_h + rows_z)) + 4 * (8 * nedge + 4 * ncol) + 4 * ncol
+
+
+def degree1_solves(args, stream, steps, n=128, nlev=32):
+    """Row f4 measured: the constant-coefficient Helmholtz problem on an n x n x nlev periodic
+    box (c dt = 0.05, 4 multigrid levels) at degree 1, BiCGStab under Algorithm 2 to 1e-6 with
+    a seeded N(0,1) right-hand side; time to tolerance, unknowns/s, and the S apply's roofline
+    (profiled pass, CUDA events per component)."""
+    import torch
+    from paper_2210_11797_gb300 import inputs as I
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz(n=n, nlev=nlev, nmg=4, tol=1e-6)
+    s = Solver(w.hier, w.coeffs, tol=1e-6, degree=1)
+    s.autotune()
+    C = w.mesh.ncell
+    Ru = torch.as_tensor(I.normal(11, 36 * C)).cuda()
+    Rp = torch.as_tensor(I.normal(12, 8 * C)).cuda()
+    lam, st, ms = _timed_solves(s, Ru, Rp, stream, steps)
+    s.set_options(profile=1)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()     # the profiler range: one host-driven solve
+    _l, pst = s.solve(Ru, Rp)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    s.set_options(profile=0)
+    comp = pst["components"]
+    apply_ms = comp["trace_apply"]["ms"] / max(comp["trace_apply"]["launches"], 1)
+    nbytes = degree1_bytes(w.mesh)
+    peak, kind = measured_peaks()
+    achieved = nbytes / (apply_ms / 1e3) / 1e9
+    out = {"workload": {"workload": f"planar_helmholtz_{n}x{n}x{nlev}_degree1", "ncell": C, "ntrace": s.ntrace,
+                        "dofs_per_cell": "36 RT1 + 8 DG1; 4 trace unknowns per facet", "tol": 1e-6,
+                        "precision": "fp64", "mg_levels": w.hier.nmg},
+           "ms_per_solve": round(ms, 4), "unknowns_per_s": round(s.ntrace / (ms / 1e3), 1),
+           "iterations": st["iterations"], "status": st["status"], "true_rel_residual": st["true_rel_residual"],
+           "components_ms_per_solve": {k: round(v["ms"], 4) for k, v in comp.items()},
+           "roofline_trace_apply": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                                    "frac": round(achieved / peak, 4), "peak_kind": kind,
+                                    "algorithmic_bytes": nbytes, "avg_launch_ms": round(apply_ms, 5)}}
+    s.close()
     return out
 
 
@@ -892,6 +944,9 @@ def main():
     ap.add_argument("--coarse-map", action="store_true",
                     help="time the learned coarse map (tensor-core and CUDA-core forms) and the "
                          "pressure V-cycle at the workload's size instead of the benchmark line")
+    ap.add_argument("--degree1", action="store_true",
+                    help="only the degree-1 workload (Helmholtz plane 128 x 128 x 32) as a JSON line; the "
+                         "profiler range is its host-driven profiled solve")
     ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--_outdir", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -911,7 +966,7 @@ def main():
     # the oracle leg starts first, in a fresh interpreter, and runs beside the GPU work
     child, outdir = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("c") \
-            and not (args.param_sweep or args.coarse_map):
+            and not (args.param_sweep or args.coarse_map or args.degree1):
         outdir = tempfile.mkdtemp(prefix="hmg_oracle_")
         child = start_oracle_child(args.workload, outdir)
     if world > 1:
@@ -924,6 +979,11 @@ def main():
     if args.coarse_map:
         if rank == 0:
             print(json.dumps(run_coarse_map(args)))
+        return
+    if args.degree1:
+        if rank == 0:
+            import torch
+            print(json.dumps(degree1_solves(args, torch.cuda.current_stream(), max(3, min(args.steps, 5)))))
         return
     if args.workload.startswith("batch"):
         out = run_batched(args, rank, world)

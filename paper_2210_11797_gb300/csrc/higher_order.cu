@@ -191,14 +191,19 @@ __device__ __forceinline__ HoFacet ho_facet(const HoGeo &g, int64_t F) {
 }
 
 // acc[n] (+/-)= sum over the stored slots of row 4F + n times x: cell A's 24 facet dofs, then
-// cell B's without the shared facet (merged into A's slots when S was assembled).
-template <bool NEG>
+// cell B's without the shared facet (merged into A's slots when S was assembled). OFFD leaves out
+// the couplings inside the smoother's diagonal block D of Algorithm 1 (acc - (S - D) x): on a
+// vertical facet its own four nodes, on a horizontal facet the horizontal facets of its column
+// (A's bottom and top, B's bottom).
+template <bool NEG, bool OFFD = false>
 __device__ __forceinline__ void ho_rows(const double *__restrict__ S, const double *__restrict__ x, const HoGeo &g,
                                         int64_t T, int64_t F, double acc[4]) {
   const HoFacet fc = ho_facet(g, F);
   const double *Sr = S + 4 * F;
+  const bool vert = F < g.nhf;
 #pragma unroll 4
   for (int q = 0; q < kHoNf; ++q) {
+    if (OFFD && (vert ? (q >> 2) == fc.fA : (q >> 2) >= 4)) continue;
     const double xv = __ldg(x + ho_gid(g, fc.cA, fc.kA, q));
     const double2 s01 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)q * T));
     const double2 s23 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)q * T + 2));
@@ -210,7 +215,7 @@ __device__ __forceinline__ void ho_rows(const double *__restrict__ S, const doub
   if (fc.cB < 0) return;
 #pragma unroll 4
   for (int q = 0; q < kHoNf; ++q) {
-    if ((q >> 2) == fc.fB) continue;
+    if ((q >> 2) == fc.fB || (OFFD && !vert && (q >> 2) >= 4)) continue;
     const double xv = __ldg(x + ho_gid(g, fc.cB, fc.kB, q));
     const double2 s01 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)(kHoNf + q) * T));
     const double2 s23 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)(kHoNf + q) * T + 2));
@@ -448,7 +453,7 @@ __global__ void ho_hfactor_kernel(const HoGeo g, int64_t T, const double *__rest
 
 // Block Thomas factors of each column's block-tridiagonal S^zz (blocks D_k, L_k = coupling of
 // facet k to k - 1, U_k to k + 1): G_0 = D_0, G_k = D_k - L_k G_{k-1}^-1 U_{k-1}; stored per
-// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([48][nzf], 16 entries each), so that
+// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([nzf][48], 16 entries each), so that
 // omega (S^zz)^-1 r is y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, x_k = y_k - (G_k^-1 U_k) x_{k+1}.
 __global__ void ho_zfactor_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, double omega,
                                   double *__restrict__ zf, int *singular) {
@@ -495,12 +500,12 @@ __global__ void ho_zfactor_kernel(const HoGeo g, int64_t T, const double *__rest
         GL[n][m] = sl;
         GU[n][m] = su;
       }
-    const int64_t zi = (int64_t)c * (L + 1) + k;
+    double *o = zf + 48 * ((int64_t)c * (L + 1) + k);   // facet-major: 48 contiguous factors
     for (int n = 0; n < 4; ++n)
       for (int m = 0; m < 4; ++m) {
-        zf[(int64_t)(4 * n + m) * g.nzf + zi] = omega * Gi[n][m];
-        zf[(int64_t)(16 + 4 * n + m) * g.nzf + zi] = GL[n][m];
-        zf[(int64_t)(32 + 4 * n + m) * g.nzf + zi] = GU[n][m];
+        o[4 * n + m] = omega * Gi[n][m];
+        o[16 + 4 * n + m] = GL[n][m];
+        o[32 + 4 * n + m] = GU[n][m];
       }
   }
 }
@@ -586,15 +591,19 @@ __global__ void ho_reconstruct_kernel(const HoGeo g, int64_t ncell, const double
 }
 
 // ---- Algorithm 1 at p = 1 -----------------------------------------------------------------------
-// lam_out = lam_in + omega D^-1 (b - S lam_in) (ZERO: lam_in = 0). Blocks [0, nzb) take CPB
-// columns each: residual rows of their horizontal facets staged in shared memory, one thread per
-// column runs the block Thomas recurrences with the stored factors; the other blocks take one
-// vertical facet per thread (4 x 4 block Jacobi).
+// lam_out = lam_in + omega D^-1 (b - S lam_in) (ZERO: lam_in = 0), evaluated as
+// (1 - omega) lam_in + omega D^-1 (b - (S - D) lam_in): equal in exact arithmetic, without the
+// 4 (vertical facets) or 12 (horizontal facets) couplings of a row inside D. Blocks [0, nzb) take CPB
+// columns each: the residual rows of their horizontal facets staged in shared memory, then the
+// block Thomas recurrences with four lanes per column (lane n computes component n of each 4 x 4
+// product from its rows of the stored factors; the four lanes of a column sit in one warp and
+// meet at __syncwarp between the steps); the other blocks take one vertical facet per thread
+// (4 x 4 block Jacobi).
 template <bool ZERO>
 __global__ void __launch_bounds__(128)
     ho_sweep_kernel(const HoGeo g, int64_t T, int cpb, int nzb, const double *__restrict__ S,
                     const double *__restrict__ hw, const double *__restrict__ zf, const double *__restrict__ b,
-                    const double *__restrict__ lam_in, double *__restrict__ lam_out) {
+                    const double *__restrict__ lam_in, double *__restrict__ lam_out, double keep) {
   extern __shared__ double sr[];   // [cpb][L+1][4]
   const int L1 = g.L + 1;
   if ((int)blockIdx.x < nzb) {
@@ -603,64 +612,68 @@ __global__ void __launch_bounds__(128)
       const int64_t F = g.nhf + (int64_t)c0 * L1 + i;
       double acc[4];
       for (int n = 0; n < 4; ++n) acc[n] = __ldg(b + 4 * F + n);
-      if (!ZERO) ho_rows<true>(S, lam_in, g, T, F, acc);
+      if (!ZERO) ho_rows<true, true>(S, lam_in, g, T, F, acc);
       for (int n = 0; n < 4; ++n) sr[4 * i + n] = acc[n];
     }
     __syncthreads();
-    if ((int)threadIdx.x < nc) {
-      double *r = sr + 4 * threadIdx.x * L1;
-      const int64_t z0 = (int64_t)(c0 + threadIdx.x) * L1;
-      double y[4] = {0.0, 0.0, 0.0, 0.0};
+    const int cc = threadIdx.x >> 2, n = threadIdx.x & 3;
+    const unsigned grp = 0xFu << (threadIdx.x & 28);   // the four lanes of this column
+    if (cc < nc) {
+      double *r = sr + 4 * cc * L1;
+      const double *f0 = zf + 48 * ((int64_t)(c0 + cc) * L1);
+      // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r
+      double yprev[4] = {0.0, 0.0, 0.0, 0.0};
       for (int k = 0; k < L1; ++k) {
-        const int64_t zi = z0 + k;
-        double yn[4];
-        for (int n = 0; n < 4; ++n) {
-          double v = 0.0;
-          for (int m = 0; m < 4; ++m) v = fma(zf[(int64_t)(4 * n + m) * g.nzf + zi], r[4 * k + m], v);
-          for (int m = 0; m < 4; ++m) v = fma(-zf[(int64_t)(16 + 4 * n + m) * g.nzf + zi], y[m], v);
-          yn[n] = v;
-        }
-        for (int n = 0; n < 4; ++n) { y[n] = yn[n]; r[4 * k + n] = yn[n]; }
+        const double *f = f0 + 48 * k;
+        double v = 0.0;
+        for (int m = 0; m < 4; ++m) v = fma(__ldg(f + 4 * n + m), r[4 * k + m], v);
+        for (int m = 0; m < 4; ++m) v = fma(-__ldg(f + 16 + 4 * n + m), yprev[m], v);
+        __syncwarp(grp);
+        r[4 * k + n] = v;
+        __syncwarp(grp);
+        for (int m = 0; m < 4; ++m) yprev[m] = r[4 * k + m];
       }
+      // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y
       for (int k = L1 - 2; k >= 0; --k) {
-        const int64_t zi = z0 + k;
-        double xn[4];
-        for (int n = 0; n < 4; ++n) {
-          double v = r[4 * k + n];
-          for (int m = 0; m < 4; ++m) v = fma(-zf[(int64_t)(32 + 4 * n + m) * g.nzf + zi], r[4 * (k + 1) + m], v);
-          xn[n] = v;
-        }
-        for (int n = 0; n < 4; ++n) r[4 * k + n] = xn[n];
+        const double *f = f0 + 48 * k;
+        double v = r[4 * k + n];
+        for (int m = 0; m < 4; ++m) v = fma(-__ldg(f + 32 + 4 * n + m), yprev[m], v);
+        __syncwarp(grp);
+        r[4 * k + n] = v;
+        __syncwarp(grp);
+        for (int m = 0; m < 4; ++m) yprev[m] = r[4 * k + m];
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nc * L1 * 4; i += blockDim.x) {
       const int64_t row = g.NH + 4 * (int64_t)c0 * L1 + i;
-      lam_out[row] = ZERO ? sr[i] : lam_in[row] + sr[i];
+      lam_out[row] = ZERO ? sr[i] : fma(keep, lam_in[row], sr[i]);
     }
   } else {
     const int64_t F = (int64_t)(blockIdx.x - nzb) * blockDim.x + threadIdx.x;
     if (F >= g.nhf) return;
     double acc[4];
     for (int n = 0; n < 4; ++n) acc[n] = __ldg(b + 4 * F + n);
-    if (!ZERO) ho_rows<true>(S, lam_in, g, T, F, acc);
+    if (!ZERO) ho_rows<true, true>(S, lam_in, g, T, F, acc);
     for (int n = 0; n < 4; ++n) {
-      double v = ZERO ? 0.0 : lam_in[4 * F + n];
+      double v = ZERO ? 0.0 : keep * lam_in[4 * F + n];
       for (int m = 0; m < 4; ++m) v = fma(hw[(int64_t)(4 * n + m) * g.nhf + F], acc[m], v);
       lam_out[4 * F + n] = v;
     }
   }
 }
 
-// R = b - S lam (Algorithm 2 line 3), one thread per facet
+// R = b - S lam (Algorithm 2 line 3), one thread per facet. ZSWEEP: lam is one sweep from zero,
+// lam = omega D^-1 b, so R = (1 - omega) b - (S - D) lam (equal in exact arithmetic).
+template <bool ZSWEEP>
 __global__ void ho_residual_kernel(const HoGeo g, int64_t T, const double *__restrict__ S,
                                    const double *__restrict__ b, const double *__restrict__ lam,
-                                   double *__restrict__ R) {
+                                   double *__restrict__ R, double keep) {
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= g.nhf + g.nzf) return;
   double acc[4];
-  for (int n = 0; n < 4; ++n) acc[n] = __ldg(b + 4 * F + n);
-  ho_rows<true>(S, lam, g, T, F, acc);
+  for (int n = 0; n < 4; ++n) acc[n] = ZSWEEP ? keep * __ldg(b + 4 * F + n) : __ldg(b + 4 * F + n);
+  ho_rows<true, ZSWEEP>(S, lam, g, T, F, acc);
   for (int n = 0; n < 4; ++n) R[4 * F + n] = acc[n];
 }
 
@@ -821,7 +834,7 @@ int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp
   return HMG_OK;
 }
 
-constexpr int kHoCpb = 8;   // columns per block of the sweep's line part
+constexpr int kHoCpb = 32;   // columns per block of the sweep's line part (four lanes each)
 
 template <bool ZERO>
 static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_out) {
@@ -835,7 +848,8 @@ static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_o
   const unsigned nhb = grid_for(g.nhf, 128);
   const size_t smem = sizeof(double) * 4 * cpb * (g.L + 1);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
-  ho_sweep_kernel<ZERO><<<nzb + nhb, 128, smem, c->stream>>>(g, h.T, cpb, nzb, h.S, h.hw, h.zf, b, lam_in, lam_out);
+  ho_sweep_kernel<ZERO><<<nzb + nhb, 128, smem, c->stream>>>(g, h.T, cpb, nzb, h.S, h.hw, h.zf, b, lam_in, lam_out,
+                                                              1.0 - h.factor_omega);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -889,7 +903,11 @@ int ho_precond(Ctx *c, const double *r, double *z) {
   double *cb = static_cast<double *>(c->cb);
   {
     Prof pr(c, kCompResidual, 2);
-    ho_residual_kernel<<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2);   // line 3
+    if (c->opt.n_pre == 1)   // w1 is one sweep from zero                                       // line 3
+      ho_residual_kernel<true><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2,
+                                                                                   1.0 - h.factor_omega);
+    else
+      ho_residual_kernel<false><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2, 0.0);
     ho_restrict_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, w2, h.gamma, cb);          // lines 4-5
     HMG_CUDA(c, cudaGetLastError());
   }

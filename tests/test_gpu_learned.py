@@ -331,12 +331,15 @@ def test_learned_mode_without_a_model_is_an_error():
 
 
 def test_trained_network_in_the_solve():
-    """What the trained network does inside the solve, measured against the method without
-    it on a right-hand side it was not trained on. As the V-cycle's initial guess it must not
-    cost flexible GMRES steps (at most one more than the plain V-cycle); as the whole coarse
-    solve, the stall fallback must bring the solve to the tolerance. (With this network's
-    one-column horizontal reach the trained map does not reduce the step count of the
-    V-cycle form; the measured counts are kept in the record of the bench's variants.)"""
+    """What the trained network does inside the solve, measured against the method without it
+    on a right-hand side it was not trained on (C12 x 30, pairs from four other right-hand
+    sides). Recorded, FGMRES steps to 1e-6: the plain V-cycle, the trained map as the V-cycle's
+    initial guess, the trained map alone (with the stall fallback), and the untrained map alone.
+    What holds and is asserted: training lowers the held-out loss; the trained map as the
+    initial guess costs at most one step more than the plain V-cycle; alone, the stall fallback
+    brings both the trained and the untrained map to the tolerance.
+    (With one column of horizontal reach the map does not beat the V-cycle it stands in for; the
+    bench records the same comparison at C96 and C192.)"""
     from paper_2210_11797_gb300.hmg import Solver
     w = I.cubed_sphere(12, 30, seed=0)
     s = Solver(w.hier, w.coeffs, tol=1e-6)
@@ -351,6 +354,10 @@ def test_trained_network_in_the_solve():
     cols = I.panel_patch_columns(12, 6, 6, 6, 3)
     pair = np.repeat(np.arange(xs.shape[0], dtype=np.int32), len(cols))
     xo, to = s.extract_patches(xs, ts, _cuda(pair, np.int32), _cuda(np.tile(cols, (xs.shape[0], 1)), np.int32))
+    held = I.cubed_sphere(12, 30, seed=2000)                  # held-out pairs for the loss
+    xh, th, _lam, _st = s.collect_coarse_pairs(_cuda(held.Rub), _cuda(held.Rpi), 8)
+    ph = np.repeat(np.arange(xh.shape[0], dtype=np.int32), len(cols))
+    xho, tho = s.extract_patches(xh, th, _cuda(ph, np.int32), _cuda(np.tile(cols, (xh.shape[0], 1)), np.int32))
     test = I.cubed_sphere(12, 30, seed=99)
     Rub, Rpi = _cuda(test.Rub), _cuda(test.Rpi)
 
@@ -358,13 +365,20 @@ def test_trained_network_in_the_solve():
         s.set_options(krylov="fgmres", tol=1e-6, max_iter=400, **opt)
         _lam, st = s.solve(Rub, Rpi)
         assert st["status"] == "ok" and st["true_rel_residual"] < 2e-6
-        return st["iterations"]
+        return st["iterations"], st["coarse_fallback"]
 
-    plain = steps(coarse="vcycle")
+    plain, _f = steps(coarse="vcycle")
+    untrained_alone, _fu = steps(coarse="learned", stall_ratio=0.9)
+    loss_before, _g = s.coarse_model_grad(xho, tho, 6, 6)
     hist = s.train_coarse_model(xo, to, 6, 6, batch=32, epochs=20, lr=2e-3, seed=1)
-    assert hist[-1] < hist[0]
-    assert steps(coarse="learned_vcycle") <= plain + 1
-    steps(coarse="learned", stall_ratio=0.9)
+    loss_after, _g = s.coarse_model_grad(xho, tho, 6, 6)
+    guess, _fg = steps(coarse="learned_vcycle")
+    alone, fallback = steps(coarse="learned", stall_ratio=0.9)
+    print(f"FGMRES steps to 1e-6 on a held-out right-hand side: plain V-cycle {plain}, trained map as its "
+          f"initial guess {guess}, trained map alone {alone} (fallback {fallback}), untrained map alone "
+          f"{untrained_alone}; held-out loss {loss_before:.3f} -> {loss_after:.3f}")
+    assert hist[-1] < hist[0] and loss_after < loss_before
+    assert guess <= plain + 1
     s.close()
 
 
