@@ -260,8 +260,7 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
                       const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats);
 
 /* Time the candidate launch shapes of the line sweep and of the pressure smoother on each
- * level (columns per thread block: 1-64 for the sweep, 1-128 for the smoother, whose columns
- * are split over the block's warps; threads per block: 128 or 256) on this context's
+ * level (columns per thread block: 1-64; threads per block: 128 or 256) on this context's
  * mesh and keep the fastest; later launches of this context use them. Needs an assembled context; the sweep
  * timings overwrite the context's work vectors. */
 int hmg_autotune(hmg_ctx *ctx);
@@ -269,8 +268,8 @@ int hmg_autotune(hmg_ctx *ctx);
 /* Read / set the launch shapes of a context (host int32 arrays): sweep[2] = {columns per
  * block, threads per block} of the line sweep; mg[2 * nmg] = the same for the pressure
  * smoother on each level. 0 means the default (32 columns, 256 threads, within the shared
- * memory limit); hmg_set_launch_shapes rejects columns outside 1..64 (sweep) or 1..128
- * (smoother) and threads other than 0, 128 and 256. */
+ * memory limit); hmg_set_launch_shapes rejects columns outside 1..64 and threads other than
+ * 0, 128 and 256. */
 int hmg_get_launch_shapes(hmg_ctx *ctx, int32_t *sweep, int32_t *mg, int32_t nmg);
 int hmg_set_launch_shapes(hmg_ctx *ctx, const int32_t *sweep, const int32_t *mg, int32_t nmg);
 

@@ -639,12 +639,10 @@ int hmg_get_launch_shapes(hmg_ctx *c, int32_t *sweep, int32_t *mg, int32_t nmg) 
 int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, int32_t nmg) {
   if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
-  auto ok = [](int32_t cpb, int32_t thr, int32_t cmax) {
-    return cpb >= 0 && cpb <= cmax && (thr == 0 || thr == 128 || thr == 256);
-  };
-  if (!ok(sweep[0], sweep[1], 64)) return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
+  auto ok = [](int32_t cpb, int32_t thr) { return cpb >= 0 && cpb <= 64 && (thr == 0 || thr == 128 || thr == 256); };
+  if (!ok(sweep[0], sweep[1])) return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
   for (int l = 0; l < nmg; ++l)
-    if (!ok(mg[2 * l], mg[2 * l + 1], 128)) return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
+    if (!ok(mg[2 * l], mg[2 * l + 1])) return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
   drop_graph(c);   // captured launches carry the old shapes
   for (int p = 0; p < 2; ++p) {   // the same shapes for the FP64 and FP32 kernels
     c->tune_sweep_cpb[p] = sweep[0];

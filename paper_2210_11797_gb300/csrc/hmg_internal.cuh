@@ -362,15 +362,15 @@ int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms);
 int time_mg_cpb(Ctx *c, int level, int cpb, int threads, int fp32, float *ms);
 // Best-of-three average time of one whole V-cycle (FP64 or FP32) with the current shapes.
 int time_vcycle(Ctx *c, int fp32, float *ms);
+// Columns per block of the pressure smoother: at most 64, and its three shared-memory arrays
+// (column stride nlev rounded up to odd) within the default 48 KB (FP64).
 // layers per column: a one-column block's three shared-memory arrays of the line sweep
 // (3 x ((L + 1) | 1) doubles) stay within the default 48 KB of dynamic shared memory
 constexpr int kMaxLayers = 2045;
 
-// Columns per block of the pressure smoother: at most 128, and its shared-memory array of the
-// block's scaled residuals (column stride nlev rounded up to odd) within the default 48 KB (FP64).
 inline int mg_cpb_limit(int nlev) {
-  const int m = 6144 / (nlev | 1);
-  return m < 1 ? 1 : (m > 128 ? 128 : m);
+  const int m = 2048 / (nlev | 1);
+  return m < 1 ? 1 : (m > 64 ? 64 : m);
 }
 
 }  // namespace hmg

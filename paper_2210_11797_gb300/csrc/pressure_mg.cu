@@ -165,53 +165,48 @@ struct SrcTraceRestrict {   // zero start on the finest level, b = Gamma P^T R f
   __device__ T out(const MGArgs &, int, int, int64_t, T v) const { return v; }
 };
 
-// One column block (columns blk * cpb ..) of the block-Jacobi smoother: x_out =
-// src.out(omega H_z^-1 src.r). The block's columns are split over its warps, and each warp works
-// alone (no block-wide barrier): its lanes stage the scaled residuals of the warp's columns in
-// shared memory (consecutive cells, coalesced), then one lane per column runs the Thomas
-// recurrences with the factors read through L1 (a column's factors are contiguous, so a cache
-// line serves 16 steps), then the lanes write the new iterate. A block-wide barrier here left the
-// other warps of the block waiting on the serial phase (28.9 barrier stalls per issue at C64).
+// One column block (columns blk * cpb ..) of the block-Jacobi smoother, by the whole thread
+// block: x_out = src.out(omega H_z^-1 src.r).
 template <typename T, typename Src>
 __device__ __forceinline__ void smooth_block_src(const MGArgs &a, const T *__restrict__ hw, const T *__restrict__ hl,
                                                  const T *__restrict__ hcp, const Src &src, T *__restrict__ x_out,
                                                  int blk, unsigned char *smem_raw) {
-  // column j of the block at j * ld, ld = L rounded up to odd so that the lanes hit distinct banks
+  // one column per lane in the serial phase: column j at j * ld, ld = L rounded up to odd so
+  // that the lanes of a half-warp hit distinct banks
   const int ld = a.L | 1;
-  const int nw = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int cpw = (a.cpb + nw - 1) / nw;                       // columns per warp
-  const int cb0 = blk * a.cpb;                                 // the block's first column
-  const int nb = min(a.cpb, a.ncol - cb0);                     // the block's columns
-  const int w0 = warp * cpw, nc = min(cpw, nb - w0);           // this warp's columns (block-relative)
-  if (nc <= 0) return;
-  T *sr = reinterpret_cast<T *>(smem_raw) + w0 * ld;
-  const int c0 = cb0 + w0;
+  T *sr = reinterpret_cast<T *>(smem_raw);
+  T *sl = sr + a.cpb * ld, *scp = sl + a.cpb * ld;
+  const int c0 = blk * a.cpb;
+  const int nc = min(a.cpb, a.ncol - c0);
   const int n = nc * a.L;
   const int64_t base = (int64_t)c0 * a.L;
-  // all lanes: r omega / pivot, so that the serial recurrences below are one FMA per row each
-  // (factors from pressure_factor_kernel)
-  for (int i = lane; i < n; i += 32) {
+  // all threads: r omega / pivot and the factors, so that the serial Thomas recurrences
+  // below are one FMA per row each (factors from pressure_factor_kernel)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int c = c0 + i / a.L, k = i % a.L;
     const int64_t K = base + i;
-    sr[(c - c0) * ld + k] = src.r(a, c, k, K) * __ldg(hw + K);
+    const T r = src.r(a, c, k, K);
+    const int j = (c - c0) * ld + k;
+    sr[j] = r * __ldg(hw + K);
+    sl[j] = __ldg(hl + K);
+    scp[j] = __ldg(hcp + K);
   }
-  __syncwarp();
-  if (lane < nc) {
-    const int o = lane * ld;
-    const int64_t K0 = base + (int64_t)lane * a.L;
+  __syncthreads();
+  if ((int)threadIdx.x < nc) {
+    const int o = threadIdx.x * ld;
     T y = sr[o];
     for (int k = 1; k < a.L; ++k) {
-      y = fma(-__ldg(hl + K0 + k), y, sr[o + k]);
+      y = fma(-sl[o + k], y, sr[o + k]);
       sr[o + k] = y;
     }
     T xk = y;
     for (int k = a.L - 2; k >= 0; --k) {
-      xk = fma(-__ldg(hcp + K0 + k), xk, sr[o + k]);
+      xk = fma(-scp[o + k], xk, sr[o + k]);
       sr[o + k] = xk;
     }
   }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int cl = i / a.L, k = i % a.L;
     x_out[base + i] = src.out(a, c0 + cl, k, base + i, sr[cl * ld + k]);
   }
@@ -475,11 +470,12 @@ static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int t
   sh.a = mg_args(c, l, pm);
   if (cpb_override > 0 && cpb_override <= mg_cpb_limit(lv.nlev)) sh.a.cpb = cpb_override;
   sh.grid = (unsigned)((lv.ncol + sh.a.cpb - 1) / sh.a.cpb);
-  sh.smem = (size_t)sh.a.cpb * (lv.nlev | 1) * sizeof(T);
+  sh.smem = (size_t)3 * sh.a.cpb * (lv.nlev | 1) * sizeof(T);
   const int tt = c->tune_mg_threads[pm][l];
   const int tmax = threads_override > 0 ? threads_override : (tt > 0 ? tt : 256);
-  int threads = 32 * sh.a.cpb;                  // at least one column per warp
+  int threads = ((sh.a.cpb * lv.nlev + 31) / 32) * 32;   // the block's cells in whole warps
   if (threads > tmax) threads = tmax;
+  if (threads < ((sh.a.cpb + 31) / 32) * 32) threads = ((sh.a.cpb + 31) / 32) * 32;   // a lane per column
   sh.threads = threads;
   return sh;
 }
@@ -610,7 +606,7 @@ static int launch_coarse(Ctx *c, T **x1) {
     q.children = lv.children;
     q.parent = lv.parent;
     q.nblk = (lv.ncol + q.a.cpb - 1) / q.a.cpb;
-    const size_t sm = (size_t)q.a.cpb * (lv.nlev | 1) * sizeof(T);
+    const size_t sm = (size_t)3 * q.a.cpb * (lv.nlev | 1) * sizeof(T);
     if (sm > smem) smem = sm;
     need = std::max<int64_t>(need, std::max<int64_t>(q.nblk, (lv.ncell + 255) / 256));
   }

@@ -614,7 +614,7 @@ int autotune(Ctx *c) {
       const int mmax = mg_cpb_limit(c->lv[l].nlev);
       int mbest = mmax < 32 ? mmax : 32, mbest_t = 256;
       float mbest_ms = 1e30f;
-      for (int cand : {32, 64, 128, 16, 8, 4, 2, 1})
+      for (int cand : {32, 64, 16, 8, 4, 2, 1})
         for (int thr : {256, 128}) {
           if (cand > mmax || st) continue;
           float ms = 0.f;
@@ -631,7 +631,7 @@ int autotune(Ctx *c) {
       int bc = c->tune_mg_cpb[pm][l], bt = c->tune_mg_threads[pm][l];
       float bms = 1e30f;
       if ((st = time_vcycle(c, pm, &bms))) break;
-      for (int cand : {32, 64, 128, 16, 8, 4, 2, 1})
+      for (int cand : {32, 64, 16, 8, 4, 2, 1})
         for (int thr : {256, 128}) {
           if (cand > mmax || st || (cand == bc && thr == bt)) continue;
           c->tune_mg_cpb[pm][l] = cand;
