@@ -31,9 +31,9 @@ UNIT = "trace unknowns/s"
 # DRAM traffic per launch of the dominant kernel from an ncu capture (see profiles/), keyed
 # by the sha256 of the kernel sources it was taken on; a changed source makes it stale (null).
 # C96: dram__bytes_read.sum + dram__bytes_write.sum of the full sweep, captured at full size
-# (a one-pass metric set), mean of two launches.
+# (a one-pass metric set), mean of two launches (585.7 + 24.0 and 584.2 + 24.5 MB).
 TRAFFIC = {
-    "line_sweep:c96:fp64:ed4bc81c8a240f39": 656322688,
+    "line_sweep:c96:fp64:d4db54aecf673935": 609250048,
 }
 
 
@@ -542,6 +542,52 @@ def coarse_map_bytes(ncell, elem=8):
     return ncell * ((2 * elem + 64) + (64 + elem))
 
 
+def run_train(args):
+    """The learned map's training on its own: 96 pairs from six FP64 solves of the workload,
+    TRAIN_PATCHES random 16 x 16 patches, then `--steps` epochs (batch 64) timed with CUDA
+    events; the profiler range is the first epoch."""
+    import numpy as np
+    import torch
+    from paper_2210_11797_gb300 import inputs as I
+    from paper_2210_11797_gb300.hmg import Solver
+    w = workload_spec(args.workload)
+    solver = Solver(w.hier, w.coeffs, tol=w.tol)
+    solver.set_coarse_model(I.flatten_coarse_model(I.coarse_model_init(0)))
+    m = w.hier.meshes[0]
+    n = m.n_per_side
+    xs, ts = [], []
+    for i in range(6):
+        rub, rpi = I.draw_rhs(m.ncell, 1000 + i, "normal")
+        x, t, _l, _st = solver.collect_coarse_pairs(torch.as_tensor(rub.ravel()).cuda(), torch.as_tensor(rpi).cuda(), 16)
+        xs.append(x)
+        ts.append(t)
+    xs, ts = torch.cat(xs), torch.cat(ts)
+    P = 16 if n >= 32 else 4
+    pair, cols = I.random_panel_patches(n, 6 if m.geometry == 1 else 1, P, P, TRAIN_PATCHES, xs.shape[0], 7)
+    xo, to = solver.extract_patches(xs, ts, torch.as_tensor(pair).cuda(), torch.as_tensor(cols).cuda())
+    del xs, ts
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h1 = solver.train_coarse_model(xo, to, P, P, batch=64, epochs=1, lr=1e-3, seed=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    first = e0.elapsed_time(e1)
+    e0.record(stream)
+    hist = solver.train_coarse_model(xo, to, P, P, batch=64, epochs=max(args.steps, 1), lr=1e-3, seed=2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"mode": "train", "workload": w.name, "patches": int(xo.shape[0]), "batch": 64,
+           "ms_first_epoch": round(first, 2), "epochs": len(hist),
+           "ms_per_epoch": round(e0.elapsed_time(e1) / max(len(hist), 1), 2),
+           "loss": [round(float(v), 4) for v in np.concatenate([h1, hist])]}
+    solver.close()
+    return out
+
+
 def run_coarse_map(args):
     """The learned coarse map (growth axis: the network that may replace or seed the pressure
     V-cycle) timed at the workload's size beside the V-cycle it stands in for. Each forward is
@@ -944,6 +990,9 @@ def main():
     ap.add_argument("--coarse-map", action="store_true",
                     help="time the learned coarse map (tensor-core and CUDA-core forms) and the "
                          "pressure V-cycle at the workload's size instead of the benchmark line")
+    ap.add_argument("--train", action="store_true",
+                    help="time the learned map's training alone (pairs of the workload, 20,000 patches, "
+                         "--steps epochs); the profiler range is its first epoch")
     ap.add_argument("--degree1", action="store_true",
                     help="only the degree-1 workload (Helmholtz plane 128 x 128 x 32) as a JSON line; the "
                          "profiler range is its host-driven profiled solve")
@@ -966,7 +1015,7 @@ def main():
     # the oracle leg starts first, in a fresh interpreter, and runs beside the GPU work
     child, outdir = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("c") \
-            and not (args.param_sweep or args.coarse_map or args.degree1):
+            and not (args.param_sweep or args.coarse_map or args.degree1 or args.train):
         outdir = tempfile.mkdtemp(prefix="hmg_oracle_")
         child = start_oracle_child(args.workload, outdir)
     if world > 1:
@@ -979,6 +1028,10 @@ def main():
     if args.coarse_map:
         if rank == 0:
             print(json.dumps(run_coarse_map(args)))
+        return
+    if args.train:
+        if rank == 0:
+            print(json.dumps(run_train(args)))
         return
     if args.degree1:
         if rank == 0:
