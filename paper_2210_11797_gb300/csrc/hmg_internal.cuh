@@ -163,6 +163,7 @@ struct Ctx {
   void *nn_act = nullptr;
   int32_t *nn_diag = nullptr;
   void *nn_bimg = nullptr;        // W2 as the BF16 B operand image of the tensor-core layer (6 KB)
+  void *nn_bimg_t = nullptr;      // W2 transposed and flipped: the B operand of the training's dX (6 KB)
   TrainBufs train;
   bool coarse_fallback = false;   // set by the flexible Krylov loop when it stalls
   // set when a bounded wait of the tensor-core network layer ran out: from then on the

@@ -671,13 +671,265 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < 96) part1[(int64_t)blockIdx.x * 96 + threadIdx.x] = a1;
 }
 
-// Sum of per-block partials [nblocks][n] into out[n] (fixed order), one thread per entry.
-__global__ void sum_partials_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// ---- the training backward of the 32 -> 32 convolution on the tensor cores -----------------------
+// BF16 minibatch on patches: h1 [32][C] BF16 and ga2 [32][C] FP32 channel-major, x [C]. Per tile of
+// 128 padded rows (R = col (L + 2) + k + 1, rows k = -1 and L empty), two GEMMs on tcgen05.mma:
+//   dX: D1[m][i] = sum_{d, o} ga2[o](m + d - 1) W2[o][i][2 - d]   (M 128, N 32, K 96: six MMAs), then
+//       ga1 = D1 [h1 > 0] and gW1[i][d] += ga1[m][i] x(m + d - 1) on the CUDA cores;
+//   dW: D2[d 32 + i][o] += sum_m h1[i](m + d - 1) ga2[o](m)        (M 128 (96 used), N 32, K = the tile's
+//       128 rows: eight MMAs), accumulated in tensor memory over all the CTA's tiles.
+// A1 is ga2 on the tile's rows -1 .. 128 in the forward's layout ([8-channel group][row][8 channels]),
+// so the three taps are three start addresses a row apart; B1 is W2 transposed and flipped in the
+// forward's B layout. A2 ([m / 8][d 32 + i][8 m]) and B2 ([m / 8][o][8 m]) are K-major over the rows.
+// ga2 is FP32: it enters as two BF16 parts, hi = bf16(g) and lo = bf16(g - hi), two MMAs into the same
+// accumulator, so the products keep about 16 bits (W2 and h1 are BF16 values already).
+constexpr int kBwRows = 130;                                  // A1 rows: tile rows -1 .. 128
+constexpr int kBwLbo = kBwRows * 16;                          // A1: bytes between 8-channel groups
+constexpr int kBwA1 = 4 * kBwLbo;                             // 8,320 B per part
+constexpr int kBwB1 = ((2 * kBwA1 + 1023) / 1024) * 1024;     // W2 image (6 KB)
+constexpr int kBwA2 = kBwB1 + 6 * 1024;                       // h1 shifted: 16 x 128 x 16 B = 32 KB
+constexpr int kBwB2 = kBwA2 + 16 * 128 * 16;                  // ga2 over the rows: 16 x 32 x 16 B = 8 KB per part
+constexpr int kBwX = kBwB2 + 2 * 16 * 32 * 16;                // x on rows -1 .. 128 (130 floats)
+constexpr int kBwBar = kBwX + ((kBwRows * 4 + 15) / 16) * 16; // mbarrier (8 B), TMEM address (4 B)
+constexpr int kBwSmem = kBwBar + 64;
+constexpr int kBwRed = kBwA2;                                 // end-of-kernel reduction scratch (reuses A2)
+
+// W2 -> B1[i][kk], kk = d 32 + o, value W2[o][i][2 - d], in the core-matrix order of the forward's B
+__global__ void nn_pack_bt_kernel(const float *__restrict__ wts, __nv_bfloat16 *__restrict__ bimg) {
+  for (int e = threadIdx.x; e < 32 * 96; e += blockDim.x) {
+    const int i = e / 96, kk = e % 96, d = kk / 32, o = kk % 32;
+    const int off = ((kk >> 3) * 4 + (i >> 3)) * 64 + (i & 7) * 8 + (kk & 7);   // in elements
+    bimg[off] = __float2bfloat16(wts[kOffW2 + (o * 32 + i) * 3 + (2 - d)]);
+  }
+}
+
+struct BwArgs {
+  int ncol, L;
+  int64_t C, nrows, ntiles;
+};
+
+__device__ __forceinline__ int64_t bw_cell(const BwArgs &a, int64_t R) {   // cell of padded row R, or -1
+  if (R < 0 || R >= a.nrows) return -1;
+  const int64_t col = R / (a.L + 2);
+  const int k = (int)(R - col * (a.L + 2)) - 1;
+  return (k >= 0 && k < a.L) ? col * a.L + k : -1;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo) {
+  hi = __bfloat162float(__float2bfloat16(v));
+  lo = v - hi;
+}
+
+__global__ void __launch_bounds__(128)
+    nn_bwd1_tc_kernel(const BwArgs a, const __nv_bfloat16 *__restrict__ bt, const __nv_bfloat16 *__restrict__ h1,
+                      const float *__restrict__ ga2, const float *__restrict__ xin, float *__restrict__ part2,
+                      float *__restrict__ part1, int *__restrict__ wait_flag) {
+  extern __shared__ __align__(1024) unsigned char bw_smem[];
+  unsigned char *sA1 = bw_smem, *sB1 = bw_smem + kBwB1, *sA2 = bw_smem + kBwA2, *sB2 = bw_smem + kBwB2;
+  float *xs = reinterpret_cast<float *>(bw_smem + kBwX);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(bw_smem + kBwBar);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bw_smem + kBwBar + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {   // 64 TMEM columns: D1 at 0, D2 at 32
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // B1 (the W2 image), and the unused rows 96 .. 127 of A2, once
+  for (int e = tid; e < 6 * 1024 / 16; e += blockDim.x)
+    reinterpret_cast<uint4 *>(sB1)[e] = reinterpret_cast<const uint4 *>(bt)[e];
+  for (int e = tid; e < 16 * 32; e += blockDim.x) {
+    const int kg = e / 32, row = 96 + e % 32;
+    *reinterpret_cast<uint4 *>(sA2 + kg * 2048 + row * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  float acc1[96];                   // gW1[i][d] partials of this thread's rows
+#pragma unroll
+  for (int q = 0; q < 96; ++q) acc1[q] = 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = umma_idesc_bf16(kTcM, 32);
+  bool ok = true, first = true;
+  uint32_t phase = 0;
+  for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+    const int64_t R0 = t * kTcM;
+    // A1: ga2 on rows R0 - 1 .. R0 + 128, hi and lo parts; x on the same rows (BF16-rounded)
+    for (int e = tid; e < 4 * kBwRows; e += blockDim.x) {
+      const int r = e % kBwRows, g = e / kBwRows;
+      const int64_t cell = bw_cell(a, R0 - 1 + r);
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h0 = 0.f, l0 = 0.f, h1v = 0.f, l1 = 0.f;
+        if (cell >= 0) {
+          split_bf16(ga2[(int64_t)(8 * g + 2 * q) * a.C + cell], h0, l0);
+          split_bf16(ga2[(int64_t)(8 * g + 2 * q + 1) * a.C + cell], h1v, l1);
+        }
+        hw[q] = pack_bf16x2(h0, h1v);
+        lw[q] = pack_bf16x2(l0, l1);
+      }
+      *reinterpret_cast<uint4 *>(sA1 + g * kBwLbo + r * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(sA1 + kBwA1 + g * kBwLbo + r * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      if (g == 0) xs[r] = cell >= 0 ? rnd<__nv_bfloat16>(xin[cell]) : 0.f;
+    }
+    // A2: h1[i] on rows R0 + m + d - 1 (row d 32 + i, m = 8 kg .. 8 kg + 7)
+    for (int e = tid; e < 96 * 16; e += blockDim.x) {
+      const int kg = e % 16, row = e / 16, d = row / 32, i = row % 32;
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int64_t cell = bw_cell(a, R0 + 8 * kg + 2 * q + u + d - 1);
+          v[u] = cell >= 0 ? __bfloat162float(h1[(int64_t)i * a.C + cell]) : 0.f;
+        }
+        w[q] = pack_bf16x2(v[0], v[1]);
+      }
+      *reinterpret_cast<uint4 *>(sA2 + kg * 2048 + row * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    // B2: ga2[o] on rows R0 + m, hi and lo parts
+    for (int e = tid; e < 32 * 16; e += blockDim.x) {
+      const int kg = e % 16, o = e / 16;
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float hv[2] = {0.f, 0.f}, lv[2] = {0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int64_t cell = bw_cell(a, R0 + 8 * kg + 2 * q + u);
+          if (cell >= 0) split_bf16(ga2[(int64_t)o * a.C + cell], hv[u], lv[u]);
+        }
+        hw[q] = pack_bf16x2(hv[0], hv[1]);
+        lw[q] = pack_bf16x2(lv[0], lv[1]);
+      }
+      *reinterpret_cast<uint4 *>(sB2 + kg * 512 + o * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(sB2 + 8192 + kg * 512 + o * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a1 = smem_u32(sA1), b1 = smem_u32(sB1), a2 = smem_u32(sA2), b2 = smem_u32(sB2);
+      for (int part = 0; part < 2; ++part)   // dX: hi, then lo part of ga2
+        for (int s6 = 0; s6 < 6; ++s6) {
+          const int d = s6 >> 1, h = s6 & 1;
+          const uint64_t ad = umma_desc(a1 + part * kBwA1 + 2 * h * kBwLbo + d * 16, kBwLbo, 128);
+          const uint64_t bd = umma_desc(b1 + s6 * 2 * 4 * 128, 4 * 128, 128);
+          const uint32_t accum = (part | s6) ? 1u : 0u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                       "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+      for (int part = 0; part < 2; ++part)   // dW: B = hi, then lo part of ga2
+        for (int j = 0; j < 8; ++j) {
+          const uint64_t ad = umma_desc(a2 + 2 * j * 2048, 2048, 128);
+          const uint64_t bd = umma_desc(b2 + part * 8192 + 2 * j * 512, 512, 128);
+          const uint32_t accum = (first && part == 0 && j == 0) ? 0u : 1u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + 32u),
+                       "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+    }
+    first = false;
+    ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    if (!ok) {   // the MMAs may still be running: one more bounded wait before anything is freed
+      if (tid == 0) {
+        atomicExch(wait_flag, 1);
+        mbar_wait(bar, phase);
+      }
+      __syncthreads();
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = warp * 32 + lane;
+    const int64_t cell = bw_cell(a, R0 + m);
+    if (cell >= 0) {
+      const float x0 = xs[m], x1 = xs[m + 1], x2 = xs[m + 2];   // x(m - 1), x(m), x(m + 1)
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float g = __bfloat162float(h1[(int64_t)i * a.C + cell]) > 0.f ? __uint_as_float(r[i]) : 0.f;
+        acc1[3 * i] = fmaf(g, x0, acc1[3 * i]);
+        acc1[3 * i + 1] = fmaf(g, x1, acc1[3 * i + 1]);
+        acc1[3 * i + 2] = fmaf(g, x2, acc1[3 * i + 2]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // the next tile rewrites the operands and D1
+  }
+  // D2 -> gW2 partials (row d 32 + i, column o), then the gW1 partials reduced over the block
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    uint32_t r[32];
+    const uint32_t taddr = tmem + 32u + ((uint32_t)(warp * 32) << 16);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = warp * 32 + lane;
+    if (row < 96) {
+      const int d = row / 32, i = row % 32;
+#pragma unroll
+      for (int o = 0; o < 32; ++o)
+        part2[(int64_t)blockIdx.x * 3072 + (o * 32 + i) * 3 + d] = __uint_as_float(r[o]);
+    }
+  }
+  float *red = reinterpret_cast<float *>(bw_smem + kBwRed);   // [4 warps][96]
+#pragma unroll
+  for (int q = 0; q < 96; ++q) {
+    float v = acc1[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp * 96 + q] = v;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < 96) part1[(int64_t)blockIdx.x * 96 + tid] = (red[tid] + red[96 + tid]) + (red[192 + tid] + red[288 + tid]);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+// Sum of per-block partials [nblocks][n] into out[n]: one block per entry, its threads striding the
+// partials, then a fixed-order tree (deterministic for a given nblocks).
+__global__ void __launch_bounds__(256)
+    sum_partials_kernel(const float *__restrict__ part, int nblocks, int n, float *__restrict__ out) {
+  const int i = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * n + i];
-  out[i] = (float)s;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[(int64_t)b * n + i];
+  s = warp_sum(s);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[i] = (float)t;
+  }
 }
 
 __global__ void sum_loss_kernel(const double *__restrict__ part, int n, double *out) {
@@ -854,6 +1106,7 @@ static int nn_forward_mesh(Ctx *c, const Tin *bbar, Tout *out, const double *dH,
 // an image that matches them.
 int nn_pack_weights(Ctx *c) {
   nn_pack_b_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg));
+  nn_pack_bt_kernel<<<1, 256, 0, c->stream>>>(c->nn_w, static_cast<__nv_bfloat16 *>(c->nn_bimg_t));
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -884,12 +1137,15 @@ int nn_setup(Ctx *c) {
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   if ((st = dev_alloc(c, &c->nn_w, kNParams))) return st;
   {
     __nv_bfloat16 *bimg;
     if ((st = dev_alloc(c, &bimg, (size_t)32 * 96))) return st;   // cudaMalloc: 256-B aligned
     c->nn_bimg = bimg;
+    if ((st = dev_alloc(c, &bimg, (size_t)32 * 96))) return st;
+    c->nn_bimg_t = bimg;
   }
   float *tmp;
   if ((st = dev_alloc(c, &tmp, (size_t)kCh * f.ncell))) return st;   // BF16 h2 fits in half
@@ -928,15 +1184,38 @@ static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn
   nn_bwd3_kernel<A><<<g, 128, (96 + kNnCpb * (L + 2) + 96) * 4, c->stream>>>(c->nn_w, h3, tb.gy, ncol, L, kNnCpb,
                                                                              tb.ga3, tb.part3);
   nn_bwd2_kernel<A><<<g, 128, 0, c->stream>>>(c->nn_w, h2, tb.ga3, nb, ncol, L, kNnCpb, tb.ga2, tb.partM);
-  const int cpb1 = 64;
-  const unsigned g1 = (unsigned)((ncol + cpb1 - 1) / cpb1);
-  nn_bwd1_kernel<A><<<g1, 256, bwd1_smem(L), c->stream>>>(c->nn_w, h1, tb.ga2, x, ncol, L, cpb1, tb.part2, tb.part1);
-  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.part1, (int)g1, 96, grad + kOffW1);
-  sum_partials_kernel<<<grid_for(3072, 256), 256, 0, c->stream>>>(tb.part2, (int)g1, 3072, grad + kOffW2);
-  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.partM, (int)g, 96, grad + kOffM);
-  sum_partials_kernel<<<1, 128, 0, c->stream>>>(tb.part3, (int)g, 96, grad + kOffW3);
+  unsigned g1;
+  if (sizeof(A) == 2) {   // BF16 storage: the 32 -> 32 convolution's dX and dW on the tensor cores
+    BwArgs ba;
+    ba.ncol = ncol;
+    ba.L = L;
+    ba.C = C;
+    ba.nrows = (int64_t)ncol * (L + 2);
+    ba.ntiles = (ba.nrows + kTcM - 1) / kTcM;
+    const int64_t gmax = (int64_t)2 * c->num_sms;
+    g1 = (unsigned)(ba.ntiles < gmax ? ba.ntiles : gmax);
+    nn_bwd1_tc_kernel<<<g1, 128, kBwSmem, c->stream>>>(ba, static_cast<const __nv_bfloat16 *>(c->nn_bimg_t),
+                                                        reinterpret_cast<const __nv_bfloat16 *>(h1), tb.ga2, x,
+                                                        tb.part2, tb.part1, c->state + 3);
+  } else {
+    const int cpb1 = 64;
+    g1 = (unsigned)((ncol + cpb1 - 1) / cpb1);
+    nn_bwd1_kernel<A><<<g1, 256, bwd1_smem(L), c->stream>>>(c->nn_w, h1, tb.ga2, x, ncol, L, cpb1, tb.part2,
+                                                            tb.part1);
+  }
+  sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.part1, (int)g1, 96, grad + kOffW1);
+  sum_partials_kernel<<<3072, 256, 0, c->stream>>>(tb.part2, (int)g1, 3072, grad + kOffW2);
+  sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.partM, (int)g, 96, grad + kOffM);
+  sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.part3, (int)g, 96, grad + kOffW3);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
+}
+
+// Per-block partial-sum rows a minibatch of `ncol` columns needs: the column-block kernels' blocks
+// and the tensor-core backward's grid (at most two CTAs per SM).
+static int partial_blocks(const Ctx *c, int ncol) {
+  const int cb = (ncol + kNnCpb - 1) / kNnCpb + 1;
+  return cb > 2 * c->num_sms ? cb : 2 * c->num_sms;
 }
 
 int train_buffers(Ctx *c, int64_t cells, int nblocks_max) {
@@ -986,7 +1265,7 @@ int coarse_model_grad(Ctx *c, const float *x, const float *t, int nsamp, int nx,
   const int64_t cells = (int64_t)nsamp * nx * ny * L;
   int st;
   if ((st = nn_setup(c))) return st;
-  if ((st = train_buffers(c, cells, (int)(nsamp * nx * ny + kNnCpb - 1) / kNnCpb + 1))) return st;
+  if ((st = train_buffers(c, cells, partial_blocks(c, nsamp * nx * ny)))) return st;
   if ((st = dev_grow(c, &c->train.tn, &c->train.cap_tn, (size_t)nsamp))) return st;
   float *tn = c->train.tn;
   tnorm_kernel<<<nsamp, 256, 0, c->stream>>>(t, (int64_t)nx * ny * L, tn);
@@ -1015,7 +1294,7 @@ int train_coarse_model(Ctx *c, const float *x, const float *t, int nsamp, int nx
   int st;
   if ((st = nn_setup(c))) return st;
   if (batch < 1 || batch > nsamp) return fail(c, HMG_ERR_INVALID_ARG, "bad batch size");
-  if ((st = train_buffers(c, (int64_t)batch * per, (batch * P + kNnCpb - 1) / kNnCpb + 1))) return st;
+  if ((st = train_buffers(c, (int64_t)batch * per, partial_blocks(c, batch * P)))) return st;
   TrainBufs &T = c->train;
   if ((st = dev_grow(c, &T.tn, &T.cap_tn, (size_t)nsamp))) return st;
   if ((st = dev_grow(c, &T.order, &T.cap_order, (size_t)nsamp))) return st;

@@ -150,13 +150,15 @@ def test_gradient_matches_oracle():
 
 @pytest.mark.parametrize("nx,ny,ns", [(5, 4, 3), (8, 8, 4)])
 def test_bf16_gradient_matches_the_oracle_with_bf16_storage(nx, ny, ns):
-    """The gradient the training uses (BF16 weights and activations, FP32 accumulation)
-    against the oracle's gradient of the same network with BF16 storage (weights, input and
-    activations rounded to BF16, the rest FP64), per weight tensor, max-abs error relative to
-    the tensor's largest entry. The two differ by the GPU's FP32 sums and the few stored
-    activations those move across a BF16 rounding boundary (one BF16 step, 2^-8 relative).
-    Measured at most 4.8e-7; the bound 1e-4 leaves room for such boundary cases and is 200
-    times tighter than the 2e-2 a comparison with the FP64 network would need."""
+    """The gradient the training uses (BF16 weights and activations, FP32 accumulation; the
+    32 -> 32 convolution's dX and dW on the tensor cores with the FP32 gradient split into two
+    BF16 parts) against the oracle's gradient of the same network with BF16 storage (weights,
+    input and activations rounded to BF16, the rest FP64), per weight tensor, max-abs error
+    relative to the tensor's largest entry. The two differ by the GPU's FP32 sums, the ~2^-16
+    of the split products, and the few stored activations those move across a BF16 rounding
+    boundary (one BF16 step, 2^-8 relative). Measured at most 8.2e-7; the bound 1e-4 leaves room
+    for such boundary cases and is 200 times tighter than the 2e-2 a comparison with the FP64
+    network would need."""
     _w, _ora, gpu = _setup("planar16")
     params = I.coarse_model_init(7)
     gpu.set_coarse_model(I.flatten_coarse_model(params))
@@ -171,6 +173,31 @@ def test_bf16_gradient_matches_the_oracle_with_bf16_storage(nx, ny, ns):
         err = np.abs(gd[k] - g_ref[k]).max() / np.abs(g_ref[k]).max()
         print(f"BF16 gradient {k}: max-abs error / max = {err:.2e}")
         assert err < 1e-4, (k, err)
+
+
+@pytest.mark.parametrize("nlev,nx,ny,ns", [(45, 3, 2, 2), (128, 2, 2, 3)])
+def test_bf16_gradient_on_tall_columns(nlev, nx, ny, ns):
+    """The tensor-core backward tiles the padded rows (L + 2 per column) by 128: columns longer
+    than a tile, columns straddling tiles, a ragged last tile and the 128-level limit, against the
+    BF16-storage oracle as above."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.planar_helmholtz(n=4, nlev=nlev, nmg=1)
+    gpu = Solver(w.hier, w.coeffs, tol=w.tol)
+    try:
+        params = I.coarse_model_init(8)
+        gpu.set_coarse_model(I.flatten_coarse_model(params))
+        p = _rounded(params)
+        x, t = _patch_batch(nx, ny, ns, nlev, 61)
+        loss_ref, g_ref = _oracle_batch_grad(p, x, t, nx, ny, quant="bf16")
+        loss, g = gpu.coarse_model_grad(_cuda(x, np.float32), _cuda(t, np.float32), nx, ny, fp32=False)
+        assert abs(loss - loss_ref) / loss_ref < 1e-3
+        gd = I.unflatten_coarse_model(g)
+        for k in g_ref:
+            err = np.abs(gd[k] - g_ref[k]).max() / np.abs(g_ref[k]).max()
+            print(f"L={nlev} BF16 gradient {k}: max-abs error / max = {err:.2e}")
+            assert err < 1e-4, (k, err)
+    finally:
+        gpu.close()
 
 
 def test_adam_kernel_matches_oracle():
