@@ -690,7 +690,10 @@ constexpr int kBwB1 = ((2 * kBwA1 + 1023) / 1024) * 1024;     // W2 image (6 KB)
 constexpr int kBwA2 = kBwB1 + 6 * 1024;                       // h1 shifted: 16 x 128 x 16 B = 32 KB
 constexpr int kBwB2 = kBwA2 + 16 * 128 * 16;                  // ga2 over the rows: 16 x 32 x 16 B = 8 KB per part
 constexpr int kBwX = kBwB2 + 2 * 16 * 32 * 16;                // x on rows -1 .. 128 (130 floats)
-constexpr int kBwBar = kBwX + ((kBwRows * 4 + 15) / 16) * 16; // mbarrier (8 B), TMEM address (4 B)
+constexpr int kBwG = kBwX + ((kBwRows * 4 + 15) / 16) * 16;   // ga2 tile, FP32 [32][130]
+constexpr int kBwH = kBwG + 32 * kBwRows * 4;                 // h1 tile, BF16 [32][130]
+constexpr int kBwCell = kBwH + 32 * kBwRows * 2;              // cell of each row, int32 [130]
+constexpr int kBwBar = kBwCell + ((kBwRows * 4 + 15) / 16) * 16;   // mbarrier (8 B), TMEM address (4 B)
 constexpr int kBwSmem = kBwBar + 64;
 constexpr int kBwRed = kBwA2;                                 // end-of-kernel reduction scratch (reuses A2)
 
@@ -732,6 +735,9 @@ __global__ void __launch_bounds__(128)
   extern __shared__ __align__(1024) unsigned char bw_smem[];
   unsigned char *sA1 = bw_smem, *sB1 = bw_smem + kBwB1, *sA2 = bw_smem + kBwA2, *sB2 = bw_smem + kBwB2;
   float *xs = reinterpret_cast<float *>(bw_smem + kBwX);
+  float *Gs = reinterpret_cast<float *>(bw_smem + kBwG);
+  __nv_bfloat16 *Hs = reinterpret_cast<__nv_bfloat16 *>(bw_smem + kBwH);
+  int *cellr = reinterpret_cast<int *>(bw_smem + kBwCell);
   uint64_t *bar = reinterpret_cast<uint64_t *>(bw_smem + kBwBar);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bw_smem + kBwBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -762,55 +768,56 @@ __global__ void __launch_bounds__(128)
   uint32_t phase = 0;
   for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
     const int64_t R0 = t * kTcM;
-    // A1: ga2 on rows R0 - 1 .. R0 + 128, hi and lo parts; x on the same rows (BF16-rounded)
+    // the tile's rows R0 - 1 .. R0 + 128 (buffer row r = R - R0 + 1): their cells, then ga2 (FP32),
+    // h1 (BF16) and x (BF16-rounded) on them, each value read once from global memory
+    for (int r = tid; r < kBwRows; r += blockDim.x) {
+      const int64_t cell = bw_cell(a, R0 - 1 + r);
+      cellr[r] = (int)cell;
+      xs[r] = cell >= 0 ? rnd<__nv_bfloat16>(xin[cell]) : 0.f;
+    }
+    __syncthreads();
+    for (int e = tid; e < 32 * kBwRows; e += blockDim.x) {
+      const int ch = e / kBwRows, r = e - ch * kBwRows, cell = cellr[r];
+      Gs[e] = cell >= 0 ? ga2[(int64_t)ch * a.C + cell] : 0.f;
+      Hs[e] = cell >= 0 ? h1[(int64_t)ch * a.C + cell] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    // A1: ga2 on rows -1 .. 128 in the forward's layout, hi and lo parts
     for (int e = tid; e < 4 * kBwRows; e += blockDim.x) {
       const int r = e % kBwRows, g = e / kBwRows;
-      const int64_t cell = bw_cell(a, R0 - 1 + r);
       uint32_t hw[4], lw[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float h0 = 0.f, l0 = 0.f, h1v = 0.f, l1 = 0.f;
-        if (cell >= 0) {
-          split_bf16(ga2[(int64_t)(8 * g + 2 * q) * a.C + cell], h0, l0);
-          split_bf16(ga2[(int64_t)(8 * g + 2 * q + 1) * a.C + cell], h1v, l1);
-        }
+        float h0, l0, h1v, l1;
+        split_bf16(Gs[(8 * g + 2 * q) * kBwRows + r], h0, l0);
+        split_bf16(Gs[(8 * g + 2 * q + 1) * kBwRows + r], h1v, l1);
         hw[q] = pack_bf16x2(h0, h1v);
         lw[q] = pack_bf16x2(l0, l1);
       }
       *reinterpret_cast<uint4 *>(sA1 + g * kBwLbo + r * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
       *reinterpret_cast<uint4 *>(sA1 + kBwA1 + g * kBwLbo + r * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      if (g == 0) xs[r] = cell >= 0 ? rnd<__nv_bfloat16>(xin[cell]) : 0.f;
     }
-    // A2: h1[i] on rows R0 + m + d - 1 (row d 32 + i, m = 8 kg .. 8 kg + 7)
+    // A2: h1[i] on rows m + d - 1 (buffer row m + d), row d 32 + i, m = 8 kg .. 8 kg + 7
     for (int e = tid; e < 96 * 16; e += blockDim.x) {
       const int kg = e % 16, row = e / 16, d = row / 32, i = row % 32;
+      const __nv_bfloat16 *hr = Hs + i * kBwRows + 8 * kg + d;
       uint32_t w[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float v[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int64_t cell = bw_cell(a, R0 + 8 * kg + 2 * q + u + d - 1);
-          v[u] = cell >= 0 ? __bfloat162float(h1[(int64_t)i * a.C + cell]) : 0.f;
-        }
-        w[q] = pack_bf16x2(v[0], v[1]);
-      }
+      for (int q = 0; q < 4; ++q) w[q] = pack_bf16x2(__bfloat162float(hr[2 * q]), __bfloat162float(hr[2 * q + 1]));
       *reinterpret_cast<uint4 *>(sA2 + kg * 2048 + row * 16) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    // B2: ga2[o] on rows R0 + m, hi and lo parts
+    // B2: ga2[o] on rows m (buffer row m + 1), hi and lo parts
     for (int e = tid; e < 32 * 16; e += blockDim.x) {
       const int kg = e % 16, o = e / 16;
+      const float *gr = Gs + o * kBwRows + 8 * kg + 1;
       uint32_t hw[4], lw[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float hv[2] = {0.f, 0.f}, lv[2] = {0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int64_t cell = bw_cell(a, R0 + 8 * kg + 2 * q + u);
-          if (cell >= 0) split_bf16(ga2[(int64_t)o * a.C + cell], hv[u], lv[u]);
-        }
-        hw[q] = pack_bf16x2(hv[0], hv[1]);
-        lw[q] = pack_bf16x2(lv[0], lv[1]);
+        float h0, l0, h1v, l1;
+        split_bf16(gr[2 * q], h0, l0);
+        split_bf16(gr[2 * q + 1], h1v, l1);
+        hw[q] = pack_bf16x2(h0, h1v);
+        lw[q] = pack_bf16x2(l0, l1);
       }
       *reinterpret_cast<uint4 *>(sB2 + kg * 512 + o * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
       *reinterpret_cast<uint4 *>(sB2 + 8192 + kg * 512 + o * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -865,12 +872,11 @@ __global__ void __launch_bounds__(128)
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const int m = warp * 32 + lane;
-    const int64_t cell = bw_cell(a, R0 + m);
-    if (cell >= 0) {
+    if (cellr[m + 1] >= 0) {
       const float x0 = xs[m], x1 = xs[m + 1], x2 = xs[m + 2];   // x(m - 1), x(m), x(m + 1)
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const float g = __bfloat162float(h1[(int64_t)i * a.C + cell]) > 0.f ? __uint_as_float(r[i]) : 0.f;
+        const float g = __bfloat162float(Hs[i * kBwRows + m + 1]) > 0.f ? __uint_as_float(r[i]) : 0.f;
         acc1[3 * i] = fmaf(g, x0, acc1[3 * i]);
         acc1[3 * i + 1] = fmaf(g, x1, acc1[3 * i + 1]);
         acc1[3 * i + 2] = fmaf(g, x2, acc1[3 * i + 2]);
