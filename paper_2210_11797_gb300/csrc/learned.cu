@@ -560,49 +560,63 @@ __global__ void __launch_bounds__(128)
 
 // B2: gh2 = w_c ga3 + w_e sum(edge nbrs of ga3) + w_d sum(corner nbrs) (the neighbour relation is
 // symmetric on a patch), ga2 = gh2 [h2 > 0]; partials of gM: (ga3 . h2, ga3 . sum_e h2,
-// ga3 . sum_d h2) per channel. Thread per (column, channel) over the levels.
+// ga3 . sum_d h2) per channel. Thread per cell (consecutive threads on consecutive levels, so every
+// channel's loads and stores are coalesced), grid-stride over the cells; blockIdx.y picks 4 of the
+// 32 channels. Block x writes entries 12 y .. 12 y + 11 of partial row x.
+constexpr int kBw2Ch = 4;
 template <typename A>
 __global__ void __launch_bounds__(128)
     nn_bwd2_kernel(const float *__restrict__ wts, const A *__restrict__ h2, const float *__restrict__ ga3,
-                   Nbrs nb, int ncol, int L, int cpb, float *__restrict__ ga2, float *__restrict__ part) {
-  __shared__ float Mw[96], acc[96 * 4];
-  for (int i = threadIdx.x; i < 96; i += blockDim.x) Mw[i] = rnd<A>(wts[kOffM + i]);
-  for (int i = threadIdx.x; i < 96 * 4; i += blockDim.x) acc[i] = 0.f;
+                   Nbrs nb, int ncol, int L, float *__restrict__ ga2, float *__restrict__ part) {
+  __shared__ float Mw[3 * kBw2Ch], red[4][3 * kBw2Ch];
+  const int ch0 = blockIdx.y * kBw2Ch;
+  if (threadIdx.x < 3 * kBw2Ch) Mw[threadIdx.x] = rnd<A>(wts[kOffM + 3 * ch0 + threadIdx.x]);
   __syncthreads();
-  const int c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
   const int64_t C = (int64_t)ncol * L;
-  // per-thread gM partials (channel, kind) accumulated, then combined through shared memory
-  for (int i = threadIdx.x; i < nc * kCh; i += blockDim.x) {
-    const int cc = i / kCh, ch = i % kCh, col = c0 + cc;
+  float acc[3 * kBw2Ch];
+#pragma unroll
+  for (int q = 0; q < 3 * kBw2Ch; ++q) acc[q] = 0.f;
+  for (int64_t K = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; K < C; K += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(K / L), k = (int)(K - (int64_t)col * L);
     int e[4], d[4];
     nb.get(col, e, d);
-    const float *g = ga3 + (int64_t)ch * C;
-    const A *h = h2 + (int64_t)ch * C;
-    float sc = 0.f, se = 0.f, sd = 0.f;
-    for (int k = 0; k < L; ++k) {
-      const float gk = g[(int64_t)col * L + k];
+    int64_t oe[4], od[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      oe[s] = e[s] >= 0 ? (int64_t)e[s] * L + k : -1;
+      od[s] = d[s] >= 0 ? (int64_t)d[s] * L + k : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < kBw2Ch; ++j) {
+      const float *g = ga3 + (int64_t)(ch0 + j) * C;
+      const A *h = h2 + (int64_t)(ch0 + j) * C;
+      const float gk = g[K], hk = to_f<A>(h[K]);
       float ge = 0.f, gd = 0.f, he = 0.f, hd = 0.f;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        if (e[s] >= 0) { ge += g[(int64_t)e[s] * L + k]; he += to_f<A>(h[(int64_t)e[s] * L + k]); }
-        if (d[s] >= 0) { gd += g[(int64_t)d[s] * L + k]; hd += to_f<A>(h[(int64_t)d[s] * L + k]); }
+        if (oe[s] >= 0) { ge += g[oe[s]]; he += to_f<A>(h[oe[s]]); }
+        if (od[s] >= 0) { gd += g[od[s]]; hd += to_f<A>(h[od[s]]); }
       }
-      const float hk = to_f<A>(h[(int64_t)col * L + k]);
-      const float gh = fmaf(Mw[3 * ch], gk, fmaf(Mw[3 * ch + 1], ge, Mw[3 * ch + 2] * gd));
-      ga2[(int64_t)ch * C + (int64_t)col * L + k] = hk > 0.f ? gh : 0.f;
-      sc = fmaf(gk, hk, sc);
-      se = fmaf(gk, he, se);
-      sd = fmaf(gk, hd, sd);
+      const float gh = fmaf(Mw[3 * j], gk, fmaf(Mw[3 * j + 1], ge, Mw[3 * j + 2] * gd));
+      ga2[(int64_t)(ch0 + j) * C + K] = hk > 0.f ? gh : 0.f;
+      acc[3 * j] = fmaf(gk, hk, acc[3 * j]);
+      acc[3 * j + 1] = fmaf(gk, he, acc[3 * j + 1]);
+      acc[3 * j + 2] = fmaf(gk, hd, acc[3 * j + 2]);
     }
-    // deterministic: each (column, channel) owns one slot of acc; sum the block's columns below
-    if (cc < 4) { acc[(cc * kCh + ch) * 3 + 0] = sc; acc[(cc * kCh + ch) * 3 + 1] = se; acc[(cc * kCh + ch) * 3 + 2] = sd; }
+  }
+  // fixed-order reduction: lanes by butterfly, then the four warps
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 3 * kBw2Ch; ++q) {
+    float v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
-  for (int w = threadIdx.x; w < 96; w += blockDim.x) {
-    float s = 0.f;
-    for (int cc = 0; cc < min(nc, 4); ++cc) s += acc[cc * 96 + w];
-    part[(int64_t)blockIdx.x * 96 + w] = s;
-  }
+  if (threadIdx.x < 3 * kBw2Ch)
+    part[(int64_t)blockIdx.x * 96 + 3 * ch0 + threadIdx.x] =
+        (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
 }
 
 // B1: gh1 = conv^T(W2, ga2), ga1 = gh1 [h1 > 0]; partials of gW2 = sum ga2[o][k] h1[i][k+d-1]
@@ -1189,7 +1203,10 @@ static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn
   sum_loss_kernel<<<1, 256, 0, c->stream>>>(tb.loss_part, (int)g, loss_dev);
   nn_bwd3_kernel<A><<<g, 128, (96 + kNnCpb * (L + 2) + 96) * 4, c->stream>>>(c->nn_w, h3, tb.gy, ncol, L, kNnCpb,
                                                                              tb.ga3, tb.part3);
-  nn_bwd2_kernel<A><<<g, 128, 0, c->stream>>>(c->nn_w, h2, tb.ga3, nb, ncol, L, kNnCpb, tb.ga2, tb.partM);
+  const int64_t g2max = (int64_t)2 * c->num_sms, g2need = (C + 127) / 128;   // partial rows: at most 2 per SM
+  const unsigned g2 = (unsigned)(g2need < g2max ? g2need : g2max);
+  nn_bwd2_kernel<A><<<dim3(g2, kCh / kBw2Ch), 128, 0, c->stream>>>(c->nn_w, h2, tb.ga3, nb, ncol, L, tb.ga2,
+                                                                   tb.partM);
   unsigned g1;
   if (sizeof(A) == 2) {   // BF16 storage: the 32 -> 32 convolution's dX and dW on the tensor cores
     BwArgs ba;
@@ -1211,7 +1228,7 @@ static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn
   }
   sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.part1, (int)g1, 96, grad + kOffW1);
   sum_partials_kernel<<<3072, 256, 0, c->stream>>>(tb.part2, (int)g1, 3072, grad + kOffW2);
-  sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.partM, (int)g, 96, grad + kOffM);
+  sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.partM, (int)g2, 96, grad + kOffM);
   sum_partials_kernel<<<96, 256, 0, c->stream>>>(tb.part3, (int)g, 96, grad + kOffW3);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
