@@ -2,8 +2,9 @@
 paper fix: the one-dimensional rules, the RT_p basis (divergence theorem, facet fluxes), the
 dof counts of the paper's table of unknowns per cell, the reduction to the lowest-order oracle
 at p = 0, hybridise-then-recover against a direct solve of the unhybridised mixed system at
-p = 1 and 2 (plane and sphere), symmetry and definiteness of S, the convergence order of a
-smooth solution, and the two-level preconditioner at p = 1."""
+p = 1, 2 and 3 (plane and sphere), symmetry and definiteness of S with its row lengths, the
+convergence order of a smooth solution (p = 0, 1, 2), and the two-level preconditioner at
+p = 1 and 3."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -45,7 +46,7 @@ def test_dof_counts_match_the_table_of_unknowns(p, nu_avg, npr, nlam_avg, mixed,
     assert el.nu + el.npr == mixed and el.nlam == hybrid
 
 
-@pytest.mark.parametrize("p", [0, 1, 2])
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
 def test_rt_basis_fluxes_and_divergence_theorem(p):
     """Facet dof (f, s, t) has outward flux equal to the Lagrange function of node (s, t) on
     face f and zero flux through every other face; interior dofs have no flux; and the volume
@@ -144,42 +145,45 @@ def _hybrid_equals_mixed(hier, co, p, seed):
     assert np.abs(pi - pim).max() <= 1e-12 * np.abs(pim).max()
 
 
-@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("p", [1, 2, 3])
 def test_hybridised_solution_equals_the_mixed_solution_on_the_plane(p):
     w = _planar(n=3, nlev=2, nmg=1)
     _hybrid_equals_mixed(w.hier, w.coeffs, p, 3 + p)
 
 
-def test_hybridised_solution_equals_the_mixed_solution_on_the_sphere():
+@pytest.mark.parametrize("p", [1, 2])
+def test_hybridised_solution_equals_the_mixed_solution_on_the_sphere(p):
     """Curved cells and the reversed traversal of every vertical facet by its second column
-    (the s <-> p - s map), at p = 1."""
+    (the s <-> p - s map; at p = 2 the middle node maps to itself)."""
     hier, co = _sphere_helmholtz()
-    _hybrid_equals_mixed(hier, co, 1, 11)
+    _hybrid_equals_mixed(hier, co, p, 11 + p)
 
 
-def test_trace_operator_is_symmetric_positive_definite():
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_trace_operator_is_symmetric_positive_definite(p):
     w = _planar(n=3, nlev=2, nmg=1)
-    ho = HO.HigherOrderHybrid(w.hier, w.coeffs, 1)
+    ho = HO.HigherOrderHybrid(w.hier, w.coeffs, p)
     S = ho.S.toarray()
     assert np.abs(S - S.T).max() <= 1e-13 * np.abs(S).max()
     assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
-    # 44 couplings on an interior row (two cells x 24 facet nodes, the shared 4 once), 24 on
-    # ground and lid rows
+    # an interior row couples two cells x 6 (p+1)^2 facet nodes with the shared facet's
+    # (p+1)^2 once: 11 (p+1)^2 (44, 99, 176); ground and lid rows 6 (p+1)^2
+    nb = (p + 1) ** 2
     nnz = np.diff(ho.S.indptr)
-    assert nnz.max() == 44 and nnz.min() == 24
+    assert nnz.max() == 11 * nb and nnz.min() == 6 * nb
 
 
 def test_smooth_solution_converges_at_order_p_plus_one():
     """sigma Pi - lap Pi = f on the periodic box with Pi = sin(2 pi x) cos(2 pi y) cos(pi z / H):
     the L2 error of the DG_p pressure falls by 2^(p+1) per halving of the mesh (p = 0: 2,
-    p = 1: 4)."""
+    p = 1: 4, p = 2: 8)."""
     H = 0.1
 
     def pi_exact(x):
         return np.sin(2 * np.pi * x[:, 0]) * np.cos(2 * np.pi * x[:, 1]) * np.cos(np.pi * x[:, 2] / H)
 
     rates = {}
-    for p in (0, 1):
+    for p in (0, 1, 2):
         errs = []
         for n in (4, 8):
             w = I.planar_helmholtz(n=n, nlev=n, nmg=1, top=H)
@@ -195,14 +199,16 @@ def test_smooth_solution_converges_at_order_p_plus_one():
         rates[p] = np.log2(errs[0] / errs[1])
     assert 0.8 < rates[0] < 1.3, rates
     assert 1.8 < rates[1] < 2.4, rates
+    assert 2.7 < rates[2] < 3.5, rates
 
 
-def test_two_level_preconditioner_at_degree_one():
-    """Algorithm 2 with the piecewise-constant coarse space at p = 1: BiCGStab reaches 1e-10,
-    well before the iteration count of the unpreconditioned method, and the converged lambda is
-    the direct solution."""
-    w = _planar(n=8, nlev=4, nmg=2)
-    ho = HO.HigherOrderHybrid(w.hier, w.coeffs, 1)
+@pytest.mark.parametrize("p,n", [(1, 8), (3, 4)])
+def test_two_level_preconditioner_at_degree_p(p, n):
+    """Algorithm 2 with the piecewise-constant coarse space at p = 1 and 3: BiCGStab reaches
+    1e-10, well before the iteration count of the unpreconditioned method, and the converged
+    lambda is the direct solution."""
+    w = _planar(n=n, nlev=4, nmg=2 if n >= 8 else 1)
+    ho = HO.HigherOrderHybrid(w.hier, w.coeffs, p)
     rng = np.random.default_rng(7)
     Ru, Rpi = rng.standard_normal((ho.mesh.ncell, ho.el.nu)), rng.standard_normal((ho.mesh.ncell, ho.el.npr))
     lam, hist, st = ho.solve(Ru, Rpi, 1e-10)
