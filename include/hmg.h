@@ -146,22 +146,26 @@ typedef struct {
                            and batched solves stay synchronous */
   int32_t degree;       /* polynomial degree p of the discretisation (Sec. 2.2; the paper's runs and
                            the default: 0, broken RT0 / DG0 / one trace unknown per facet).
-                           1: broken RT1 (36 dofs per cell, 24 of them on the facets), DG1 (8) and
-                           Q1 trace multipliers (4 per facet), the 44 x 44 cell matrices
-                           condensed to 24 x 24 (the paper's table of unknowns per cell), for the
-                           Helmholtz preset (hmg_scalars.preset = 1) in FP64, with Algorithm 1 on
-                           facet blocks and Algorithm 2 on the DG0 coarse space and the
-                           lowest-order pressure multigrid. Set before hmg_assemble_trace (a
-                           change needs a new assembly). With degree 1 every call that takes cell
-                           residuals takes Rub [ncell][36] (the cell's RT1 dofs: the 24 outward
-                           facet fluxes, face by face e0..e3, bottom, top, node (s, t) at
-                           4 f + 2 s + t, then 12 interior dofs) and Rpi [ncell][8] (DG1, node
-                           (i, j, k) at 4 i + 2 j + k), and lambda has hmg_sizes' ntrace entries:
-                           four per facet, facet by facet in the order of the lowest-order
-                           numbering, node (s, t) at + 2 s + t (s along a vertical facet in the
-                           traversal of the column that owns its edge, t upwards; on a horizontal
-                           facet the xi and eta nodes). Batched, mixed-precision, learned,
-                           configuration-1 and allocation-free calls stay degree 0 */
+                           p = 1, 2, 3: broken RT_p (3 (p+1)^2 (p+2) dofs per cell, 6 (p+1)^2 of
+                           them on the facets), DG_p ((p+1)^3) and Q_p trace multipliers
+                           ((p+1)^2 per facet): mixed cell matrices of 44 x 44, 135 x 135 and
+                           304 x 304 condensed to 24 x 24, 54 x 54 and 96 x 96 (the paper's table
+                           of unknowns per cell), for the Helmholtz preset (hmg_scalars.preset =
+                           1) in FP64, with Algorithm 1 on facet blocks and Algorithm 2 on the
+                           DG0 coarse space and the lowest-order pressure multigrid. Set before
+                           hmg_assemble_trace (a change needs a new assembly; the assembly holds
+                           A_K^-1: N^2 doubles per cell, N = 44, 135, 304; HMG_ERR_OUT_OF_MEMORY when the
+                           device cannot hold it). With degree p every call that takes cell
+                           residuals takes Rub [ncell][3 (p+1)^2 (p+2)] (the cell's RT_p dofs:
+                           the outward facet fluxes, face by face e0..e3, bottom, top, node
+                           (s, t) at (p+1)^2 f + (p+1) s + t, then the interior dofs component by
+                           component) and Rpi [ncell][(p+1)^3] (DG_p, node (i, j, k) at
+                           (p+1)^2 i + (p+1) j + k), and lambda has hmg_sizes' ntrace entries:
+                           (p+1)^2 per facet, facet by facet in the order of the lowest-order
+                           numbering, node (s, t) at + (p+1) s + t (s along a vertical facet in
+                           the traversal of the column that owns its edge, t upwards; on a
+                           horizontal facet the xi and eta nodes). Batched, mixed-precision,
+                           learned, configuration-1 and allocation-free calls stay degree 0 */
 } hmg_options;
 
 #define HMG_COARSE_VCYCLE 0         /* one pressure V-cycle (configuration 3c) */
@@ -225,7 +229,7 @@ int hmg_set_coefficients(hmg_ctx *ctx, const hmg_scalars *scalars, const hmg_bac
 int hmg_assemble_trace(hmg_ctx *ctx);
 
 /* Sizes: cells and trace unknowns of the finest level (either pointer may be NULL); with
- * degree 1 (assembled) ntrace counts the four unknowns of every facet. */
+ * degree p >= 1 (assembled) ntrace counts the (p+1)^2 unknowns of every facet. */
 int hmg_sizes(const hmg_ctx *ctx, int64_t *ncell, int64_t *ntrace);
 
 void hmg_destroy(hmg_ctx *ctx);

@@ -53,10 +53,10 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_fused != 0 && o.mg_fused != 1) return bad("mg_fused must be 0 or 1");
   if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
   if (o.async_stats != 0 && o.async_stats != 1) return bad("async_stats must be 0 or 1");
-  if (o.degree != 0 && o.degree != 1) return bad("degree must be 0 or 1");
-  if (o.degree == 1 && (o.precision != HMG_PRECISION_FP64 || o.precond == HMG_PRECOND_SCHUR ||
+  if (o.degree < 0 || o.degree > 3) return bad("degree must be in 0..3");
+  if (o.degree >= 1 && (o.precision != HMG_PRECISION_FP64 || o.precond == HMG_PRECOND_SCHUR ||
                         o.coarse != HMG_COARSE_VCYCLE))
-    return bad("degree 1 runs in FP64 with the trace preconditioners and the V-cycle coarse solve");
+    return bad("degree p >= 1 runs in FP64 with the trace preconditioners and the V-cycle coarse solve");
   return HMG_OK;
 }
 
@@ -207,7 +207,7 @@ int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
     if ((st = build_factors(c))) return st;
     HMG_CUDA(c, cudaStreamSynchronize(c->stream));
   }
-  if (c->assembled && c->degree == 1) {   // (outside any stream capture: the solve graph replays them)
+  if (c->assembled && c->degree >= 1) {   // (outside any stream capture: the solve graph replays them)
     HMG_CUDA(c, cudaSetDevice(c->device));
     if ((st = ho_refactor_if_needed(c))) return st;
   }
@@ -369,12 +369,12 @@ int hmg_assemble_trace(hmg_ctx *c) {
   if (st) return st;
   const Level &f = c->lv[0];
   const int64_t T = f.ntrace, C = f.ncell;
-  const int64_t T1 = c->opt.degree == 1 ? ho_trace_size(c) : 0;
+  const int64_t T1 = c->opt.degree >= 1 ? ho_trace_size(c, c->opt.degree) : 0;
   // Krylov vectors long enough for the 2x2 system of configuration 1 ([u | Pi]) and for the
-  // degree-1 trace system; work vectors for the longer trace system; the host-copy staging area
+  // degree-p trace system; work vectors for the longer trace system; the host-copy staging area
   // for the cell residuals and lambda of either degree
   const int64_t nvec = std::max(T + C, T1), nwork = std::max(T, T1);
-  const int64_t nhost = std::max(7 * C + T, T1 ? 44 * C + T1 : 0);
+  const int64_t nhost = std::max(7 * C + T, T1 ? (int64_t)(cell_nu_of(c->opt.degree) + cell_np_of(c->opt.degree)) * C + T1 : 0);
   if (c->vec_cap < nvec) {
     double **vecs[] = {&c->B, &c->r, &c->rhat, &c->p, &c->v, &c->s, &c->t, &c->phat, &c->shat};
     for (double **v : vecs) {
@@ -408,10 +408,12 @@ int hmg_assemble_trace(hmg_ctx *c) {
     c->host_cap = nhost;
   }
   c->degree = c->opt.degree;
-  if (c->degree == 1 && (st = ho_assemble(c))) {
+  if (c->degree >= 1 && (st = ho_assemble(c))) {
     c->degree = 0;
+    ho_free(c);
     return st;
   }
+  if (c->degree == 0 && c->ho.degree != 0) ho_free(c);   // the degree-p system is no longer in use
   if (!c->noalloc_scratch && (st = noalloc_setup(c))) return st;
   c->assembled = true;
   return HMG_OK;
@@ -421,7 +423,7 @@ int hmg_sizes(const hmg_ctx *c, int64_t *ncell, int64_t *ntrace) {
   if (!c) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh) return HMG_ERR_NOT_READY;
   if (ncell) *ncell = c->lv[0].ncell;
-  if (ntrace) *ntrace = c->assembled && c->degree == 1 ? c->ho.T : c->lv[0].ntrace;
+  if (ntrace) *ntrace = c->assembled && c->degree >= 1 ? c->ho.T : c->lv[0].ntrace;
   return HMG_OK;
 }
 
@@ -477,7 +479,7 @@ int hmg_trace_rhs(hmg_ctx *c, const double *Rub, const double *Rpi, double *B) {
   int st = ready(c);
   if (st) return st;
   if (!Rub || !Rpi || !B) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
-  if (c->degree == 1) return finish(c, ho_trace_rhs(c, Rub, Rpi, B));
+  if (c->degree >= 1) return finish(c, ho_trace_rhs(c, Rub, Rpi, B));
   return finish(c, launch_trace_rhs(c, Rub, Rpi, B));
 }
 
@@ -543,7 +545,7 @@ int hmg_reconstruct(hmg_ctx *c, const double *lambda, const double *Rub, const d
   int st = ready(c);
   if (st) return st;
   if (!lambda || !Rub || !Rpi || !ub || !pi) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
-  if (c->degree == 1) return finish(c, ho_reconstruct(c, lambda, Rub, Rpi, ub, pi));
+  if (c->degree >= 1) return finish(c, ho_reconstruct(c, lambda, Rub, Rpi, ub, pi));
   return finish(c, launch_reconstruct(c, lambda, Rub, Rpi, ub, pi));
 }
 
@@ -551,7 +553,7 @@ int hmg_apply_trace(hmg_ctx *c, const double *x, double *y) {
   int st = ready(c);
   if (st) return st;
   if (!x || !y || x == y) return fail(c, HMG_ERR_INVALID_ARG, "bad pointers");
-  if (c->degree == 1) return finish(c, ho_launch_spmv(c, x, y, 0, nullptr, 0, 0));
+  if (c->degree >= 1) return finish(c, ho_launch_spmv(c, x, y, 0, nullptr, 0, 0));
   return finish(c, launch_spmv(c, x, y, 0, nullptr, 0, 0));
 }
 
@@ -567,7 +569,7 @@ int hmg_line_smooth(hmg_ctx *c, const double *b, double *lambda, int32_t nsweeps
   int st = ready(c);
   if (st) return st;
   if (!b || !lambda || nsweeps < 0) return fail(c, HMG_ERR_INVALID_ARG, "bad arguments");
-  if (c->degree == 1) return finish(c, ho_line_smooth(c, b, lambda, nsweeps));
+  if (c->degree >= 1) return finish(c, ho_line_smooth(c, b, lambda, nsweeps));
   return finish(c, line_smooth_fp64(c, b, lambda, nsweeps));
 }
 
@@ -590,7 +592,7 @@ int hmg_get_gamma(hmg_ctx *c, double *gamma) {
   int st = ready(c);
   if (st) return st;
   if (!gamma) return fail(c, HMG_ERR_INVALID_ARG, "null pointer");
-  HMG_CUDA(c, cudaMemcpyAsync(gamma, c->degree == 1 ? c->ho.gamma : c->gamma, sizeof(double) * c->lv[0].ncell,
+  HMG_CUDA(c, cudaMemcpyAsync(gamma, c->degree >= 1 ? c->ho.gamma : c->gamma, sizeof(double) * c->lv[0].ncell,
                               cudaMemcpyDeviceToDevice, c->stream));
   return finish(c, HMG_OK);
 }

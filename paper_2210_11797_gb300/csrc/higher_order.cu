@@ -1,20 +1,23 @@
-// The hybridised system of degree p = 1 (broken RT_1 velocity, DG_1 pressure, Q_1 trace
-// multipliers: four per facet) for the constant-coefficient Helmholtz form of the operator,
+// The hybridised system of degree p = 1, 2, 3 (broken RT_p velocity, DG_p pressure, Q_p trace
+// multipliers: (p+1)^2 per facet) for the constant-coefficient Helmholtz form of the operator,
 // and its non-nested two-level preconditioner with the piecewise-constant coarse space.
 //
 // Paper (arXiv 2210.11797): Sec. 2.2 (spaces of degree p, n = p + 3 Gauss points per
 // direction), Sec. 2.4 (Eqs. hybrid-S, hybrid-rhs, hybrid-recovery), Sec. 4.1 and the table
-// of unknowns per cell (24 x 24 hybridised and 44 x 44 mixed cell matrices at p = 1),
-// Algorithm 1 (here on facet blocks and block-tridiagonal columns), Algorithm 2 with the DG0
-// coarse space of Sec. 2.5 (P lambda = {{Pi}}, Restrict = P^T, Eq. scaling_matrix) and the
-// lowest-order pressure multigrid as its coarse solve.
+// of unknowns per cell (hybridised cell matrices of 24 x 24, 54 x 54 and 96 x 96, mixed cell
+// matrices of 44 x 44, 135 x 135 and 304 x 304 at p = 1, 2, 3), Algorithm 1 (here on facet
+// blocks and block-tridiagonal columns), Algorithm 2 with the DG0 coarse space of Sec. 2.5
+// (P lambda = {{Pi}}, Restrict = P^T, Eq. scaling_matrix) and the lowest-order pressure
+// multigrid as its coarse solve.
 //
-// Numbering. Cell dofs: the 36 RT_1 dofs (24 facet dofs, face f = e0..e3, bottom, top, node
-// (s, t) at 4 f + 2 s + t, each the cell's outward normal flux at a Gauss-Legendre node of the
-// facet; then 12 interior dofs), then the 8 DG_1 dofs. Trace rows: four per facet, facet-major:
-// vertical facet (edge e, level k) at 4 (e L + k), horizontal facet (column c, interface k) at
-// NH + 4 (c (L + 1) + k), node (s, t) at + 2 s + t; on a vertical facet s counts along the edge
-// in the traversal of its owner column (the other column's local s is 1 - s).
+// Numbering (NT = p + 1, NB = NT^2 nodes per facet, NF = 6 NB facet dofs per cell). Cell dofs:
+// the RT_p dofs (NF facet dofs, face f = e0..e3, bottom, top, node (s, t) at NB f + NT s + t,
+// each the cell's outward normal flux at a Gauss-Legendre node of the facet; then the
+// 3 p NT^2 interior dofs, component-major), then the NT^3 DG_p dofs. Trace rows: NB per facet,
+// facet-major: vertical facet (edge e, level k) at NB (e L + k), horizontal facet (column c,
+// interface k) at NH + NB (c (L + 1) + k), node (s, t) at + NT s + t; on a vertical facet s
+// counts along the edge in the traversal of its owner column (the other column's local s is
+// p - s).
 #include <cmath>
 #include <vector>
 
@@ -24,19 +27,69 @@
 
 namespace hmg {
 
-constexpr int kHoNu = 36;                 // RT_1 dofs
-constexpr int kHoNp = 8;                  // DG_1 dofs
-constexpr int kHoN = kHoNu + kHoNp;       // 44: the mixed cell matrix
-constexpr int kHoNf = 24;                 // facet dofs (the hybridised cell matrix is 24 x 24)
-constexpr int kHoQ = 64;                  // 4 x 4 x 4 Gauss points
-constexpr int kHoSlots = 48;              // S coefficients stored per trace row (two cells x 24)
-constexpr int kHoTabV = 0, kHoTabPhi = kHoTabV + kHoQ * kHoNu, kHoTabW = kHoTabPhi + kHoQ * kHoNp,
-              kHoTabX = kHoTabW + kHoQ, kHoTabG = kHoTabX + 3 * kHoQ, kHoTab = kHoTabG + kHoNu * kHoNp;
-constexpr double kHoC = 0.25;             // C_K on a facet dof: the product of two Gauss-Legendre weights 1/2
+template <int P>
+struct Ho {
+  static constexpr int NT = P + 1;                    // Gauss-Legendre nodes per direction
+  static constexpr int NB = NT * NT;                  // nodes (trace rows) per facet
+  static constexpr int NF = 6 * NB;                   // facet dofs: the hybridised cell matrix is NF x NF
+  static constexpr int NU = 3 * NT * NT * (P + 2);    // RT_p dofs
+  static constexpr int NP = NT * NT * NT;             // DG_p dofs
+  static constexpr int N = NU + NP;                   // the mixed cell matrix
+  static constexpr int NQ1 = P + 3;                   // volume Gauss points per direction
+  static constexpr int Q = NQ1 * NQ1 * NQ1;
+  static constexpr int SLOTS = 2 * NF;                // S coefficients stored per trace row
+  static constexpr int NINT = P * NT * NT;            // interior dofs per component
+  // reference tables: velocity values, pressure values, weights, points, G, facet weights
+  static constexpr int TV = 0, TPHI = TV + Q * NU, TW = TPHI + Q * NP, TX = TW + Q, TG = TX + 3 * Q,
+                       TC = TG + NU * NP, TAB = TC + NB;
+  // the sweep's line part: lanes per column (a group of LPC lanes of one warp; lane n < NB
+  // computes component n of each block product)
+  static constexpr int LPC = P == 1 ? 4 : 16;
+};
 
 // ---- reference tables, formed on the host ---------------------------------------------------
-// 1-D Lagrange values / derivatives, the RT_1 basis (value of its one nonzero component and its
-// divergence) and the DG_1 basis at the 64 Gauss points, and G(f, j) = -int phi_j div v_f.
+// n-point Gauss-Legendre rule on [0, 1]: Newton's method on the Legendre polynomial P_n from the
+// initial guesses cos(pi (i + 3/4) / (n + 1/2)), weights 2 / ((1 - x^2) P_n'(x)^2) on [-1, 1],
+// halved
+static void gauss_legendre01(int n, double *x, double *w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_n(z), p0 = P_{n-1}(z) (n = 1: P_1 = z, P_0 = 1)
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[n - 1 - i] = 0.5 * (z + 1.0);   // ascending
+    w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// n = 2 .. 5 Gauss-Lobatto points on [0, 1]: the end points and the roots of P'_{n-1}
+static void gauss_lobatto01(int n, double *x) {
+  x[0] = 0.0;
+  x[n - 1] = 1.0;
+  if (n == 3) x[1] = 0.5;
+  if (n == 4) {
+    const double r = 1.0 / std::sqrt(5.0);
+    x[1] = 0.5 * (1.0 - r);
+    x[2] = 0.5 * (1.0 + r);
+  }
+  if (n == 5) {
+    const double r = std::sqrt(3.0 / 7.0);
+    x[1] = 0.5 * (1.0 - r);
+    x[2] = 0.5;
+    x[3] = 0.5 * (1.0 + r);
+  }
+}
+
 static void lagrange1d(const double *nodes, int n, double x, double *val, double *der) {
   for (int i = 0; i < n; ++i) {
     double v = 1.0, d = 0.0;
@@ -54,101 +107,107 @@ static void lagrange1d(const double *nodes, int n, double x, double *val, double
   }
 }
 
-// component, normal node (0 or 2), sign of the facet dofs of face f; (tangential node indices
-// of the two other coordinates in increasing coordinate order) from the facet node (s, t)
+// face f: the component normal to it, whether it is the far end (xi, eta or zeta = 1), the sign
+// of the outward normal
 static const int kFaceComp[6] = {1, 0, 1, 0, 2, 2};
-static const int kFaceEnd[6] = {0, 2, 2, 0, 0, 2};
+static const int kFaceFar[6] = {0, 1, 1, 0, 0, 1};
 static const double kFaceSign[6] = {-1.0, 1.0, 1.0, -1.0, -1.0, 1.0};
 
+// a velocity dof: its component d, its node a along d (Gauss-Lobatto), its nodes (b, c) across d
+// (Gauss-Legendre, the other two coordinates in increasing order), its sign
 struct HoDof { int d, a, b, c; double sign; };
 
+template <int P>
 static std::vector<HoDof> ho_dofs() {
+  using H = Ho<P>;
   std::vector<HoDof> v;
   for (int f = 0; f < 6; ++f)
-    for (int s = 0; s < 2; ++s)
-      for (int t = 0; t < 2; ++t) {
-        const int b = (f == 2 || f == 3) ? 1 - s : s;   // e2, e3 traverse their edge backwards
-        v.push_back({kFaceComp[f], kFaceEnd[f], b, t, kFaceSign[f]});
+    for (int s = 0; s < H::NT; ++s)
+      for (int t = 0; t < H::NT; ++t) {
+        const int b = (f == 2 || f == 3) ? P - s : s;   // e2, e3 traverse their edge backwards
+        v.push_back({kFaceComp[f], kFaceFar[f] ? P + 1 : 0, b, t, kFaceSign[f]});
       }
   for (int d = 0; d < 3; ++d)
-    for (int b = 0; b < 2; ++b)
-      for (int c = 0; c < 2; ++c) v.push_back({d, 1, b, c, 1.0});
+    for (int a = 1; a <= P; ++a)
+      for (int b = 0; b < H::NT; ++b)
+        for (int c = 0; c < H::NT; ++c) v.push_back({d, a, b, c, 1.0});
   return v;
 }
 
+// the RT_p basis (value of its one nonzero component and its divergence) and the DG_p basis at
+// the Q Gauss points, G(f, j) = -int phi_j div v_f, and the facet weights of C_K
+template <int P>
 static void ho_tables(std::vector<double> &tab) {
-  tab.assign(kHoTab, 0.0);
-  const double g = 0.5 / std::sqrt(3.0);
-  const double gl[2] = {0.5 - g, 0.5 + g};
-  const double gll[3] = {0.0, 0.5, 1.0};
-  const double r1 = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
-  const double r2 = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
-  const double w1 = (18.0 + std::sqrt(30.0)) / 36.0, w2 = (18.0 - std::sqrt(30.0)) / 36.0;
-  const double qx[4] = {0.5 * (1.0 - r2), 0.5 * (1.0 - r1), 0.5 * (1.0 + r1), 0.5 * (1.0 + r2)};
-  const double qw[4] = {0.5 * w2, 0.5 * w1, 0.5 * w1, 0.5 * w2};
-  const std::vector<HoDof> dofs = ho_dofs();
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      for (int c = 0; c < 4; ++c) {
-        const int q = (a * 4 + b) * 4 + c;
+  using H = Ho<P>;
+  tab.assign(H::TAB, 0.0);
+  double gl[H::NT], glw[H::NT], gll[P + 2], qx[H::NQ1], qw[H::NQ1];
+  gauss_legendre01(H::NT, gl, glw);
+  gauss_lobatto01(P + 2, gll);
+  gauss_legendre01(H::NQ1, qx, qw);
+  const std::vector<HoDof> dofs = ho_dofs<P>();
+  for (int a = 0; a < H::NQ1; ++a)
+    for (int b = 0; b < H::NQ1; ++b)
+      for (int c = 0; c < H::NQ1; ++c) {
+        const int q = (a * H::NQ1 + b) * H::NQ1 + c;
         const double x[3] = {qx[a], qx[b], qx[c]};
-        double tv[3][2], td[3][2], nv[3][3], nd[3][3];
+        double tv[3][H::NT], td[3][H::NT], nv[3][P + 2], nd[3][P + 2];
         for (int k = 0; k < 3; ++k) {
-          lagrange1d(gl, 2, x[k], tv[k], td[k]);
-          lagrange1d(gll, 3, x[k], nv[k], nd[k]);
+          lagrange1d(gl, H::NT, x[k], tv[k], td[k]);
+          lagrange1d(gll, P + 2, x[k], nv[k], nd[k]);
         }
-        tab[kHoTabW + q] = qw[a] * qw[b] * qw[c];
-        for (int k = 0; k < 3; ++k) tab[kHoTabX + 3 * q + k] = x[k];
-        for (int i = 0; i < kHoNu; ++i) {
+        const double wq = qw[a] * qw[b] * qw[c];
+        tab[H::TW + q] = wq;
+        for (int k = 0; k < 3; ++k) tab[H::TX + 3 * q + k] = x[k];
+        double phi[H::NP];
+        for (int ii = 0; ii < H::NT; ++ii)
+          for (int jj = 0; jj < H::NT; ++jj)
+            for (int kk = 0; kk < H::NT; ++kk) phi[(ii * H::NT + jj) * H::NT + kk] = tv[0][ii] * tv[1][jj] * tv[2][kk];
+        for (int j = 0; j < H::NP; ++j) tab[H::TPHI + q * H::NP + j] = phi[j];
+        for (int i = 0; i < H::NU; ++i) {
           const HoDof &o = dofs[i];
-          int t1 = 0, t2 = 0;
-          if (o.d == 0) { t1 = 1; t2 = 2; } else if (o.d == 1) { t1 = 0; t2 = 2; } else { t1 = 0; t2 = 1; }
+          const int t1 = o.d == 0 ? 1 : 0, t2 = o.d == 2 ? 1 : 2;
           const double tan = tv[t1][o.b] * tv[t2][o.c];
-          tab[kHoTabV + q * kHoNu + i] = o.sign * nv[o.d][o.a] * tan;
+          tab[H::TV + q * H::NU + i] = o.sign * nv[o.d][o.a] * tan;
           // divergence: the derivative of the one nonzero component along its own coordinate
           const double dv = o.sign * nd[o.d][o.a] * tan;
-          for (int ii = 0; ii < 2; ++ii)
-            for (int jj = 0; jj < 2; ++jj)
-              for (int kk = 0; kk < 2; ++kk) {
-                const int j = (ii * 2 + jj) * 2 + kk;
-                const double phi = tv[0][ii] * tv[1][jj] * tv[2][kk];
-                tab[kHoTabG + i * kHoNp + j] -= tab[kHoTabW + q] * dv * phi;
-              }
+          for (int j = 0; j < H::NP; ++j) tab[H::TG + i * H::NP + j] -= wq * dv * phi[j];
         }
-        for (int ii = 0; ii < 2; ++ii)
-          for (int jj = 0; jj < 2; ++jj)
-            for (int kk = 0; kk < 2; ++kk)
-              tab[kHoTabPhi + q * kHoNp + (ii * 2 + jj) * 2 + kk] = tv[0][ii] * tv[1][jj] * tv[2][kk];
       }
+  for (int s = 0; s < H::NT; ++s)
+    for (int t = 0; t < H::NT; ++t) tab[H::TC + s * H::NT + t] = glw[s] * glw[t];
 }
 
+template <int P>
 __device__ __forceinline__ int ho_comp(int i) {   // the nonzero component of velocity dof i
-  if (i < kHoNf) {
-    const int f = i >> 2;
+  using H = Ho<P>;
+  if (i < H::NF) {
+    const int f = i / H::NB;
     return f == 0 || f == 2 ? 1 : (f == 1 || f == 3 ? 0 : 2);
   }
-  return (i - kHoNf) >> 2;
+  return (i - H::NF) / H::NINT;
 }
 
 // ---- mesh access ------------------------------------------------------------------------------
 struct HoGeo {
   int L, ncol;
-  int64_t NH;                 // rows of the vertical facets (4 nedge L)
+  int64_t NH;                 // rows of the vertical facets (NB nedge L)
   int64_t nhf, nzf;           // vertical and horizontal facets
   const int32_t *col_edges, *stencil, *edge_fc;
   const int8_t *own;          // [ncol][4] 1 if the column owns the edge of that face
 };
 
 // trace row of local facet dof q of cell (c, k)
+template <int P>
 __device__ __forceinline__ int64_t ho_gid(const HoGeo &g, int c, int k, int q) {
-  const int f = q >> 2, s = (q >> 1) & 1, t = q & 1;
+  using H = Ho<P>;
+  const int f = q / H::NB, r = q - f * H::NB, s = r / H::NT, t = r - s * H::NT;
   if (f < 4) {
     const int64_t e = g.col_edges[4 * (int64_t)c + f];
-    const int sg = g.own[4 * (int64_t)c + f] ? s : 1 - s;
-    return 4 * (e * g.L + k) + 2 * sg + t;
+    const int sg = g.own[4 * (int64_t)c + f] ? s : P - s;
+    return H::NB * (e * g.L + k) + H::NT * sg + t;
   }
   const int kk = k + (f == 5 ? 1 : 0);
-  return g.NH + 4 * ((int64_t)c * (g.L + 1) + kk) + 2 * s + t;
+  return g.NH + H::NB * ((int64_t)c * (g.L + 1) + kk) + H::NT * s + t;
 }
 
 // The one or two cells of facet F: A (and B), their local faces, and whether a node's local s is
@@ -190,39 +249,50 @@ __device__ __forceinline__ HoFacet ho_facet(const HoGeo &g, int64_t F) {
   return r;
 }
 
-// acc[n] (+/-)= sum over the stored slots of row 4F + n times x: cell A's 24 facet dofs, then
+// NB consecutive coefficients of one slot (the facet's rows) times x into acc
+template <int NB, bool NEG>
+__device__ __forceinline__ void ho_slot(const double *__restrict__ s, double xv, double acc[NB]) {
+  if constexpr (NB % 2 == 0) {
+#pragma unroll
+    for (int n = 0; n < NB; n += 2) {
+      const double2 v = __ldcs(reinterpret_cast<const double2 *>(s + n));
+      acc[n] = fma(NEG ? -v.x : v.x, xv, acc[n]);
+      acc[n + 1] = fma(NEG ? -v.y : v.y, xv, acc[n + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int n = 0; n < NB; ++n) {
+      const double v = __ldcs(s + n);
+      acc[n] = fma(NEG ? -v : v, xv, acc[n]);
+    }
+  }
+}
+
+// acc[n] (+/-)= sum over the stored slots of row NB F + n times x: cell A's NF facet dofs, then
 // cell B's without the shared facet (merged into A's slots when S was assembled). OFFD leaves out
 // the couplings inside the smoother's diagonal block D of Algorithm 1 (acc - (S - D) x): on a
-// vertical facet its own four nodes, on a horizontal facet the horizontal facets of its column
-// (A's bottom and top, B's bottom).
-template <bool NEG, bool OFFD = false>
+// vertical facet its own nodes, on a horizontal facet the horizontal facets of its column (A's
+// bottom and top, B's bottom).
+template <int P, bool NEG, bool OFFD = false>
 __device__ __forceinline__ void ho_rows(const double *__restrict__ S, const double *__restrict__ x, const HoGeo &g,
-                                        int64_t T, int64_t F, double acc[4]) {
+                                        int64_t T, int64_t F, double acc[Ho<P>::NB]) {
+  using H = Ho<P>;
   const HoFacet fc = ho_facet(g, F);
-  const double *Sr = S + 4 * F;
+  const double *Sr = S + (int64_t)H::NB * F;
   const bool vert = F < g.nhf;
-#pragma unroll 4
-  for (int q = 0; q < kHoNf; ++q) {
-    if (OFFD && (vert ? (q >> 2) == fc.fA : (q >> 2) >= 4)) continue;
-    const double xv = __ldg(x + ho_gid(g, fc.cA, fc.kA, q));
-    const double2 s01 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)q * T));
-    const double2 s23 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)q * T + 2));
-    acc[0] = fma(NEG ? -s01.x : s01.x, xv, acc[0]);
-    acc[1] = fma(NEG ? -s01.y : s01.y, xv, acc[1]);
-    acc[2] = fma(NEG ? -s23.x : s23.x, xv, acc[2]);
-    acc[3] = fma(NEG ? -s23.y : s23.y, xv, acc[3]);
+  constexpr int U = P == 1 ? 4 : 2;
+#pragma unroll U
+  for (int q = 0; q < H::NF; ++q) {
+    if (OFFD && (vert ? q / H::NB == fc.fA : q / H::NB >= 4)) continue;
+    const double xv = __ldg(x + ho_gid<P>(g, fc.cA, fc.kA, q));
+    ho_slot<H::NB, NEG>(Sr + (int64_t)q * T, xv, acc);
   }
   if (fc.cB < 0) return;
-#pragma unroll 4
-  for (int q = 0; q < kHoNf; ++q) {
-    if ((q >> 2) == fc.fB || (OFFD && !vert && (q >> 2) >= 4)) continue;
-    const double xv = __ldg(x + ho_gid(g, fc.cB, fc.kB, q));
-    const double2 s01 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)(kHoNf + q) * T));
-    const double2 s23 = __ldcs(reinterpret_cast<const double2 *>(Sr + (int64_t)(kHoNf + q) * T + 2));
-    acc[0] = fma(NEG ? -s01.x : s01.x, xv, acc[0]);
-    acc[1] = fma(NEG ? -s01.y : s01.y, xv, acc[1]);
-    acc[2] = fma(NEG ? -s23.x : s23.x, xv, acc[2]);
-    acc[3] = fma(NEG ? -s23.y : s23.y, xv, acc[3]);
+#pragma unroll U
+  for (int q = 0; q < H::NF; ++q) {
+    if (q / H::NB == fc.fB || (OFFD && !vert && q / H::NB >= 4)) continue;
+    const double xv = __ldg(x + ho_gid<P>(g, fc.cB, fc.kB, q));
+    ho_slot<H::NB, NEG>(Sr + (int64_t)(H::NF + q) * T, xv, acc);
   }
 }
 
@@ -234,21 +304,41 @@ struct HoCellArgs {
   const double *corners, *z;
 };
 
-// A_K = [[M, G], [-G^T, Mp]] by the 4 x 4 x 4 Gauss rule (M with the contravariant Piola map,
-// Mp = sigma int phi_i phi_j), then A_K^-1 by Gauss-Jordan elimination with partial pivoting
-// of the symmetrically equilibrated D A_K D, D = |diag A_K|^-1/2: A^-1 = D (D A D)^-1 D.
-// One cell per block; m[K] = sigma |K|_1 (the one-point volume), H 1 of the coarse operator.
-__global__ void __launch_bounds__(128)
+// Shared memory of the cell kernel: the mixed matrix when it fits (p <= 2), then the per-point
+// metric terms and the elimination's vectors.
+template <int P>
+struct HoCellSmem {
+  static constexpr bool IN_SMEM = P <= 2;
+  static constexpr size_t MAT = IN_SMEM ? sizeof(double) * Ho<P>::N * Ho<P>::N : 0;
+  static constexpr size_t BYTES =
+      MAT + sizeof(double) * (Ho<P>::Q * 7 + 3 * Ho<P>::N + 24) + sizeof(int) * (Ho<P>::N + 8);
+};
+
+// A_K = [[M, G], [-G^T, Mp]] by the (p+3)^3 Gauss rule (M with the contravariant Piola map,
+// Mp = sigma int phi_i phi_j), then A_K^-1 by in-place Gauss-Jordan elimination with partial
+// pivoting of the symmetrically equilibrated D A_K D, D = |diag A_K|^-1/2: A^-1 = D (D A D)^-1 D.
+// The row interchanges are undone at the end as column interchanges in reverse order. One cell
+// per block; the matrix lives in shared memory for p <= 2 and in its output slot (global memory)
+// at p = 3. m[K] = sigma |K|_1 (the one-point volume), H 1 of the coarse operator.
+template <int P>
+__global__ void __launch_bounds__(256)
     ho_cell_kernel(const HoCellArgs a, const double *__restrict__ tab, double *__restrict__ Ainv,
                    double *__restrict__ mK, int *singular) {
-  __shared__ double X[8][3];
-  __shared__ double Kq[kHoQ][6];   // (w / det) J^T J: xx, yy, zz, xy, xz, yz
-  __shared__ double wd[kHoQ];      // sigma w det
-  __shared__ double Ag[kHoN][2 * kHoN + 1];
-  __shared__ double dsc[kHoN], fac[kHoN];
-  __shared__ int piv;
+  using H = Ho<P>;
+  using SM = HoCellSmem<P>;
+  constexpr int N = H::N;
+  extern __shared__ __align__(16) unsigned char ho_smem[];
   const int64_t K = blockIdx.x;
-  const int tid = threadIdx.x;
+  double *Ag = SM::IN_SMEM ? reinterpret_cast<double *>(ho_smem) : Ainv + K * (int64_t)(N * N);
+  double *Kq = reinterpret_cast<double *>(ho_smem + SM::MAT);   // [Q][6] (w / det) J^T J
+  double *wd = Kq + 6 * H::Q;                                     // [Q] sigma w det
+  double *dsc = wd + H::Q, *fac = dsc + N, *rowk = fac + N;
+  double *X = rowk + N;                                           // [8][3] corners
+  int *perm = reinterpret_cast<int *>(X + 24);
+  int *piv = perm + N;
+  __shared__ double bestv[8];
+  __shared__ int besti[8];
+  const int tid = threadIdx.x, nthr = blockDim.x;
   const int c = (int)(K / a.L), k = (int)(K - (int64_t)c * a.L);
   if (tid < 8) {
     const int va = tid & 1, vb = (tid >> 1) & 1, vc = (tid >> 2) & 1;
@@ -256,11 +346,11 @@ __global__ void __launch_bounds__(128)
     const double *cp = a.corners + (4 * (int64_t)c + corner) * 3;
     const double h = a.z[k + vc];
     if (a.geometry == 1) {
-      for (int i = 0; i < 3; ++i) X[tid][i] = cp[i] * (a.radius + h);
+      for (int i = 0; i < 3; ++i) X[3 * tid + i] = cp[i] * (a.radius + h);
     } else {
-      X[tid][0] = cp[0];
-      X[tid][1] = cp[1];
-      X[tid][2] = h;
+      X[3 * tid] = cp[0];
+      X[3 * tid + 1] = cp[1];
+      X[3 * tid + 2] = h;
     }
   }
   __syncthreads();
@@ -272,95 +362,128 @@ __global__ void __launch_bounds__(128)
       const double gx = va ? 1.0 : -1.0, gy = vb ? 1.0 : -1.0, gz = vc ? 1.0 : -1.0;
       const double dn[3] = {gx * fy * fz, fx * gy * fz, fx * fy * gz};
       for (int i = 0; i < 3; ++i)
-        for (int d = 0; d < 3; ++d) J[i][d] += X[v][i] * dn[d];
+        for (int d = 0; d < 3; ++d) J[i][d] += X[3 * v + i] * dn[d];
     }
   };
   auto det3 = [](const double J[3][3]) {
     return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
   };
-  if (tid < kHoQ) {
-    const double *xq = tab + kHoTabX + 3 * tid;
-    double J[3][3];
-    jacobian(xq[0], xq[1], xq[2], J);
-    const double det = det3(J), w = tab[kHoTabW + tid];
-    double G[3][3];
-    for (int p = 0; p < 3; ++p)
-      for (int q = 0; q < 3; ++q) G[p][q] = J[0][p] * J[0][q] + J[1][p] * J[1][q] + J[2][p] * J[2][q];
-    const double s = w / det;
-    Kq[tid][0] = s * G[0][0];
-    Kq[tid][1] = s * G[1][1];
-    Kq[tid][2] = s * G[2][2];
-    Kq[tid][3] = s * G[0][1];
-    Kq[tid][4] = s * G[0][2];
-    Kq[tid][5] = s * G[1][2];
-    wd[tid] = a.sigma * w * det;
-  } else if (tid == kHoQ) {
-    double J[3][3];
-    jacobian(0.5, 0.5, 0.5, J);
-    mK[K] = a.sigma * det3(J);
-  }
-  __syncthreads();
-  const double *tv = tab + kHoTabV, *tp = tab + kHoTabPhi, *tg = tab + kHoTabG;
-  for (int idx = tid; idx < kHoN * kHoN; idx += blockDim.x) {
-    const int i = idx / kHoN, j = idx - i * kHoN;
-    double v = 0.0;
-    if (i < kHoNu && j < kHoNu) {
-      const int di = ho_comp(i), dj = ho_comp(j);
-      const int kk = di == dj ? di : (di + dj == 1 ? 3 : (di + dj == 2 ? 4 : 5));
-      for (int q = 0; q < kHoQ; ++q) v = fma(__ldg(tv + q * kHoNu + i) * __ldg(tv + q * kHoNu + j), Kq[q][kk], v);
-    } else if (i < kHoNu) {
-      v = __ldg(tg + i * kHoNp + (j - kHoNu));
-    } else if (j < kHoNu) {
-      v = -__ldg(tg + j * kHoNp + (i - kHoNu));
+  for (int q = tid; q <= H::Q; q += nthr) {
+    if (q < H::Q) {
+      const double *xq = tab + H::TX + 3 * q;
+      double J[3][3];
+      jacobian(xq[0], xq[1], xq[2], J);
+      const double det = det3(J), w = tab[H::TW + q];
+      double G[3][3];
+      for (int p = 0; p < 3; ++p)
+        for (int r = 0; r < 3; ++r) G[p][r] = J[0][p] * J[0][r] + J[1][p] * J[1][r] + J[2][p] * J[2][r];
+      const double s = w / det;
+      Kq[6 * q] = s * G[0][0];
+      Kq[6 * q + 1] = s * G[1][1];
+      Kq[6 * q + 2] = s * G[2][2];
+      Kq[6 * q + 3] = s * G[0][1];
+      Kq[6 * q + 4] = s * G[0][2];
+      Kq[6 * q + 5] = s * G[1][2];
+      wd[q] = a.sigma * w * det;
     } else {
-      for (int q = 0; q < kHoQ; ++q)
-        v = fma(wd[q] * __ldg(tp + q * kHoNp + (i - kHoNu)), __ldg(tp + q * kHoNp + (j - kHoNu)), v);
+      double J[3][3];
+      jacobian(0.5, 0.5, 0.5, J);
+      mK[K] = a.sigma * det3(J);
     }
-    Ag[i][j] = v;
-    Ag[i][kHoN + j] = i == j ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (tid < kHoN) dsc[tid] = 1.0 / sqrt(fabs(Ag[tid][tid]));
-  __syncthreads();
-  for (int idx = tid; idx < kHoN * kHoN; idx += blockDim.x) {
-    const int i = idx / kHoN, j = idx - i * kHoN;
-    Ag[i][j] *= dsc[i] * dsc[j];
+  const double *tv = tab + H::TV, *tp = tab + H::TPHI, *tg = tab + H::TG;
+  for (int idx = tid; idx < N * N; idx += nthr) {
+    const int i = idx / N, j = idx - i * N;
+    double v = 0.0;
+    if (i < H::NU && j < H::NU) {
+      const int di = ho_comp<P>(i), dj = ho_comp<P>(j);
+      const int kk = di == dj ? di : (di + dj == 1 ? 3 : (di + dj == 2 ? 4 : 5));
+      for (int q = 0; q < H::Q; ++q)
+        v = fma(__ldg(tv + q * H::NU + i) * __ldg(tv + q * H::NU + j), Kq[6 * q + kk], v);
+    } else if (i < H::NU) {
+      v = __ldg(tg + i * H::NP + (j - H::NU));
+    } else if (j < H::NU) {
+      v = -__ldg(tg + j * H::NP + (i - H::NU));
+    } else {
+      for (int q = 0; q < H::Q; ++q)
+        v = fma(wd[q] * __ldg(tp + q * H::NP + (i - H::NU)), __ldg(tp + q * H::NP + (j - H::NU)), v);
+    }
+    Ag[idx] = v;
   }
   __syncthreads();
-  for (int col = 0; col < kHoN; ++col) {
+  for (int i = tid; i < N; i += nthr) dsc[i] = 1.0 / sqrt(fabs(Ag[(int64_t)i * N + i]));
+  __syncthreads();
+  for (int idx = tid; idx < N * N; idx += nthr) {
+    const int i = idx / N, j = idx - i * N;
+    Ag[idx] *= dsc[i] * dsc[j];
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+  for (int col = 0; col < N; ++col) {
+    // pivot: the largest |A[r][col]|, r >= col (the first such row on ties)
+    double bv = -1.0;
+    int bi = col;
+    for (int r = col + tid; r < N; r += nthr) {
+      const double v = fabs(Ag[(int64_t)r * N + col]);
+      if (v > bv) { bv = v; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { bestv[warp] = bv; besti[warp] = bi; }
+    __syncthreads();
     if (tid == 0) {
-      int p = col;
-      double best = fabs(Ag[col][col]);
-      for (int r = col + 1; r < kHoN; ++r)
-        if (fabs(Ag[r][col]) > best) { best = fabs(Ag[r][col]); p = r; }
-      if (!(best > 0.0)) atomicExch(singular, 1);
-      piv = p;
+      double v = bestv[0];
+      int p = besti[0];
+      for (int w = 1; w < nwarp; ++w)
+        if (bestv[w] > v || (bestv[w] == v && besti[w] < p)) { v = bestv[w]; p = besti[w]; }
+      if (!(v > 0.0)) atomicExch(singular, 1);
+      piv[0] = p;
+      perm[col] = p;
     }
     __syncthreads();
-    const int p = piv;
+    const int p = piv[0];
     if (p != col)
-      for (int j = tid; j < 2 * kHoN; j += blockDim.x) {
-        const double t = Ag[col][j];
-        Ag[col][j] = Ag[p][j];
-        Ag[p][j] = t;
+      for (int j = tid; j < N; j += nthr) {
+        const double t = Ag[(int64_t)col * N + j];
+        Ag[(int64_t)col * N + j] = Ag[(int64_t)p * N + j];
+        Ag[(int64_t)p * N + j] = t;
       }
     __syncthreads();
-    if (tid < kHoN) fac[tid] = Ag[tid][col];
+    for (int r = tid; r < N; r += nthr) fac[r] = Ag[(int64_t)r * N + col];
     __syncthreads();
     const double pinv = 1.0 / fac[col];
-    for (int j = tid; j < 2 * kHoN; j += blockDim.x) Ag[col][j] *= pinv;
+    for (int j = tid; j < N; j += nthr) {
+      const double v = (j == col ? 1.0 : Ag[(int64_t)col * N + j]) * pinv;
+      Ag[(int64_t)col * N + j] = v;
+      rowk[j] = v;
+    }
     __syncthreads();
-    for (int idx = tid; idx < kHoN * 2 * kHoN; idx += blockDim.x) {
-      const int r = idx / (2 * kHoN), j = idx - r * 2 * kHoN;
-      if (r != col) Ag[r][j] = fma(-fac[r], Ag[col][j], Ag[r][j]);
+    for (int idx = tid; idx < N * N; idx += nthr) {
+      const int r = idx / N, j = idx - r * N;
+      if (r != col) Ag[idx] = fma(-fac[r], rowk[j], j == col ? 0.0 : Ag[idx]);
     }
     __syncthreads();
   }
-  double *out = Ainv + K * (kHoN * kHoN);
-  for (int idx = tid; idx < kHoN * kHoN; idx += blockDim.x) {
-    const int i = idx / kHoN, j = idx - i * kHoN;
-    out[idx] = dsc[i] * Ag[i][kHoN + j] * dsc[j];
+  for (int col = N - 1; col >= 0; --col) {   // undo the row interchanges: columns, in reverse
+    const int p = perm[col];
+    if (p != col)
+      for (int r = tid; r < N; r += nthr) {
+        const double t = Ag[(int64_t)r * N + col];
+        Ag[(int64_t)r * N + col] = Ag[(int64_t)r * N + p];
+        Ag[(int64_t)r * N + p] = t;
+      }
+    __syncthreads();
+  }
+  double *out = Ainv + K * (int64_t)(N * N);
+  for (int idx = tid; idx < N * N; idx += nthr) {
+    const int i = idx / N, j = idx - i * N;
+    out[idx] = dsc[i] * Ag[idx] * dsc[j];
   }
 }
 
@@ -373,165 +496,206 @@ __global__ void ho_own_kernel(const int32_t *__restrict__ stencil, const int32_t
   own[4 * (int64_t)stencil[8 * (int64_t)e + 1] + edge_fc[2 * (int64_t)e + 1]] = 0;
 }
 
-// Rows of S = sum_K C_K^T A_K^-1 C_K (C_K = 1/4 on every facet dof): row 4F + n holds, in slots
-// 0-23, (1/16) A_A^-1 restricted to the facet dofs of cell A (row: the node's local index in A),
-// and in slots 24-47 the same of cell B, whose shared-facet entries are added into A's slots.
-__global__ void ho_rows_kernel(const HoGeo g, int64_t T, const double *__restrict__ Ainv, double *__restrict__ S) {
+// Rows of S = sum_K C_K^T A_K^-1 C_K (C_K diagonal on the facet dofs: w_s w_t of the node): row
+// NB F + n holds, in slots 0 .. NF - 1, C A_A^-1 C restricted to the facet dofs of cell A (row:
+// the node's local index in A), and in slots NF .. 2 NF - 1 the same of cell B, whose
+// shared-facet entries are added into A's slots (and stored as 0).
+template <int P>
+__global__ void ho_rows_kernel(const HoGeo g, int64_t T, const double *__restrict__ tab,
+                               const double *__restrict__ Ainv, double *__restrict__ S) {
+  using H = Ho<P>;
+  constexpr int N = H::N;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= T) return;
-  const int64_t F = row >> 2;
-  const int n = (int)(row & 3), s = n >> 1, t = n & 1;
+  const int64_t F = row / H::NB;
+  const int n = (int)(row - F * H::NB), s = n / H::NT, t = n - s * H::NT;
+  const double *Cw = tab + H::TC;
   const HoFacet fc = ho_facet(g, F);
-  const int qa = 4 * fc.fA + 2 * s + t;
-  const double *IA = Ainv + ((int64_t)fc.cA * g.L + fc.kA) * (kHoN * kHoN) + qa * kHoN;
-  double v[kHoNf];
-  for (int q = 0; q < kHoNf; ++q) v[q] = kHoC * kHoC * IA[q];
+  const int qa = H::NB * fc.fA + n;
+  const double *IA = Ainv + ((int64_t)fc.cA * g.L + fc.kA) * (int64_t)(N * N) + (int64_t)qa * N;
+  for (int q = 0; q < H::NF; ++q) S[(int64_t)q * T + row] = Cw[n] * Cw[q % H::NB] * IA[q];
   if (fc.cB >= 0) {
-    const int sb = fc.flipB ? 1 - s : s;
-    const int qb = 4 * fc.fB + 2 * sb + t;
-    const double *IB = Ainv + ((int64_t)fc.cB * g.L + fc.kB) * (kHoN * kHoN) + qb * kHoN;
-    for (int q = 0; q < kHoNf; ++q) {
-      const double w = kHoC * kHoC * IB[q];
-      if ((q >> 2) == fc.fB) {   // the shared facet: the same trace row as A's node
-        const int sq = (q >> 1) & 1, tq = q & 1;
-        const int sa = fc.flipB ? 1 - sq : sq;
-        v[4 * fc.fA + 2 * sa + tq] += w;
-        S[(int64_t)(kHoNf + q) * T + row] = 0.0;
+    const int sb = fc.flipB ? P - s : s;
+    const int nb = H::NT * sb + t;
+    const int qb = H::NB * fc.fB + nb;
+    const double *IB = Ainv + ((int64_t)fc.cB * g.L + fc.kB) * (int64_t)(N * N) + (int64_t)qb * N;
+    for (int q = 0; q < H::NF; ++q) {
+      const double w = Cw[nb] * Cw[q % H::NB] * IB[q];
+      if (q / H::NB == fc.fB) {   // the shared facet: the same trace row as A's node
+        const int r = q % H::NB, sq = r / H::NT, tq = r - sq * H::NT;
+        const int sa = fc.flipB ? P - sq : sq;
+        S[(int64_t)(H::NB * fc.fA + H::NT * sa + tq) * T + row] += w;
+        S[(int64_t)(H::NF + q) * T + row] = 0.0;
       } else {
-        S[(int64_t)(kHoNf + q) * T + row] = w;
+        S[(int64_t)(H::NF + q) * T + row] = w;
       }
     }
   } else {
-    for (int q = 0; q < kHoNf; ++q) S[(int64_t)(kHoNf + q) * T + row] = 0.0;
+    for (int q = 0; q < H::NF; ++q) S[(int64_t)(H::NF + q) * T + row] = 0.0;
   }
-  for (int q = 0; q < kHoNf; ++q) S[(int64_t)q * T + row] = v[q];
 }
 
-// 4 x 4 inverse by Gauss-Jordan elimination with partial pivoting; false if singular
-__device__ bool inv4(const double A[4][4], double R[4][4]) {
-  double M[4][8];
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      M[i][j] = A[i][j];
-      M[i][4 + j] = i == j ? 1.0 : 0.0;
-    }
-  for (int c = 0; c < 4; ++c) {
+// Gauss-Jordan elimination with partial pivoting by one warp: W [NB][2 NB] (shared memory) holds
+// [A | I] on entry and [I | A^-1] on return; lane j < 2 NB owns column j. Every lane finds the
+// same pivot (they read the same values), so the branches are uniform. False if A is singular.
+template <int NB>
+__device__ bool warp_gauss_jordan(double *W, int lane) {
+  constexpr int W2 = 2 * NB;
+  static_assert(W2 <= 32, "one lane per column");
+  for (int c = 0; c < NB; ++c) {
     int p = c;
-    for (int r = c + 1; r < 4; ++r)
-      if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
-    if (!(fabs(M[p][c]) > 0.0)) return false;
-    if (p != c)
-      for (int j = 0; j < 8; ++j) { const double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
-    const double inv = 1.0 / M[c][c];
-    for (int j = 0; j < 8; ++j) M[c][j] *= inv;
-    for (int r = 0; r < 4; ++r) {
-      if (r == c) continue;
-      const double f = M[r][c];
-      for (int j = 0; j < 8; ++j) M[r][j] = fma(-f, M[c][j], M[r][j]);
+    double best = fabs(W[c * W2 + c]);
+    for (int r = c + 1; r < NB; ++r) {
+      const double v = fabs(W[r * W2 + c]);
+      if (v > best) { best = v; p = r; }
     }
+    if (!(best > 0.0)) return false;
+    if (p != c && lane < W2) {
+      const double t = W[c * W2 + lane];
+      W[c * W2 + lane] = W[p * W2 + lane];
+      W[p * W2 + lane] = t;
+    }
+    __syncwarp();
+    const double inv = 1.0 / W[c * W2 + c];
+    double fr[NB];   // column c, read before its owner lane changes it
+#pragma unroll
+    for (int r = 0; r < NB; ++r) fr[r] = W[r * W2 + c];
+    __syncwarp();
+    if (lane < W2) {
+      const double pv = W[c * W2 + lane] * inv;
+      W[c * W2 + lane] = pv;
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r != c) W[r * W2 + lane] = fma(-fr[r], pv, W[r * W2 + lane]);
+    }
+    __syncwarp();
   }
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) R[i][j] = M[i][4 + j];
   return true;
 }
 
-// omega times the inverse of each vertical facet's 4 x 4 block of S (the Jacobi part of
-// Algorithm 1), entry (n, m) at hw[(4 n + m) nhf + F]. The facet block lives in the slots of
-// cell A's face (A owns the edge, so its local nodes are the facet's).
-__global__ void ho_hfactor_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, double omega,
-                                  double *__restrict__ hw, int *singular) {
-  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (F >= g.nhf) return;
+constexpr int kHoFacWarps = 4;   // warps per block of the factor kernels
+
+// omega times the inverse of each vertical facet's NB x NB block of S (the Jacobi part of
+// Algorithm 1), entry (n, m) at hw[(NB n + m) nhf + F]; one warp per facet. The facet block lives
+// in the slots of cell A's face (A owns the edge, so its local nodes are the facet's).
+template <int P>
+__global__ void __launch_bounds__(32 * kHoFacWarps)
+    ho_hfactor_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, double omega,
+                      double *__restrict__ hw, int *singular) {
+  constexpr int NB = Ho<P>::NB, W2 = 2 * NB;
+  __shared__ double Wsh[kHoFacWarps][NB * W2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t F = (int64_t)blockIdx.x * kHoFacWarps + warp;
+  if (F >= g.nhf) return;   // whole warps leave
+  double *W = Wsh[warp];
   const HoFacet fc = ho_facet(g, F);
-  double D[4][4], R[4][4];
-  for (int n = 0; n < 4; ++n)
-    for (int m = 0; m < 4; ++m) D[n][m] = S[(int64_t)(4 * fc.fA + m) * T + 4 * F + n];
-  if (!inv4(D, R)) atomicExch(singular, 1);
-  for (int n = 0; n < 4; ++n)
-    for (int m = 0; m < 4; ++m) hw[(int64_t)(4 * n + m) * g.nhf + F] = omega * R[n][m];
+  for (int e = lane; e < NB * NB; e += 32) {
+    const int n = e / NB, m = e - n * NB;
+    W[n * W2 + m] = S[(int64_t)(NB * fc.fA + m) * T + NB * F + n];
+    W[n * W2 + NB + m] = n == m ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  if (!warp_gauss_jordan<NB>(W, lane) && lane == 0) atomicExch(singular, 1);
+  for (int e = lane; e < NB * NB; e += 32) {
+    const int n = e / NB, m = e - n * NB;
+    hw[(int64_t)(NB * n + m) * g.nhf + F] = omega * W[n * W2 + NB + m];
+  }
 }
 
 // Block Thomas factors of each column's block-tridiagonal S^zz (blocks D_k, L_k = coupling of
 // facet k to k - 1, U_k to k + 1): G_0 = D_0, G_k = D_k - L_k G_{k-1}^-1 U_{k-1}; stored per
-// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([nzf][48], 16 entries each), so that
+// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([nzf][3 NB^2]), so that
 // omega (S^zz)^-1 r is y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, x_k = y_k - (G_k^-1 U_k) x_{k+1}.
-__global__ void ho_zfactor_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, double omega,
-                                  double *__restrict__ zf, int *singular) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncol) return;
+// Slots: the cell above (c, k) is A for k < L: its bottom (face 4) is this facet, its top (face 5)
+// facet k + 1; the cell below (c, k - 1) is B, its bottom facet k - 1. The lid row's A is the
+// cell below: its top is this facet, its bottom the facet below. One warp per column.
+template <int P>
+__global__ void __launch_bounds__(32 * kHoFacWarps)
+    ho_zfactor_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, double omega,
+                      double *__restrict__ zf, int *singular) {
+  using H = Ho<P>;
+  constexpr int NB = H::NB, NB2 = NB * NB, W2 = 2 * NB;
+  extern __shared__ double zsh[];   // per warp: GU, Lk, U [NB2] and W [NB][2 NB]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kHoFacWarps + warp;
+  if (c >= g.ncol) return;   // whole warps leave
+  double *GU = zsh + warp * (3 * NB2 + NB * W2), *Lk = GU + NB2, *U = Lk + NB2, *W = U + NB2;
   const int L = g.L;
-  double GU[4][4];   // G_{k-1}^-1 U_{k-1}
+  bool ok = true;
   for (int k = 0; k <= L; ++k) {
-    const int64_t F = (int64_t)c * (L + 1) + k, row0 = g.NH + 4 * F;
-    double D[4][4], Lk[4][4], U[4][4];
-    // slots: cell above (c, k) [A, k < L]: bottom 16-19 (this facet), top 20-23 (facet k + 1);
-    // cell below (c, k - 1) [B]: bottom 40-43 (facet k - 1). The lid row's A is the cell below:
-    // its top 20-23 is this facet, its bottom 16-19 the facet below.
-    for (int n = 0; n < 4; ++n)
-      for (int m = 0; m < 4; ++m) {
-        const double *r = S + row0 + n;
-        if (k < L) {
-          D[n][m] = r[(int64_t)(16 + m) * T];
-          U[n][m] = r[(int64_t)(20 + m) * T];
-          Lk[n][m] = k > 0 ? r[(int64_t)(40 + m) * T] : 0.0;
-        } else {
-          D[n][m] = r[(int64_t)(20 + m) * T];
-          Lk[n][m] = r[(int64_t)(16 + m) * T];
-          U[n][m] = 0.0;
-        }
+    const int64_t F = (int64_t)c * (L + 1) + k, row0 = g.NH + NB * F;
+    for (int e = lane; e < NB2; e += 32) {
+      const int n = e / NB, m = e - n * NB;
+      const double *r = S + row0 + n;
+      if (k < L) {
+        W[n * W2 + m] = r[(int64_t)(4 * NB + m) * T];
+        U[e] = r[(int64_t)(5 * NB + m) * T];
+        Lk[e] = k > 0 ? r[(int64_t)(H::NF + 4 * NB + m) * T] : 0.0;
+      } else {
+        W[n * W2 + m] = r[(int64_t)(5 * NB + m) * T];
+        Lk[e] = r[(int64_t)(4 * NB + m) * T];
+        U[e] = 0.0;
       }
-    if (k > 0)
-      for (int n = 0; n < 4; ++n)
-        for (int m = 0; m < 4; ++m) {
-          double s = D[n][m];
-          for (int j = 0; j < 4; ++j) s = fma(-Lk[n][j], GU[j][m], s);
-          D[n][m] = s;
-        }
-    double Gi[4][4];
-    if (!inv4(D, Gi)) atomicExch(singular, 1);
-    double GL[4][4];
-    for (int n = 0; n < 4; ++n)
-      for (int m = 0; m < 4; ++m) {
-        double sl = 0.0, su = 0.0;
-        for (int j = 0; j < 4; ++j) {
-          sl = fma(Gi[n][j], Lk[j][m], sl);
-          su = fma(Gi[n][j], U[j][m], su);
-        }
-        GL[n][m] = sl;
-        GU[n][m] = su;
+      W[n * W2 + NB + m] = n == m ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    if (k > 0) {
+      for (int e = lane; e < NB2; e += 32) {   // G_k = D_k - L_k (G_{k-1}^-1 U_{k-1})
+        const int n = e / NB, m = e - n * NB;
+        double s = W[n * W2 + m];
+        for (int j = 0; j < NB; ++j) s = fma(-Lk[n * NB + j], GU[j * NB + m], s);
+        W[n * W2 + m] = s;
       }
-    double *o = zf + 48 * ((int64_t)c * (L + 1) + k);   // facet-major: 48 contiguous factors
-    for (int n = 0; n < 4; ++n)
-      for (int m = 0; m < 4; ++m) {
-        o[4 * n + m] = omega * Gi[n][m];
-        o[16 + 4 * n + m] = GL[n][m];
-        o[32 + 4 * n + m] = GU[n][m];
+      __syncwarp();
+    }
+    if (!warp_gauss_jordan<NB>(W, lane)) ok = false;
+    double *o = zf + 3 * NB2 * F;   // facet-major: 3 NB^2 contiguous factors
+    for (int e = lane; e < NB2; e += 32) {
+      const int n = e / NB, m = e - n * NB;
+      double sl = 0.0, su = 0.0;
+      for (int j = 0; j < NB; ++j) {
+        sl = fma(W[n * W2 + NB + j], Lk[j * NB + m], sl);
+        su = fma(W[n * W2 + NB + j], U[j * NB + m], su);
       }
+      o[e] = omega * W[n * W2 + NB + m];
+      o[NB2 + e] = sl;
+      o[2 * NB2 + e] = su;
+    }
+    __syncwarp();
+    for (int e = lane; e < NB2; e += 32) GU[e] = o[2 * NB2 + e];
+    __syncwarp();
   }
+  if (!ok && lane == 0) atomicExch(singular, 1);
 }
 
 // ---- the operator, the right-hand side and the recovery --------------------------------------
-// y = S x, one thread per facet (its four rows share the gathered values); MODE 1, 2, 3 fuse the
+// y = S x, one thread per facet (its NB rows share the gathered values); MODE 1, 2, 3 fuse the
 // inner products of the Krylov loop as the lowest-order S apply does (3: (b - S x, b - S x), no y).
-template <int MODE>
+template <int P, int MODE>
 __global__ void __launch_bounds__(kRedThreads)
     ho_spmv_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, const double *__restrict__ x,
                    double *__restrict__ y, const double *__restrict__ w, double *part, int slot0, int slot1) {
+  constexpr int NB = Ho<P>::NB;
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double a0 = 0.0, a1 = 0.0;
   if (F < g.nhf + g.nzf) {
-    double acc[4];
+    double acc[NB];
+    const int64_t r0 = (int64_t)NB * F;
     if (MODE == 3) {
-      for (int n = 0; n < 4; ++n) acc[n] = __ldg(w + 4 * F + n);
-      ho_rows<true>(S, x, g, T, F, acc);
-      for (int n = 0; n < 4; ++n) a0 = fma(acc[n], acc[n], a0);
+#pragma unroll
+      for (int n = 0; n < NB; ++n) acc[n] = __ldg(w + r0 + n);
+      ho_rows<P, true>(S, x, g, T, F, acc);
+#pragma unroll
+      for (int n = 0; n < NB; ++n) a0 = fma(acc[n], acc[n], a0);
     } else {
-      acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-      ho_rows<false>(S, x, g, T, F, acc);
-      for (int n = 0; n < 4; ++n) {
-        y[4 * F + n] = acc[n];
-        if (MODE == 1) a0 = fma(__ldg(w + 4 * F + n), acc[n], a0);
-        if (MODE == 2) { a0 = fma(acc[n], __ldg(w + 4 * F + n), a0); a1 = fma(acc[n], acc[n], a1); }
+#pragma unroll
+      for (int n = 0; n < NB; ++n) acc[n] = 0.0;
+      ho_rows<P, false>(S, x, g, T, F, acc);
+#pragma unroll
+      for (int n = 0; n < NB; ++n) {
+        y[r0 + n] = acc[n];
+        if (MODE == 1) a0 = fma(__ldg(w + r0 + n), acc[n], a0);
+        if (MODE == 2) { a0 = fma(acc[n], __ldg(w + r0 + n), a0); a1 = fma(acc[n], acc[n], a1); }
       }
     }
   }
@@ -546,160 +710,182 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// B_lambda row 4F + n: the sum over the facet's cells of (1/4) (A_K^-1 R_K) at the node's local dof
-__global__ void ho_rhs_kernel(const HoGeo g, int64_t T, const double *__restrict__ Ainv,
-                              const double *__restrict__ Ru, const double *__restrict__ Rp,
-                              double *__restrict__ B) {
+// B_lambda row NB F + n: the sum over the facet's cells of C_K (A_K^-1 R_K) at the node's local dof
+template <int P>
+__global__ void ho_rhs_kernel(const HoGeo g, int64_t T, const double *__restrict__ tab,
+                              const double *__restrict__ Ainv, const double *__restrict__ Ru,
+                              const double *__restrict__ Rp, double *__restrict__ B) {
+  using H = Ho<P>;
+  constexpr int N = H::N;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= T) return;
-  const int64_t F = row >> 2;
-  const int n = (int)(row & 3), s = n >> 1, t = n & 1;
+  const int64_t F = row / H::NB;
+  const int n = (int)(row - F * H::NB), s = n / H::NT, t = n - s * H::NT;
   const HoFacet fc = ho_facet(g, F);
   auto cell = [&](int cc, int kk, int q) {
     const int64_t K = (int64_t)cc * g.L + kk;
-    const double *I = Ainv + K * (kHoN * kHoN) + q * kHoN;
+    const double *I = Ainv + K * (int64_t)(N * N) + (int64_t)q * N;
     double v = 0.0;
-    for (int j = 0; j < kHoNu; ++j) v = fma(I[j], Ru[K * kHoNu + j], v);
-    for (int j = 0; j < kHoNp; ++j) v = fma(I[kHoNu + j], Rp[K * kHoNp + j], v);
-    return kHoC * v;
+    for (int j = 0; j < H::NU; ++j) v = fma(I[j], Ru[K * H::NU + j], v);
+    for (int j = 0; j < H::NP; ++j) v = fma(I[H::NU + j], Rp[K * H::NP + j], v);
+    return v;
   };
-  double v = cell(fc.cA, fc.kA, 4 * fc.fA + 2 * s + t);
-  if (fc.cB >= 0) v += cell(fc.cB, fc.kB, 4 * fc.fB + 2 * (fc.flipB ? 1 - s : s) + t);
-  B[row] = v;
+  double v = cell(fc.cA, fc.kA, H::NB * fc.fA + n);
+  if (fc.cB >= 0) v += cell(fc.cB, fc.kB, H::NB * fc.fB + H::NT * (fc.flipB ? P - s : s) + t);
+  B[row] = tab[H::TC + n] * v;
 }
 
-// X_K = A_K^-1 (R_K - C_K lambda_K): u [ncell][36], pi [ncell][8]; one thread per (cell, dof)
-__global__ void ho_reconstruct_kernel(const HoGeo g, int64_t ncell, const double *__restrict__ Ainv,
-                                      const double *__restrict__ lam, const double *__restrict__ Ru,
-                                      const double *__restrict__ Rp, double *__restrict__ u,
-                                      double *__restrict__ pi) {
+// X_K = A_K^-1 (R_K - C_K lambda_K): u [ncell][NU], pi [ncell][NP]; one thread per (cell, dof)
+template <int P>
+__global__ void ho_reconstruct_kernel(const HoGeo g, int64_t ncell, const double *__restrict__ tab,
+                                      const double *__restrict__ Ainv, const double *__restrict__ lam,
+                                      const double *__restrict__ Ru, const double *__restrict__ Rp,
+                                      double *__restrict__ u, double *__restrict__ pi) {
+  using H = Ho<P>;
+  constexpr int N = H::N;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= ncell * kHoN) return;
-  const int64_t K = idx / kHoN;
-  const int i = (int)(idx - K * kHoN);
+  if (idx >= ncell * N) return;
+  const int64_t K = idx / N;
+  const int i = (int)(idx - K * N);
   const int c = (int)(K / g.L), k = (int)(K - (int64_t)c * g.L);
-  const double *I = Ainv + K * (kHoN * kHoN) + i * kHoN;
+  const double *I = Ainv + K * (int64_t)(N * N) + (int64_t)i * N;
   double v = 0.0;
-  for (int j = 0; j < kHoNu; ++j) {
-    double r = Ru[K * kHoNu + j];
-    if (j < kHoNf) r = fma(-kHoC, lam[ho_gid(g, c, k, j)], r);
+  for (int j = 0; j < H::NU; ++j) {
+    double r = Ru[K * H::NU + j];
+    if (j < H::NF) r = fma(-tab[H::TC + j % H::NB], lam[ho_gid<P>(g, c, k, j)], r);
     v = fma(I[j], r, v);
   }
-  for (int j = 0; j < kHoNp; ++j) v = fma(I[kHoNu + j], Rp[K * kHoNp + j], v);
-  if (i < kHoNu) u[K * kHoNu + i] = v;
-  else pi[K * kHoNp + (i - kHoNu)] = v;
+  for (int j = 0; j < H::NP; ++j) v = fma(I[H::NU + j], Rp[K * H::NP + j], v);
+  if (i < H::NU) u[K * H::NU + i] = v;
+  else pi[K * H::NP + (i - H::NU)] = v;
 }
 
-// ---- Algorithm 1 at p = 1 -----------------------------------------------------------------------
+// ---- Algorithm 1 at p >= 1 ------------------------------------------------------------------------
 // lam_out = lam_in + omega D^-1 (b - S lam_in) (ZERO: lam_in = 0), evaluated as
 // (1 - omega) lam_in + omega D^-1 (b - (S - D) lam_in): equal in exact arithmetic, without the
-// 4 (vertical facets) or 12 (horizontal facets) couplings of a row inside D. Blocks [0, nzb) take CPB
-// columns each: the residual rows of their horizontal facets staged in shared memory, then the
-// block Thomas recurrences with four lanes per column (lane n computes component n of each 4 x 4
-// product from its rows of the stored factors; the four lanes of a column sit in one warp and
-// meet at __syncwarp between the steps); the other blocks take one vertical facet per thread
-// (4 x 4 block Jacobi).
-template <bool ZERO>
+// couplings of a row inside D. Blocks [0, nzb) take CPB columns each: the residual rows of their
+// horizontal facets staged in shared memory, then the block Thomas recurrences with LPC lanes per
+// column (lane n < NB computes component n of each NB x NB product from its rows of the stored
+// factors; the lanes of a column sit in one warp and meet at __syncwarp between the steps); the
+// other blocks take one vertical facet per thread (NB x NB block Jacobi).
+template <int P, bool ZERO>
 __global__ void __launch_bounds__(128)
     ho_sweep_kernel(const HoGeo g, int64_t T, int cpb, int nzb, const double *__restrict__ S,
                     const double *__restrict__ hw, const double *__restrict__ zf, const double *__restrict__ b,
                     const double *__restrict__ lam_in, double *__restrict__ lam_out, double keep) {
-  extern __shared__ double sr[];   // [cpb][L+1][4]
+  using H = Ho<P>;
+  constexpr int NB = H::NB, NB2 = NB * NB, LPC = H::LPC;
+  extern __shared__ double sr[];   // [cpb][L+1][NB]
   const int L1 = g.L + 1;
   if ((int)blockIdx.x < nzb) {
     const int c0 = blockIdx.x * cpb, nc = min(cpb, g.ncol - c0);
     for (int i = threadIdx.x; i < nc * L1; i += blockDim.x) {
       const int64_t F = g.nhf + (int64_t)c0 * L1 + i;
-      double acc[4];
-      for (int n = 0; n < 4; ++n) acc[n] = __ldg(b + 4 * F + n);
-      if (!ZERO) ho_rows<true, true>(S, lam_in, g, T, F, acc);
-      for (int n = 0; n < 4; ++n) sr[4 * i + n] = acc[n];
+      double acc[NB];
+#pragma unroll
+      for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + (int64_t)NB * F + n);
+      if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
+#pragma unroll
+      for (int n = 0; n < NB; ++n) sr[NB * i + n] = acc[n];
     }
     __syncthreads();
-    const int cc = threadIdx.x >> 2, n = threadIdx.x & 3;
-    const unsigned grp = 0xFu << (threadIdx.x & 28);   // the four lanes of this column
+    const int cc = threadIdx.x / LPC, n = threadIdx.x % LPC;
+    const unsigned grp = ((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1));   // this column's lanes
     if (cc < nc) {
-      double *r = sr + 4 * cc * L1;
-      const double *f0 = zf + 48 * ((int64_t)(c0 + cc) * L1);
+      double *r = sr + NB * cc * L1;
+      const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1);
       // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r
-      double yprev[4] = {0.0, 0.0, 0.0, 0.0};
       for (int k = 0; k < L1; ++k) {
-        const double *f = f0 + 48 * k;
+        const double *f = f0 + 3 * NB2 * k;
         double v = 0.0;
-        for (int m = 0; m < 4; ++m) v = fma(__ldg(f + 4 * n + m), r[4 * k + m], v);
-        for (int m = 0; m < 4; ++m) v = fma(-__ldg(f + 16 + 4 * n + m), yprev[m], v);
+        if (n < NB) {
+          for (int m = 0; m < NB; ++m) v = fma(__ldg(f + NB * n + m), r[NB * k + m], v);
+          if (k > 0)
+            for (int m = 0; m < NB; ++m) v = fma(-__ldg(f + NB2 + NB * n + m), r[NB * (k - 1) + m], v);
+        }
         __syncwarp(grp);
-        r[4 * k + n] = v;
+        if (n < NB) r[NB * k + n] = v;
         __syncwarp(grp);
-        for (int m = 0; m < 4; ++m) yprev[m] = r[4 * k + m];
       }
-      // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y
+      // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y (row k + 1 is not written
+      // in this step, row k only by its own lane)
       for (int k = L1 - 2; k >= 0; --k) {
-        const double *f = f0 + 48 * k;
-        double v = r[4 * k + n];
-        for (int m = 0; m < 4; ++m) v = fma(-__ldg(f + 32 + 4 * n + m), yprev[m], v);
+        const double *f = f0 + 3 * NB2 * k;
+        if (n < NB) {
+          double v = r[NB * k + n];
+          for (int m = 0; m < NB; ++m) v = fma(-__ldg(f + 2 * NB2 + NB * n + m), r[NB * (k + 1) + m], v);
+          r[NB * k + n] = v;
+        }
         __syncwarp(grp);
-        r[4 * k + n] = v;
-        __syncwarp(grp);
-        for (int m = 0; m < 4; ++m) yprev[m] = r[4 * k + m];
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nc * L1 * 4; i += blockDim.x) {
-      const int64_t row = g.NH + 4 * (int64_t)c0 * L1 + i;
+    for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) {
+      const int64_t row = g.NH + (int64_t)NB * c0 * L1 + i;
       lam_out[row] = ZERO ? sr[i] : fma(keep, lam_in[row], sr[i]);
     }
   } else {
     const int64_t F = (int64_t)(blockIdx.x - nzb) * blockDim.x + threadIdx.x;
     if (F >= g.nhf) return;
-    double acc[4];
-    for (int n = 0; n < 4; ++n) acc[n] = __ldg(b + 4 * F + n);
-    if (!ZERO) ho_rows<true, true>(S, lam_in, g, T, F, acc);
-    for (int n = 0; n < 4; ++n) {
-      double v = ZERO ? 0.0 : keep * lam_in[4 * F + n];
-      for (int m = 0; m < 4; ++m) v = fma(hw[(int64_t)(4 * n + m) * g.nhf + F], acc[m], v);
-      lam_out[4 * F + n] = v;
+    double acc[NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + (int64_t)NB * F + n);
+    if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
+    for (int n = 0; n < NB; ++n) {
+      double v = ZERO ? 0.0 : keep * lam_in[(int64_t)NB * F + n];
+#pragma unroll
+      for (int m = 0; m < NB; ++m) v = fma(hw[(int64_t)(NB * n + m) * g.nhf + F], acc[m], v);
+      lam_out[(int64_t)NB * F + n] = v;
     }
   }
 }
 
 // R = b - S lam (Algorithm 2 line 3), one thread per facet. ZSWEEP: lam is one sweep from zero,
 // lam = omega D^-1 b, so R = (1 - omega) b - (S - D) lam (equal in exact arithmetic).
-template <bool ZSWEEP>
+template <int P, bool ZSWEEP>
 __global__ void ho_residual_kernel(const HoGeo g, int64_t T, const double *__restrict__ S,
                                    const double *__restrict__ b, const double *__restrict__ lam,
                                    double *__restrict__ R, double keep) {
+  constexpr int NB = Ho<P>::NB;
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= g.nhf + g.nzf) return;
-  double acc[4];
-  for (int n = 0; n < 4; ++n) acc[n] = ZSWEEP ? keep * __ldg(b + 4 * F + n) : __ldg(b + 4 * F + n);
-  ho_rows<true, ZSWEEP>(S, lam, g, T, F, acc);
-  for (int n = 0; n < 4; ++n) R[4 * F + n] = acc[n];
+  double acc[NB];
+#pragma unroll
+  for (int n = 0; n < NB; ++n) {
+    const double bv = __ldg(b + (int64_t)NB * F + n);
+    acc[n] = ZSWEEP ? keep * bv : bv;
+  }
+  ho_rows<P, true, ZSWEEP>(S, lam, g, T, F, acc);
+#pragma unroll
+  for (int n = 0; n < NB; ++n) R[(int64_t)NB * F + n] = acc[n];
 }
 
-// bbar_K = Gamma_K (P^T R)_K (Algorithm 2 lines 4-5): P is constant on a facet (all four nodes)
-// and averages the facet's cells, so P^T sums the cell's 24 facet nodes with weight 1/2 (1 on
+// bbar_K = Gamma_K (P^T R)_K (Algorithm 2 lines 4-5): P is constant on a facet (all its nodes)
+// and averages the facet's cells, so P^T sums the cell's facet nodes with weight 1/2 (1 on
 // ground and lid facets)
+template <int P>
 __global__ void ho_restrict_kernel(const HoGeo g, int64_t ncell, const double *__restrict__ R,
                                    const double *__restrict__ gamma, double *__restrict__ bbar) {
+  using H = Ho<P>;
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= ncell) return;
   const int c = (int)(K / g.L), k = (int)(K - (int64_t)c * g.L);
   double s = 0.0;
-  for (int q = 0; q < kHoNf; ++q) {
-    const int f = q >> 2;
+  for (int q = 0; q < H::NF; ++q) {
+    const int f = q / H::NB;
     const bool boundary = (f == 4 && k == 0) || (f == 5 && k == g.L - 1);
-    s = fma(boundary ? 1.0 : 0.5, R[ho_gid(g, c, k, q)], s);
+    s = fma(boundary ? 1.0 : 0.5, R[ho_gid<P>(g, c, k, q)], s);
   }
   bbar[K] = gamma ? gamma[K] * s : s;
 }
 
 // lam_out = lam_in + P dPi (Algorithm 2 line 7), one thread per row
+template <int P>
 __global__ void ho_prolong_kernel(const HoGeo g, int64_t T, const double *__restrict__ lam_in,
                                   const double *__restrict__ dpi, double *__restrict__ lam_out) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= T) return;
-  const HoFacet fc = ho_facet(g, row >> 2);
+  const HoFacet fc = ho_facet(g, row / Ho<P>::NB);
   const double a = dpi[(int64_t)fc.cA * g.L + fc.kA];
   lam_out[row] = fc.cB >= 0 ? fma(0.5, a + dpi[(int64_t)fc.cB * g.L + fc.kB], lam_in[row]) : lam_in[row] + a;
 }
@@ -715,6 +901,7 @@ __global__ void ho_gamma_kernel(int64_t ncell, const double *__restrict__ m, dou
 }
 
 // ---- host side ------------------------------------------------------------------------------------
+template <int P>
 static HoGeo ho_geo(const Ctx *c) {
   const Level &f = c->lv[0];
   HoGeo g;
@@ -722,7 +909,7 @@ static HoGeo ho_geo(const Ctx *c) {
   g.ncol = f.ncol;
   g.nhf = (int64_t)f.nedge * f.nlev;
   g.nzf = (int64_t)f.ncol * (f.nlev + 1);
-  g.NH = 4 * g.nhf;
+  g.NH = (int64_t)Ho<P>::NB * g.nhf;
   g.col_edges = f.col_edges;
   g.stencil = f.edge_stencil;
   g.edge_fc = f.edge_fc;
@@ -730,137 +917,168 @@ static HoGeo ho_geo(const Ctx *c) {
   return g;
 }
 
-int64_t ho_trace_size(const Ctx *c) {
+int64_t ho_trace_size(const Ctx *c, int p) {
   const Level &f = c->lv[0];
-  return 4 * ((int64_t)f.nedge * f.nlev + (int64_t)f.ncol * (f.nlev + 1));
+  return (int64_t)(p + 1) * (p + 1) * ((int64_t)f.nedge * f.nlev + (int64_t)f.ncol * (f.nlev + 1));
 }
 
+template <int P>
 static int ho_build_factors(Ctx *c) {
   HoData &h = c->ho;
-  const HoGeo g = ho_geo(c);
+  const HoGeo g = ho_geo<P>(c);
   int *sing = h.flag;
   HMG_CUDA(c, cudaMemsetAsync(sing, 0, sizeof(int), c->stream));
-  ho_hfactor_kernel<<<grid_for(g.nhf, 128), 128, 0, c->stream>>>(g, h.T, h.S, c->opt.omega, h.hw, sing);
-  ho_zfactor_kernel<<<grid_for(g.ncol, 64), 64, 0, c->stream>>>(g, h.T, h.S, c->opt.omega, h.zf, sing);
+  constexpr int NB = Ho<P>::NB;
+  const size_t zsmem = sizeof(double) * kHoFacWarps * (3 * NB * NB + 2 * NB * NB);
+  ho_hfactor_kernel<P><<<grid_for(g.nhf, kHoFacWarps), 32 * kHoFacWarps, 0, c->stream>>>(g, h.T, h.S, c->opt.omega,
+                                                                                      h.hw, sing);
+  ho_zfactor_kernel<P><<<grid_for(g.ncol, kHoFacWarps), 32 * kHoFacWarps, zsmem, c->stream>>>(
+      g, h.T, h.S, c->opt.omega, h.zf, sing);
   HMG_CUDA(c, cudaGetLastError());
   int s = 0;
   HMG_CUDA(c, cudaMemcpyAsync(&s, sing, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (s) return fail(c, HMG_ERR_INVALID_ARG, "a smoother block of the degree-1 trace operator is singular");
+  if (s) return fail(c, HMG_ERR_INVALID_ARG, "a smoother block of the degree-p trace operator is singular");
   h.factor_omega = c->opt.omega;
   return HMG_OK;
 }
 
-int ho_assemble(Ctx *c) {
+void ho_free(Ctx *c) {
+  HoData &h = c->ho;
+  double **bufs[] = {&h.tab, &h.S, &h.Ainv, &h.hw, &h.zf, &h.gamma, &h.m};
+  for (double **b : bufs) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
+  dev_free(c, h.own);
+  h.own = nullptr;
+  dev_free(c, h.flag);
+  h.flag = nullptr;
+  h.degree = 0;
+  h.ncell = 0;
+  h.T = 0;
+}
+
+template <int P>
+static int ho_assemble_p(Ctx *c) {
+  using H = Ho<P>;
   const Level &f = c->lv[0];
   HoData &h = c->ho;
-  if (c->sc.preset != 1) return fail(c, HMG_ERR_INVALID_ARG, "degree 1 is built for the Helmholtz preset (preset 1)");
   const int64_t C = f.ncell;
   int st;
-  if (!h.S) {
-    h.T = ho_trace_size(c);
+  if (C > 0x7fffffff) return fail(c, HMG_ERR_INVALID_ARG, "too many cells for one launch");
+  if (h.degree != P || h.ncell != C || h.T != ho_trace_size(c, P)) {   // (re)allocate for this degree and mesh
+    ho_free(c);
     std::vector<double> tab;
-    ho_tables(tab);
+    ho_tables<P>(tab);
     if ((st = dev_alloc(c, &h.tab, tab.size()))) return st;
     HMG_CUDA(c, cudaMemcpy(h.tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
-    if ((st = dev_alloc(c, &h.S, (size_t)kHoSlots * h.T))) return st;
-    if ((st = dev_alloc(c, &h.Ainv, (size_t)kHoN * kHoN * C))) return st;
-    if ((st = dev_alloc(c, &h.hw, (size_t)16 * f.nedge * f.nlev))) return st;
-    if ((st = dev_alloc(c, &h.zf, (size_t)48 * f.ncol * (f.nlev + 1)))) return st;
+    const int64_t T = ho_trace_size(c, P);
+    if ((st = dev_alloc(c, &h.S, (size_t)H::SLOTS * T))) return st;
+    if ((st = dev_alloc(c, &h.Ainv, (size_t)H::N * H::N * C))) return st;
+    if ((st = dev_alloc(c, &h.hw, (size_t)H::NB * H::NB * f.nedge * f.nlev))) return st;
+    if ((st = dev_alloc(c, &h.zf, (size_t)3 * H::NB * H::NB * f.ncol * (f.nlev + 1)))) return st;
     if ((st = dev_alloc(c, &h.gamma, (size_t)C))) return st;
     if ((st = dev_alloc(c, &h.m, (size_t)C))) return st;
     if ((st = dev_alloc(c, &h.own, (size_t)4 * f.ncol))) return st;
     if ((st = dev_alloc(c, &h.flag, 1))) return st;
+    h.degree = P;
+    h.ncell = C;
+    h.T = T;
   }
+  h.factor_omega = 0.0;
   HMG_CUDA(c, cudaMemsetAsync(h.own, 0, 4 * (size_t)f.ncol, c->stream));
   ho_own_kernel<<<grid_for(f.nedge, 256), 256, 0, c->stream>>>(f.edge_stencil, f.edge_fc, f.nedge, h.own);
   HMG_CUDA(c, cudaMemsetAsync(h.flag, 0, sizeof(int), c->stream));
   HoCellArgs a{f.geometry, f.ncol, f.nlev, C, f.radius, c->sc.sigma, f.corners, f.z};
-  ho_cell_kernel<<<(unsigned)C, 128, 0, c->stream>>>(a, h.tab, h.Ainv, h.m, h.flag);
+  const size_t smem = HoCellSmem<P>::BYTES;
+  HMG_CUDA(c, cudaFuncSetAttribute(ho_cell_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ho_cell_kernel<P><<<(unsigned)C, 256, smem, c->stream>>>(a, h.tab, h.Ainv, h.m, h.flag);
   HMG_CUDA(c, cudaGetLastError());
   int sing = 0;
   HMG_CUDA(c, cudaMemcpyAsync(&sing, h.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (sing) return fail(c, HMG_ERR_INVALID_ARG, "a degree-1 cell matrix A_K is singular");
-  const HoGeo g = ho_geo(c);
-  ho_rows_kernel<<<grid_for(h.T, 256), 256, 0, c->stream>>>(g, h.T, h.Ainv, h.S);
+  if (sing) return fail(c, HMG_ERR_INVALID_ARG, "a degree-p cell matrix A_K is singular");
+  const HoGeo g = ho_geo<P>(c);
+  ho_rows_kernel<P><<<grid_for(h.T, 256), 256, 0, c->stream>>>(g, h.T, h.tab, h.Ainv, h.S);
   HMG_CUDA(c, cudaGetLastError());
   // Gamma = (H 1) / (P^T S P 1): S applied to the ones vector (P 1 = 1), then P^T
   double *ones = static_cast<double *>(c->w1), *s1 = static_cast<double *>(c->w2);
   ho_fill_kernel<<<grid_for(h.T, 256), 256, 0, c->stream>>>(ones, h.T, 1.0);
-  ho_spmv_kernel<0><<<grid_for(g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
+  ho_spmv_kernel<P, 0><<<grid_for(g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
       g, h.T, h.S, ones, s1, nullptr, c->part, 0, 0);
-  ho_restrict_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, s1, nullptr, h.gamma);
+  ho_restrict_kernel<P><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, s1, nullptr, h.gamma);
   ho_gamma_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(C, h.m, h.gamma);
   HMG_CUDA(c, cudaGetLastError());
-  return ho_build_factors(c);
+  return ho_build_factors<P>(c);
 }
 
-int ho_refactor_if_needed(Ctx *c) {
-  if (c->ho.factor_omega == c->opt.omega) return HMG_OK;
-  return ho_build_factors(c);
-}
-
-int ho_launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1) {
+template <int P>
+static int ho_launch_spmv_p(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1) {
   const HoData &h = c->ho;
-  const HoGeo g = ho_geo(c);
+  const HoGeo g = ho_geo<P>(c);
   const unsigned grid = grid_for(g.nhf + g.nzf, kRedThreads);
   if (grid > (unsigned)kMaxRedBlocks) return fail(c, HMG_ERR_INVALID_ARG, "too many facets for one reduction");
   Prof prof(c, kCompApply);
   switch (mode) {
-    case 0: ho_spmv_kernel<0><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
-    case 1: ho_spmv_kernel<1><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
-    case 2: ho_spmv_kernel<2><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
-    default: ho_spmv_kernel<3><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
+    case 0: ho_spmv_kernel<P, 0><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
+    case 1: ho_spmv_kernel<P, 1><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
+    case 2: ho_spmv_kernel<P, 2><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
+    default: ho_spmv_kernel<P, 3><<<grid, kRedThreads, 0, c->stream>>>(g, h.T, h.S, x, y, w, c->part, slot0, slot1); break;
   }
   HMG_CUDA(c, cudaGetLastError());
   if (mode != 0) return launch_finalize(c, (int)grid, slot0, mode == 2 ? slot1 : -1);
   return HMG_OK;
 }
 
-int ho_trace_rhs(Ctx *c, const double *Ru, const double *Rp, double *B) {
+template <int P>
+static int ho_trace_rhs_p(Ctx *c, const double *Ru, const double *Rp, double *B) {
   const HoData &h = c->ho;
   Prof prof(c, kCompRhs);
-  ho_rhs_kernel<<<grid_for(h.T, 128), 128, 0, c->stream>>>(ho_geo(c), h.T, h.Ainv, Ru, Rp, B);
+  ho_rhs_kernel<P><<<grid_for(h.T, 128), 128, 0, c->stream>>>(ho_geo<P>(c), h.T, h.tab, h.Ainv, Ru, Rp, B);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
 
-int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi) {
+template <int P>
+static int ho_reconstruct_p(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi) {
   const int64_t C = c->lv[0].ncell;
-  ho_reconstruct_kernel<<<grid_for(C * kHoN, 128), 128, 0, c->stream>>>(ho_geo(c), C, c->ho.Ainv, lam, Ru, Rp, u,
-                                                                        pi);
+  ho_reconstruct_kernel<P><<<grid_for(C * Ho<P>::N, 128), 128, 0, c->stream>>>(ho_geo<P>(c), C, c->ho.tab,
+                                                                              c->ho.Ainv, lam, Ru, Rp, u, pi);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
 
-constexpr int kHoCpb = 32;   // columns per block of the sweep's line part (four lanes each)
-
-template <bool ZERO>
+template <int P, bool ZERO>
 static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_out) {
+  using H = Ho<P>;
   const HoData &h = c->ho;
-  const HoGeo g = ho_geo(c);
-  // columns per block: the block's residual rows (4 (L + 1) doubles per column) within 48 KB
-  const int cap = (int)((48 * 1024) / (sizeof(double) * 4 * (g.L + 1)));
-  if (cap < 1) return fail(c, HMG_ERR_INVALID_ARG, "degree 1 takes at most 1535 layers");
-  const int cpb = cap < kHoCpb ? cap : kHoCpb;
+  const HoGeo g = ho_geo<P>(c);
+  // columns per block: 128 / LPC, and the block's residual rows (NB (L + 1) doubles per column)
+  // within 48 KB
+  const int cap = (int)((48 * 1024) / (sizeof(double) * H::NB * (g.L + 1)));
+  if (cap < 1) return fail(c, HMG_ERR_INVALID_ARG, "too many layers for the degree-p line smoother");
+  const int cpb = cap < 128 / H::LPC ? cap : 128 / H::LPC;
   const int nzb = (g.ncol + cpb - 1) / cpb;
   const unsigned nhb = grid_for(g.nhf, 128);
-  const size_t smem = sizeof(double) * 4 * cpb * (g.L + 1);
+  const size_t smem = sizeof(double) * H::NB * cpb * (g.L + 1);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
-  ho_sweep_kernel<ZERO><<<nzb + nhb, 128, smem, c->stream>>>(g, h.T, cpb, nzb, h.S, h.hw, h.zf, b, lam_in, lam_out,
-                                                              1.0 - h.factor_omega);
+  ho_sweep_kernel<P, ZERO><<<nzb + nhb, 128, smem, c->stream>>>(g, h.T, cpb, nzb, h.S, h.hw, h.zf, b, lam_in,
+                                                                 lam_out, 1.0 - h.factor_omega);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
 
-int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps) {
+template <int P>
+static int ho_line_smooth_p(Ctx *c, const double *b, double *lam, int nsweeps) {
   int st;
   if ((st = ho_refactor_if_needed(c))) return st;
   double *cur = lam, *nxt = static_cast<double *>(c->w3);
   for (int i = 0; i < nsweeps; ++i) {
-    if ((st = ho_sweep<false>(c, b, cur, nxt))) return st;
-    double *t = cur; cur = nxt; nxt = t;
+    if ((st = ho_sweep<P, false>(c, b, cur, nxt))) return st;
+    double *t = cur;
+    cur = nxt;
+    nxt = t;
   }
   if (cur != lam)
     HMG_CUDA(c, cudaMemcpyAsync(lam, cur, sizeof(double) * c->ho.T, cudaMemcpyDeviceToDevice, c->stream));
@@ -869,9 +1087,10 @@ int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps) {
 
 // z = M^-1 r: configuration 3c (Algorithm 2, the V-cycle of the lowest-order pressure operator as
 // the coarse solve), configuration 2 (n_smooth sweeps of Algorithm 1 from zero) or none.
-int ho_precond(Ctx *c, const double *r, double *z) {
+template <int P>
+static int ho_precond_p(Ctx *c, const double *r, double *z) {
   const HoData &h = c->ho;
-  const HoGeo g = ho_geo(c);
+  const HoGeo g = ho_geo<P>(c);
   const int64_t T = h.T, C = c->lv[0].ncell;
   int st;
   double *w1 = static_cast<double *>(c->w1), *w2 = static_cast<double *>(c->w2), *w3 = static_cast<double *>(c->w3);
@@ -881,21 +1100,25 @@ int ho_precond(Ctx *c, const double *r, double *z) {
   }
   if (c->opt.precond == HMG_PRECOND_LINESMOOTH) {
     const int n = c->opt.n_smooth;
-    if (n == 1) return ho_sweep<true>(c, r, nullptr, z);
-    if ((st = ho_sweep<true>(c, r, nullptr, w1))) return st;
+    if (n == 1) return ho_sweep<P, true>(c, r, nullptr, z);
+    if ((st = ho_sweep<P, true>(c, r, nullptr, w1))) return st;
     double *cur = w1, *nxt = w2;
     for (int i = 1; i < n; ++i) {
-      if ((st = ho_sweep<false>(c, r, cur, i == n - 1 ? z : nxt))) return st;
-      double *t = cur; cur = nxt; nxt = t;
+      if ((st = ho_sweep<P, false>(c, r, cur, i == n - 1 ? z : nxt))) return st;
+      double *t = cur;
+      cur = nxt;
+      nxt = t;
     }
     return HMG_OK;
   }
   // lines 1-2: presmoothing from zero
   if (c->opt.n_pre >= 1) {
-    if ((st = ho_sweep<true>(c, r, nullptr, w1))) return st;
+    if ((st = ho_sweep<P, true>(c, r, nullptr, w1))) return st;
     for (int i = 1; i < c->opt.n_pre; ++i) {
-      if ((st = ho_sweep<false>(c, r, w1, w2))) return st;
-      double *t = w1; w1 = w2; w2 = t;
+      if ((st = ho_sweep<P, false>(c, r, w1, w2))) return st;
+      double *t = w1;
+      w1 = w2;
+      w2 = t;
     }
   } else {
     HMG_CUDA(c, cudaMemsetAsync(w1, 0, sizeof(double) * T, c->stream));
@@ -904,11 +1127,11 @@ int ho_precond(Ctx *c, const double *r, double *z) {
   {
     Prof pr(c, kCompResidual, 2);
     if (c->opt.n_pre == 1)   // w1 is one sweep from zero                                       // line 3
-      ho_residual_kernel<true><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2,
-                                                                                   1.0 - h.factor_omega);
+      ho_residual_kernel<P, true><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2,
+                                                                                      1.0 - h.factor_omega);
     else
-      ho_residual_kernel<false><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2, 0.0);
-    ho_restrict_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, w2, h.gamma, cb);          // lines 4-5
+      ho_residual_kernel<P, false><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2, 0.0);
+    ho_restrict_kernel<P><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, w2, h.gamma, cb);       // lines 4-5
     HMG_CUDA(c, cudaGetLastError());
   }
   double *dpi = nullptr;
@@ -918,7 +1141,7 @@ int ho_precond(Ctx *c, const double *r, double *z) {
   }
   {
     Prof pp(c, kCompProlong);
-    ho_prolong_kernel<<<grid_for(T, 256), 256, 0, c->stream>>>(g, T, w1, dpi, w2);                  // line 7
+    ho_prolong_kernel<P><<<grid_for(T, 256), 256, 0, c->stream>>>(g, T, w1, dpi, w2);               // line 7
     HMG_CUDA(c, cudaGetLastError());
   }
   const int np = c->opt.n_post;                                                                    // line 8
@@ -928,10 +1151,80 @@ int ho_precond(Ctx *c, const double *r, double *z) {
   }
   double *cur = w2, *nxt = w3;
   for (int i = 0; i < np - 1; ++i) {
-    if ((st = ho_sweep<false>(c, r, cur, nxt))) return st;
-    double *t = cur; cur = nxt; nxt = t;
+    if ((st = ho_sweep<P, false>(c, r, cur, nxt))) return st;
+    double *t = cur;
+    cur = nxt;
+    nxt = t;
   }
-  return ho_sweep<false>(c, r, cur, z);
+  return ho_sweep<P, false>(c, r, cur, z);
+}
+
+// ---- degree dispatch ------------------------------------------------------------------------------
+static int bad_degree(Ctx *c) { return fail(c, HMG_ERR_INVALID_ARG, "the degree-p path takes p = 1, 2, 3"); }
+
+int ho_assemble(Ctx *c) {
+  if (c->sc.preset != 1) return fail(c, HMG_ERR_INVALID_ARG, "degree p >= 1 is built for the Helmholtz preset (preset 1)");
+  switch (c->degree) {
+    case 1: return ho_assemble_p<1>(c);
+    case 2: return ho_assemble_p<2>(c);
+    case 3: return ho_assemble_p<3>(c);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_refactor_if_needed(Ctx *c) {
+  if (c->ho.factor_omega == c->opt.omega) return HMG_OK;
+  switch (c->degree) {
+    case 1: return ho_build_factors<1>(c);
+    case 2: return ho_build_factors<2>(c);
+    case 3: return ho_build_factors<3>(c);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1) {
+  switch (c->degree) {
+    case 1: return ho_launch_spmv_p<1>(c, x, y, mode, w, slot0, slot1);
+    case 2: return ho_launch_spmv_p<2>(c, x, y, mode, w, slot0, slot1);
+    case 3: return ho_launch_spmv_p<3>(c, x, y, mode, w, slot0, slot1);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_trace_rhs(Ctx *c, const double *Ru, const double *Rp, double *B) {
+  switch (c->degree) {
+    case 1: return ho_trace_rhs_p<1>(c, Ru, Rp, B);
+    case 2: return ho_trace_rhs_p<2>(c, Ru, Rp, B);
+    case 3: return ho_trace_rhs_p<3>(c, Ru, Rp, B);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi) {
+  switch (c->degree) {
+    case 1: return ho_reconstruct_p<1>(c, lam, Ru, Rp, u, pi);
+    case 2: return ho_reconstruct_p<2>(c, lam, Ru, Rp, u, pi);
+    case 3: return ho_reconstruct_p<3>(c, lam, Ru, Rp, u, pi);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps) {
+  switch (c->degree) {
+    case 1: return ho_line_smooth_p<1>(c, b, lam, nsweeps);
+    case 2: return ho_line_smooth_p<2>(c, b, lam, nsweeps);
+    case 3: return ho_line_smooth_p<3>(c, b, lam, nsweeps);
+    default: return bad_degree(c);
+  }
+}
+
+int ho_precond(Ctx *c, const double *r, double *z) {
+  switch (c->degree) {
+    case 1: return ho_precond_p<1>(c, r, z);
+    case 2: return ho_precond_p<2>(c, r, z);
+    case 3: return ho_precond_p<3>(c, r, z);
+    default: return bad_degree(c);
+  }
 }
 
 }  // namespace hmg

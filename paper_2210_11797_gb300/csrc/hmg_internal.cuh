@@ -84,13 +84,16 @@ struct TrainBufs {
   size_t cap_tn = 0, cap_tnb = 0, cap_xb = 0, cap_tb = 0, cap_order = 0;
 };
 
-// The degree-1 trace system (higher_order.cu), finest level only.
+// The trace system of degree p = 1, 2, 3 (higher_order.cu), finest level only; NB = (p+1)^2
+// rows per facet, NF = 6 NB facet dofs per cell, N = the mixed cell matrix's order.
 struct HoData {
-  int64_t T = 0;               // trace rows: four per facet
-  double *S = nullptr;         // [48][T] two cells x 24 facet-dof coefficients per row
-  double *Ainv = nullptr;      // [ncell][44][44] A_K^-1
-  double *hw = nullptr;        // [16][vertical facets] omega (facet block of S)^-1
-  double *zf = nullptr;        // [48][horizontal facets] block Thomas factors of S^zz
+  int degree = 0;              // the degree the buffers below are laid out for (0: none)
+  int64_t ncell = 0;
+  int64_t T = 0;               // trace rows: NB per facet
+  double *S = nullptr;         // [2 NF][T] two cells x NF facet-dof coefficients per row
+  double *Ainv = nullptr;      // [ncell][N][N] A_K^-1
+  double *hw = nullptr;        // [NB^2][vertical facets] omega (facet block of S)^-1
+  double *zf = nullptr;        // [horizontal facets][3 NB^2] block Thomas factors of S^zz
   double *gamma = nullptr;     // [ncell] Gamma of Eq. scaling_matrix
   double *m = nullptr;         // [ncell] sigma |K|_1 = (H 1)_K
   int8_t *own = nullptr;       // [ncol][4] 1 where the column owns the edge of its face
@@ -108,7 +111,7 @@ struct Ctx {
   int nmg = 0;
   Level lv[kMaxLevels];
   bool have_mesh = false, have_coeffs = false, assembled = false, have_fp32 = false;
-  int degree = 0;              // polynomial degree of the assembled system (0 or 1)
+  int degree = 0;              // polynomial degree of the assembled system (0 .. 3)
   HoData ho;
   // finest-level trace system (device)
   double *S = nullptr;        // [11][ntrace]
@@ -304,7 +307,7 @@ int schur_precond(Ctx *c, const double *r, double *z);
 // the Krylov system of the context's configuration: its length, operator and right-hand side
 inline bool mixed_system(const Ctx *c) { return c->opt.precond == HMG_PRECOND_SCHUR; }
 inline int64_t sys_n(const Ctx *c) {
-  if (c->degree == 1) return c->ho.T;
+  if (c->degree >= 1) return c->ho.T;
   return c->lv[0].ntrace + (mixed_system(c) ? c->lv[0].ncell : 0);
 }
 // Batched solves: one CUDA graph with one branch per context (contexts on one device).
@@ -313,19 +316,23 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
 // Releases the context's cached solve graph.
 void drop_graph(Ctx *c);
 
-// ---- degree 1 (higher_order.cu) ----------------------------------------------------------
-int64_t ho_trace_size(const Ctx *c);
+// ---- degree p = 1, 2, 3 (higher_order.cu) -----------------------------------------------------
+int64_t ho_trace_size(const Ctx *c, int p);                // (p+1)^2 rows per facet
 int ho_assemble(Ctx *c);                                   // needs w1, w2 of ho_trace_size doubles
+void ho_free(Ctx *c);
 int ho_launch_spmv(Ctx *c, const double *x, double *y, int mode, const double *w, int slot0, int slot1);
 int ho_trace_rhs(Ctx *c, const double *Ru, const double *Rp, double *B);
 int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi);
 int ho_precond(Ctx *c, const double *r, double *z);
 int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps);
-// rebuilds the degree-1 smoother factors when omega changed since they were built (synchronises)
+// rebuilds the degree-p smoother factors when omega changed since they were built (synchronises)
 int ho_refactor_if_needed(Ctx *c);
-// cell residual sizes of the assembled degree: velocity and pressure dofs per cell
-inline int cell_nu(const Ctx *c) { return c->degree == 1 ? 36 : 6; }
-inline int cell_np(const Ctx *c) { return c->degree == 1 ? 8 : 1; }
+// cell residual sizes of degree p: 3 (p+1)^2 (p+2) velocity and (p+1)^3 pressure dofs per cell
+// (6 and 1 at the lowest order)
+inline int cell_nu_of(int p) { return 3 * (p + 1) * (p + 1) * (p + 2); }
+inline int cell_np_of(int p) { return (p + 1) * (p + 1) * (p + 1); }
+inline int cell_nu(const Ctx *c) { return cell_nu_of(c->degree); }
+inline int cell_np(const Ctx *c) { return cell_np_of(c->degree); }
 
 // ---- learned coarse correction (learned.cu) ---------------------------------------------
 constexpr int kCoarseParams = 3360;

@@ -54,11 +54,11 @@ enum { kIt = 0, kStatus = 1, kContinue = 2, kWaitFlag = 3 };
 // The system the Krylov loop iterates on: S lambda = B_lambda (hybridised configurations) or
 // the 2x2 system on [u | Pi] (configuration 1).
 static int sys_apply(Ctx *c, const double *x, double *y, int mode, const double *w, int s0, int s1) {
-  if (c->degree == 1) return ho_launch_spmv(c, x, y, mode, w, s0, s1);
+  if (c->degree >= 1) return ho_launch_spmv(c, x, y, mode, w, s0, s1);
   return mixed_system(c) ? launch_mixed_apply(c, x, y, mode, w, s0, s1) : launch_spmv(c, x, y, mode, w, s0, s1);
 }
 static int sys_rhs(Ctx *c, const double *Rub, const double *Rpi, double *B) {
-  if (c->degree == 1) return ho_trace_rhs(c, Rub, Rpi, B);
+  if (c->degree >= 1) return ho_trace_rhs(c, Rub, Rpi, B);
   return mixed_system(c) ? launch_mixed_rhs(c, Rub, Rpi, B) : launch_trace_rhs(c, Rub, Rpi, B);
 }
 

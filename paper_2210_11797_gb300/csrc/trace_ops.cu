@@ -466,7 +466,7 @@ static int two_level(Ctx *c, const double *r, double *z) {
 }
 
 int precond_apply(Ctx *c, const double *r, double *z) {
-  if (c->degree == 1) return ho_precond(c, r, z);
+  if (c->degree >= 1) return ho_precond(c, r, z);
   const bool mixed = c->opt.precision == HMG_PRECISION_MIXED;
   switch (c->opt.precond) {
     case HMG_PRECOND_SCHUR:

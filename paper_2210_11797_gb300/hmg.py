@@ -213,13 +213,13 @@ class Solver:
         self._keep = []
 
     def _sizes(self):
-        """Cells, trace unknowns and the cell residual dofs of the assembled degree (velocity:
-        6 at degree 0, 36 at degree 1; pressure: 1, 8)."""
+        """Cells, trace unknowns and the cell residual dofs of the assembled degree p (velocity:
+        3 (p+1)^2 (p+2) = 6, 36, 108, 240; pressure: (p+1)^3 = 1, 8, 27, 64)."""
         nc, nt = C.c_int64(), C.c_int64()
         _check(self.ctx, lib().hmg_sizes(self.ctx, C.byref(nc), C.byref(nt)))
         self.ncell, self.ntrace = nc.value, nt.value
-        self.degree = self.opts.degree
-        self.nu, self.npr = (36, 8) if self.degree == 1 else (6, 1)
+        self.degree = p = self.opts.degree
+        self.nu, self.npr = 3 * (p + 1) ** 2 * (p + 2), (p + 1) ** 3
 
     def _arr(self, a, dtype):
         a = np.ascontiguousarray(a, dtype=dtype)

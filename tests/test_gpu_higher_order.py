@@ -1,8 +1,8 @@
-"""Degree 1 on the GPU (hmg_options.degree = 1, through the C ABI) against the degree-p oracle
-(oracle/higher_order.py): the trace operator, B_lambda, recovery, Gamma, the line smoother
-(facet blocks and block-tridiagonal columns), Algorithm 2 with the DG0 coarse space, and whole
-solves, on the periodic plane and on curved cubed-sphere cells, plus a one-layer mesh and a
-ragged column block.
+"""Degrees 1, 2 and 3 on the GPU (hmg_options.degree = p, through the C ABI) against the
+degree-p oracle (oracle/higher_order.py): the trace operator, B_lambda, recovery, Gamma, the
+line smoother (facet blocks and block-tridiagonal columns), Algorithm 2 with the DG0 coarse
+space, and whole solves, on the periodic plane and on curved cubed-sphere cells, plus one-layer
+meshes and ragged column blocks (32 columns per block of the line part at p = 1, 8 at p = 2, 3).
 
 Tolerances (FP64 on both sides, different summation orders): single operator applications and
 right-hand sides within 1e-13 of the row scale; sweeps, the two-level cycle and recovery
@@ -35,24 +35,35 @@ def _sphere(n=4, nlev=5, nmg=2):
 
 _CACHE = {}
 
+# (mesh, degree): the plane (periodic, affine cells), curved cubed-sphere cells, and one-layer
+# meshes whose column count leaves a ragged last block of the line smoother
+CASES = [("planar8", 1), ("sphereC4L5", 1), ("planar5L1", 1),
+         ("planar6", 2), ("sphereC3L3", 2), ("planar5L1", 2),
+         ("planar4", 3), ("sphereC2L3", 3), ("planar3L1", 3)]
+IDS = [f"{n}-p{p}" for n, p in CASES]
 
-def _pair(name):
-    if name not in _CACHE:
+
+def _mesh(name):
+    if name == "sphereC4L5":
+        return _sphere()
+    if name == "sphereC3L3":
+        return _sphere(3, 3, 1)
+    if name == "sphereC2L3":
+        return _sphere(2, 3, 1)
+    n, nlev = {"planar8": (8, 4), "planar6": (6, 3), "planar4": (4, 3), "planar5L1": (5, 1),
+               "planar3L1": (3, 1)}[name]
+    w = I.planar_helmholtz(n=n, nlev=nlev, nmg=2 if n >= 8 else 1)
+    return w.hier, w.coeffs
+
+
+def _pair(name, p):
+    if (name, p) not in _CACHE:
         from paper_2210_11797_gb300.hmg import Solver
-        if name == "planar8":
-            w = I.planar_helmholtz(n=8, nlev=4, nmg=2)
-            hier, co = w.hier, w.coeffs
-        elif name == "sphereC4L5":
-            hier, co = _sphere()
-        elif name == "planar5L1":                 # one layer, odd columns: a ragged column block
-            w = I.planar_helmholtz(n=5, nlev=1, nmg=1)
-            hier, co = w.hier, w.coeffs
-        else:
-            raise KeyError(name)
-        ora = HO.HigherOrderHybrid(hier, co, 1)
-        gpu = Solver(hier, co, tol=1e-12, degree=1)
-        _CACHE[name] = (ora, gpu)
-    ora, gpu = _CACHE[name]
+        hier, co = _mesh(name)
+        ora = HO.HigherOrderHybrid(hier, co, p)
+        gpu = Solver(hier, co, tol=1e-12, degree=p)
+        _CACHE[(name, p)] = (ora, gpu)
+    ora, gpu = _CACHE[(name, p)]
     gpu.set_options(tol=1e-12, max_iter=200, precond="nonnested", n_smooth=1, krylov="bicgstab")
     return ora, gpu
 
@@ -63,13 +74,10 @@ def _rhs(ora, seed):
     return rng.standard_normal((C, ora.el.nu)), rng.standard_normal((C, ora.el.npr))
 
 
-NAMES = ["planar8", "sphereC4L5", "planar5L1"]
-
-
-@pytest.mark.parametrize("name", NAMES)
-def test_sizes_and_trace_operator(name):
-    ora, gpu = _pair(name)
-    assert gpu.ntrace == ora.T and gpu.degree == 1 and (gpu.nu, gpu.npr) == (36, 8)
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_sizes_and_trace_operator(name, p):
+    ora, gpu = _pair(name, p)
+    assert gpu.ntrace == ora.T and gpu.degree == p and (gpu.nu, gpu.npr) == (ora.el.nu, ora.el.npr)
     x = np.random.default_rng(1).standard_normal(ora.T)
     y = _np(gpu.apply_trace(_cuda(x)))
     ref = ora.S @ x
@@ -77,9 +85,9 @@ def test_sizes_and_trace_operator(name):
     assert np.all(np.abs(y - ref) <= 1e-13 * scale + 1e-300)
 
 
-@pytest.mark.parametrize("name", NAMES)
-def test_rhs_gamma_and_recovery(name):
-    ora, gpu = _pair(name)
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_rhs_gamma_and_recovery(name, p):
+    ora, gpu = _pair(name, p)
     Ru, Rpi = _rhs(ora, 2)
     B = _np(gpu.trace_rhs(_cuda(Ru), _cuda(Rpi)))
     Bo = ora.rhs(Ru, Rpi)
@@ -93,9 +101,9 @@ def test_rhs_gamma_and_recovery(name):
     assert np.abs(_np(pi).reshape(pio.shape) - pio).max() <= 1e-11 * np.abs(pio).max()
 
 
-@pytest.mark.parametrize("name", NAMES)
-def test_line_smoother_and_two_level_cycle(name):
-    ora, gpu = _pair(name)
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_line_smoother_and_two_level_cycle(name, p):
+    ora, gpu = _pair(name, p)
     rng = np.random.default_rng(4)
     lam, b = rng.standard_normal(ora.T), ora.S @ rng.standard_normal(ora.T)
     got = _np(gpu.line_smooth(_cuda(b), _cuda(lam), 2))
@@ -107,9 +115,9 @@ def test_line_smoother_and_two_level_cycle(name):
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("name", NAMES)
-def test_solve_matches_oracle(name):
-    ora, gpu = _pair(name)
+@pytest.mark.parametrize("name,p", CASES, ids=IDS)
+def test_solve_matches_oracle(name, p):
+    ora, gpu = _pair(name, p)
     Ru, Rpi = _rhs(ora, 5)
     lam, st = gpu.solve(_cuda(Ru), _cuda(Rpi))
     lo, hist, sto = ora.solve(Ru, Rpi, 1e-12)
@@ -127,7 +135,8 @@ def test_solve_matches_oracle(name):
     assert np.array_equal(lam_h, _np(lam))
 
 
-def test_solve_at_degree_one_with_a_smooth_solution():
+@pytest.mark.parametrize("p", [1, 2])
+def test_solve_at_degree_p_with_a_smooth_solution(p):
     """The manufactured solution of the oracle's convergence pin, solved on the GPU: the same
     discrete pressure, hence the same L2 error."""
     H = 0.1
@@ -138,9 +147,9 @@ def test_solve_at_degree_one_with_a_smooth_solution():
     from paper_2210_11797_gb300.hmg import Solver
     w = I.planar_helmholtz(n=8, nlev=8, nmg=2, top=H)
     sigma = w.coeffs.sigma
-    ora = HO.HigherOrderHybrid(w.hier, w.coeffs, 1)
+    ora = HO.HigherOrderHybrid(w.hier, w.coeffs, p)
     Ru, Rpi, l2 = HO.manufactured_rhs(ora, pi_exact, lambda x: (sigma + 8 * np.pi ** 2 + (np.pi / H) ** 2) * pi_exact(x))
-    gpu = Solver(w.hier, w.coeffs, tol=1e-12, degree=1)
+    gpu = Solver(w.hier, w.coeffs, tol=1e-12, degree=p)
     try:
         lam, st = gpu.solve(_cuda(Ru), _cuda(Rpi))
         assert st["status"] == "ok"
@@ -153,18 +162,19 @@ def test_solve_at_degree_one_with_a_smooth_solution():
         gpu.close()
 
 
-def test_degree_one_options_are_checked():
+def test_degree_p_options_are_checked():
     from paper_2210_11797_gb300.hmg import HmgError, Solver
     w = I.planar_helmholtz(n=4, nlev=2, nmg=1)
     with pytest.raises(HmgError):
         Solver(w.hier, w.coeffs, degree=1, precision="mixed")
-    ws = I.cubed_sphere(4, 3, nmg=1)            # the physical preset: degree 1 covers preset 1 only
     with pytest.raises(HmgError):
-        Solver(ws.hier, ws.coeffs, degree=1)
-    s = Solver(w.hier, w.coeffs)                # degree 0 first, then switched to degree 1
+        Solver(w.hier, w.coeffs, degree=4)
+    ws = I.cubed_sphere(4, 3, nmg=1)            # the physical preset: degree p covers preset 1 only
+    with pytest.raises(HmgError):
+        Solver(ws.hier, ws.coeffs, degree=2)
+    s = Solver(w.hier, w.coeffs)                # degree 0 first, then switched through 1, 2, 3
     n0 = s.ntrace
-    s.set_options(degree=1)
-    assert s.ntrace == 4 * n0 and s.nu == 36
-    s.set_options(degree=0)
-    assert s.ntrace == n0 and s.nu == 6
+    for p in (1, 2, 3, 0, 2):
+        s.set_options(degree=p)
+        assert s.ntrace == (p + 1) ** 2 * n0 and s.nu == 3 * (p + 1) ** 2 * (p + 2) and s.npr == (p + 1) ** 3
     s.close()
