@@ -782,35 +782,47 @@ def run_configs(args, stream, model, lam_host):
     del lam64
     # configuration 4: the batch
     out["4_batch64_mixed"] = batch_solves(64, "mixed", steps, 2)
-    # row f4: degree 1 (RT1 / DG1 / Q1 trace) on the Helmholtz plane, larger than L2
-    out["f4_degree1_planar128"] = degree1_solves(args, stream, steps)
+    # row f4: degrees 1-3 (RT_p / DG_p / Q_p trace) on Helmholtz planes, larger than L2
+    for p in (1, 2, 3):
+        out[f"f4_degree{p}_planar{DEGREE_MESH[p]}"] = degree_solves(args, stream, steps, p)
     return out
 
 
-def degree1_bytes(mesh):
-    """Algorithmic bytes of one degree-1 S apply: per trace row the coefficients it reads (24 of
-    cell A, 20 of cell B: 44; 24 on ground and lid rows), x once and y once; the index tables."""
+DEGREE_MESH = {1: 128, 2: 88, 3: 64}   # n x n x 32 planes with about the same trace unknowns (6.2-6.8M)
+
+
+def degree_bytes(mesh, p):
+    """Algorithmic bytes of one degree-p S apply: per trace row the coefficients it reads (the
+    6 (p+1)^2 facet nodes of cell A, the 5 (p+1)^2 not shared of cell B: 11 (p+1)^2; 6 (p+1)^2 on
+    ground and lid rows), x once and y once; the index tables."""
     L, ncol, nedge = mesh.nlev, mesh.ncol, mesh.nedge
-    rows_h, rows_z = 4 * nedge * L, 4 * ncol * (L + 1)
-    rows_bnd = 8 * ncol                                   # ground and lid facets, four rows each
-    coeffs = 44 * (rows_h + rows_z - rows_bnd) + 24 * rows_bnd
+    nb = (p + 1) ** 2
+    rows_h, rows_z = nb * nedge * L, nb * ncol * (L + 1)
+    rows_bnd = 2 * nb * ncol                              # ground and lid facets
+    coeffs = 11 * nb * (rows_h + rows_z - rows_bnd) + 6 * nb * rows_bnd
     return 8 * (coeffs + 2 * (rows_h + rows_z)) + 4 * (8 * nedge + 4 * ncol) + 4 * ncol
 
 
-def degree1_solves(args, stream, steps, n=128, nlev=32):
+def degree_solves(args, stream, steps, p, nlev=32):
     """Row f4 measured: the constant-coefficient Helmholtz problem on an n x n x nlev periodic
-    box (c dt = 0.05, 4 multigrid levels) at degree 1, BiCGStab under Algorithm 2 to 1e-6 with
-    a seeded N(0,1) right-hand side; time to tolerance, unknowns/s, and the S apply's roofline
-    (profiled pass, CUDA events per component)."""
+    box (c dt = 0.05, 4 multigrid levels) at degree p (n = 128, 88, 64 for p = 1, 2, 3: about the
+    same number of trace unknowns), BiCGStab under Algorithm 2 to 1e-6 with a seeded N(0,1)
+    right-hand side; time to tolerance, unknowns/s, the assembly's wall time, and the S apply's
+    roofline (profiled pass, CUDA events per component)."""
     import torch
     from paper_2210_11797_gb300 import inputs as I
     from paper_2210_11797_gb300.hmg import Solver
+    n = DEGREE_MESH[p]
     w = I.planar_helmholtz(n=n, nlev=nlev, nmg=4, tol=1e-6)
-    s = Solver(w.hier, w.coeffs, tol=1e-6, degree=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = Solver(w.hier, w.coeffs, tol=1e-6, degree=p)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
     s.autotune()
     C = w.mesh.ncell
-    Ru = torch.as_tensor(I.normal(11, 36 * C)).cuda()
-    Rp = torch.as_tensor(I.normal(12, 8 * C)).cuda()
+    Ru = torch.as_tensor(I.normal(11, s.nu * C)).cuda()
+    Rp = torch.as_tensor(I.normal(12, s.npr * C)).cuda()
     lam, st, ms = _timed_solves(s, Ru, Rp, stream, steps)
     s.set_options(profile=1)
     torch.cuda.synchronize()
@@ -821,14 +833,17 @@ def degree1_solves(args, stream, steps, n=128, nlev=32):
     s.set_options(profile=0)
     comp = pst["components"]
     apply_ms = comp["trace_apply"]["ms"] / max(comp["trace_apply"]["launches"], 1)
-    nbytes = degree1_bytes(w.mesh)
+    nbytes = degree_bytes(w.mesh, p)
     peak, kind = measured_peaks()
     achieved = nbytes / (apply_ms / 1e3) / 1e9
-    out = {"workload": {"workload": f"planar_helmholtz_{n}x{n}x{nlev}_degree1", "ncell": C, "ntrace": s.ntrace,
-                        "dofs_per_cell": "36 RT1 + 8 DG1; 4 trace unknowns per facet", "tol": 1e-6,
-                        "precision": "fp64", "mg_levels": w.hier.nmg},
+    nb, nf, N = (p + 1) ** 2, 6 * (p + 1) ** 2, s.nu + s.npr
+    out = {"workload": {"workload": f"planar_helmholtz_{n}x{n}x{nlev}_degree{p}", "ncell": C, "ntrace": s.ntrace,
+                        "dofs_per_cell": f"{s.nu} RT{p} + {s.npr} DG{p}; {nb} trace unknowns per facet; "
+                                         f"cell matrices {N} x {N} condensed to {nf} x {nf}",
+                        "tol": 1e-6, "precision": "fp64", "mg_levels": w.hier.nmg},
            "ms_per_solve": round(ms, 4), "unknowns_per_s": round(s.ntrace / (ms / 1e3), 1),
            "iterations": st["iterations"], "status": st["status"], "true_rel_residual": st["true_rel_residual"],
+           "assembly_s": round(setup_s, 2),
            "components_ms_per_solve": {k: round(v["ms"], 4) for k, v in comp.items()},
            "roofline_trace_apply": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                                     "frac": round(achieved / peak, 4), "peak_kind": kind,
@@ -993,9 +1008,10 @@ def main():
     ap.add_argument("--train", action="store_true",
                     help="time the learned map's training alone (pairs of the workload, 20,000 patches, "
                          "--steps epochs); the profiler range is its first epoch")
-    ap.add_argument("--degree1", action="store_true",
-                    help="only the degree-1 workload (Helmholtz plane 128 x 128 x 32) as a JSON line; the "
-                         "profiler range is its host-driven profiled solve")
+    ap.add_argument("--degree", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="only the degree-p workload (Helmholtz plane n x n x 32, n = 128, 88, 64 for "
+                         "p = 1, 2, 3) as a JSON line; the profiler range is its host-driven profiled solve")
+    ap.add_argument("--degree1", action="store_true", help="the same as --degree 1")
     ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--_outdir", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1015,7 +1031,7 @@ def main():
     # the oracle leg starts first, in a fresh interpreter, and runs beside the GPU work
     child, outdir = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload.startswith("c") \
-            and not (args.param_sweep or args.coarse_map or args.degree1 or args.train):
+            and not (args.param_sweep or args.coarse_map or args.degree1 or args.degree or args.train):
         outdir = tempfile.mkdtemp(prefix="hmg_oracle_")
         child = start_oracle_child(args.workload, outdir)
     if world > 1:
@@ -1033,10 +1049,11 @@ def main():
         if rank == 0:
             print(json.dumps(run_train(args)))
         return
-    if args.degree1:
+    if args.degree1 or args.degree:
         if rank == 0:
             import torch
-            print(json.dumps(degree1_solves(args, torch.cuda.current_stream(), max(3, min(args.steps, 5)))))
+            print(json.dumps(degree_solves(args, torch.cuda.current_stream(), max(3, min(args.steps, 5)),
+                                           args.degree or 1)))
         return
     if args.workload.startswith("batch"):
         out = run_batched(args, rank, world)

@@ -763,81 +763,116 @@ __global__ void ho_reconstruct_kernel(const HoGeo g, int64_t ncell, const double
 // ---- Algorithm 1 at p >= 1 ------------------------------------------------------------------------
 // lam_out = lam_in + omega D^-1 (b - S lam_in) (ZERO: lam_in = 0), evaluated as
 // (1 - omega) lam_in + omega D^-1 (b - (S - D) lam_in): equal in exact arithmetic, without the
-// couplings of a row inside D. Blocks [0, nzb) take CPB columns each: the residual rows of their
-// horizontal facets staged in shared memory, then the block Thomas recurrences with LPC lanes per
-// column (lane n < NB computes component n of each NB x NB product from its rows of the stored
-// factors; the lanes of a column sit in one warp and meet at __syncwarp between the steps); the
-// other blocks take one vertical facet per thread (NB x NB block Jacobi).
+// couplings of a row inside D. Two launches per sweep. Part 1, one thread per facet (all facets,
+// as parallel as the S apply): the residual rows r = b - (S - D) lam_in; on a vertical facet the
+// NB x NB block Jacobi step lam_out = keep lam_in + (omega D_F^-1) r at once, on a horizontal
+// facet r is parked in lam_out's rows (ZERO: vertical facets only, r = b). Part 2, the line
+// solves: each column's r staged in shared memory, the block Thomas recurrences with LPC lanes
+// per column (lane n < NB computes component n of each NB x NB product from its rows of the
+// stored factors; the lanes of a column sit in one warp and meet at __syncwarp between the
+// steps), lam_out = keep lam_in + omega (S^zz_c)^-1 r.
+template <int P, bool ZERO>
+__global__ void __launch_bounds__(kRedThreads)
+    ho_sweep_rows_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, const double *__restrict__ hw,
+                         const double *__restrict__ b, const double *__restrict__ lam_in,
+                         double *__restrict__ lam_out, double keep) {
+  constexpr int NB = Ho<P>::NB;
+  const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (F >= (ZERO ? g.nhf : g.nhf + g.nzf)) return;
+  const int64_t r0 = (int64_t)NB * F;
+  double acc[NB];
+#pragma unroll
+  for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + r0 + n);
+  if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
+  if (F < g.nhf) {
+    for (int n = 0; n < NB; ++n) {
+      double v = ZERO ? 0.0 : keep * lam_in[r0 + n];
+#pragma unroll
+      for (int m = 0; m < NB; ++m) v = fma(hw[(int64_t)(NB * n + m) * g.nhf + F], acc[m], v);
+      lam_out[r0 + n] = v;
+    }
+  } else {
+#pragma unroll
+    for (int n = 0; n < NB; ++n) lam_out[r0 + n] = acc[n];
+  }
+}
+
+// Part 2; r is read from src (lam_out after part 1, b for a sweep from zero)
 template <int P, bool ZERO>
 __global__ void __launch_bounds__(128)
-    ho_sweep_kernel(const HoGeo g, int64_t T, int cpb, int nzb, const double *__restrict__ S,
-                    const double *__restrict__ hw, const double *__restrict__ zf, const double *__restrict__ b,
-                    const double *__restrict__ lam_in, double *__restrict__ lam_out, double keep) {
+    ho_sweep_lines_kernel(const HoGeo g, int cpb, const double *__restrict__ zf, const double *src,
+                          const double *__restrict__ lam_in, double *lam_out, double keep) {
   using H = Ho<P>;
   constexpr int NB = H::NB, NB2 = NB * NB, LPC = H::LPC;
   extern __shared__ double sr[];   // [cpb][L+1][NB]
   const int L1 = g.L + 1;
-  if ((int)blockIdx.x < nzb) {
-    const int c0 = blockIdx.x * cpb, nc = min(cpb, g.ncol - c0);
-    for (int i = threadIdx.x; i < nc * L1; i += blockDim.x) {
-      const int64_t F = g.nhf + (int64_t)c0 * L1 + i;
-      double acc[NB];
+  const int c0 = blockIdx.x * cpb, nc = min(cpb, g.ncol - c0);
+  const int64_t base = g.NH + (int64_t)NB * c0 * L1;
+  for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) sr[i] = src[base + i];
+  __syncthreads();
+  const int cc = threadIdx.x / LPC, n = threadIdx.x % LPC;
+  const unsigned grp = ((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1));   // this column's lanes
+  if (cc < nc) {
+    double *r = sr + NB * cc * L1;
+    const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + NB * n;   // this lane's factor rows
+    const bool act = n < NB;
+    // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r; the next level's
+    // factor rows are loaded one step ahead (the serial recurrence waits on nothing else)
+    double fa[NB], fb[NB];
+    if (act) {
 #pragma unroll
-      for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + (int64_t)NB * F + n);
-      if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
-#pragma unroll
-      for (int n = 0; n < NB; ++n) sr[NB * i + n] = acc[n];
+      for (int m = 0; m < NB; ++m) { fa[m] = __ldg(f0 + m); fb[m] = __ldg(f0 + NB2 + m); }
     }
-    __syncthreads();
-    const int cc = threadIdx.x / LPC, n = threadIdx.x % LPC;
-    const unsigned grp = ((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1));   // this column's lanes
-    if (cc < nc) {
-      double *r = sr + NB * cc * L1;
-      const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1);
-      // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r
-      for (int k = 0; k < L1; ++k) {
-        const double *f = f0 + 3 * NB2 * k;
-        double v = 0.0;
-        if (n < NB) {
-          for (int m = 0; m < NB; ++m) v = fma(__ldg(f + NB * n + m), r[NB * k + m], v);
-          if (k > 0)
-            for (int m = 0; m < NB; ++m) v = fma(-__ldg(f + NB2 + NB * n + m), r[NB * (k - 1) + m], v);
-        }
-        __syncwarp(grp);
-        if (n < NB) r[NB * k + n] = v;
-        __syncwarp(grp);
+    for (int k = 0; k < L1; ++k) {
+      double na[NB], nb[NB];
+      if (act && k + 1 < L1) {
+        const double *f = f0 + 3 * NB2 * (k + 1);
+#pragma unroll
+        for (int m = 0; m < NB; ++m) { na[m] = __ldg(f + m); nb[m] = __ldg(f + NB2 + m); }
       }
-      // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y (row k + 1 is not written
-      // in this step, row k only by its own lane)
-      for (int k = L1 - 2; k >= 0; --k) {
-        const double *f = f0 + 3 * NB2 * k;
-        if (n < NB) {
-          double v = r[NB * k + n];
-          for (int m = 0; m < NB; ++m) v = fma(-__ldg(f + 2 * NB2 + NB * n + m), r[NB * (k + 1) + m], v);
-          r[NB * k + n] = v;
+      double v = 0.0, u = 0.0;
+      if (act) {
+#pragma unroll
+        for (int m = 0; m < NB; ++m) v = fma(fa[m], r[NB * k + m], v);
+        if (k > 0) {
+#pragma unroll
+          for (int m = 0; m < NB; ++m) u = fma(-fb[m], r[NB * (k - 1) + m], u);
         }
-        __syncwarp(grp);
       }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) {
-      const int64_t row = g.NH + (int64_t)NB * c0 * L1 + i;
-      lam_out[row] = ZERO ? sr[i] : fma(keep, lam_in[row], sr[i]);
-    }
-  } else {
-    const int64_t F = (int64_t)(blockIdx.x - nzb) * blockDim.x + threadIdx.x;
-    if (F >= g.nhf) return;
-    double acc[NB];
+      __syncwarp(grp);
+      if (act) r[NB * k + n] = v + u;
+      __syncwarp(grp);
 #pragma unroll
-    for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + (int64_t)NB * F + n);
-    if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
-    for (int n = 0; n < NB; ++n) {
-      double v = ZERO ? 0.0 : keep * lam_in[(int64_t)NB * F + n];
+      for (int m = 0; m < NB; ++m) { fa[m] = na[m]; fb[m] = nb[m]; }
+    }
+    // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y (row k + 1 is not written in
+    // this step, row k only by its own lane); G_k^-1 U_k one step ahead as well
+    if (act && L1 >= 2) {
+      const double *f = f0 + 3 * NB2 * (L1 - 2) + 2 * NB2;
 #pragma unroll
-      for (int m = 0; m < NB; ++m) v = fma(hw[(int64_t)(NB * n + m) * g.nhf + F], acc[m], v);
-      lam_out[(int64_t)NB * F + n] = v;
+      for (int m = 0; m < NB; ++m) fa[m] = __ldg(f + m);
+    }
+    for (int k = L1 - 2; k >= 0; --k) {
+      double na[NB];
+      if (act && k > 0) {
+        const double *f = f0 + 3 * NB2 * (k - 1) + 2 * NB2;
+#pragma unroll
+        for (int m = 0; m < NB; ++m) na[m] = __ldg(f + m);
+      }
+      if (act) {
+        double v = r[NB * k + n];
+#pragma unroll
+        for (int m = 0; m < NB; ++m) v = fma(-fa[m], r[NB * (k + 1) + m], v);
+        r[NB * k + n] = v;
+      }
+      __syncwarp(grp);
+#pragma unroll
+      for (int m = 0; m < NB; ++m) fa[m] = na[m];
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x)
+    lam_out[base + i] = ZERO ? sr[i] : fma(keep, lam_in[base + i], sr[i]);
 }
 
 // R = b - S lam (Algorithm 2 line 3), one thread per facet. ZSWEEP: lam is one sweep from zero,
@@ -1054,17 +1089,19 @@ static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_o
   using H = Ho<P>;
   const HoData &h = c->ho;
   const HoGeo g = ho_geo<P>(c);
-  // columns per block: 128 / LPC, and the block's residual rows (NB (L + 1) doubles per column)
-  // within 48 KB
+  // columns per block of the line part: 128 / LPC, and the block's rows (NB (L + 1) doubles per
+  // column) within 48 KB
   const int cap = (int)((48 * 1024) / (sizeof(double) * H::NB * (g.L + 1)));
   if (cap < 1) return fail(c, HMG_ERR_INVALID_ARG, "too many layers for the degree-p line smoother");
   const int cpb = cap < 128 / H::LPC ? cap : 128 / H::LPC;
-  const int nzb = (g.ncol + cpb - 1) / cpb;
-  const unsigned nhb = grid_for(g.nhf, 128);
+  const unsigned nzb = (unsigned)((g.ncol + cpb - 1) / cpb);
   const size_t smem = sizeof(double) * H::NB * cpb * (g.L + 1);
-  Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
-  ho_sweep_kernel<P, ZERO><<<nzb + nhb, 128, smem, c->stream>>>(g, h.T, cpb, nzb, h.S, h.hw, h.zf, b, lam_in,
-                                                                 lam_out, 1.0 - h.factor_omega);
+  const double keep = 1.0 - h.factor_omega;
+  Prof prof(c, ZERO ? kCompPresmooth : kCompSweep, 2);
+  ho_sweep_rows_kernel<P, ZERO><<<grid_for(ZERO ? g.nhf : g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
+      g, h.T, h.S, h.hw, b, lam_in, lam_out, keep);
+  ho_sweep_lines_kernel<P, ZERO><<<nzb, 128, smem, c->stream>>>(g, cpb, h.zf, ZERO ? b : lam_out, lam_in, lam_out,
+                                                                keep);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
