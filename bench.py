@@ -1068,6 +1068,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_configs:
         import torch
         out["configs"] = run_configs(args, torch.cuda.current_stream(), model, lam_host)
+        # the batch's rate of (iterations x trace unknowns) per second against the single C96 solve
+        # in the same precision: how much of the one big solve's efficiency 64 small ones keep
+        b, mx = out["configs"].get("4_batch64_mixed") or {}, (out.get("variants") or {}).get("mixed_bicgstab_vcycle")
+        if b.get("iterations_x_unknowns_per_s") and mx and mx.get("ms_per_solve"):
+            single = mx["iterations"] * out["config"]["ntrace"] / (mx["ms_per_solve"] / 1e3)
+            b["per_iteration_rate_vs_single_c96_mixed"] = round(b["iterations_x_unknowns_per_s"] / single, 4)
     if child is not None:
         r, fwd = finish_oracle_child(child, lam_host, args.workload)
         if fwd is None:
