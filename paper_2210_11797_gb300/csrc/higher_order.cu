@@ -604,7 +604,8 @@ __global__ void __launch_bounds__(32 * kHoFacWarps)
 
 // Block Thomas factors of each column's block-tridiagonal S^zz (blocks D_k, L_k = coupling of
 // facet k to k - 1, U_k to k + 1): G_0 = D_0, G_k = D_k - L_k G_{k-1}^-1 U_{k-1}; stored per
-// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([nzf][3 NB^2]), so that
+// horizontal facet: omega G_k^-1, G_k^-1 L_k, G_k^-1 U_k ([nzf][3][NB][NB], each transposed: entry
+// (n, m) at m NB + n, so that the NB lanes of a column read one contiguous run per m), so that
 // omega (S^zz)^-1 r is y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, x_k = y_k - (G_k^-1 U_k) x_{k+1}.
 // Slots: the cell above (c, k) is A for k < L: its bottom (face 4) is this facet, its top (face 5)
 // facet k + 1; the cell below (c, k - 1) is B, its bottom facet k - 1. The lid row's A is the
@@ -649,7 +650,7 @@ __global__ void __launch_bounds__(32 * kHoFacWarps)
       __syncwarp();
     }
     if (!warp_gauss_jordan<NB>(W, lane)) ok = false;
-    double *o = zf + 3 * NB2 * F;   // facet-major: 3 NB^2 contiguous factors
+    double *o = zf + 3 * NB2 * F;   // facet-major: 3 NB^2 contiguous factors, each matrix transposed
     for (int e = lane; e < NB2; e += 32) {
       const int n = e / NB, m = e - n * NB;
       double sl = 0.0, su = 0.0;
@@ -657,12 +658,11 @@ __global__ void __launch_bounds__(32 * kHoFacWarps)
         sl = fma(W[n * W2 + NB + j], Lk[j * NB + m], sl);
         su = fma(W[n * W2 + NB + j], U[j * NB + m], su);
       }
-      o[e] = omega * W[n * W2 + NB + m];
-      o[NB2 + e] = sl;
-      o[2 * NB2 + e] = su;
+      o[m * NB + n] = omega * W[n * W2 + NB + m];
+      o[NB2 + m * NB + n] = sl;
+      o[2 * NB2 + m * NB + n] = su;
+      GU[e] = su;   // (row-major, for the next level's G; nothing reads GU in this loop)
     }
-    __syncwarp();
-    for (int e = lane; e < NB2; e += 32) GU[e] = o[2 * NB2 + e];
     __syncwarp();
   }
   if (!ok && lane == 0) atomicExch(singular, 1);
@@ -814,21 +814,21 @@ __global__ void __launch_bounds__(128)
   const unsigned grp = ((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1));   // this column's lanes
   if (cc < nc) {
     double *r = sr + NB * cc * L1;
-    const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + NB * n;   // this lane's factor rows
+    const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + n;   // this lane's rows (transposed)
     const bool act = n < NB;
     // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r; the next level's
     // factor rows are loaded one step ahead (the serial recurrence waits on nothing else)
     double fa[NB], fb[NB];
     if (act) {
 #pragma unroll
-      for (int m = 0; m < NB; ++m) { fa[m] = __ldg(f0 + m); fb[m] = __ldg(f0 + NB2 + m); }
+      for (int m = 0; m < NB; ++m) { fa[m] = __ldg(f0 + NB * m); fb[m] = __ldg(f0 + NB2 + NB * m); }
     }
     for (int k = 0; k < L1; ++k) {
       double na[NB], nb[NB];
       if (act && k + 1 < L1) {
         const double *f = f0 + 3 * NB2 * (k + 1);
 #pragma unroll
-        for (int m = 0; m < NB; ++m) { na[m] = __ldg(f + m); nb[m] = __ldg(f + NB2 + m); }
+        for (int m = 0; m < NB; ++m) { na[m] = __ldg(f + NB * m); nb[m] = __ldg(f + NB2 + NB * m); }
       }
       double v = 0.0, u = 0.0;
       if (act) {
@@ -850,14 +850,14 @@ __global__ void __launch_bounds__(128)
     if (act && L1 >= 2) {
       const double *f = f0 + 3 * NB2 * (L1 - 2) + 2 * NB2;
 #pragma unroll
-      for (int m = 0; m < NB; ++m) fa[m] = __ldg(f + m);
+      for (int m = 0; m < NB; ++m) fa[m] = __ldg(f + NB * m);
     }
     for (int k = L1 - 2; k >= 0; --k) {
       double na[NB];
       if (act && k > 0) {
         const double *f = f0 + 3 * NB2 * (k - 1) + 2 * NB2;
 #pragma unroll
-        for (int m = 0; m < NB; ++m) na[m] = __ldg(f + m);
+        for (int m = 0; m < NB; ++m) na[m] = __ldg(f + NB * m);
       }
       if (act) {
         double v = r[NB * k + n];

@@ -93,7 +93,7 @@ struct HoData {
   double *S = nullptr;         // [2 NF][T] two cells x NF facet-dof coefficients per row
   double *Ainv = nullptr;      // [ncell][N][N] A_K^-1
   double *hw = nullptr;        // [NB^2][vertical facets] omega (facet block of S)^-1
-  double *zf = nullptr;        // [horizontal facets][3 NB^2] block Thomas factors of S^zz
+  double *zf = nullptr;        // [horizontal facets][3][NB][NB] block Thomas factors of S^zz (transposed)
   double *gamma = nullptr;     // [ncell] Gamma of Eq. scaling_matrix
   double *m = nullptr;         // [ncell] sigma |K|_1 = (H 1)_K
   int8_t *own = nullptr;       // [ncol][4] 1 where the column owns the edge of its face
