@@ -42,9 +42,11 @@ struct Ho {
   // reference tables: velocity values, pressure values, weights, points, G, facet weights
   static constexpr int TV = 0, TPHI = TV + Q * NU, TW = TPHI + Q * NP, TX = TW + Q, TG = TX + 3 * Q,
                        TC = TG + NU * NP, TAB = TC + NB;
-  // the sweep's line part: lanes per column (a group of LPC lanes of one warp; lane n < NB
-  // computes component n of each block product)
-  static constexpr int LPC = P == 1 ? 4 : 16;
+  // the sweep's line part: lanes per column (a group of LPC >= NB lanes of one warp; lane n < NB
+  // computes component n of each block product) and columns per warp (p = 2: three groups of
+  // nine, five lanes idle)
+  static constexpr int LPC = P == 1 ? 4 : (P == 2 ? 9 : 16);
+  static constexpr int CPW = 32 / LPC;
 };
 
 // ---- reference tables, formed on the host ---------------------------------------------------
@@ -810,8 +812,9 @@ __global__ void __launch_bounds__(128)
   const int64_t base = g.NH + (int64_t)NB * c0 * L1;
   for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) sr[i] = src[base + i];
   __syncthreads();
-  const int cc = threadIdx.x / LPC, n = threadIdx.x % LPC;
-  const unsigned grp = ((1u << LPC) - 1u) << ((threadIdx.x & 31) & ~(LPC - 1));   // this column's lanes
+  const int lane = threadIdx.x & 31, gw = lane / LPC;   // the lane's group within its warp
+  const int cc = gw < H::CPW ? (threadIdx.x >> 5) * H::CPW + gw : cpb, n = lane - gw * LPC;
+  const unsigned grp = ((1u << LPC) - 1u) << (gw * LPC);   // this column's lanes
   if (cc < nc) {
     double *r = sr + NB * cc * L1;
     const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + n;   // this lane's rows (transposed)
@@ -1089,11 +1092,11 @@ static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_o
   using H = Ho<P>;
   const HoData &h = c->ho;
   const HoGeo g = ho_geo<P>(c);
-  // columns per block of the line part: 128 / LPC, and the block's rows (NB (L + 1) doubles per
-  // column) within 48 KB
+  // columns per block of the line part: 4 warps of CPW columns, and the block's rows
+  // (NB (L + 1) doubles per column) within 48 KB
   const int cap = (int)((48 * 1024) / (sizeof(double) * H::NB * (g.L + 1)));
   if (cap < 1) return fail(c, HMG_ERR_INVALID_ARG, "too many layers for the degree-p line smoother");
-  const int cpb = cap < 128 / H::LPC ? cap : 128 / H::LPC;
+  const int cpb = cap < 4 * H::CPW ? cap : 4 * H::CPW;
   const unsigned nzb = (unsigned)((g.ncol + cpb - 1) / cpb);
   const size_t smem = sizeof(double) * H::NB * cpb * (g.L + 1);
   const double keep = 1.0 - h.factor_omega;
