@@ -803,7 +803,7 @@ def degree_bytes(mesh, p):
     return 8 * (coeffs + 2 * (rows_h + rows_z)) + 4 * (8 * nedge + 4 * ncol) + 4 * ncol
 
 
-def degree_solves(args, stream, steps, p, nlev=32):
+def degree_solves(args, stream, steps, p, nlev=32, n=None):
     """Row f4 measured: the constant-coefficient Helmholtz problem on an n x n x nlev periodic
     box (c dt = 0.05, 4 multigrid levels) at degree p (n = 128, 88, 64 for p = 1, 2, 3: about the
     same number of trace unknowns), BiCGStab under Algorithm 2 to 1e-6 with a seeded N(0,1)
@@ -812,8 +812,9 @@ def degree_solves(args, stream, steps, p, nlev=32):
     import torch
     from paper_2210_11797_gb300 import inputs as I
     from paper_2210_11797_gb300.hmg import Solver
-    n = DEGREE_MESH[p]
-    w = I.planar_helmholtz(n=n, nlev=nlev, nmg=4, tol=1e-6)
+    n = n or DEGREE_MESH[p]
+    nmg = 4 if n % 8 == 0 else (2 if n % 2 == 0 else 1)   # horizontal coarsening by 2 per level
+    w = I.planar_helmholtz(n=n, nlev=nlev, nmg=nmg, tol=1e-6)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s = Solver(w.hier, w.coeffs, tol=1e-6, degree=p)
@@ -1012,6 +1013,9 @@ def main():
                     help="only the degree-p workload (Helmholtz plane n x n x 32, n = 128, 88, 64 for "
                          "p = 1, 2, 3) as a JSON line; the profiler range is its host-driven profiled solve")
     ap.add_argument("--degree1", action="store_true", help="the same as --degree 1")
+    ap.add_argument("--degree-mesh", default=None,
+                    help="n,nlev: the degree-p plane's size in --degree mode (default: the bench workload; "
+                         "smaller planes for full ncu captures)")
     ap.add_argument("--_oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--_outdir", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1052,8 +1056,9 @@ def main():
     if args.degree1 or args.degree:
         if rank == 0:
             import torch
+            n, nlev = (int(v) for v in args.degree_mesh.split(",")) if args.degree_mesh else (None, 32)
             print(json.dumps(degree_solves(args, torch.cuda.current_stream(), max(3, min(args.steps, 5)),
-                                           args.degree or 1)))
+                                           args.degree or 1, nlev=nlev, n=n)))
         return
     if args.workload.startswith("batch"):
         out = run_batched(args, rank, world)
