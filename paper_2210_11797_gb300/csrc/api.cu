@@ -644,16 +644,17 @@ int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, i
   auto ok = [](int32_t cpb, int32_t thr) { return cpb >= 0 && cpb <= 64 && (thr == 0 || thr == 128 || thr == 256); };
   if (!ok(sweep[0], sweep[1])) return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
   for (int l = 0; l < nmg; ++l)
-    if (!ok(mg[2 * l], mg[2 * l + 1])) return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
+    if (!ok(mg[2 * l], mg[2 * l + 1]) && !(mg[2 * l] == -1 && c->lv[l].nlev <= 128))
+      return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
   drop_graph(c);   // captured launches carry the old shapes
   for (int p = 0; p < 2; ++p) {   // the same shapes for the FP64 and FP32 kernels
     c->tune_sweep_cpb[p] = sweep[0];
     c->tune_sweep_threads[p] = sweep[1];
   }
   for (int l = 0; l < nmg; ++l) {
-    for (int p = 0; p < 2; ++p) {
-      c->tune_mg_cpb[p][l] = mg[2 * l];
-      c->tune_mg_threads[p][l] = mg[2 * l + 1];
+    for (int p = 0; p < 2; ++p) {   // -1: the FP32 kernels' warp-per-column form, the FP64 default
+      c->tune_mg_cpb[p][l] = mg[2 * l] == -1 ? (p == 1 ? -1 : 0) : mg[2 * l];
+      c->tune_mg_threads[p][l] = mg[2 * l] == -1 ? 0 : mg[2 * l + 1];
     }
   }
   return HMG_OK;

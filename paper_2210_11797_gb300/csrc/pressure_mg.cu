@@ -231,6 +231,100 @@ __global__ void __launch_bounds__(256)
   smooth_block<T, MODE, false>(a, H, hw, hl, hcp, b, x, x_out, blockIdx.x, smem_raw);
 }
 
+// One column of the block-Jacobi smoother by one warp, the FP32 preconditioner's latency-bound
+// form: lane j holds layers j M .. j M + M - 1 (M = 1 for up to 32 layers). The Thomas
+// recurrences y_k = s_k - l_k y_{k-1} (s = omega r / pivot) and x_k = y_k - u_k x_{k+1} are
+// chains of affine maps; their compositions over the lanes come from a warp scan (five shuffle
+// steps each way), then each lane replays its own layers from the value it receives. No shared
+// memory and no block barrier; in FP32 the scan's extra multiply-adds cost nothing next to the
+// loads. x_out = src.out(omega H_z^-1 src.r), as smooth_block_src.
+template <typename T, int M, typename Src>
+__device__ __forceinline__ void smooth_warp_src(const MGArgs &a, const T *__restrict__ hw, const T *__restrict__ hl,
+                                                const T *__restrict__ hcp, const Src &src, T *__restrict__ x_out,
+                                                int c) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)c * a.L;
+  T s[M], lo[M], up[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int k = lane * M + i;
+    s[i] = lo[i] = up[i] = (T)0;
+    if (k < a.L) {
+      const int64_t K = base + k;
+      s[i] = src.r(a, c, k, K) * __ldg(hw + K);
+      if (k > 0) lo[i] = __ldg(hl + K);
+      if (k < a.L - 1) up[i] = __ldg(hcp + K);
+    }
+  }
+  // forward: the lane's map y_in -> y (A + Mf y_in), an inclusive scan over the lanes below,
+  // then the lane's layers from the previous lane's last y (0 before layer 0, whose lo is 0)
+  T A = (T)0, Mf = (T)1;
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+    if (lane * M + i < a.L) {
+      A = fma(-lo[i], A, s[i]);
+      Mf = -lo[i] * Mf;
+    }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T A2 = __shfl_up_sync(kAll, A, off), M2 = __shfl_up_sync(kAll, Mf, off);
+    if (lane >= off) {
+      A = fma(Mf, A2, A);
+      Mf *= M2;
+    }
+  }
+  T y = __shfl_up_sync(kAll, A, 1);
+  if (lane == 0) y = (T)0;
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+    if (lane * M + i < a.L) {
+      y = fma(-lo[i], y, s[i]);
+      s[i] = y;
+    }
+  // backward: the same with x_k = y_k - u_k x_{k+1} from the lanes above (the last layer's up
+  // is 0)
+  A = (T)0;
+  Mf = (T)1;
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i)
+    if (lane * M + i < a.L) {
+      A = fma(-up[i], A, s[i]);
+      Mf = -up[i] * Mf;
+    }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T A2 = __shfl_down_sync(kAll, A, off), M2 = __shfl_down_sync(kAll, Mf, off);
+    if (lane + off < 32) {
+      A = fma(Mf, A2, A);
+      Mf *= M2;
+    }
+  }
+  T xk = __shfl_down_sync(kAll, A, 1);
+  if (lane == 31) xk = (T)0;
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i)
+    if (lane * M + i < a.L) {
+      xk = fma(-up[i], xk, s[i]);
+      s[i] = xk;
+    }
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int k = lane * M + i;
+    if (k < a.L) x_out[base + k] = src.out(a, c, k, base + k, s[i]);
+  }
+}
+
+// One warp per column (whole warps leave together, so the shuffles see full warps).
+template <typename T, int M, typename Src>
+__global__ void __launch_bounds__(256)
+    mg_warp_kernel(const MGArgs a, const T *__restrict__ hw, const T *__restrict__ hl, const T *__restrict__ hcp,
+                   const Src src, T *__restrict__ x_out) {
+  const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (c >= a.ncol) return;
+  smooth_warp_src<T, M>(a, hw, hl, hcp, src, x_out, (int)c);
+}
+
 // x_out = x + P e: injection of the coarse-level correction e (prolongation, Sec. 2.3).
 template <typename T, bool COH>
 __device__ __forceinline__ void inject_cell(const T *__restrict__ x, const T *__restrict__ e,
@@ -480,10 +574,37 @@ static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int t
   return sh;
 }
 
+// The warp-per-column form serves the FP32 kernels of level l when the tuned (or given) columns
+// per block is -1 and the level has at most 128 layers.
+template <typename T>
+static bool warp_form(const Ctx *c, int l, int cpb_override = 0) {
+  if (sizeof(T) != 4 || c->lv[l].nlev > 128) return false;
+  return cpb_override == -1 || (cpb_override == 0 && c->tune_mg_cpb[1][l] == -1);
+}
+
+template <typename T, typename Src>
+static int launch_warp(Ctx *c, int l, const Src &src, T *out) {
+  const Level &lv = c->lv[l];
+  const MGArgs a = mg_args(c, l, 1);
+  const unsigned grid = grid_for((int64_t)lv.ncol * 32, 256);
+  const T *hw = Prec<T>::Hz_w(lv), *hl = Prec<T>::Hz_l(lv), *hcp = Prec<T>::Hz_cp(lv);
+  if (lv.nlev <= 32) mg_warp_kernel<T, 1, Src><<<grid, 256, 0, c->stream>>>(a, hw, hl, hcp, src, out);
+  else if (lv.nlev <= 64) mg_warp_kernel<T, 2, Src><<<grid, 256, 0, c->stream>>>(a, hw, hl, hcp, src, out);
+  else mg_warp_kernel<T, 4, Src><<<grid, 256, 0, c->stream>>>(a, hw, hl, hcp, src, out);
+  HMG_CUDA(c, cudaGetLastError());
+  return HMG_OK;
+}
+
 template <typename T, int MODE>
 static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0, int threads_override = 0) {
   const Level &lv = c->lv[l];
-  const SmoothShape sh = smooth_shape<T>(c, l, cpb_override, threads_override);
+  if constexpr (sizeof(T) == 4) {
+    if (warp_form<T>(c, l, cpb_override)) {
+      if (MODE == 0) return launch_warp<T>(c, l, SrcZero<T, false>{b}, out);
+      return launch_warp<T>(c, l, SrcIter<T, false>{Prec<T>::H(lv), b, x}, out);
+    }
+  }
+  const SmoothShape sh = smooth_shape<T>(c, l, cpb_override > 0 ? cpb_override : 0, threads_override);
   mg_smooth_kernel<T, MODE><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::H(lv), Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x, out);
   HMG_CUDA(c, cudaGetLastError());
@@ -495,6 +616,11 @@ static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_overrid
 template <typename T>
 static int restrict_smooth(Ctx *c, int l, const T *bf, const T *xf, T *out, bool zsweep) {
   const Level &fine = c->lv[l], &lv = c->lv[l + 1];
+  if constexpr (sizeof(T) == 4) {
+    if (warp_form<T>(c, l + 1))
+      return launch_warp<T>(c, l + 1, SrcRestrict<T>{mg_args(c, l), Prec<T>::H(fine), bf, xf, lv.children,
+                                                     static_cast<T *>(lv.vb), zsweep}, out);
+  }
   const SmoothShape sh = smooth_shape<T>(c, l + 1);
   mg_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), mg_args(c, l), Prec<T>::H(fine), bf, xf,
@@ -507,8 +633,12 @@ static int restrict_smooth(Ctx *c, int l, const T *bf, const T *xf, T *out, bool
 template <typename T>
 static int trace_restrict_smooth(Ctx *c, const T *R, T *cb, T *out) {
   const Level &lv = c->lv[0];
-  const SmoothShape sh = smooth_shape<T>(c, 0);
   const TraceDims d{lv.nlev, lv.nth, lv.ntrace};
+  if constexpr (sizeof(T) == 4) {
+    if (warp_form<T>(c, 0))
+      return launch_warp<T>(c, 0, SrcTraceRestrict<T>{R, Prec<T>::gamma(c), lv.col_edges, d, cb}, out);
+  }
+  const SmoothShape sh = smooth_shape<T>(c, 0);
   mg_trace_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), R, Prec<T>::gamma(c), lv.col_edges, d,
       cb, out);
@@ -520,6 +650,9 @@ static int trace_restrict_smooth(Ctx *c, const T *R, T *cb, T *out) {
 template <typename T>
 static int inject_smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
   const Level &lv = c->lv[l];
+  if constexpr (sizeof(T) == 4) {
+    if (warp_form<T>(c, l)) return launch_warp<T>(c, l, SrcInject<T>{Prec<T>::H(lv), b, x, e, lv.parent}, out);
+  }
   const SmoothShape sh = smooth_shape<T>(c, l);
   mg_inject_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::H(lv), Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x, e, lv.parent, out);
