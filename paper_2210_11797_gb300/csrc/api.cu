@@ -642,14 +642,15 @@ int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, i
   if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
   auto ok = [](int32_t cpb, int32_t thr) { return cpb >= 0 && cpb <= 64 && (thr == 0 || thr == 128 || thr == 256); };
-  if (!ok(sweep[0], sweep[1])) return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
+  if (!ok(sweep[0], sweep[1]) && !(sweep[0] == -1 && c->lv[0].nlev + 1 <= 128))
+    return fail(c, HMG_ERR_INVALID_ARG, "bad sweep launch shape");
   for (int l = 0; l < nmg; ++l)
     if (!ok(mg[2 * l], mg[2 * l + 1]) && !(mg[2 * l] == -1 && c->lv[l].nlev <= 128))
       return fail(c, HMG_ERR_INVALID_ARG, "bad smoother launch shape");
   drop_graph(c);   // captured launches carry the old shapes
-  for (int p = 0; p < 2; ++p) {   // the same shapes for the FP64 and FP32 kernels
-    c->tune_sweep_cpb[p] = sweep[0];
-    c->tune_sweep_threads[p] = sweep[1];
+  for (int p = 0; p < 2; ++p) {   // the same shapes for the FP64 and FP32 kernels (-1: FP32 only)
+    c->tune_sweep_cpb[p] = sweep[0] == -1 ? (p == 1 ? -1 : 0) : sweep[0];
+    c->tune_sweep_threads[p] = sweep[0] == -1 ? 0 : sweep[1];
   }
   for (int l = 0; l < nmg; ++l) {
     for (int p = 0; p < 2; ++p) {   // -1: the FP32 kernels' warp-per-column form, the FP64 default

@@ -266,6 +266,65 @@ __device__ __forceinline__ TA s_row_z_off(const TS *__restrict__ S, const TX *__
   return acc;
 }
 
+// A tridiagonal solve with precomputed Thomas factors by one warp (n <= 32 M rows; lane j holds
+// rows j M .. j M + M - 1): on entry s = the scaled right-hand side (r omega / pivot), lo the
+// sub-diagonal / pivot (0 on row 0), up the super-diagonal / pivot (0 on row n - 1); on return
+// s = the solution. The recurrences y_k = s_k - lo_k y_{k-1} and x_k = y_k - up_k x_{k+1} are
+// chains of affine maps v -> A + M v: each lane composes its own rows, a warp scan (five shuffle
+// steps) composes the lanes before it (after it, backwards), then the lane replays its rows from
+// the value it receives. About ten times the serial form's multiply-adds: for FP32 kernels.
+template <typename T, int M>
+__device__ __forceinline__ void warp_thomas(T (&s)[M], const T (&lo)[M], const T (&up)[M], int lane, int n) {
+  constexpr unsigned kAll = 0xffffffffu;
+  T A = (T)0, Mf = (T)1;
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+    if (lane * M + i < n) {
+      A = fma(-lo[i], A, s[i]);
+      Mf = -lo[i] * Mf;
+    }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T A2 = __shfl_up_sync(kAll, A, off), M2 = __shfl_up_sync(kAll, Mf, off);
+    if (lane >= off) {
+      A = fma(Mf, A2, A);
+      Mf *= M2;
+    }
+  }
+  T y = __shfl_up_sync(kAll, A, 1);
+  if (lane == 0) y = (T)0;
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+    if (lane * M + i < n) {
+      y = fma(-lo[i], y, s[i]);
+      s[i] = y;
+    }
+  A = (T)0;
+  Mf = (T)1;
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i)
+    if (lane * M + i < n) {
+      A = fma(-up[i], A, s[i]);
+      Mf = -up[i] * Mf;
+    }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const T A2 = __shfl_down_sync(kAll, A, off), M2 = __shfl_down_sync(kAll, Mf, off);
+    if (lane + off < 32) {
+      A = fma(Mf, A2, A);
+      Mf *= M2;
+    }
+  }
+  T x = __shfl_down_sync(kAll, A, 1);
+  if (lane == 31) x = (T)0;
+#pragma unroll
+  for (int i = M - 1; i >= 0; --i)
+    if (lane * M + i < n) {
+      x = fma(-up[i], x, s[i]);
+      s[i] = x;
+    }
+}
+
 template <typename TS, typename TX, typename TA, bool NEG>
 __device__ __forceinline__ TA s_row(const TS *__restrict__ S, const TX *__restrict__ x,
                                     const int32_t *__restrict__ stencil,

@@ -232,17 +232,14 @@ __global__ void __launch_bounds__(256)
 }
 
 // One column of the block-Jacobi smoother by one warp, the FP32 preconditioner's latency-bound
-// form: lane j holds layers j M .. j M + M - 1 (M = 1 for up to 32 layers). The Thomas
-// recurrences y_k = s_k - l_k y_{k-1} (s = omega r / pivot) and x_k = y_k - u_k x_{k+1} are
-// chains of affine maps; their compositions over the lanes come from a warp scan (five shuffle
-// steps each way), then each lane replays its own layers from the value it receives. No shared
-// memory and no block barrier; in FP32 the scan's extra multiply-adds cost nothing next to the
-// loads. x_out = src.out(omega H_z^-1 src.r), as smooth_block_src.
+// form: lane j holds layers j M .. j M + M - 1 (M = 1 for up to 32 layers) and the Thomas
+// recurrences run as a warp scan (warp_thomas). No shared memory and no block barrier; in FP32
+// the scan's extra multiply-adds cost nothing next to the loads. x_out = src.out(omega H_z^-1
+// src.r), as smooth_block_src.
 template <typename T, int M, typename Src>
 __device__ __forceinline__ void smooth_warp_src(const MGArgs &a, const T *__restrict__ hw, const T *__restrict__ hl,
                                                 const T *__restrict__ hcp, const Src &src, T *__restrict__ x_out,
                                                 int c) {
-  constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)c * a.L;
   T s[M], lo[M], up[M];
@@ -257,57 +254,7 @@ __device__ __forceinline__ void smooth_warp_src(const MGArgs &a, const T *__rest
       if (k < a.L - 1) up[i] = __ldg(hcp + K);
     }
   }
-  // forward: the lane's map y_in -> y (A + Mf y_in), an inclusive scan over the lanes below,
-  // then the lane's layers from the previous lane's last y (0 before layer 0, whose lo is 0)
-  T A = (T)0, Mf = (T)1;
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-    if (lane * M + i < a.L) {
-      A = fma(-lo[i], A, s[i]);
-      Mf = -lo[i] * Mf;
-    }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const T A2 = __shfl_up_sync(kAll, A, off), M2 = __shfl_up_sync(kAll, Mf, off);
-    if (lane >= off) {
-      A = fma(Mf, A2, A);
-      Mf *= M2;
-    }
-  }
-  T y = __shfl_up_sync(kAll, A, 1);
-  if (lane == 0) y = (T)0;
-#pragma unroll
-  for (int i = 0; i < M; ++i)
-    if (lane * M + i < a.L) {
-      y = fma(-lo[i], y, s[i]);
-      s[i] = y;
-    }
-  // backward: the same with x_k = y_k - u_k x_{k+1} from the lanes above (the last layer's up
-  // is 0)
-  A = (T)0;
-  Mf = (T)1;
-#pragma unroll
-  for (int i = M - 1; i >= 0; --i)
-    if (lane * M + i < a.L) {
-      A = fma(-up[i], A, s[i]);
-      Mf = -up[i] * Mf;
-    }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const T A2 = __shfl_down_sync(kAll, A, off), M2 = __shfl_down_sync(kAll, Mf, off);
-    if (lane + off < 32) {
-      A = fma(Mf, A2, A);
-      Mf *= M2;
-    }
-  }
-  T xk = __shfl_down_sync(kAll, A, 1);
-  if (lane == 31) xk = (T)0;
-#pragma unroll
-  for (int i = M - 1; i >= 0; --i)
-    if (lane * M + i < a.L) {
-      xk = fma(-up[i], xk, s[i]);
-      s[i] = xk;
-    }
+  warp_thomas<T, M>(s, lo, up, lane, a.L);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const int k = lane * M + i;

@@ -262,6 +262,53 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same sweep with one warp per lambda^z column (the FP32 preconditioner's form, columns per
+// block -1; L + 1 <= 32 M rows): lane j holds rows j M .. j M + M - 1, whose residuals it
+// computes, and the Thomas recurrences run as a warp scan (warp_thomas); 8 columns per block of
+// 256 threads. The remaining blocks take lambda^h rows as in sweep_kernel.
+template <typename T, typename Tb, typename Tout, bool ZERO, int M>
+__global__ void __launch_bounds__(256)
+    sweep_warp_kernel(const SweepArgs a, const T *__restrict__ S, const T *__restrict__ zw,
+                      const T *__restrict__ zl, const T *__restrict__ zcp, const T *__restrict__ hw,
+                      const Tb *__restrict__ b, const T *__restrict__ lam_in, Tout *__restrict__ lam_out) {
+  const TraceDims &d = a.d;
+  if ((int)blockIdx.x < a.nzb) {
+    const int64_t col = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (col >= a.ncol) return;   // whole warps
+    const int lane = threadIdx.x & 31, L1 = d.L + 1;
+    const int64_t base = d.NH + col * L1;
+    T s[M], lo[M], up[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int k = lane * M + i;
+      s[i] = lo[i] = up[i] = (T)0;
+      if (k < L1) {
+        const int64_t row = base + k;
+        T r = (T)__ldg(b + row);
+        if (!ZERO) r = s_row_z_off<T, T, T>(S, lam_in, a.col_edges, d, row, r);
+        s[i] = r * __ldg(zw + (row - d.NH));
+        if (k > 0) lo[i] = __ldg(zl + (row - d.NH));
+        if (k < L1 - 1) up[i] = __ldg(zcp + (row - d.NH));
+      }
+    }
+    warp_thomas<T, M>(s, lo, up, lane, L1);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int k = lane * M + i;
+      if (k < L1) {
+        const int64_t row = base + k;
+        lam_out[row] = (Tout)(ZERO ? s[i] : fma((T)a.keep, lam_in[row], s[i]));
+      }
+    }
+  } else {
+    const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
+    if (row >= d.NH) return;
+    T r = (T)__ldg(b + row);
+    if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
+    lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
+  }
+}
+
 // Columns per block of the sweep: at most 64, and the three shared-memory arrays of the
 // block's column rows within the default 48 KB (FP64).
 static int sweep_cpb_limit(int nlev) {
@@ -279,6 +326,28 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   const int cpb_max = sweep_cpb_limit(f.nlev);
   const int cpb_def = cpb_max < 32 ? cpb_max : 32;
   const int pm = sizeof(T) == 4 ? 1 : 0;   // FP32 preconditioner kernels have their own tuned shape
+  if constexpr (sizeof(T) == 4) {
+    // columns per block -1 (given or tuned): one warp per lambda^z column
+    if ((cpb_override == -1 || (cpb_override == 0 && c->tune_sweep_cpb[1] == -1)) && f.nlev + 1 <= 128) {
+      a.stencil = f.edge_stencil;
+      a.col_edges = f.col_edges;
+      a.keep = 1.0 - c->factor_omega;
+      a.cpb = 8;
+      a.nzb = (int)grid_for((int64_t)f.ncol * 32, 256);
+      const unsigned nhb = grid_for(f.nth, 256);
+      Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
+      const int L1 = f.nlev + 1;
+      auto go = [&](auto kern) {
+        kern<<<a.nzb + nhb, 256, 0, c->stream>>>(a, Prec<T>::S(c), Prec<T>::Sz_w(c), Prec<T>::Sz_l(c),
+                                                 Prec<T>::Sz_cp(c), Prec<T>::Sh_w(c), b, lam_in, lam_out);
+      };
+      if (L1 <= 32) go(sweep_warp_kernel<T, Tb, Tout, ZERO, 1>);
+      else if (L1 <= 64) go(sweep_warp_kernel<T, Tb, Tout, ZERO, 2>);
+      else go(sweep_warp_kernel<T, Tb, Tout, ZERO, 4>);
+      HMG_CUDA(c, cudaGetLastError());
+      return HMG_OK;
+    }
+  }
   a.cpb = cpb_override > 0 ? cpb_override : (c->tune_sweep_cpb[pm] > 0 ? c->tune_sweep_cpb[pm] : cpb_def);
   if (a.cpb > cpb_max) a.cpb = cpb_max;
   a.nzb = (f.ncol + a.cpb - 1) / a.cpb;
@@ -557,9 +626,9 @@ extern "C" int hmg_line_smooth_noalloc(hmg_ctx *ctx, const double *b, double *la
 // ---- launch-shape autotuning ---------------------------------------------------------------
 namespace hmg {
 
-// Average time of 5 full FP64 sweeps with `cpb` columns per z-block (work vectors as data).
-// Best-of-three average time of a full sweep with `cpb` columns per block, in FP64 or (fp32)
-// with the FP32 preconditioner's types (FP32 S and lambda in, FP64 b and lambda out).
+// Best-of-three average time of a full sweep with `cpb` columns per block (-1: one warp per
+// column, FP32 only), in FP64 or (fp32) with the FP32 preconditioner's types (FP32 S and
+// lambda in, FP64 b and lambda out); the work vectors serve as data.
 int time_sweep_cpb(Ctx *c, int cpb, int threads, int fp32, float *ms) {
   const int64_t T = c->lv[0].ntrace;
   double *b = static_cast<double *>(c->w1), *x = static_cast<double *>(c->w2), *y = static_cast<double *>(c->w3);
@@ -609,6 +678,10 @@ int autotune(Ctx *c) {
         if ((st = time_sweep_cpb(c, cand, thr, pm, &ms))) break;
         if (ms < best_ms) { best_ms = ms; best = cand; best_t = thr; }
       }
+    if (pm == 1 && !st && f.nlev + 1 <= 128) {   // FP32: one warp per column competes too
+      float ms = 0.f;
+      if (!(st = time_sweep_cpb(c, -1, 256, pm, &ms)) && ms < best_ms) { best_ms = ms; best = -1; best_t = 256; }
+    }
     if (!st) { c->tune_sweep_cpb[pm] = best; c->tune_sweep_threads[pm] = best_t; }
     for (int l = 0; l < c->nmg && !st; ++l) {
       const int mmax = mg_cpb_limit(c->lv[l].nlev);

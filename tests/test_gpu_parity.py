@@ -288,18 +288,18 @@ def test_fp32_preconditioner_against_the_fp64_oracle(name, bound):
 
 
 @pytest.mark.parametrize("name,bound", [("planar16", 1.5e-6), ("sphereC12L30", 6e-5)])
-def test_fp32_warp_smoother_against_the_fp64_oracle(name, bound):
-    """The FP32 pressure smoother as one warp per column (columns -1 in the launch shapes: the
-    Thomas recurrences as a warp scan of affine maps) inside one application of Algorithm 2:
-    within the same bound of the FP64 oracle as the block form, and within FP32 rounding
-    (amplified by the vertical conditioning) of the block form's result."""
+def test_fp32_warp_forms_against_the_fp64_oracle(name, bound):
+    """The FP32 line sweep and pressure smoother as one warp per column (columns -1 in the
+    launch shapes: the Thomas recurrences as a warp scan of affine maps) inside one application
+    of Algorithm 2: within the same bound of the FP64 oracle as the block forms, and within FP32
+    rounding (amplified by the vertical conditioning) of the block forms' result."""
     w, ora, gpu = _pair(name)
     r = ora.S @ np.random.default_rng(17).standard_normal(gpu.ntrace)
     sw, mg = gpu.launch_shapes()
     gpu.set_options(precision="mixed")
     try:
         base = _np(gpu.precond(_cuda(r)))
-        gpu.set_launch_shapes(sw, [(-1, 0)] * len(mg))
+        gpu.set_launch_shapes((-1, 0), [(-1, 0)] * len(mg))
         got = _np(gpu.precond(_cuda(r)))
     finally:
         gpu.set_launch_shapes(sw, mg)
@@ -312,10 +312,10 @@ def test_fp32_warp_smoother_against_the_fp64_oracle(name, bound):
 
 
 @pytest.mark.parametrize("nlev", [50, 70])
-def test_fp32_warp_smoother_on_tall_columns(nlev):
-    """Two and three layers per lane (50 and 70 layers, the batch's tallest columns): the warp
-    form's mixed-precision solve reaches the FP64 tolerance in the block form's iterations, and
-    one preconditioner application agrees with the block form's to FP32 accuracy."""
+def test_fp32_warp_forms_on_tall_columns(nlev):
+    """Two and three rows per lane (50 and 70 layers, the batch's tallest columns): the warp
+    forms' mixed-precision solve reaches the FP64 tolerance in the block forms' iterations, and
+    one preconditioner application agrees with the block forms' to FP32 accuracy."""
     from paper_2210_11797_gb300.hmg import Solver
     w = I.cubed_sphere(12, nlev, seed=5)
     gpu = Solver(w.hier, w.coeffs, tol=w.tol, precision="mixed")
@@ -325,7 +325,7 @@ def test_fp32_warp_smoother_on_tall_columns(nlev):
         sw, mg = gpu.launch_shapes()
         lam0, st0 = gpu.solve(Rub, Rpi)
         z0 = _np(gpu.precond(r))
-        gpu.set_launch_shapes(sw, [(-1, 0)] * len(mg))
+        gpu.set_launch_shapes((-1, 0), [(-1, 0)] * len(mg))
         lam1, st1 = gpu.solve(Rub, Rpi)
         z1 = _np(gpu.precond(r))
         assert st1["status"] == "ok" and abs(st1["iterations"] - st0["iterations"]) <= 1
