@@ -264,8 +264,8 @@ int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
                       const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats);
 
 /* Time the candidate launch shapes of the line sweep and of the pressure smoother on each
- * level (columns per thread block: 1-64; threads per block: 128 or 256; for the FP32
- * preconditioner's kernels also one warp per column, up to 128 rows per column) on this
+ * level (columns per thread block: 1-64; threads per block: 128 or 256; also one warp per
+ * column, up to 128 rows per column: the smoother in both precisions, the sweep in FP32) on this
  * context's mesh and keep the fastest; later launches of this context use them. Needs an assembled context; the sweep
  * timings overwrite the context's work vectors. */
 int hmg_autotune(hmg_ctx *ctx);
@@ -273,10 +273,10 @@ int hmg_autotune(hmg_ctx *ctx);
 /* Read / set the launch shapes of a context (host int32 arrays): sweep[2] = {columns per
  * block, threads per block} of the line sweep; mg[2 * nmg] = the same for the pressure
  * smoother on each level. 0 means the default (32 columns, 256 threads, within the shared
- * memory limit); columns -1 for the sweep or for a smoother level (at most 127 / 128 layers)
- * selects one warp per column for the FP32 preconditioner's kernels there, the FP64 kernels
- * taking the default (Thomas recurrences as a warp scan: the same iterate up to FP32 rounding
- * order); hmg_get_launch_shapes reports the FP64 shapes. hmg_set_launch_shapes rejects other columns
+ * memory limit); columns -1 selects one warp per column (Thomas recurrences as a warp scan:
+ * the same iterate up to rounding order): for a smoother level of at most 128 layers in both
+ * precisions, for the sweep (at most 127 layers) in the FP32 preconditioner's kernels only, the
+ * FP64 sweep taking the default; hmg_get_launch_shapes reports the FP64 shapes. hmg_set_launch_shapes rejects other columns
  * outside 1..64 and threads other than 0, 128 and 256. */
 int hmg_get_launch_shapes(hmg_ctx *ctx, int32_t *sweep, int32_t *mg, int32_t nmg);
 int hmg_set_launch_shapes(hmg_ctx *ctx, const int32_t *sweep, const int32_t *mg, int32_t nmg);

@@ -653,8 +653,8 @@ int hmg_set_launch_shapes(hmg_ctx *c, const int32_t *sweep, const int32_t *mg, i
     c->tune_sweep_threads[p] = sweep[0] == -1 ? 0 : sweep[1];
   }
   for (int l = 0; l < nmg; ++l) {
-    for (int p = 0; p < 2; ++p) {   // -1: the FP32 kernels' warp-per-column form, the FP64 default
-      c->tune_mg_cpb[p][l] = mg[2 * l] == -1 ? (p == 1 ? -1 : 0) : mg[2 * l];
+    for (int p = 0; p < 2; ++p) {   // -1: the warp-per-column form for both precisions
+      c->tune_mg_cpb[p][l] = mg[2 * l];
       c->tune_mg_threads[p][l] = mg[2 * l] == -1 ? 0 : mg[2 * l + 1];
     }
   }

@@ -521,18 +521,18 @@ static SmoothShape smooth_shape(const Ctx *c, int l, int cpb_override = 0, int t
   return sh;
 }
 
-// The warp-per-column form serves the FP32 kernels of level l when the tuned (or given) columns
-// per block is -1 and the level has at most 128 layers.
+// The warp-per-column form serves level l when the tuned (or given) columns per block of the
+// precision is -1 and the level has at most 128 layers.
 template <typename T>
 static bool warp_form(const Ctx *c, int l, int cpb_override = 0) {
-  if (sizeof(T) != 4 || c->lv[l].nlev > 128) return false;
-  return cpb_override == -1 || (cpb_override == 0 && c->tune_mg_cpb[1][l] == -1);
+  if (c->lv[l].nlev > 128) return false;
+  return cpb_override == -1 || (cpb_override == 0 && c->tune_mg_cpb[sizeof(T) == 4 ? 1 : 0][l] == -1);
 }
 
 template <typename T, typename Src>
 static int launch_warp(Ctx *c, int l, const Src &src, T *out) {
   const Level &lv = c->lv[l];
-  const MGArgs a = mg_args(c, l, 1);
+  const MGArgs a = mg_args(c, l, sizeof(T) == 4 ? 1 : 0);
   const unsigned grid = grid_for((int64_t)lv.ncol * 32, 256);
   const T *hw = Prec<T>::Hz_w(lv), *hl = Prec<T>::Hz_l(lv), *hcp = Prec<T>::Hz_cp(lv);
   if (lv.nlev <= 32) mg_warp_kernel<T, 1, Src><<<grid, 256, 0, c->stream>>>(a, hw, hl, hcp, src, out);
@@ -545,11 +545,9 @@ static int launch_warp(Ctx *c, int l, const Src &src, T *out) {
 template <typename T, int MODE>
 static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_override = 0, int threads_override = 0) {
   const Level &lv = c->lv[l];
-  if constexpr (sizeof(T) == 4) {
-    if (warp_form<T>(c, l, cpb_override)) {
-      if (MODE == 0) return launch_warp<T>(c, l, SrcZero<T, false>{b}, out);
-      return launch_warp<T>(c, l, SrcIter<T, false>{Prec<T>::H(lv), b, x}, out);
-    }
+  if (warp_form<T>(c, l, cpb_override)) {
+    if (MODE == 0) return launch_warp<T>(c, l, SrcZero<T, false>{b}, out);
+    return launch_warp<T>(c, l, SrcIter<T, false>{Prec<T>::H(lv), b, x}, out);
   }
   const SmoothShape sh = smooth_shape<T>(c, l, cpb_override > 0 ? cpb_override : 0, threads_override);
   mg_smooth_kernel<T, MODE><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
@@ -563,11 +561,9 @@ static int smooth(Ctx *c, int l, const T *b, const T *x, T *out, int cpb_overrid
 template <typename T>
 static int restrict_smooth(Ctx *c, int l, const T *bf, const T *xf, T *out, bool zsweep) {
   const Level &fine = c->lv[l], &lv = c->lv[l + 1];
-  if constexpr (sizeof(T) == 4) {
-    if (warp_form<T>(c, l + 1))
-      return launch_warp<T>(c, l + 1, SrcRestrict<T>{mg_args(c, l), Prec<T>::H(fine), bf, xf, lv.children,
-                                                     static_cast<T *>(lv.vb), zsweep}, out);
-  }
+  if (warp_form<T>(c, l + 1))
+    return launch_warp<T>(c, l + 1, SrcRestrict<T>{mg_args(c, l), Prec<T>::H(fine), bf, xf, lv.children,
+                                                   static_cast<T *>(lv.vb), zsweep}, out);
   const SmoothShape sh = smooth_shape<T>(c, l + 1);
   mg_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), mg_args(c, l), Prec<T>::H(fine), bf, xf,
@@ -581,10 +577,8 @@ template <typename T>
 static int trace_restrict_smooth(Ctx *c, const T *R, T *cb, T *out) {
   const Level &lv = c->lv[0];
   const TraceDims d{lv.nlev, lv.nth, lv.ntrace};
-  if constexpr (sizeof(T) == 4) {
-    if (warp_form<T>(c, 0))
-      return launch_warp<T>(c, 0, SrcTraceRestrict<T>{R, Prec<T>::gamma(c), lv.col_edges, d, cb}, out);
-  }
+  if (warp_form<T>(c, 0))
+    return launch_warp<T>(c, 0, SrcTraceRestrict<T>{R, Prec<T>::gamma(c), lv.col_edges, d, cb}, out);
   const SmoothShape sh = smooth_shape<T>(c, 0);
   mg_trace_restrict_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), R, Prec<T>::gamma(c), lv.col_edges, d,
@@ -597,9 +591,7 @@ static int trace_restrict_smooth(Ctx *c, const T *R, T *cb, T *out) {
 template <typename T>
 static int inject_smooth(Ctx *c, int l, const T *b, const T *x, const T *e, T *out) {
   const Level &lv = c->lv[l];
-  if constexpr (sizeof(T) == 4) {
-    if (warp_form<T>(c, l)) return launch_warp<T>(c, l, SrcInject<T>{Prec<T>::H(lv), b, x, e, lv.parent}, out);
-  }
+  if (warp_form<T>(c, l)) return launch_warp<T>(c, l, SrcInject<T>{Prec<T>::H(lv), b, x, e, lv.parent}, out);
   const SmoothShape sh = smooth_shape<T>(c, l);
   mg_inject_smooth_kernel<T><<<sh.grid, sh.threads, sh.smem, c->stream>>>(
       sh.a, Prec<T>::H(lv), Prec<T>::Hz_w(lv), Prec<T>::Hz_l(lv), Prec<T>::Hz_cp(lv), b, x, e, lv.parent, out);

@@ -694,8 +694,9 @@ int autotune(Ctx *c) {
           if ((st = time_mg_cpb(c, l, cand, thr, pm, &ms))) break;
           if (ms < mbest_ms) { mbest_ms = ms; mbest = cand; mbest_t = thr; }
         }
-      // FP32: the warp-per-column form (columns per block -1) competes too
-      if (pm == 1 && !st && c->lv[l].nlev <= 128) {
+      // the warp-per-column form (columns per block -1) competes too (in FP64 it wins only on
+      // small, latency-bound levels: its scan costs ten times the Thomas form's multiply-adds)
+      if (!st && c->lv[l].nlev <= 128) {
         float ms = 0.f;
         if (!(st = time_mg_cpb(c, l, -1, 256, pm, &ms)) && ms < mbest_ms) { mbest_ms = ms; mbest = -1; mbest_t = 256; }
       }
@@ -712,7 +713,7 @@ int autotune(Ctx *c) {
       for (int cand : {32, 64, 16, 8, 4, 2, 1, -1})
         for (int thr : {256, 128}) {
           if (cand > mmax || st || (cand == bc && thr == bt)) continue;
-          if (cand == -1 && (pm == 0 || thr != 256 || c->lv[l].nlev > 128)) continue;   // FP32 warp form
+          if (cand == -1 && (thr != 256 || c->lv[l].nlev > 128)) continue;   // the warp form
           c->tune_mg_cpb[pm][l] = cand;
           c->tune_mg_threads[pm][l] = thr;
           float ms = 0.f;

@@ -68,8 +68,13 @@ def test_autotuned_shapes_keep_results():
     lam0, st0 = gpu.solve(Rub, Rpi)
     gpu.autotune()
     lam1, st1 = gpu.solve(Rub, Rpi)
-    # the column-block shape changes which block solves which columns, not the arithmetic
-    assert torch.equal(lam0, lam1) and st0["iterations"] == st1["iterations"]
+    assert st0["iterations"] == st1["iterations"]
+    _sw, mg = gpu.launch_shapes()
+    if all(c > 0 for c, _t in mg):
+        # the column-block shape changes which block solves which columns, not the arithmetic
+        assert torch.equal(lam0, lam1)
+    else:   # a warp-per-column level: the column solves' rounding order only
+        assert float(torch.linalg.norm(lam1 - lam0) / torch.linalg.norm(lam0)) <= 1e-10
     gpu.close()
 
 

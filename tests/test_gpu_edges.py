@@ -198,8 +198,11 @@ def test_async_stats_enqueue_the_solve_and_report_later():
 
 
 def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
-    """Launch shapes change no arithmetic: a solve captured before hmg_autotune and the solve
-    re-captured after it (autotune drops the old graph) give the same lambda bit for bit."""
+    """Block launch shapes change no arithmetic: a solve captured before hmg_autotune and the
+    solve re-captured after it (autotune drops the old graph) give the same lambda bit for bit,
+    unless the autotuner took the warp-per-column smoother (columns -1) on some level, whose scan
+    changes the rounding order of the column solves only; resetting the shapes restores the
+    first lambda bit for bit."""
     from paper_2210_11797_gb300.hmg import Solver
     w = I.cubed_sphere(16, 12, seed=12)
     gpu = Solver(w.hier, w.coeffs, tol=1e-8)
@@ -209,9 +212,12 @@ def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
     gpu.autotune()
     lam1, st1 = gpu.solve(Rub, Rpi, torch.empty_like(lam0))
     assert st1["iterations"] == st0["iterations"]
-    np.testing.assert_array_equal(_np(lam1), _np(lam0))
     sw, mg = gpu.launch_shapes()
-    assert sw[0] > 0 and all(c > 0 for c, _t in mg)      # tuned shapes are recorded
+    assert sw[0] > 0 and all(c > 0 or c == -1 for c, _t in mg)   # tuned shapes are recorded
+    if all(c > 0 for c, _t in mg):
+        np.testing.assert_array_equal(_np(lam1), _np(lam0))
+    else:
+        assert np.linalg.norm(_np(lam1) - _np(lam0)) <= 1e-10 * np.linalg.norm(_np(lam0))
     gpu.set_launch_shapes(*before)                          # and can be reset
     lam2, _st = gpu.solve(Rub, Rpi, torch.empty_like(lam0))
     np.testing.assert_array_equal(_np(lam2), _np(lam0))
