@@ -178,3 +178,23 @@ def test_degree_p_options_are_checked():
         s.set_options(degree=p)
         assert s.ntrace == (p + 1) ** 2 * n0 and s.nu == 3 * (p + 1) ** 2 * (p + 2) and s.npr == (p + 1) ** 3
     s.close()
+
+
+def test_degree_p_line_smoother_layer_limit():
+    """The degree-p line part stages a column block's rows in 48 KB of shared memory: at p = 3
+    (16 rows per facet) a column of 384 layers no longer fits one column per block, and the
+    sweep (hence the solve) reports HMG_ERR_INVALID_ARG instead of launching; 383 layers run."""
+    from paper_2210_11797_gb300.hmg import HmgError, Solver
+    for nlev, ok in ((383, True), (384, False)):
+        w = I.planar_helmholtz(n=3, nlev=nlev, nmg=1)   # 3456 cells, A_K^-1 2.6 GB
+        s = Solver(w.hier, w.coeffs, tol=1e-6, degree=3)
+        try:
+            b = torch.ones(s.ntrace, dtype=torch.float64, device="cuda")
+            if ok:
+                out = s.line_smooth(b, torch.zeros_like(b), 1)
+                assert bool(torch.isfinite(out).all())
+            else:
+                with pytest.raises(HmgError):
+                    s.line_smooth(b, torch.zeros_like(b), 1)
+        finally:
+            s.close()
