@@ -5,7 +5,9 @@
 // mg_npre / mg_npost sweeps per level and mg_ncoarse sweeps on the coarsest level. On small
 // (latency-bound) levels the restriction runs inside the level's first sweep and the
 // injection inside its first post-sweep; with option mg_fused all coarse levels run as one
-// cooperative launch. Every form does the same arithmetic in the same order.
+// cooperative launch. Every block form does the same arithmetic in the same order; the
+// warp-per-column form (a per-level launch shape) evaluates the column solves as a warp scan,
+// the same iterate up to rounding order.
 #include <algorithm>
 #include <cmath>
 
