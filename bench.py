@@ -838,6 +838,16 @@ def degree_solves(args, stream, steps, p, nlev=32, n=None):
     peak, kind = measured_peaks()
     achieved = nbytes / (apply_ms / 1e3) / 1e9
     nb, nf, N = (p + 1) ** 2, 6 * (p + 1) ** 2, s.nu + s.npr
+    # the FP32 preconditioner at the same degree (its copies made from the assembled operator)
+    s.set_options(precision="mixed")
+    s.autotune()
+    lam32, st32, ms32 = _timed_solves(s, Ru, Rp, stream, steps)
+    mixed = {"ms_per_solve": round(ms32, 4), "unknowns_per_s": round(s.ntrace / (ms32 / 1e3), 1),
+             "iterations": st32["iterations"], "status": st32["status"],
+             "true_rel_residual": st32["true_rel_residual"],
+             "rel_diff_vs_fp64": float(torch.linalg.norm(lam32 - lam) / torch.linalg.norm(lam)),
+             "speedup_vs_fp64": round(ms / ms32, 3)}
+    s.set_options(precision="fp64")
     out = {"workload": {"workload": f"planar_helmholtz_{n}x{n}x{nlev}_degree{p}", "ncell": C, "ntrace": s.ntrace,
                         "dofs_per_cell": f"{s.nu} RT{p} + {s.npr} DG{p}; {nb} trace unknowns per facet; "
                                          f"cell matrices {N} x {N} condensed to {nf} x {nf}",
@@ -848,7 +858,8 @@ def degree_solves(args, stream, steps, p, nlev=32, n=None):
            "components_ms_per_solve": {k: round(v["ms"], 4) for k, v in comp.items()},
            "roofline_trace_apply": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                                     "frac": round(achieved / peak, 4), "peak_kind": kind,
-                                    "algorithmic_bytes": nbytes, "avg_launch_ms": round(apply_ms, 5)}}
+                                    "algorithmic_bytes": nbytes, "avg_launch_ms": round(apply_ms, 5)},
+           "mixed": mixed}
     s.close()
     return out
 

@@ -151,8 +151,10 @@ typedef struct {
                            ((p+1)^2 per facet): mixed cell matrices of 44 x 44, 135 x 135 and
                            304 x 304 condensed to 24 x 24, 54 x 54 and 96 x 96 (the paper's table
                            of unknowns per cell), for the Helmholtz preset (hmg_scalars.preset =
-                           1) in FP64, with Algorithm 1 on facet blocks and Algorithm 2 on the
-                           DG0 coarse space and the lowest-order pressure multigrid. Set before
+                           1), with Algorithm 1 on facet blocks and Algorithm 2 on the DG0 coarse
+                           space and the lowest-order pressure multigrid; with precision mixed the
+                           preconditioner (S, smoother factors, Gamma, V-cycle) runs in FP32 and
+                           the Krylov method, its S apply and residuals in FP64. Set before
                            hmg_assemble_trace (a change needs a new assembly; the assembly holds
                            A_K^-1: N^2 doubles per cell, N = 44, 135, 304; HMG_ERR_OUT_OF_MEMORY when the
                            device cannot hold it). With degree p every call that takes cell
@@ -209,8 +211,10 @@ int hmg_default_options(hmg_options *opt);
  * cuda_stream: a cudaStream_t owned by the caller (NULL = the legacy default stream). */
 int hmg_create(hmg_ctx **out, const hmg_options *opt, void *cuda_stream);
 
-/* Replace the options (e.g. the tolerance or precision) without reassembling, except that
- * switching to HMG_PRECISION_MIXED needs hmg_assemble_trace to build the FP32 copies. */
+/* Replace the options (e.g. the tolerance or precision) without reassembling. On an assembled
+ * context, switching to HMG_PRECISION_MIXED makes the FP32 copies of the operators and factors
+ * from the assembled FP64 ones (device memory for them is allocated here, once; synchronises);
+ * a change of degree needs hmg_assemble_trace. */
 int hmg_set_options(hmg_ctx *ctx, const hmg_options *opt);
 
 /* Set the mesh hierarchy: levels[0] finest ... levels[nmg-1] coarsest; every level has

@@ -54,9 +54,8 @@ static int check_options(Ctx *c, const hmg_options &o) {
   if (o.mg_fuse_cells < 0) return bad("mg_fuse_cells must be >= 0");
   if (o.async_stats != 0 && o.async_stats != 1) return bad("async_stats must be 0 or 1");
   if (o.degree < 0 || o.degree > 3) return bad("degree must be in 0..3");
-  if (o.degree >= 1 && (o.precision != HMG_PRECISION_FP64 || o.precond == HMG_PRECOND_SCHUR ||
-                        o.coarse != HMG_COARSE_VCYCLE))
-    return bad("degree p >= 1 runs in FP64 with the trace preconditioners and the V-cycle coarse solve");
+  if (o.degree >= 1 && (o.precond == HMG_PRECOND_SCHUR || o.coarse != HMG_COARSE_VCYCLE))
+    return bad("degree p >= 1 runs with the trace preconditioners and the V-cycle coarse solve");
   return HMG_OK;
 }
 
@@ -199,9 +198,13 @@ int hmg_set_options(hmg_ctx *c, const hmg_options *opt) {
   int st = check_options(c, *opt);
   if (st) return st;
   c->opt = *opt;
-  if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32)
-    c->assembled = false;  // the FP32 copies are built by hmg_assemble_trace
   if (c->assembled && c->opt.degree != c->degree) c->assembled = false;   // a new discretisation
+  if (c->assembled && c->opt.precision == HMG_PRECISION_MIXED && !c->have_fp32) {
+    // the FP32 copies from the assembled FP64 operators (the degree-p ones below)
+    HMG_CUDA(c, cudaSetDevice(c->device));
+    if ((st = make_fp32(c))) return st;
+    HMG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   if (c->assembled && (c->opt.omega != c->factor_omega || c->opt.mg_omega != c->factor_mg_omega)) {
     HMG_CUDA(c, cudaSetDevice(c->device));
     if ((st = build_factors(c))) return st;

@@ -529,6 +529,22 @@ static int to_float(Ctx *c, const double *in, float **out, int64_t n) {
   return HMG_OK;
 }
 
+// The FP32 preconditioner's copies of the assembled lowest-order operators (S, Gamma, H on every
+// level, then the factors with their copies through build_factors), made from the FP64 data on
+// the device when a context switches to precision mixed: no reassembly.
+int make_fp32(Ctx *c) {
+  const Level &f = c->lv[0];
+  int st;
+  if ((st = to_float(c, c->S, &c->S32, (int64_t)kSlots * f.ntrace))) return st;
+  if ((st = to_float(c, c->gamma, &c->gamma32, f.ncell))) return st;
+  for (int l = 0; l < c->nmg; ++l) {
+    Level &lv = c->lv[l];
+    if ((st = to_float(c, lv.H, &lv.H32, (int64_t)kHCoef * lv.ncell))) return st;
+  }
+  c->have_fp32 = true;
+  return build_factors(c);
+}
+
 // Relaxation-weighted Thomas factors of S^zz, 1/diag S^hh and H_z on every level for the
 // current omega and mg_omega (and their FP32 copies when those exist). Rebuilt whenever
 // either relaxation weight changes.

@@ -251,20 +251,30 @@ __device__ __forceinline__ HoFacet ho_facet(const HoGeo &g, int64_t F) {
   return r;
 }
 
-// NB consecutive coefficients of one slot (the facet's rows) times x into acc
-template <int NB, bool NEG>
-__device__ __forceinline__ void ho_slot(const double *__restrict__ s, double xv, double acc[NB]) {
-  if constexpr (NB % 2 == 0) {
+// NB consecutive coefficients of one slot (the facet's rows) times x into acc: FP64 coefficients
+// as double2 pairs, FP32 ones (the FP32 preconditioner's copy) as float4 quads where NB allows
+template <int NB, bool NEG, typename TS, typename TA>
+__device__ __forceinline__ void ho_slot(const TS *__restrict__ s, TA xv, TA acc[NB]) {
+  if constexpr (sizeof(TS) == 8 && NB % 2 == 0) {
 #pragma unroll
     for (int n = 0; n < NB; n += 2) {
       const double2 v = __ldcs(reinterpret_cast<const double2 *>(s + n));
-      acc[n] = fma(NEG ? -v.x : v.x, xv, acc[n]);
-      acc[n + 1] = fma(NEG ? -v.y : v.y, xv, acc[n + 1]);
+      acc[n] = fma(NEG ? -(TA)v.x : (TA)v.x, xv, acc[n]);
+      acc[n + 1] = fma(NEG ? -(TA)v.y : (TA)v.y, xv, acc[n + 1]);
+    }
+  } else if constexpr (sizeof(TS) == 4 && NB % 4 == 0) {
+#pragma unroll
+    for (int n = 0; n < NB; n += 4) {
+      const float4 v = __ldcs(reinterpret_cast<const float4 *>(s + n));
+      acc[n] = fma(NEG ? -(TA)v.x : (TA)v.x, xv, acc[n]);
+      acc[n + 1] = fma(NEG ? -(TA)v.y : (TA)v.y, xv, acc[n + 1]);
+      acc[n + 2] = fma(NEG ? -(TA)v.z : (TA)v.z, xv, acc[n + 2]);
+      acc[n + 3] = fma(NEG ? -(TA)v.w : (TA)v.w, xv, acc[n + 3]);
     }
   } else {
 #pragma unroll
     for (int n = 0; n < NB; ++n) {
-      const double v = __ldcs(s + n);
+      const TA v = (TA)__ldcs(s + n);
       acc[n] = fma(NEG ? -v : v, xv, acc[n]);
     }
   }
@@ -275,25 +285,25 @@ __device__ __forceinline__ void ho_slot(const double *__restrict__ s, double xv,
 // the couplings inside the smoother's diagonal block D of Algorithm 1 (acc - (S - D) x): on a
 // vertical facet its own nodes, on a horizontal facet the horizontal facets of its column (A's
 // bottom and top, B's bottom).
-template <int P, bool NEG, bool OFFD = false>
-__device__ __forceinline__ void ho_rows(const double *__restrict__ S, const double *__restrict__ x, const HoGeo &g,
-                                        int64_t T, int64_t F, double acc[Ho<P>::NB]) {
+template <int P, bool NEG, bool OFFD = false, typename TS = double, typename TX = double, typename TA = double>
+__device__ __forceinline__ void ho_rows(const TS *__restrict__ S, const TX *__restrict__ x, const HoGeo &g,
+                                        int64_t T, int64_t F, TA acc[Ho<P>::NB]) {
   using H = Ho<P>;
   const HoFacet fc = ho_facet(g, F);
-  const double *Sr = S + (int64_t)H::NB * F;
+  const TS *Sr = S + (int64_t)H::NB * F;
   const bool vert = F < g.nhf;
   constexpr int U = P == 1 ? 4 : 2;
 #pragma unroll U
   for (int q = 0; q < H::NF; ++q) {
     if (OFFD && (vert ? q / H::NB == fc.fA : q / H::NB >= 4)) continue;
-    const double xv = __ldg(x + ho_gid<P>(g, fc.cA, fc.kA, q));
+    const TA xv = (TA)__ldg(x + ho_gid<P>(g, fc.cA, fc.kA, q));
     ho_slot<H::NB, NEG>(Sr + (int64_t)q * T, xv, acc);
   }
   if (fc.cB < 0) return;
 #pragma unroll U
   for (int q = 0; q < H::NF; ++q) {
     if (q / H::NB == fc.fB || (OFFD && !vert && q / H::NB >= 4)) continue;
-    const double xv = __ldg(x + ho_gid<P>(g, fc.cB, fc.kB, q));
+    const TA xv = (TA)__ldg(x + ho_gid<P>(g, fc.cB, fc.kB, q));
     ho_slot<H::NB, NEG>(Sr + (int64_t)(H::NF + q) * T, xv, acc);
   }
 }
@@ -772,68 +782,71 @@ __global__ void ho_reconstruct_kernel(const HoGeo g, int64_t ncell, const double
 // solves: each column's r staged in shared memory, the block Thomas recurrences with LPC lanes
 // per column (lane n < NB computes component n of each NB x NB product from its rows of the
 // stored factors; the lanes of a column sit in one warp and meet at __syncwarp between the
-// steps), lam_out = keep lam_in + omega (S^zz_c)^-1 r.
-template <int P, bool ZERO>
+// steps), lam_out = keep lam_in + omega (S^zz_c)^-1 r. T is the arithmetic and coefficient
+// type (double, or float in the FP32 preconditioner, whose b is the FP64 Krylov residual and
+// whose last sweep writes FP64).
+template <int P, bool ZERO, typename T = double, typename Tb = double, typename Tin = double, typename Tout = double>
 __global__ void __launch_bounds__(kRedThreads)
-    ho_sweep_rows_kernel(const HoGeo g, int64_t T, const double *__restrict__ S, const double *__restrict__ hw,
-                         const double *__restrict__ b, const double *__restrict__ lam_in,
-                         double *__restrict__ lam_out, double keep) {
+    ho_sweep_rows_kernel(const HoGeo g, int64_t TT, const T *__restrict__ S, const T *__restrict__ hw,
+                         const Tb *__restrict__ b, const Tin *__restrict__ lam_in,
+                         Tout *__restrict__ lam_out, double keep) {
   constexpr int NB = Ho<P>::NB;
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= (ZERO ? g.nhf : g.nhf + g.nzf)) return;
   const int64_t r0 = (int64_t)NB * F;
-  double acc[NB];
+  T acc[NB];
 #pragma unroll
-  for (int n = 0; n < NB; ++n) acc[n] = __ldg(b + r0 + n);
-  if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, T, F, acc);
+  for (int n = 0; n < NB; ++n) acc[n] = (T)__ldg(b + r0 + n);
+  if (!ZERO) ho_rows<P, true, true>(S, lam_in, g, TT, F, acc);
   if (F < g.nhf) {
     for (int n = 0; n < NB; ++n) {
-      double v = ZERO ? 0.0 : keep * lam_in[r0 + n];
+      T v = ZERO ? (T)0 : (T)keep * (T)lam_in[r0 + n];
 #pragma unroll
       for (int m = 0; m < NB; ++m) v = fma(hw[(int64_t)(NB * n + m) * g.nhf + F], acc[m], v);
-      lam_out[r0 + n] = v;
+      lam_out[r0 + n] = (Tout)v;
     }
   } else {
 #pragma unroll
-    for (int n = 0; n < NB; ++n) lam_out[r0 + n] = acc[n];
+    for (int n = 0; n < NB; ++n) lam_out[r0 + n] = (Tout)acc[n];
   }
 }
 
 // Part 2; r is read from src (lam_out after part 1, b for a sweep from zero)
-template <int P, bool ZERO>
+template <int P, bool ZERO, typename T = double, typename Ts = double, typename Tin = double, typename Tout = double>
 __global__ void __launch_bounds__(128)
-    ho_sweep_lines_kernel(const HoGeo g, int cpb, const double *__restrict__ zf, const double *src,
-                          const double *__restrict__ lam_in, double *lam_out, double keep) {
+    ho_sweep_lines_kernel(const HoGeo g, int cpb, const T *__restrict__ zf, const Ts *src,
+                          const Tin *__restrict__ lam_in, Tout *lam_out, double keep) {
   using H = Ho<P>;
   constexpr int NB = H::NB, NB2 = NB * NB, LPC = H::LPC;
-  extern __shared__ double sr[];   // [cpb][L+1][NB]
+  extern __shared__ __align__(16) unsigned char ho_lines_smem[];
+  T *sr = reinterpret_cast<T *>(ho_lines_smem);   // [cpb][L+1][NB]
   const int L1 = g.L + 1;
   const int c0 = blockIdx.x * cpb, nc = min(cpb, g.ncol - c0);
   const int64_t base = g.NH + (int64_t)NB * c0 * L1;
-  for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) sr[i] = src[base + i];
+  for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x) sr[i] = (T)src[base + i];
   __syncthreads();
   const int lane = threadIdx.x & 31, gw = lane / LPC;   // the lane's group within its warp
   const int cc = gw < H::CPW ? (threadIdx.x >> 5) * H::CPW + gw : cpb, n = lane - gw * LPC;
   const unsigned grp = ((1u << LPC) - 1u) << (gw * LPC);   // this column's lanes
   if (cc < nc) {
-    double *r = sr + NB * cc * L1;
-    const double *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + n;   // this lane's rows (transposed)
+    T *r = sr + NB * cc * L1;
+    const T *f0 = zf + 3 * NB2 * ((int64_t)(c0 + cc) * L1) + n;   // this lane's rows (transposed)
     const bool act = n < NB;
     // forward: y_k = (omega G_k^-1) r_k - (G_k^-1 L_k) y_{k-1}, y written over r; the next level's
     // factor rows are loaded one step ahead (the serial recurrence waits on nothing else)
-    double fa[NB], fb[NB];
+    T fa[NB], fb[NB];
     if (act) {
 #pragma unroll
       for (int m = 0; m < NB; ++m) { fa[m] = __ldg(f0 + NB * m); fb[m] = __ldg(f0 + NB2 + NB * m); }
     }
     for (int k = 0; k < L1; ++k) {
-      double na[NB], nb[NB];
+      T na[NB], nb[NB];
       if (act && k + 1 < L1) {
-        const double *f = f0 + 3 * NB2 * (k + 1);
+        const T *f = f0 + 3 * NB2 * (k + 1);
 #pragma unroll
         for (int m = 0; m < NB; ++m) { na[m] = __ldg(f + NB * m); nb[m] = __ldg(f + NB2 + NB * m); }
       }
-      double v = 0.0, u = 0.0;
+      T v = (T)0, u = (T)0;
       if (act) {
 #pragma unroll
         for (int m = 0; m < NB; ++m) v = fma(fa[m], r[NB * k + m], v);
@@ -851,19 +864,19 @@ __global__ void __launch_bounds__(128)
     // backward: x_k = y_k - (G_k^-1 U_k) x_{k+1}, x written over y (row k + 1 is not written in
     // this step, row k only by its own lane); G_k^-1 U_k one step ahead as well
     if (act && L1 >= 2) {
-      const double *f = f0 + 3 * NB2 * (L1 - 2) + 2 * NB2;
+      const T *f = f0 + 3 * NB2 * (L1 - 2) + 2 * NB2;
 #pragma unroll
       for (int m = 0; m < NB; ++m) fa[m] = __ldg(f + NB * m);
     }
     for (int k = L1 - 2; k >= 0; --k) {
-      double na[NB];
+      T na[NB];
       if (act && k > 0) {
-        const double *f = f0 + 3 * NB2 * (k - 1) + 2 * NB2;
+        const T *f = f0 + 3 * NB2 * (k - 1) + 2 * NB2;
 #pragma unroll
         for (int m = 0; m < NB; ++m) na[m] = __ldg(f + NB * m);
       }
       if (act) {
-        double v = r[NB * k + n];
+        T v = r[NB * k + n];
 #pragma unroll
         for (int m = 0; m < NB; ++m) v = fma(-fa[m], r[NB * (k + 1) + m], v);
         r[NB * k + n] = v;
@@ -875,25 +888,25 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nc * L1 * NB; i += blockDim.x)
-    lam_out[base + i] = ZERO ? sr[i] : fma(keep, lam_in[base + i], sr[i]);
+    lam_out[base + i] = (Tout)(ZERO ? sr[i] : fma((T)keep, (T)lam_in[base + i], sr[i]));
 }
 
 // R = b - S lam (Algorithm 2 line 3), one thread per facet. ZSWEEP: lam is one sweep from zero,
 // lam = omega D^-1 b, so R = (1 - omega) b - (S - D) lam (equal in exact arithmetic).
-template <int P, bool ZSWEEP>
-__global__ void ho_residual_kernel(const HoGeo g, int64_t T, const double *__restrict__ S,
-                                   const double *__restrict__ b, const double *__restrict__ lam,
-                                   double *__restrict__ R, double keep) {
+template <int P, bool ZSWEEP, typename T = double>
+__global__ void ho_residual_kernel(const HoGeo g, int64_t TT, const T *__restrict__ S,
+                                   const double *__restrict__ b, const T *__restrict__ lam,
+                                   T *__restrict__ R, double keep) {
   constexpr int NB = Ho<P>::NB;
   const int64_t F = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (F >= g.nhf + g.nzf) return;
-  double acc[NB];
+  T acc[NB];
 #pragma unroll
   for (int n = 0; n < NB; ++n) {
-    const double bv = __ldg(b + (int64_t)NB * F + n);
-    acc[n] = ZSWEEP ? keep * bv : bv;
+    const T bv = (T)__ldg(b + (int64_t)NB * F + n);
+    acc[n] = ZSWEEP ? (T)keep * bv : bv;
   }
-  ho_rows<P, true, ZSWEEP>(S, lam, g, T, F, acc);
+  ho_rows<P, true, ZSWEEP>(S, lam, g, TT, F, acc);
 #pragma unroll
   for (int n = 0; n < NB; ++n) R[(int64_t)NB * F + n] = acc[n];
 }
@@ -901,31 +914,39 @@ __global__ void ho_residual_kernel(const HoGeo g, int64_t T, const double *__res
 // bbar_K = Gamma_K (P^T R)_K (Algorithm 2 lines 4-5): P is constant on a facet (all its nodes)
 // and averages the facet's cells, so P^T sums the cell's facet nodes with weight 1/2 (1 on
 // ground and lid facets)
-template <int P>
-__global__ void ho_restrict_kernel(const HoGeo g, int64_t ncell, const double *__restrict__ R,
-                                   const double *__restrict__ gamma, double *__restrict__ bbar) {
+template <int P, typename T = double>
+__global__ void ho_restrict_kernel(const HoGeo g, int64_t ncell, const T *__restrict__ R,
+                                   const T *__restrict__ gamma, T *__restrict__ bbar) {
   using H = Ho<P>;
   const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (K >= ncell) return;
   const int c = (int)(K / g.L), k = (int)(K - (int64_t)c * g.L);
-  double s = 0.0;
+  T s = (T)0;
   for (int q = 0; q < H::NF; ++q) {
     const int f = q / H::NB;
     const bool boundary = (f == 4 && k == 0) || (f == 5 && k == g.L - 1);
-    s = fma(boundary ? 1.0 : 0.5, R[ho_gid<P>(g, c, k, q)], s);
+    s = fma(boundary ? (T)1 : (T)0.5, R[ho_gid<P>(g, c, k, q)], s);
   }
   bbar[K] = gamma ? gamma[K] * s : s;
 }
 
 // lam_out = lam_in + P dPi (Algorithm 2 line 7), one thread per row
-template <int P>
-__global__ void ho_prolong_kernel(const HoGeo g, int64_t T, const double *__restrict__ lam_in,
-                                  const double *__restrict__ dpi, double *__restrict__ lam_out) {
+template <int P, typename T = double>
+__global__ void ho_prolong_kernel(const HoGeo g, int64_t TT, const T *__restrict__ lam_in,
+                                  const T *__restrict__ dpi, T *__restrict__ lam_out) {
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= T) return;
+  if (row >= TT) return;
   const HoFacet fc = ho_facet(g, row / Ho<P>::NB);
-  const double a = dpi[(int64_t)fc.cA * g.L + fc.kA];
-  lam_out[row] = fc.cB >= 0 ? fma(0.5, a + dpi[(int64_t)fc.cB * g.L + fc.kB], lam_in[row]) : lam_in[row] + a;
+  const T a = dpi[(int64_t)fc.cA * g.L + fc.kA];
+  lam_out[row] = fc.cB >= 0 ? fma((T)0.5, a + dpi[(int64_t)fc.cB * g.L + fc.kB], lam_in[row]) : lam_in[row] + a;
+}
+
+// the FP32 preconditioner's copies of the degree-p operator and factors; the last step's FP32
+// result widened to FP64
+template <typename Ta, typename Tb>
+__global__ void ho_convert_kernel(const Ta *__restrict__ x, Tb *__restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (Tb)x[i];
 }
 
 __global__ void ho_fill_kernel(double *__restrict__ x, int64_t n, double v) {
@@ -964,20 +985,49 @@ template <int P>
 static int ho_build_factors(Ctx *c) {
   HoData &h = c->ho;
   const HoGeo g = ho_geo<P>(c);
+  constexpr int NB = Ho<P>::NB;
   int *sing = h.flag;
   HMG_CUDA(c, cudaMemsetAsync(sing, 0, sizeof(int), c->stream));
-  constexpr int NB = Ho<P>::NB;
   const size_t zsmem = sizeof(double) * kHoFacWarps * (3 * NB * NB + 2 * NB * NB);
   ho_hfactor_kernel<P><<<grid_for(g.nhf, kHoFacWarps), 32 * kHoFacWarps, 0, c->stream>>>(g, h.T, h.S, c->opt.omega,
                                                                                       h.hw, sing);
   ho_zfactor_kernel<P><<<grid_for(g.ncol, kHoFacWarps), 32 * kHoFacWarps, zsmem, c->stream>>>(
       g, h.T, h.S, c->opt.omega, h.zf, sing);
   HMG_CUDA(c, cudaGetLastError());
+  if (h.S32) {   // the FP32 preconditioner's copies of the factors follow them
+    const int64_t nh = (int64_t)NB * NB * g.nhf, nz = (int64_t)3 * NB * NB * g.nzf;
+    ho_convert_kernel<double, float><<<grid_for(nh, 256), 256, 0, c->stream>>>(h.hw, h.hw32, nh);
+    ho_convert_kernel<double, float><<<grid_for(nz, 256), 256, 0, c->stream>>>(h.zf, h.zf32, nz);
+    HMG_CUDA(c, cudaGetLastError());
+  }
   int s = 0;
   HMG_CUDA(c, cudaMemcpyAsync(&s, sing, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HMG_CUDA(c, cudaStreamSynchronize(c->stream));
   if (s) return fail(c, HMG_ERR_INVALID_ARG, "a smoother block of the degree-p trace operator is singular");
   h.factor_omega = c->opt.omega;
+  return HMG_OK;
+}
+
+// The FP32 copies of S, Gamma and the smoother factors (allocated once per layout)
+template <int P>
+static int ho_build_fp32(Ctx *c) {
+  using H = Ho<P>;
+  HoData &h = c->ho;
+  const HoGeo g = ho_geo<P>(c);
+  const int64_t C = c->lv[0].ncell, nS = (int64_t)H::SLOTS * h.T;
+  const int64_t nh = (int64_t)H::NB * H::NB * g.nhf, nz = (int64_t)3 * H::NB * H::NB * g.nzf;
+  int st;
+  if (!h.S32) {
+    if ((st = dev_alloc(c, &h.S32, (size_t)nS))) return st;
+    if ((st = dev_alloc(c, &h.hw32, (size_t)nh))) return st;
+    if ((st = dev_alloc(c, &h.zf32, (size_t)nz))) return st;
+    if ((st = dev_alloc(c, &h.gamma32, (size_t)C))) return st;
+  }
+  ho_convert_kernel<double, float><<<grid_for(nS, 256), 256, 0, c->stream>>>(h.S, h.S32, nS);
+  ho_convert_kernel<double, float><<<grid_for(nh, 256), 256, 0, c->stream>>>(h.hw, h.hw32, nh);
+  ho_convert_kernel<double, float><<<grid_for(nz, 256), 256, 0, c->stream>>>(h.zf, h.zf32, nz);
+  ho_convert_kernel<double, float><<<grid_for(C, 256), 256, 0, c->stream>>>(h.gamma, h.gamma32, C);
+  HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
 
@@ -992,6 +1042,11 @@ void ho_free(Ctx *c) {
   h.own = nullptr;
   dev_free(c, h.flag);
   h.flag = nullptr;
+  float **f32[] = {&h.S32, &h.hw32, &h.zf32, &h.gamma32};
+  for (float **b : f32) {
+    dev_free(c, *b);
+    *b = nullptr;
+  }
   h.degree = 0;
   h.ncell = 0;
   h.T = 0;
@@ -1045,10 +1100,12 @@ static int ho_assemble_p(Ctx *c) {
   ho_fill_kernel<<<grid_for(h.T, 256), 256, 0, c->stream>>>(ones, h.T, 1.0);
   ho_spmv_kernel<P, 0><<<grid_for(g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
       g, h.T, h.S, ones, s1, nullptr, c->part, 0, 0);
-  ho_restrict_kernel<P><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, s1, nullptr, h.gamma);
+  ho_restrict_kernel<P, double><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, s1, nullptr, h.gamma);
   ho_gamma_kernel<<<grid_for(C, 256), 256, 0, c->stream>>>(C, h.m, h.gamma);
   HMG_CUDA(c, cudaGetLastError());
-  return ho_build_factors<P>(c);
+  if ((st = ho_build_factors<P>(c))) return st;
+  if (c->opt.precision == HMG_PRECISION_MIXED) return ho_build_fp32<P>(c);
+  return HMG_OK;
 }
 
 template <int P>
@@ -1087,24 +1144,46 @@ static int ho_reconstruct_p(Ctx *c, const double *lam, const double *Ru, const d
   return HMG_OK;
 }
 
-template <int P, bool ZERO>
-static int ho_sweep(Ctx *c, const double *b, const double *lam_in, double *lam_out) {
+// The FP64 operator or the FP32 preconditioner's copies
+template <typename T> struct HoPrec;
+template <> struct HoPrec<double> {
+  static const double *S(const HoData &h) { return h.S; }
+  static const double *hw(const HoData &h) { return h.hw; }
+  static const double *zf(const HoData &h) { return h.zf; }
+  static const double *gamma(const HoData &h) { return h.gamma; }
+};
+template <> struct HoPrec<float> {
+  static const float *S(const HoData &h) { return h.S32; }
+  static const float *hw(const HoData &h) { return h.hw32; }
+  static const float *zf(const HoData &h) { return h.zf32; }
+  static const float *gamma(const HoData &h) { return h.gamma32; }
+};
+
+// One sweep of Algorithm 1 in arithmetic T: b (the Krylov residual, FP64) and lam_in (Tin) in,
+// lam_out (Tout) out.
+template <int P, bool ZERO, typename T = double, typename Tin = double, typename Tout = double>
+static int ho_sweep(Ctx *c, const double *b, const Tin *lam_in, Tout *lam_out) {
   using H = Ho<P>;
   const HoData &h = c->ho;
   const HoGeo g = ho_geo<P>(c);
   // columns per block of the line part: 4 warps of CPW columns, and the block's rows
-  // (NB (L + 1) doubles per column) within 48 KB
-  const int cap = (int)((48 * 1024) / (sizeof(double) * H::NB * (g.L + 1)));
+  // (NB (L + 1) values per column) within 48 KB
+  const int cap = (int)((48 * 1024) / (sizeof(T) * H::NB * (g.L + 1)));
   if (cap < 1) return fail(c, HMG_ERR_INVALID_ARG, "too many layers for the degree-p line smoother");
   const int cpb = cap < 4 * H::CPW ? cap : 4 * H::CPW;
   const unsigned nzb = (unsigned)((g.ncol + cpb - 1) / cpb);
-  const size_t smem = sizeof(double) * H::NB * cpb * (g.L + 1);
+  const size_t smem = sizeof(T) * H::NB * cpb * (g.L + 1);
   const double keep = 1.0 - h.factor_omega;
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep, 2);
-  ho_sweep_rows_kernel<P, ZERO><<<grid_for(ZERO ? g.nhf : g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
-      g, h.T, h.S, h.hw, b, lam_in, lam_out, keep);
-  ho_sweep_lines_kernel<P, ZERO><<<nzb, 128, smem, c->stream>>>(g, cpb, h.zf, ZERO ? b : lam_out, lam_in, lam_out,
-                                                                keep);
+  ho_sweep_rows_kernel<P, ZERO, T, double, Tin, Tout>
+      <<<grid_for(ZERO ? g.nhf : g.nhf + g.nzf, kRedThreads), kRedThreads, 0, c->stream>>>(
+          g, h.T, HoPrec<T>::S(h), HoPrec<T>::hw(h), b, lam_in, lam_out, keep);
+  if constexpr (ZERO)
+    ho_sweep_lines_kernel<P, ZERO, T, double, Tin, Tout><<<nzb, 128, smem, c->stream>>>(g, cpb, HoPrec<T>::zf(h), b,
+                                                                                      lam_in, lam_out, keep);
+  else
+    ho_sweep_lines_kernel<P, ZERO, T, Tout, Tin, Tout><<<nzb, 128, smem, c->stream>>>(
+        g, cpb, HoPrec<T>::zf(h), lam_out, lam_in, lam_out, keep);
   HMG_CUDA(c, cudaGetLastError());
   return HMG_OK;
 }
@@ -1126,26 +1205,30 @@ static int ho_line_smooth_p(Ctx *c, const double *b, double *lam, int nsweeps) {
 }
 
 // z = M^-1 r: configuration 3c (Algorithm 2, the V-cycle of the lowest-order pressure operator as
-// the coarse solve), configuration 2 (n_smooth sweeps of Algorithm 1 from zero) or none.
-template <int P>
+// the coarse solve), configuration 2 (n_smooth sweeps of Algorithm 1 from zero) or none. T = float
+// is the FP32 preconditioner: its coefficients, work vectors and V-cycle in FP32, r read and z
+// written in FP64 (the Krylov vectors).
+template <int P, typename T>
 static int ho_precond_p(Ctx *c, const double *r, double *z) {
   const HoData &h = c->ho;
   const HoGeo g = ho_geo<P>(c);
-  const int64_t T = h.T, C = c->lv[0].ncell;
+  const int64_t TT = h.T, C = c->lv[0].ncell;
   int st;
-  double *w1 = static_cast<double *>(c->w1), *w2 = static_cast<double *>(c->w2), *w3 = static_cast<double *>(c->w3);
+  if (!HoPrec<T>::S(h)) return fail(c, HMG_ERR_NOT_READY, "the FP32 copies of the degree-p operator are missing");
+  T *w1 = static_cast<T *>(c->w1), *w2 = static_cast<T *>(c->w2), *w3 = static_cast<T *>(c->w3);
   if (c->opt.precond == HMG_PRECOND_NONE) {
-    HMG_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * T, cudaMemcpyDeviceToDevice, c->stream));
+    HMG_CUDA(c, cudaMemcpyAsync(z, r, sizeof(double) * TT, cudaMemcpyDeviceToDevice, c->stream));
     return HMG_OK;
   }
   if (c->opt.precond == HMG_PRECOND_LINESMOOTH) {
     const int n = c->opt.n_smooth;
-    if (n == 1) return ho_sweep<P, true>(c, r, nullptr, z);
-    if ((st = ho_sweep<P, true>(c, r, nullptr, w1))) return st;
-    double *cur = w1, *nxt = w2;
+    if (n == 1) return ho_sweep<P, true, T, T, double>(c, r, nullptr, z);
+    if ((st = ho_sweep<P, true, T, T, T>(c, r, nullptr, w1))) return st;
+    T *cur = w1, *nxt = w2;
     for (int i = 1; i < n; ++i) {
-      if ((st = ho_sweep<P, false>(c, r, cur, i == n - 1 ? z : nxt))) return st;
-      double *t = cur;
+      if (i == n - 1) return ho_sweep<P, false, T, T, double>(c, r, cur, z);
+      if ((st = ho_sweep<P, false, T, T, T>(c, r, cur, nxt))) return st;
+      T *t = cur;
       cur = nxt;
       nxt = t;
     }
@@ -1153,50 +1236,52 @@ static int ho_precond_p(Ctx *c, const double *r, double *z) {
   }
   // lines 1-2: presmoothing from zero
   if (c->opt.n_pre >= 1) {
-    if ((st = ho_sweep<P, true>(c, r, nullptr, w1))) return st;
+    if ((st = ho_sweep<P, true, T, T, T>(c, r, nullptr, w1))) return st;
     for (int i = 1; i < c->opt.n_pre; ++i) {
-      if ((st = ho_sweep<P, false>(c, r, w1, w2))) return st;
-      double *t = w1;
+      if ((st = ho_sweep<P, false, T, T, T>(c, r, w1, w2))) return st;
+      T *t = w1;
       w1 = w2;
       w2 = t;
     }
   } else {
-    HMG_CUDA(c, cudaMemsetAsync(w1, 0, sizeof(double) * T, c->stream));
+    HMG_CUDA(c, cudaMemsetAsync(w1, 0, sizeof(T) * TT, c->stream));
   }
-  double *cb = static_cast<double *>(c->cb);
+  T *cb = static_cast<T *>(c->cb);
   {
     Prof pr(c, kCompResidual, 2);
     if (c->opt.n_pre == 1)   // w1 is one sweep from zero                                       // line 3
-      ho_residual_kernel<P, true><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2,
-                                                                                      1.0 - h.factor_omega);
+      ho_residual_kernel<P, true, T><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(
+          g, TT, HoPrec<T>::S(h), r, w1, w2, 1.0 - h.factor_omega);
     else
-      ho_residual_kernel<P, false><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(g, T, h.S, r, w1, w2, 0.0);
-    ho_restrict_kernel<P><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, w2, h.gamma, cb);       // lines 4-5
+      ho_residual_kernel<P, false, T><<<grid_for(g.nhf + g.nzf, 128), 128, 0, c->stream>>>(
+          g, TT, HoPrec<T>::S(h), r, w1, w2, 0.0);
+    ho_restrict_kernel<P, T><<<grid_for(C, 256), 256, 0, c->stream>>>(g, C, w2, HoPrec<T>::gamma(h), cb);   // lines 4-5
     HMG_CUDA(c, cudaGetLastError());
   }
-  double *dpi = nullptr;
+  T *dpi = nullptr;
   {
     Prof pv(c, kCompVcycle, vcycle_launches(c));
-    if ((st = vcycle<double>(c, cb, &dpi))) return st;                                            // line 6
+    if ((st = vcycle<T>(c, cb, &dpi))) return st;                                                 // line 6
   }
   {
     Prof pp(c, kCompProlong);
-    ho_prolong_kernel<P><<<grid_for(T, 256), 256, 0, c->stream>>>(g, T, w1, dpi, w2);               // line 7
+    ho_prolong_kernel<P, T><<<grid_for(TT, 256), 256, 0, c->stream>>>(g, TT, w1, dpi, w2);          // line 7
     HMG_CUDA(c, cudaGetLastError());
   }
   const int np = c->opt.n_post;                                                                    // line 8
   if (np == 0) {
-    HMG_CUDA(c, cudaMemcpyAsync(z, w2, sizeof(double) * T, cudaMemcpyDeviceToDevice, c->stream));
+    ho_convert_kernel<T, double><<<grid_for(TT, 256), 256, 0, c->stream>>>(w2, z, TT);
+    HMG_CUDA(c, cudaGetLastError());
     return HMG_OK;
   }
-  double *cur = w2, *nxt = w3;
+  T *cur = w2, *nxt = w3;
   for (int i = 0; i < np - 1; ++i) {
-    if ((st = ho_sweep<P, false>(c, r, cur, nxt))) return st;
-    double *t = cur;
+    if ((st = ho_sweep<P, false, T, T, T>(c, r, cur, nxt))) return st;
+    T *t = cur;
     cur = nxt;
     nxt = t;
   }
-  return ho_sweep<P, false>(c, r, cur, z);
+  return ho_sweep<P, false, T, T, double>(c, r, cur, z);
 }
 
 // ---- degree dispatch ------------------------------------------------------------------------------
@@ -1213,6 +1298,16 @@ int ho_assemble(Ctx *c) {
 }
 
 int ho_refactor_if_needed(Ctx *c) {
+  if (c->opt.precision == HMG_PRECISION_MIXED && !c->ho.S32) {   // switched to the FP32 preconditioner
+    int st = HMG_OK;
+    switch (c->degree) {
+      case 1: st = ho_build_fp32<1>(c); break;
+      case 2: st = ho_build_fp32<2>(c); break;
+      case 3: st = ho_build_fp32<3>(c); break;
+      default: return bad_degree(c);
+    }
+    if (st) return st;
+  }
   if (c->ho.factor_omega == c->opt.omega) return HMG_OK;
   switch (c->degree) {
     case 1: return ho_build_factors<1>(c);
@@ -1259,10 +1354,11 @@ int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps) {
 }
 
 int ho_precond(Ctx *c, const double *r, double *z) {
+  const bool mixed = c->opt.precision == HMG_PRECISION_MIXED;
   switch (c->degree) {
-    case 1: return ho_precond_p<1>(c, r, z);
-    case 2: return ho_precond_p<2>(c, r, z);
-    case 3: return ho_precond_p<3>(c, r, z);
+    case 1: return mixed ? ho_precond_p<1, float>(c, r, z) : ho_precond_p<1, double>(c, r, z);
+    case 2: return mixed ? ho_precond_p<2, float>(c, r, z) : ho_precond_p<2, double>(c, r, z);
+    case 3: return mixed ? ho_precond_p<3, float>(c, r, z) : ho_precond_p<3, double>(c, r, z);
     default: return bad_degree(c);
   }
 }

@@ -100,6 +100,8 @@ struct HoData {
   double *tab = nullptr;       // reference-element tables
   int *flag = nullptr;         // singular-matrix flag of the assembly
   double factor_omega = 0.0;   // the omega the smoother factors hold
+  // FP32 copies for the FP32 preconditioner (precision mixed): S, the smoother factors, Gamma
+  float *S32 = nullptr, *hw32 = nullptr, *zf32 = nullptr, *gamma32 = nullptr;
 };
 
 struct Ctx {
@@ -268,6 +270,7 @@ inline unsigned grid_for(int64_t n, int threads) {
 int assemble_all(Ctx *c);
 // (Re)builds the relaxation-weighted Thomas factors for the context's omega and mg_omega.
 int build_factors(Ctx *c);
+int make_fp32(Ctx *c);   // FP32 copies of the assembled operators and factors (no reassembly)
 
 // ---- trace-space kernels (trace_ops.cu) -----------------------------------------------
 // y = S x (FP64). mode 0: plain; 1: also (w, y) -> scal[slot0]; 2: also (y, w) -> slot0 and
@@ -325,7 +328,8 @@ int ho_trace_rhs(Ctx *c, const double *Ru, const double *Rp, double *B);
 int ho_reconstruct(Ctx *c, const double *lam, const double *Ru, const double *Rp, double *u, double *pi);
 int ho_precond(Ctx *c, const double *r, double *z);
 int ho_line_smooth(Ctx *c, const double *b, double *lam, int nsweeps);
-// rebuilds the degree-p smoother factors when omega changed since they were built (synchronises)
+// rebuilds the degree-p smoother factors when omega changed since they were built, and makes the
+// FP32 preconditioner's copies when the precision is mixed (synchronises)
 int ho_refactor_if_needed(Ctx *c);
 // cell residual sizes of degree p: 3 (p+1)^2 (p+2) velocity and (p+1)^3 pressure dofs per cell
 // (6 and 1 at the lowest order)

@@ -268,11 +268,10 @@ class Solver:
     def set_options(self, **kw):
         for k, v in kw.items():
             setattr(self.opts, k, _option_value(k, v))
+        # (hmg_set_options makes the FP32 copies of the operators when the precision becomes
+        # mixed, and rebuilds them with the factors when a relaxation weight changes)
         _check(self.ctx, lib().hmg_set_options(self.ctx, C.byref(self.opts)))
-        # the FP32 copies of the operators are built by assembly, once; later changes of the
-        # relaxation weights rebuild them inside hmg_set_options
-        if self.opts.precision == PRECISION["mixed"] and not self._fp32_built:
-            _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
+        if self.opts.precision == PRECISION["mixed"]:
             self._fp32_built = True
         if self.opts.degree != self.degree:       # a new discretisation: assemble it
             _check(self.ctx, lib().hmg_assemble_trace(self.ctx))
