@@ -183,13 +183,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   return done != 0;
 }
 
-template <typename Tin>
+// TRAIN (the training minibatch's forward, x unscaled): h1 and h2 are stored channel-major
+// [32][ncell] BF16 for the backward instead of h2 cell-major, and no scale is kept.
+template <typename Tin, bool TRAIN = false>
 __global__ void __launch_bounds__(128)
     nn_front_tc_kernel(const float *__restrict__ wts, const __nv_bfloat16 *__restrict__ bimg,
                        const Tin *__restrict__ xin, const double *__restrict__ diagH,
                        const float *__restrict__ diagH32, int ncol, int L,
                        __nv_bfloat16 *__restrict__ h2_out, float *__restrict__ dscale_out,
-                       int *__restrict__ wait_flag) {
+                       int *__restrict__ wait_flag, __nv_bfloat16 *__restrict__ h1_out = nullptr) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char *sA = tc_smem, *sB = tc_smem + kTcB;
   float *xs = reinterpret_cast<float *>(tc_smem + kTcX);            // 132 floats
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(128)
       const int64_t q = (int64_t)(R / P) * L + k;
       const float sc = rsqrtf(diagH ? (float)diagH[q] : diagH32 ? diagH32[q] : 1.f);
       v = rnd<__nv_bfloat16>((float)xin[q] * sc);
-      if (j >= 2 && j < kTcM + 2) dscale_out[q] = sc;
+      if (!TRAIN && j >= 2 && j < kTcM + 2) dscale_out[q] = sc;
     }
     xs[j] = v;
   }
@@ -254,6 +256,11 @@ __global__ void __launch_bounds__(128)
         }
         const __nv_bfloat162 b2 = __floats2bfloat162_rn(hv[0], hv[1]);
         wds[q] = *reinterpret_cast<const uint32_t *>(&b2);
+        if (TRAIN && row >= 1 && row <= kTcM) {   // the tile's own rows: h1 for the backward
+          const int64_t C = (int64_t)ncol * L, cell = (int64_t)((R0 - 1 + row) / P) * L + lev[row + 1];
+          h1_out[(int64_t)(g * 8 + 2 * q) * C + cell] = b2.x;
+          h1_out[(int64_t)(g * 8 + 2 * q + 1) * C + cell] = b2.y;
+        }
       }
       pack = make_uint4(wds[0], wds[1], wds[2], wds[3]);
     }
@@ -310,7 +317,11 @@ __global__ void __launch_bounds__(128)
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const int R = R0 + warp * 32 + lane, k = lev[warp * 32 + lane + 2];
-    if (k >= 0) {   // cell-major: the 32 channels of a cell in 64 contiguous bytes
+    if (TRAIN && k >= 0) {   // channel-major: each channel's store coalesced over the warp's cells
+      const int64_t C = (int64_t)ncol * L, cell = (int64_t)(R / P) * L + k;
+#pragma unroll
+      for (int i = 0; i < kCh; ++i) h2_out[(int64_t)i * C + cell] = __float2bfloat16_rn(fmaxf(__uint_as_float(r[i]), 0.f));
+    } else if (k >= 0) {   // cell-major: the 32 channels of a cell in 64 contiguous bytes
       const int64_t cell = (int64_t)(R / P) * L + k;
       uint32_t wd[16];
 #pragma unroll
@@ -1157,6 +1168,8 @@ int nn_setup(Ctx *c) {
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  HMG_CUDA(c, cudaFuncSetAttribute(nn_front_tc_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kTcSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwSmem));
   HMG_CUDA(c, cudaFuncSetAttribute(nn_bwd1_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
   if ((st = dev_alloc(c, &c->nn_w, kNParams))) return st;
@@ -1195,8 +1208,16 @@ static int nn_batch_grad(Ctx *c, const float *x, const float *t, const float *tn
   A *h1 = reinterpret_cast<A *>(tb.h1), *h2 = reinterpret_cast<A *>(tb.h2), *h3 = reinterpret_cast<A *>(tb.h3);
   const unsigned g = (unsigned)((ncol + kNnCpb - 1) / kNnCpb);
   Nbrs nb{nullptr, nullptr, nx, ny};
-  nn_front_kernel<A, float><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, x, nullptr, nullptr, ncol, L,
-                                                                          kNnCpb, h1, h2);
+  if (sizeof(A) == 2) {   // BF16 storage: the column-local layers on the tensor cores, h1 kept
+    const int64_t nrows = (int64_t)ncol * (L + 2);
+    if (nrows > INT32_MAX - 2 * kTcM) return fail(c, HMG_ERR_INVALID_ARG, "training batch too large");
+    nn_front_tc_kernel<float, true><<<grid_for(nrows, kTcM), 128, kTcSmem, c->stream>>>(
+        c->nn_w, static_cast<const __nv_bfloat16 *>(c->nn_bimg), x, nullptr, nullptr, ncol, L,
+        reinterpret_cast<__nv_bfloat16 *>(h2), nullptr, c->state + 3, reinterpret_cast<__nv_bfloat16 *>(h1));
+  } else {
+    nn_front_kernel<A, float><<<g, 128, front_smem(kNnCpb, L), c->stream>>>(c->nn_w, x, nullptr, nullptr, ncol, L,
+                                                                            kNnCpb, h1, h2);
+  }
   nn_back_kernel<A, float><<<g, 128, back_smem(kNnCpb, L), c->stream>>>(
       c->nn_w, h2, nb, ncol, L, kNnCpb, nullptr, nullptr, nullptr, h3, t, tn, P, 1.f / (float)nsamp, tb.gy,
       tb.loss_part);
