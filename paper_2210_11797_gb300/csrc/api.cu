@@ -720,7 +720,10 @@ int hmg_apply_coarse_model(hmg_ctx *c, const double *bbar, double *out, int32_t 
   if (!c->nn_w) return fail(c, HMG_ERR_NOT_READY, "no coarse model set");
   if ((st = finish(c, apply_coarse_model(c, bbar, out, mode)))) return st;
   st = check_wait_flag(c);
-  if (st == HMG_ERR_TIMEOUT && mode == 0) c->nn_tc_off = true;   // see hmg_apply_coarse_model
+  if (st == HMG_ERR_TIMEOUT && mode == 0 && !c->nn_tc_off) {   // see hmg_apply_coarse_model
+    drop_graph(c);   // captured solve graphs hold the tensor-core launches
+    c->nn_tc_off = true;
+  }
   return st;
 }
 

@@ -104,6 +104,10 @@ struct HoData {
   float *S32 = nullptr, *hw32 = nullptr, *zf32 = nullptr, *gamma32 = nullptr;
 };
 
+// A process-wide counter: a context takes a new value when it is created and whenever its
+// captured launches go stale, so (context address, generation) never names two states.
+uint64_t next_graph_gen();
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -158,6 +162,18 @@ struct Ctx {
     const void *Rub, *Rpi, *lam;
     hmg_options opt;
   } graph_key{};
+  uint64_t graph_gen = next_graph_gen();
+  // the batched-solve graph this context holds as the first context of a batch, and what it
+  // was captured for: each member's address, generation, vectors and options
+  struct BatchMember {
+    const void *ctx;
+    uint64_t gen;
+    const void *Rub, *Rpi, *lam;
+    hmg_options opt;
+  };
+  std::vector<BatchMember> batch_key;
+  cudaGraphExec_t batch_exec = nullptr;
+  cudaGraph_t batch_graph = nullptr;
   // autotuned launch shapes (0 = default): columns per block of the line sweep and of the
   // pressure smoother on each level
   // launch shapes chosen by autotune, [0] for the FP64 kernels, [1] for the FP32 preconditioner's

@@ -11,6 +11,7 @@
 // costs one graph launch and one synchronisation. Batched solves put one such branch per
 // context into a single graph. With graph = 0 (or profile = 1) the host drives the loop.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -412,6 +413,19 @@ static bool same_key(const Ctx::GraphKey &k, const double *Rub, const double *Rp
   return k.Rub == Rub && k.Rpi == Rpi && k.lam == lam && std::memcmp(&k.opt, &o, sizeof(o)) == 0;
 }
 
+uint64_t next_graph_gen() {
+  static std::atomic<uint64_t> gen{0};
+  return ++gen;
+}
+
+static void drop_batch_graph(Ctx *c) {
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  if (c->batch_graph) cudaGraphDestroy(c->batch_graph);
+  c->batch_exec = nullptr;
+  c->batch_graph = nullptr;
+  c->batch_key.clear();
+}
+
 void drop_graph(Ctx *c) {
   // an enqueued (async_stats) solve may still be running the graph: let it finish first
   if (c->graph_exec && c->stats_pending) cudaEventSynchronize(c->as_e1);
@@ -419,6 +433,10 @@ void drop_graph(Ctx *c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
+  // batch graphs that hold this context's launches (its own, or another context's) no longer
+  // match its generation
+  c->graph_gen = next_graph_gen();
+  drop_batch_graph(c);
 }
 
 static int ensure_solve_graph(Ctx *c, const double *Rub, const double *Rpi, double *x) {
@@ -462,7 +480,11 @@ static int fill_stats(Ctx *c, hmg_solve_stats *st, float ms) {
     status = HMG_ERR_TIMEOUT;
     // with a learned coarse solve the wait may have been the tensor-core layer's: the context
     // runs the network on the CUDA cores from now on
-    if (c->opt.coarse == HMG_COARSE_LEARNED || c->opt.coarse == HMG_COARSE_LEARNED_VCYCLE) c->nn_tc_off = true;
+    // (captured solve graphs hold the tensor-core launches: they are captured again)
+    if ((c->opt.coarse == HMG_COARSE_LEARNED || c->opt.coarse == HMG_COARSE_LEARNED_VCYCLE) && !c->nn_tc_off) {
+      drop_graph(c);
+      c->nn_tc_off = true;
+    }
   }
   if (st) {
     const double bb = c->scal_host[Scal::BB];
@@ -593,10 +615,8 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
     if (ctxs[i]->opt.krylov != HMG_KRYLOV_BICGSTAB || ctxs[i]->collect_x ||
         ctxs[i]->opt.coarse == HMG_COARSE_KRYLOV_EXACT || ctxs[i]->opt.coarse == HMG_COARSE_KRYLOV_APPROX)
       return fail(c0, HMG_ERR_INVALID_ARG, "batched solves take BiCGStab contexts without pair collection");
-  cudaGraph_t g = nullptr;
-  HMG_CUDA(c0, cudaGraphCreate(&g, 0));
-  int s = HMG_OK;
-  for (int i = 0; i < n && !s; ++i) {
+  bool profile = false;
+  for (int i = 0; i < n; ++i) {
     Ctx *c = ctxs[i];
     c->marks.clear();
     c->ev_next = 0;
@@ -605,13 +625,41 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
       cudaEventSynchronize(c->as_e1);
       c->stats_pending = false;
     }
-    s = add_solve_branch(c, g, Rub[i], Rpi[i], lambda[i]);
-    if (s && c != c0) c0->err = c->err;
+    profile = profile || c->opt.profile;
   }
+  // the instantiated graph is kept on the first context while the batch (contexts, their
+  // generations, vectors and options) stays the same; a profiled batch is captured afresh
+  // each call, since its event marks are recorded at capture
+  bool cached = !profile && c0->batch_exec && (int)c0->batch_key.size() == n;
+  for (int i = 0; cached && i < n; ++i) {
+    const Ctx::BatchMember &k = c0->batch_key[i];
+    const Ctx *c = ctxs[i];
+    cached = k.ctx == c && k.gen == c->graph_gen && k.Rub == Rub[i] && k.Rpi == Rpi[i] && k.lam == lambda[i] &&
+             std::memcmp(&k.opt, &c->opt, sizeof(hmg_options)) == 0;
+  }
+  int s = HMG_OK;
+  cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
-  if (!s) {
-    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-    if (e != cudaSuccess) s = cuda_fail(c0, e, "cudaGraphInstantiate (batched)");
+  if (cached) {
+    ex = c0->batch_exec;
+  } else {
+    drop_batch_graph(c0);
+    HMG_CUDA(c0, cudaGraphCreate(&g, 0));
+    for (int i = 0; i < n && !s; ++i) {
+      Ctx *c = ctxs[i];
+      s = add_solve_branch(c, g, Rub[i], Rpi[i], lambda[i]);
+      if (s && c != c0) c0->err = c->err;
+    }
+    if (!s) {
+      cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+      if (e != cudaSuccess) s = cuda_fail(c0, e, "cudaGraphInstantiate (batched)");
+    }
+    if (!s && !profile) {
+      c0->batch_graph = g;
+      c0->batch_exec = ex;
+      for (int i = 0; i < n; ++i)
+        c0->batch_key.push_back({ctxs[i], ctxs[i]->graph_gen, Rub[i], Rpi[i], lambda[i], ctxs[i]->opt});
+    }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!s) {
@@ -627,8 +675,11 @@ int krylov_solve_batched(hmg_ctx *const *ctxs, int n, const double *const *Rub,
   if (!s) cudaEventElapsedTime(&ms, e0, e1);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (ex) cudaGraphExecDestroy(ex);
-  cudaGraphDestroy(g);
+  if (!(ex && ex == c0->batch_exec)) {   // not kept: a profiled batch, or one that failed
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+  }
+  if (s) drop_batch_graph(c0);
   if (s) return s;
   int worst = HMG_OK;
   for (int i = 0; i < n; ++i) {

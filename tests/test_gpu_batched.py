@@ -107,3 +107,59 @@ def test_batch_of_the_seed3_draw():
             assert np.linalg.norm(B - ora.S @ lo) / np.linalg.norm(B) <= 1.05e-6
     for s in solvers:
         s.close()
+
+
+def test_batch_graph_is_kept_and_captured_again_when_stale():
+    """The instantiated batch graph is reused while the contexts, their vectors and options
+    stay the same; new values in the same vectors are read at launch; a changed option, launch
+    shape, member order or vector makes it capture again. Every answer equals the member's
+    single solve."""
+    from paper_2210_11797_gb300.hmg import Solver, solve_batched
+    ws = _workloads()[1:]
+    solvers = [Solver(w.hier, w.coeffs, tol=1e-9, precision="mixed") for w in ws]
+    Rubs = [_cuda(w.Rub.ravel()) for w in ws]
+    Rpis = [_cuda(w.Rpi) for w in ws]
+    lams = [torch.empty(s.ntrace, dtype=torch.float64, device="cuda") for s in solvers]
+
+    def check_against_single(lams_, stats_):
+        for s, r, p, lam, st in zip(solvers, Rubs, Rpis, lams_, stats_):
+            single, st1 = s.solve(r, p, check=False)
+            assert st["status"] == st1["status"] and st["iterations"] == st1["iterations"]
+            assert torch.equal(lam, single)
+
+    _l, st_a = solve_batched(solvers, Rubs, Rpis, lams)
+    first = [l.clone() for l in lams]
+    _l, st_b = solve_batched(solvers, Rubs, Rpis, lams)          # the kept graph
+    assert all(torch.equal(a, b) for a, b in zip(first, lams))
+    assert [s["iterations"] for s in st_a] == [s["iterations"] for s in st_b]
+    check_against_single(lams, st_b)
+    # new values in the same vectors: the kept graph reads them (the answer scales by 2 exactly)
+    Rubs[0].mul_(2.0)
+    Rpis[0].mul_(2.0)
+    _l, st_c = solve_batched(solvers, Rubs, Rpis, lams)
+    assert torch.equal(lams[0], 2.0 * first[0]) and st_c[0]["iterations"] == st_a[0]["iterations"]
+    check_against_single(lams, st_c)
+    # a changed option of one member
+    solvers[1].set_options(max_iter=2, tol=1e-14)
+    _l, st_d = solve_batched(solvers, Rubs, Rpis, lams, check=False)
+    assert st_d[1]["status"] == "not_converged" and st_d[1]["iterations"] == 2
+    assert st_d[0]["status"] == st_d[2]["status"] == "ok"
+    check_against_single(lams, st_d)
+    solvers[1].set_options(max_iter=500, tol=1e-9)
+    # a changed launch shape of one member (the block form with 2 columns per block)
+    sw, mg = solvers[2].launch_shapes()
+    solvers[2].set_launch_shapes((2, 128), [(2, 128) for _ in mg])
+    _l, st_e = solve_batched(solvers, Rubs, Rpis, lams)
+    check_against_single(lams, st_e)
+    # another order of the same members, then a member replaced by a new context
+    order = [2, 0, 1]
+    lo = [lams[i] for i in order]
+    _l, st_f = solve_batched([solvers[i] for i in order], [Rubs[i] for i in order],
+                             [Rpis[i] for i in order], lo)
+    assert [s["iterations"] for s in st_f] == [st_e[i]["iterations"] for i in order]
+    solvers[0].close()
+    solvers[0] = Solver(ws[0].hier, ws[0].coeffs, tol=1e-9, precision="mixed")
+    _l, st_g = solve_batched(solvers, Rubs, Rpis, lams)
+    check_against_single(lams, st_g)
+    for s in solvers:
+        s.close()
