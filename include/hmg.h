@@ -263,7 +263,11 @@ int hmg_solve_stats_get(hmg_ctx *ctx, hmg_solve_stats *stats);
  * B_lambda -> a device-side WHILE loop of BiCGStab iterations -> the final residual, the
  * branches running concurrently. Rub[i], Rpi[i], lambda[i] are device pointers of context
  * i; stats (host, may be NULL) has n entries. Returns the first non-OK status of any solve
- * (details in that solve's stats). The graph runs on ctxs[0]'s stream. */
+ * (details in that solve's stats). The graph runs on ctxs[0]'s stream. ctxs[0] keeps the
+ * instantiated graph and launches it again while the next call passes the same contexts in
+ * the same order, the same vector pointers and unchanged options and launch shapes (new
+ * values in those vectors are read at launch); any change captures it again. Destroying a
+ * context releases the batch graph it holds. */
 int hmg_solve_batched(hmg_ctx *const *ctxs, int32_t n, const double *const *Rub,
                       const double *const *Rpi, double *const *lambda, hmg_solve_stats *stats);
 
