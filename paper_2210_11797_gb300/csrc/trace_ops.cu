@@ -197,6 +197,12 @@ int launch_reconstruct(Ctx *c, const double *lam, const double *Rub, const doubl
 // On the lambda^z rows the update is evaluated as (1 - omega) lam_in + omega (S^zz_c)^-1
 // (b - (S - D) lam_in), equal in exact arithmetic: eight couplings instead of eleven in the
 // residual (the sweep is bound by the FP64 issue rate) and three fewer coefficients read.
+// lambda^h rows per thread of the sweep (block-strided): four in a sweep from zero (two loads
+// and a store per row, no gathers), two in an FP32 sweep (it waits on the gathered iterate
+// values rather than on arithmetic), one in an FP64 sweep (FP64 issue-bound)
+template <typename T, bool ZERO>
+constexpr int kSweepHRows = ZERO ? 4 : (sizeof(T) == 4 ? 2 : 1);
+
 struct SweepArgs {
   TraceDims d;
   int ncol, cpb, nzb;
@@ -254,11 +260,17 @@ __global__ void __launch_bounds__(256)
       lam_out[row] = (Tout)(ZERO ? v : fma((T)a.keep, lam_in[row], v));
     }
   } else {
-    const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
-    if (row >= d.NH) return;
-    T r = (T)__ldg(b + row);
-    if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
-    lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
+    constexpr int HR = kSweepHRows<T, ZERO>;
+    const int64_t base = (int64_t)(blockIdx.x - a.nzb) * blockDim.x * HR + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < HR; ++j) {
+      const int64_t row = base + (int64_t)j * blockDim.x;
+      if (row < d.NH) {
+        T r = (T)__ldg(b + row);
+        if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
+        lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
+      }
+    }
   }
 }
 
@@ -301,11 +313,17 @@ __global__ void __launch_bounds__(256)
       }
     }
   } else {
-    const int64_t row = (int64_t)(blockIdx.x - a.nzb) * blockDim.x + threadIdx.x;
-    if (row >= d.NH) return;
-    T r = (T)__ldg(b + row);
-    if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
-    lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
+    constexpr int HR = kSweepHRows<T, ZERO>;
+    const int64_t base = (int64_t)(blockIdx.x - a.nzb) * blockDim.x * HR + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < HR; ++j) {
+      const int64_t row = base + (int64_t)j * blockDim.x;
+      if (row < d.NH) {
+        T r = (T)__ldg(b + row);
+        if (!ZERO) r = s_row_h<T, T, T, true>(S, lam_in, a.stencil, d, row, r);
+        lam_out[row] = (Tout)(ZERO ? r * __ldg(hw + row) : fma(r, __ldg(hw + row), lam_in[row]));
+      }
+    }
   }
 }
 
@@ -334,7 +352,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
       a.keep = 1.0 - c->factor_omega;
       a.cpb = 8;
       a.nzb = (int)grid_for((int64_t)f.ncol * 32, 256);
-      const unsigned nhb = grid_for(f.nth, 256);
+      const unsigned nhb = grid_for(f.nth, 256 * kSweepHRows<T, ZERO>);
       Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
       const int L1 = f.nlev + 1;
       auto go = [&](auto kern) {
@@ -359,7 +377,7 @@ static int launch_sweep(Ctx *c, const Tb *b, const T *lam_in, Tout *lam_out, int
   int threads = ((a.cpb * (f.nlev + 1) + 31) / 32) * 32;
   if (threads > tmax) threads = tmax;
   if (threads < ((a.cpb + 31) / 32) * 32) threads = ((a.cpb + 31) / 32) * 32;   // a lane per column
-  const unsigned nhb = grid_for(f.nth, threads);
+  const unsigned nhb = grid_for(f.nth, (int64_t)threads * kSweepHRows<T, ZERO>);
   const size_t smem = (size_t)3 * a.cpb * ((f.nlev + 1) | 1) * sizeof(T);
   Prof prof(c, ZERO ? kCompPresmooth : kCompSweep);
   sweep_kernel<T, Tb, Tout, ZERO><<<a.nzb + nhb, threads, smem, c->stream>>>(
