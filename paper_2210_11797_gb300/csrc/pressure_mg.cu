@@ -283,13 +283,21 @@ __device__ __forceinline__ void inject_cell(const T *__restrict__ x, const T *__
   x_out[K] = ldv<COH>(x + K) + ldv<COH>(e + (int64_t)__ldg(parent + c) * L + k);
 }
 
+constexpr int kInjectCells = 4;
+
 template <typename T>
 __global__ void mg_inject_kernel(const T *__restrict__ x, const T *__restrict__ e,
                                  const int32_t *__restrict__ parent, int L, int64_t ncell,
                                  T *__restrict__ x_out) {
-  const int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (K >= ncell) return;
-  inject_cell<T, false>(x, e, parent, L, K, x_out);
+  // kInjectCells cells per thread, block-strided: a few loads and one add per cell, so more
+  // cells per thread keep more loads in flight
+  const int64_t base = blockIdx.x * (int64_t)blockDim.x * kInjectCells + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kInjectCells; ++j) {
+    const int64_t K = base + (int64_t)j * blockDim.x;
+    if (K >= ncell) break;
+    inject_cell<T, false>(x, e, parent, L, K, x_out);
+  }
 }
 
 template <typename T, bool COH>
@@ -809,7 +817,7 @@ static int vcycle_impl(Ctx *c, const T *b0, T **x_out, const T *x0, const T *R, 
       if ((st = inject_smooth<T>(c, l, b[l], x[l], x[l + 1], other))) return st;
       done = 1;
     } else {
-      mg_inject_kernel<T><<<grid_for(lv.ncell, 256), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,
+      mg_inject_kernel<T><<<grid_for(lv.ncell, 256 * kInjectCells), 256, 0, c->stream>>>(x[l], x[l + 1], lv.parent, lv.nlev,
                                                                           lv.ncell, other);
       HMG_CUDA(c, cudaGetLastError());
     }

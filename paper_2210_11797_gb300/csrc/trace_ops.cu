@@ -421,29 +421,37 @@ __global__ void restrict_kernel(const T *__restrict__ R, const T *__restrict__ g
 }
 
 // ---- lam_out = lam_in + P dPi (Algorithm 2 line 7) ---------------------------------------
+constexpr int kProlongRows = 4;
+
 template <typename T>
 __global__ void prolong_kernel(const T *__restrict__ lam_in, const T *__restrict__ dpi,
                                T *__restrict__ lam_out, const TraceDims d,
                                const int32_t *__restrict__ stencil) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= d.NT) return;
-  // lam_in + (1/2)(a + b) as one FMA: the halving is exact, so it rounds as the add did
-  const T li = lam_in[row];
-  T out;
-  if (row < d.NH) {   // 32-bit index arithmetic (row indices stay below 2^31)
-    const unsigned ru = (unsigned)row, Lu = (unsigned)d.L;
-    const int e = (int)(ru / Lu), k = (int)(ru - (unsigned)e * Lu);
-    out = fma((T)0.5, dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e) * d.L + k] +
-                          dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e + 1) * d.L + k], li);
-  } else {
-    const unsigned zr = (unsigned)(row - d.NH), L1 = (unsigned)d.L + 1u;
-    const int c = (int)(zr / L1), k = (int)(zr - (unsigned)c * L1);
-    const int64_t K = (int64_t)c * d.L + k;
-    if (k == 0) out = li + dpi[K];
-    else if (k == d.L) out = li + dpi[K - 1];
-    else out = fma((T)0.5, dpi[K - 1] + dpi[K], li);
+  // kProlongRows rows per thread, block-strided: few operations per row, so the kernel waits on
+  // its loads and more rows per thread keep more of them in flight
+  const int64_t base = blockIdx.x * (int64_t)blockDim.x * kProlongRows + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kProlongRows; ++j) {
+    const int64_t row = base + (int64_t)j * blockDim.x;
+    if (row >= d.NT) break;
+    // lam_in + (1/2)(a + b) as one FMA: the halving is exact, so it rounds as the add did
+    const T li = lam_in[row];
+    T out;
+    if (row < d.NH) {   // 32-bit index arithmetic (row indices stay below 2^31)
+      const unsigned ru = (unsigned)row, Lu = (unsigned)d.L;
+      const int e = (int)(ru / Lu), k = (int)(ru - (unsigned)e * Lu);
+      out = fma((T)0.5, dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e) * d.L + k] +
+                            dpi[(int64_t)__ldg(stencil + 8 * (int64_t)e + 1) * d.L + k], li);
+    } else {
+      const unsigned zr = (unsigned)(row - d.NH), L1 = (unsigned)d.L + 1u;
+      const int c = (int)(zr / L1), k = (int)(zr - (unsigned)c * L1);
+      const int64_t K = (int64_t)c * d.L + k;
+      if (k == 0) out = li + dpi[K];
+      else if (k == d.L) out = li + dpi[K - 1];
+      else out = fma((T)0.5, dpi[K - 1] + dpi[K], li);
+    }
+    lam_out[row] = out;
   }
-  lam_out[row] = out;
 }
 
 template <typename Tin, typename Tout>
@@ -534,7 +542,7 @@ static int two_level(Ctx *c, const double *r, double *z) {
   // line 7: lambda += P dPi
   {
     Prof pp(c, kCompProlong);
-    prolong_kernel<T><<<grid_for(f.ntrace, 256), 256, 0, c->stream>>>(w1, dpi, w2, d, f.edge_stencil);
+    prolong_kernel<T><<<grid_for(f.ntrace, 256 * kProlongRows), 256, 0, c->stream>>>(w1, dpi, w2, d, f.edge_stencil);
   }
   HMG_CUDA(c, cudaGetLastError());
   // line 8: postsmooth
