@@ -284,8 +284,11 @@ int hmg_autotune(hmg_ctx *ctx);
  * memory limit); columns -1 selects one warp per column (Thomas recurrences as a warp scan:
  * the same iterate up to rounding order): for a smoother level of at most 128 layers in both
  * precisions, for the sweep (at most 127 layers) in the FP32 preconditioner's kernels only, the
- * FP64 sweep taking the default; hmg_get_launch_shapes reports the FP64 shapes. hmg_set_launch_shapes rejects other columns
- * outside 1..64 and threads other than 0, 128 and 256. */
+ * FP64 sweep taking the default. hmg_get_launch_shapes reports the shapes of the kernels the
+ * preconditioner runs: the FP32 kernels' under precision mixed, else the FP64 kernels';
+ * hmg_set_launch_shapes sets both (so the shapes read from a context set the same kernels'
+ * shapes on another context of the same mesh and precision). hmg_set_launch_shapes rejects
+ * other columns outside 1..64 and threads other than 0, 128 and 256. */
 int hmg_get_launch_shapes(hmg_ctx *ctx, int32_t *sweep, int32_t *mg, int32_t nmg);
 int hmg_set_launch_shapes(hmg_ctx *ctx, const int32_t *sweep, const int32_t *mg, int32_t nmg);
 

@@ -632,11 +632,13 @@ int hmg_autotune(hmg_ctx *c) {
 int hmg_get_launch_shapes(hmg_ctx *c, int32_t *sweep, int32_t *mg, int32_t nmg) {
   if (!c || !sweep || (nmg > 0 && !mg)) return HMG_ERR_INVALID_ARG;
   if (!c->have_mesh || nmg != c->nmg) return fail(c, HMG_ERR_INVALID_ARG, "nmg must equal the mesh's levels");
-  sweep[0] = c->tune_sweep_cpb[0];
-  sweep[1] = c->tune_sweep_threads[0];
+  // the shapes of the preconditioner's kernels: FP32 ones under precision mixed, else FP64
+  const int p = c->opt.precision == HMG_PRECISION_MIXED ? 1 : 0;
+  sweep[0] = c->tune_sweep_cpb[p];
+  sweep[1] = c->tune_sweep_threads[p];
   for (int l = 0; l < nmg; ++l) {
-    mg[2 * l] = c->tune_mg_cpb[0][l];
-    mg[2 * l + 1] = c->tune_mg_threads[0][l];
+    mg[2 * l] = c->tune_mg_cpb[p][l];
+    mg[2 * l + 1] = c->tune_mg_threads[p][l];
   }
   return HMG_OK;
 }
