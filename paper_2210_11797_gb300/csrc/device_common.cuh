@@ -266,6 +266,54 @@ __device__ __forceinline__ TA s_row_z_off(const TS *__restrict__ S, const TX *__
   return acc;
 }
 
+// The serial Thomas recurrences of one column held in shared memory (one thread): on entry
+// s[o + k] = the scaled right-hand side, lo[o + k] the sub-diagonal / pivot (k >= 1), up[o + k]
+// the super-diagonal / pivot (k <= n - 2); on return s[o + k] = the solution. Forward
+// y_k = s_k - lo_k y_{k-1}, backward x_k = y_k - up_k x_{k+1}, one FMA per row each, in the
+// order of the plain loops; the loads of CH rows are issued ahead of their FMAs, so that only
+// the FMA latency stays on the dependent chain.
+template <typename T, int CH = 8>
+__device__ __forceinline__ void thomas_smem(T *s, const T *lo, const T *up, int o, int n) {
+  T y = s[o];
+  int k = 1;
+  for (; k + CH - 1 < n; k += CH) {
+    T l[CH], r[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      l[j] = lo[o + k + j];
+      r[j] = s[o + k + j];
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      y = fma(-l[j], y, r[j]);
+      s[o + k + j] = y;
+    }
+  }
+  for (; k < n; ++k) {
+    y = fma(-lo[o + k], y, s[o + k]);
+    s[o + k] = y;
+  }
+  T x = y;
+  k = n - 2;
+  for (; k >= CH - 1; k -= CH) {
+    T u[CH], r[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      u[j] = up[o + k - j];
+      r[j] = s[o + k - j];
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      x = fma(-u[j], x, r[j]);
+      s[o + k - j] = x;
+    }
+  }
+  for (; k >= 0; --k) {
+    x = fma(-up[o + k], x, s[o + k]);
+    s[o + k] = x;
+  }
+}
+
 // A tridiagonal solve with precomputed Thomas factors by one warp (n <= 32 M rows; lane j holds
 // rows j M .. j M + M - 1): on entry s = the scaled right-hand side (r omega / pivot), lo the
 // sub-diagonal / pivot (0 on row 0), up the super-diagonal / pivot (0 on row n - 1); on return

@@ -194,19 +194,7 @@ __device__ __forceinline__ void smooth_block_src(const MGArgs &a, const T *__res
     scp[j] = __ldg(hcp + K);
   }
   __syncthreads();
-  if ((int)threadIdx.x < nc) {
-    const int o = threadIdx.x * ld;
-    T y = sr[o];
-    for (int k = 1; k < a.L; ++k) {
-      y = fma(-sl[o + k], y, sr[o + k]);
-      sr[o + k] = y;
-    }
-    T xk = y;
-    for (int k = a.L - 2; k >= 0; --k) {
-      xk = fma(-scp[o + k], xk, sr[o + k]);
-      sr[o + k] = xk;
-    }
-  }
+  if ((int)threadIdx.x < nc) thomas_smem(sr, sl, scp, (int)threadIdx.x * ld, a.L);
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int cl = i / a.L, k = i % a.L;

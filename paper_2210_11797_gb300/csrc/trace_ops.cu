@@ -240,19 +240,7 @@ __global__ void __launch_bounds__(256)
       scp[j] = __ldg(zcp + (row - d.NH));
     }
     __syncthreads();
-    if ((int)threadIdx.x < nc) {
-      const int o = threadIdx.x * ld;
-      T y = sr[o];
-      for (int k = 1; k < L1; ++k) {
-        y = fma(-sl[o + k], y, sr[o + k]);
-        sr[o + k] = y;
-      }
-      T xk = y;
-      for (int k = L1 - 2; k >= 0; --k) {
-        xk = fma(-scp[o + k], xk, sr[o + k]);
-        sr[o + k] = xk;
-      }
-    }
+    if ((int)threadIdx.x < nc) thomas_smem<T, sizeof(T) == 4 ? 8 : 1>(sr, sl, scp, (int)threadIdx.x * ld, L1);
     __syncthreads();
     for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
       const int64_t row = base + i;
