@@ -696,7 +696,8 @@ int autotune(Ctx *c) {
       float ms = 0.f;
       if (!(st = time_sweep_cpb(c, -1, 256, pm, &ms)) && ms < best_ms) { best_ms = ms; best = -1; best_t = 256; }
     }
-    if (!st) { c->tune_sweep_cpb[pm] = best; c->tune_sweep_threads[pm] = best_t; }
+    // threads are not a parameter of the warp-per-column form: 0, as hmg_set_launch_shapes stores
+    if (!st) { c->tune_sweep_cpb[pm] = best; c->tune_sweep_threads[pm] = best == -1 ? 0 : best_t; }
     for (int l = 0; l < c->nmg && !st; ++l) {
       const int mmax = mg_cpb_limit(c->lv[l].nlev);
       int mbest = mmax < 32 ? mmax : 32, mbest_t = 256;
@@ -714,7 +715,7 @@ int autotune(Ctx *c) {
         float ms = 0.f;
         if (!(st = time_mg_cpb(c, l, -1, 256, pm, &ms)) && ms < mbest_ms) { mbest_ms = ms; mbest = -1; mbest_t = 256; }
       }
-      if (!st) { c->tune_mg_cpb[pm][l] = mbest; c->tune_mg_threads[pm][l] = mbest_t; }
+      if (!st) { c->tune_mg_cpb[pm][l] = mbest; c->tune_mg_threads[pm][l] = mbest == -1 ? 0 : mbest_t; }
     }
     // then one coordinate-descent pass over the levels, coarsest first, timing whole
     // V-cycles: the fused restriction / injection sweeps of the small levels take the level's
@@ -726,7 +727,7 @@ int autotune(Ctx *c) {
       if ((st = time_vcycle(c, pm, &bms))) break;
       for (int cand : {32, 64, 16, 8, 4, 2, 1, -1})
         for (int thr : {256, 128}) {
-          if (cand > mmax || st || (cand == bc && thr == bt)) continue;
+          if (cand > mmax || st || (cand == bc && (thr == bt || cand == -1))) continue;
           if (cand == -1 && (thr != 256 || c->lv[l].nlev > 128)) continue;   // the warp form
           c->tune_mg_cpb[pm][l] = cand;
           c->tune_mg_threads[pm][l] = thr;
@@ -735,7 +736,7 @@ int autotune(Ctx *c) {
           if (ms < 0.98f * bms) { bms = ms; bc = cand; bt = thr; }   // 2%: beyond the timing noise
         }
       c->tune_mg_cpb[pm][l] = bc;
-      c->tune_mg_threads[pm][l] = bt;
+      c->tune_mg_threads[pm][l] = bc == -1 ? 0 : bt;
     }
   }
   c->opt.profile = profile;

@@ -224,6 +224,30 @@ def test_autotune_after_a_captured_solve_changes_nothing_but_speed():
     gpu.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tuned_shapes_carry_over_to_a_context_of_the_same_mesh(precision):
+    """hmg_get_launch_shapes reports the shapes of the kernels the preconditioner runs (the FP32
+    kernels' under precision mixed): applied to a second context of the same mesh and
+    precision, they make the same launches, so its solve equals the tuned context's bit for bit."""
+    from paper_2210_11797_gb300.hmg import Solver
+    w = I.cubed_sphere(16, 12, seed=13)
+    a = Solver(w.hier, w.coeffs, tol=1e-8, precision=precision)
+    b = Solver(w.hier, w.coeffs, tol=1e-8, precision=precision)
+    try:
+        a.autotune()
+        shapes = a.launch_shapes()
+        b.set_launch_shapes(*shapes)
+        assert b.launch_shapes() == shapes
+        Rub, Rpi = _cuda(w.Rub.ravel()), _cuda(w.Rpi)
+        lam_a, st_a = a.solve(Rub, Rpi)
+        lam_b, st_b = b.solve(Rub, Rpi)
+        assert st_a["status"] == st_b["status"] == "ok" and st_a["iterations"] == st_b["iterations"]
+        np.testing.assert_array_equal(_np(lam_a), _np(lam_b))
+    finally:
+        a.close()
+        b.close()
+
+
 def test_tallest_columns_solve_and_one_more_layer_is_rejected():
     """The layer limit (2045: one column's three Thomas arrays fill a block's 48 KB of shared
     memory): a 4 x 4 x 2045 Helmholtz box solves (one column per block in the sweep and the
