@@ -2,7 +2,8 @@
 workload, on CPU: one JSON line with the contract's keys, impl "reference", the workload's
 own tolerance and the same config dict as the GPU arm's, full solves counted honestly (at
 most one warm-up), and e2e / cpu_baseline describing the same run. Also the multi-core leg of
-the oracle on the batch (processes started together at a barrier)."""
+the oracle on the batch (processes started together at a barrier), and the --shapes file that
+lets a profiler run reuse the launch shapes of the plain run."""
 import json
 import os
 import subprocess
@@ -38,3 +39,40 @@ def test_oracle_batch_leg_on_two_cores(repo_root):
     assert r["cores"] == 2 and r["all_ok"] and r["sample"] == ["C12xL50", "C32xL10"]
     assert r["value"] > 0 and r["wall_s"] > 0 and len(r["iterations"]) == 2
     assert all(i > 0 for i in r["iterations"])
+
+
+class _ShapesStub:
+    """Stands in for a Solver: records autotune and set_launch_shapes calls."""
+
+    def __init__(self, tuned):
+        self.tuned, self.calls, self.shapes = tuned, [], None
+
+    def autotune(self):
+        self.calls.append("autotune")
+        self.shapes = self.tuned
+
+    def launch_shapes(self):
+        return self.shapes
+
+    def set_launch_shapes(self, sweep, mg):
+        self.calls.append("set")
+        self.shapes = (tuple(sweep), [tuple(x) for x in mg])
+
+
+def test_shapes_file_written_by_the_plain_run_and_applied_by_the_profiled_run(repo_root, tmp_path):
+    """bench.py --shapes: the first run autotunes and writes its launch shapes; a second run of
+    the same command applies them without tuning (so a profiler run times the same kernels);
+    without the option every run autotunes."""
+    sys.path.insert(0, repo_root)
+    import bench
+    tuned = ((32, 256), [(32, 256), (16, 128), (-1, 0)])
+    path = str(tmp_path / "shapes.json")
+    first = _ShapesStub(tuned)
+    bench.tune_shapes(first, path)
+    assert first.calls == ["autotune"] and os.path.exists(path)
+    second = _ShapesStub(((1, 1), []))
+    bench.tune_shapes(second, path)
+    assert second.calls == ["set"] and second.launch_shapes() == tuned
+    plain = _ShapesStub(tuned)
+    bench.tune_shapes(plain, None)
+    assert plain.calls == ["autotune"]
