@@ -287,7 +287,8 @@ int hmg_autotune(hmg_ctx *ctx);
  * FP64 sweep taking the default. hmg_get_launch_shapes reports the shapes of the kernels the
  * preconditioner runs: the FP32 kernels' under precision mixed, else the FP64 kernels';
  * hmg_set_launch_shapes sets both (so the shapes read from a context set the same kernels'
- * shapes on another context of the same mesh and precision). hmg_set_launch_shapes rejects
+ * shapes on another context of the same mesh and precision; columns -1 come with threads 0,
+ * which that form does not use). hmg_set_launch_shapes rejects
  * other columns outside 1..64 and threads other than 0, 128 and 256. */
 int hmg_get_launch_shapes(hmg_ctx *ctx, int32_t *sweep, int32_t *mg, int32_t nmg);
 int hmg_set_launch_shapes(hmg_ctx *ctx, const int32_t *sweep, const int32_t *mg, int32_t nmg);
